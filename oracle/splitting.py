@@ -309,7 +309,8 @@ def lambda_reg_closed_form(n: int, p: int, dirichlet) -> np.ndarray:
     t = h * alpha
     sk = cardinal_symbol(2 * p - 1, p - 1, t)
     sm = cardinal_symbol(2 * p + 1, p, t)
-    return (2.0 - 2.0 * np.cos(t)) / h ** 2 * sk / sm
+    # 2 - 2 cos t written as 4 sin^2(t/2): the same number without cancellation
+    return 4.0 * np.sin(0.5 * t) ** 2 / h ** 2 * sk / sm
 
 
 def dtilde_closed_form(n: int, p: int, dirichlet) -> np.ndarray:
