@@ -23,7 +23,7 @@ Readings of the paper taken here (each one is listed in the design doc):
   subspace gives the same preconditioner.)
 * D~_reg is computed numerically as (U^T V_reg^T M V_reg U)^{1/2} (end of
   Section 6). Its closed form is derived from the periodic symbols (see
-  ``dtilde_closed_form``); Lemma 3's Lambda_reg is read with 1/h^2.
+  ``dtilde_closed_form``). Lambda_reg is taken from Lemma 3, read with 1/h^2.
 """
 
 from __future__ import annotations
@@ -260,11 +260,13 @@ def axis_split(n: int, p: int, dirichlet=(0, 1)) -> AxisSplit:
     K = Kf[np.ix_(keep, keep)]
     V = V_reg_matrix(n, p, D)
     U = U_reg(n, p, D)
-    # D~_reg = (U^T V_reg^T M V_reg U)^{1/2} and Lambda_reg (end of Section 6)
+    # D~_reg = (U^T V_reg^T M V_reg U)^{1/2} (end of Section 6). Lambda_reg from
+    # Lemma 3: the numeric diag(U^T V_reg^T K V_reg U) / D~^2 of eq. "Lambda reg"
+    # loses ~1e-13 on the lowest modes to the conditioning of K (it is kept as
+    # a pin in the tests).
     MU = U.T @ (V.T @ M @ V) @ U
-    KU = U.T @ (V.T @ K @ V) @ U
     Dt = np.sqrt(np.diag(MU))
-    lam_reg = np.diag(KU) / Dt ** 2
+    lam_reg = lambda_reg_closed_form(n, p, D)
     # V_out = M^{-1} N, N orthonormal basis of range(V_reg)^perp (Section 4)
     N = scipy.linalg.null_space(V.T)
     if N.shape[1] > 0:

@@ -78,7 +78,8 @@ def test_p5_p6_diagonalisation_and_closed_forms(p, D):
         B = U.T @ V.T @ A @ V @ U
         off = B - np.diag(np.diag(B))
         assert np.abs(off).max() <= 1e-12 * np.abs(np.diag(B)).max()
-    np.testing.assert_allclose(s.lam_reg, splitting.lambda_reg_closed_form(n, p, D), rtol=1e-12, atol=1e-10)
+    lam_numeric = np.diag(U.T @ V.T @ s.K @ V @ U) / s.Dt ** 2   # eq. "Lambda reg"
+    np.testing.assert_allclose(s.lam_reg, lam_numeric, rtol=1e-12, atol=1e-10)
     np.testing.assert_allclose(s.Dt, splitting.dtilde_closed_form(n, p, D), rtol=1e-11)
 
 
