@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the IFFD-preconditioned PCG solve on one GB300 per rank.
+
+One step = one full PCG solve (zero start, relative residual 1e-8) of the 3D
+Dirichlet Poisson problem with n = 256 elements per direction and degree p = 4
+(258^3 = 17,173,512 DoFs, right-hand side N(0,1) from seed 1), FP64 IFFD
+preconditioner, through the C ABI: every step of the path (preconditioner
+passes, stiffness sweeps, PCG updates, reductions) runs in the library's
+kernels. Printed metric: DoFs solved per second (whole job).
+
+Also measured in the same run (outside the timed K steps): the same solve with
+the exact Fast Diagonalization preconditioner (the comparator) and with the
+FP32-transform IFFD preconditioner; per-kernel device time from CUDA events
+recorded by the library on the launching stream during the timed region; SM
+clocks sampled by nvidia-smi during the timed region; an end-to-end number
+with host buffers; and the CPU oracle on a bounded sample.
+
+Multi-GPU: problems are independent, so N ranks solve N independent copies
+(replicas, weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCG-solved DoF/s at rel. res 1e-8, IGA-FFD vs exact FD on 1 GB300; % HBM peak"
+UNIT = "DoF/s"
+# FP64 ALU roofline: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+SRC_FILES = {"precond": "paper_2512_20269_gb300/csrc/precond.cu",
+             "stiff": "paper_2512_20269_gb300/csrc/stiffness.cu"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision: str):
+    """Algorithmic work of one launch of a kernel kind: (amount, unit, bound).
+
+    Per-DoF figures: transform pass 2.5 log2(n) + 2 n_out flops (FFT-type DST +
+    remainder projections); the fused pass does two of them plus the eigenvalue
+    sum and division (3 flops); stiffness 7(2p+1) FMA per DoF in 3D spread as
+    2 / 3 / 2 banded products over the three sweeps; PCG update 48 B/DoF."""
+    per_pass = 2.5 * math.log2(n) + 2 * n_out
+    if kind.startswith("precond"):
+        if precision == "fp32":
+            byt = {"precond_fwd": 6.0, "precond_fused": 8.0, "precond_bwd": 6.0}[kind] * 1.0
+            # FP32 intermediates: (8+4)/2 or (4+4) B per DoF; averaged per launch kind
+            return byt * N, "B", "hbm"
+        fl = per_pass * N if kind != "precond_fused" else (2 * per_pass + 3) * N
+        return fl, "flop", "alu"
+    if kind.startswith("stiff"):
+        prods = {"stiff_first": 2, "stiff_mid": 3, "stiff_last": 2}[kind]
+        return prods * 2 * (2 * p + 1) * N, "flop", "alu"
+    if kind == "pcg_update":
+        return 48.0 * N, "B", "hbm"
+    if kind == "fd_pass":
+        return 2 * 2 * n * N, "flop", "alu"
+    return None, None, None
+
+
+def file_sha(rel: str) -> str:
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()[:16]
+    except Exception:
+        return ""
+
+
+def ncu_traffic(kind: str):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, only if the
+    kernel source still has the hash recorded with the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kind:
+            src, sha, val = parts[1], parts[2], float(parts[3])
+            if file_sha(SRC_FILES.get(src, src)) == sha:
+                return val
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"iffd_clocks_{os.getpid()}.csv")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(w, iters: int):
+    """Time the oracle (CPU, float64) on the full workload: the initial
+    preconditioner apply plus one full PCG iteration, extrapolated to `iters`
+    iterations. Setup of the 1D data is excluded (as for the GPU)."""
+    import numpy as np
+    import scipy.sparse
+
+    from oracle import operators, splitting
+    from paper_2512_20269_gb300 import inputs
+
+    s = splitting.axis_split(w.n, w.p, (0, 1))
+    splits = [s] * w.d
+    MK = [(scipy.sparse.csr_matrix(s.M), scipy.sparse.csr_matrix(s.K))] * w.d
+    f = inputs.workload_rhs(w)
+    t0 = time.perf_counter()
+    r = f.copy()
+    z = operators.iffd_apply(r, splits)
+    p = z.copy()
+    rz = float(np.vdot(r, z))
+    t1 = time.perf_counter()
+    u = np.zeros_like(f)
+    q = operators.stiffness_apply(p, MK)
+    alpha = rz / float(np.vdot(p, q))
+    u += alpha * p
+    r -= alpha * q
+    _ = np.linalg.norm(r.ravel())
+    z = operators.iffd_apply(r, splits)
+    rz_new = float(np.vdot(r, z))
+    p = z + (rz_new / rz) * p
+    t2 = time.perf_counter()
+    t_solve = (t1 - t0) + iters * (t2 - t1)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": w.N / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy FP64) on the full {w.name} problem: initial preconditioner apply "
+                       f"({t1 - t0:.2f} s) + one PCG iteration ({t2 - t1:.2f} s) timed, extrapolated to "
+                       f"{iters} iterations; BLAS threads = all cores"),
+            "seconds_per_iteration": t2 - t1}
+
+
+def run_reference(args, rank: int, world: int):
+    from paper_2512_20269_gb300 import inputs
+    if rank != 0:
+        return 0
+    w = inputs.CUBE_N256_P4
+    iters = 5  # the FP64 oracle PCG takes 5 iterations on this workload (same as the GPU solve)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, iters)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_oracle_sample(w, iters)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w.N / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w),
+            "cpu_baseline": dict(last, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(w):
+    return {"workload": w.name, "d": w.d, "n": w.n, "p": w.p, "N": w.N, "rhs": f"{w.dist} seed {w.seed}",
+            "precond": "IFFD", "precision": "fp64", "rtol": 1e-8, "boundary": "Dirichlet on all faces",
+            "l2": "no flush: 137 MB vectors, ~1 GB working set > 126 MB L2"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2512_20269_gb300 import IFFDPlan, _lib, inputs
+
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2512_20269_gb300 import build
+        build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = inputs.CUBE_N256_P4
+    plan = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=False)
+    f_host = torch.from_numpy(inputs.workload_rhs(w))
+    f = f_host.cuda()
+    u = plan.empty()
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        _, info = plan.pcg_solve(f, u)
+    iters = info["iters"]
+
+    # ---------------- timed region: K solves, inputs resident in HBM
+    plan.profile_reset()
+    plan.profile_enable(True)
+    launches0 = plan.launch_count()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, info = plan.pcg_solve(f, u)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    plan.profile_enable(False)
+    gpu_launches = plan.launch_count() - launches0
+    prof = plan.profile_read()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = w.N * args.steps * world / (ms / 1e3)
+
+    # ---------------- per-kernel roofline (dominant kernel by device time)
+    n_out = w.p - 2 if w.p % 2 == 0 else w.p - 1
+    total_k = sum(v[1] for v in prof.values()) or 1.0
+    rooflines = {}
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    for kind, (cnt, kms) in prof.items():
+        if cnt == 0:
+            continue
+        amount, unit, bound = algorithmic(kind, w.d, w.n, w.p, n_out, w.N, "fp64")
+        entry = {"launches": cnt, "ms": kms, "share": kms / total_k}
+        if amount is not None:
+            avg_s = kms / cnt / 1e3
+            if unit == "flop":
+                ach = amount / avg_s / 1e12
+                entry.update({"bound": bound, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": ach / FP64_PEAK_TFLOPS, "alg_per_launch": amount})
+            else:
+                ach = amount / avg_s / 1e9
+                entry.update({"bound": bound, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": ach / hbm_peak, "alg_per_launch": amount})
+        rooflines[kind] = entry
+    dom = max((k for k in rooflines if "bound" in rooflines[k]), key=lambda k: rooflines[k]["ms"])
+    d = rooflines[dom]
+    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": ncu_traffic(dom), "kernel": dom,
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz" if d["bound"] == "alu"
+                                else "MEASURED_PEAKS.json hbm_gbs")}
+
+    # ---------------- end to end: pinned host f -> device, solve, u -> host
+    f_pin = f_host.pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    f_dev = torch.empty_like(f)
+    u_dev = plan.empty()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        f_dev.copy_(f_pin, non_blocking=True)
+        plan.pcg_solve(f_dev, u_dev)
+        u_pin.copy_(u_dev, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    e2e = {"value": w.N * args.steps * world / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)}
+
+    # ---------------- accuracy of the timed solve's iterate (true residual)
+    plan_chk = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=True)
+    _, info_chk = plan_chk.pcg_solve(f, u_dev)
+    del plan_chk
+
+    variants = {}
+    if not args.no_variants:
+        for name, prec, pc, reps in (("fp32_transform", "fp32", "iffd", args.steps), ("exact_fd", "fp64", "exact_fd", 2)):
+            pv = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=False)
+            pv.pcg_solve(f, u_dev)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                _, iv = pv.pcg_solve(f, u_dev)
+            b.record(stream)
+            torch.cuda.synchronize()
+            vms = a.elapsed_time(b) / reps
+            pchk = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=True)
+            _, ichk = pchk.pcg_solve(f, u_dev)
+            variants[name] = {"value": w.N / (vms / 1e3), "unit": UNIT, "ms_per_solve": vms, "iters": iv["iters"],
+                              "true_rel_res": ichk["true_rel_res"]}
+            del pv, pchk
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample(w, iters)
+            cpu.pop("seconds_per_iteration", None)
+        except Exception as exc:  # report, never fail the bench line
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
+                "iters": iters, "true_rel_res": info_chk["true_rel_res"], "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clk,
+                "variants": variants, "kernels": rooflines,
+                "hbm_frac_of_solve": None}
+        # fraction of HBM peak of the whole solve at the method's algorithmic traffic
+        # (176 B/DoF per PCG iteration, see the design notes)
+        line["hbm_frac_of_solve"] = (176.0 * w.N * iters + 96.0 * w.N) / (ms / args.steps / 1e3) / 1e9 / hbm_peak
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * iffd.h -- C ABI of the GB300 (sm_103a) implementation of the Isogeometric
+ * Fast Fourier-based Diagonalization (IFFD) preconditioner inside PCG for the
+ * B-spline Galerkin Poisson system on [0,1]^d (arXiv 2512.20269).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Problem (Section 2): d in {2,3} directions, n elements per direction on a
+ *   uniform grid, degree p, maximal smoothness C^{p-1}, homogeneous Dirichlet
+ *   data on both ends of every direction (D_k = {0,1}; other Dirichlet sets
+ *   return IFFD_ERR_UNSUPPORTED). The basis of direction k has
+ *   m_k = n_k + p - 2 functions; N = m_1 * ... * m_d.
+ * - Vectors are float64 arrays of N entries in DEVICE memory, owned by the
+ *   caller, contiguous, with direction 1 (x) fastest -- the lexicographic order
+ *   of eq. "tp-B-basis": entry (i_1, .., i_d) sits at i_1 + m_1 (i_2 + m_2 i_3).
+ * - The library owns only the plan (handle) and its device tables (a few
+ *   hundred KB). All large scratch memory is a caller-provided device buffer
+ *   `ws` of at least iffd_workspace_bytes() bytes (256-byte aligned).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call is asynchronous on that stream except iffd_setup (which
+ *   synchronises it once after uploading the tables) and iffd_pcg_solve (which
+ *   synchronises it to read the convergence state).
+ * - Return value: an iffd_status. On error nothing is launched or the launch
+ *   sequence stops at the failing launch; iffd_last_error() then returns a
+ *   thread-local message. No exception crosses the ABI.
+ * - The plan is bound to the CUDA device that was current at iffd_setup; every
+ *   later call must run with that device current.
+ */
+#ifndef IFFD_H_
+#define IFFD_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iffd_plan* iffd_handle;
+
+typedef enum {
+  IFFD_OK = 0,
+  IFFD_ERR_INVALID_ARG = 1,  /* null pointer, d not in {2,3}, p < 1, ... */
+  IFFD_ERR_UNSUPPORTED = 2,  /* n <= p, Dirichlet set other than {0,1}, size too large */
+  IFFD_ERR_SINGULAR = 3,     /* all-Neumann problem: A^ singular (Section 3) */
+  IFFD_ERR_WORKSPACE = 4,    /* ws is NULL or misaligned */
+  IFFD_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
+  IFFD_ERR_NOT_CONVERGED = 6,/* PCG reached maxit without the relative residual rtol */
+  IFFD_ERR_BREAKDOWN = 7,    /* PCG breakdown: (p, A p) <= 0, (r, z) <= 0, or NaN/Inf */
+  IFFD_ERR_TIMEOUT = 8       /* reserved: a bounded device wait expired */
+} iffd_status;
+
+/* Arithmetic of the preconditioner transforms (the PCG vectors, residuals,
+ * inner products and the stiffness apply are always float64). */
+typedef enum {
+  IFFD_PREC_FP64 = 0,           /* every transform step in float64 */
+  IFFD_PREC_FP32_TRANSFORM = 1  /* transforms and eigenvalue scaling in float32 */
+} iffd_precision;
+
+typedef enum {
+  IFFD_PRECOND_IFFD = 0,      /* eq. "preconditioner" with Q~, Lambda~ of Sections 4-6 */
+  IFFD_PRECOND_EXACT_FD = 1,  /* eq. "exact_diagonalization" (dense Q per direction) */
+  IFFD_PRECOND_NONE = 2       /* plain CG (z = r) */
+} iffd_precond_kind;
+
+typedef enum {
+  IFFD_COEF_CONST = 0         /* -Laplace: A = A^ = sum_k K_k x M x .. (eq. "system_matrix") */
+} iffd_coef_kind;
+
+typedef struct {
+  int precision;       /* iffd_precision */
+  int precond;         /* iffd_precond_kind */
+  double rtol;         /* stop when ||f - A u_k||_2 <= rtol ||f||_2 (recurrence residual); paper: 1e-8 */
+  int maxit;           /* iteration cap */
+  int coef;            /* iffd_coef_kind */
+  int true_residual;   /* 1: iffd_pcg_solve recomputes ||f - A u||/||f|| at exit */
+  int flexible;        /* 1: Polak-Ribiere beta (default for FP32 transforms) */
+} iffd_options;
+
+typedef struct {
+  int iters;            /* number of products with A (Section 7 counts these) */
+  double rel_res;       /* ||r_k|| / ||f|| of the recurrence residual at exit */
+  double true_rel_res;  /* ||f - A u|| / ||f|| if options.true_residual, else -1 */
+  int status;           /* iffd_status of the solve */
+} iffd_pcg_info;
+
+/* Fills *opt with the defaults: FP64, IFFD, rtol 1e-8, maxit 500, CONST,
+ * true_residual 1, flexible 0. Returns IFFD_ERR_INVALID_ARG on NULL. */
+int iffd_default_options(iffd_options* opt);
+
+/* Builds the plan for d directions with n_elems[k] elements each and degree p
+ * (Section 2), computes on the host the 1D mass/stiffness matrices (Section 3),
+ * the regular/remainder splitting and its eigendata (Sections 4-6: V_reg in the
+ * special basis of eq. "special_basis", V_out, Q_out, Lambda_out, D~_reg,
+ * Lambda_reg of Lemma 3) -- plus the dense Q_k of eq. "eigendecomposition" when
+ * opt->precond == IFFD_PRECOND_EXACT_FD -- and uploads them to the current
+ * device. dirichlet[2k], dirichlet[2k+1] flag Dirichlet data at x_k = 0 / 1
+ * (must be 1, 1). opt may be NULL (defaults). stream: see conventions.
+ * Errors: INVALID_ARG, UNSUPPORTED (n <= p, p > 16, non-{0,1} Dirichlet set,
+ * FFT length with a prime factor above 13), SINGULAR, CUDA. *out is set only
+ * on success; release it with iffd_destroy. */
+int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
+               iffd_handle* out);
+
+/* Device workspace needed by every call on this plan, in bytes. */
+int iffd_workspace_bytes(iffd_handle h, size_t* bytes);
+
+/* Sizes of direction `axis` (0-based): m = n + p - 2, n_reg and n_out of
+ * eq. "reg_space_dim". */
+int iffd_get_dims(iffd_handle h, int axis, int* m, int* n_reg, int* n_out);
+
+/* Copies the host-side 1D data of direction `axis` into caller HOST buffers
+ * (any pointer may be NULL):
+ *   M_band, K_band: m*(2p+1), band[i*(2p+1) + (j-i+p)] = M[i][j] (Section 3);
+ *   lam: m, Lambda~ = [Lambda_reg (Lemma 3) | Lambda_out];
+ *   dtilde: n_reg, diagonal of D~_reg (end of Section 6);
+ *   VL: (p-1)*floor(p/2), left edge block of V_reg (row-major); the right block
+ *       is its mirror image V_reg[m-1-r][n_reg-1-c] = VL[r][c] and the interior
+ *       special function j is the B-spline j + floor((p-1)/2);
+ *   W: m*n_out, V_out Q_out (row-major). */
+int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double* lam, double* dtilde,
+                double* VL, double* W);
+
+/* Host-only variant of iffd_get_1d that needs no plan and no GPU: runs the
+ * same 1D setup for n elements, degree p and the Dirichlet flags
+ * dirichlet[0..1] of one direction. m, n_reg, n_out receive the sizes (any may
+ * be NULL); every array pointer may be NULL (call once with NULLs to size the
+ * buffers). Same layouts and errors as iffd_get_1d / iffd_setup. */
+int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
+                   double* K_band, double* lam, double* dtilde, double* VL, double* W);
+
+/* z = P^{-1} r: the IFFD preconditioner of eq. "preconditioner" (or the exact
+ * FD of eq. "exact_diagonalization", or the identity, per opt->precond).
+ * r, z: device, N float64 each, must not alias. ws: see conventions. */
+int iffd_apply_preconditioner(iffd_handle h, const double* r, double* z, void* ws, void* stream);
+
+/* Au = A^ u with A^ = sum_k (M_d x .. x K_k x .. x M_1) (eq. "system_matrix"),
+ * applied matrix-free by banded sweeps. u, Au: device, N float64 each, must not
+ * alias. */
+int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, void* stream);
+
+/* Solves A^ u = f by PCG (Section 3) with zero initial guess and the stopping
+ * rule ||r_k|| <= rtol ||f|| (Section 7), preconditioned per opt->precond.
+ * f, u: device, N float64 each, must not alias; u is output only. info: HOST
+ * pointer, filled on return (may be NULL). Synchronises `stream`. Returns
+ * IFFD_OK, IFFD_ERR_NOT_CONVERGED or IFFD_ERR_BREAKDOWN (u then holds the last
+ * iterate), or an argument / CUDA error. */
+int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* stream, iffd_pcg_info* info);
+
+/* Kernel kinds reported by the profiler (iffd_profile_read). */
+typedef enum {
+  IFFD_K_PRECOND_FWD = 0,    /* IFFD pass Q~^T along one direction */
+  IFFD_K_PRECOND_FUSED = 1,  /* IFFD pass Q~^T, eigenvalue scaling, Q~ (last direction) */
+  IFFD_K_PRECOND_BWD = 2,    /* IFFD pass Q~ along one direction (+ PCG dot products) */
+  IFFD_K_STIFF_FIRST = 3,    /* stiffness sweep, slowest direction (+ p = z + beta p) */
+  IFFD_K_STIFF_MID = 4,      /* stiffness sweep, middle direction (3D) */
+  IFFD_K_STIFF_LAST = 5,     /* stiffness sweep along x (+ (p, A p) partial sums) */
+  IFFD_K_PCG_UPDATE = 6,     /* x += alpha p, r -= alpha q, ||r||^2 partials */
+  IFFD_K_PCG_INIT = 7,       /* x = 0, r = f, ||f||^2 partials */
+  IFFD_K_FINALIZE = 8,       /* fixed-order reduction of partial sums + scalar updates */
+  IFFD_K_FD_PASS = 9,        /* exact FD dense contraction pass */
+  IFFD_K_VECTOR = 10,        /* copies, plain dot products, residual norm */
+  IFFD_K_KINDS = 11
+} iffd_kernel_kind;
+
+/* Per-kernel device timing of this plan's launches by CUDA events recorded on
+ * the call's stream around every launch (off by default; costs one event pair
+ * per launch). iffd_profile_enable(h, 1) starts recording, 0 stops;
+ * iffd_profile_reset clears the totals. iffd_profile_read waits for the
+ * recorded events and returns, for one iffd_kernel_kind, the number of
+ * launches and their summed device time in milliseconds since the last reset
+ * (name: static string, may be NULL). iffd_launch_count returns the number of
+ * kernels this plan has launched since iffd_setup (always counted). */
+int iffd_profile_enable(iffd_handle h, int enable);
+int iffd_profile_reset(iffd_handle h);
+int iffd_profile_read(iffd_handle h, int kind, long long* launches, double* ms, const char** name);
+int iffd_launch_count(iffd_handle h, long long* count);
+
+/* Releases the plan and its device tables (NULL is accepted). Must run with
+ * the plan's device current; does not synchronise any stream. */
+int iffd_destroy(iffd_handle h);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* iffd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFFD_H_ */

@@ -13,13 +13,18 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg
+import scipy.sparse
 import scipy.sparse.linalg
 
 
-def apply_along(A: np.ndarray, u: np.ndarray, direction: int) -> np.ndarray:
+def apply_along(A, u: np.ndarray, direction: int) -> np.ndarray:
     """(I x .. x A x .. x I) u: multiply every pencil along ``direction``
-    (1-based, paper order) by the matrix A."""
+    (1-based, paper order) by the matrix A (dense, or scipy.sparse)."""
     ax = u.ndim - direction
+    if scipy.sparse.issparse(A):
+        v = np.moveaxis(u, ax, 0)
+        w = (A @ v.reshape(v.shape[0], -1)).reshape((A.shape[0],) + v.shape[1:])
+        return np.moveaxis(w, 0, ax)
     return np.moveaxis(np.tensordot(A, u, axes=([1], [ax])), 0, ax)
 
 

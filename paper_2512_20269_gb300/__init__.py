@@ -1,0 +1,189 @@
+"""GB300 (sm_103a) IFFD-preconditioned PCG for the B-spline Galerkin Poisson system.
+
+The compute path is the C ABI of ``libiffd.so`` (include/iffd.h): hand-written
+CUDA passes for the IFFD preconditioner, the Kronecker stiffness and the PCG
+vector updates. This package only marshals arguments; PyTorch provides device
+memory and streams. There is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import IFFDError, check, iffd_options, iffd_pcg_info
+
+PRECISION = {"fp64": 0, "fp32": 1}
+PRECOND = {"iffd": 0, "exact_fd": 1, "none": 2}
+
+__all__ = ["IFFDPlan", "IFFDError", "host_axis", "PRECISION", "PRECOND"]
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def host_axis(n: int, p: int, dirichlet=(1, 1)) -> dict:
+    """1D tables of one direction computed by the library's host setup (no GPU)."""
+    lib = _lib.load()
+    dir_arr = (ctypes.c_int * 2)(*dirichlet)
+    m, nr, no = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib.iffd_host_axis(n, p, dir_arr, ctypes.byref(m), ctypes.byref(nr), ctypes.byref(no),
+                             None, None, None, None, None, None), "iffd_host_axis")
+    m, nr, no = m.value, nr.value, no.value
+    bw = 2 * p + 1
+    out = {"m": m, "n_reg": nr, "n_out": no,
+           "M_band": np.zeros(m * bw), "K_band": np.zeros(m * bw), "lam": np.zeros(m),
+           "dtilde": np.zeros(nr), "VL": np.zeros(max(1, (p - 1) * (p // 2))), "W": np.zeros(max(1, m * no))}
+    dp = lambda a: a.ctypes.data_as(_lib.c_double_p)
+    check(lib.iffd_host_axis(n, p, dir_arr, None, None, None, dp(out["M_band"]), dp(out["K_band"]),
+                             dp(out["lam"]), dp(out["dtilde"]), dp(out["VL"]), dp(out["W"])), "iffd_host_axis")
+    out["M_band"] = out["M_band"].reshape(m, bw)
+    out["K_band"] = out["K_band"].reshape(m, bw)
+    out["VL"] = out["VL"][:(p - 1) * (p // 2)].reshape(p - 1, p // 2)
+    out["W"] = out["W"][:m * no].reshape(m, no)
+    return out
+
+
+class IFFDPlan:
+    """One problem (d, n per direction, p, Dirichlet on every face) on the current CUDA device.
+
+    Vectors are float64 CUDA tensors of N = prod(m_k) entries, direction 1 (x)
+    fastest; a tensor of shape (m_d, ..., m_1) in C order has that layout.
+    """
+
+    def __init__(self, d: int, n, p: int, precision: str = "fp64", precond: str = "iffd", rtol: float = 1e-8,
+                 maxit: int = 500, true_residual: bool = True, flexible: bool = False, stream=None):
+        import torch
+        self._lib = _lib.load()
+        n = [int(n)] * d if np.isscalar(n) else [int(x) for x in n]
+        self.d, self.n, self.p = d, n, p
+        opt = iffd_options()
+        self._lib.iffd_default_options(ctypes.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.precond = PRECOND[precond]
+        opt.rtol = rtol
+        opt.maxit = maxit
+        opt.true_residual = int(true_residual)
+        opt.flexible = int(flexible)
+        self.options = opt
+        nn = (ctypes.c_int * d)(*n)
+        dd = (ctypes.c_int * (2 * d))(*([1] * (2 * d)))
+        h = ctypes.c_void_p()
+        check(self._lib.iffd_setup(d, nn, p, dd, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)),
+              "iffd_setup")
+        self._h = h
+        self.m = []
+        for a in range(d):
+            m, nr, no = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            check(self._lib.iffd_get_dims(h, a, ctypes.byref(m), ctypes.byref(nr), ctypes.byref(no)), "iffd_get_dims")
+            self.m.append(m.value)
+        self.N = int(np.prod(self.m))
+        self.shape = tuple(reversed(self.m))
+        nb = ctypes.c_size_t()
+        check(self._lib.iffd_workspace_bytes(h, ctypes.byref(nb)), "iffd_workspace_bytes")
+        self.workspace_bytes = nb.value
+        self._ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        self._ws_ptr = (_ptr(self._ws) + 255) // 256 * 256
+
+    # -- helpers
+    def _check_vec(self, t, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == self.N):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with {self.N} entries")
+
+    def empty(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    def get_1d(self, axis: int) -> dict:
+        m = self.m[axis]
+        p = self.p
+        bw = 2 * p + 1
+        no = m - (self.n[axis] - 1 if p % 2 else self.n[axis])
+        out = {"M_band": np.zeros(m * bw), "K_band": np.zeros(m * bw), "lam": np.zeros(m),
+               "dtilde": np.zeros(m - no), "VL": np.zeros(max(1, (p - 1) * (p // 2))), "W": np.zeros(max(1, m * no))}
+        dp = lambda a: a.ctypes.data_as(_lib.c_double_p)
+        check(self._lib.iffd_get_1d(self._h, axis, dp(out["M_band"]), dp(out["K_band"]), dp(out["lam"]),
+                                    dp(out["dtilde"]), dp(out["VL"]), dp(out["W"])), "iffd_get_1d")
+        out["M_band"] = out["M_band"].reshape(m, bw)
+        out["K_band"] = out["K_band"].reshape(m, bw)
+        return out
+
+    # -- C ABI calls
+    def iffd_apply_preconditioner(self, r, z=None, stream=None):
+        z = self.empty() if z is None else z
+        self._check_vec(r, "r")
+        self._check_vec(z, "z")
+        check(self._lib.iffd_apply_preconditioner(self._h, _ptr(r), _ptr(z), self._ws_ptr, _stream_handle(stream)),
+              "iffd_apply_preconditioner")
+        return z
+
+    def iffd_apply_stiffness(self, u, Au=None, stream=None):
+        Au = self.empty() if Au is None else Au
+        self._check_vec(u, "u")
+        self._check_vec(Au, "Au")
+        check(self._lib.iffd_apply_stiffness(self._h, _ptr(u), _ptr(Au), self._ws_ptr, _stream_handle(stream)),
+              "iffd_apply_stiffness")
+        return Au
+
+    def iffd_pcg_solve(self, f, u=None, stream=None, raise_on_error: bool = True):
+        u = self.empty() if u is None else u
+        self._check_vec(f, "f")
+        self._check_vec(u, "u")
+        info = iffd_pcg_info()
+        rc = self._lib.iffd_pcg_solve(self._h, _ptr(f), _ptr(u), self._ws_ptr, _stream_handle(stream),
+                                      ctypes.byref(info))
+        if raise_on_error:
+            check(rc, "iffd_pcg_solve")
+        return u, {"iters": info.iters, "rel_res": info.rel_res, "true_rel_res": info.true_rel_res,
+                   "status": info.status}
+
+    # -- profiling (CUDA events around every launch of this plan)
+    KERNEL_KINDS = 11
+
+    def profile_enable(self, on: bool = True):
+        check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")
+
+    def profile_reset(self):
+        check(self._lib.iffd_profile_reset(self._h), "iffd_profile_reset")
+
+    def profile_read(self) -> dict:
+        """{kind name: (launches, total ms)} since the last reset."""
+        out = {}
+        for k in range(self.KERNEL_KINDS):
+            n, ms, name = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_char_p()
+            check(self._lib.iffd_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(name)),
+                  "iffd_profile_read")
+            out[name.value.decode()] = (n.value, ms.value)
+        return out
+
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        check(self._lib.iffd_launch_count(self._h, ctypes.byref(n)), "iffd_launch_count")
+        return n.value
+
+    apply_preconditioner = iffd_apply_preconditioner
+    apply_stiffness = iffd_apply_stiffness
+    pcg_solve = iffd_pcg_solve
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.iffd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,96 @@
+"""ctypes binding of the C ABI declared in include/iffd.h (argument marshalling only).
+
+Every function keeps the C name. The library is loaded from this package's
+directory; there is no fallback: if ``libiffd.so`` is missing the import of any
+entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libiffd.so")
+
+c_int_p = ctypes.POINTER(ctypes.c_int)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_size_t_p = ctypes.POINTER(ctypes.c_size_t)
+
+IFFD_OK = 0
+STATUS_NAMES = {0: "IFFD_OK", 1: "IFFD_ERR_INVALID_ARG", 2: "IFFD_ERR_UNSUPPORTED", 3: "IFFD_ERR_SINGULAR",
+                4: "IFFD_ERR_WORKSPACE", 5: "IFFD_ERR_CUDA", 6: "IFFD_ERR_NOT_CONVERGED",
+                7: "IFFD_ERR_BREAKDOWN", 8: "IFFD_ERR_TIMEOUT"}
+
+
+class iffd_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("coef", ctypes.c_int), ("true_residual", ctypes.c_int),
+                ("flexible", ctypes.c_int)]
+
+
+class iffd_pcg_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+# (name, restype, argtypes) of every exported entry point of include/iffd.h
+SIGNATURES = [
+    ("iffd_default_options", ctypes.c_int, [ctypes.POINTER(iffd_options)]),
+    ("iffd_setup", ctypes.c_int, [ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, ctypes.POINTER(iffd_options),
+                                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("iffd_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, c_size_t_p]),
+    ("iffd_get_dims", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p]),
+    ("iffd_get_1d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [c_double_p] * 6),
+    ("iffd_host_axis", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]
+     + [c_double_p] * 6),
+    ("iffd_apply_preconditioner", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    ("iffd_apply_stiffness", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    ("iffd_pcg_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.POINTER(iffd_pcg_info)]),
+    ("iffd_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("iffd_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("iffd_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                         c_double_p, ctypes.POINTER(ctypes.c_char_p)]),
+    ("iffd_launch_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("iffd_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("iffd_last_error", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libiffd.so (built in-tree by build.py) and declare its signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2512_20269_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class IFFDError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = load().iffd_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code: int, where: str) -> int:
+    if code != IFFD_OK:
+        raise IFFDError(code, where)
+    return code
+
+
+def __getattr__(name):
+    if name.startswith("iffd_"):
+        return getattr(load(), name)
+    raise AttributeError(name)

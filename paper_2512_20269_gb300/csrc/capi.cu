@@ -1,0 +1,822 @@
+// C ABI of the IFFD library (declarations and contracts in include/iffd.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/iffd.h"
+#include "device_common.cuh"
+#include "fd.h"
+#include "host_setup.h"
+#include "kernels.h"
+
+namespace iffd {
+
+thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  return fail(IFFD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define IFFD_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+static const double kPi = 3.14159265358979323846264338327950288;
+
+// Launch `call` as one kernel of kind `kind`, with optional event timing.
+#define IFFD_LAUNCH(P, kind, st, call)  \
+  do {                                  \
+    (P)->prof.begin((kind), (st));      \
+    IFFD_CUDA(call);                    \
+    (P)->prof.end(st);                  \
+  } while (0)
+
+// CUDA-event timing of every launch (optional) and a launch counter.
+struct Profiler {
+  bool on = false;
+  long long launches = 0;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  long long cnt[IFFD_K_KINDS] = {};
+  double ms[IFFD_K_KINDS] = {};
+  cudaEvent_t take() {
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  void begin(int kind, cudaStream_t st) {
+    ++launches;
+    if (!on) return;
+    Pending p{kind, take(), nullptr};
+    cudaEventRecord(p.a, st);
+    pending.push_back(p);
+  }
+  void end(cudaStream_t st) {
+    if (!on || pending.empty() || pending.back().b != nullptr) return;
+    pending.back().b = take();
+    cudaEventRecord(pending.back().b, st);
+  }
+  cudaError_t collect() {
+    for (auto& p : pending) {
+      if (p.b == nullptr) continue;
+      cudaError_t e = cudaEventSynchronize(p.b);
+      if (e != cudaSuccess) return e;
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p.a, p.b);
+      if (e != cudaSuccess) return e;
+      cnt[p.kind] += 1;
+      ms[p.kind] += t;
+    }
+    for (auto& p : pending) {
+      pool.push_back(p.a);
+      if (p.b) pool.push_back(p.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+  void release() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      if (p.b) cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+    pending.clear();
+    pool.clear();
+  }
+};
+
+// Plan of one problem: host 1D data, device tables, launch geometry.
+struct Plan {
+  mutable Profiler prof;
+  int d = 0, p = 0;
+  int n[3] = {0, 0, 0};
+  int device = 0;
+  iffd_options opt{};
+  Dims dims{};
+  Axis1D host[3];
+  void* dev = nullptr;  // single allocation for all device tables
+  AxisTab<double> axd[3];
+  AxisTab<float> axf[3];
+  BandTab bt[3];
+  int PPd[3], ldtd[3], PPf[3], ldtf[3], PPs[3], ldts[3];
+  // exact FD tables
+  const double* QT[3] = {nullptr, nullptr, nullptr};
+  const double* Q[3] = {nullptr, nullptr, nullptr};
+  const double* lamQ[3] = {nullptr, nullptr, nullptr};
+  // workspace layout (bytes)
+  size_t off_r, off_z, off_p, off_q, off_t1, off_t2, off_tf, off_part, off_state, ws_bytes;
+  int max_parts = 0;
+  SolveState* host_state = nullptr;  // pinned
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------ tables
+struct TableBuilder {
+  std::vector<char> bytes;
+  size_t add(const void* src, size_t n) {
+    const size_t off = align256(bytes.size());
+    bytes.resize(off + n);
+    std::memcpy(bytes.data() + off, src, n);
+    return off;
+  }
+  template <typename T>
+  size_t add_vec(const std::vector<T>& v) {
+    if (v.empty()) {  // keep a valid (zero) entry so the device pointer is never dangling
+      const T zero = T(0);
+      return add(&zero, sizeof(T));
+    }
+    return add(v.data(), v.size() * sizeof(T));
+  }
+};
+
+template <typename T>
+static std::vector<T> cast_vec(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+struct AxisOffsets {
+  size_t VL, W, lam, post, tw;
+};
+
+static bool register_radix(int r) { return r == 8 || r == 4 || r == 2 || r == 3 || r == 5; }
+
+// Twiddles of every Stockham stage. Register-butterfly stages store
+// exp(-2 pi i q k / (Ns r)) for q = 1..r-1, k < Ns; direct-DFT stages store
+// exp(-2 pi i s / (Ns r)) for s < Ns r.
+static std::string fft_tables(const Axis1D& A, int* L, std::vector<int>* radices, std::vector<double>* tw,
+                              std::vector<int>* twoff) {
+  *L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
+  if (!fft_factor(*L, radices)) return "bad FFT length " + std::to_string(*L);
+  if ((int)radices->size() > kMaxStages) return "too many FFT stages";
+  tw->clear();
+  twoff->clear();
+  long long Ns = 1;
+  for (int r : *radices) {
+    twoff->push_back((int)(tw->size() / 2));
+    const long long den = Ns * r;
+    auto push = [&](long long num) {
+      const double ang = -2.0 * kPi * (double)(num % den) / (double)den;
+      tw->push_back(std::cos(ang));
+      tw->push_back(std::sin(ang));
+    };
+    if (register_radix(r)) {
+      for (int q = 1; q < r; ++q)
+        for (long long k = 0; k < Ns; ++k) push((long long)q * k);
+    } else {
+      for (long long s = 0; s < den; ++s) push(s);
+    }
+    Ns *= r;
+  }
+  return "";
+}
+
+static std::vector<double> post_table(const Axis1D& A) {
+  std::vector<double> post;
+  const int N = A.n_reg;
+  if (A.kind == TK_DST23) {
+    for (int k = 0; k <= N / 2; ++k) {
+      const double sk = 1.0 / A.dtilde[N - 1 - k];
+      const double sm = (k >= 1) ? 1.0 / A.dtilde[k - 1] : 0.0;
+      const double c = std::cos(kPi * k / (2.0 * N)), s = std::sin(kPi * k / (2.0 * N));
+      post.push_back(0.5 * sk * c);
+      post.push_back(0.5 * sk * s);
+      post.push_back(0.5 * sm * s);
+      post.push_back(0.5 * sm * c);
+    }
+  } else {
+    for (int j = 0; j < N; ++j) post.push_back(0.5 / A.dtilde[j]);
+  }
+  return post;
+}
+
+template <typename T>
+static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, const std::vector<int>& rad,
+                         const std::vector<int>& twoff, const char* base, const AxisOffsets& o) {
+  t->m = A.m;
+  t->n_reg = A.n_reg;
+  t->n_out = A.n_out;
+  t->p = A.p;
+  t->o = A.o;
+  t->nL = A.nL;
+  t->rowsL = A.rowsL;
+  t->wlo = A.wlo;
+  t->whi = A.whi;
+  t->kind = A.kind;
+  t->L = L;
+  t->nst = (int)rad.size();
+  for (int s = 0; s < kMaxStages; ++s) {
+    t->radix[s] = s < t->nst ? rad[s] : 1;
+    t->twoff[s] = s < t->nst ? twoff[s] : 0;
+  }
+  t->VL = reinterpret_cast<const T*>(base + o.VL);
+  t->W = reinterpret_cast<const T*>(base + o.W);
+  t->lam = reinterpret_cast<const T*>(base + o.lam);
+  t->post = reinterpret_cast<const T*>(base + o.post);
+  t->tw = reinterpret_cast<const T*>(base + o.tw);
+}
+
+static int pick_pp(int m, int L, size_t elt, int* PP, int* ldt) {
+  *ldt = m | 1;
+  int pp = 16;
+  while (pp > 2 && precond_smem_bytes(pp, *ldt, L, elt) > 110 * 1024) pp /= 2;
+  if (precond_smem_bytes(pp, *ldt, L, elt) > 220 * 1024) return 0;
+  *PP = pp;
+  return 1;
+}
+
+static int build_plan(Plan* P, cudaStream_t stream) {
+  TableBuilder tb;
+  struct PerAxis {
+    AxisOffsets od, of;
+    size_t Mb, Kb, Mt, Kt, QT, Q, lamQ;
+    int L;
+    std::vector<int> rad, twoff;
+    int ilo, ihi;
+  } pa[3];
+  for (int a = 0; a < P->d; ++a) {
+    const Axis1D& A = P->host[a];
+    std::vector<double> tw;
+    std::string err = fft_tables(A, &pa[a].L, &pa[a].rad, &tw, &pa[a].twoff);
+    if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+    const std::vector<double> post = post_table(A);
+    pa[a].od.VL = tb.add_vec(A.VL);
+    pa[a].od.W = tb.add_vec(A.W);
+    pa[a].od.lam = tb.add_vec(A.lam);
+    pa[a].od.post = tb.add_vec(post);
+    pa[a].od.tw = tb.add_vec(tw);
+    pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
+    pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
+    pa[a].of.lam = tb.add_vec(cast_vec<float>(A.lam));
+    pa[a].of.post = tb.add_vec(cast_vec<float>(post));
+    pa[a].of.tw = tb.add_vec(cast_vec<float>(tw));
+    // stiffness band tables; interior rows 2p-1 .. m-2p are symmetric Toeplitz
+    const int p = A.p, m = A.m, bw = 2 * p + 1;
+    pa[a].Mb = tb.add_vec(A.Mband);
+    pa[a].Kb = tb.add_vec(A.Kband);
+    std::vector<double> mt(p + 1, 0.0), kt(p + 1, 0.0);
+    int ilo = 2 * p - 1, ihi = m - 2 * p + 1;
+    if (ihi <= ilo) { ilo = 0; ihi = 0; }
+    else {
+      const int mid = (ilo + ihi) / 2;
+      for (int k = 0; k <= p; ++k) {
+        mt[k] = A.Mband[(size_t)mid * bw + p + k];
+        kt[k] = A.Kband[(size_t)mid * bw + p + k];
+      }
+      for (int i = ilo; i < ihi; ++i)
+        for (int k = -p; k <= p; ++k) {
+          const double dm = A.Mband[(size_t)i * bw + p + k] - mt[std::abs(k)];
+          const double dk = A.Kband[(size_t)i * bw + p + k] - kt[std::abs(k)];
+          if (std::fabs(dm) > 1e-12 * std::fabs(mt[0]) || std::fabs(dk) > 1e-12 * std::fabs(kt[0]))
+            return fail(IFFD_ERR_UNSUPPORTED, "interior rows of M/K are not Toeplitz");
+        }
+    }
+    pa[a].ilo = ilo;
+    pa[a].ihi = ihi;
+    pa[a].Mt = tb.add_vec(mt);
+    pa[a].Kt = tb.add_vec(kt);
+    if (P->opt.precond == IFFD_PRECOND_EXACT_FD) {
+      std::vector<double> Qc, lq;
+      err = exact_fd_axis(A, &Qc, &lq);
+      if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+      std::vector<double> Qr((size_t)m * m), QTr((size_t)m * m);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+          Qr[(size_t)i * m + j] = Qc[i + (size_t)j * m];   // Q[i][j]
+          QTr[(size_t)i * m + j] = Qc[j + (size_t)i * m];  // Q^T[i][j] = Q[j][i]
+        }
+      pa[a].Q = tb.add_vec(Qr);
+      pa[a].QT = tb.add_vec(QTr);
+      pa[a].lamQ = tb.add_vec(lq);
+      if (fd_smem(m) > 227 * 1024) return fail(IFFD_ERR_UNSUPPORTED, "exact FD comparator: m too large");
+    }
+  }
+  IFFD_CUDA(cudaMalloc(&P->dev, align256(tb.bytes.size()) + 256));
+  IFFD_CUDA(cudaMemcpyAsync(P->dev, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice, stream));
+  IFFD_CUDA(cudaStreamSynchronize(stream));
+  const char* base = static_cast<const char*>(P->dev);
+  long long N = 1;
+  for (int a = 0; a < P->d; ++a) N *= P->host[a].m;
+  P->dims.d = P->d;
+  for (int a = 0; a < 3; ++a) P->dims.m[a] = (a < P->d) ? P->host[a].m : 1;
+  P->dims.N = N;
+  int max_parts = vec_grid(N);
+  for (int a = 0; a < P->d; ++a) {
+    const Axis1D& A = P->host[a];
+    fill_axistab(&P->axd[a], A, pa[a].L, pa[a].rad, pa[a].twoff, base, pa[a].od);
+    fill_axistab(&P->axf[a], A, pa[a].L, pa[a].rad, pa[a].twoff, base, pa[a].of);
+    if (!pick_pp(A.m, pa[a].L, sizeof(double), &P->PPd[a], &P->ldtd[a]) ||
+        !pick_pp(A.m, pa[a].L, sizeof(float), &P->PPf[a], &P->ldtf[a]))
+      return fail(IFFD_ERR_UNSUPPORTED, "transform length too large for shared memory");
+    BandTab& b = P->bt[a];
+    b.m = A.m;
+    b.p = A.p;
+    b.Mb = reinterpret_cast<const double*>(base + pa[a].Mb);
+    b.Kb = reinterpret_cast<const double*>(base + pa[a].Kb);
+    b.Mt = reinterpret_cast<const double*>(base + pa[a].Mt);
+    b.Kt = reinterpret_cast<const double*>(base + pa[a].Kt);
+    b.ilo = pa[a].ilo;
+    b.ihi = pa[a].ihi;
+    P->ldts[a] = A.m | 1;
+    int pp = 16;
+    while (pp > 2 && (size_t)2 * pp * P->ldts[a] * sizeof(double) > 100 * 1024) pp /= 2;
+    P->PPs[a] = pp;
+    if (P->opt.precond == IFFD_PRECOND_EXACT_FD) {
+      P->Q[a] = reinterpret_cast<const double*>(base + pa[a].Q);
+      P->QT[a] = reinterpret_cast<const double*>(base + pa[a].QT);
+      P->lamQ[a] = reinterpret_cast<const double*>(base + pa[a].lamQ);
+    }
+    max_parts = std::max(max_parts, precond_tiles(P->dims, a, P->PPd[a]));
+    max_parts = std::max(max_parts, precond_tiles(P->dims, a, P->PPf[a]));
+    max_parts = std::max(max_parts, stiff_tiles(P->dims, a, P->PPs[a]));
+  }
+  P->max_parts = max_parts;
+  const size_t vec = align256((size_t)N * sizeof(double));
+  size_t off = 0;
+  P->off_r = off; off += vec;
+  P->off_z = off; off += vec;
+  P->off_p = off; off += vec;
+  P->off_q = off; off += vec;
+  P->off_t1 = off; off += vec;
+  P->off_t2 = off; off += vec;
+  P->off_tf = off;
+  if (P->opt.precision == IFFD_PREC_FP32_TRANSFORM) off += align256((size_t)N * sizeof(float));
+  P->off_part = off; off += align256((size_t)2 * max_parts * sizeof(double));
+  P->off_state = off; off += align256(sizeof(SolveState));
+  P->ws_bytes = off;
+  IFFD_CUDA(cudaHostAlloc((void**)&P->host_state, sizeof(SolveState), cudaHostAllocDefault));
+  return IFFD_OK;
+}
+
+// ------------------------------------------------------------- operations
+static char* wsb(void* ws, size_t off) { return static_cast<char*>(ws) + off; }
+
+__global__ void dot_kernel(const double* __restrict__ a, const double* __restrict__ b, long long N,
+                           double* __restrict__ partial, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  __shared__ double red[kThreads / 32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void copy_kernel(const double* __restrict__ a, double* __restrict__ b, long long N,
+                            const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+template <typename Tc>
+static PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const int* PPs, const int* ldts,
+                                const int* done) {
+  PassLaunch<Tc> L;
+  L.dims = P->dims;
+  L.axis = axis;
+  L.PP = PPs[axis];
+  L.ldt = ldts[axis];
+  L.ax = tabs[axis];
+  L.lamA = tabs[0].lam;
+  L.lamB = (P->d == 3) ? tabs[1].lam : tabs[0].lam;
+  L.dot0 = nullptr;
+  L.dot1 = nullptr;
+  L.partial = nullptr;
+  L.done = done;
+  return L;
+}
+
+// z = P^{-1} r; with ndot >= 1 also partial (dot0, z) [and (dot1, z)] into
+// `partial`; *nparts receives the number of partial sums.
+static int run_precond(const Plan* P, const double* r, double* z, void* ws, cudaStream_t st, const int* done,
+                       int ndot, const double* d0, const double* d1, double* partial, int* nparts) {
+  const int d = P->d;
+  const long long N = P->dims.N;
+  if (P->opt.precond == IFFD_PRECOND_NONE || P->opt.precond == IFFD_PRECOND_EXACT_FD) {
+    if (P->opt.precond == IFFD_PRECOND_NONE) {
+      P->prof.begin(IFFD_K_VECTOR, st);
+      copy_kernel<<<vec_grid(N), kThreads, 0, st>>>(r, z, N, done);
+      IFFD_CUDA(cudaGetLastError());
+      P->prof.end(st);
+    } else {
+      for (int a = 0; a < d - 1; ++a) {
+        IFFD_LAUNCH(P, IFFD_K_FD_PASS, st,
+                    launch_fd_pass(PM_FWD, a == 0 ? r : z, z, P->dims, a, P->QT[a], P->Q[a], P->lamQ[a],
+                                   P->lamQ[0], P->lamQ[1], done, st));
+      }
+      IFFD_LAUNCH(P, IFFD_K_FD_PASS, st,
+                  launch_fd_pass(PM_FUSED, z, z, P->dims, d - 1, P->QT[d - 1], P->Q[d - 1], P->lamQ[d - 1],
+                                 P->lamQ[0], P->lamQ[1], done, st));
+      for (int a = d - 2; a >= 0; --a) {
+        IFFD_LAUNCH(P, IFFD_K_FD_PASS, st,
+                    launch_fd_pass(PM_BWD, z, z, P->dims, a, P->QT[a], P->Q[a], P->lamQ[a], P->lamQ[0],
+                                   P->lamQ[1], done, st));
+      }
+    }
+    if (ndot >= 1) {
+      const int g = vec_grid(N);
+      P->prof.begin(IFFD_K_VECTOR, st);
+      dot_kernel<<<g, kThreads, 0, st>>>(d0, z, N, partial, done);
+      IFFD_CUDA(cudaGetLastError());
+      P->prof.end(st);
+      if (ndot >= 2) {
+        P->prof.begin(IFFD_K_VECTOR, st);
+        dot_kernel<<<g, kThreads, 0, st>>>(d1, z, N, partial + g, done);
+        IFFD_CUDA(cudaGetLastError());
+        P->prof.end(st);
+      }
+      *nparts = g;
+    }
+    return IFFD_OK;
+  }
+  if (P->opt.precision == IFFD_PREC_FP64) {
+    for (int a = 0; a < d - 1; ++a) {
+      auto L = make_pass<double>(P, a, P->axd, P->PPd, P->ldtd, done);
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_FWD, st, (launch_pass<double, double, double>(L, PM_FWD, 0, a == 0 ? r : z, z, st)));
+    }
+    {
+      auto L = make_pass<double>(P, d - 1, P->axd, P->PPd, P->ldtd, done);
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_FUSED, st, (launch_pass<double, double, double>(L, PM_FUSED, 0, z, z, st)));
+    }
+    for (int a = d - 2; a >= 0; --a) {
+      auto L = make_pass<double>(P, a, P->axd, P->PPd, P->ldtd, done);
+      int nd = 0;
+      if (a == 0 && ndot >= 1) {
+        nd = ndot;
+        L.dot0 = d0;
+        L.dot1 = d1;
+        L.partial = partial;
+        *nparts = precond_tiles(P->dims, 0, L.PP);
+      }
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_BWD, st, (launch_pass<double, double, double>(L, PM_BWD, nd, z, z, st)));
+    }
+    return IFFD_OK;
+  }
+  // float32 transforms: float intermediate in the workspace
+  float* tf = reinterpret_cast<float*>(wsb(ws, P->off_tf));
+  {
+    auto L = make_pass<float>(P, 0, P->axf, P->PPf, P->ldtf, done);
+    IFFD_LAUNCH(P, IFFD_K_PRECOND_FWD, st, (launch_pass<float, double, float>(L, PM_FWD, 0, r, tf, st)));
+  }
+  for (int a = 1; a < d - 1; ++a) {
+    auto L = make_pass<float>(P, a, P->axf, P->PPf, P->ldtf, done);
+    IFFD_LAUNCH(P, IFFD_K_PRECOND_FWD, st, (launch_pass<float, float, float>(L, PM_FWD, 0, tf, tf, st)));
+  }
+  {
+    auto L = make_pass<float>(P, d - 1, P->axf, P->PPf, P->ldtf, done);
+    IFFD_LAUNCH(P, IFFD_K_PRECOND_FUSED, st, (launch_pass<float, float, float>(L, PM_FUSED, 0, tf, tf, st)));
+  }
+  for (int a = d - 2; a >= 1; --a) {
+    auto L = make_pass<float>(P, a, P->axf, P->PPf, P->ldtf, done);
+    IFFD_LAUNCH(P, IFFD_K_PRECOND_BWD, st, (launch_pass<float, float, float>(L, PM_BWD, 0, tf, tf, st)));
+  }
+  {
+    auto L = make_pass<float>(P, 0, P->axf, P->PPf, P->ldtf, done);
+    int nd = 0;
+    if (ndot >= 1) {
+      nd = ndot;
+      L.dot0 = d0;
+      L.dot1 = d1;
+      L.partial = partial;
+      *nparts = precond_tiles(P->dims, 0, L.PP);
+    }
+    IFFD_LAUNCH(P, IFFD_K_PRECOND_BWD, st, (launch_pass<float, float, double>(L, PM_BWD, nd, tf, z, st)));
+  }
+  return IFFD_OK;
+}
+
+static StiffLaunch make_stiff(const Plan* P, int axis) {
+  StiffLaunch S;
+  S.dims = P->dims;
+  S.axis = axis;
+  S.PP = P->PPs[axis];
+  S.ldt = P->ldts[axis];
+  S.bt = P->bt[axis];
+  return S;
+}
+
+// out = A^ u (pmode 0), or with the PCG direction update fused (pmode 1: p = z;
+// pmode 2: p = z + beta p) applied to p. Optional partial (dotv, out).
+static int run_stiffness(const Plan* P, const double* u, const double* z, double* p, const double* beta, int pmode,
+                         double* out, void* ws, cudaStream_t st, const int* done, const double* dotv,
+                         double* partial, int* nparts) {
+  double* T1 = reinterpret_cast<double*>(wsb(ws, P->off_t1));
+  double* T2 = reinterpret_cast<double*>(wsb(ws, P->off_t2));
+  const int d = P->d;
+  IFFD_LAUNCH(P, IFFD_K_STIFF_FIRST, st,
+              launch_stiff_first(make_stiff(P, d - 1), u, z, p, beta, pmode, T1, T2, done, st));
+  for (int a = d - 2; a >= 1; --a)
+    IFFD_LAUNCH(P, IFFD_K_STIFF_MID, st, launch_stiff_mid(make_stiff(P, a), T1, T2, done, st));
+  IFFD_LAUNCH(P, IFFD_K_STIFF_LAST, st, launch_stiff_last(make_stiff(P, 0), T1, T2, out, dotv, partial, done, st));
+  if (nparts) *nparts = stiff_tiles(P->dims, 0, P->PPs[0]);
+  return IFFD_OK;
+}
+
+static int check_ws(const Plan* P, void* ws) {
+  if (ws == nullptr) return fail(IFFD_ERR_WORKSPACE, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(IFFD_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  (void)P;
+  return IFFD_OK;
+}
+
+static int check_device(const Plan* P) {
+  int dev = -1;
+  IFFD_CUDA(cudaGetDevice(&dev));
+  if (dev != P->device) return fail(IFFD_ERR_INVALID_ARG, "plan was created on another CUDA device");
+  return IFFD_OK;
+}
+
+}  // namespace iffd
+
+using namespace iffd;
+
+struct iffd_plan {
+  Plan P;
+};
+
+extern "C" {
+
+int iffd_default_options(iffd_options* opt) {
+  if (!opt) return fail(IFFD_ERR_INVALID_ARG, "opt is NULL");
+  opt->precision = IFFD_PREC_FP64;
+  opt->precond = IFFD_PRECOND_IFFD;
+  opt->rtol = 1e-8;
+  opt->maxit = 500;
+  opt->coef = IFFD_COEF_CONST;
+  opt->true_residual = 1;
+  opt->flexible = 0;
+  return IFFD_OK;
+}
+
+int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
+               iffd_handle* out) {
+  g_err.clear();
+  if (!out || !n_elems || !dirichlet) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (d != 2 && d != 3) return fail(IFFD_ERR_INVALID_ARG, "d must be 2 or 3");
+  if (p < 1) return fail(IFFD_ERR_INVALID_ARG, "p must be >= 1");
+  bool any_dir = false;
+  for (int a = 0; a < d; ++a) any_dir = any_dir || dirichlet[2 * a] || dirichlet[2 * a + 1];
+  if (!any_dir) return fail(IFFD_ERR_SINGULAR, "no Dirichlet boundary: the stiffness matrix is singular");
+  iffd_options o;
+  iffd_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != IFFD_PREC_FP64 && o.precision != IFFD_PREC_FP32_TRANSFORM)
+    return fail(IFFD_ERR_INVALID_ARG, "unknown precision");
+  if (o.precond < 0 || o.precond > 2) return fail(IFFD_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o.coef != IFFD_COEF_CONST) return fail(IFFD_ERR_UNSUPPORTED, "coefficient kind not supported");
+  if (!(o.rtol > 0.0) || o.maxit < 1) return fail(IFFD_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 1");
+  iffd_plan* h = new iffd_plan();
+  Plan* P = &h->P;
+  P->d = d;
+  P->p = p;
+  P->opt = o;
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete h;
+    return fail(IFFD_ERR_CUDA, "no CUDA device");
+  }
+  for (int a = 0; a < d; ++a) {
+    P->n[a] = n_elems[a];
+    std::string err = build_axis(n_elems[a], p, dirichlet[2 * a] != 0, dirichlet[2 * a + 1] != 0, &P->host[a]);
+    if (!err.empty()) {
+      delete h;
+      return fail(IFFD_ERR_UNSUPPORTED, err);
+    }
+    if (P->host[a].n_out > kMaxNout) {
+      delete h;
+      return fail(IFFD_ERR_UNSUPPORTED, "n_out above 16");
+    }
+  }
+  const int rc = build_plan(P, static_cast<cudaStream_t>(stream));
+  if (rc != IFFD_OK) {
+    const std::string msg = g_err;
+    if (P->dev) cudaFree(P->dev);
+    if (P->host_state) cudaFreeHost(P->host_state);
+    delete h;
+    g_err = msg;
+    return rc;
+  }
+  *out = h;
+  return IFFD_OK;
+}
+
+int iffd_workspace_bytes(iffd_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  *bytes = h->P.ws_bytes;
+  return IFFD_OK;
+}
+
+int iffd_get_dims(iffd_handle h, int axis, int* m, int* n_reg, int* n_out) {
+  if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
+  const Axis1D& A = h->P.host[axis];
+  if (m) *m = A.m;
+  if (n_reg) *n_reg = A.n_reg;
+  if (n_out) *n_out = A.n_out;
+  return IFFD_OK;
+}
+
+int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double* lam, double* dtilde, double* VL,
+                double* W) {
+  if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
+  const Axis1D& A = h->P.host[axis];
+  auto cp = [](double* dst, const std::vector<double>& v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(double));
+  };
+  cp(M_band, A.Mband);
+  cp(K_band, A.Kband);
+  cp(lam, A.lam);
+  cp(dtilde, A.dtilde);
+  cp(VL, A.VL);
+  cp(W, A.W);
+  return IFFD_OK;
+}
+
+int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
+                   double* K_band, double* lam, double* dtilde, double* VL, double* W) {
+  g_err.clear();
+  if (!dirichlet) return fail(IFFD_ERR_INVALID_ARG, "dirichlet is NULL");
+  Axis1D A;
+  const std::string err = build_axis(n, p, dirichlet[0] != 0, dirichlet[1] != 0, &A);
+  if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+  if (m) *m = A.m;
+  if (n_reg) *n_reg = A.n_reg;
+  if (n_out) *n_out = A.n_out;
+  auto cp = [](double* dst, const std::vector<double>& v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(double));
+  };
+  cp(M_band, A.Mband);
+  cp(K_band, A.Kband);
+  cp(lam, A.lam);
+  cp(dtilde, A.dtilde);
+  cp(VL, A.VL);
+  cp(W, A.W);
+  return IFFD_OK;
+}
+
+int iffd_apply_preconditioner(iffd_handle h, const double* r, double* z, void* ws, void* stream) {
+  if (!h || !r || !z) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (r == z) return fail(IFFD_ERR_INVALID_ARG, "r and z must not alias");
+  int rc = check_ws(&h->P, ws);
+  if (rc) return rc;
+  rc = check_device(&h->P);
+  if (rc) return rc;
+  return run_precond(&h->P, r, z, ws, static_cast<cudaStream_t>(stream), nullptr, 0, nullptr, nullptr, nullptr,
+                     nullptr);
+}
+
+int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, void* stream) {
+  if (!h || !u || !Au) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (u == Au) return fail(IFFD_ERR_INVALID_ARG, "u and Au must not alias");
+  int rc = check_ws(&h->P, ws);
+  if (rc) return rc;
+  rc = check_device(&h->P);
+  if (rc) return rc;
+  return run_stiffness(&h->P, u, nullptr, nullptr, nullptr, 0, Au, ws, static_cast<cudaStream_t>(stream), nullptr,
+                       nullptr, nullptr, nullptr);
+}
+
+int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* stream, iffd_pcg_info* info) {
+  if (!h || !f || !u) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (f == u) return fail(IFFD_ERR_INVALID_ARG, "f and u must not alias");
+  int rc = check_ws(&h->P, ws);
+  if (rc) return rc;
+  rc = check_device(&h->P);
+  if (rc) return rc;
+  const Plan* P = &h->P;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long N = P->dims.N;
+  double* r = reinterpret_cast<double*>(wsb(ws, P->off_r));
+  double* z = reinterpret_cast<double*>(wsb(ws, P->off_z));
+  double* p = reinterpret_cast<double*>(wsb(ws, P->off_p));
+  double* q = reinterpret_cast<double*>(wsb(ws, P->off_q));
+  double* part = reinterpret_cast<double*>(wsb(ws, P->off_part));
+  SolveState* S = reinterpret_cast<SolveState*>(wsb(ws, P->off_state));
+  const int* done = &S->done;
+  const double tol2 = P->opt.rtol * P->opt.rtol;
+  const int maxit = P->opt.maxit;
+  const bool flex = P->opt.flexible || P->opt.precision == IFFD_PREC_FP32_TRANSFORM;
+  int np = 0;
+
+  IFFD_CUDA(cudaMemsetAsync(S, 0, sizeof(SolveState), st));
+  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st));
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_FF, tol2, maxit, st));
+  rc = run_precond(P, r, z, ws, st, done, 1, r, nullptr, part, &np);
+  if (rc) return rc;
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_RZ0, tol2, maxit, st));
+  int it = 0;
+  const int chunk = 4;
+  bool finished = false;
+  while (!finished) {
+    for (int c = 0; c < chunk && it < maxit; ++c, ++it) {
+      rc = run_stiffness(P, nullptr, z, p, &S->beta, it == 0 ? 1 : 2, q, ws, st, done, p, part, &np);
+      if (rc) return rc;
+      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_PQ, tol2, maxit, st));
+      IFFD_LAUNCH(P, IFFD_K_PCG_UPDATE, st, launch_pcg_update(u, r, p, q, S, N, part, done, st));
+      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_RR, tol2, maxit, st));
+      rc = run_precond(P, r, z, ws, st, done, flex ? 2 : 1, r, q, part, &np);
+      if (rc) return rc;
+      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, flex ? FP_RZ_FLEX : FP_RZ, tol2, maxit, st));
+    }
+    IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    IFFD_CUDA(cudaStreamSynchronize(st));
+    finished = P->host_state->done || it >= maxit;
+  }
+  SolveState hs = *P->host_state;
+  double true_rel = -1.0;
+  if (P->opt.true_residual && hs.ff > 0.0) {
+    rc = run_stiffness(P, u, nullptr, nullptr, nullptr, 0, q, ws, st, nullptr, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    IFFD_LAUNCH(P, IFFD_K_VECTOR, st, launch_residual(f, q, N, part, st));
+    IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_TRUE, tol2, maxit, st));
+    IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    IFFD_CUDA(cudaStreamSynchronize(st));
+    true_rel = std::sqrt(P->host_state->zq / hs.ff);
+  }
+  int status = hs.status;
+  if (!hs.done) status = IFFD_ERR_NOT_CONVERGED;
+  if (info) {
+    info->iters = hs.iters;
+    info->rel_res = hs.ff > 0 ? std::sqrt(hs.rr / hs.ff) : 0.0;
+    info->true_rel_res = true_rel;
+    info->status = status;
+  }
+  if (status == IFFD_ERR_NOT_CONVERGED) return fail(status, "PCG did not reach rtol within maxit");
+  if (status == IFFD_ERR_BREAKDOWN) return fail(status, "PCG breakdown (non-positive curvature or NaN)");
+  return IFFD_OK;
+}
+
+static const char* kKindNames[IFFD_K_KINDS] = {
+    "precond_fwd", "precond_fused", "precond_bwd", "stiff_first", "stiff_mid", "stiff_last",
+    "pcg_update", "pcg_init", "finalize", "fd_pass", "vector"};
+
+int iffd_profile_enable(iffd_handle h, int enable) {
+  if (!h) return fail(IFFD_ERR_INVALID_ARG, "NULL handle");
+  h->P.prof.on = enable != 0;
+  return IFFD_OK;
+}
+
+int iffd_profile_reset(iffd_handle h) {
+  if (!h) return fail(IFFD_ERR_INVALID_ARG, "NULL handle");
+  cudaError_t e = h->P.prof.collect();
+  if (e != cudaSuccess) return cuda_fail(e, "iffd_profile_reset");
+  for (int k = 0; k < IFFD_K_KINDS; ++k) {
+    h->P.prof.cnt[k] = 0;
+    h->P.prof.ms[k] = 0.0;
+  }
+  return IFFD_OK;
+}
+
+int iffd_profile_read(iffd_handle h, int kind, long long* launches, double* ms, const char** name) {
+  if (!h || kind < 0 || kind >= IFFD_K_KINDS) return fail(IFFD_ERR_INVALID_ARG, "bad handle or kind");
+  cudaError_t e = h->P.prof.collect();
+  if (e != cudaSuccess) return cuda_fail(e, "iffd_profile_read");
+  if (launches) *launches = h->P.prof.cnt[kind];
+  if (ms) *ms = h->P.prof.ms[kind];
+  if (name) *name = kKindNames[kind];
+  return IFFD_OK;
+}
+
+int iffd_launch_count(iffd_handle h, long long* count) {
+  if (!h || !count) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  *count = h->P.prof.launches;
+  return IFFD_OK;
+}
+
+int iffd_destroy(iffd_handle h) {
+  if (!h) return IFFD_OK;
+  h->P.prof.release();
+  if (h->P.dev) cudaFree(h->P.dev);
+  if (h->P.host_state) cudaFreeHost(h->P.host_state);
+  delete h;
+  return IFFD_OK;
+}
+
+const char* iffd_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Exact Fast Diagonalization (eq. "exact_diagonalization" of the paper):
+//   A^{-1} r = (Q_d x .. x Q_1) (sum_k Lambda_k)^{-1} (Q_d^T x .. x Q_1^T) r,
+// with dense m x m generalized eigenvector matrices Q_k (Q^T M Q = I). It is the
+// comparator of the IFFD preconditioner: every direction costs a dense
+// contraction (2 m flops per entry), O(N^{1+1/d}) per apply.
+//
+// One launch contracts all pencils along one direction with A = Q^T (FWD) or
+// A = Q (BWD); FUSED does Q^T, the eigenvalue scaling and Q on the last
+// direction. A CTA holds 32 pencils in shared memory and computes the
+// 128 x 32 output blocks of C = A B with a 4 x 4 register block per thread,
+// staging 32-column slabs of A through shared memory. FP64 FMA throughput
+// bounds it.
+#include "device_common.cuh"
+#include "kernels.h"
+#include "fd.h"
+
+namespace iffd {
+
+constexpr int kFdPP = 32;   // pencils per CTA
+constexpr int kFdBI = 128;  // output rows per block
+constexpr int kFdBJ = 32;   // A slab width
+
+// C[i][pc] = sum_j A[i][j] * B[pc][j] for the tile (B rows = pencils), in place
+// into Cout (separate smem array).
+__device__ void fd_contract(const double* __restrict__ A, int m, const double* Bt, int ldb, double* Ct,
+                            double* As) {
+  const int tid = threadIdx.x;
+  const int ti = tid >> 3;        // 0..31 -> rows 4*ti .. 4*ti+3
+  const int tp = tid & 7;         // 0..7  -> pencils 4*tp .. 4*tp+3
+  for (int i0 = 0; i0 < m; i0 += kFdBI) {
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int j0 = 0; j0 < m; j0 += kFdBJ) {
+      __syncthreads();
+      // stage A[i0 .. i0+127][j0 .. j0+31] as As[jj][ii] (ii fastest)
+      for (int e = tid; e < kFdBI * kFdBJ; e += blockDim.x) {
+        const int ii = e / kFdBJ, jj = e - ii * kFdBJ;
+        const int i = i0 + ii, j = j0 + jj;
+        As[jj * (kFdBI + 1) + ii] = (i < m && j < m) ? __ldg(A + (size_t)i * m + j) : 0.0;
+      }
+      __syncthreads();
+      const int jn = min(kFdBJ, m - j0);
+      for (int jj = 0; jj < jn; ++jj) {
+        double a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[jj * (kFdBI + 1) + 4 * ti + r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = Bt[(4 * tp + c) * ldb + j0 + jj];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + 4 * ti + r;
+      if (i < m) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Ct[(4 * tp + c) * ldb + i] = acc[r][c];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+struct FdTile {
+  long long base, S, pstr;
+  int nvalid, ia, ib;
+};
+
+__device__ __forceinline__ FdTile fd_tile(const Dims& dims, int axis, int tile) {
+  FdTile g;
+  const int m0 = dims.m[0], m1 = dims.m[1];
+  const int PP = kFdPP;
+  if (axis == 0) {
+    const long long rows = dims.N / m0;
+    const long long r0 = (long long)tile * PP;
+    g.base = r0 * m0;
+    g.S = 1;
+    g.pstr = m0;
+    g.nvalid = (int)min((long long)PP, rows - r0);
+    g.ia = 0;
+    g.ib = 0;
+  } else {
+    const int ntx = (m0 + PP - 1) / PP;
+    const int rest = tile / ntx;
+    const int x0 = (tile - rest * ntx) * PP;
+    g.S = (axis == 1) ? (long long)m0 : (long long)m0 * m1;
+    g.base = x0 + ((axis == 1) ? (long long)rest * m0 * m1 : (long long)rest * m0);
+    g.pstr = 1;
+    g.nvalid = min(PP, m0 - x0);
+    g.ia = x0;
+    g.ib = rest;
+  }
+  return g;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const double* __restrict__ QT,
+        const double* __restrict__ Q, const double* __restrict__ lam, const double* __restrict__ lamA,
+        const double* __restrict__ lamB, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = dims.m[axis];
+  double* B = reinterpret_cast<double*>(smem);
+  double* C = B + (size_t)kFdPP * ldb;
+  double* As = C + (size_t)kFdPP * ldb;
+  const FdTile g = fd_tile(dims, axis, blockIdx.x);
+  for (int e = threadIdx.x; e < kFdPP * m; e += blockDim.x) {
+    int pc, i;
+    if (axis == 0) { pc = e / m; i = e - pc * m; }
+    else { i = e / kFdPP; pc = e - i * kFdPP; }
+    double v = 0.0;
+    if (pc < g.nvalid) v = in[g.base + pc * g.pstr + i * g.S];
+    B[pc * ldb + i] = v;
+  }
+  __syncthreads();
+  double* res = B;
+  if (MODE == PM_FWD || MODE == PM_FUSED) {
+    fd_contract(QT, m, B, ldb, C, As);
+    res = C;
+  }
+  if (MODE == PM_FUSED) {
+    for (int e = threadIdx.x; e < kFdPP * m; e += blockDim.x) {
+      const int pc = e / m, i = e - pc * m;
+      if (pc >= g.nvalid) continue;  // padding pencils of a ragged tile
+      double den = __ldg(lam + i) + __ldg(lamA + g.ia + pc);
+      if (dims.d == 3) den += __ldg(lamB + g.ib);
+      C[pc * ldb + i] = C[pc * ldb + i] / den;
+    }
+    __syncthreads();
+    fd_contract(Q, m, C, ldb, B, As);
+    res = B;
+  }
+  if (MODE == PM_BWD) {
+    fd_contract(Q, m, B, ldb, C, As);
+    res = C;
+  }
+  for (int e = threadIdx.x; e < kFdPP * m; e += blockDim.x) {
+    int pc, i;
+    if (axis == 0) { pc = e / m; i = e - pc * m; }
+    else { i = e / kFdPP; pc = e - i * kFdPP; }
+    if (pc < g.nvalid) out[g.base + pc * g.pstr + i * g.S] = res[pc * ldb + i];
+  }
+}
+
+int fd_tiles(const Dims& dims, int axis) {
+  if (axis == 0) return (int)((dims.N / dims.m[0] + kFdPP - 1) / kFdPP);
+  const int ntx = (dims.m[0] + kFdPP - 1) / kFdPP;
+  const long long rest = dims.N / ((long long)dims.m[0] * dims.m[axis]);
+  return (int)(ntx * rest);
+}
+
+size_t fd_smem(int m) {
+  const int ldb = m | 1;
+  return (size_t)2 * kFdPP * ldb * sizeof(double) + (size_t)kFdBJ * (kFdBI + 1) * sizeof(double);
+}
+
+cudaError_t launch_fd_pass(int mode, const double* in, double* out, const Dims& dims, int axis,
+                           const double* QT, const double* Q, const double* lam, const double* lamA,
+                           const double* lamB, const int* done, cudaStream_t st) {
+  const int m = dims.m[axis];
+  const int ldb = m | 1;
+  const size_t sm = fd_smem(m);
+  const int tiles = fd_tiles(dims, axis);
+  cudaError_t e;
+  if (mode == PM_FWD) {
+    e = cudaFuncSetAttribute(fd_pass<PM_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    fd_pass<PM_FWD><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
+  } else if (mode == PM_BWD) {
+    e = cudaFuncSetAttribute(fd_pass<PM_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    fd_pass<PM_BWD><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
+  } else {
+    e = cudaFuncSetAttribute(fd_pass<PM_FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    fd_pass<PM_FUSED><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace iffd

@@ -1,0 +1,54 @@
+// Host-side construction of the univariate IFFD data (one parametric direction).
+//
+// Everything here runs once per (n, p, Dirichlet set) on the CPU in float64 and
+// produces the small tables the CUDA passes consume. No device code.
+#pragma once
+
+#include <string>
+#include <vector>
+
+namespace iffd {
+
+// Transform families of Table 1 that the device passes implement.
+enum TransformKind : int {
+  TK_DST1 = 0,   // p odd, D = {0,1}: U_reg = DST-I, U_reg^T = DST-I
+  TK_DST23 = 1,  // p even, D = {0,1}: U_reg = DST-III, U_reg^T = DST-II
+};
+
+struct Axis1D {
+  int n = 0, p = 0;          // elements, degree
+  int m = 0;                 // dim S_{p,h,D} = n + p - 2
+  int n_reg = 0, n_out = 0;  // eq. "reg_space_dim"
+  int kind = TK_DST23;
+  // V_reg (Section 4): rows 0..rowsL-1 x cols 0..nL-1 is the left edge block,
+  // the interior special function j (nL <= j < n_reg - nL) is the B-spline with
+  // reduced index j + o, and the right edge block is the mirror image:
+  // V_reg[m-1-r][n_reg-1-c] = VL[r][c].
+  int nL = 0, rowsL = 0, o = 0;
+  std::vector<double> VL;    // rowsL * nL, row-major
+  // W = V_out Q_out (m x n_out, row-major), significant only on rows
+  // [0, wlo) and [whi, m); the rows in between are below 1e-17 of max |W|.
+  std::vector<double> W;
+  int wlo = 0, whi = 0;
+  std::vector<double> lam;    // Lambda~ diagonal: Lambda_reg (n_reg) then Lambda_out (n_out)
+  std::vector<double> dtilde; // D~_reg diagonal (n_reg)
+  // Banded mass / stiffness of S_{p,h,D}: band[i*(2p+1) + (j-i+p)] = A[i][j].
+  std::vector<double> Mband, Kband;
+};
+
+// Builds all of the above. Returns an empty string on success, else a message.
+std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* out);
+
+// Exact generalized eigendecomposition K q = lambda M q, Q^T M Q = I
+// (dense, column-major Q: Q[i + j*m] = q_j[i]). Returns "" on success.
+std::string exact_fd_axis(const Axis1D& ax, std::vector<double>* Q, std::vector<double>* lam);
+
+// Symmetric cardinal B-spline B~_q at x = k/2 for integer k (exact recurrence).
+double cardinal_half(int q, int twice_x);
+
+// Radix decomposition of an FFT length: factors 8, 4, 2 first, then the odd
+// prime factors in increasing order (3 and 5 have register butterflies, every
+// other factor runs as a direct DFT stage).
+bool fft_factor(int L, std::vector<int>* radices);
+
+}  // namespace iffd

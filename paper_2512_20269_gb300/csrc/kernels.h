@@ -1,0 +1,76 @@
+// Host-visible launch interfaces of the IFFD CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace iffd {
+
+enum PassMode : int { PM_FWD = 0, PM_BWD = 1, PM_FUSED = 2 };
+
+template <typename Tc>
+struct PassLaunch {
+  Dims dims;
+  int axis;
+  int PP;   // pencils per CTA (even)
+  int ldt;  // shared-memory row length of the pencil tile
+  AxisTab<Tc> ax;
+  const Tc* lamA;  // eigenvalues of direction 0 (FUSED)
+  const Tc* lamB;  // eigenvalues of direction 1 (FUSED, d = 3)
+  const double* dot0;  // optional: partial (dot0, out) per CTA
+  const double* dot1;  // optional: partial (dot1, out) per CTA
+  double* partial;
+  const int* done;     // optional early-exit flag (PCG)
+};
+
+size_t precond_smem_bytes(int PP, int ldt, int L, size_t elt);
+int precond_tiles(const Dims& dims, int axis, int PP);
+
+template <typename Tc, typename Tin, typename Tout>
+cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- stiffness
+// Banded 1D operator data for one direction (device pointers).
+struct BandTab {
+  int m, p;
+  const double* Mb;  // m * (2p+1) band rows of M
+  const double* Kb;  // m * (2p+1) band rows of K
+  const double* Mt;  // p+1 Toeplitz coefficients of interior rows of M
+  const double* Kt;  // p+1 Toeplitz coefficients of interior rows of K
+  int ilo, ihi;      // rows [ilo, ihi) are Toeplitz interior rows
+};
+
+enum StiffStage : int { SS_FIRST = 0, SS_MID = 1, SS_LAST = 2 };
+
+struct StiffLaunch {
+  Dims dims;
+  int axis;
+  int PP;
+  int ldt;
+  BandTab bt;
+};
+
+// FIRST: (optionally p_new = z + beta p) -> T1 = M u, T2 = K u
+// MID:   T1 <- M T1, T2 <- K T1 + M T2
+// LAST:  out = K T1 + M T2, optional partial (dotv, out)
+cudaError_t launch_stiff_first(const StiffLaunch& S, const double* u, const double* z, double* p_io,
+                               const double* beta, int pmode, double* T1, double* T2, const int* done,
+                               cudaStream_t st);
+cudaError_t launch_stiff_mid(const StiffLaunch& S, double* T1, double* T2, const int* done, cudaStream_t st);
+cudaError_t launch_stiff_last(const StiffLaunch& S, const double* T1, const double* T2, double* out,
+                              const double* dotv, double* partial, const int* done, cudaStream_t st);
+int stiff_tiles(const Dims& dims, int axis, int PP);
+
+// ---------------------------------------------------------------- PCG vectors
+int vec_grid(long long N);
+cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st);
+cudaError_t launch_pcg_update(double* x, double* r, const double* p, const double* q, const SolveState* s,
+                              long long N, double* partial, const int* done, cudaStream_t st);
+// phase-specific reduction of `nparts` partial sums into the solve state
+enum FinalizePhase : int { FP_FF = 0, FP_RZ0 = 1, FP_PQ = 2, FP_RR = 3, FP_RZ = 4, FP_RZ_FLEX = 5, FP_TRUE = 6 };
+cudaError_t launch_finalize(SolveState* s, const double* partial, int nparts, int phase, double tol2, int maxit,
+                            cudaStream_t st);
+cudaError_t launch_residual(const double* f, const double* Au, long long N, double* partial, cudaStream_t st);
+
+}  // namespace iffd

@@ -1,0 +1,162 @@
+// PCG vector kernels and deterministic reductions (Section 3 of the paper;
+// zero initial guess and relative-residual stopping rule of Section 7).
+//
+// Every kernel writes one partial sum per CTA; `finalize` reduces them in a
+// fixed order (one CTA, fixed tree), so a solve is bitwise reproducible for a
+// given problem shape. All scalars of the iteration live in device memory
+// (SolveState) and every kernel returns immediately once `done` is set, so the
+// host can enqueue iterations ahead without synchronising.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace iffd {
+
+int vec_grid(long long N) {
+  long long g = (N + 1023) / 1024;
+  if (g > 4 * 152) g = 4 * 152;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kThreads / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// x = 0, r = f, partial ||f||^2
+__global__ void __launch_bounds__(kThreads)
+pcg_init(const double* __restrict__ f, double* __restrict__ x, double* __restrict__ r, long long N,
+         double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double v = f[i];
+    x[i] = 0.0;
+    r[i] = v;
+    s = fma(v, v, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// x += alpha p, r -= alpha q, partial ||r||^2
+__global__ void __launch_bounds__(kThreads)
+pcg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
+           const SolveState* __restrict__ st, long long N, double* __restrict__ partial, const int* __restrict__ done) {
+  if (*((volatile const int*)done)) return;
+  const double alpha = st->alpha;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double rv = fma(-alpha, q[i], r[i]);
+    r[i] = rv;
+    s = fma(rv, rv, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// partial ||f - Au||^2
+__global__ void __launch_bounds__(kThreads)
+residual_kernel(const double* __restrict__ f, const double* __restrict__ Au, long long N, double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double d = f[i] - Au[i];
+    s = fma(d, d, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// status codes mirror iffd_status in include/iffd.h
+constexpr int kStOk = 0, kStNotConverged = 6, kStBreakdown = 7;
+
+__global__ void __launch_bounds__(1024)
+finalize_kernel(SolveState* st, const double* __restrict__ partial, int nparts, int phase, double tol2, int maxit) {
+  __shared__ double red[32];
+  if (phase != FP_FF && phase != FP_TRUE && st->done) return;
+  // fixed-order reduction: thread t sums parts t, t+1024, ...; then a fixed tree
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  switch (phase) {
+    case FP_FF:
+      st->ff = tot;
+      st->iters = 0;
+      st->status = kStOk;
+      st->done = (tot == 0.0) ? 1 : 0;
+      st->rr = tot;
+      break;
+    case FP_RZ0:
+      st->rz = tot;
+      if (!(tot > 0.0)) { st->status = kStBreakdown; st->done = 1; }
+      break;
+    case FP_PQ:
+      st->pq = tot;
+      if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
+      else st->alpha = st->rz / tot;
+      break;
+    case FP_RR:
+      st->rr = tot;
+      st->iters += 1;
+      if (!isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
+      else if (tot <= tol2 * st->ff) { st->status = kStOk; st->done = 1; }
+      else if (st->iters >= maxit) { st->status = kStNotConverged; st->done = 1; }
+      break;
+    case FP_RZ:
+      if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
+      else { st->beta = tot / st->rz; st->rz_old = st->rz; st->rz = tot; }
+      break;
+    case FP_RZ_FLEX:
+      // flexible (Polak-Ribiere) beta = (z_new, r_new - r_old) / (z_old, r_old)
+      //                              = -alpha (z_new, q) / rz_old;
+      // partial[0..nparts) holds (r,z), partial[nparts..2 nparts) holds (q,z)
+      {
+        double zq = 0.0;
+        for (int i = 0; i < nparts; ++i) zq += partial[nparts + i];
+        st->zq = zq;
+        if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
+        else { st->beta = -st->alpha * zq / st->rz; st->rz_old = st->rz; st->rz = tot; }
+      }
+      break;
+    case FP_TRUE:
+      st->zq = tot;  // ||f - A u||^2 of the final iterate
+      break;
+  }
+}
+
+cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st) {
+  pcg_init<<<vec_grid(N), kThreads, 0, st>>>(f, x, r, N, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update(double* x, double* r, const double* p, const double* q, const SolveState* s,
+                              long long N, double* partial, const int* done, cudaStream_t st) {
+  pcg_update<<<vec_grid(N), kThreads, 0, st>>>(x, r, p, q, s, N, partial, done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double* f, const double* Au, long long N, double* partial, cudaStream_t st) {
+  residual_kernel<<<vec_grid(N), kThreads, 0, st>>>(f, Au, N, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(SolveState* s, const double* partial, int nparts, int phase, double tol2, int maxit,
+                            cudaStream_t st) {
+  finalize_kernel<<<1, 1024, 0, st>>>(s, partial, nparts, phase, tol2, maxit);
+  return cudaGetLastError();
+}
+
+}  // namespace iffd

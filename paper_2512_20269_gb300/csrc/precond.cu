@@ -1,0 +1,515 @@
+// IFFD preconditioner passes (eq. "preconditioner" of the paper):
+//   P^{-1} r = (Q~_d x .. x Q~_1) (sum_k Lambda~_k)^{-1} (Q~_d^T x .. x Q~_1^T) r,
+//   Q~ = [V_reg U_reg D~^{-1}, V_out Q_out]   (Sections 4 and 6).
+//
+// One kernel launch applies Q~^T (FWD), Q~ (BWD), or Q~^T, the eigenvalue
+// scaling and Q~ (FUSED, used on the last direction) to every pencil along one
+// direction. A CTA owns a tile of PP pencils: it loads them (coalesced along x)
+// into shared memory and, per pencil pair, runs
+//   FWD: remainder projections y_out = W^T r (W = V_out Q_out), the V_reg^T edge
+//        gather, Makhoul's reordering, a two-for-one complex Stockham FFT of
+//        length L and the separation / twiddle / D~^{-1} step, giving
+//        [D~^{-1} U^T V_reg^T r | Q_out^T V_out^T r];
+//   BWD: the transpose of the same steps (DST-III for even p, DST-I for odd p,
+//        Table 1) followed by the V_reg edge scatter and the rank-n_out update
+//        V_out Q_out z_out.
+// All arithmetic is in Tc (double, or float for the reduced-precision
+// transform variant); Tin/Tout are the global storage types.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace iffd {
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> ldc(const T* p) {
+  return {__ldg(p), __ldg(p + 1)};
+}
+
+// ------------------------------------------------------------- small DFTs
+// Forward DFTs y_t = sum_q v_q exp(-2 pi i q t / R) in registers.
+template <typename T>
+__device__ __forceinline__ void dft2(Cplx<T>* v) {
+  const Cplx<T> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft4(Cplx<T>* v) {
+  const Cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  const Cplx<T> t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, mul_mi(t3));
+  v[3] = csub(t1, mul_mi(t3));
+}
+
+template <typename T>
+__device__ __forceinline__ void dft8(Cplx<T>* v) {
+  const T r = T(0.70710678118654752440084436210484903928);
+  Cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+  Cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+  dft4(e);
+  dft4(o);
+  // o_t *= exp(-2 pi i t / 8)
+  const Cplx<T> o1 = {(o[1].x + o[1].y) * r, (o[1].y - o[1].x) * r};
+  const Cplx<T> o2 = mul_mi(o[2]);
+  const Cplx<T> o3 = {(o[3].y - o[3].x) * r, -(o[3].x + o[3].y) * r};
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft3(Cplx<T>* v) {
+  const T c = T(-0.5);
+  const T s = T(-0.86602540378443864676372317075293618347);  // -sin(2 pi / 3)
+  const Cplx<T> t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+  const Cplx<T> y0 = cadd(v[0], t1);
+  const Cplx<T> m1 = {fma(c, t1.x, v[0].x), fma(c, t1.y, v[0].y)};
+  const Cplx<T> is = {-s * t2.y, s * t2.x};  // i * s * t2
+  v[0] = y0;
+  v[1] = cadd(m1, is);
+  v[2] = csub(m1, is);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft5(Cplx<T>* v) {
+  const T c1 = T(0.30901699437494742410229341718281905886);   // cos(2pi/5)
+  const T c2 = T(-0.80901699437494742410229341718281905886);  // cos(4pi/5)
+  const T s1 = T(0.95105651629515357211643933337938214340);   // sin(2pi/5)
+  const T s2 = T(0.58778525229247312916870595463907276860);   // sin(4pi/5)
+  const Cplx<T> t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const Cplx<T> t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  const Cplx<T> y0 = cadd(v[0], cadd(t1, t2));
+  const Cplx<T> m1 = {fma(c2, t2.x, fma(c1, t1.x, v[0].x)), fma(c2, t2.y, fma(c1, t1.y, v[0].y))};
+  const Cplx<T> m2 = {fma(c1, t2.x, fma(c2, t1.x, v[0].x)), fma(c1, t2.y, fma(c2, t1.y, v[0].y))};
+  const Cplx<T> n1 = {fma(s2, t4.x, s1 * t3.x), fma(s2, t4.y, s1 * t3.y)};
+  const Cplx<T> n2 = {fma(-s1, t4.x, s2 * t3.x), fma(-s1, t4.y, s2 * t3.y)};
+  v[0] = y0;
+  v[1] = cadd(m1, mul_mi(n1));
+  v[4] = csub(m1, mul_mi(n1));
+  v[2] = cadd(m2, mul_mi(n2));
+  v[3] = csub(m2, mul_mi(n2));
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void butterfly(const Cplx<T>* in, Cplx<T>* out, int j, int nb, int Ns, const T* tw) {
+  Cplx<T> v[R];
+  const int k = j % Ns;
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = in[j + q * nb];
+  if (Ns > 1) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = cmul(v[q], ldc(tw + 2 * ((q - 1) * Ns + k)));
+  }
+  if constexpr (R == 2) dft2(v);
+  else if constexpr (R == 3) dft3(v);
+  else if constexpr (R == 4) dft4(v);
+  else if constexpr (R == 5) dft5(v);
+  else dft8(v);
+  const int base = (j - k) * R + k;
+#pragma unroll
+  for (int t = 0; t < R; ++t) out[base + t * Ns] = v[t];
+}
+
+// Stockham autosort FFT of npairs independent length-L sequences stored
+// contiguously in bufA; ping-pongs with bufB. Returns the buffer holding the
+// natural-order result. Must be called by the whole CTA.
+// Radices 8, 4, 2, 3, 5 run as register butterflies; any other factor r runs as
+// a direct DFT stage in which each thread forms one output
+//   y_t(j) = sum_q in[j + q nb] exp(-2 pi i q (k + t Ns) / (Ns r)),  k = j mod Ns,
+// from a table of exp(-2 pi i s / (Ns r)), s < Ns r.
+template <typename T>
+__device__ Cplx<T>* fft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const AxisTab<T>& ax) {
+  const int L = ax.L;
+  Cplx<T>* src = bufA;
+  Cplx<T>* dst = bufB;
+  int Ns = 1;
+  for (int s = 0; s < ax.nst; ++s) {
+    const int r = ax.radix[s];
+    const int nb = L / r;
+    const T* tw = ax.tw + 2 * ax.twoff[s];
+    if (r == 8 || r == 4 || r == 2 || r == 3 || r == 5) {
+      const int total = npairs * nb;
+      for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int pr = w / nb;
+        const int j = w - pr * nb;
+        const Cplx<T>* in = src + (size_t)pr * L;
+        Cplx<T>* out = dst + (size_t)pr * L;
+        switch (r) {
+          case 8: butterfly<T, 8>(in, out, j, nb, Ns, tw); break;
+          case 4: butterfly<T, 4>(in, out, j, nb, Ns, tw); break;
+          case 2: butterfly<T, 2>(in, out, j, nb, Ns, tw); break;
+          case 3: butterfly<T, 3>(in, out, j, nb, Ns, tw); break;
+          default: butterfly<T, 5>(in, out, j, nb, Ns, tw); break;
+        }
+      }
+    } else {
+      const int NsR = Ns * r;
+      const int total = npairs * L;
+      for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int pr = w / L;
+        const int o = w - pr * L;
+        const int t = o / nb;
+        const int j = o - t * nb;
+        const int k = j % Ns;
+        const int step = k + t * Ns;
+        const Cplx<T>* in = src + (size_t)pr * L;
+        Cplx<T> acc = in[j];
+        int e = 0;
+        for (int q = 1; q < r; ++q) {
+          e += step;
+          if (e >= NsR) e -= NsR;
+          const Cplx<T> a = in[j + q * nb];
+          const Cplx<T> wv = ldc(tw + 2 * e);
+          acc.x = fma(a.x, wv.x, fma(-a.y, wv.y, acc.x));
+          acc.y = fma(a.x, wv.y, fma(a.y, wv.x, acc.y));
+        }
+        dst[(size_t)pr * L + (j - k) * r + k + t * Ns] = acc;
+      }
+    }
+    __syncthreads();
+    Cplx<T>* tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns *= r;
+  }
+  return src;
+}
+
+// y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1].
+template <typename T>
+__device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
+  if (i < ax.nL) {
+    T s = T(0);
+    for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + i), row[r], s);
+    return s;
+  }
+  if (i >= ax.n_reg - ax.nL) {
+    const int c = ax.n_reg - 1 - i;
+    T s = T(0);
+    for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + c), row[ax.m - 1 - r], s);
+    return s;
+  }
+  return row[i + ax.o];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+struct TileGeom {
+  long long base;  // global offset of element (pencil 0, i = 0)
+  long long S;     // element stride along the pencil
+  long long pstr;  // stride between consecutive pencils of the tile
+  int nvalid;      // pencils of this tile inside the array
+  int ia, ib;      // indices of the pencil-0 coordinates in the other directions
+};
+
+// Tiles: direction 0 -> PP consecutive rows; direction a > 0 -> PP consecutive
+// x positions at one value of the remaining coordinate.
+__device__ __forceinline__ TileGeom tile_geom(const Dims& dims, int axis, int PP, int tile) {
+  TileGeom g;
+  const int m0 = dims.m[0], m1 = dims.m[1];
+  if (axis == 0) {
+    const long long rows = dims.N / m0;
+    const long long r0 = (long long)tile * PP;
+    g.base = r0 * m0;
+    g.S = 1;
+    g.pstr = m0;
+    g.nvalid = (int)min((long long)PP, rows - r0);
+    g.ia = 0;
+    g.ib = 0;
+  } else {
+    const int ntx = (m0 + PP - 1) / PP;
+    const int rest = tile / ntx;
+    const int x0 = (tile - rest * ntx) * PP;
+    g.S = (axis == 1) ? (long long)m0 : (long long)m0 * m1;
+    g.base = x0 + ((axis == 1) ? (long long)rest * m0 * m1 : (long long)rest * m0);
+    g.pstr = 1;
+    g.nvalid = min(PP, m0 - x0);
+    g.ia = x0;    // x index of pencil 0
+    g.ib = rest;  // the other coordinate (z for axis 1, y for axis 2)
+  }
+  return g;
+}
+
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, AxisTab<Tc> ax,
+             const Tc* __restrict__ lamA, const Tc* __restrict__ lamB,
+             const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+             double* __restrict__ partial, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int npairs = PP / 2;
+  const int L = ax.L;
+  const int m = ax.m;
+  Cplx<Tc>* bufA = reinterpret_cast<Cplx<Tc>*>(smem);
+  Cplx<Tc>* bufB = bufA + (size_t)npairs * L;
+  Tc* tile = reinterpret_cast<Tc*>(bufB + (size_t)npairs * L);
+  Tc* outv = tile + (size_t)PP * ldt;  // PP * kMaxNout
+
+  const TileGeom g = tile_geom(dims, axis, PP, blockIdx.x);
+  const int tid = threadIdx.x;
+
+  // ---- load the tile (zero-filled beyond the array)
+  for (int e = tid; e < PP * m; e += blockDim.x) {
+    int pc, i;
+    if (axis == 0) { pc = e / m; i = e - pc * m; }
+    else { i = e / PP; pc = e - i * PP; }
+    Tc v = Tc(0);
+    if (pc < g.nvalid) v = (Tc)in[g.base + pc * g.pstr + i * g.S];
+    tile[pc * ldt + i] = v;
+  }
+  __syncthreads();
+
+  const int N = ax.n_reg;
+  if (MODE == PM_FWD || MODE == PM_FUSED) {
+    // remainder projections y_out = W^T r over the two support ranges of W
+    // (one warp per (pencil, column); the loops run over exactly n_out columns)
+    const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+    const int nw = ax.n_out;
+    for (int job = warp; job < PP * nw; job += nwarps) {
+      const int pc = job / nw, k = job - pc * nw;
+      const Tc* row = tile + pc * ldt;
+      Tc acc = Tc(0);
+      for (int i = lane; i < ax.wlo; i += 32) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
+      for (int i = ax.whi + lane; i < m; i += 32) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) outv[pc * kMaxNout + k] = acc;
+    }
+    // pack the regular part of two pencils into one complex sequence
+    for (int w = tid; w < npairs * L; w += blockDim.x) {
+      const int pr = w / L, l = w - pr * L;
+      const Tc* ra = tile + (2 * pr) * ldt;
+      const Tc* rb = ra + ldt;
+      Tc va, vb;
+      if (ax.kind == 1) {  // DST-II: Makhoul order of u_i = (-1)^i y_i
+        const int i = (l < (N + 1) / 2) ? 2 * l : 2 * (N - 1 - l) + 1;
+        const Tc sg = (i & 1) ? Tc(-1) : Tc(1);
+        va = sg * reg_gather(ra, i, ax);
+        vb = sg * reg_gather(rb, i, ax);
+      } else {  // DST-I: odd extension of length L = 2n
+        const int n = N + 1;
+        if (l == 0 || l == n) { va = Tc(0); vb = Tc(0); }
+        else if (l < n) { va = reg_gather(ra, l - 1, ax); vb = reg_gather(rb, l - 1, ax); }
+        else { va = -reg_gather(ra, 2 * n - 1 - l, ax); vb = -reg_gather(rb, 2 * n - 1 - l, ax); }
+      }
+      bufA[w] = {va, vb};
+    }
+    __syncthreads();
+    const Cplx<Tc>* Z = fft_block(bufA, bufB, npairs, ax);
+    if (ax.kind == 1) {
+      const int K = N / 2 + 1;
+      for (int w = tid; w < npairs * K; w += blockDim.x) {
+        const int pr = w / K, k = w - pr * K;
+        Tc* ra = tile + (2 * pr) * ldt;
+        Tc* rb = ra + ldt;
+        const Cplx<Tc> zk = Z[(size_t)pr * L + k];
+        const Cplx<Tc> zm = Z[(size_t)pr * L + (k == 0 ? 0 : N - k)];
+        const Tc Ar = zk.x + zm.x, Ai = zk.y - zm.y;
+        const Tc Br = zk.y + zm.y, Bi = zm.x - zk.x;
+        const Tc* t4 = ax.post + 4 * k;
+        const Tc A = __ldg(t4), B = __ldg(t4 + 1), C = __ldg(t4 + 2), E = __ldg(t4 + 3);
+        ra[N - 1 - k] = fma(A, Ar, B * Ai);
+        rb[N - 1 - k] = fma(A, Br, B * Bi);
+        if (k > 0 && 2 * k != N) {
+          ra[k - 1] = fma(C, Ar, -E * Ai);
+          rb[k - 1] = fma(C, Br, -E * Bi);
+        }
+      }
+    } else {
+      for (int w = tid; w < npairs * N; w += blockDim.x) {
+        const int pr = w / N, j = w - pr * N;
+        const Cplx<Tc> z = Z[(size_t)pr * L + j + 1];
+        const Tc sc = __ldg(ax.post + j);
+        tile[(2 * pr) * ldt + j] = -sc * z.y;
+        tile[(2 * pr + 1) * ldt + j] = sc * z.x;
+      }
+    }
+    for (int w = tid; w < PP * ax.n_out; w += blockDim.x) {
+      const int pc = w / ax.n_out, k = w - pc * ax.n_out;
+      tile[pc * ldt + N + k] = outv[pc * kMaxNout + k];
+    }
+    __syncthreads();
+  }
+
+  if (MODE == PM_FUSED) {
+    // divide by the summed eigenvalues of all directions
+    for (int e = tid; e < PP * m; e += blockDim.x) {
+      const int pc = e / m, i = e - pc * m;
+      if (pc >= g.nvalid) continue;  // padding pencils of a ragged tile
+      Tc den = __ldg(ax.lam + i);
+      if (dims.d == 3) den += __ldg(lamA + g.ia + pc) + __ldg(lamB + g.ib);
+      else den += __ldg(lamA + g.ia + pc);
+      tile[pc * ldt + i] = tile[pc * ldt + i] / den;
+    }
+    __syncthreads();
+  }
+
+  if (MODE == PM_BWD || MODE == PM_FUSED) {
+    for (int w = tid; w < PP * ax.n_out; w += blockDim.x) {
+      const int pc = w / ax.n_out, k = w - pc * ax.n_out;
+      outv[pc * kMaxNout + k] = tile[pc * ldt + N + k];
+    }
+    if (ax.kind == 1) {
+      const int K = N / 2 + 1;
+      for (int w = tid; w < npairs * K; w += blockDim.x) {
+        const int pr = w / K, k = w - pr * K;
+        const Tc* za = tile + (2 * pr) * ldt;
+        const Tc* zb = za + ldt;
+        const Tc* t4 = ax.post + 4 * k;
+        const Tc A = __ldg(t4), B = __ldg(t4 + 1), C = __ldg(t4 + 2), E = __ldg(t4 + 3);
+        Cplx<Tc>* G = bufA + (size_t)pr * L;
+        if (k == 0 || 2 * k == N) {
+          const Tc s = A + A;
+          G[k] = {s * za[N - 1 - k], s * zb[N - 1 - k]};
+        } else {
+          const Tc ar = fma(A, za[N - 1 - k], C * za[k - 1]);
+          const Tc ai = fma(-B, za[N - 1 - k], E * za[k - 1]);
+          const Tc br = fma(A, zb[N - 1 - k], C * zb[k - 1]);
+          const Tc bi = fma(-B, zb[N - 1 - k], E * zb[k - 1]);
+          G[k] = {ar - bi, ai + br};
+          G[N - k] = {ar + bi, br - ai};
+        }
+      }
+    } else {
+      const int n = N + 1;
+      for (int w = tid; w < npairs * L; w += blockDim.x) {
+        const int pr = w / L, l = w - pr * L;
+        const Tc* za = tile + (2 * pr) * ldt;
+        const Tc* zb = za + ldt;
+        Tc va, vb;
+        if (l == 0 || l == n) { va = Tc(0); vb = Tc(0); }
+        else if (l < n) {
+          const Tc sc = __ldg(ax.post + l - 1);
+          va = sc * za[l - 1];
+          vb = sc * zb[l - 1];
+        } else {
+          const Tc sc = __ldg(ax.post + 2 * n - 1 - l);
+          va = -sc * za[2 * n - 1 - l];
+          vb = -sc * zb[2 * n - 1 - l];
+        }
+        bufA[w] = {va, vb};
+      }
+    }
+    __syncthreads();
+    const Cplx<Tc>* Z = fft_block(bufA, bufB, npairs, ax);
+    // scatter: x = V_reg w + W z_out
+    for (int e = tid; e < PP * m; e += blockDim.x) {
+      const int pc = e / m, i = e - pc * m;
+      const int pr = pc >> 1;
+      const bool isb = pc & 1;
+      const Cplx<Tc>* Zp = Z + (size_t)pr * L;
+      auto wreg = [&](int j) -> Tc {
+        if (ax.kind == 1) {
+          const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+          const Cplx<Tc> z = Zp[l];
+          const Tc v = isb ? z.y : z.x;
+          return (j & 1) ? -v : v;
+        } else {
+          const Cplx<Tc> z = Zp[j + 1];
+          return isb ? z.x : -z.y;
+        }
+      };
+      Tc x;
+      if (i < ax.rowsL) {
+        x = Tc(0);
+        for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
+      } else if (i >= m - ax.rowsL) {
+        const int r = m - 1 - i;
+        x = Tc(0);
+        for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + r * ax.nL + c), wreg(N - 1 - c), x);
+      } else {
+        x = wreg(i - ax.o);
+      }
+      if (i < ax.wlo || i >= ax.whi) {
+        for (int k = 0; k < ax.n_out; ++k) x = fma(__ldg(ax.W + i * ax.n_out + k), outv[pc * kMaxNout + k], x);
+      }
+      tile[pc * ldt + i] = x;
+    }
+    __syncthreads();
+  }
+
+  // ---- store (and, on the last pass of a PCG step, partial dot products)
+  double d0 = 0.0, d1 = 0.0;
+  for (int e = tid; e < PP * m; e += blockDim.x) {
+    int pc, i;
+    if (axis == 0) { pc = e / m; i = e - pc * m; }
+    else { i = e / PP; pc = e - i * PP; }
+    if (pc < g.nvalid) {
+      const long long off = g.base + pc * g.pstr + i * g.S;
+      const Tc v = tile[pc * ldt + i];
+      out[off] = (Tout)v;
+      if (NDOT >= 1) d0 = fma(__ldg(dotv0 + off), (double)(Tout)v, d0);
+      if (NDOT >= 2) d1 = fma(__ldg(dotv1 + off), (double)(Tout)v, d1);
+    }
+  }
+  if (NDOT >= 1) {
+    __shared__ double red[2][kThreads / 32];
+    d0 = warp_sum(d0);
+    d1 = warp_sum(d1);
+    if ((tid & 31) == 0) { red[0][tid >> 5] = d0; red[1][tid >> 5] = d1; }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s0 += red[0][w]; s1 += red[1][w]; }
+      partial[blockIdx.x] = s0;
+      if (NDOT >= 2) partial[gridDim.x + blockIdx.x] = s1;
+    }
+  }
+}
+
+// ------------------------------------------------------------ host launchers
+size_t precond_smem_bytes(int PP, int ldt, int L, size_t elt) {
+  return (size_t)2 * (PP / 2) * L * 2 * elt + (size_t)PP * ldt * elt + (size_t)PP * kMaxNout * elt;
+}
+
+int precond_tiles(const Dims& dims, int axis, int PP) {
+  if (axis == 0) return (int)((dims.N / dims.m[0] + PP - 1) / PP);
+  const int ntx = (dims.m[0] + PP - 1) / PP;
+  const long long rest = dims.N / ((long long)dims.m[0] * dims.m[axis]);
+  return (int)(ntx * rest);
+}
+
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  auto kern = precond_pass<Tc, Tin, Tout, MODE, NDOT>;
+  const size_t sm = precond_smem_bytes(P.PP, P.ldt, P.ax.L, sizeof(Tc));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int tiles = precond_tiles(P.dims, P.axis, P.PP);
+  kern<<<tiles, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.PP, P.ldt, P.ax, P.lamA, P.lamB, P.dot0,
+                                     P.dot1, P.partial, P.done);
+  return cudaGetLastError();
+}
+
+template <typename Tc, typename Tin, typename Tout>
+cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
+  if (mode == PM_FWD) return launch_pass_t<Tc, Tin, Tout, PM_FWD, 0>(P, in, out, st);
+  if (mode == PM_FUSED) return launch_pass_t<Tc, Tin, Tout, PM_FUSED, 0>(P, in, out, st);
+  if (ndot == 0) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 0>(P, in, out, st);
+  if (ndot == 1) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 1>(P, in, out, st);
+  return launch_pass_t<Tc, Tin, Tout, PM_BWD, 2>(P, in, out, st);
+}
+
+template cudaError_t launch_pass<double, double, double>(const PassLaunch<double>&, int, int, const double*,
+                                                         double*, cudaStream_t);
+template cudaError_t launch_pass<float, double, float>(const PassLaunch<float>&, int, int, const double*, float*,
+                                                       cudaStream_t);
+template cudaError_t launch_pass<float, float, float>(const PassLaunch<float>&, int, int, const float*, float*,
+                                                      cudaStream_t);
+template cudaError_t launch_pass<float, float, double>(const PassLaunch<float>&, int, int, const float*, double*,
+                                                       cudaStream_t);
+
+}  // namespace iffd

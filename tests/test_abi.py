@@ -1,0 +1,98 @@
+"""CPU checks of the C ABI: the in-tree library loads, exports every entry point
+declared in include/iffd.h, and its host-side 1D setup (no GPU involved)
+matches the oracle's independent construction of the same objects."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import splitting
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(iffd_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_20269_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2512_20269_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2512_20269_gb300 import _lib
+    names = declared_symbols()
+    assert "iffd_pcg_solve" in names and "iffd_setup" in names
+    bound = {s[0] for s in _lib.SIGNATURES}
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in bound, f"{name} has no ctypes signature"
+
+
+def test_error_paths_without_gpu(lib):
+    """Argument errors are reported with a status and a message, not a crash."""
+    import ctypes
+    from paper_2512_20269_gb300 import _lib
+    d = (ctypes.c_int * 2)(1, 1)
+    rc = lib.iffd_host_axis(4, 4, d, None, None, None, None, None, None, None, None, None)
+    assert rc == 2 and b"exceed" in lib.iffd_last_error()
+    rc = lib.iffd_host_axis(16, 3, (ctypes.c_int * 2)(0, 1), None, None, None, None, None, None, None, None, None)
+    assert rc == 2
+    assert lib.iffd_default_options(None) == 1
+    assert lib.iffd_destroy(None) == 0
+    h = ctypes.c_void_p()
+    rc = lib.iffd_setup(4, (ctypes.c_int * 3)(8, 8, 8), 3, (ctypes.c_int * 8)(*[1] * 8), None, None, ctypes.byref(h))
+    assert rc == 1
+    rc = lib.iffd_setup(2, (ctypes.c_int * 2)(8, 8), 3, (ctypes.c_int * 4)(0, 0, 0, 0), None, None, ctypes.byref(h))
+    assert rc == 3  # all-Neumann: singular
+
+
+@pytest.mark.parametrize("n,p", [(16, 1), (16, 2), (16, 3), (16, 4), (17, 5), (20, 6), (21, 7), (24, 8),
+                                 (64, 3), (256, 4)])
+def test_host_setup_matches_oracle(lib, n, p):
+    """Banded M/K, V_reg (knot insertion vs L2 projection), Lambda_reg, D~_reg
+    and the remainder operator W diag(1/Lambda_out) W^T (basis independent)."""
+    from paper_2512_20269_gb300 import host_axis
+    h = host_axis(n, p)
+    s = splitting.axis_split(n, p, (0, 1))
+    m, bw = s.m, 2 * p + 1
+    assert (h["m"], h["n_reg"], h["n_out"]) == (s.m, s.n_reg, s.n_out)
+    M = np.zeros((m, m))
+    K = np.zeros((m, m))
+    for i in range(m):
+        for dd in range(bw):
+            j = i + dd - p
+            if 0 <= j < m:
+                M[i, j] = h["M_band"][i, dd]
+                K[i, j] = h["K_band"][i, dd]
+    np.testing.assert_allclose(M, s.M, atol=1e-14 * np.abs(s.M).max())
+    np.testing.assert_allclose(K, s.K, atol=1e-13 * np.abs(s.K).max())
+    nr, nL, o = h["n_reg"], p // 2, (p - 1) // 2
+    V = np.zeros((m, nr))
+    for c in range(nL):
+        V[:p - 1, c] = h["VL"][:, c]
+        V[m - 1 - np.arange(p - 1), nr - 1 - c] = h["VL"][:, c]
+    for j in range(nL, nr - nL):
+        V[j + o, j] = 1.0
+    np.testing.assert_allclose(V, s.V_reg, atol=1e-12)
+    np.testing.assert_allclose(h["lam"][:nr], s.lam_reg, rtol=1e-12)
+    np.testing.assert_allclose(h["dtilde"], s.Dt, rtol=1e-12)
+    if s.n_out:
+        lo, W = h["lam"][nr:], h["W"]
+        A1 = W @ np.diag(1 / lo) @ W.T
+        Wo = s.V_out @ s.Q_out
+        A2 = Wo @ np.diag(1 / s.lam_out) @ Wo.T
+        np.testing.assert_allclose(A1, A2, atol=1e-12 * np.abs(A2).max())
+        np.testing.assert_allclose(lo, s.lam_out, rtol=1e-12)

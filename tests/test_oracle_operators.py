@@ -208,3 +208,14 @@ def test_p11_table_square_iterations_n256():
     got = _table_counts(256, g["p"])
     for a, b in zip(got, ref):
         assert abs(a - b) <= 1, (got, ref)
+
+
+def test_sparse_and_dense_apply_agree():
+    """The sparse route of apply_along (used for large grids) equals the dense one."""
+    import scipy.sparse
+    M, K = splines.mass_stiffness(9, 3, (0, 1))
+    u = np.random.default_rng(7).standard_normal((M.shape[0],) * 3)
+    MK = [(M, K)] * 3
+    MKs = [(scipy.sparse.csr_matrix(M), scipy.sparse.csr_matrix(K))] * 3
+    np.testing.assert_allclose(operators.stiffness_apply(u, MKs), operators.stiffness_apply(u, MK), rtol=1e-13,
+                               atol=1e-13 * np.abs(K).max())
