@@ -102,7 +102,7 @@ def ncu_traffic(kind: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -114,7 +114,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(gpu_index), "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -215,6 +215,23 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def reduce_max_ms(ms: float, dist, device: str) -> float:
+    """Max of the per-rank timed-region durations (the slowest replica bounds
+    the job). `dist` is torch.distributed (or None for one rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(dofs_per_solve: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job DoF/s of `world` independent replicas that each solved
+    `steps` problems of `dofs_per_solve` DoFs within `max_ms` milliseconds."""
+    return dofs_per_solve * steps * world / (max_ms / 1e3)
+
+
 def workload_config(w):
     return {"workload": w.name, "d": w.d, "n": w.n, "p": w.p, "N": w.N, "rhs": f"{w.dist} seed {w.seed}",
             "precond": "IFFD", "precision": "fp64", "rtol": 1e-8, "boundary": "Dirichlet on all faces",
@@ -224,7 +241,7 @@ def workload_config(w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -284,11 +301,8 @@ def main():
     plan.profile_enable(False)
     gpu_launches = plan.launch_count() - launches0
     prof = plan.profile_read()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = w.N * args.steps * world / (ms / 1e3)
+    ms = reduce_max_ms(ms, dist, "cuda")
+    value = replica_throughput(w.N, args.steps, world, ms)
 
     # ---------------- per-kernel roofline (dominant kernel by device time)
     n_out = w.p - 2 if w.p % 2 == 0 else w.p - 1

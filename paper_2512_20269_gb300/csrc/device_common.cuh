@@ -53,6 +53,66 @@ struct AxisTab {
   const T* tw;    // complex FFT twiddles (interleaved), per stage offsets twoff
 };
 
+// Pencil tiles. The pencils along direction `axis` are numbered q = 0..Q-1:
+// for axis 0, q is the row index (the (y, z) pair, y fastest); for axis a > 0,
+// q = x + m0 * rest with rest the remaining coordinate (z for axis 1, y for
+// axis 2), so consecutive pencils of a tile are consecutive in x (coalesced)
+// and a tile may continue across the edge of the x range instead of leaving
+// part of a CTA idle. A CTA owns PP consecutive pencils; pencil pc starts at
+// pbase[pc] and its entries are pbase[pc] + i * S. ia/ib are the pencil's
+// coordinates in the other two directions (x, rest for axis > 0; y, z for
+// axis 0). Padding pencils (q >= Q) alias the last pencil and are never stored.
+struct TileInfo {
+  long long S;
+  int nvalid;
+};
+
+__device__ __forceinline__ long long num_pencils(const Dims& dims, int axis) { return dims.N / dims.m[axis]; }
+
+__device__ __forceinline__ TileInfo tile_setup(const Dims& dims, int axis, int PP, long long tile, long long* pbase,
+                                               int* pia, int* pib) {
+  const int m0 = dims.m[0], m1 = dims.m[1];
+  const long long Q = num_pencils(dims, axis);
+  const long long q0 = tile * PP;
+  TileInfo t;
+  t.nvalid = (int)min((long long)PP, Q - q0);
+  t.S = (axis == 0) ? 1 : ((axis == 1) ? (long long)m0 : (long long)m0 * m1);
+  for (int pc = threadIdx.x; pc < PP; pc += blockDim.x) {
+    long long q = q0 + pc;
+    if (q >= Q) q = Q - 1;
+    long long base;
+    int ia, ib;
+    if (axis == 0) {
+      base = q * m0;
+      ia = (int)(q % m1);
+      ib = (int)(q / m1);
+    } else {
+      const long long x = q % m0, rest = q / m0;
+      ia = (int)x;
+      ib = (int)rest;
+      base = x + rest * ((axis == 1) ? (long long)m0 * m1 : (long long)m0);
+    }
+    pbase[pc] = base;
+    if (pia) pia[pc] = ia;
+    if (pib) pib[pc] = ib;
+  }
+  return t;
+}
+
+inline long long host_num_tiles(const Dims& dims, int axis, int PP) {
+  const long long Q = dims.N / dims.m[axis];
+  return (Q + PP - 1) / PP;
+}
+
+// v or -v without an FP64 (or FP32) instruction: flips the sign bit on the
+// integer pipe.
+__device__ __forceinline__ double neg_if(double v, bool neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+__device__ __forceinline__ float neg_if(float v, bool neg) {
+  return __int_as_float(__float_as_int(v) ^ ((int)neg << 31));
+}
+
 // Global run status shared by the kernels of one solve (device memory).
 struct SolveState {
   double rz, rz_old, pq, rr, ff, alpha, beta, zq;

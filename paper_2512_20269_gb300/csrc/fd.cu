@@ -67,38 +67,6 @@ __device__ void fd_contract(const double* __restrict__ A, int m, const double* B
   __syncthreads();
 }
 
-struct FdTile {
-  long long base, S, pstr;
-  int nvalid, ia, ib;
-};
-
-__device__ __forceinline__ FdTile fd_tile(const Dims& dims, int axis, int tile) {
-  FdTile g;
-  const int m0 = dims.m[0], m1 = dims.m[1];
-  const int PP = kFdPP;
-  if (axis == 0) {
-    const long long rows = dims.N / m0;
-    const long long r0 = (long long)tile * PP;
-    g.base = r0 * m0;
-    g.S = 1;
-    g.pstr = m0;
-    g.nvalid = (int)min((long long)PP, rows - r0);
-    g.ia = 0;
-    g.ib = 0;
-  } else {
-    const int ntx = (m0 + PP - 1) / PP;
-    const int rest = tile / ntx;
-    const int x0 = (tile - rest * ntx) * PP;
-    g.S = (axis == 1) ? (long long)m0 : (long long)m0 * m1;
-    g.base = x0 + ((axis == 1) ? (long long)rest * m0 * m1 : (long long)rest * m0);
-    g.pstr = 1;
-    g.nvalid = min(PP, m0 - x0);
-    g.ia = x0;
-    g.ib = rest;
-  }
-  return g;
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const double* __restrict__ QT,
@@ -110,14 +78,15 @@ fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const doubl
   double* B = reinterpret_cast<double*>(smem);
   double* C = B + (size_t)kFdPP * ldb;
   double* As = C + (size_t)kFdPP * ldb;
-  const FdTile g = fd_tile(dims, axis, blockIdx.x);
+  __shared__ long long pbase[kFdPP];
+  __shared__ int pia[kFdPP], pib[kFdPP];
+  const TileInfo g = tile_setup(dims, axis, kFdPP, blockIdx.x, pbase, pia, pib);
+  __syncthreads();
   for (int e = threadIdx.x; e < kFdPP * m; e += blockDim.x) {
     int pc, i;
     if (axis == 0) { pc = e / m; i = e - pc * m; }
     else { i = e / kFdPP; pc = e - i * kFdPP; }
-    double v = 0.0;
-    if (pc < g.nvalid) v = in[g.base + pc * g.pstr + i * g.S];
-    B[pc * ldb + i] = v;
+    B[pc * ldb + i] = in[pbase[pc] + i * g.S];
   }
   __syncthreads();
   double* res = B;
@@ -128,9 +97,9 @@ fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const doubl
   if (MODE == PM_FUSED) {
     for (int e = threadIdx.x; e < kFdPP * m; e += blockDim.x) {
       const int pc = e / m, i = e - pc * m;
-      if (pc >= g.nvalid) continue;  // padding pencils of a ragged tile
-      double den = __ldg(lam + i) + __ldg(lamA + g.ia + pc);
-      if (dims.d == 3) den += __ldg(lamB + g.ib);
+      if (pc >= g.nvalid) continue;  // padding pencils
+      double den = __ldg(lam + i) + __ldg(lamA + pia[pc]);
+      if (dims.d == 3) den += __ldg(lamB + pib[pc]);
       C[pc * ldb + i] = C[pc * ldb + i] / den;
     }
     __syncthreads();
@@ -145,16 +114,11 @@ fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const doubl
     int pc, i;
     if (axis == 0) { pc = e / m; i = e - pc * m; }
     else { i = e / kFdPP; pc = e - i * kFdPP; }
-    if (pc < g.nvalid) out[g.base + pc * g.pstr + i * g.S] = res[pc * ldb + i];
+    if (pc < g.nvalid) out[pbase[pc] + i * g.S] = res[pc * ldb + i];
   }
 }
 
-int fd_tiles(const Dims& dims, int axis) {
-  if (axis == 0) return (int)((dims.N / dims.m[0] + kFdPP - 1) / kFdPP);
-  const int ntx = (dims.m[0] + kFdPP - 1) / kFdPP;
-  const long long rest = dims.N / ((long long)dims.m[0] * dims.m[axis]);
-  return (int)(ntx * rest);
-}
+int fd_tiles(const Dims& dims, int axis) { return (int)host_num_tiles(dims, axis, kFdPP); }
 
 size_t fd_smem(int m) {
   const int ldb = m | 1;

@@ -500,20 +500,18 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
         wmax = std::max(wmax, std::fabs(s));
       }
     for (int k = 0; k < no; ++k) A->lam[A->n_reg + k] = lo[k];
-    // support: rows whose entries are all below 1e-17 max|W| are dropped
+    // support: the maximal block of rows around the middle whose entries are all
+    // below 1e-17 max|W| is dropped (W decays geometrically away from both ends)
     auto small = [&](int i) {
       for (int k = 0; k < no; ++k)
         if (std::fabs(A->W[(size_t)i * no + k]) > 1e-17 * wmax) return false;
       return true;
     };
-    int lo_i = 0;
-    while (lo_i < m && !small(lo_i)) ++lo_i;
-    int hi_i = m;
-    while (hi_i > lo_i && !small(hi_i - 1)) --hi_i;
-    bool middle_small = true;
-    for (int i = lo_i; i < hi_i; ++i)
-      if (!small(i)) { middle_small = false; break; }
-    if (middle_small && lo_i < hi_i) {
+    const int mid = m / 2;
+    if (small(mid)) {
+      int lo_i = mid, hi_i = mid;
+      while (lo_i > 0 && small(lo_i - 1)) --lo_i;
+      while (hi_i < m && small(hi_i)) ++hi_i;
       A->wlo = lo_i;
       A->whi = hi_i;
     } else {

@@ -207,42 +207,6 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-struct TileGeom {
-  long long base;  // global offset of element (pencil 0, i = 0)
-  long long S;     // element stride along the pencil
-  long long pstr;  // stride between consecutive pencils of the tile
-  int nvalid;      // pencils of this tile inside the array
-  int ia, ib;      // indices of the pencil-0 coordinates in the other directions
-};
-
-// Tiles: direction 0 -> PP consecutive rows; direction a > 0 -> PP consecutive
-// x positions at one value of the remaining coordinate.
-__device__ __forceinline__ TileGeom tile_geom(const Dims& dims, int axis, int PP, int tile) {
-  TileGeom g;
-  const int m0 = dims.m[0], m1 = dims.m[1];
-  if (axis == 0) {
-    const long long rows = dims.N / m0;
-    const long long r0 = (long long)tile * PP;
-    g.base = r0 * m0;
-    g.S = 1;
-    g.pstr = m0;
-    g.nvalid = (int)min((long long)PP, rows - r0);
-    g.ia = 0;
-    g.ib = 0;
-  } else {
-    const int ntx = (m0 + PP - 1) / PP;
-    const int rest = tile / ntx;
-    const int x0 = (tile - rest * ntx) * PP;
-    g.S = (axis == 1) ? (long long)m0 : (long long)m0 * m1;
-    g.base = x0 + ((axis == 1) ? (long long)rest * m0 * m1 : (long long)rest * m0);
-    g.pstr = 1;
-    g.nvalid = min(PP, m0 - x0);
-    g.ia = x0;    // x index of pencil 0
-    g.ib = rest;  // the other coordinate (z for axis 1, y for axis 2)
-  }
-  return g;
-}
-
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
 precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, AxisTab<Tc> ax,
@@ -259,17 +223,20 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
   Tc* tile = reinterpret_cast<Tc*>(bufB + (size_t)npairs * L);
   Tc* outv = tile + (size_t)PP * ldt;  // PP * kMaxNout
 
-  const TileGeom g = tile_geom(dims, axis, PP, blockIdx.x);
+  __shared__ long long pbase[64];
+  __shared__ int pia[64], pib[64];
+  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, pia, pib);
   const int tid = threadIdx.x;
+  __syncthreads();
 
-  // ---- load the tile (zero-filled beyond the array)
+  // ---- load the tile. Padding pencils are zero: two pencils share one complex
+  // FFT, so a padding partner must not carry data (its rounding would leak into
+  // the valid pencil, e.g. undivided values in the fused pass).
   for (int e = tid; e < PP * m; e += blockDim.x) {
     int pc, i;
     if (axis == 0) { pc = e / m; i = e - pc * m; }
     else { i = e / PP; pc = e - i * PP; }
-    Tc v = Tc(0);
-    if (pc < g.nvalid) v = (Tc)in[g.base + pc * g.pstr + i * g.S];
-    tile[pc * ldt + i] = v;
+    tile[pc * ldt + i] = (pc < g.nvalid) ? (Tc)in[pbase[pc] + i * g.S] : Tc(0);
   }
   __syncthreads();
 
@@ -296,14 +263,13 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
       Tc va, vb;
       if (ax.kind == 1) {  // DST-II: Makhoul order of u_i = (-1)^i y_i
         const int i = (l < (N + 1) / 2) ? 2 * l : 2 * (N - 1 - l) + 1;
-        const Tc sg = (i & 1) ? Tc(-1) : Tc(1);
-        va = sg * reg_gather(ra, i, ax);
-        vb = sg * reg_gather(rb, i, ax);
+        va = neg_if(reg_gather(ra, i, ax), i & 1);
+        vb = neg_if(reg_gather(rb, i, ax), i & 1);
       } else {  // DST-I: odd extension of length L = 2n
         const int n = N + 1;
         if (l == 0 || l == n) { va = Tc(0); vb = Tc(0); }
         else if (l < n) { va = reg_gather(ra, l - 1, ax); vb = reg_gather(rb, l - 1, ax); }
-        else { va = -reg_gather(ra, 2 * n - 1 - l, ax); vb = -reg_gather(rb, 2 * n - 1 - l, ax); }
+        else { va = neg_if(reg_gather(ra, 2 * n - 1 - l, ax), true); vb = neg_if(reg_gather(rb, 2 * n - 1 - l, ax), true); }
       }
       bufA[w] = {va, vb};
     }
@@ -348,10 +314,9 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
     // divide by the summed eigenvalues of all directions
     for (int e = tid; e < PP * m; e += blockDim.x) {
       const int pc = e / m, i = e - pc * m;
-      if (pc >= g.nvalid) continue;  // padding pencils of a ragged tile
-      Tc den = __ldg(ax.lam + i);
-      if (dims.d == 3) den += __ldg(lamA + g.ia + pc) + __ldg(lamB + g.ib);
-      else den += __ldg(lamA + g.ia + pc);
+      if (pc >= g.nvalid) continue;  // padding pencils
+      Tc den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
+      if (dims.d == 3) den += __ldg(lamB + pib[pc]);
       tile[pc * ldt + i] = tile[pc * ldt + i] / den;
     }
     __syncthreads();
@@ -415,8 +380,7 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
         if (ax.kind == 1) {
           const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
           const Cplx<Tc> z = Zp[l];
-          const Tc v = isb ? z.y : z.x;
-          return (j & 1) ? -v : v;
+          return neg_if(isb ? z.y : z.x, j & 1);
         } else {
           const Cplx<Tc> z = Zp[j + 1];
           return isb ? z.x : -z.y;
@@ -448,7 +412,7 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
     if (axis == 0) { pc = e / m; i = e - pc * m; }
     else { i = e / PP; pc = e - i * PP; }
     if (pc < g.nvalid) {
-      const long long off = g.base + pc * g.pstr + i * g.S;
+      const long long off = pbase[pc] + i * g.S;
       const Tc v = tile[pc * ldt + i];
       out[off] = (Tout)v;
       if (NDOT >= 1) d0 = fma(__ldg(dotv0 + off), (double)(Tout)v, d0);
@@ -475,12 +439,7 @@ size_t precond_smem_bytes(int PP, int ldt, int L, size_t elt) {
   return (size_t)2 * (PP / 2) * L * 2 * elt + (size_t)PP * ldt * elt + (size_t)PP * kMaxNout * elt;
 }
 
-int precond_tiles(const Dims& dims, int axis, int PP) {
-  if (axis == 0) return (int)((dims.N / dims.m[0] + PP - 1) / PP);
-  const int ntx = (dims.m[0] + PP - 1) / PP;
-  const long long rest = dims.N / ((long long)dims.m[0] * dims.m[axis]);
-  return (int)(ntx * rest);
-}
+int precond_tiles(const Dims& dims, int axis, int PP) { return (int)host_num_tiles(dims, axis, PP); }
 
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {

@@ -72,43 +72,21 @@ __device__ __forceinline__ double toeplitz_k(const Coefs<P>& c, const double* ro
   return a;
 }
 
-struct STile {
-  long long base, S, pstr;
-  int nvalid;
-};
+int stiff_tiles(const Dims& dims, int axis, int PP) { return (int)host_num_tiles(dims, axis, PP); }
 
-__device__ __forceinline__ STile stile(const Dims& dims, int axis, int PP, int tile) {
-  STile g;
-  const int m0 = dims.m[0], m1 = dims.m[1];
-  if (axis == 0) {
-    const long long rows = dims.N / m0;
-    const long long r0 = (long long)tile * PP;
-    g.base = r0 * m0;
-    g.S = 1;
-    g.pstr = m0;
-    g.nvalid = (int)min((long long)PP, rows - r0);
-  } else {
-    const int ntx = (m0 + PP - 1) / PP;
-    const int rest = tile / ntx;
-    const int x0 = (tile - rest * ntx) * PP;
-    g.S = (axis == 1) ? (long long)m0 : (long long)m0 * m1;
-    g.base = x0 + ((axis == 1) ? (long long)rest * m0 * m1 : (long long)rest * m0);
-    g.pstr = 1;
-    g.nvalid = min(PP, m0 - x0);
-  }
-  return g;
-}
-
-__device__ __forceinline__ void tile_index(int axis, int e, int PP, int m, int& pc, int& i) {
+// Loads one array's tile: element (pc, i) of pencil pc (x fastest among
+// pencils for axis > 0, so a warp reads consecutive addresses).
+__device__ __forceinline__ void tile_coords(int axis, int e, int PP, int m, int& pc, int& i) {
   if (axis == 0) { pc = e / m; i = e - pc * m; }
   else { i = e / PP; pc = e - i * PP; }
 }
 
-int stiff_tiles(const Dims& dims, int axis, int PP) {
-  if (axis == 0) return (int)((dims.N / dims.m[0] + PP - 1) / PP);
-  const int ntx = (dims.m[0] + PP - 1) / PP;
-  const long long rest = dims.N / ((long long)dims.m[0] * dims.m[axis]);
-  return (int)(ntx * rest);
+// Work split of the compute loops: first every interior (Toeplitz) row of
+// every pencil, then the 2(2p-1) boundary rows, so that no warp mixes the two
+// code paths. Item e of a region of nr rows starting at row r0:
+__device__ __forceinline__ void region_coords(int axis, int e, int PP, int nr, int& pc, int& r) {
+  if (axis == 0) { pc = e / nr; r = e - pc * nr; }
+  else { r = e / PP; pc = e - r * PP; }
 }
 
 // pmode: 0 -> u = u; 1 -> u = z, p <- z; 2 -> u = z + beta p, p <- u
@@ -120,15 +98,17 @@ stiff_first(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __re
   if (done != nullptr && *((volatile const int*)done)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   double* tile = reinterpret_cast<double*>(smem);
-  const STile g = stile(dims, axis, PP, blockIdx.x);
+  __shared__ long long pbase[64];
+  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, nullptr, nullptr);
+  __syncthreads();
   const int m = bt.m;
   const double beta = (pmode == 2) ? *betap : 0.0;
   for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
     int pc, i;
-    tile_index(axis, e, PP, m, pc, i);
+    tile_coords(axis, e, PP, m, pc, i);
     double v = 0.0;
     if (pc < g.nvalid) {
-      const long long off = g.base + pc * g.pstr + i * g.S;
+      const long long off = pbase[pc] + i * g.S;
       if (pmode == 0) {
         v = u[off];
       } else if (pmode == 1) {
@@ -144,21 +124,27 @@ stiff_first(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __re
   __syncthreads();
   Coefs<P> c;
   load_coefs<P>(bt, c);
-  for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
-    int pc, i;
-    tile_index(axis, e, PP, m, pc, i);
+  const int nint = bt.ihi - bt.ilo, nbd = m - nint;
+  for (int e = threadIdx.x; e < PP * nint; e += blockDim.x) {
+    int pc, r;
+    region_coords(axis, e, PP, nint, pc, r);
     if (pc >= g.nvalid) continue;
-    const double* row = tile + pc * ldt;
+    const int i = bt.ilo + r;
     double mx, kx;
-    if (i >= bt.ilo && i < bt.ihi) {
-      toeplitz_mk<P>(c, row, i, mx, kx);
-    } else {
-      mx = band_row<P>(bt.Mb, row, i, m);
-      kx = band_row<P>(bt.Kb, row, i, m);
-    }
-    const long long off = g.base + pc * g.pstr + i * g.S;
+    toeplitz_mk<P>(c, tile + pc * ldt, i, mx, kx);
+    const long long off = pbase[pc] + i * g.S;
     T1[off] = mx;
     T2[off] = kx;
+  }
+  for (int e = threadIdx.x; e < PP * nbd; e += blockDim.x) {
+    int pc, r;
+    region_coords(axis, e, PP, nbd, pc, r);
+    if (pc >= g.nvalid) continue;
+    const int i = (r < bt.ilo) ? r : bt.ihi + (r - bt.ilo);
+    const double* row = tile + pc * ldt;
+    const long long off = pbase[pc] + i * g.S;
+    T1[off] = band_row<P>(bt.Mb, row, i, m);
+    T2[off] = band_row<P>(bt.Kb, row, i, m);
   }
 }
 
@@ -170,41 +156,43 @@ stiff_mid(Dims dims, int axis, int PP, int ldt, BandTab bt, double* __restrict__
   extern __shared__ __align__(16) unsigned char smem[];
   double* t1 = reinterpret_cast<double*>(smem);
   double* t2 = t1 + (size_t)PP * ldt;
-  const STile g = stile(dims, axis, PP, blockIdx.x);
+  __shared__ long long pbase[64];
+  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, nullptr, nullptr);
+  __syncthreads();
   const int m = bt.m;
   for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
     int pc, i;
-    tile_index(axis, e, PP, m, pc, i);
-    double a = 0.0, b = 0.0;
-    if (pc < g.nvalid) {
-      const long long off = g.base + pc * g.pstr + i * g.S;
-      a = T1[off];
-      b = T2[off];
-    }
-    t1[pc * ldt + i] = a;
-    t2[pc * ldt + i] = b;
+    tile_coords(axis, e, PP, m, pc, i);
+    const long long off = pbase[pc] + i * g.S;
+    t1[pc * ldt + i] = T1[off];
+    t2[pc * ldt + i] = T2[off];
   }
   __syncthreads();
   Coefs<P> c;
   load_coefs<P>(bt, c);
-  for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
-    int pc, i;
-    tile_index(axis, e, PP, m, pc, i);
+  const int nint = bt.ihi - bt.ilo, nbd = m - nint;
+  for (int e = threadIdx.x; e < PP * nint; e += blockDim.x) {
+    int pc, r;
+    region_coords(axis, e, PP, nint, pc, r);
     if (pc >= g.nvalid) continue;
-    const double* r1 = t1 + pc * ldt;
-    const double* r2 = t2 + pc * ldt;
-    double mx, kx, m2;
-    if (i >= bt.ilo && i < bt.ihi) {
-      toeplitz_mk<P>(c, r1, i, mx, kx);
-      m2 = toeplitz_m<P>(c, r2, i);
-    } else {
-      mx = band_row<P>(bt.Mb, r1, i, m);
-      kx = band_row<P>(bt.Kb, r1, i, m);
-      m2 = band_row<P>(bt.Mb, r2, i, m);
-    }
-    const long long off = g.base + pc * g.pstr + i * g.S;
+    const int i = bt.ilo + r;
+    double mx, kx;
+    toeplitz_mk<P>(c, t1 + pc * ldt, i, mx, kx);
+    const double m2 = toeplitz_m<P>(c, t2 + pc * ldt, i);
+    const long long off = pbase[pc] + i * g.S;
     T1[off] = mx;
     T2[off] = kx + m2;
+  }
+  for (int e = threadIdx.x; e < PP * nbd; e += blockDim.x) {
+    int pc, r;
+    region_coords(axis, e, PP, nbd, pc, r);
+    if (pc >= g.nvalid) continue;
+    const int i = (r < bt.ilo) ? r : bt.ihi + (r - bt.ilo);
+    const double* r1 = t1 + pc * ldt;
+    const double* r2 = t2 + pc * ldt;
+    const long long off = pbase[pc] + i * g.S;
+    T1[off] = band_row<P>(bt.Mb, r1, i, m);
+    T2[off] = band_row<P>(bt.Kb, r1, i, m) + band_row<P>(bt.Mb, r2, i, m);
   }
 }
 
@@ -217,37 +205,39 @@ stiff_last(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __res
   extern __shared__ __align__(16) unsigned char smem[];
   double* t1 = reinterpret_cast<double*>(smem);
   double* t2 = t1 + (size_t)PP * ldt;
-  const STile g = stile(dims, axis, PP, blockIdx.x);
+  __shared__ long long pbase[64];
+  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, nullptr, nullptr);
+  __syncthreads();
   const int m = bt.m;
   for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
     int pc, i;
-    tile_index(axis, e, PP, m, pc, i);
-    double a = 0.0, b = 0.0;
-    if (pc < g.nvalid) {
-      const long long off = g.base + pc * g.pstr + i * g.S;
-      a = T1[off];
-      b = T2[off];
-    }
-    t1[pc * ldt + i] = a;
-    t2[pc * ldt + i] = b;
+    tile_coords(axis, e, PP, m, pc, i);
+    const long long off = pbase[pc] + i * g.S;
+    t1[pc * ldt + i] = T1[off];
+    t2[pc * ldt + i] = T2[off];
   }
   __syncthreads();
   Coefs<P> c;
   load_coefs<P>(bt, c);
   double dsum = 0.0;
-  for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
-    int pc, i;
-    tile_index(axis, e, PP, m, pc, i);
+  const int nint = bt.ihi - bt.ilo, nbd = m - nint;
+  for (int e = threadIdx.x; e < PP * nint; e += blockDim.x) {
+    int pc, r;
+    region_coords(axis, e, PP, nint, pc, r);
     if (pc >= g.nvalid) continue;
-    const double* r1 = t1 + pc * ldt;
-    const double* r2 = t2 + pc * ldt;
-    double v;
-    if (i >= bt.ilo && i < bt.ihi) {
-      v = toeplitz_k<P>(c, r1, i) + toeplitz_m<P>(c, r2, i);
-    } else {
-      v = band_row<P>(bt.Kb, r1, i, m) + band_row<P>(bt.Mb, r2, i, m);
-    }
-    const long long off = g.base + pc * g.pstr + i * g.S;
+    const int i = bt.ilo + r;
+    const double v = toeplitz_k<P>(c, t1 + pc * ldt, i) + toeplitz_m<P>(c, t2 + pc * ldt, i);
+    const long long off = pbase[pc] + i * g.S;
+    out[off] = v;
+    if (dotv != nullptr) dsum = fma(dotv[off], v, dsum);
+  }
+  for (int e = threadIdx.x; e < PP * nbd; e += blockDim.x) {
+    int pc, r;
+    region_coords(axis, e, PP, nbd, pc, r);
+    if (pc >= g.nvalid) continue;
+    const int i = (r < bt.ilo) ? r : bt.ihi + (r - bt.ilo);
+    const double v = band_row<P>(bt.Kb, t1 + pc * ldt, i, m) + band_row<P>(bt.Mb, t2 + pc * ldt, i, m);
+    const long long off = pbase[pc] + i * g.S;
     out[off] = v;
     if (dotv != nullptr) dsum = fma(dotv[off], v, dsum);
   }
