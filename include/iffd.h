@@ -138,6 +138,30 @@ int iffd_apply_preconditioner(iffd_handle h, const double* r, double* z, void* w
  * alias. */
 int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, void* stream);
 
+/* Allocation-free variant of iffd_apply_stiffness (the paper has no
+ * counterpart: it exists for callers that cannot allocate device memory when
+ * they need A^ u -- code running while its stream is captured into a CUDA
+ * graph, latency-critical loops that must avoid cudaMalloc's implicit
+ * synchronisation, frameworks whose allocator owns all device memory, or
+ * callers with a device-memory budget fixed at start-up).
+ * Same result as iffd_apply_stiffness(h, u, Au, ws, stream), without a
+ * workspace: the two N-vector temporaries live in a static device array of
+ * 2 * IFFD_NOALLOC_MAX_DOFS doubles (16 MiB) inside the library, which every
+ * GPU that loads the library's module holds until the process exits. The call
+ * itself allocates nothing (no cudaMalloc / cudaFree).
+ * - Plans with N > IFFD_NOALLOC_MAX_DOFS are rejected with
+ *   IFFD_ERR_UNSUPPORTED and a message naming the limit.
+ * - The first call on each device resolves the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *   first call before any stream capture.
+ * - Every call shares the one array, so calls that overlap on the GPU (other
+ *   streams, other plans, other host threads) race: order them on one stream
+ *   or synchronise between them. The array keeps the last call's contents;
+ *   nothing in it needs to start at zero.
+ * u, Au: device, N float64 each, must not alias. */
+#define IFFD_NOALLOC_MAX_DOFS (1 << 20)
+int iffd_apply_stiffness_noalloc(iffd_handle h, const double* u, double* Au, void* stream);
+
 /* Solves A^ u = f by PCG (Section 3) with zero initial guess and the stopping
  * rule ||r_k|| <= rtol ||f|| (Section 7), preconditioned per opt->precond.
  * f, u: device, N float64 each, must not alias; u is output only. info: HOST

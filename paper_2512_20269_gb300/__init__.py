@@ -149,6 +149,15 @@ class IFFDPlan:
         return u, {"iters": info.iters, "rel_res": info.rel_res, "true_rel_res": info.true_rel_res,
                    "status": info.status}
 
+    def iffd_apply_stiffness_noalloc(self, u, Au, stream=None):
+        """A^ u without a workspace (static scratch inside the library, for
+        callers that cannot allocate; problems up to IFFD_NOALLOC_MAX_DOFS)."""
+        self._check_vec(u, "u")
+        self._check_vec(Au, "Au")
+        check(self._lib.iffd_apply_stiffness_noalloc(self._h, _ptr(u), _ptr(Au), _stream_handle(stream)),
+              "iffd_apply_stiffness_noalloc")
+        return Au
+
     # -- profiling (CUDA events around every launch of this plan)
     KERNEL_KINDS = 11
 

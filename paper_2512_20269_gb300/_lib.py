@@ -18,6 +18,8 @@ c_double_p = ctypes.POINTER(ctypes.c_double)
 c_size_t_p = ctypes.POINTER(ctypes.c_size_t)
 
 IFFD_OK = 0
+# Largest problem served by iffd_apply_stiffness_noalloc (include/iffd.h).
+IFFD_NOALLOC_MAX_DOFS = 1 << 20
 STATUS_NAMES = {0: "IFFD_OK", 1: "IFFD_ERR_INVALID_ARG", 2: "IFFD_ERR_UNSUPPORTED", 3: "IFFD_ERR_SINGULAR",
                 4: "IFFD_ERR_WORKSPACE", 5: "IFFD_ERR_CUDA", 6: "IFFD_ERR_NOT_CONVERGED",
                 7: "IFFD_ERR_BREAKDOWN", 8: "IFFD_ERR_TIMEOUT"}
@@ -48,6 +50,8 @@ SIGNATURES = [
                                                  ctypes.c_void_p, ctypes.c_void_p]),
     ("iffd_apply_stiffness", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
+    ("iffd_apply_stiffness_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p]),
     ("iffd_pcg_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.POINTER(iffd_pcg_info)]),
     ("iffd_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

@@ -561,6 +561,30 @@ struct iffd_plan {
   Plan P;
 };
 
+namespace iffd {
+
+// Support of iffd_apply_stiffness_noalloc (csrc/noalloc.cu): the three
+// stiffness sweeps of plan h with caller-given temporaries T1, T2 (each at
+// least N doubles). Counts the launches; records no profiler events.
+int plan_stiffness_with_scratch(iffd_handle h, const double* u, double* Au, double* T1, double* T2,
+                                cudaStream_t st) {
+  const Plan* P = &h->P;
+  int rc = check_device(P);
+  if (rc) return rc;
+  const int d = P->d;
+  P->prof.launches += d;
+  IFFD_CUDA(launch_stiff_first(make_stiff(P, d - 1), u, nullptr, nullptr, nullptr, 0, T1, T2, nullptr, st));
+  for (int a = d - 2; a >= 1; --a) IFFD_CUDA(launch_stiff_mid(make_stiff(P, a), T1, T2, nullptr, st));
+  IFFD_CUDA(launch_stiff_last(make_stiff(P, 0), T1, T2, Au, nullptr, nullptr, nullptr, st));
+  return IFFD_OK;
+}
+
+long long plan_num_dofs(iffd_handle h) { return h->P.dims.N; }
+
+int record_error(int code, const std::string& msg) { return fail(code, msg); }
+
+}  // namespace iffd
+
 extern "C" {
 
 int iffd_default_options(iffd_options* opt) {
