@@ -63,7 +63,12 @@ typedef enum {
 } iffd_precond_kind;
 
 typedef enum {
-  IFFD_COEF_CONST = 0         /* -Laplace: A = A^ = sum_k K_k x M x .. (eq. "system_matrix") */
+  IFFD_COEF_CONST = 0,        /* -Laplace: A = A^ = sum_k K_k x M x .. (eq. "system_matrix") */
+  IFFD_COEF_SEPARABLE_SIN = 1 /* -div(a grad u), a = 1 + coef_amp prod_k sin(2 pi x_k), stiffness
+                                 integrated with the tensor (p+1)-point Gauss rule (which factorises
+                                 it exactly into A^ + coef_amp sum_k M^s x .. K^s_k .. x M^s);
+                                 A != A^, the constant-coefficient IFFD stays the preconditioner, as
+                                 for the geometry-mapped problems of Section 7 */
 } iffd_coef_kind;
 
 typedef struct {
@@ -74,6 +79,7 @@ typedef struct {
   int coef;            /* iffd_coef_kind */
   int true_residual;   /* 1: iffd_pcg_solve recomputes ||f - A u||/||f|| at exit */
   int flexible;        /* 1: Polak-Ribiere beta (default for FP32 transforms) */
+  double coef_amp;     /* amplitude c of IFFD_COEF_SEPARABLE_SIN (|c| < 1 keeps a > 0) */
 } iffd_options;
 
 typedef struct {
@@ -84,7 +90,7 @@ typedef struct {
 } iffd_pcg_info;
 
 /* Fills *opt with the defaults: FP64, IFFD, rtol 1e-8, maxit 500, CONST,
- * true_residual 1, flexible 0. Returns IFFD_ERR_INVALID_ARG on NULL. */
+ * true_residual 1, flexible 0, coef_amp 0.5. Returns IFFD_ERR_INVALID_ARG on NULL. */
 int iffd_default_options(iffd_options* opt);
 
 /* Builds the plan for d directions with n_elems[k] elements each and degree p
@@ -133,9 +139,10 @@ int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* 
  * r, z: device, N float64 each, must not alias. ws: see conventions. */
 int iffd_apply_preconditioner(iffd_handle h, const double* r, double* z, void* ws, void* stream);
 
-/* Au = A^ u with A^ = sum_k (M_d x .. x K_k x .. x M_1) (eq. "system_matrix"),
- * applied matrix-free by banded sweeps. u, Au: device, N float64 each, must not
- * alias. */
+/* Au = A u: A^ u with A^ = sum_k (M_d x .. x K_k x .. x M_1) (eq.
+ * "system_matrix") for IFFD_COEF_CONST, or the variable-coefficient operator of
+ * IFFD_COEF_SEPARABLE_SIN, applied matrix-free by banded sweeps. u, Au: device,
+ * N float64 each, must not alias. */
 int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, void* stream);
 
 /* Allocation-free variant of iffd_apply_stiffness (the paper has no
@@ -144,7 +151,8 @@ int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, v
  * graph, latency-critical loops that must avoid cudaMalloc's implicit
  * synchronisation, frameworks whose allocator owns all device memory, or
  * callers with a device-memory budget fixed at start-up).
- * Same result as iffd_apply_stiffness(h, u, Au, ws, stream), without a
+ * Same result as iffd_apply_stiffness(h, u, Au, ws, stream) for plans with
+ * IFFD_COEF_CONST (other plans are rejected with IFFD_ERR_UNSUPPORTED), without a
  * workspace: the two N-vector temporaries live in a static device array of
  * 2 * IFFD_NOALLOC_MAX_DOFS doubles (16 MiB) inside the library, which every
  * GPU that loads the library's module holds until the process exits. The call
@@ -162,7 +170,7 @@ int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, v
 #define IFFD_NOALLOC_MAX_DOFS (1 << 20)
 int iffd_apply_stiffness_noalloc(iffd_handle h, const double* u, double* Au, void* stream);
 
-/* Solves A^ u = f by PCG (Section 3) with zero initial guess and the stopping
+/* Solves A u = f (A as in iffd_apply_stiffness) by PCG (Section 3) with zero initial guess and the stopping
  * rule ||r_k|| <= rtol ||f|| (Section 7), preconditioned per opt->precond.
  * f, u: device, N float64 each, must not alias; u is output only. info: HOST
  * pointer, filled on return (may be NULL). Synchronises `stream`. Returns

@@ -17,6 +17,7 @@ from ._lib import IFFDError, check, iffd_options, iffd_pcg_info
 
 PRECISION = {"fp64": 0, "fp32": 1}
 PRECOND = {"iffd": 0, "exact_fd": 1, "none": 2}
+COEF = {"const": 0, "sin": 1}
 
 __all__ = ["IFFDPlan", "IFFDError", "host_axis", "PRECISION", "PRECOND"]
 
@@ -62,7 +63,8 @@ class IFFDPlan:
     """
 
     def __init__(self, d: int, n, p: int, precision: str = "fp64", precond: str = "iffd", rtol: float = 1e-8,
-                 maxit: int = 500, true_residual: bool = True, flexible: bool = False, stream=None):
+                 maxit: int = 500, true_residual: bool = True, flexible: bool = False, coef: str = "const",
+                 coef_amp: float = 0.5, stream=None):
         import torch
         self._lib = _lib.load()
         n = [int(n)] * d if np.isscalar(n) else [int(x) for x in n]
@@ -75,6 +77,8 @@ class IFFDPlan:
         opt.maxit = maxit
         opt.true_residual = int(true_residual)
         opt.flexible = int(flexible)
+        opt.coef = COEF[coef]
+        opt.coef_amp = coef_amp
         self.options = opt
         nn = (ctypes.c_int * d)(*n)
         dd = (ctypes.c_int * (2 * d))(*([1] * (2 * d)))

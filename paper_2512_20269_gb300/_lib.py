@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "IFFD_OK", 1: "IFFD_ERR_INVALID_ARG", 2: "IFFD_ERR_UNSUPPORTE
 class iffd_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("coef", ctypes.c_int), ("true_residual", ctypes.c_int),
-                ("flexible", ctypes.c_int)]
+                ("flexible", ctypes.c_int), ("coef_amp", ctypes.c_double)]
 
 
 class iffd_pcg_info(ctypes.Structure):

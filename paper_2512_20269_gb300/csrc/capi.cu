@@ -118,13 +118,14 @@ struct Plan {
   AxisTab<double> axd[3];
   AxisTab<float> axf[3];
   BandTab bt[3];
-  int PPd[3], ldtd[3], PPf[3], ldtf[3], PPs[3], ldts[3];
+  WBandTab wb[3];  // variable-coefficient bands (IFFD_COEF_SEPARABLE_SIN)
+  int PPd[3], ldtd[3], PPf[3], ldtf[3], PPs[3], ldts[3], PPv[3];
   // exact FD tables
   const double* QT[3] = {nullptr, nullptr, nullptr};
   const double* Q[3] = {nullptr, nullptr, nullptr};
   const double* lamQ[3] = {nullptr, nullptr, nullptr};
   // workspace layout (bytes)
-  size_t off_r, off_z, off_p, off_q, off_t1, off_t2, off_tf, off_part, off_state, ws_bytes;
+  size_t off_r, off_z, off_p, off_q, off_t1, off_t2, off_t3, off_t4, off_tf, off_part, off_state, ws_bytes;
   int max_parts = 0;
   SolveState* host_state = nullptr;  // pinned
 };
@@ -249,7 +250,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
   TableBuilder tb;
   struct PerAxis {
     AxisOffsets od, of;
-    size_t Mb, Kb, Mt, Kt, QT, Q, lamQ;
+    size_t Mb, Kb, Mt, Kt, QT, Q, lamQ, Msb, Ksb;
     int L;
     std::vector<int> rad, twoff;
     int ilo, ihi;
@@ -295,6 +296,10 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     pa[a].ihi = ihi;
     pa[a].Mt = tb.add_vec(mt);
     pa[a].Kt = tb.add_vec(kt);
+    if (P->opt.coef == IFFD_COEF_SEPARABLE_SIN) {
+      pa[a].Msb = tb.add_vec(A.Msband);
+      pa[a].Ksb = tb.add_vec(A.Ksband);
+    }
     if (P->opt.precond == IFFD_PRECOND_EXACT_FD) {
       std::vector<double> Qc, lq;
       err = exact_fd_axis(A, &Qc, &lq);
@@ -341,6 +346,15 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     int pp = 16;
     while (pp > 2 && (size_t)2 * pp * P->ldts[a] * sizeof(double) > 100 * 1024) pp /= 2;
     P->PPs[a] = pp;
+    pp = 16;
+    while (pp > 2 && (size_t)4 * pp * P->ldts[a] * sizeof(double) > 110 * 1024) pp /= 2;
+    P->PPv[a] = pp;
+    if (P->opt.coef == IFFD_COEF_SEPARABLE_SIN) {
+      P->wb[a].Msb = reinterpret_cast<const double*>(base + pa[a].Msb);
+      P->wb[a].Ksb = reinterpret_cast<const double*>(base + pa[a].Ksb);
+      P->wb[a].c = P->opt.coef_amp;
+      max_parts = std::max(max_parts, stiff_tiles(P->dims, a, P->PPv[a]));
+    }
     if (P->opt.precond == IFFD_PRECOND_EXACT_FD) {
       P->Q[a] = reinterpret_cast<const double*>(base + pa[a].Q);
       P->QT[a] = reinterpret_cast<const double*>(base + pa[a].QT);
@@ -359,6 +373,12 @@ static int build_plan(Plan* P, cudaStream_t stream) {
   P->off_q = off; off += vec;
   P->off_t1 = off; off += vec;
   P->off_t2 = off; off += vec;
+  P->off_t3 = off;
+  P->off_t4 = off;
+  if (P->opt.coef == IFFD_COEF_SEPARABLE_SIN) {
+    P->off_t4 = off + vec;
+    off += 2 * vec;
+  }
   P->off_tf = off;
   if (P->opt.precision == IFFD_PREC_FP32_TRANSFORM) off += align256((size_t)N * sizeof(float));
   P->off_part = off; off += align256((size_t)2 * max_parts * sizeof(double));
@@ -530,6 +550,23 @@ static int run_stiffness(const Plan* P, const double* u, const double* z, double
   double* T1 = reinterpret_cast<double*>(wsb(ws, P->off_t1));
   double* T2 = reinterpret_cast<double*>(wsb(ws, P->off_t2));
   const int d = P->d;
+  if (P->opt.coef == IFFD_COEF_SEPARABLE_SIN) {
+    double* T3 = reinterpret_cast<double*>(wsb(ws, P->off_t3));
+    double* T4 = reinterpret_cast<double*>(wsb(ws, P->off_t4));
+    auto SV = [&](int a) {
+      StiffLaunch S = make_stiff(P, a);
+      S.PP = P->PPv[a];
+      return S;
+    };
+    IFFD_LAUNCH(P, IFFD_K_STIFF_FIRST, st,
+                launch_vstiff_first(SV(d - 1), P->wb[d - 1], u, z, p, beta, pmode, T1, T2, T3, T4, done, st));
+    for (int a = d - 2; a >= 1; --a)
+      IFFD_LAUNCH(P, IFFD_K_STIFF_MID, st, launch_vstiff_mid(SV(a), P->wb[a], T1, T2, T3, T4, done, st));
+    IFFD_LAUNCH(P, IFFD_K_STIFF_LAST, st,
+                launch_vstiff_last(SV(0), P->wb[0], T1, T2, T3, T4, out, dotv, partial, done, st));
+    if (nparts) *nparts = stiff_tiles(P->dims, 0, P->PPv[0]);
+    return IFFD_OK;
+  }
   IFFD_LAUNCH(P, IFFD_K_STIFF_FIRST, st,
               launch_stiff_first(make_stiff(P, d - 1), u, z, p, beta, pmode, T1, T2, done, st));
   for (int a = d - 2; a >= 1; --a)
@@ -569,6 +606,8 @@ namespace iffd {
 int plan_stiffness_with_scratch(iffd_handle h, const double* u, double* Au, double* T1, double* T2,
                                 cudaStream_t st) {
   const Plan* P = &h->P;
+  if (P->opt.coef != IFFD_COEF_CONST)
+    return fail(IFFD_ERR_UNSUPPORTED, "iffd_apply_stiffness_noalloc: only IFFD_COEF_CONST plans are supported");
   int rc = check_device(P);
   if (rc) return rc;
   const int d = P->d;
@@ -596,6 +635,7 @@ int iffd_default_options(iffd_options* opt) {
   opt->coef = IFFD_COEF_CONST;
   opt->true_residual = 1;
   opt->flexible = 0;
+  opt->coef_amp = 0.5;
   return IFFD_OK;
 }
 
@@ -614,7 +654,10 @@ int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iff
   if (o.precision != IFFD_PREC_FP64 && o.precision != IFFD_PREC_FP32_TRANSFORM)
     return fail(IFFD_ERR_INVALID_ARG, "unknown precision");
   if (o.precond < 0 || o.precond > 2) return fail(IFFD_ERR_INVALID_ARG, "unknown preconditioner");
-  if (o.coef != IFFD_COEF_CONST) return fail(IFFD_ERR_UNSUPPORTED, "coefficient kind not supported");
+  if (o.coef != IFFD_COEF_CONST && o.coef != IFFD_COEF_SEPARABLE_SIN)
+    return fail(IFFD_ERR_UNSUPPORTED, "coefficient kind not supported");
+  if (o.coef == IFFD_COEF_SEPARABLE_SIN && !(std::fabs(o.coef_amp) < 1.0))
+    return fail(IFFD_ERR_INVALID_ARG, "coef_amp must satisfy |c| < 1 (positive coefficient)");
   if (!(o.rtol > 0.0) || o.maxit < 1) return fail(IFFD_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 1");
   iffd_plan* h = new iffd_plan();
   Plan* P = &h->P;
@@ -636,6 +679,7 @@ int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iff
       delete h;
       return fail(IFFD_ERR_UNSUPPORTED, "n_out above 16");
     }
+    if (o.coef == IFFD_COEF_SEPARABLE_SIN) build_weighted_bands(&P->host[a]);
   }
   const int rc = build_plan(P, static_cast<cudaStream_t>(stream));
   if (rc != IFFD_OK) {

@@ -288,6 +288,44 @@ void insert_knot(std::vector<double>* kn, std::vector<double>* c, int p, double 
   *c = nc;
 }
 
+// Banded M and K of S_{p,h,{0,1}} (B-splines 0 and n+p-1 removed), with an
+// optional weight w(x) under both integrals; (p+1)-point Gauss per element.
+void assemble_bands(int n, int p, double (*w)(double), std::vector<double>* Mb, std::vector<double>* Kb) {
+  const int m = n + p - 2, bw = 2 * p + 1, F = n + p;
+  const std::vector<double> kn = open_knots(n, p);
+  std::vector<double> gx, gw;
+  gauss_legendre(p + 1, &gx, &gw);
+  std::vector<double> Mf((size_t)F * bw, 0.0), Kf((size_t)F * bw, 0.0);
+  std::vector<double> B(p + 1), dB(p + 1);
+  for (int e = 0; e < n; ++e) {
+    const double a = double(e) / n, b = double(e + 1) / n;
+    for (int g = 0; g <= p; ++g) {
+      const double x = 0.5 * (b - a) * gx[g] + 0.5 * (a + b);
+      double wt = 0.5 * (b - a) * gw[g];
+      if (w) wt *= w(x);
+      bspline_local(kn, p, e, x, 0, B.data());
+      bspline_local(kn, p, e, x, 1, dB.data());
+      for (int s = 0; s <= p; ++s)
+        for (int t = 0; t <= p; ++t) {
+          const int i = e + s, j = e + t;
+          Mf[(size_t)i * bw + (j - i + p)] += wt * B[s] * B[t];
+          Kf[(size_t)i * bw + (j - i + p)] += wt * dB[s] * dB[t];
+        }
+    }
+  }
+  Mb->assign((size_t)m * bw, 0.0);
+  Kb->assign((size_t)m * bw, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int d = 0; d < bw; ++d) {
+      const int j = i + d - p;
+      if (j < 0 || j >= m) continue;
+      (*Mb)[(size_t)i * bw + d] = Mf[(size_t)(i + 1) * bw + d];
+      (*Kb)[(size_t)i * bw + d] = Kf[(size_t)(i + 1) * bw + d];
+    }
+}
+
+double sin_2pi(double x) { return std::sin(2.0 * kPi * x); }
+
 }  // namespace
 
 double cardinal_half(int q, int twice_x) {
@@ -346,36 +384,8 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
   A->n_out = m - A->n_reg;
 
   // ---- banded M, K of S_{p,h}, Dirichlet B-splines 0 and n+p-1 removed
+  assemble_bands(n, p, nullptr, &A->Mband, &A->Kband);
   const std::vector<double> kn = open_knots(n, p);
-  std::vector<double> gx, gw;
-  gauss_legendre(p + 1, &gx, &gw);
-  const int F = n + p;
-  std::vector<double> Mf((size_t)F * bw, 0.0), Kf((size_t)F * bw, 0.0);
-  std::vector<double> B(p + 1), dB(p + 1);
-  for (int e = 0; e < n; ++e) {
-    const double a = double(e) / n, b = double(e + 1) / n;
-    for (int g = 0; g <= p; ++g) {
-      const double x = 0.5 * (b - a) * gx[g] + 0.5 * (a + b);
-      const double w = 0.5 * (b - a) * gw[g];
-      bspline_local(kn, p, e, x, 0, B.data());
-      bspline_local(kn, p, e, x, 1, dB.data());
-      for (int s = 0; s <= p; ++s)
-        for (int t = 0; t <= p; ++t) {
-          const int i = e + s, j = e + t;
-          Mf[(size_t)i * bw + (j - i + p)] += w * B[s] * B[t];
-          Kf[(size_t)i * bw + (j - i + p)] += w * dB[s] * dB[t];
-        }
-    }
-  }
-  A->Mband.assign((size_t)m * bw, 0.0);
-  A->Kband.assign((size_t)m * bw, 0.0);
-  for (int i = 0; i < m; ++i)
-    for (int d = 0; d < bw; ++d) {
-      const int j = i + d - p;
-      if (j < 0 || j >= m) continue;
-      A->Mband[(size_t)i * bw + d] = Mf[(size_t)(i + 1) * bw + d];
-      A->Kband[(size_t)i * bw + d] = Kf[(size_t)(i + 1) * bw + d];
-    }
 
   // ---- special basis edge block (Section 6, D = {0,1}) by knot insertion
   const int half = p / 2;                 // floor(p/2)
@@ -521,6 +531,8 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
   }
   return "";
 }
+
+void build_weighted_bands(Axis1D* A) { assemble_bands(A->n, A->p, sin_2pi, &A->Msband, &A->Ksband); }
 
 std::string exact_fd_axis(const Axis1D& ax, std::vector<double>* Q, std::vector<double>* lam) {
   const int m = ax.m, p = ax.p, bw = 2 * p + 1;

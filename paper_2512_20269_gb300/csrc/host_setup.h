@@ -34,7 +34,14 @@ struct Axis1D {
   std::vector<double> dtilde; // D~_reg diagonal (n_reg)
   // Banded mass / stiffness of S_{p,h,D}: band[i*(2p+1) + (j-i+p)] = A[i][j].
   std::vector<double> Mband, Kband;
+  // Same, weighted by s(x) = sin(2 pi x) under the integral (variable
+  // coefficient a = 1 + c prod_k s(x_k)); filled by build_weighted_bands.
+  std::vector<double> Msband, Ksband;
 };
+
+// M^s_ij = int s B_i B_j, K^s_ij = int s B_i' B_j' with s(x) = sin(2 pi x) and the
+// same (p+1)-point Gauss rule per element as M and K (bands as above).
+void build_weighted_bands(Axis1D* A);
 
 // Builds all of the above. Returns an empty string on success, else a message.
 std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* out);

@@ -24,6 +24,26 @@ struct PassLaunch {
   const int* done;     // optional early-exit flag (PCG)
 };
 
+// Per-system descriptor of one batched transform pass.
+template <typename Tc, typename Tin, typename Tout>
+struct PassDesc {
+  const Tin* in;
+  Tout* out;
+  Dims dims;
+  int axis, PP, ldt;
+  AxisTab<Tc> ax;
+  const Tc* lamA;
+  const Tc* lamB;
+  const double* dot0;
+  const double* dot1;
+  double* partial;
+  const int* done;
+};
+
+template <typename Tc, typename Tin, typename Tout>
+cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st);
+
 size_t precond_smem_bytes(int PP, int ldt, int L, size_t elt);
 int precond_tiles(const Dims& dims, int axis, int PP);
 
@@ -62,6 +82,47 @@ cudaError_t launch_stiff_last(const StiffLaunch& S, const double* T1, const doub
                               const double* dotv, double* partial, const int* done, cudaStream_t st);
 int stiff_tiles(const Dims& dims, int axis, int PP);
 
+// Per-system descriptor of one batched stiffness sweep (fields unused by a
+// stage are ignored).
+struct StiffDesc {
+  Dims dims;
+  int axis, PP, ldt;
+  BandTab bt;
+  const double* u;
+  const double* z;
+  double* p_io;
+  const double* beta;
+  int pmode;
+  double* T1;
+  double* T2;
+  double* out;
+  const double* dotv;
+  double* partial;
+  const int* done;
+};
+// All systems of one launch share the degree p.
+cudaError_t launch_stiff_batched(int p, int stage, const StiffDesc* sys, const long long* tile_prefix, int nsys,
+                                 long long total_tiles, size_t smem, cudaStream_t st);
+
+// Variable coefficient a = 1 + c prod_k s(x_k): the operator is
+// A^ + c sum_k (M^s x .. x K^s_k x .. x M^s) with banded 1D matrices weighted by s.
+struct WBandTab {
+  const double* Msb;  // m * (2p+1) band rows of M^s
+  const double* Ksb;  // m * (2p+1) band rows of K^s
+  double c;
+};
+// FIRST: T1 = M u, T2 = K u, T3 = M^s u, T4 = K^s u (optional p update as above)
+// MID:   T1 <- M T1, T2 <- K T1 + M T2, T3 <- M^s T3, T4 <- K^s T3 + M^s T4
+// LAST:  out = K T1 + M T2 + c (K^s T3 + M^s T4), optional partial (dotv, out)
+cudaError_t launch_vstiff_first(const StiffLaunch& S, const WBandTab& wb, const double* u, const double* z,
+                                double* p_io, const double* beta, int pmode, double* T1, double* T2, double* T3,
+                                double* T4, const int* done, cudaStream_t st);
+cudaError_t launch_vstiff_mid(const StiffLaunch& S, const WBandTab& wb, double* T1, double* T2, double* T3,
+                              double* T4, const int* done, cudaStream_t st);
+cudaError_t launch_vstiff_last(const StiffLaunch& S, const WBandTab& wb, const double* T1, const double* T2,
+                               const double* T3, const double* T4, double* out, const double* dotv,
+                               double* partial, const int* done, cudaStream_t st);
+
 // ---------------------------------------------------------------- PCG vectors
 int vec_grid(long long N);
 cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st);
@@ -72,5 +133,27 @@ enum FinalizePhase : int { FP_FF = 0, FP_RZ0 = 1, FP_PQ = 2, FP_RR = 3, FP_RZ = 
 cudaError_t launch_finalize(SolveState* s, const double* partial, int nparts, int phase, double tol2, int maxit,
                             cudaStream_t st);
 cudaError_t launch_residual(const double* f, const double* Au, long long N, double* partial, cudaStream_t st);
+
+// Batched vector kernels (one descriptor per system).
+struct VecDesc {
+  const double* f;
+  double* x;
+  double* r;
+  const double* p;
+  const double* q;
+  SolveState* st;
+  long long N;
+  double* part_rr;  // partial sums of ||f||^2 / ||r||^2 (vec_grid(N) entries)
+};
+struct FinDesc {
+  SolveState* st;
+  const double* partial;
+  int nparts;
+};
+cudaError_t launch_pcg_init_batched(const VecDesc* sys, const long long* prefix, int nsys, long long total_blocks,
+                                    cudaStream_t st);
+cudaError_t launch_pcg_update_batched(const VecDesc* sys, const long long* prefix, int nsys, long long total_blocks,
+                                      cudaStream_t st);
+cudaError_t launch_finalize_batched(const FinDesc* sys, int nsys, int phase, double tol2, int maxit, cudaStream_t st);
 
 }  // namespace iffd

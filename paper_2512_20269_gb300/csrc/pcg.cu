@@ -30,36 +30,79 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
-// x = 0, r = f, partial ||f||^2
-__global__ void __launch_bounds__(kThreads)
-pcg_init(const double* __restrict__ f, double* __restrict__ x, double* __restrict__ r, long long N,
-         double* __restrict__ partial) {
+// x = 0, r = f, partial ||f||^2 (block `blk` of `nblk`)
+__device__ __forceinline__ void init_body(const double* __restrict__ f, double* __restrict__ x, double* __restrict__ r,
+                                          long long N, double* __restrict__ partial, int blk, int nblk) {
   double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)nblk * blockDim.x) {
     const double v = f[i];
     x[i] = 0.0;
     r[i] = v;
     s = fma(v, v, s);
   }
   s = block_sum(s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (threadIdx.x == 0) partial[blk] = s;
 }
 
 // x += alpha p, r -= alpha q, partial ||r||^2
-__global__ void __launch_bounds__(kThreads)
-pcg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
-           const SolveState* __restrict__ st, long long N, double* __restrict__ partial, const int* __restrict__ done) {
-  if (*((volatile const int*)done)) return;
+__device__ __forceinline__ void update_body(double* __restrict__ x, double* __restrict__ r,
+                                            const double* __restrict__ p, const double* __restrict__ q,
+                                            const SolveState* __restrict__ st, long long N,
+                                            double* __restrict__ partial, int blk, int nblk) {
   const double alpha = st->alpha;
   double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)nblk * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     const double rv = fma(-alpha, q[i], r[i]);
     r[i] = rv;
     s = fma(rv, rv, s);
   }
   s = block_sum(s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (threadIdx.x == 0) partial[blk] = s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+pcg_init(const double* __restrict__ f, double* __restrict__ x, double* __restrict__ r, long long N,
+         double* __restrict__ partial) {
+  init_body(f, x, r, N, partial, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads)
+pcg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
+           const SolveState* __restrict__ st, long long N, double* __restrict__ partial, const int* __restrict__ done) {
+  if (*((volatile const int*)done)) return;
+  update_body(x, r, p, q, st, N, partial, blockIdx.x, gridDim.x);
+}
+
+// Batched vector kernels: block b serves local block b - block_prefix[s] of
+// system s (which has vec_grid(N_s) blocks, as when solved alone).
+__device__ __forceinline__ int find_system(const long long* __restrict__ prefix, int nsys, long long b) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads)
+pcg_init_batched(const VecDesc* __restrict__ sys, const long long* __restrict__ prefix, int nsys) {
+  const int s = find_system(prefix, nsys, blockIdx.x);
+  const VecDesc& d = sys[s];
+  const int blk = (int)(blockIdx.x - prefix[s]);
+  const int nblk = (int)(prefix[s + 1] - prefix[s]);
+  init_body(d.f, d.x, d.r, d.N, d.part_rr, blk, nblk);
+}
+
+__global__ void __launch_bounds__(kThreads)
+pcg_update_batched(const VecDesc* __restrict__ sys, const long long* __restrict__ prefix, int nsys) {
+  const int s = find_system(prefix, nsys, blockIdx.x);
+  const VecDesc& d = sys[s];
+  if (*((volatile const int*)&d.st->done)) return;
+  const int blk = (int)(blockIdx.x - prefix[s]);
+  const int nblk = (int)(prefix[s + 1] - prefix[s]);
+  update_body(d.x, d.r, d.p, d.q, d.st, d.N, d.part_rr, blk, nblk);
 }
 
 // partial ||f - Au||^2
@@ -77,8 +120,8 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ Au, lon
 // status codes mirror iffd_status in include/iffd.h
 constexpr int kStOk = 0, kStNotConverged = 6, kStBreakdown = 7;
 
-__global__ void __launch_bounds__(1024)
-finalize_kernel(SolveState* st, const double* __restrict__ partial, int nparts, int phase, double tol2, int maxit) {
+__device__ __forceinline__ void finalize_body(SolveState* st, const double* __restrict__ partial, int nparts, int phase,
+                                              double tol2, int maxit) {
   __shared__ double red[32];
   if (phase != FP_FF && phase != FP_TRUE && st->done) return;
   // fixed-order reduction: thread t sums parts t, t+1024, ...; then a fixed tree
@@ -137,6 +180,18 @@ finalize_kernel(SolveState* st, const double* __restrict__ partial, int nparts, 
   }
 }
 
+__global__ void __launch_bounds__(1024)
+finalize_kernel(SolveState* st, const double* __restrict__ partial, int nparts, int phase, double tol2, int maxit) {
+  finalize_body(st, partial, nparts, phase, tol2, maxit);
+}
+
+// One CTA per system; the reduction order equals finalize_kernel's.
+__global__ void __launch_bounds__(1024)
+finalize_batched(const FinDesc* __restrict__ sys, int phase, double tol2, int maxit) {
+  const FinDesc& d = sys[blockIdx.x];
+  finalize_body(d.st, d.partial, d.nparts, phase, tol2, maxit);
+}
+
 cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st) {
   pcg_init<<<vec_grid(N), kThreads, 0, st>>>(f, x, r, N, partial);
   return cudaGetLastError();
@@ -150,6 +205,23 @@ cudaError_t launch_pcg_update(double* x, double* r, const double* p, const doubl
 
 cudaError_t launch_residual(const double* f, const double* Au, long long N, double* partial, cudaStream_t st) {
   residual_kernel<<<vec_grid(N), kThreads, 0, st>>>(f, Au, N, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init_batched(const VecDesc* sys, const long long* prefix, int nsys, long long total_blocks,
+                                    cudaStream_t st) {
+  pcg_init_batched<<<(unsigned)total_blocks, kThreads, 0, st>>>(sys, prefix, nsys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update_batched(const VecDesc* sys, const long long* prefix, int nsys, long long total_blocks,
+                                      cudaStream_t st) {
+  pcg_update_batched<<<(unsigned)total_blocks, kThreads, 0, st>>>(sys, prefix, nsys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(const FinDesc* sys, int nsys, int phase, double tol2, int maxit, cudaStream_t st) {
+  finalize_batched<<<nsys, 1024, 0, st>>>(sys, phase, tol2, maxit);
   return cudaGetLastError();
 }
 

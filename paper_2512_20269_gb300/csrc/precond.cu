@@ -207,14 +207,14 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Body of one CTA of a transform pass: tile `tile` of the pencils along `axis`.
+// Partial dot products go to partial[ptile] (and partial[pstride + ptile]).
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
-__global__ void __launch_bounds__(kThreads)
-precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, AxisTab<Tc> ax,
-             const Tc* __restrict__ lamA, const Tc* __restrict__ lamB,
-             const double* __restrict__ dotv0, const double* __restrict__ dotv1,
-             double* __restrict__ partial, const int* __restrict__ done) {
-  if (done != nullptr && *((volatile const int*)done)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dims& dims, int axis, int PP, int ldt,
+                                             const AxisTab<Tc>& ax, const Tc* __restrict__ lamA,
+                                             const Tc* __restrict__ lamB, const double* __restrict__ dotv0,
+                                             const double* __restrict__ dotv1, double* __restrict__ partial,
+                                             long long tile_id, int ptile, int pstride, unsigned char* smem) {
   const int npairs = PP / 2;
   const int L = ax.L;
   const int m = ax.m;
@@ -225,7 +225,7 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
 
   __shared__ long long pbase[64];
   __shared__ int pia[64], pib[64];
-  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, pia, pib);
+  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
   const int tid = threadIdx.x;
   __syncthreads();
 
@@ -428,10 +428,52 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
     if (tid == 0) {
       double s0 = 0.0, s1 = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s0 += red[0][w]; s1 += red[1][w]; }
-      partial[blockIdx.x] = s0;
-      if (NDOT >= 2) partial[gridDim.x + blockIdx.x] = s1;
+      partial[ptile] = s0;
+      if (NDOT >= 2) partial[pstride + ptile] = s1;
     }
   }
+}
+
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, AxisTab<Tc> ax,
+             const Tc* __restrict__ lamA, const Tc* __restrict__ lamB,
+             const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+             double* __restrict__ partial, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  precond_body<Tc, Tin, Tout, MODE, NDOT>(in, out, dims, axis, PP, ldt, ax, lamA, lamB, dotv0, dotv1, partial,
+                                          blockIdx.x, blockIdx.x, gridDim.x, smem);
+}
+
+// Batched pass: the grid covers the tiles of many independent systems; CTA b
+// serves tile b - tile_prefix[s] of system s with tile_prefix[s] <= b <
+// tile_prefix[s+1]. Each system's work and reductions are exactly those of the
+// single-system kernel, so a result does not depend on the rest of the batch.
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_pass_batched(const PassDesc<Tc, Tin, Tout>* __restrict__ sys, const long long* __restrict__ tile_prefix,
+                     int nsys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ PassDesc<Tc, Tin, Tout> sd;
+  __shared__ int s_sys;
+  if (threadIdx.x == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {  // last s with tile_prefix[s] <= b
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_sys = lo;
+    sd = sys[lo];
+  }
+  __syncthreads();
+  if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
+  const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
+  const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
+  precond_body<Tc, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.PP, sd.ldt, sd.ax, sd.lamA, sd.lamB,
+                                          sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
 }
 
 // ------------------------------------------------------------ host launchers
@@ -461,6 +503,36 @@ cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* 
   if (ndot == 1) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 1>(P, in, out, st);
   return launch_pass_t<Tc, Tin, Tout, PM_BWD, 2>(P, in, out, st);
 }
+
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+static cudaError_t launch_batched_t(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                   long long total_tiles, size_t smem, cudaStream_t st) {
+  auto kern = precond_pass_batched<Tc, Tin, Tout, MODE, NDOT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (total_tiles <= 0) return cudaSuccess;
+  kern<<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
+  return cudaGetLastError();
+}
+
+template <typename Tc, typename Tin, typename Tout>
+cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st) {
+  if (mode == PM_FWD) return launch_batched_t<Tc, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (mode == PM_FUSED)
+    return launch_batched_t<Tc, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (ndot == 0) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (ndot == 1) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  return launch_batched_t<Tc, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
+}
+
+#define IFFD_INST_BATCHED(Tc, Tin, Tout)                                                                      \
+  template cudaError_t launch_pass_batched<Tc, Tin, Tout>(const PassDesc<Tc, Tin, Tout>*, const long long*, int, \
+                                                          long long, size_t, int, int, cudaStream_t);
+IFFD_INST_BATCHED(double, double, double)
+IFFD_INST_BATCHED(float, double, float)
+IFFD_INST_BATCHED(float, float, float)
+IFFD_INST_BATCHED(float, float, double)
 
 template cudaError_t launch_pass<double, double, double>(const PassLaunch<double>&, int, int, const double*,
                                                          double*, cudaStream_t);

@@ -91,15 +91,14 @@ __device__ __forceinline__ void region_coords(int axis, int e, int PP, int nr, i
 
 // pmode: 0 -> u = u; 1 -> u = z, p <- z; 2 -> u = z + beta p, p <- u
 template <int P>
-__global__ void __launch_bounds__(kThreads)
-stiff_first(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __restrict__ u,
-            const double* __restrict__ z, double* __restrict__ p_io, const double* __restrict__ betap, int pmode,
-            double* __restrict__ T1, double* __restrict__ T2, const int* __restrict__ done) {
-  if (done != nullptr && *((volatile const int*)done)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void first_body(const Dims& dims, int axis, int PP, int ldt, const BandTab& bt,
+                                           const double* __restrict__ u, const double* __restrict__ z,
+                                           double* __restrict__ p_io, const double* __restrict__ betap, int pmode,
+                                           double* __restrict__ T1, double* __restrict__ T2, long long tile_id,
+                                           unsigned char* smem) {
   double* tile = reinterpret_cast<double*>(smem);
   __shared__ long long pbase[64];
-  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, nullptr, nullptr);
+  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, nullptr, nullptr);
   __syncthreads();
   const int m = bt.m;
   const double beta = (pmode == 2) ? *betap : 0.0;
@@ -149,15 +148,13 @@ stiff_first(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __re
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads)
-stiff_mid(Dims dims, int axis, int PP, int ldt, BandTab bt, double* __restrict__ T1, double* __restrict__ T2,
-          const int* __restrict__ done) {
-  if (done != nullptr && *((volatile const int*)done)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void mid_body(const Dims& dims, int axis, int PP, int ldt, const BandTab& bt,
+                                         double* __restrict__ T1, double* __restrict__ T2, long long tile_id,
+                                         unsigned char* smem) {
   double* t1 = reinterpret_cast<double*>(smem);
   double* t2 = t1 + (size_t)PP * ldt;
   __shared__ long long pbase[64];
-  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, nullptr, nullptr);
+  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, nullptr, nullptr);
   __syncthreads();
   const int m = bt.m;
   for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
@@ -197,16 +194,15 @@ stiff_mid(Dims dims, int axis, int PP, int ldt, BandTab bt, double* __restrict__
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads)
-stiff_last(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __restrict__ T1,
-           const double* __restrict__ T2, double* __restrict__ out, const double* __restrict__ dotv,
-           double* __restrict__ partial, const int* __restrict__ done) {
-  if (done != nullptr && *((volatile const int*)done)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void last_body(const Dims& dims, int axis, int PP, int ldt, const BandTab& bt,
+                                          const double* __restrict__ T1, const double* __restrict__ T2,
+                                          double* __restrict__ out, const double* __restrict__ dotv,
+                                          double* __restrict__ partial, long long tile_id, int ptile,
+                                          unsigned char* smem) {
   double* t1 = reinterpret_cast<double*>(smem);
   double* t2 = t1 + (size_t)PP * ldt;
   __shared__ long long pbase[64];
-  const TileInfo g = tile_setup(dims, axis, PP, blockIdx.x, pbase, nullptr, nullptr);
+  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, nullptr, nullptr);
   __syncthreads();
   const int m = bt.m;
   for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
@@ -250,9 +246,69 @@ stiff_last(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __res
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      partial[blockIdx.x] = s;
+      partial[ptile] = s;
     }
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+stiff_first(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __restrict__ u,
+            const double* __restrict__ z, double* __restrict__ p_io, const double* __restrict__ betap, int pmode,
+            double* __restrict__ T1, double* __restrict__ T2, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  first_body<P>(dims, axis, PP, ldt, bt, u, z, p_io, betap, pmode, T1, T2, blockIdx.x, smem);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+stiff_mid(Dims dims, int axis, int PP, int ldt, BandTab bt, double* __restrict__ T1, double* __restrict__ T2,
+          const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  mid_body<P>(dims, axis, PP, ldt, bt, T1, T2, blockIdx.x, smem);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+stiff_last(Dims dims, int axis, int PP, int ldt, BandTab bt, const double* __restrict__ T1,
+           const double* __restrict__ T2, double* __restrict__ out, const double* __restrict__ dotv,
+           double* __restrict__ partial, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  last_body<P>(dims, axis, PP, ldt, bt, T1, T2, out, dotv, partial, blockIdx.x, blockIdx.x, smem);
+}
+
+// Batched sweep over many systems of the same degree P (see precond_pass_batched).
+template <int P, int STAGE>
+__global__ void __launch_bounds__(kThreads)
+stiff_batched(const StiffDesc* __restrict__ sys, const long long* __restrict__ tile_prefix, int nsys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ StiffDesc sd;
+  __shared__ int s_sys;
+  if (threadIdx.x == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_sys = lo;
+    sd = sys[lo];
+  }
+  __syncthreads();
+  if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
+  const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
+  if (STAGE == SS_FIRST)
+    first_body<P>(sd.dims, sd.axis, sd.PP, sd.ldt, sd.bt, sd.u, sd.z, sd.p_io, sd.beta, sd.pmode, sd.T1, sd.T2,
+                  tile, smem);
+  else if (STAGE == SS_MID)
+    mid_body<P>(sd.dims, sd.axis, sd.PP, sd.ldt, sd.bt, sd.T1, sd.T2, tile, smem);
+  else
+    last_body<P>(sd.dims, sd.axis, sd.PP, sd.ldt, sd.bt, sd.T1, sd.T2, sd.out, sd.dotv, sd.partial, tile, (int)tile,
+                 smem);
 }
 
 static size_t stiff_smem(const StiffLaunch& S, int arrays) { return (size_t)arrays * S.PP * S.ldt * sizeof(double); }
@@ -301,6 +357,33 @@ static cudaError_t last_p(const StiffLaunch& S, const double* T1, const double* 
     case 15: return CALL(15); case 16: return CALL(16);            \
     default: return cudaErrorInvalidValue;                         \
   }
+
+template <int P>
+static cudaError_t batched_p(int stage, const StiffDesc* sys, const long long* tile_prefix, int nsys,
+                             long long total_tiles, size_t smem, cudaStream_t st) {
+  cudaError_t e;
+  if (stage == SS_FIRST) {
+    e = cudaFuncSetAttribute(stiff_batched<P, SS_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || total_tiles <= 0) return e;
+    stiff_batched<P, SS_FIRST><<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
+  } else if (stage == SS_MID) {
+    e = cudaFuncSetAttribute(stiff_batched<P, SS_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || total_tiles <= 0) return e;
+    stiff_batched<P, SS_MID><<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
+  } else {
+    e = cudaFuncSetAttribute(stiff_batched<P, SS_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || total_tiles <= 0) return e;
+    stiff_batched<P, SS_LAST><<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stiff_batched(int p, int stage, const StiffDesc* sys, const long long* tile_prefix, int nsys,
+                                 long long total_tiles, size_t smem, cudaStream_t st) {
+#define CALL_B(P) batched_p<P>(stage, sys, tile_prefix, nsys, total_tiles, smem, st)
+  IFFD_DISPATCH_P(p, CALL_B)
+#undef CALL_B
+}
 
 cudaError_t launch_stiff_first(const StiffLaunch& S, const double* u, const double* z, double* p_io,
                                const double* beta, int pmode, double* T1, double* T2, const int* done,
