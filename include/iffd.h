@@ -211,6 +211,53 @@ int iffd_launch_count(iffd_handle h, long long* count);
  * the plan's device current; does not synchronise any stream. */
 int iffd_destroy(iffd_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves / continuous batching (many independent problems; the paper
+ * solves one problem at a time and has no counterpart).
+ * An engine owns a device arena of `budget_bytes` from which every admitted
+ * request takes its workspace (iffd_engine_request_bytes). Each step
+ * initialises the requests admitted since the previous step and advances every
+ * active request by `iterations` PCG iterations; all active requests share the
+ * launches of each phase (one batched launch per phase, the stiffness sweeps
+ * grouped by degree), the per-iteration launch sequence is a CUDA graph that is
+ * replayed while the set of requests is unchanged. After the step the finished
+ * requests are retired (their workspace returns to the arena) and can be
+ * collected with iffd_engine_poll. A request's kernels, tile decomposition and
+ * reduction order are those of iffd_pcg_solve with the same options, so its
+ * result does not depend on the other requests in the engine.
+ * Only IFFD-preconditioned, constant-coefficient, Dirichlet cube/square
+ * problems (d, n elements per direction, degree p) are served. */
+typedef struct iffd_engine* iffd_engine_handle;
+
+typedef struct {
+  long long id;        /* request id returned by iffd_engine_submit */
+  iffd_pcg_info info;  /* true_rel_res is -1 (not computed by the engine) */
+} iffd_completion;
+
+/* opt: precision, rtol, maxit, flexible are used (NULL = defaults). The arena
+ * is allocated here (cudaMalloc of budget_bytes on the current device). The
+ * engine runs on a stream of its own; every step first waits for the work
+ * already enqueued on `stream` (so f may be produced there) and returns after
+ * the step's work has finished. */
+int iffd_engine_create(const iffd_options* opt, size_t budget_bytes, void* stream, iffd_engine_handle* out);
+/* Workspace a request (d, n, p) takes from the arena (builds and caches the
+ * plan of (d, n, p) if needed). */
+int iffd_engine_request_bytes(iffd_engine_handle e, int d, int n, int p, size_t* bytes);
+/* Admits a request if its workspace fits the arena now: f (right-hand side)
+ * and u (solution, output) are caller-owned device arrays of N float64 that
+ * must stay valid until the request completes. Returns IFFD_ERR_WORKSPACE if
+ * the arena has no room now (resubmit after completions) and
+ * IFFD_ERR_UNSUPPORTED if the request can never fit. */
+int iffd_engine_submit(iffd_engine_handle e, int d, int n, int p, const double* f, double* u, long long* id);
+/* One step (see above); *active receives the number of requests still
+ * iterating. Synchronises the engine's stream once (to read the states). */
+int iffd_engine_step(iffd_engine_handle e, int iterations, int* active);
+/* Moves up to `capacity` completions into out; *count receives how many. */
+int iffd_engine_poll(iffd_engine_handle e, iffd_completion* out, int capacity, int* count);
+/* Active requests, free arena bytes, kernels launched so far (any may be NULL). */
+int iffd_engine_stats(iffd_engine_handle e, int* active, size_t* bytes_free, long long* kernel_launches);
+int iffd_engine_destroy(iffd_engine_handle e);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* iffd_last_error(void);
 

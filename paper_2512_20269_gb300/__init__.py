@@ -19,7 +19,7 @@ PRECISION = {"fp64": 0, "fp32": 1}
 PRECOND = {"iffd": 0, "exact_fd": 1, "none": 2}
 COEF = {"const": 0, "sin": 1}
 
-__all__ = ["IFFDPlan", "IFFDError", "host_axis", "PRECISION", "PRECOND"]
+__all__ = ["IFFDPlan", "IFFDEngine", "IFFDError", "host_axis", "PRECISION", "PRECOND"]
 
 
 def _ptr(t) -> int:
@@ -193,6 +193,89 @@ class IFFDPlan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.iffd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class IFFDEngine:
+    """Batched / continuously batched IFFD-PCG solves (iffd_engine_* of the C ABI).
+
+    Requests (d, n, p, f, u) with caller-owned float64 CUDA tensors are admitted
+    while their workspace fits the device arena of `budget_bytes`; step() runs
+    one engine step (initialise new requests, `iterations` PCG iterations of
+    every active request, retire finished ones); poll() returns completions.
+    """
+
+    def __init__(self, budget_bytes: int, precision: str = "fp32", rtol: float = 1e-8, maxit: int = 500,
+                 flexible: bool = False, stream=None):
+        self._lib = _lib.load()
+        opt = iffd_options()
+        self._lib.iffd_default_options(ctypes.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.rtol = rtol
+        opt.maxit = maxit
+        opt.flexible = int(flexible)
+        self.options = opt
+        self._stream = stream
+        h = ctypes.c_void_p()
+        check(self._lib.iffd_engine_create(ctypes.byref(opt), int(budget_bytes), _stream_handle(stream),
+                                           ctypes.byref(h)), "iffd_engine_create")
+        self._h = h
+        self._keep = {}  # request id -> (f, u) tensors kept alive until completion
+
+    def request_bytes(self, d: int, n: int, p: int) -> int:
+        nb = ctypes.c_size_t()
+        check(self._lib.iffd_engine_request_bytes(self._h, d, n, p, ctypes.byref(nb)), "iffd_engine_request_bytes")
+        return nb.value
+
+    def submit(self, d: int, n: int, p: int, f, u):
+        """Returns the request id, or None if the arena has no room right now."""
+        rid = ctypes.c_longlong()
+        rc = self._lib.iffd_engine_submit(self._h, d, n, p, _ptr(f), _ptr(u), ctypes.byref(rid))
+        if rc == 4:  # IFFD_ERR_WORKSPACE: admission refused for now
+            return None
+        check(rc, "iffd_engine_submit")
+        self._keep[rid.value] = (f, u)
+        return rid.value
+
+    def step(self, iterations: int = 1) -> int:
+        active = ctypes.c_int()
+        check(self._lib.iffd_engine_step(self._h, int(iterations), ctypes.byref(active)), "iffd_engine_step")
+        return active.value
+
+    def poll(self, capacity: int = 4096):
+        buf = (_lib.iffd_completion * capacity)()
+        cnt = ctypes.c_int()
+        check(self._lib.iffd_engine_poll(self._h, buf, capacity, ctypes.byref(cnt)), "iffd_engine_poll")
+        out = []
+        for k in range(cnt.value):
+            c = buf[k]
+            self._keep.pop(c.id, None)
+            out.append((c.id, {"iters": c.info.iters, "rel_res": c.info.rel_res, "status": c.info.status}))
+        return out
+
+    def stats(self) -> dict:
+        a, fb, kl = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_longlong()
+        check(self._lib.iffd_engine_stats(self._h, ctypes.byref(a), ctypes.byref(fb), ctypes.byref(kl)),
+              "iffd_engine_stats")
+        return {"active": a.value, "bytes_free": fb.value, "kernel_launches": kl.value}
+
+    def run_to_completion(self, iterations_per_step: int = 4) -> list:
+        done = []
+        while True:
+            active = self.step(iterations_per_step)
+            done += self.poll()
+            if active == 0:
+                return done
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.iffd_engine_destroy(self._h)
             self._h = None
 
     def __del__(self):

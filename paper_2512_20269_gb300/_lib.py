@@ -36,6 +36,10 @@ class iffd_pcg_info(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class iffd_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("info", iffd_pcg_info)]
+
+
 # (name, restype, argtypes) of every exported entry point of include/iffd.h
 SIGNATURES = [
     ("iffd_default_options", ctypes.c_int, [ctypes.POINTER(iffd_options)]),
@@ -60,6 +64,16 @@ SIGNATURES = [
                                          c_double_p, ctypes.POINTER(ctypes.c_char_p)]),
     ("iffd_launch_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     ("iffd_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("iffd_engine_create", ctypes.c_int, [ctypes.POINTER(iffd_options), ctypes.c_size_t, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    ("iffd_engine_request_bytes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 c_size_t_p]),
+    ("iffd_engine_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("iffd_engine_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p]),
+    ("iffd_engine_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(iffd_completion), ctypes.c_int, c_int_p]),
+    ("iffd_engine_stats", ctypes.c_int, [ctypes.c_void_p, c_int_p, c_size_t_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("iffd_engine_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("iffd_last_error", ctypes.c_char_p, []),
 ]
 

@@ -12,123 +12,22 @@
 #include "fd.h"
 #include "host_setup.h"
 #include "kernels.h"
+#include "plan.h"
 
 namespace iffd {
 
 thread_local std::string g_err;
 
-static int fail(int code, const std::string& msg) {
+int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
 
-static int cuda_fail(cudaError_t e, const char* where) {
+int cuda_fail(cudaError_t e, const char* where) {
   return fail(IFFD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define IFFD_CUDA(call)                                   \
-  do {                                                    \
-    cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
-  } while (0)
-
 static const double kPi = 3.14159265358979323846264338327950288;
-
-// Launch `call` as one kernel of kind `kind`, with optional event timing.
-#define IFFD_LAUNCH(P, kind, st, call)  \
-  do {                                  \
-    (P)->prof.begin((kind), (st));      \
-    IFFD_CUDA(call);                    \
-    (P)->prof.end(st);                  \
-  } while (0)
-
-// CUDA-event timing of every launch (optional) and a launch counter.
-struct Profiler {
-  bool on = false;
-  long long launches = 0;
-  struct Pending {
-    int kind;
-    cudaEvent_t a, b;
-  };
-  std::vector<cudaEvent_t> pool;
-  std::vector<Pending> pending;
-  long long cnt[IFFD_K_KINDS] = {};
-  double ms[IFFD_K_KINDS] = {};
-  cudaEvent_t take() {
-    cudaEvent_t e = nullptr;
-    if (!pool.empty()) {
-      e = pool.back();
-      pool.pop_back();
-    } else {
-      cudaEventCreate(&e);
-    }
-    return e;
-  }
-  void begin(int kind, cudaStream_t st) {
-    ++launches;
-    if (!on) return;
-    Pending p{kind, take(), nullptr};
-    cudaEventRecord(p.a, st);
-    pending.push_back(p);
-  }
-  void end(cudaStream_t st) {
-    if (!on || pending.empty() || pending.back().b != nullptr) return;
-    pending.back().b = take();
-    cudaEventRecord(pending.back().b, st);
-  }
-  cudaError_t collect() {
-    for (auto& p : pending) {
-      if (p.b == nullptr) continue;
-      cudaError_t e = cudaEventSynchronize(p.b);
-      if (e != cudaSuccess) return e;
-      float t = 0.f;
-      e = cudaEventElapsedTime(&t, p.a, p.b);
-      if (e != cudaSuccess) return e;
-      cnt[p.kind] += 1;
-      ms[p.kind] += t;
-    }
-    for (auto& p : pending) {
-      pool.push_back(p.a);
-      if (p.b) pool.push_back(p.b);
-    }
-    pending.clear();
-    return cudaSuccess;
-  }
-  void release() {
-    for (auto& p : pending) {
-      cudaEventDestroy(p.a);
-      if (p.b) cudaEventDestroy(p.b);
-    }
-    for (auto e : pool) cudaEventDestroy(e);
-    pending.clear();
-    pool.clear();
-  }
-};
-
-// Plan of one problem: host 1D data, device tables, launch geometry.
-struct Plan {
-  mutable Profiler prof;
-  int d = 0, p = 0;
-  int n[3] = {0, 0, 0};
-  int device = 0;
-  iffd_options opt{};
-  Dims dims{};
-  Axis1D host[3];
-  void* dev = nullptr;  // single allocation for all device tables
-  AxisTab<double> axd[3];
-  AxisTab<float> axf[3];
-  BandTab bt[3];
-  WBandTab wb[3];  // variable-coefficient bands (IFFD_COEF_SEPARABLE_SIN)
-  int PPd[3], ldtd[3], PPf[3], ldtf[3], PPs[3], ldts[3], PPv[3];
-  // exact FD tables
-  const double* QT[3] = {nullptr, nullptr, nullptr};
-  const double* Q[3] = {nullptr, nullptr, nullptr};
-  const double* lamQ[3] = {nullptr, nullptr, nullptr};
-  // workspace layout (bytes)
-  size_t off_r, off_z, off_p, off_q, off_t1, off_t2, off_t3, off_t4, off_tf, off_part, off_state, ws_bytes;
-  int max_parts = 0;
-  SolveState* host_state = nullptr;  // pinned
-};
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -594,9 +493,6 @@ static int check_device(const Plan* P) {
 
 using namespace iffd;
 
-struct iffd_plan {
-  Plan P;
-};
 
 namespace iffd {
 
@@ -624,25 +520,11 @@ int record_error(int code, const std::string& msg) { return fail(code, msg); }
 
 }  // namespace iffd
 
-extern "C" {
+namespace iffd {
 
-int iffd_default_options(iffd_options* opt) {
-  if (!opt) return fail(IFFD_ERR_INVALID_ARG, "opt is NULL");
-  opt->precision = IFFD_PREC_FP64;
-  opt->precond = IFFD_PRECOND_IFFD;
-  opt->rtol = 1e-8;
-  opt->maxit = 500;
-  opt->coef = IFFD_COEF_CONST;
-  opt->true_residual = 1;
-  opt->flexible = 0;
-  opt->coef_amp = 0.5;
-  return IFFD_OK;
-}
-
-int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
-               iffd_handle* out) {
-  g_err.clear();
-  if (!out || !n_elems || !dirichlet) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, cudaStream_t stream,
+                iffd_plan** outp) {
+  if (!outp || !n_elems || !dirichlet) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
   if (d != 2 && d != 3) return fail(IFFD_ERR_INVALID_ARG, "d must be 2 or 3");
   if (p < 1) return fail(IFFD_ERR_INVALID_ARG, "p must be >= 1");
   bool any_dir = false;
@@ -681,7 +563,7 @@ int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iff
     }
     if (o.coef == IFFD_COEF_SEPARABLE_SIN) build_weighted_bands(&P->host[a]);
   }
-  const int rc = build_plan(P, static_cast<cudaStream_t>(stream));
+  const int rc = build_plan(P, stream);
   if (rc != IFFD_OK) {
     const std::string msg = g_err;
     if (P->dev) cudaFree(P->dev);
@@ -690,6 +572,45 @@ int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iff
     g_err = msg;
     return rc;
   }
+  *outp = h;
+  return IFFD_OK;
+}
+
+void plan_release(iffd_plan* h) {
+  if (!h) return;
+  Plan* P = &h->P;
+  P->prof.release();
+  if (P->dev) cudaFree(P->dev);
+  if (P->host_state) cudaFreeHost(P->host_state);
+  delete h;
+}
+
+StiffLaunch plan_stiff_launch(const Plan* P, int axis) { return make_stiff(P, axis); }
+
+}  // namespace iffd
+
+extern "C" {
+
+int iffd_default_options(iffd_options* opt) {
+  if (!opt) return fail(IFFD_ERR_INVALID_ARG, "opt is NULL");
+  opt->precision = IFFD_PREC_FP64;
+  opt->precond = IFFD_PRECOND_IFFD;
+  opt->rtol = 1e-8;
+  opt->maxit = 500;
+  opt->coef = IFFD_COEF_CONST;
+  opt->true_residual = 1;
+  opt->flexible = 0;
+  opt->coef_amp = 0.5;
+  return IFFD_OK;
+}
+
+int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
+               iffd_handle* out) {
+  g_err.clear();
+  if (!out) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  iffd_plan* h = nullptr;
+  const int rc = plan_create(d, n_elems, p, dirichlet, opt, static_cast<cudaStream_t>(stream), &h);
+  if (rc != IFFD_OK) return rc;
   *out = h;
   return IFFD_OK;
 }
@@ -878,10 +799,7 @@ int iffd_launch_count(iffd_handle h, long long* count) {
 
 int iffd_destroy(iffd_handle h) {
   if (!h) return IFFD_OK;
-  h->P.prof.release();
-  if (h->P.dev) cudaFree(h->P.dev);
-  if (h->P.host_state) cudaFreeHost(h->P.host_state);
-  delete h;
+  plan_release(h);
   return IFFD_OK;
 }
 

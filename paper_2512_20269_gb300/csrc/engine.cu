@@ -1,0 +1,734 @@
+// Batched solves with continuous batching (iffd_engine_*).
+//
+// Many independent IFFD-PCG solves advance together: each phase of a PCG
+// iteration (stiffness sweeps, reductions, vector update, transform passes) is
+// one batched launch covering the tiles of every active system (the stiffness
+// sweeps are grouped by degree). A system's kernels, tile decomposition and
+// reduction order are exactly those of the single-system path, so its result
+// does not depend on which other systems share the launches.
+//
+// Requests are admitted while their workspace fits the engine's device arena
+// (the budget); an admitted request is initialised at the next step and then
+// iterates with the others; finished systems are retired after each step and
+// their workspace returns to the arena, so later requests can join while
+// earlier ones are still iterating. The per-iteration launch sequence is
+// captured into a CUDA graph and replayed while the set of systems is unchanged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/iffd.h"
+#include "device_common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace iffd {
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// First-fit sub-allocator over one device allocation.
+struct Arena {
+  char* base = nullptr;
+  size_t bytes = 0;
+  std::map<size_t, size_t> free_;  // offset -> size
+  void init(char* b, size_t n) {
+    base = b;
+    bytes = n;
+    free_.clear();
+    free_[0] = n;
+  }
+  bool alloc(size_t n, size_t* off) {
+    n = al256(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n;
+        const size_t noff = it->first + n;
+        free_.erase(it);
+        if (rest) free_[noff] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = al256(n);
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t available() const {
+    size_t s = 0;
+    for (auto& kv : free_) s += kv.second;
+    return s;
+  }
+};
+
+struct Sys {
+  long long id;
+  iffd_plan* plan;
+  const double* f;
+  double* u;
+  size_t off, bytes;
+  char* ws;
+  int phase;  // 0: admitted, not initialised; 1: iterating
+};
+
+// Growable device buffer.
+struct DevBuf {
+  char* p = nullptr;
+  size_t cap = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) cap = n;
+    return e;
+  }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Host staging of all descriptors of one launch sequence; uploaded in one copy.
+struct Staging {
+  std::vector<char> bytes;
+  template <typename T>
+  size_t put(const std::vector<T>& v) {
+    const size_t off = al256(bytes.size());
+    bytes.resize(off + std::max<size_t>(1, v.size()) * sizeof(T));
+    if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+}  // namespace
+
+struct Engine {
+  iffd_options opt{};
+  cudaStream_t st = nullptr;       // the engine's own stream (graph capture needs a non-default stream)
+  cudaStream_t user_st = nullptr;  // the caller's stream: each step starts after its pending work
+  cudaEvent_t ev = nullptr;
+  int device = 0;
+  char* arena_mem = nullptr;
+  Arena arena;
+  std::map<std::tuple<int, int, int>, iffd_plan*> plans;
+  std::vector<Sys> active;
+  std::vector<iffd_completion> done_list;
+  long long next_id = 1;
+  long long launches = 0;
+  // descriptor buffers: init phase and iteration phase
+  DevBuf dinit, diter, dstates;
+  SolveState* hstates = nullptr;
+  size_t hstates_cap = 0;
+  // captured iteration graph, its kernel count and the membership it was built for
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  std::vector<long long> graph_ids;
+  ~Engine() {
+    if (st) cudaStreamSynchronize(st);
+    if (graph) cudaGraphExecDestroy(graph);
+    if (ev) cudaEventDestroy(ev);
+    if (st) cudaStreamDestroy(st);
+    for (auto& kv : plans) plan_release(kv.second);
+    if (arena_mem) cudaFree(arena_mem);
+    if (hstates) cudaFreeHost(hstates);
+  }
+};
+
+namespace {
+
+template <typename T>
+T* at(char* base, size_t off) {
+  return reinterpret_cast<T*>(base + off);
+}
+
+double* vr(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_r); }
+double* vz(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_z); }
+double* vp(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_p); }
+double* vq(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_q); }
+double* vt1(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_t1); }
+double* vt2(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_t2); }
+float* vtf(const Sys& s) { return reinterpret_cast<float*>(s.ws + s.plan->P.off_tf); }
+double* vpart(const Sys& s) { return reinterpret_cast<double*>(s.ws + s.plan->P.off_part); }
+SolveState* vst(const Sys& s) { return reinterpret_cast<SolveState*>(s.ws + s.plan->P.off_state); }
+
+// One batched transform launch: descriptors of the systems taking part.
+template <typename Tc, typename Tin, typename Tout>
+struct PassLaunchB {
+  std::vector<PassDesc<Tc, Tin, Tout>> desc;
+  std::vector<long long> prefix{0};
+  size_t smem = 0;
+  int mode = PM_FWD, ndot = 0;
+  size_t off_desc = 0, off_prefix = 0;
+  void add(const PassDesc<Tc, Tin, Tout>& d, int tiles, size_t sm) {
+    desc.push_back(d);
+    prefix.push_back(prefix.back() + tiles);
+    smem = std::max(smem, sm);
+  }
+};
+
+struct StiffLaunchB {
+  int p = 0, stage = 0;
+  std::vector<StiffDesc> desc;
+  std::vector<long long> prefix{0};
+  size_t smem = 0;
+  size_t off_desc = 0, off_prefix = 0;
+};
+
+struct VecLaunchB {
+  std::vector<VecDesc> desc;
+  std::vector<long long> prefix{0};
+  size_t off_desc = 0, off_prefix = 0;
+};
+
+struct FinLaunchB {
+  std::vector<FinDesc> desc;
+  int phase = 0;
+  size_t off = 0;
+};
+
+// The transform passes of one preconditioner apply for a set of systems, as
+// batched launches. ndot: dot products fused into the last pass.
+struct PrecondSeq {
+  bool fp32 = false;
+  // FP64 passes
+  std::vector<PassLaunchB<double, double, double>> d64;
+  // FP32 passes: first (r -> tf), middle (tf -> tf), last (tf -> z)
+  PassLaunchB<float, double, float> f_first;
+  std::vector<PassLaunchB<float, float, float>> f_mid;
+  PassLaunchB<float, float, double> f_last;
+};
+
+template <typename Tc>
+PassDesc<Tc, Tc, Tc> pdesc_same(const Plan& P, int axis, const AxisTab<Tc>* tabs, const int* PPs, const int* ldts,
+                                const int* done) {
+  PassDesc<Tc, Tc, Tc> d{};
+  d.dims = P.dims;
+  d.axis = axis;
+  d.PP = PPs[axis];
+  d.ldt = ldts[axis];
+  d.ax = tabs[axis];
+  d.lamA = tabs[0].lam;
+  d.lamB = (P.d == 3) ? tabs[1].lam : tabs[0].lam;
+  d.done = done;
+  return d;
+}
+
+// Builds the pass sequence; pass k of the sequence is: FWD axis 0, FWD axis 1
+// (3D), FUSED last axis, BWD axis 1 (3D), BWD axis 0 (+dots).
+void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, PrecondSeq* seq) {
+  seq->fp32 = !sys.empty() && sys[0]->plan->P.opt.precision == IFFD_PREC_FP32_TRANSFORM;
+  if (!seq->fp32) {
+    seq->d64.assign(5, {});
+    const int modes[5] = {PM_FWD, PM_FWD, PM_FUSED, PM_BWD, PM_BWD};
+    for (int k = 0; k < 5; ++k) seq->d64[k].mode = modes[k];
+    seq->d64[4].ndot = ndot;
+    for (const Sys* s : sys) {
+      const Plan& P = s->plan->P;
+      const int* done = &vst(*s)->done;
+      const int d = P.d;
+      const int axes[5] = {0, 1, d - 1, 1, 0};
+      for (int k = 0; k < 5; ++k) {
+        if (d == 2 && (k == 1 || k == 3)) continue;
+        const int a = axes[k];
+        auto D = pdesc_same<double>(P, a, P.axd, P.PPd, P.ldtd, done);
+        D.in = (k == 0) ? vr(*s) : vz(*s);
+        D.out = vz(*s);
+        if (k == 4) {
+          D.dot0 = vr(*s);
+          D.dot1 = use_q ? vq(*s) : nullptr;
+          D.partial = vpart(*s);
+        }
+        seq->d64[k].add(D, precond_tiles(P.dims, a, P.PPd[a]),
+                        precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].L, sizeof(double)));
+      }
+    }
+    return;
+  }
+  seq->f_first = {};
+  seq->f_first.mode = PM_FWD;
+  seq->f_mid.assign(3, {});
+  seq->f_mid[0].mode = PM_FWD;    // axis 1 (3D)
+  seq->f_mid[1].mode = PM_FUSED;  // last axis
+  seq->f_mid[2].mode = PM_BWD;    // axis 1 (3D)
+  seq->f_last = {};
+  seq->f_last.mode = PM_BWD;
+  seq->f_last.ndot = ndot;
+  for (const Sys* s : sys) {
+    const Plan& P = s->plan->P;
+    const int* done = &vst(*s)->done;
+    const int d = P.d;
+    {
+      PassDesc<float, double, float> D{};
+      auto T = pdesc_same<float>(P, 0, P.axf, P.PPf, P.ldtf, done);
+      D.dims = T.dims; D.axis = 0; D.PP = T.PP; D.ldt = T.ldt; D.ax = T.ax; D.lamA = T.lamA; D.lamB = T.lamB;
+      D.done = done;
+      D.in = vr(*s);
+      D.out = vtf(*s);
+      seq->f_first.add(D, precond_tiles(P.dims, 0, P.PPf[0]),
+                       precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].L, sizeof(float)));
+    }
+    const int axes[3] = {1, d - 1, 1};
+    for (int k = 0; k < 3; ++k) {
+      if (d == 2 && k != 1) continue;
+      const int a = axes[k];
+      auto D = pdesc_same<float>(P, a, P.axf, P.PPf, P.ldtf, done);
+      D.in = vtf(*s);
+      D.out = vtf(*s);
+      seq->f_mid[k].add(D, precond_tiles(P.dims, a, P.PPf[a]),
+                        precond_smem_bytes(P.PPf[a], P.ldtf[a], P.axf[a].L, sizeof(float)));
+    }
+    {
+      PassDesc<float, float, double> D{};
+      auto T = pdesc_same<float>(P, 0, P.axf, P.PPf, P.ldtf, done);
+      D.dims = T.dims; D.axis = 0; D.PP = T.PP; D.ldt = T.ldt; D.ax = T.ax; D.lamA = T.lamA; D.lamB = T.lamB;
+      D.done = done;
+      D.in = vtf(*s);
+      D.out = vz(*s);
+      D.dot0 = vr(*s);
+      D.dot1 = use_q ? vq(*s) : nullptr;
+      D.partial = vpart(*s);
+      seq->f_last.add(D, precond_tiles(P.dims, 0, P.PPf[0]),
+                      precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].L, sizeof(float)));
+    }
+  }
+}
+
+template <typename L>
+void stage_pass(Staging& sg, L& l) {
+  l.off_desc = sg.put(l.desc);
+  l.off_prefix = sg.put(l.prefix);
+}
+
+void stage_precond(Staging& sg, PrecondSeq& q) {
+  if (!q.fp32) {
+    for (auto& l : q.d64) stage_pass(sg, l);
+  } else {
+    stage_pass(sg, q.f_first);
+    for (auto& l : q.f_mid) stage_pass(sg, l);
+    stage_pass(sg, q.f_last);
+  }
+}
+
+template <typename Tc, typename Tin, typename Tout>
+int run_pass(Engine* E, char* base, PassLaunchB<Tc, Tin, Tout>& l) {
+  if (l.desc.empty()) return IFFD_OK;
+  IFFD_CUDA((launch_pass_batched<Tc, Tin, Tout>(at<PassDesc<Tc, Tin, Tout>>(base, l.off_desc),
+                                                at<long long>(base, l.off_prefix), (int)l.desc.size(),
+                                                l.prefix.back(), l.smem, l.mode, l.ndot, E->st)));
+  if (l.prefix.back() > 0) ++E->launches;
+  return IFFD_OK;
+}
+
+int run_precond_seq(Engine* E, char* base, PrecondSeq& q) {
+  int rc;
+  if (!q.fp32) {
+    for (auto& l : q.d64)
+      if ((rc = run_pass(E, base, l))) return rc;
+    return IFFD_OK;
+  }
+  if ((rc = run_pass(E, base, q.f_first))) return rc;
+  for (auto& l : q.f_mid)
+    if ((rc = run_pass(E, base, l))) return rc;
+  return run_pass(E, base, q.f_last);
+}
+
+int run_fin(Engine* E, char* base, FinLaunchB& f) {
+  if (f.desc.empty()) return IFFD_OK;
+  IFFD_CUDA(launch_finalize_batched(at<FinDesc>(base, f.off), (int)f.desc.size(), f.phase,
+                                    E->opt.rtol * E->opt.rtol, E->opt.maxit, E->st));
+  ++E->launches;
+  return IFFD_OK;
+}
+
+// ---- init phase of newly admitted systems
+int run_init(Engine* E, const std::vector<const Sys*>& sys) {
+  if (sys.empty()) return IFFD_OK;
+  VecLaunchB vl;
+  FinLaunchB fff, frz0;
+  fff.phase = FP_FF;
+  frz0.phase = FP_RZ0;
+  for (const Sys* s : sys) {
+    const Plan& P = s->plan->P;
+    VecDesc v{};
+    v.f = s->f;
+    v.x = s->u;
+    v.r = vr(*s);
+    v.st = vst(*s);
+    v.N = P.dims.N;
+    v.part_rr = vpart(*s);
+    v.p_zero = vp(*s);
+    vl.desc.push_back(v);
+    vl.prefix.push_back(vl.prefix.back() + vec_grid(P.dims.N));
+    fff.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
+    const int* PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? P.PPf : P.PPd;
+    frz0.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0[0])});
+  }
+  PrecondSeq pc;
+  build_precond(sys, 1, false, &pc);
+  Staging sg;
+  stage_pass(sg, vl);
+  fff.off = sg.put(fff.desc);
+  frz0.off = sg.put(frz0.desc);
+  stage_precond(sg, pc);
+  IFFD_CUDA(E->dinit.reserve(sg.bytes.size()));
+  char* base = E->dinit.p;
+  IFFD_CUDA(cudaMemcpyAsync(base, sg.bytes.data(), sg.bytes.size(), cudaMemcpyHostToDevice, E->st));
+  IFFD_CUDA(launch_pcg_init_batched(at<VecDesc>(base, vl.off_desc), at<long long>(base, vl.off_prefix),
+                                    (int)vl.desc.size(), vl.prefix.back(), E->st));
+  ++E->launches;
+  int rc;
+  if ((rc = run_fin(E, base, fff))) return rc;
+  if ((rc = run_precond_seq(E, base, pc))) return rc;
+  if ((rc = run_fin(E, base, frz0))) return rc;
+  // the host copy of the staging must outlive the asynchronous upload
+  IFFD_CUDA(cudaStreamSynchronize(E->st));
+  return IFFD_OK;
+}
+
+// ---- one PCG iteration of all iterating systems, captured into a graph
+struct IterSeq {
+  std::vector<StiffLaunchB> stiff;  // grouped by (stage, p)
+  FinLaunchB fpq, frr, frz;
+  VecLaunchB upd;
+  PrecondSeq pc;
+};
+
+int enqueue_iteration(Engine* E, char* base, IterSeq& it) {
+  int rc;
+  for (auto& l : it.stiff) {
+    if (l.desc.empty()) continue;
+    IFFD_CUDA(launch_stiff_batched(l.p, l.stage, at<StiffDesc>(base, l.off_desc), at<long long>(base, l.off_prefix),
+                                   (int)l.desc.size(), l.prefix.back(), l.smem, E->st));
+    ++E->launches;
+  }
+  if ((rc = run_fin(E, base, it.fpq))) return rc;
+  IFFD_CUDA(launch_pcg_update_batched(at<VecDesc>(base, it.upd.off_desc), at<long long>(base, it.upd.off_prefix),
+                                      (int)it.upd.desc.size(), it.upd.prefix.back(), E->st));
+  ++E->launches;
+  if ((rc = run_fin(E, base, it.frr))) return rc;
+  if ((rc = run_precond_seq(E, base, it.pc))) return rc;
+  return run_fin(E, base, it.frz);
+}
+
+int build_iteration(Engine* E) {
+  std::vector<const Sys*> sys;
+  for (auto& s : E->active) sys.push_back(&s);
+  IterSeq it;
+  std::map<std::pair<int, int>, size_t> group;  // (stage, p) -> index
+  const bool flex = E->opt.flexible || E->opt.precision == IFFD_PREC_FP32_TRANSFORM;
+  it.fpq.phase = FP_PQ;
+  it.frr.phase = FP_RR;
+  it.frz.phase = flex ? FP_RZ_FLEX : FP_RZ;
+  for (const Sys* s : sys) {
+    const Plan& P = s->plan->P;
+    const int d = P.d;
+    for (int stage = SS_FIRST; stage <= SS_LAST; ++stage) {
+      if (d == 2 && stage == SS_MID) continue;
+      const int axis = (stage == SS_FIRST) ? d - 1 : (stage == SS_MID ? 1 : 0);
+      auto key = std::make_pair(stage, P.p);
+      if (!group.count(key)) {
+        group[key] = it.stiff.size();
+        it.stiff.push_back({});
+        it.stiff.back().p = P.p;
+        it.stiff.back().stage = stage;
+      }
+      StiffLaunchB& l = it.stiff[group[key]];
+      const StiffLaunch S = plan_stiff_launch(&P, axis);
+      StiffDesc D{};
+      D.dims = S.dims;
+      D.axis = axis;
+      D.PP = S.PP;
+      D.ldt = S.ldt;
+      D.bt = S.bt;
+      D.z = vz(*s);
+      D.p_io = vp(*s);
+      D.beta = &vst(*s)->beta;
+      D.pmode = 2;  // p = z + beta p, beta = 0 and p = 0 after the batched init
+      D.T1 = vt1(*s);
+      D.T2 = vt2(*s);
+      D.out = vq(*s);
+      D.dotv = vp(*s);
+      D.partial = vpart(*s);
+      D.done = &vst(*s)->done;
+      l.desc.push_back(D);
+      l.prefix.push_back(l.prefix.back() + stiff_tiles(P.dims, axis, S.PP));
+      l.smem = std::max(l.smem, (size_t)(stage == SS_FIRST ? 1 : 2) * S.PP * S.ldt * sizeof(double));
+    }
+    it.fpq.desc.push_back({vst(*s), vpart(*s), stiff_tiles(P.dims, 0, P.PPs[0])});
+    VecDesc v{};
+    v.x = s->u;
+    v.r = vr(*s);
+    v.p = vp(*s);
+    v.q = vq(*s);
+    v.st = vst(*s);
+    v.N = P.dims.N;
+    v.part_rr = vpart(*s);
+    it.upd.desc.push_back(v);
+    it.upd.prefix.push_back(it.upd.prefix.back() + vec_grid(P.dims.N));
+    it.frr.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
+    const int* PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? P.PPf : P.PPd;
+    it.frz.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0[0])});
+  }
+  build_precond(sys, flex ? 2 : 1, flex, &it.pc);
+  Staging sg;
+  for (auto& l : it.stiff) stage_pass(sg, l);
+  it.fpq.off = sg.put(it.fpq.desc);
+  it.frr.off = sg.put(it.frr.desc);
+  it.frz.off = sg.put(it.frz.desc);
+  stage_pass(sg, it.upd);
+  stage_precond(sg, it.pc);
+  IFFD_CUDA(E->diter.reserve(sg.bytes.size()));
+  char* base = E->diter.p;
+  IFFD_CUDA(cudaMemcpyAsync(base, sg.bytes.data(), sg.bytes.size(), cudaMemcpyHostToDevice, E->st));
+  IFFD_CUDA(cudaStreamSynchronize(E->st));
+  // raise the shared-memory attributes outside the capture (zero-tile launches)
+  for (auto& l : it.stiff)
+    IFFD_CUDA(launch_stiff_batched(l.p, l.stage, nullptr, nullptr, 0, 0, l.smem, E->st));
+  if (E->graph) {
+    cudaGraphExecDestroy(E->graph);
+    E->graph = nullptr;
+  }
+  // warm the pass-kernel attributes the same way by a capture-free dry pass
+  {
+    IterSeq dry = it;
+    for (auto& l : dry.pc.d64) l.prefix.assign(l.prefix.size(), 0);
+    dry.pc.f_first.prefix.assign(dry.pc.f_first.prefix.size(), 0);
+    for (auto& l : dry.pc.f_mid) l.prefix.assign(l.prefix.size(), 0);
+    dry.pc.f_last.prefix.assign(dry.pc.f_last.prefix.size(), 0);
+    int rc = run_precond_seq(E, base, dry.pc);
+    if (rc) return rc;
+  }
+  cudaGraph_t g = nullptr;
+  IFFD_CUDA(cudaStreamBeginCapture(E->st, cudaStreamCaptureModeThreadLocal));
+  const long long before = E->launches;
+  int rc = enqueue_iteration(E, base, it);
+  cudaError_t ce = cudaStreamEndCapture(E->st, &g);
+  E->graph_kernels = E->launches - before;  // kernels per replay, counted when the graph is launched
+  E->launches = before;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&E->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+  E->graph_ids.clear();
+  for (auto& s : E->active) E->graph_ids.push_back(s.id);
+  return IFFD_OK;
+}
+
+}  // namespace
+
+}  // namespace iffd
+
+using namespace iffd;
+
+struct iffd_engine {
+  Engine E;
+};
+
+extern "C" {
+
+int iffd_engine_create(const iffd_options* opt, size_t budget_bytes, void* stream, iffd_engine_handle* out) {
+  g_err.clear();
+  if (!out) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  iffd_options o;
+  iffd_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precond != IFFD_PRECOND_IFFD || o.coef != IFFD_COEF_CONST)
+    return fail(IFFD_ERR_UNSUPPORTED, "the engine serves IFFD-preconditioned constant-coefficient solves");
+  if (budget_bytes < 4096) return fail(IFFD_ERR_INVALID_ARG, "budget too small");
+  iffd_engine* h = new iffd_engine();
+  Engine& E = h->E;
+  E.opt = o;
+  E.user_st = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&E.device);
+  cudaError_t e = cudaStreamCreateWithFlags(&E.st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "engine stream");
+  }
+  e = cudaMalloc(&E.arena_mem, budget_bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "engine arena");
+  }
+  E.arena.init(E.arena_mem, budget_bytes);
+  *out = h;
+  return IFFD_OK;
+}
+
+static int engine_plan(iffd_engine* h, int d, int n, int p, iffd_plan** out) {
+  Engine& E = h->E;
+  auto key = std::make_tuple(d, n, p);
+  auto it = E.plans.find(key);
+  if (it != E.plans.end()) {
+    *out = it->second;
+    return IFFD_OK;
+  }
+  const int nn[3] = {n, n, n};
+  const int dir[6] = {1, 1, 1, 1, 1, 1};
+  iffd_options o = E.opt;
+  o.true_residual = 0;
+  iffd_plan* P = nullptr;
+  const int rc = plan_create(d, nn, p, dir, &o, E.st, &P);
+  if (rc) return rc;
+  E.plans[key] = P;
+  *out = P;
+  return IFFD_OK;
+}
+
+int iffd_engine_request_bytes(iffd_engine_handle h, int d, int n, int p, size_t* bytes) {
+  if (!h || !bytes) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  iffd_plan* P = nullptr;
+  const int rc = engine_plan(h, d, n, p, &P);
+  if (rc) return rc;
+  *bytes = al256(P->P.ws_bytes);
+  return IFFD_OK;
+}
+
+int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const double* f, double* u, long long* id) {
+  if (!h || !f || !u || !id) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (f == u) return fail(IFFD_ERR_INVALID_ARG, "f and u must not alias");
+  Engine& E = h->E;
+  iffd_plan* P = nullptr;
+  int rc = engine_plan(h, d, n, p, &P);
+  if (rc) return rc;
+  const size_t need = al256(P->P.ws_bytes);
+  if (need > E.arena.bytes) return fail(IFFD_ERR_UNSUPPORTED, "request needs more workspace than the whole budget");
+  size_t off = 0;
+  if (!E.arena.alloc(need, &off)) return fail(IFFD_ERR_WORKSPACE, "budget exhausted: resubmit after completions");
+  Sys s{};
+  s.id = E.next_id++;
+  s.plan = P;
+  s.f = f;
+  s.u = u;
+  s.off = off;
+  s.bytes = need;
+  s.ws = E.arena_mem + off;
+  s.phase = 0;
+  E.active.push_back(s);
+  *id = s.id;
+  return IFFD_OK;
+}
+
+int iffd_engine_step(iffd_engine_handle h, int iterations, int* active) {
+  if (!h || iterations < 0) return fail(IFFD_ERR_INVALID_ARG, "bad argument");
+  Engine& E = h->E;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != E.device) return fail(IFFD_ERR_INVALID_ARG, "engine was created on another device");
+  IFFD_CUDA(cudaEventRecord(E.ev, E.user_st));
+  IFFD_CUDA(cudaStreamWaitEvent(E.st, E.ev, 0));
+  // 1. initialise newly admitted systems
+  std::vector<const Sys*> fresh;
+  for (auto& s : E.active)
+    if (s.phase == 0) fresh.push_back(&s);
+  int rc = run_init(&E, fresh);
+  if (rc) return rc;
+  for (auto& s : E.active) s.phase = 1;
+  // 2. iterations of every active system (graph rebuilt when membership changed)
+  if (!E.active.empty() && iterations > 0) {
+    bool same = E.graph && E.graph_ids.size() == E.active.size();
+    for (size_t i = 0; same && i < E.active.size(); ++i) same = E.graph_ids[i] == E.active[i].id;
+    if (!same) {
+      rc = build_iteration(&E);
+      if (rc) return rc;
+    }
+    for (int k = 0; k < iterations; ++k) {
+      cudaError_t e = cudaGraphLaunch(E.graph, E.st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+      E.launches += E.graph_kernels;
+    }
+  }
+  // 3. read every state, retire finished systems
+  const int n = (int)E.active.size();
+  if (n > 0) {
+    std::vector<SolveState*> ptrs(n);
+    for (int i = 0; i < n; ++i) ptrs[i] = vst(E.active[i]);
+    IFFD_CUDA(E.dstates.reserve(al256(n * sizeof(SolveState*)) + n * sizeof(SolveState)));
+    SolveState** dptr = reinterpret_cast<SolveState**>(E.dstates.p);
+    SolveState* dst = reinterpret_cast<SolveState*>(E.dstates.p + al256(n * sizeof(SolveState*)));
+    IFFD_CUDA(cudaMemcpyAsync(dptr, ptrs.data(), n * sizeof(SolveState*), cudaMemcpyHostToDevice, E.st));
+    IFFD_CUDA(launch_gather_states(dptr, dst, n, E.st));
+    ++E.launches;
+    if ((size_t)n > E.hstates_cap) {
+      if (E.hstates) cudaFreeHost(E.hstates);
+      E.hstates = nullptr;
+      IFFD_CUDA(cudaHostAlloc((void**)&E.hstates, n * sizeof(SolveState), cudaHostAllocDefault));
+      E.hstates_cap = n;
+    }
+    IFFD_CUDA(cudaMemcpyAsync(E.hstates, dst, n * sizeof(SolveState), cudaMemcpyDeviceToHost, E.st));
+    IFFD_CUDA(cudaStreamSynchronize(E.st));
+    std::vector<Sys> keep;
+    for (int i = 0; i < n; ++i) {
+      const SolveState& ss = E.hstates[i];
+      if (ss.done) {
+        iffd_completion c{};
+        c.id = E.active[i].id;
+        c.info.iters = ss.iters;
+        c.info.rel_res = ss.ff > 0 ? std::sqrt(ss.rr / ss.ff) : 0.0;
+        c.info.true_rel_res = -1.0;
+        c.info.status = ss.status;
+        E.done_list.push_back(c);
+        E.arena.release(E.active[i].off, E.active[i].bytes);
+      } else {
+        keep.push_back(E.active[i]);
+      }
+    }
+    E.active.swap(keep);
+  }
+  if (active) *active = (int)E.active.size();
+  return IFFD_OK;
+}
+
+int iffd_engine_poll(iffd_engine_handle h, iffd_completion* out, int capacity, int* count) {
+  if (!h || !count || (capacity > 0 && !out)) return fail(IFFD_ERR_INVALID_ARG, "bad argument");
+  Engine& E = h->E;
+  const int n = std::min<int>(capacity, (int)E.done_list.size());
+  for (int i = 0; i < n; ++i) out[i] = E.done_list[i];
+  E.done_list.erase(E.done_list.begin(), E.done_list.begin() + n);
+  *count = n;
+  return IFFD_OK;
+}
+
+int iffd_engine_stats(iffd_engine_handle h, int* active, size_t* bytes_free, long long* kernel_launches) {
+  if (!h) return fail(IFFD_ERR_INVALID_ARG, "NULL handle");
+  if (active) *active = (int)h->E.active.size();
+  if (bytes_free) *bytes_free = h->E.arena.available();
+  if (kernel_launches) *kernel_launches = h->E.launches;
+  return IFFD_OK;
+}
+
+int iffd_engine_destroy(iffd_engine_handle h) {
+  if (!h) return IFFD_OK;
+  cudaStreamSynchronize(h->E.st);
+  delete h;
+  return IFFD_OK;
+}
+
+}  // extern "C"

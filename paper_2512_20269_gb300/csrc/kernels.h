@@ -144,7 +144,9 @@ struct VecDesc {
   SolveState* st;
   long long N;
   double* part_rr;  // partial sums of ||f||^2 / ||r||^2 (vec_grid(N) entries)
+  double* p_zero;   // batched init only: search direction to clear (may be null)
 };
+cudaError_t launch_gather_states(SolveState* const* src, SolveState* dst, int n, cudaStream_t st);
 struct FinDesc {
   SolveState* st;
   const double* partial;

@@ -92,7 +92,23 @@ pcg_init_batched(const VecDesc* __restrict__ sys, const long long* __restrict__ 
   const VecDesc& d = sys[s];
   const int blk = (int)(blockIdx.x - prefix[s]);
   const int nblk = (int)(prefix[s + 1] - prefix[s]);
+  if (blk == 0 && threadIdx.x == 0) *d.st = SolveState{};
   init_body(d.f, d.x, d.r, d.N, d.part_rr, blk, nblk);
+  if (d.p_zero != nullptr)
+    for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < d.N; i += (long long)nblk * blockDim.x)
+      d.p_zero[i] = 0.0;
+}
+
+// Copies the solve state of every system into one array (one D2H copy).
+__global__ void gather_states(SolveState* const* __restrict__ src, SolveState* __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = *src[i];
+}
+
+cudaError_t launch_gather_states(SolveState* const* src, SolveState* dst, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  gather_states<<<(n + 127) / 128, 128, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kThreads)

@@ -1,0 +1,138 @@
+// Internal plan structure shared by the C ABI (capi.cu) and the batched /
+// serving engine (engine.cu). Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iffd.h"
+#include "device_common.cuh"
+#include "host_setup.h"
+#include "kernels.h"
+
+namespace iffd {
+
+extern thread_local std::string g_err;
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+#define IFFD_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::iffd::cuda_fail(e_, #call); \
+  } while (0)
+
+// Launch `call` as one kernel of kind `kind`, with optional event timing.
+#define IFFD_LAUNCH(P, kind, st, call)  \
+  do {                                  \
+    (P)->prof.begin((kind), (st));      \
+    IFFD_CUDA(call);                    \
+    (P)->prof.end(st);                  \
+  } while (0)
+
+// CUDA-event timing of every launch (optional) and a launch counter.
+struct Profiler {
+  bool on = false;
+  long long launches = 0;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  long long cnt[IFFD_K_KINDS] = {};
+  double ms[IFFD_K_KINDS] = {};
+  cudaEvent_t take() {
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  void begin(int kind, cudaStream_t st) {
+    ++launches;
+    if (!on) return;
+    Pending p{kind, take(), nullptr};
+    cudaEventRecord(p.a, st);
+    pending.push_back(p);
+  }
+  void end(cudaStream_t st) {
+    if (!on || pending.empty() || pending.back().b != nullptr) return;
+    pending.back().b = take();
+    cudaEventRecord(pending.back().b, st);
+  }
+  cudaError_t collect() {
+    for (auto& p : pending) {
+      if (p.b == nullptr) continue;
+      cudaError_t e = cudaEventSynchronize(p.b);
+      if (e != cudaSuccess) return e;
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p.a, p.b);
+      if (e != cudaSuccess) return e;
+      cnt[p.kind] += 1;
+      ms[p.kind] += t;
+    }
+    for (auto& p : pending) {
+      pool.push_back(p.a);
+      if (p.b) pool.push_back(p.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+  void release() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      if (p.b) cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+    pending.clear();
+    pool.clear();
+  }
+};
+
+// Plan of one problem: host 1D data, device tables, launch geometry.
+struct Plan {
+  mutable Profiler prof;
+  int d = 0, p = 0;
+  int n[3] = {0, 0, 0};
+  int device = 0;
+  iffd_options opt{};
+  Dims dims{};
+  Axis1D host[3];
+  void* dev = nullptr;  // single allocation for all device tables
+  AxisTab<double> axd[3];
+  AxisTab<float> axf[3];
+  BandTab bt[3];
+  WBandTab wb[3];  // variable-coefficient bands (IFFD_COEF_SEPARABLE_SIN)
+  int PPd[3], ldtd[3], PPf[3], ldtf[3], PPs[3], ldts[3], PPv[3];
+  // exact FD tables
+  const double* QT[3] = {nullptr, nullptr, nullptr};
+  const double* Q[3] = {nullptr, nullptr, nullptr};
+  const double* lamQ[3] = {nullptr, nullptr, nullptr};
+  // workspace layout (bytes)
+  size_t off_r, off_z, off_p, off_q, off_t1, off_t2, off_t3, off_t4, off_tf, off_part, off_state, ws_bytes;
+  int max_parts = 0;
+  SolveState* host_state = nullptr;  // pinned
+};
+
+
+}  // namespace iffd
+
+struct iffd_plan {
+  iffd::Plan P;
+};
+
+namespace iffd {
+
+// Builds a plan (host 1D setup + device tables) on the current device.
+int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, cudaStream_t stream,
+                iffd_plan** out);
+void plan_release(iffd_plan* h);
+StiffLaunch plan_stiff_launch(const Plan* P, int axis);
+
+}  // namespace iffd

@@ -508,8 +508,12 @@ template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 static cudaError_t launch_batched_t(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                    long long total_tiles, size_t smem, cudaStream_t st) {
   auto kern = precond_pass_batched<Tc, Tin, Tout, MODE, NDOT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static size_t smem_set = 0;  // attribute is raised only when needed (not inside a graph capture)
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
   if (total_tiles <= 0) return cudaSuccess;
   kern<<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
   return cudaGetLastError();

@@ -361,18 +361,33 @@ static cudaError_t last_p(const StiffLaunch& S, const double* T1, const double* 
 template <int P>
 static cudaError_t batched_p(int stage, const StiffDesc* sys, const long long* tile_prefix, int nsys,
                              long long total_tiles, size_t smem, cudaStream_t st) {
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   if (stage == SS_FIRST) {
-    e = cudaFuncSetAttribute(stiff_batched<P, SS_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess || total_tiles <= 0) return e;
+    static size_t set_SS_FIRST = 0;
+    if (smem > set_SS_FIRST) {
+      e = cudaFuncSetAttribute(stiff_batched<P, SS_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set_SS_FIRST = smem;
+    }
+    if (total_tiles <= 0) return cudaSuccess;
     stiff_batched<P, SS_FIRST><<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
   } else if (stage == SS_MID) {
-    e = cudaFuncSetAttribute(stiff_batched<P, SS_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess || total_tiles <= 0) return e;
+    static size_t set_SS_MID = 0;
+    if (smem > set_SS_MID) {
+      e = cudaFuncSetAttribute(stiff_batched<P, SS_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set_SS_MID = smem;
+    }
+    if (total_tiles <= 0) return cudaSuccess;
     stiff_batched<P, SS_MID><<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
   } else {
-    e = cudaFuncSetAttribute(stiff_batched<P, SS_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess || total_tiles <= 0) return e;
+    static size_t set_SS_LAST = 0;
+    if (smem > set_SS_LAST) {
+      e = cudaFuncSetAttribute(stiff_batched<P, SS_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set_SS_LAST = smem;
+    }
+    if (total_tiles <= 0) return cudaSuccess;
     stiff_batched<P, SS_LAST><<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
   }
   return cudaGetLastError();
