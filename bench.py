@@ -33,6 +33,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -238,6 +240,107 @@ def workload_config(w):
             "l2": "no flush: 137 MB vectors, ~1 GB working set > 126 MB L2"}
 
 
+def _timed(fn, reps: int, warm: int):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, out
+
+
+def run_other_workload(args, rank: int, world: int, local: int) -> int:
+    """Secondary workloads (one JSON line each, same metric); not the headline."""
+    import torch
+
+    from paper_2512_20269_gb300 import IFFDEngine, IFFDPlan, _lib, inputs
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2512_20269_gb300 import build
+        build.build()
+    torch.cuda.set_device(local)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
+    if args.workload in ("square", "varcoef"):
+        w = inputs.SQUARE_N64_P3 if args.workload == "square" else inputs.CUBE_N384_P8
+        coef = "const" if args.workload == "square" else "sin"
+        f = torch.from_numpy(inputs.workload_rhs(w)).cuda()
+        res = {}
+        for prec in ("fp64", "fp32"):
+            plan = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=False)
+            u = plan.empty()
+            ms, (_, info) = _timed(lambda: plan.pcg_solve(f, u), args.steps, max(args.warmup, 1))
+            chk = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=True)
+            _, ic = chk.pcg_solve(f)
+            res[prec] = {"value": w.N / (ms / 1e3), "ms_per_solve": ms, "iters": info["iters"],
+                         "true_rel_res": ic["true_rel_res"]}
+            del plan, chk
+        line.update({"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_solve"], "dtype": "f64",
+                     "config": {"workload": w.name, "d": w.d, "n": w.n, "p": w.p, "N": w.N,
+                                "coefficient": "1 + 0.5 prod sin(2 pi x_k)" if coef == "sin" else "1",
+                                "rhs": f"{w.dist} seed {w.seed}"},
+                     "variants": {"fp32_transform": res["fp32"]}, "fp64": res["fp64"]})
+    elif args.workload == "batched":
+        probs = inputs.batched_problems()
+        systems = []
+        for k, (d, n, p, nrhs) in enumerate(probs):
+            for j in range(nrhs):
+                N = (n + p - 2) ** d
+                systems.append((d, n, p, inputs.device_rhs(N, 3_000_003 * (k + 1) + j)))
+        total = sum(f.numel() for *_, f in systems)
+        budget = 64 << 30
+        outs = [torch.empty_like(f) for *_, f in systems]
+
+        eng = IFFDEngine(budget, precision="fp32")
+
+        def solve_all():
+            k0 = eng.stats()["kernel_launches"]
+            for (d, n, p, f), u in zip(systems, outs):
+                assert eng.submit(d, n, p, f, u) is not None
+            done = eng.run_to_completion(iterations_per_step=4)
+            return done, eng.stats()["kernel_launches"] - k0
+
+        for _ in range(max(args.warmup, 1)):
+            solve_all()  # the first call also builds and caches every (n, p) plan
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            done, kl = solve_all()
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / reps
+        eng.close()
+        iters = [info["iters"] for _, info in done]
+        line.update({"value": total / sec, "ms_per_step": sec * 1e3, "dtype": "f64",
+                     "config": {"workload": "batched_512_cubes", "problems": len(probs), "systems": len(systems),
+                                "dofs": int(total), "n": list(inputs.BATCH_N), "p": list(inputs.BATCH_P),
+                                "precond": "IFFD, FP32 transforms", "pcg": "fp64", "seed": 3},
+                     "iters_min_max_mean": [min(iters), max(iters), float(np.mean(iters))],
+                     "gpu_launches": kl,
+                     "timing": "wall clock around submit + engine steps to completion; plans cached, arena "
+                               "allocated once (setup excluded)"})
+    else:
+        from paper_2512_20269_gb300.serving import Server
+        reqs = inputs.serving_requests()
+        cap = args.serve_cap_dofs if args.serve_cap_dofs > 0 else None
+        srv = Server(budget_bytes=150 * (1 << 30), precision="fp32", iterations_per_step=2, max_inflight_dofs=cap)
+        st = srv.run(reqs, max_wall_s=args.serve_seconds)
+        line.update({"value": st["dof_per_s"], "ms_per_step": None, "dtype": "f64",
+                     "config": {"workload": "serving_poisson_2000rps", "rate_rps": 2000, "arrival_window_s": 60,
+                                "run_wall_s": args.serve_seconds, "budget_bytes": 150 * (1 << 30),
+                                "precond": "IFFD, FP32 transforms", "seed": 4, "max_inflight_dofs": cap},
+                     "serving": st})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -246,12 +349,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", default="cube", choices=["cube", "square", "varcoef", "batched", "serving"],
+                    help="cube (default, the headline line): 258^3 p=4; square: 65^2 p=3; varcoef: 390^3 p=8 "
+                         "variable coefficient; batched: 512 uneven 3D problems; serving: Poisson request stream")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-cap-dofs", type=int, default=0,
+                    help="serving: cap on the DoFs in flight (0 = HBM budget only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "cube":
+        return run_other_workload(args, rank, world, local)
 
     import numpy as np
     import torch

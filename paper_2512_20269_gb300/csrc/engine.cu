@@ -491,6 +491,11 @@ int build_iteration(Engine* E) {
     const int* PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? P.PPf : P.PPd;
     it.frz.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0[0])});
   }
+  // A system's three sweeps must run in stage order. Groups are created in the
+  // order systems are met (a 2D system creates no MID group), so order them by
+  // stage: every FIRST launch, then every MID, then every LAST.
+  std::stable_sort(it.stiff.begin(), it.stiff.end(),
+                   [](const StiffLaunchB& a, const StiffLaunchB& b) { return a.stage < b.stage; });
   build_precond(sys, flex ? 2 : 1, flex, &it.pc);
   Staging sg;
   for (auto& l : it.stiff) stage_pass(sg, l);

@@ -61,3 +61,60 @@ def rhs(shape, dist: str = "normal", seed: int = 0) -> np.ndarray:
 
 def workload_rhs(w: Workload) -> np.ndarray:
     return rhs(w.shape, w.dist, w.seed)
+
+
+# ---------------------------------------------------------------- batched
+BATCH_N = (16, 24, 32, 48, 64, 96, 128)
+BATCH_P = (2, 3, 4, 5, 6)
+
+
+def batched_problems(count: int = 512, seed: int = 3):
+    """512 independent 3D Dirichlet problems: n uniform in BATCH_N, p uniform in
+    BATCH_P (seed 3); one right-hand side each, eight for the n = 64 problems.
+    Returns [(d, n, p, nrhs), ...]."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(BATCH_N, count)
+    ps = rng.choice(BATCH_P, count)
+    return [(3, int(n), int(p), 8 if int(n) == 64 else 1) for n, p in zip(ns, ps)]
+
+
+def device_rhs(N: int, seed: int, dist: str = "normal"):
+    """Seeded right-hand side generated directly on the current CUDA device
+    (torch generator), for workloads too large to draw on the host."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    if dist == "normal":
+        return torch.randn(N, generator=g, dtype=torch.float64, device="cuda")
+    return torch.rand(N, generator=g, dtype=torch.float64, device="cuda") * 2.0 - 1.0
+
+
+# ---------------------------------------------------------------- serving
+@dataclass(frozen=True)
+class Request:
+    index: int
+    t: float  # arrival time (s)
+    d: int
+    n: int
+    p: int
+
+    @property
+    def N(self) -> int:
+        return (self.n + self.p - 2) ** self.d
+
+
+def serving_requests(rate: float = 2000.0, duration: float = 60.0, seed: int = 4):
+    """Poisson arrivals at `rate` req/s over `duration` s (seed 4). Each request
+    is 2D or 3D with equal probability; n uniform in 128..2048 (2D) or 32..256
+    (3D); p uniform in 2..8."""
+    rng = np.random.default_rng(seed)
+    out, t, k = [], 0.0, 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            return out
+        d = int(rng.integers(2, 4))
+        n = int(rng.integers(128, 2049)) if d == 2 else int(rng.integers(32, 257))
+        p = int(rng.integers(2, 9))
+        out.append(Request(k, t, d, n, p))
+        k += 1

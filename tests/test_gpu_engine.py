@@ -13,7 +13,10 @@ from gpu_common import oracle_stiffness, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-MIX = [(3, 16, 2), (3, 24, 3), (3, 32, 4), (3, 16, 5), (3, 24, 6), (2, 64, 3), (3, 48, 4), (2, 40, 2)]
+# A 2D system comes before 3D systems of the same degree (p = 4, 7): the 2D one
+# has no middle sweep, so this checks that every system's sweeps run in order.
+MIX = [(2, 30, 4), (3, 16, 2), (3, 24, 3), (3, 32, 4), (3, 16, 5), (3, 24, 6), (2, 64, 3), (3, 48, 4), (2, 40, 2),
+       (2, 33, 7), (3, 15, 7)]
 
 
 def _alone(torch, d, n, p, f, precision):
