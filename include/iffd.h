@@ -102,7 +102,7 @@ int iffd_default_options(iffd_options* opt);
  * device. dirichlet[2k], dirichlet[2k+1] flag Dirichlet data at x_k = 0 / 1
  * (must be 1, 1). opt may be NULL (defaults). stream: see conventions.
  * Errors: INVALID_ARG, UNSUPPORTED (n <= p, p > 16, non-{0,1} Dirichlet set,
- * FFT length with a prime factor above 13), SINGULAR, CUDA. *out is set only
+ * transform too large for shared memory), SINGULAR, CUDA. *out is set only
  * on success; release it with iffd_destroy. */
 int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
                iffd_handle* out);
@@ -133,6 +133,16 @@ int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double*
  * buffers). Same layouts and errors as iffd_get_1d / iffd_setup. */
 int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
                    double* K_band, double* lam, double* dtilde, double* VL, double* W);
+
+/* Host-only: how the preconditioner passes of one direction carry its DST
+ * (Table 1: DST-I for odd p, DST-II/III for even p, D = {0,1}) for the given
+ * precision (IFFD_PREC_FP64 or IFFD_PREC_FP32_TRANSFORM). *L receives the
+ * length of the complex DFT (two pencils per sequence: n_reg for DST-II/III,
+ * 2 (n_reg + 1) for DST-I); *F the length of the FFT that runs: F == L for the
+ * direct mixed-radix FFT, F > L (5-smooth, F >= 2L - 1) when the DFT runs as
+ * Bluestein's chirp convolution because L has large prime factors; *pencils
+ * (may be NULL) the pencils per tile. Same errors as iffd_setup. Needs no GPU. */
+int iffd_host_transform(int n, int p, const int* dirichlet, int precision, int* L, int* F, int* pencils);
 
 /* z = P^{-1} r: the IFFD preconditioner of eq. "preconditioner" (or the exact
  * FD of eq. "exact_diagonalization", or the identity, per opt->precond).

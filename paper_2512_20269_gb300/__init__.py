@@ -33,6 +33,17 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def host_transform(n: int, p: int, precision: str = "fp64", dirichlet=(1, 1)) -> dict:
+    """How the transform passes of one direction run (library's host planner,
+    no GPU): DFT length L, FFT length F (F > L: Bluestein), pencils per tile."""
+    lib = _lib.load()
+    dir_arr = (ctypes.c_int * 2)(*dirichlet)
+    L, F, pp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib.iffd_host_transform(n, p, dir_arr, PRECISION[precision], ctypes.byref(L), ctypes.byref(F),
+                                  ctypes.byref(pp)), "iffd_host_transform")
+    return {"L": L.value, "F": F.value, "bluestein": F.value > L.value, "pencils": pp.value}
+
+
 def host_axis(n: int, p: int, dirichlet=(1, 1)) -> dict:
     """1D tables of one direction computed by the library's host setup (no GPU)."""
     lib = _lib.load()

@@ -50,6 +50,8 @@ SIGNATURES = [
     ("iffd_get_1d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [c_double_p] * 6),
     ("iffd_host_axis", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]
      + [c_double_p] * 6),
+    ("iffd_host_transform", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, c_int_p,
+                                           c_int_p]),
     ("iffd_apply_preconditioner", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
     ("iffd_apply_stiffness", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

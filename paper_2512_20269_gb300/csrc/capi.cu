@@ -56,29 +56,34 @@ static std::vector<T> cast_vec(const std::vector<double>& v) {
 }
 
 struct AxisOffsets {
-  size_t VL, W, lam, post, tw;
+  size_t VL, W, lam, post, tw, chirp, bhat;
 };
 
 static bool register_radix(int r) { return r == 8 || r == 4 || r == 2 || r == 3 || r == 5; }
 
-// Twiddles of every Stockham stage. Register-butterfly stages store
-// exp(-2 pi i q k / (Ns r)) for q = 1..r-1, k < Ns; direct-DFT stages store
-// exp(-2 pi i s / (Ns r)) for s < Ns r.
-static std::string fft_tables(const Axis1D& A, int* L, std::vector<int>* radices, std::vector<double>* tw,
-                              std::vector<int>* twoff) {
-  *L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
-  if (!fft_factor(*L, radices)) return "bad FFT length " + std::to_string(*L);
-  if ((int)radices->size() > kMaxStages) return "too many FFT stages";
-  tw->clear();
-  twoff->clear();
+// Stages and twiddles of one Stockham FFT of length len. Register-butterfly
+// stages store exp(-2 pi i q k / (Ns r)) for q = 1..r-1, k < Ns; direct-DFT
+// stages store exp(-2 pi i s / (Ns r)) for s < Ns r.
+struct FftPlan {
+  int len = 0;
+  std::vector<int> rad, twoff;
+  std::vector<double> tw;
+};
+
+static std::string fft_plan(int len, FftPlan* f) {
+  f->len = len;
+  if (!fft_factor(len, &f->rad)) return "bad FFT length " + std::to_string(len);
+  if ((int)f->rad.size() > kMaxStages) return "too many FFT stages";
+  f->tw.clear();
+  f->twoff.clear();
   long long Ns = 1;
-  for (int r : *radices) {
-    twoff->push_back((int)(tw->size() / 2));
+  for (int r : f->rad) {
+    f->twoff.push_back((int)(f->tw.size() / 2));
     const long long den = Ns * r;
     auto push = [&](long long num) {
       const double ang = -2.0 * kPi * (double)(num % den) / (double)den;
-      tw->push_back(std::cos(ang));
-      tw->push_back(std::sin(ang));
+      f->tw.push_back(std::cos(ang));
+      f->tw.push_back(std::sin(ang));
     };
     if (register_radix(r)) {
       for (int q = 1; q < r; ++q)
@@ -89,6 +94,122 @@ static std::string fft_tables(const Axis1D& A, int* L, std::vector<int>* radices
     Ns *= r;
   }
   return "";
+}
+
+// Estimated real flops per element of one FFT stage of radix r: (r-1) twiddle
+// products and the r-point DFT of a register butterfly, or r - 1 complex
+// multiply-adds per output of a direct stage.
+static double stage_cost(int r) {
+  switch (r) {
+    case 2: return 5.0;
+    case 3: return 8.0;
+    case 4: return 8.5;
+    case 5: return 11.6;
+    case 8: return 11.75;
+    default: return 8.0 * (r - 1) + 2.0;
+  }
+}
+
+static double fft_cost(int len) {
+  std::vector<int> rad;
+  fft_factor(len, &rad);
+  double c = 0.0;
+  for (int r : rad) c += stage_cost(r);
+  return c * len;
+}
+
+static bool smooth5(int x) {
+  for (int r : {2, 3, 5})
+    while (x % r == 0) x /= r;
+  return x == 1;
+}
+
+// Bluestein length for a length-L DFT: the cheapest 5-smooth F in [2L-1, 4L],
+// taken when two length-F FFTs and the chirp products cost less than 0.7 of
+// the direct mixed-radix FFT of length L (whose large prime factors run as
+// direct DFT stages). Returns 0 when the direct FFT is kept.
+static int bluestein_length(int L) {
+  if (L < 16) return 0;
+  int best = 0;
+  double best_cost = 0.0;
+  for (int f = 2 * L - 1; f <= 4 * L; ++f) {
+    if (!smooth5(f)) continue;
+    const double c = 2.0 * fft_cost(f) + 7.0 * f + 12.0 * L;
+    if (best == 0 || c < best_cost) { best = f; best_cost = c; }
+  }
+  return (best != 0 && best_cost < 0.7 * fft_cost(L)) ? best : 0;
+}
+
+// Forward DFT of a 5-smooth length in double precision (host; Bluestein
+// kernel spectrum only), recursive decimation in time with twiddles
+// exp(-2 pi i e / n) from exactly reduced integer angles.
+static void host_dft(std::vector<double>& re, std::vector<double>& im) {
+  const int n = (int)re.size();
+  std::vector<double> c(n), sn(n);
+  for (int e = 0; e < n; ++e) {
+    const double ang = -2.0 * kPi * (double)e / (double)n;
+    c[e] = std::cos(ang);
+    sn[e] = std::sin(ang);
+  }
+  // rec(len, stride, off): DFT of x[off + j * stride], j < len, into out
+  std::vector<double> ore(n), oim(n);
+  struct Rec {
+    const std::vector<double>& c;
+    const std::vector<double>& sn;
+    int n;
+    void run(const double* xr, const double* xi, int len, int stride, double* yr, double* yi) const {
+      if (len == 1) { yr[0] = xr[0]; yi[0] = xi[0]; return; }
+      int r = 2;
+      while (len % r) ++r;
+      const int l2 = len / r;
+      std::vector<double> tr(len), ti(len);
+      for (int q = 0; q < r; ++q) run(xr + (size_t)q * stride, xi + (size_t)q * stride, l2, stride * r,
+                                      tr.data() + (size_t)q * l2, ti.data() + (size_t)q * l2);
+      const int step = n / len;  // exp(-2 pi i e / len) = table[e * step]
+      for (int t = 0; t < r; ++t)
+        for (int k = 0; k < l2; ++k) {
+          const int kk = k + t * l2;
+          double ar = 0.0, ai = 0.0;
+          for (int q = 0; q < r; ++q) {
+            const long long e = ((long long)q * kk) % len;
+            const double wr = c[(size_t)(e * step)], wi = sn[(size_t)(e * step)];
+            const double vr = tr[(size_t)q * l2 + k], vi = ti[(size_t)q * l2 + k];
+            ar += vr * wr - vi * wi;
+            ai += vr * wi + vi * wr;
+          }
+          yr[kk] = ar;
+          yi[kk] = ai;
+        }
+    }
+  } rec{c, sn, n};
+  rec.run(re.data(), im.data(), n, 1, ore.data(), oim.data());
+  re.swap(ore);
+  im.swap(oim);
+}
+
+// Chirp c_j = exp(i pi j^2 / L) (j < L) and bhat = DFT_F(b) / F for the
+// Bluestein kernel b_t = c_t (t < L), b_{F-t} = c_t (0 < t < L), 0 otherwise.
+static void bluestein_tables(int L, int F, std::vector<double>* chirp, std::vector<double>* bhat) {
+  chirp->assign(2 * (size_t)L, 0.0);
+  std::vector<double> br(F, 0.0), bi(F, 0.0);
+  for (int j = 0; j < L; ++j) {
+    const long long e = ((long long)j * j) % (2LL * L);  // exact reduction of j^2 mod 2L
+    const double ang = kPi * (double)e / (double)L;
+    (*chirp)[2 * j] = std::cos(ang);
+    (*chirp)[2 * j + 1] = std::sin(ang);
+    br[j] = std::cos(ang);
+    bi[j] = std::sin(ang);
+    if (j > 0) {
+      br[F - j] = br[j];
+      bi[F - j] = bi[j];
+    }
+  }
+  host_dft(br, bi);
+  bhat->resize(2 * (size_t)F);
+  for (int k = 0; k < F; ++k) {
+    (*bhat)[2 * k] = br[k] / F;
+    (*bhat)[2 * k + 1] = bi[k] / F;
+  }
 }
 
 static std::vector<double> post_table(const Axis1D& A) {
@@ -110,9 +231,11 @@ static std::vector<double> post_table(const Axis1D& A) {
   return post;
 }
 
+// Fills one precision's tables. With F > 0 the length-L DFT runs as Bluestein
+// over the length-F FFT `fp` (twiddles at o.tw), else fp is the length-L FFT.
 template <typename T>
-static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, const std::vector<int>& rad,
-                         const std::vector<int>& twoff, const char* base, const AxisOffsets& o) {
+static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const FftPlan& fp, const char* base,
+                         const AxisOffsets& o, size_t tw_off) {
   t->m = A.m;
   t->n_reg = A.n_reg;
   t->n_out = A.n_out;
@@ -124,25 +247,46 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, const std::vecto
   t->whi = A.whi;
   t->kind = A.kind;
   t->L = L;
-  t->nst = (int)rad.size();
+  t->F = (F > 0) ? F : L;
+  t->blu = (F > 0) ? 1 : 0;
+  t->nst = (int)fp.rad.size();
   for (int s = 0; s < kMaxStages; ++s) {
-    t->radix[s] = s < t->nst ? rad[s] : 1;
-    t->twoff[s] = s < t->nst ? twoff[s] : 0;
+    t->radix[s] = s < t->nst ? fp.rad[s] : 1;
+    t->twoff[s] = s < t->nst ? fp.twoff[s] : 0;
   }
   t->VL = reinterpret_cast<const T*>(base + o.VL);
   t->W = reinterpret_cast<const T*>(base + o.W);
   t->lam = reinterpret_cast<const T*>(base + o.lam);
   t->post = reinterpret_cast<const T*>(base + o.post);
-  t->tw = reinterpret_cast<const T*>(base + o.tw);
+  t->tw = reinterpret_cast<const T*>(base + tw_off);
+  t->chirp = reinterpret_cast<const T*>(base + o.chirp);
+  t->bhat = reinterpret_cast<const T*>(base + o.bhat);
 }
 
-static int pick_pp(int m, int L, size_t elt, int* PP, int* ldt) {
+// Pencils per tile of a transform pass whose FFT has length F.
+static int pick_pp(int m, int F, size_t elt, int* PP, int* ldt) {
   *ldt = m | 1;
   int pp = 16;
-  while (pp > 2 && precond_smem_bytes(pp, *ldt, L, elt) > 110 * 1024) pp /= 2;
-  if (precond_smem_bytes(pp, *ldt, L, elt) > 220 * 1024) return 0;
+  while (pp > 2 && precond_smem_bytes(pp, *ldt, F, elt) > 110 * 1024) pp /= 2;
+  if (precond_smem_bytes(pp, *ldt, F, elt) > 220 * 1024) return 0;
   *PP = pp;
   return 1;
+}
+
+// Transform of one direction for one precision (element size elt): the DFT
+// length L, the FFT length F actually run (F > L: Bluestein) and the tile.
+// Bluestein is used when bluestein_length() picks it and its two length-F
+// buffers fit in shared memory; otherwise the direct length-L FFT. Returns 0
+// if neither fits.
+static int choose_transform(const Axis1D& A, size_t elt, int* L, int* F, int* PP, int* ldt) {
+  *L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
+  const int fb = bluestein_length(*L);
+  if (fb > 0 && pick_pp(A.m, fb, elt, PP, ldt)) {
+    *F = fb;
+    return 1;
+  }
+  *F = *L;
+  return pick_pp(A.m, *L, elt, PP, ldt);
 }
 
 static int build_plan(Plan* P, cudaStream_t stream) {
@@ -150,26 +294,43 @@ static int build_plan(Plan* P, cudaStream_t stream) {
   struct PerAxis {
     AxisOffsets od, of;
     size_t Mb, Kb, Mt, Kt, QT, Q, lamQ, Msb, Ksb;
-    int L;
-    std::vector<int> rad, twoff;
+    int L, F;              // DFT length; Bluestein FFT length (0: direct)
+    FftPlan direct, blu;   // length-L FFT; length-F FFT
+    size_t twB_d, twB_f;   // twiddles of the length-F FFT (FP64, FP32)
     int ilo, ihi;
   } pa[3];
   for (int a = 0; a < P->d; ++a) {
     const Axis1D& A = P->host[a];
-    std::vector<double> tw;
-    std::string err = fft_tables(A, &pa[a].L, &pa[a].rad, &tw, &pa[a].twoff);
+    // the DST of the regular part is carried by a complex DFT of length L
+    // (two pencils per sequence; Makhoul order for DST-II/III, odd extension
+    // for DST-I); lengths with large prime factors may run as Bluestein
+    pa[a].L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
+    std::string err = fft_plan(pa[a].L, &pa[a].direct);
     if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+    pa[a].F = bluestein_length(pa[a].L);
+    std::vector<double> chirp, bhat;
+    if (pa[a].F > 0) {
+      err = fft_plan(pa[a].F, &pa[a].blu);
+      if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+      bluestein_tables(pa[a].L, pa[a].F, &chirp, &bhat);
+    }
     const std::vector<double> post = post_table(A);
     pa[a].od.VL = tb.add_vec(A.VL);
     pa[a].od.W = tb.add_vec(A.W);
     pa[a].od.lam = tb.add_vec(A.lam);
     pa[a].od.post = tb.add_vec(post);
-    pa[a].od.tw = tb.add_vec(tw);
+    pa[a].od.tw = tb.add_vec(pa[a].direct.tw);
+    pa[a].od.chirp = tb.add_vec(chirp);
+    pa[a].od.bhat = tb.add_vec(bhat);
+    pa[a].twB_d = tb.add_vec(pa[a].blu.tw);
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
     pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
     pa[a].of.lam = tb.add_vec(cast_vec<float>(A.lam));
     pa[a].of.post = tb.add_vec(cast_vec<float>(post));
-    pa[a].of.tw = tb.add_vec(cast_vec<float>(tw));
+    pa[a].of.tw = tb.add_vec(cast_vec<float>(pa[a].direct.tw));
+    pa[a].of.chirp = tb.add_vec(cast_vec<float>(chirp));
+    pa[a].of.bhat = tb.add_vec(cast_vec<float>(bhat));
+    pa[a].twB_f = tb.add_vec(cast_vec<float>(pa[a].blu.tw));
     // stiffness band tables; interior rows 2p-1 .. m-2p are symmetric Toeplitz
     const int p = A.p, m = A.m, bw = 2 * p + 1;
     pa[a].Mb = tb.add_vec(A.Mband);
@@ -227,11 +388,16 @@ static int build_plan(Plan* P, cudaStream_t stream) {
   int max_parts = vec_grid(N);
   for (int a = 0; a < P->d; ++a) {
     const Axis1D& A = P->host[a];
-    fill_axistab(&P->axd[a], A, pa[a].L, pa[a].rad, pa[a].twoff, base, pa[a].od);
-    fill_axistab(&P->axf[a], A, pa[a].L, pa[a].rad, pa[a].twoff, base, pa[a].of);
-    if (!pick_pp(A.m, pa[a].L, sizeof(double), &P->PPd[a], &P->ldtd[a]) ||
-        !pick_pp(A.m, pa[a].L, sizeof(float), &P->PPf[a], &P->ldtf[a]))
+    // per precision: Bluestein (F > L) or the direct length-L FFT
+    int L, F;
+    if (!choose_transform(A, sizeof(double), &L, &F, &P->PPd[a], &P->ldtd[a]))
       return fail(IFFD_ERR_UNSUPPORTED, "transform length too large for shared memory");
+    if (F > L) fill_axistab(&P->axd[a], A, L, F, pa[a].blu, base, pa[a].od, pa[a].twB_d);
+    else fill_axistab(&P->axd[a], A, L, 0, pa[a].direct, base, pa[a].od, pa[a].od.tw);
+    if (!choose_transform(A, sizeof(float), &L, &F, &P->PPf[a], &P->ldtf[a]))
+      return fail(IFFD_ERR_UNSUPPORTED, "transform length too large for shared memory");
+    if (F > L) fill_axistab(&P->axf[a], A, L, F, pa[a].blu, base, pa[a].of, pa[a].twB_f);
+    else fill_axistab(&P->axf[a], A, L, 0, pa[a].direct, base, pa[a].of, pa[a].of.tw);
     BandTab& b = P->bt[a];
     b.m = A.m;
     b.p = A.p;
@@ -665,6 +831,21 @@ int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* 
   cp(dtilde, A.dtilde);
   cp(VL, A.VL);
   cp(W, A.W);
+  return IFFD_OK;
+}
+
+int iffd_host_transform(int n, int p, const int* dirichlet, int precision, int* L, int* F, int* pencils) {
+  g_err.clear();
+  if (!dirichlet || !L || !F) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (precision != IFFD_PREC_FP64 && precision != IFFD_PREC_FP32_TRANSFORM)
+    return fail(IFFD_ERR_INVALID_ARG, "unknown precision");
+  Axis1D A;
+  const std::string err = build_axis(n, p, dirichlet[0] != 0, dirichlet[1] != 0, &A);
+  if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+  int PP = 0, ldt = 0;
+  if (!choose_transform(A, precision == IFFD_PREC_FP64 ? sizeof(double) : sizeof(float), L, F, &PP, &ldt))
+    return fail(IFFD_ERR_UNSUPPORTED, "transform length too large for shared memory");
+  if (pencils) *pencils = PP;
   return IFFD_OK;
 }
 

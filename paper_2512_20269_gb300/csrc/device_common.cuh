@@ -43,14 +43,19 @@ struct Dims {
 template <typename T>
 struct AxisTab {
   int m, n_reg, n_out, p, o, nL, rowsL, wlo, whi, kind;
-  int L, nst;
-  int radix[kMaxStages];
+  // L: length of the complex DFT that carries the DST (two pencils per
+  // sequence). F: length of the FFT actually run, = L, or, when blu is set, the
+  // 5-smooth Bluestein length F >= 2L - 1; shared-memory sequences have stride F.
+  int L, F, blu, nst;
+  int radix[kMaxStages];  // stages of the length-F FFT
   int twoff[kMaxStages];
-  const T* VL;    // rowsL * nL (row-major); the right block is its mirror image
-  const T* W;     // m * n_out (row-major) = V_out Q_out
-  const T* lam;   // m: Lambda_reg then Lambda_out
-  const T* post;  // DST-II/III: 4 per k = 0..N/2;  DST-I: n_reg values 1/(2 D~)
-  const T* tw;    // complex FFT twiddles (interleaved), per stage offsets twoff
+  const T* VL;     // rowsL * nL (row-major); the right block is its mirror image
+  const T* W;      // m * n_out (row-major) = V_out Q_out
+  const T* lam;    // m: Lambda_reg then Lambda_out
+  const T* post;   // DST-II/III: 4 per k = 0..N/2;  DST-I: n_reg values 1/(2 D~)
+  const T* tw;     // complex FFT twiddles (interleaved), per stage offsets twoff
+  const T* chirp;  // Bluestein: c_j = exp(i pi j^2 / L), j < L (interleaved)
+  const T* bhat;   // Bluestein: DFT_F of the chirp kernel, divided by F
 };
 
 // Pencil tiles. The pencils along direction `axis` are numbered q = 0..Q-1:

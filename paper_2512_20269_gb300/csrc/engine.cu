@@ -1,18 +1,21 @@
 // Batched solves with continuous batching (iffd_engine_*).
 //
-// Many independent IFFD-PCG solves advance together: each phase of a PCG
-// iteration (stiffness sweeps, reductions, vector update, transform passes) is
-// one batched launch covering the tiles of every active system (the stiffness
-// sweeps are grouped by degree). A system's kernels, tile decomposition and
-// reduction order are exactly those of the single-system path, so its result
-// does not depend on which other systems share the launches.
+// Many independent IFFD-PCG solves advance together. The active systems are
+// split into lanes by degree and by the shared memory of their transform
+// passes; within a lane each phase of a PCG iteration (stiffness sweeps,
+// reductions, vector update, transform passes) is one batched launch covering
+// the tiles of every system of the lane, and the lanes run concurrently on
+// separate streams. A system's kernels, tile decomposition and reduction order
+// are exactly those of the single-system path, so its result does not depend
+// on which other systems share the launches.
 //
 // Requests are admitted while their workspace fits the engine's device arena
 // (the budget); an admitted request is initialised at the next step and then
 // iterates with the others; finished systems are retired after each step and
 // their workspace returns to the arena, so later requests can join while
-// earlier ones are still iterating. The per-iteration launch sequence is
-// captured into a CUDA graph and replayed while the set of systems is unchanged.
+// earlier ones are still iterating. The per-iteration launch sequence of all
+// lanes (forked from and joined to the engine stream) is captured into one CUDA
+// graph and replayed while the set of systems is unchanged.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,6 +36,8 @@ namespace iffd {
 namespace {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr size_t kLaneStreams = 8;  // streams the lanes of one iteration graph run on
 
 // First-fit sub-allocator over one device allocation.
 struct Arena {
@@ -144,10 +149,18 @@ struct Engine {
   // captured iteration graph, its kernel count and the membership it was built for
   cudaGraphExec_t graph = nullptr;
   long long graph_kernels = 0;
+  int graph_lanes = 0;
   std::vector<long long> graph_ids;
+  // lane streams (forked from and joined to `st` inside the captured graph)
+  std::vector<cudaStream_t> lane_st;
+  std::vector<cudaEvent_t> lane_ev;
+  cudaEvent_t fork_ev = nullptr;
   ~Engine() {
     if (st) cudaStreamSynchronize(st);
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto e : lane_ev) cudaEventDestroy(e);
+    for (auto s : lane_st) cudaStreamDestroy(s);
+    if (fork_ev) cudaEventDestroy(fork_ev);
     if (ev) cudaEventDestroy(ev);
     if (st) cudaStreamDestroy(st);
     for (auto& kv : plans) plan_release(kv.second);
@@ -261,7 +274,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
           D.partial = vpart(*s);
         }
         seq->d64[k].add(D, precond_tiles(P.dims, a, P.PPd[a]),
-                        precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].L, sizeof(double)));
+                        precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].F, sizeof(double)));
       }
     }
     return;
@@ -287,7 +300,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.in = vr(*s);
       D.out = vtf(*s);
       seq->f_first.add(D, precond_tiles(P.dims, 0, P.PPf[0]),
-                       precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].L, sizeof(float)));
+                       precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].F, sizeof(float)));
     }
     const int axes[3] = {1, d - 1, 1};
     for (int k = 0; k < 3; ++k) {
@@ -297,7 +310,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.in = vtf(*s);
       D.out = vtf(*s);
       seq->f_mid[k].add(D, precond_tiles(P.dims, a, P.PPf[a]),
-                        precond_smem_bytes(P.PPf[a], P.ldtf[a], P.axf[a].L, sizeof(float)));
+                        precond_smem_bytes(P.PPf[a], P.ldtf[a], P.axf[a].F, sizeof(float)));
     }
     {
       PassDesc<float, float, double> D{};
@@ -310,7 +323,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.dot1 = use_q ? vq(*s) : nullptr;
       D.partial = vpart(*s);
       seq->f_last.add(D, precond_tiles(P.dims, 0, P.PPf[0]),
-                      precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].L, sizeof(float)));
+                      precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].F, sizeof(float)));
     }
   }
 }
@@ -332,32 +345,32 @@ void stage_precond(Staging& sg, PrecondSeq& q) {
 }
 
 template <typename Tc, typename Tin, typename Tout>
-int run_pass(Engine* E, char* base, PassLaunchB<Tc, Tin, Tout>& l) {
+int run_pass(Engine* E, char* base, PassLaunchB<Tc, Tin, Tout>& l, cudaStream_t st) {
   if (l.desc.empty()) return IFFD_OK;
   IFFD_CUDA((launch_pass_batched<Tc, Tin, Tout>(at<PassDesc<Tc, Tin, Tout>>(base, l.off_desc),
                                                 at<long long>(base, l.off_prefix), (int)l.desc.size(),
-                                                l.prefix.back(), l.smem, l.mode, l.ndot, E->st)));
+                                                l.prefix.back(), l.smem, l.mode, l.ndot, st)));
   if (l.prefix.back() > 0) ++E->launches;
   return IFFD_OK;
 }
 
-int run_precond_seq(Engine* E, char* base, PrecondSeq& q) {
+int run_precond_seq(Engine* E, char* base, PrecondSeq& q, cudaStream_t st) {
   int rc;
   if (!q.fp32) {
     for (auto& l : q.d64)
-      if ((rc = run_pass(E, base, l))) return rc;
+      if ((rc = run_pass(E, base, l, st))) return rc;
     return IFFD_OK;
   }
-  if ((rc = run_pass(E, base, q.f_first))) return rc;
+  if ((rc = run_pass(E, base, q.f_first, st))) return rc;
   for (auto& l : q.f_mid)
-    if ((rc = run_pass(E, base, l))) return rc;
-  return run_pass(E, base, q.f_last);
+    if ((rc = run_pass(E, base, l, st))) return rc;
+  return run_pass(E, base, q.f_last, st);
 }
 
-int run_fin(Engine* E, char* base, FinLaunchB& f) {
+int run_fin(Engine* E, char* base, FinLaunchB& f, cudaStream_t st) {
   if (f.desc.empty()) return IFFD_OK;
   IFFD_CUDA(launch_finalize_batched(at<FinDesc>(base, f.off), (int)f.desc.size(), f.phase,
-                                    E->opt.rtol * E->opt.rtol, E->opt.maxit, E->st));
+                                    E->opt.rtol * E->opt.rtol, E->opt.maxit, st));
   ++E->launches;
   return IFFD_OK;
 }
@@ -399,9 +412,9 @@ int run_init(Engine* E, const std::vector<const Sys*>& sys) {
                                     (int)vl.desc.size(), vl.prefix.back(), E->st));
   ++E->launches;
   int rc;
-  if ((rc = run_fin(E, base, fff))) return rc;
-  if ((rc = run_precond_seq(E, base, pc))) return rc;
-  if ((rc = run_fin(E, base, frz0))) return rc;
+  if ((rc = run_fin(E, base, fff, E->st))) return rc;
+  if ((rc = run_precond_seq(E, base, pc, E->st))) return rc;
+  if ((rc = run_fin(E, base, frz0, E->st))) return rc;
   // the host copy of the staging must outlive the asynchronous upload
   IFFD_CUDA(cudaStreamSynchronize(E->st));
   return IFFD_OK;
@@ -409,33 +422,32 @@ int run_init(Engine* E, const std::vector<const Sys*>& sys) {
 
 // ---- one PCG iteration of all iterating systems, captured into a graph
 struct IterSeq {
-  std::vector<StiffLaunchB> stiff;  // grouped by (stage, p)
+  std::vector<StiffLaunchB> stiff;  // grouped by (stage, p), in stage order
   FinLaunchB fpq, frr, frz;
   VecLaunchB upd;
   PrecondSeq pc;
 };
 
-int enqueue_iteration(Engine* E, char* base, IterSeq& it) {
+int enqueue_iteration(Engine* E, char* base, IterSeq& it, cudaStream_t st) {
   int rc;
   for (auto& l : it.stiff) {
     if (l.desc.empty()) continue;
     IFFD_CUDA(launch_stiff_batched(l.p, l.stage, at<StiffDesc>(base, l.off_desc), at<long long>(base, l.off_prefix),
-                                   (int)l.desc.size(), l.prefix.back(), l.smem, E->st));
+                                   (int)l.desc.size(), l.prefix.back(), l.smem, st));
     ++E->launches;
   }
-  if ((rc = run_fin(E, base, it.fpq))) return rc;
+  if ((rc = run_fin(E, base, it.fpq, st))) return rc;
   IFFD_CUDA(launch_pcg_update_batched(at<VecDesc>(base, it.upd.off_desc), at<long long>(base, it.upd.off_prefix),
-                                      (int)it.upd.desc.size(), it.upd.prefix.back(), E->st));
+                                      (int)it.upd.desc.size(), it.upd.prefix.back(), st));
   ++E->launches;
-  if ((rc = run_fin(E, base, it.frr))) return rc;
-  if ((rc = run_precond_seq(E, base, it.pc))) return rc;
-  return run_fin(E, base, it.frz);
+  if ((rc = run_fin(E, base, it.frr, st))) return rc;
+  if ((rc = run_precond_seq(E, base, it.pc, st))) return rc;
+  return run_fin(E, base, it.frz, st);
 }
 
-int build_iteration(Engine* E) {
-  std::vector<const Sys*> sys;
-  for (auto& s : E->active) sys.push_back(&s);
-  IterSeq it;
+// The launch sequence of one iteration for the systems of one lane.
+void build_lane(const Engine* E, const std::vector<const Sys*>& sys, IterSeq* out) {
+  IterSeq& it = *out;
   std::map<std::pair<int, int>, size_t> group;  // (stage, p) -> index
   const bool flex = E->opt.flexible || E->opt.precision == IFFD_PREC_FP32_TRANSFORM;
   it.fpq.phase = FP_PQ;
@@ -497,51 +509,98 @@ int build_iteration(Engine* E) {
   std::stable_sort(it.stiff.begin(), it.stiff.end(),
                    [](const StiffLaunchB& a, const StiffLaunchB& b) { return a.stage < b.stage; });
   build_precond(sys, flex ? 2 : 1, flex, &it.pc);
+}
+
+// Lane of a system: its degree and the occupancy class of its largest
+// transform pass (CTAs of 227 KB / shared memory per SM, capped at 4), so that
+// every batched launch of a lane sizes shared memory for systems alike.
+std::pair<int, int> lane_key(const Sys& s) {
+  const Plan& P = s.plan->P;
+  const bool f32 = P.opt.precision == IFFD_PREC_FP32_TRANSFORM;
+  size_t sm = 0;
+  for (int a = 0; a < P.d; ++a)
+    sm = std::max(sm, f32 ? precond_smem_bytes(P.PPf[a], P.ldtf[a], P.axf[a].F, sizeof(float))
+                          : precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].F, sizeof(double)));
+  const int occ = (int)std::min<size_t>(4, std::max<size_t>(1, (227 * 1024) / std::max<size_t>(sm, 1)));
+  return {occ, P.p};
+}
+
+int build_iteration(Engine* E) {
+  // partition the iterating systems into lanes; each lane runs its own launch
+  // sequence on one of the engine's lane streams, concurrently with the others
+  std::map<std::pair<int, int>, std::vector<const Sys*>> lanes;
+  for (auto& s : E->active) lanes[lane_key(s)].push_back(&s);
+  std::vector<IterSeq> seqs(lanes.size());
+  {
+    size_t k = 0;
+    for (auto& kv : lanes) build_lane(E, kv.second, &seqs[k++]);
+  }
   Staging sg;
-  for (auto& l : it.stiff) stage_pass(sg, l);
-  it.fpq.off = sg.put(it.fpq.desc);
-  it.frr.off = sg.put(it.frr.desc);
-  it.frz.off = sg.put(it.frz.desc);
-  stage_pass(sg, it.upd);
-  stage_precond(sg, it.pc);
+  for (auto& it : seqs) {
+    for (auto& l : it.stiff) stage_pass(sg, l);
+    it.fpq.off = sg.put(it.fpq.desc);
+    it.frr.off = sg.put(it.frr.desc);
+    it.frz.off = sg.put(it.frz.desc);
+    stage_pass(sg, it.upd);
+    stage_precond(sg, it.pc);
+  }
   IFFD_CUDA(E->diter.reserve(sg.bytes.size()));
   char* base = E->diter.p;
   IFFD_CUDA(cudaMemcpyAsync(base, sg.bytes.data(), sg.bytes.size(), cudaMemcpyHostToDevice, E->st));
   IFFD_CUDA(cudaStreamSynchronize(E->st));
   // raise the shared-memory attributes outside the capture (zero-tile launches)
-  for (auto& l : it.stiff)
-    IFFD_CUDA(launch_stiff_batched(l.p, l.stage, nullptr, nullptr, 0, 0, l.smem, E->st));
-  if (E->graph) {
-    cudaGraphExecDestroy(E->graph);
-    E->graph = nullptr;
-  }
-  // warm the pass-kernel attributes the same way by a capture-free dry pass
-  {
+  for (auto& it : seqs) {
+    for (auto& l : it.stiff)
+      IFFD_CUDA(launch_stiff_batched(l.p, l.stage, nullptr, nullptr, 0, 0, l.smem, E->st));
     IterSeq dry = it;
     for (auto& l : dry.pc.d64) l.prefix.assign(l.prefix.size(), 0);
     dry.pc.f_first.prefix.assign(dry.pc.f_first.prefix.size(), 0);
     for (auto& l : dry.pc.f_mid) l.prefix.assign(l.prefix.size(), 0);
     dry.pc.f_last.prefix.assign(dry.pc.f_last.prefix.size(), 0);
-    int rc = run_precond_seq(E, base, dry.pc);
+    const int rc = run_precond_seq(E, base, dry.pc, E->st);
     if (rc) return rc;
   }
+  if (E->graph) {
+    cudaGraphExecDestroy(E->graph);
+    E->graph = nullptr;
+  }
+  const int nst = (int)std::min<size_t>(seqs.size(), kLaneStreams);
+  for (int k = (int)E->lane_st.size(); k < nst; ++k) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    IFFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    E->lane_st.push_back(s);
+    IFFD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    E->lane_ev.push_back(ev);
+  }
+  // capture: fork every lane stream from the engine stream, enqueue each lane
+  // on stream (lane mod nst), join them back
   cudaGraph_t g = nullptr;
   IFFD_CUDA(cudaStreamBeginCapture(E->st, cudaStreamCaptureModeThreadLocal));
   const long long before = E->launches;
-  int rc = enqueue_iteration(E, base, it);
-  cudaError_t ce = cudaStreamEndCapture(E->st, &g);
+  int rc = IFFD_OK;
+  cudaError_t ce = cudaEventRecord(E->fork_ev, E->st);
+  for (int k = 0; k < nst && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(E->lane_st[k], E->fork_ev, 0);
+  for (size_t k = 0; k < seqs.size() && ce == cudaSuccess && rc == IFFD_OK; ++k)
+    rc = enqueue_iteration(E, base, seqs[k], E->lane_st[k % nst]);
+  for (int k = 0; k < nst && ce == cudaSuccess; ++k) {
+    ce = cudaEventRecord(E->lane_ev[k], E->lane_st[k]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(E->st, E->lane_ev[k], 0);
+  }
+  const cudaError_t ce_end = cudaStreamEndCapture(E->st, &g);
   E->graph_kernels = E->launches - before;  // kernels per replay, counted when the graph is launched
   E->launches = before;
-  if (rc) {
+  if (rc || ce != cudaSuccess || ce_end != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return rc;
+    if (rc) return rc;
+    return cuda_fail(ce != cudaSuccess ? ce : ce_end, "iteration graph capture");
   }
-  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
   ce = cudaGraphInstantiate(&E->graph, g, 0);
   cudaGraphDestroy(g);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
   E->graph_ids.clear();
   for (auto& s : E->active) E->graph_ids.push_back(s.id);
+  E->graph_lanes = (int)seqs.size();
   return IFFD_OK;
 }
 
@@ -573,6 +632,7 @@ int iffd_engine_create(const iffd_options* opt, size_t budget_bytes, void* strea
   cudaGetDevice(&E.device);
   cudaError_t e = cudaStreamCreateWithFlags(&E.st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&E.fork_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     delete h;
     return cuda_fail(e, "engine stream");

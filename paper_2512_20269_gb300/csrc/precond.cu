@@ -118,7 +118,7 @@ __device__ __forceinline__ void butterfly(const Cplx<T>* in, Cplx<T>* out, int j
   for (int t = 0; t < R; ++t) out[base + t * Ns] = v[t];
 }
 
-// Stockham autosort FFT of npairs independent length-L sequences stored
+// Stockham autosort FFT of npairs independent length-F sequences stored
 // contiguously in bufA; ping-pongs with bufB. Returns the buffer holding the
 // natural-order result. Must be called by the whole CTA.
 // Radices 8, 4, 2, 3, 5 run as register butterflies; any other factor r runs as
@@ -127,7 +127,7 @@ __device__ __forceinline__ void butterfly(const Cplx<T>* in, Cplx<T>* out, int j
 // from a table of exp(-2 pi i s / (Ns r)), s < Ns r.
 template <typename T>
 __device__ Cplx<T>* fft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const AxisTab<T>& ax) {
-  const int L = ax.L;
+  const int L = ax.F;
   Cplx<T>* src = bufA;
   Cplx<T>* dst = bufB;
   int Ns = 1;
@@ -183,6 +183,43 @@ __device__ Cplx<T>* fft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const Ax
   return src;
 }
 
+// Length-L forward DFT of npairs sequences (stride F in shared memory; entries
+// j < L hold the data). Without Bluestein this is fft_block. With it (L has a
+// large prime factor), jk = (j^2 + k^2 - (k-j)^2)/2 turns the DFT into the
+// cyclic convolution of length F >= 2L-1
+//   X_k = conj(c_k) sum_j (x_j conj(c_j)) c_{k-j},   c_j = exp(i pi j^2 / L),
+// evaluated as two length-F FFTs: the inverse one through conjugation,
+// IDFT(y) = conj(DFT(conj y)) / F, with 1/F folded into bhat = DFT_F(b) / F.
+template <typename T>
+__device__ Cplx<T>* dft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const AxisTab<T>& ax) {
+  if (!ax.blu) return fft_block(bufA, bufB, npairs, ax);
+  const int L = ax.L, F = ax.F;
+  for (int w = threadIdx.x; w < npairs * F; w += blockDim.x) {
+    const int j = w % F;
+    Cplx<T> v = {T(0), T(0)};
+    if (j < L) {  // a_j = x_j conj(c_j); zero padding beyond L
+      const Cplx<T> x = bufA[w], c = ldc(ax.chirp + 2 * j);
+      v = {fma(x.x, c.x, x.y * c.y), fma(x.y, c.x, -x.x * c.y)};
+    }
+    bufA[w] = v;
+  }
+  __syncthreads();
+  Cplx<T>* R = fft_block(bufA, bufB, npairs, ax);
+  for (int w = threadIdx.x; w < npairs * F; w += blockDim.x) {
+    const Cplx<T> v = cmul(R[w], ldc(ax.bhat + 2 * (w % F)));
+    R[w] = {v.x, -v.y};
+  }
+  __syncthreads();
+  Cplx<T>* S = fft_block(R, R == bufA ? bufB : bufA, npairs, ax);
+  for (int w = threadIdx.x; w < npairs * L; w += blockDim.x) {
+    const int pr = w / L, k = w - pr * L;
+    const Cplx<T> v = cmul(S[(size_t)pr * F + k], ldc(ax.chirp + 2 * k));
+    S[(size_t)pr * F + k] = {v.x, -v.y};  // X_k = conj(c_k S_k)
+  }
+  __syncthreads();
+  return S;
+}
+
 // y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1].
 template <typename T>
 __device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
@@ -216,11 +253,12 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
                                              const double* __restrict__ dotv1, double* __restrict__ partial,
                                              long long tile_id, int ptile, int pstride, unsigned char* smem) {
   const int npairs = PP / 2;
-  const int L = ax.L;
+  const int L = ax.L;  // DFT length
+  const int F = ax.F;  // stride of a sequence in shared memory
   const int m = ax.m;
   Cplx<Tc>* bufA = reinterpret_cast<Cplx<Tc>*>(smem);
-  Cplx<Tc>* bufB = bufA + (size_t)npairs * L;
-  Tc* tile = reinterpret_cast<Tc*>(bufB + (size_t)npairs * L);
+  Cplx<Tc>* bufB = bufA + (size_t)npairs * F;
+  Tc* tile = reinterpret_cast<Tc*>(bufB + (size_t)npairs * F);
   Tc* outv = tile + (size_t)PP * ldt;  // PP * kMaxNout
 
   __shared__ long long pbase[64];
@@ -271,18 +309,18 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
         else if (l < n) { va = reg_gather(ra, l - 1, ax); vb = reg_gather(rb, l - 1, ax); }
         else { va = neg_if(reg_gather(ra, 2 * n - 1 - l, ax), true); vb = neg_if(reg_gather(rb, 2 * n - 1 - l, ax), true); }
       }
-      bufA[w] = {va, vb};
+      bufA[(size_t)pr * F + l] = {va, vb};
     }
     __syncthreads();
-    const Cplx<Tc>* Z = fft_block(bufA, bufB, npairs, ax);
+    const Cplx<Tc>* Z = dft_block(bufA, bufB, npairs, ax);
     if (ax.kind == 1) {
       const int K = N / 2 + 1;
       for (int w = tid; w < npairs * K; w += blockDim.x) {
         const int pr = w / K, k = w - pr * K;
         Tc* ra = tile + (2 * pr) * ldt;
         Tc* rb = ra + ldt;
-        const Cplx<Tc> zk = Z[(size_t)pr * L + k];
-        const Cplx<Tc> zm = Z[(size_t)pr * L + (k == 0 ? 0 : N - k)];
+        const Cplx<Tc> zk = Z[(size_t)pr * F + k];
+        const Cplx<Tc> zm = Z[(size_t)pr * F + (k == 0 ? 0 : N - k)];
         const Tc Ar = zk.x + zm.x, Ai = zk.y - zm.y;
         const Tc Br = zk.y + zm.y, Bi = zm.x - zk.x;
         const Tc* t4 = ax.post + 4 * k;
@@ -297,7 +335,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     } else {
       for (int w = tid; w < npairs * N; w += blockDim.x) {
         const int pr = w / N, j = w - pr * N;
-        const Cplx<Tc> z = Z[(size_t)pr * L + j + 1];
+        const Cplx<Tc> z = Z[(size_t)pr * F + j + 1];
         const Tc sc = __ldg(ax.post + j);
         tile[(2 * pr) * ldt + j] = -sc * z.y;
         tile[(2 * pr + 1) * ldt + j] = sc * z.x;
@@ -335,7 +373,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
         const Tc* zb = za + ldt;
         const Tc* t4 = ax.post + 4 * k;
         const Tc A = __ldg(t4), B = __ldg(t4 + 1), C = __ldg(t4 + 2), E = __ldg(t4 + 3);
-        Cplx<Tc>* G = bufA + (size_t)pr * L;
+        Cplx<Tc>* G = bufA + (size_t)pr * F;
         if (k == 0 || 2 * k == N) {
           const Tc s = A + A;
           G[k] = {s * za[N - 1 - k], s * zb[N - 1 - k]};
@@ -365,17 +403,17 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
           va = -sc * za[2 * n - 1 - l];
           vb = -sc * zb[2 * n - 1 - l];
         }
-        bufA[w] = {va, vb};
+        bufA[(size_t)pr * F + l] = {va, vb};
       }
     }
     __syncthreads();
-    const Cplx<Tc>* Z = fft_block(bufA, bufB, npairs, ax);
+    const Cplx<Tc>* Z = dft_block(bufA, bufB, npairs, ax);
     // scatter: x = V_reg w + W z_out
     for (int e = tid; e < PP * m; e += blockDim.x) {
       const int pc = e / m, i = e - pc * m;
       const int pr = pc >> 1;
       const bool isb = pc & 1;
-      const Cplx<Tc>* Zp = Z + (size_t)pr * L;
+      const Cplx<Tc>* Zp = Z + (size_t)pr * F;
       auto wreg = [&](int j) -> Tc {
         if (ax.kind == 1) {
           const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
@@ -477,8 +515,10 @@ precond_pass_batched(const PassDesc<Tc, Tin, Tout>* __restrict__ sys, const long
 }
 
 // ------------------------------------------------------------ host launchers
-size_t precond_smem_bytes(int PP, int ldt, int L, size_t elt) {
-  return (size_t)2 * (PP / 2) * L * 2 * elt + (size_t)PP * ldt * elt + (size_t)PP * kMaxNout * elt;
+// F: FFT length (stride of a sequence); two ping-pong buffers of PP/2 complex
+// sequences, the tile and the remainder coefficients.
+size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt) {
+  return (size_t)2 * (PP / 2) * F * 2 * elt + (size_t)PP * ldt * elt + (size_t)PP * kMaxNout * elt;
 }
 
 int precond_tiles(const Dims& dims, int axis, int PP) { return (int)host_num_tiles(dims, axis, PP); }
@@ -486,7 +526,7 @@ int precond_tiles(const Dims& dims, int axis, int PP) { return (int)host_num_til
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
   auto kern = precond_pass<Tc, Tin, Tout, MODE, NDOT>;
-  const size_t sm = precond_smem_bytes(P.PP, P.ldt, P.ax.L, sizeof(Tc));
+  const size_t sm = precond_smem_bytes(P.PP, P.ldt, P.ax.F, sizeof(Tc));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int tiles = precond_tiles(P.dims, P.axis, P.PP);

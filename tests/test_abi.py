@@ -96,3 +96,42 @@ def test_host_setup_matches_oracle(lib, n, p):
         A2 = Wo @ np.diag(1 / s.lam_out) @ Wo.T
         np.testing.assert_allclose(A1, A2, atol=1e-12 * np.abs(A2).max())
         np.testing.assert_allclose(lo, s.lam_out, rtol=1e-12)
+
+
+def _largest_prime_factor(x):
+    f, best = 2, 1
+    while f * f <= x:
+        while x % f == 0:
+            best, x = f, x // f
+        f += 1
+    return max(best, x) if x > 1 else best
+
+
+@pytest.mark.parametrize("n,p", [(256, 4), (64, 3), (384, 8), (149, 5), (134, 6), (61, 4), (37, 4),
+                                 (557, 3), (1939, 3), (2048, 3), (7, 1), (9, 8)])
+def test_transform_planner(lib, n, p):
+    """The DST's complex DFT has length n_reg (DST-II/III, even p) or
+    2 (n_reg + 1) (DST-I, odd p); lengths with a large prime factor run as
+    Bluestein over a 5-smooth F >= 2L - 1, smooth lengths run directly."""
+    from paper_2512_20269_gb300 import host_transform
+    n_reg = n if p % 2 == 0 else n - 1
+    L_expected = n_reg if p % 2 == 0 else 2 * (n_reg + 1)
+    for prec in ("fp64", "fp32"):
+        t = host_transform(n, p, prec)
+        assert t["L"] == L_expected
+        assert t["pencils"] >= 2 and t["pencils"] % 2 == 0
+        if t["bluestein"]:
+            F = t["F"]
+            assert F >= 2 * t["L"] - 1 and _largest_prime_factor(F) <= 5
+            assert _largest_prime_factor(t["L"]) > 13
+        else:
+            assert t["F"] == t["L"]
+        if _largest_prime_factor(t["L"]) <= 5:
+            assert not t["bluestein"]
+    # a large prime factor with room in shared memory always takes Bluestein
+    if _largest_prime_factor(L_expected) >= 37 and L_expected <= 1200:
+        assert host_transform(n, p, "fp64")["bluestein"] and host_transform(n, p, "fp32")["bluestein"]
+    # two FP64 length-F buffers no longer fit for L = 3878: FP64 keeps the
+    # direct FFT while FP32 runs Bluestein
+    if (n, p) == (1939, 3):
+        assert not host_transform(n, p, "fp64")["bluestein"] and host_transform(n, p, "fp32")["bluestein"]

@@ -179,3 +179,47 @@ def test_ragged_tiles_and_padding(d, n, p):
     r2[..., -1] = r[..., -1]
     z2 = plan.apply_preconditioner(_to_gpu(torch, r2)).cpu().numpy()
     assert rel_max_err(z2, oracle_precond(r2, n, p)) <= 1e-12
+
+
+# Transform lengths with a large prime factor run as Bluestein's chirp
+# convolution: L = 298 (2 * 149), 134 (2 * 67), 61, 37 (3D), 58 (2 * 29, 3D).
+BLUESTEIN_SHAPES = [(2, 149, 5), (2, 134, 6), (2, 61, 4), (3, 37, 4), (3, 29, 5)]
+
+
+@pytest.mark.parametrize("d,n,p", BLUESTEIN_SHAPES)
+def test_bluestein_preconditioner_parity(d, n, p):
+    torch = require_gpu()
+    from paper_2512_20269_gb300 import IFFDPlan, host_transform
+    assert host_transform(n, p, "fp64")["bluestein"] and host_transform(n, p, "fp32")["bluestein"]
+    plan = IFFDPlan(d, n, p)
+    r = inputs.rhs(plan.shape, "normal", seed=60 + n + p)
+    rg = _to_gpu(torch, r)
+    zo = oracle_precond(r, n, p)
+    z = plan.apply_preconditioner(rg).cpu().numpy()
+    assert rel_max_err(z, zo) <= 1e-12
+    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+    z32 = IFFDPlan(d, n, p, precision="fp32").apply_preconditioner(rg).cpu().numpy()
+    assert np.linalg.norm(z32 - zo) <= 1e-5 * np.linalg.norm(zo)
+
+
+def test_bluestein_long_fp32_and_pcg():
+    """A 2D DST-I of length 556 (L = 1114 = 2 * 557, F = 2304): FP32 transforms
+    within 1e-5 of the oracle, and a PCG solve through Bluestein passes reaches
+    the relative residual in the oracle's iteration count (+-1)."""
+    torch = require_gpu()
+    from paper_2512_20269_gb300 import IFFDPlan, host_transform
+    n, p = 557, 3
+    assert host_transform(n, p, "fp32")["bluestein"]
+    plan = IFFDPlan(2, n, p, precision="fp32")
+    r = inputs.rhs(plan.shape, "uniform", seed=61)
+    zo = oracle_precond(r, n, p)
+    z = plan.apply_preconditioner(_to_gpu(torch, r)).cpu().numpy()
+    assert np.linalg.norm(z - zo) <= 1e-5 * np.linalg.norm(zo)
+    n, p = 149, 5
+    plan = IFFDPlan(2, n, p)
+    f = inputs.rhs(plan.shape, "uniform", seed=62)
+    u, info = plan.pcg_solve(_to_gpu(torch, f))
+    _, it_o, _ = oracle_pcg(f, n, p)
+    assert info["status"] == 0 and abs(info["iters"] - it_o) <= 1
+    true_rel = np.linalg.norm(f - oracle_stiffness(u.cpu().numpy(), n, p)) / np.linalg.norm(f)
+    assert true_rel <= 1.1e-8
