@@ -60,8 +60,12 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
 
     Per-DoF figures: transform pass 2.5 log2(n) + 2 n_out flops (FFT-type DST +
     remainder projections); the fused pass does two of them plus the eigenvalue
-    sum and division (3 flops); stiffness 7(2p+1) FMA per DoF in 3D spread as
-    2 / 3 / 2 banded products over the three sweeps; PCG update 48 B/DoF."""
+    sum and division (3 flops). Stiffness in the symmetric-Toeplitz form of the
+    interior rows (pair sums u_{i-k} + u_{i+k} shared by M and K): first sweep
+    M u and K u from one set of pair sums, 5p + 2 flops, plus 2 for the fused
+    direction update p = z + beta p; middle sweep M T1, K T1 (shared pairs) and
+    M T2 plus the sum, 8p + 4; last sweep K T1 + M T2, 6p + 3, plus 2 for the
+    fused dot product. PCG update 48 B/DoF."""
     per_pass = 2.5 * math.log2(n) + 2 * n_out
     if kind.startswith("precond"):
         if precision == "fp32":
@@ -71,8 +75,8 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
         fl = per_pass * N if kind != "precond_fused" else (2 * per_pass + 3) * N
         return fl, "flop", "alu"
     if kind.startswith("stiff"):
-        prods = {"stiff_first": 2, "stiff_mid": 3, "stiff_last": 2}[kind]
-        return prods * 2 * (2 * p + 1) * N, "flop", "alu"
+        per = {"stiff_first": 5 * p + 4, "stiff_mid": 8 * p + 4, "stiff_last": 6 * p + 5}[kind]
+        return per * N, "flop", "alu"
     if kind == "pcg_update":
         return 48.0 * N, "B", "hbm"
     if kind == "fd_pass":
@@ -237,7 +241,8 @@ def replica_throughput(dofs_per_solve: int, steps: int, world: int, max_ms: floa
 def workload_config(w):
     return {"workload": w.name, "d": w.d, "n": w.n, "p": w.p, "N": w.N, "rhs": f"{w.dist} seed {w.seed}",
             "precond": "IFFD", "precision": "fp64", "rtol": 1e-8, "boundary": "Dirichlet on all faces",
-            "l2": "no flush: 137 MB vectors, ~1 GB working set > 126 MB L2"}
+            "l2": "no flush: 137 MB vectors, ~1 GB working set > 126 MB L2",
+            "geometry": "iffd_autotune (tiles and radix sequences tuned in setup, excluded from timing)"}
 
 
 def _timed(fn, reps: int, warm: int):
@@ -273,10 +278,10 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
         f = torch.from_numpy(inputs.workload_rhs(w)).cuda()
         res = {}
         for prec in ("fp64", "fp32"):
-            plan = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=False)
+            plan = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=False).autotune()
             u = plan.empty()
             ms, (_, info) = _timed(lambda: plan.pcg_solve(f, u), args.steps, max(args.warmup, 1))
-            chk = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=True)
+            chk = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=True).autotune()
             _, ic = chk.pcg_solve(f)
             res[prec] = {"value": w.N / (ms / 1e3), "ms_per_solve": ms, "iters": info["iters"],
                          "true_rel_res": ic["true_rel_res"]}
@@ -297,7 +302,7 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
         budget = 64 << 30
         outs = [torch.empty_like(f) for *_, f in systems]
 
-        eng = IFFDEngine(budget, precision="fp32")
+        eng = IFFDEngine(budget, precision="fp32", autotune=not args.no_autotune)
 
         def solve_all():
             k0 = eng.stats()["kernel_launches"]
@@ -320,7 +325,8 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
         line.update({"value": total / sec, "ms_per_step": sec * 1e3, "dtype": "f64",
                      "config": {"workload": "batched_512_cubes", "problems": len(probs), "systems": len(systems),
                                 "dofs": int(total), "n": list(inputs.BATCH_N), "p": list(inputs.BATCH_P),
-                                "precond": "IFFD, FP32 transforms", "pcg": "fp64", "seed": 3},
+                                "precond": "IFFD, FP32 transforms", "pcg": "fp64", "seed": 3,
+                                "autotune": not args.no_autotune},
                      "iters_min_max_mean": [min(iters), max(iters), float(np.mean(iters))],
                      "gpu_launches": kl,
                      "timing": "wall clock around submit + engine steps to completion; plans cached, arena "
@@ -353,6 +359,7 @@ def main():
                     help="cube (default, the headline line): 258^3 p=4; square: 65^2 p=3; varcoef: 390^3 p=8 "
                          "variable coefficient; batched: 512 uneven 3D problems; serving: Poisson request stream")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--no-autotune", action="store_true", help="batched: default launch geometry")
     ap.add_argument("--serve-cap-dofs", type=int, default=0,
                     help="serving: cap on the DoFs in flight (0 = HBM budget only)")
     args = ap.parse_args()
@@ -383,7 +390,8 @@ def main():
             dist.barrier()
 
     w = inputs.CUBE_N256_P4
-    plan = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=False)
+    # setup (excluded from timing): plan, then the launch-geometry autotuner
+    plan = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=False).autotune()
     f_host = torch.from_numpy(inputs.workload_rhs(w))
     f = f_host.cuda()
     u = plan.empty()
@@ -421,13 +429,22 @@ def main():
     rooflines = {}
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # Launches that did work: iterations are enqueued in chunks of 4 and the
+    # surplus launches after convergence return at their first instruction, so
+    # per-launch rates use the launches of the executed iterations only.
+    applies = args.steps * (iters + 1)  # preconditioner applies (initial + one per iteration)
+    eff = {"precond_fwd": applies * (w.d - 1), "precond_fused": applies, "precond_bwd": applies * (w.d - 1),
+           "stiff_first": args.steps * iters, "stiff_mid": args.steps * iters, "stiff_last": args.steps * iters,
+           "pcg_update": args.steps * iters}
     for kind, (cnt, kms) in prof.items():
         if cnt == 0:
             continue
         amount, unit, bound = algorithmic(kind, w.d, w.n, w.p, n_out, w.N, "fp64")
         entry = {"launches": cnt, "ms": kms, "share": kms / total_k}
         if amount is not None:
-            avg_s = kms / cnt / 1e3
+            n_eff = min(cnt, eff.get(kind, cnt))
+            entry["launches_with_work"] = n_eff
+            avg_s = kms / n_eff / 1e3
             if unit == "flop":
                 ach = amount / avg_s / 1e12
                 entry.update({"bound": bound, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -464,14 +481,14 @@ def main():
            "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)}
 
     # ---------------- accuracy of the timed solve's iterate (true residual)
-    plan_chk = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=True)
+    plan_chk = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=True).autotune()
     _, info_chk = plan_chk.pcg_solve(f, u_dev)
     del plan_chk
 
     variants = {}
     if not args.no_variants:
         for name, prec, pc, reps in (("fp32_transform", "fp32", "iffd", args.steps), ("exact_fd", "fp64", "exact_fd", 2)):
-            pv = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=False)
+            pv = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=False).autotune()
             pv.pcg_solve(f, u_dev)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
@@ -482,7 +499,7 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             vms = a.elapsed_time(b) / reps
-            pchk = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=True)
+            pchk = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=True).autotune()
             _, ichk = pchk.pcg_solve(f, u_dev)
             variants[name] = {"value": w.N / (vms / 1e3), "unit": UNIT, "ms_per_solve": vms, "iters": iv["iters"],
                               "true_rel_res": ichk["true_rel_res"]}
@@ -501,6 +518,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
                 "iters": iters, "true_rel_res": info_chk["true_rel_res"], "roofline": roofline,
+                "tiles": [plan.tiles(a) for a in range(w.d)],
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clk,
                 "variants": variants, "kernels": rooflines,
                 "hbm_frac_of_solve": None}

@@ -80,6 +80,7 @@ typedef struct {
   int true_residual;   /* 1: iffd_pcg_solve recomputes ||f - A u||/||f|| at exit */
   int flexible;        /* 1: Polak-Ribiere beta (default for FP32 transforms) */
   double coef_amp;     /* amplitude c of IFFD_COEF_SEPARABLE_SIN (|c| < 1 keeps a > 0) */
+  int autotune;        /* engine only: 1 tunes each (d, n, p) class at its first request (iffd_autotune) */
 } iffd_options;
 
 typedef struct {
@@ -90,7 +91,8 @@ typedef struct {
 } iffd_pcg_info;
 
 /* Fills *opt with the defaults: FP64, IFFD, rtol 1e-8, maxit 500, CONST,
- * true_residual 1, flexible 0, coef_amp 0.5. Returns IFFD_ERR_INVALID_ARG on NULL. */
+ * true_residual 1, flexible 0, coef_amp 0.5, autotune 0. Returns
+ * IFFD_ERR_INVALID_ARG on NULL. */
 int iffd_default_options(iffd_options* opt);
 
 /* Builds the plan for d directions with n_elems[k] elements each and degree p
@@ -109,6 +111,29 @@ int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iff
 
 /* Device workspace needed by every call on this plan, in bytes. */
 int iffd_workspace_bytes(iffd_handle h, size_t* bytes);
+
+/* Tunes the launch geometry of the plan on this GPU (the paper has no
+ * counterpart; it fixes no kernel design): for every direction, the pencils
+ * per tile (2..32, within 200 KB of shared memory) and the radix sequence of
+ * the FFT (greedy radix 8, radix 4, or the greedy sequence reversed) of the
+ * transform pass, and the pencils per tile of the stiffness sweep. Each
+ * candidate runs the plan's kernel on the workspace ws (iffd_workspace_bytes,
+ * contents overwritten) on `stream`; the fastest of three timed launches wins.
+ * Passes whose default launch has fewer than 4 x 152 CTAs (too small to fill
+ * the GPU alone) keep the default geometry.
+ * Choices are cached per size class for the life of the process, so plans of
+ * the same class get the same geometry (and bitwise the same results) without
+ * timing again. Synchronizes the stream. Results of a tuned plan equal those
+ * of the untuned plan to rounding: tiles change the order of the partial
+ * sums of the dot products, and the radix sequence changes FFT rounding.
+ * Errors: INVALID_ARG, WORKSPACE (ws NULL or not 256-byte aligned), CUDA. */
+int iffd_autotune(iffd_handle h, void* ws, void* stream);
+
+/* Launch geometry of direction `axis` (any pointer may be NULL): pencils per
+ * tile of its transform pass (for the plan's precision) and of its stiffness
+ * sweep, and the radix sequence of its FFT (radices[0..*nstages), at most 12). */
+int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
+                   int* nstages);
 
 /* Sizes of direction `axis` (0-based): m = n + p - 2, n_reg and n_out of
  * eq. "reg_space_dim". */
@@ -244,7 +269,9 @@ typedef struct {
   iffd_pcg_info info;  /* true_rel_res is -1 (not computed by the engine) */
 } iffd_completion;
 
-/* opt: precision, rtol, maxit, flexible are used (NULL = defaults). The arena
+/* opt: precision, rtol, maxit, flexible and autotune are used (NULL =
+ * defaults); with autotune, the plan of each (d, n, p) is tuned by
+ * iffd_autotune at the first submit of that class. The arena
  * is allocated here (cudaMalloc of budget_bytes on the current device). The
  * engine runs on a stream of its own; every step first waits for the work
  * already enqueued on `stream` (so f may be produced there) and returns after

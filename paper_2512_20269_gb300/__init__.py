@@ -176,6 +176,20 @@ class IFFDPlan:
     # -- profiling (CUDA events around every launch of this plan)
     KERNEL_KINDS = 11
 
+    def autotune(self, stream=None):
+        """Tune tiles and radix sequences on this GPU (iffd_autotune; uses the
+        plan's workspace, synchronizes the stream)."""
+        check(self._lib.iffd_autotune(self._h, self._ws_ptr, _stream_handle(stream)), "iffd_autotune")
+        return self
+
+    def tiles(self, axis: int) -> dict:
+        """Launch geometry of one direction (iffd_get_tiles)."""
+        pt, ps, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rad = (ctypes.c_int * 12)()
+        check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns)),
+              "iffd_get_tiles")
+        return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value])}
+
     def profile_enable(self, on: bool = True):
         check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")
 
@@ -223,7 +237,7 @@ class IFFDEngine:
     """
 
     def __init__(self, budget_bytes: int, precision: str = "fp32", rtol: float = 1e-8, maxit: int = 500,
-                 flexible: bool = False, stream=None):
+                 flexible: bool = False, stream=None, autotune: bool = False):
         self._lib = _lib.load()
         opt = iffd_options()
         self._lib.iffd_default_options(ctypes.byref(opt))
@@ -231,6 +245,7 @@ class IFFDEngine:
         opt.rtol = rtol
         opt.maxit = maxit
         opt.flexible = int(flexible)
+        opt.autotune = int(autotune)
         self.options = opt
         self._stream = stream
         h = ctypes.c_void_p()

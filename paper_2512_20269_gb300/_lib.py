@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "IFFD_OK", 1: "IFFD_ERR_INVALID_ARG", 2: "IFFD_ERR_UNSUPPORTE
 class iffd_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("coef", ctypes.c_int), ("true_residual", ctypes.c_int),
-                ("flexible", ctypes.c_int), ("coef_amp", ctypes.c_double)]
+                ("flexible", ctypes.c_int), ("coef_amp", ctypes.c_double), ("autotune", ctypes.c_int)]
 
 
 class iffd_pcg_info(ctypes.Structure):
@@ -46,6 +46,8 @@ SIGNATURES = [
     ("iffd_setup", ctypes.c_int, [ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, ctypes.POINTER(iffd_options),
                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     ("iffd_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, c_size_t_p]),
+    ("iffd_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("iffd_get_tiles", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]),
     ("iffd_get_dims", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p]),
     ("iffd_get_1d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [c_double_p] * 6),
     ("iffd_host_axis", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libiffd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host_setup.cpp", "precond.cu", "stiffness.cu", "pcg.cu", "fd.cu", "capi.cu", "noalloc.cu", "varcoef.cu", "engine.cu"]
+SOURCES = ["host_setup.cpp", "precond.cu", "stiffness.cu", "pcg.cu", "fd.cu", "capi.cu", "noalloc.cu", "varcoef.cu", "engine.cu",
+           "tune.cu"]
 
 
 def _nvcc() -> str:

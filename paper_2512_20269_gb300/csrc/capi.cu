@@ -1,6 +1,7 @@
 // C ABI of the IFFD library (declarations and contracts in include/iffd.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -56,23 +57,23 @@ static std::vector<T> cast_vec(const std::vector<double>& v) {
 }
 
 struct AxisOffsets {
-  size_t VL, W, lam, post, tw, chirp, bhat;
+  size_t VL, W, lam, post, chirp, bhat;
 };
 
 static bool register_radix(int r) { return r == 8 || r == 4 || r == 2 || r == 3 || r == 5; }
 
-// Stages and twiddles of one Stockham FFT of length len. Register-butterfly
-// stages store exp(-2 pi i q k / (Ns r)) for q = 1..r-1, k < Ns; direct-DFT
-// stages store exp(-2 pi i s / (Ns r)) for s < Ns r.
+// Stages and twiddles of one Stockham FFT of length len with the radix
+// sequence rad. Register-butterfly stages store exp(-2 pi i q k / (Ns r)) for
+// q = 1..r-1, k < Ns; direct-DFT stages store exp(-2 pi i s / (Ns r)), s < Ns r.
 struct FftPlan {
   int len = 0;
   std::vector<int> rad, twoff;
   std::vector<double> tw;
 };
 
-static std::string fft_plan(int len, FftPlan* f) {
+static std::string fft_plan(int len, const std::vector<int>& rad, FftPlan* f) {
   f->len = len;
-  if (!fft_factor(len, &f->rad)) return "bad FFT length " + std::to_string(len);
+  f->rad = rad;
   if ((int)f->rad.size() > kMaxStages) return "too many FFT stages";
   f->tw.clear();
   f->twoff.clear();
@@ -94,6 +95,28 @@ static std::string fft_plan(int len, FftPlan* f) {
     Ns *= r;
   }
   return "";
+}
+
+// Radix sequences offered to the tuner for one FFT length: the greedy
+// radix-8 sequence (the default: 8s, then 4 or 2, then odd factors
+// ascending), the radix-4 sequence, and the greedy sequence reversed (small
+// radices first). Duplicates are dropped; the first entry is the default.
+std::vector<std::vector<int>> radix_variants(int len) {
+  std::vector<int> greedy;
+  fft_factor(len, &greedy);
+  int e2 = 0, x = len;
+  while (x % 2 == 0) { x /= 2; ++e2; }
+  std::vector<int> odd(greedy.begin(), greedy.end());
+  odd.erase(std::remove_if(odd.begin(), odd.end(), [](int r) { return r % 2 == 0; }), odd.end());
+  std::vector<int> four;
+  for (int k = 0; k < e2 / 2; ++k) four.push_back(4);
+  if (e2 % 2) four.push_back(2);
+  four.insert(four.end(), odd.begin(), odd.end());
+  std::vector<int> rev(greedy.rbegin(), greedy.rend());
+  std::vector<std::vector<int>> out{greedy};
+  for (const auto& v : {four, rev})
+    if (std::find(out.begin(), out.end(), v) == out.end()) out.push_back(v);
+  return out;
 }
 
 // Estimated real flops per element of one FFT stage of radix r: (r-1) twiddle
@@ -231,11 +254,10 @@ static std::vector<double> post_table(const Axis1D& A) {
   return post;
 }
 
-// Fills one precision's tables. With F > 0 the length-L DFT runs as Bluestein
-// over the length-F FFT `fp` (twiddles at o.tw), else fp is the length-L FFT.
+// Fills one precision's tables. With F > L the length-L DFT runs as Bluestein
+// over a length-F FFT; the FFT stages are set by set_fft.
 template <typename T>
-static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const FftPlan& fp, const char* base,
-                         const AxisOffsets& o, size_t tw_off) {
+static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const char* base, const AxisOffsets& o) {
   t->m = A.m;
   t->n_reg = A.n_reg;
   t->n_out = A.n_out;
@@ -247,26 +269,49 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const Fft
   t->whi = A.whi;
   t->kind = A.kind;
   t->L = L;
-  t->F = (F > 0) ? F : L;
-  t->blu = (F > 0) ? 1 : 0;
-  t->nst = (int)fp.rad.size();
-  for (int s = 0; s < kMaxStages; ++s) {
-    t->radix[s] = s < t->nst ? fp.rad[s] : 1;
-    t->twoff[s] = s < t->nst ? fp.twoff[s] : 0;
-  }
+  t->F = F;
+  t->blu = (F > L) ? 1 : 0;
   t->VL = reinterpret_cast<const T*>(base + o.VL);
   t->W = reinterpret_cast<const T*>(base + o.W);
   t->lam = reinterpret_cast<const T*>(base + o.lam);
   t->post = reinterpret_cast<const T*>(base + o.post);
-  t->tw = reinterpret_cast<const T*>(base + tw_off);
   t->chirp = reinterpret_cast<const T*>(base + o.chirp);
   t->bhat = reinterpret_cast<const T*>(base + o.bhat);
 }
 
-// Pencils per tile of a transform pass whose FFT has length F.
+template <typename T>
+static const T* var_tw(const FftVar& v);
+template <>
+const double* var_tw<double>(const FftVar& v) { return v.twd; }
+template <>
+const float* var_tw<float>(const FftVar& v) { return v.twf; }
+
+// Selects the radix sequence v (whose length must equal t->F).
+template <typename T>
+void set_fft(AxisTab<T>* t, const FftVar& v) {
+  t->nst = v.nst;
+  for (int s = 0; s < kMaxStages; ++s) {
+    t->radix[s] = s < v.nst ? v.radix[s] : 1;
+    t->twoff[s] = s < v.nst ? v.twoff[s] : 0;
+  }
+  t->tw = var_tw<T>(v);
+}
+template void set_fft<double>(AxisTab<double>*, const FftVar&);
+template void set_fft<float>(AxisTab<float>*, const FftVar&);
+
+// Index of the default (first) radix sequence of length len in fvar.
+static int default_var(const std::vector<FftVar>& fv, int len) {
+  for (size_t i = 0; i < fv.size(); ++i)
+    if (fv[i].len == len) return (int)i;
+  return -1;
+}
+
+// Default pencils per tile of a transform pass whose FFT has length F: 8
+// (FP64) or 16 (FP32) pencils, halved while the tile needs more than 110 KB of
+// shared memory (iffd_autotune may pick others).
 static int pick_pp(int m, int F, size_t elt, int* PP, int* ldt) {
   *ldt = m | 1;
-  int pp = 16;
+  int pp = (elt == sizeof(double)) ? 8 : 16;
   while (pp > 2 && precond_smem_bytes(pp, *ldt, F, elt) > 110 * 1024) pp /= 2;
   if (precond_smem_bytes(pp, *ldt, F, elt) > 220 * 1024) return 0;
   *PP = pp;
@@ -294,9 +339,9 @@ static int build_plan(Plan* P, cudaStream_t stream) {
   struct PerAxis {
     AxisOffsets od, of;
     size_t Mb, Kb, Mt, Kt, QT, Q, lamQ, Msb, Ksb;
-    int L, F;              // DFT length; Bluestein FFT length (0: direct)
-    FftPlan direct, blu;   // length-L FFT; length-F FFT
-    size_t twB_d, twB_f;   // twiddles of the length-F FFT (FP64, FP32)
+    int L, F;                          // DFT length; Bluestein FFT length (0: direct)
+    std::vector<FftPlan> vars;         // radix sequences of length L (and F)
+    std::vector<size_t> var_d, var_f;  // their twiddle tables (FP64, FP32)
     int ilo, ihi;
   } pa[3];
   for (int a = 0; a < P->d; ++a) {
@@ -305,32 +350,34 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     // (two pencils per sequence; Makhoul order for DST-II/III, odd extension
     // for DST-I); lengths with large prime factors may run as Bluestein
     pa[a].L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
-    std::string err = fft_plan(pa[a].L, &pa[a].direct);
-    if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
     pa[a].F = bluestein_length(pa[a].L);
     std::vector<double> chirp, bhat;
-    if (pa[a].F > 0) {
-      err = fft_plan(pa[a].F, &pa[a].blu);
-      if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
-      bluestein_tables(pa[a].L, pa[a].F, &chirp, &bhat);
+    if (pa[a].F > 0) bluestein_tables(pa[a].L, pa[a].F, &chirp, &bhat);
+    std::string err;
+    for (int len : {pa[a].L, pa[a].F}) {
+      if (len <= 0) continue;
+      for (const auto& rad : radix_variants(len)) {
+        FftPlan fp;
+        err = fft_plan(len, rad, &fp);
+        if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+        pa[a].var_d.push_back(tb.add_vec(fp.tw));
+        pa[a].var_f.push_back(tb.add_vec(cast_vec<float>(fp.tw)));
+        pa[a].vars.push_back(std::move(fp));
+      }
     }
     const std::vector<double> post = post_table(A);
     pa[a].od.VL = tb.add_vec(A.VL);
     pa[a].od.W = tb.add_vec(A.W);
     pa[a].od.lam = tb.add_vec(A.lam);
     pa[a].od.post = tb.add_vec(post);
-    pa[a].od.tw = tb.add_vec(pa[a].direct.tw);
     pa[a].od.chirp = tb.add_vec(chirp);
     pa[a].od.bhat = tb.add_vec(bhat);
-    pa[a].twB_d = tb.add_vec(pa[a].blu.tw);
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
     pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
     pa[a].of.lam = tb.add_vec(cast_vec<float>(A.lam));
     pa[a].of.post = tb.add_vec(cast_vec<float>(post));
-    pa[a].of.tw = tb.add_vec(cast_vec<float>(pa[a].direct.tw));
     pa[a].of.chirp = tb.add_vec(cast_vec<float>(chirp));
     pa[a].of.bhat = tb.add_vec(cast_vec<float>(bhat));
-    pa[a].twB_f = tb.add_vec(cast_vec<float>(pa[a].blu.tw));
     // stiffness band tables; interior rows 2p-1 .. m-2p are symmetric Toeplitz
     const int p = A.p, m = A.m, bw = 2 * p + 1;
     pa[a].Mb = tb.add_vec(A.Mband);
@@ -388,16 +435,34 @@ static int build_plan(Plan* P, cudaStream_t stream) {
   int max_parts = vec_grid(N);
   for (int a = 0; a < P->d; ++a) {
     const Axis1D& A = P->host[a];
-    // per precision: Bluestein (F > L) or the direct length-L FFT
+    // FFT variants with device twiddle pointers
+    P->fvar[a].clear();
+    for (size_t k = 0; k < pa[a].vars.size(); ++k) {
+      const FftPlan& fp = pa[a].vars[k];
+      FftVar v{};
+      v.len = fp.len;
+      v.nst = (int)fp.rad.size();
+      for (int st = 0; st < v.nst; ++st) {
+        v.radix[st] = fp.rad[st];
+        v.twoff[st] = fp.twoff[st];
+      }
+      v.twd = reinterpret_cast<const double*>(base + pa[a].var_d[k]);
+      v.twf = reinterpret_cast<const float*>(base + pa[a].var_f[k]);
+      P->fvar[a].push_back(v);
+    }
+    // per precision: Bluestein (F > L) or the direct length-L FFT, default
+    // radix sequence and tile
     int L, F;
     if (!choose_transform(A, sizeof(double), &L, &F, &P->PPd[a], &P->ldtd[a]))
       return fail(IFFD_ERR_UNSUPPORTED, "transform length too large for shared memory");
-    if (F > L) fill_axistab(&P->axd[a], A, L, F, pa[a].blu, base, pa[a].od, pa[a].twB_d);
-    else fill_axistab(&P->axd[a], A, L, 0, pa[a].direct, base, pa[a].od, pa[a].od.tw);
+    fill_axistab(&P->axd[a], A, L, F, base, pa[a].od);
+    P->vsel_d[a] = default_var(P->fvar[a], F);
+    set_fft(&P->axd[a], P->fvar[a][P->vsel_d[a]]);
     if (!choose_transform(A, sizeof(float), &L, &F, &P->PPf[a], &P->ldtf[a]))
       return fail(IFFD_ERR_UNSUPPORTED, "transform length too large for shared memory");
-    if (F > L) fill_axistab(&P->axf[a], A, L, F, pa[a].blu, base, pa[a].of, pa[a].twB_f);
-    else fill_axistab(&P->axf[a], A, L, 0, pa[a].direct, base, pa[a].of, pa[a].of.tw);
+    fill_axistab(&P->axf[a], A, L, F, base, pa[a].of);
+    P->vsel_f[a] = default_var(P->fvar[a], F);
+    set_fft(&P->axf[a], P->fvar[a][P->vsel_f[a]]);
     BandTab& b = P->bt[a];
     b.m = A.m;
     b.p = A.p;
@@ -408,7 +473,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     b.ilo = pa[a].ilo;
     b.ihi = pa[a].ihi;
     P->ldts[a] = A.m | 1;
-    int pp = 16;
+    int pp = 8;
     while (pp > 2 && (size_t)2 * pp * P->ldts[a] * sizeof(double) > 100 * 1024) pp /= 2;
     P->PPs[a] = pp;
     pp = 16;
@@ -425,9 +490,9 @@ static int build_plan(Plan* P, cudaStream_t stream) {
       P->QT[a] = reinterpret_cast<const double*>(base + pa[a].QT);
       P->lamQ[a] = reinterpret_cast<const double*>(base + pa[a].lamQ);
     }
-    max_parts = std::max(max_parts, precond_tiles(P->dims, a, P->PPd[a]));
-    max_parts = std::max(max_parts, precond_tiles(P->dims, a, P->PPf[a]));
-    max_parts = std::max(max_parts, stiff_tiles(P->dims, a, P->PPs[a]));
+    // partial sums: room for the smallest tile the tuner may pick
+    max_parts = std::max(max_parts, precond_tiles(P->dims, a, kMinTunePP));
+    max_parts = std::max(max_parts, stiff_tiles(P->dims, a, kMinTunePP));
   }
   P->max_parts = max_parts;
   const size_t vec = align256((size_t)N * sizeof(double));
@@ -481,8 +546,8 @@ __global__ void copy_kernel(const double* __restrict__ a, double* __restrict__ b
 }
 
 template <typename Tc>
-static PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const int* PPs, const int* ldts,
-                                const int* done) {
+PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const int* PPs, const int* ldts,
+                         const int* done) {
   PassLaunch<Tc> L;
   L.dims = P->dims;
   L.axis = axis;
@@ -497,6 +562,10 @@ static PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs
   L.done = done;
   return L;
 }
+template PassLaunch<double> make_pass<double>(const Plan*, int, const AxisTab<double>*, const int*, const int*,
+                                              const int*);
+template PassLaunch<float> make_pass<float>(const Plan*, int, const AxisTab<float>*, const int*, const int*,
+                                            const int*);
 
 // z = P^{-1} r; with ndot >= 1 also partial (dot0, z) [and (dot1, z)] into
 // `partial`; *nparts receives the number of partial sums.
@@ -597,7 +666,7 @@ static int run_precond(const Plan* P, const double* r, double* z, void* ws, cuda
   return IFFD_OK;
 }
 
-static StiffLaunch make_stiff(const Plan* P, int axis) {
+StiffLaunch make_stiff(const Plan* P, int axis) {
   StiffLaunch S;
   S.dims = P->dims;
   S.axis = axis;
@@ -767,6 +836,7 @@ int iffd_default_options(iffd_options* opt) {
   opt->true_residual = 1;
   opt->flexible = 0;
   opt->coef_amp = 0.5;
+  opt->autotune = 0;
   return IFFD_OK;
 }
 

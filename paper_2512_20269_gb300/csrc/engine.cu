@@ -687,6 +687,15 @@ int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const double* 
   if (need > E.arena.bytes) return fail(IFFD_ERR_UNSUPPORTED, "request needs more workspace than the whole budget");
   size_t off = 0;
   if (!E.arena.alloc(need, &off)) return fail(IFFD_ERR_WORKSPACE, "budget exhausted: resubmit after completions");
+  if (E.opt.autotune && !P->P.tuned) {
+    // first request of this (d, n, p): tune its plan on the request's own
+    // workspace (no other system uses this plan yet)
+    rc = plan_autotune(&P->P, E.arena_mem + off, E.st);
+    if (rc) {
+      E.arena.release(off, need);
+      return rc;
+    }
+  }
   Sys s{};
   s.id = E.next_id++;
   s.plan = P;

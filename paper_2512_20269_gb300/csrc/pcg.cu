@@ -138,18 +138,32 @@ constexpr int kStOk = 0, kStNotConverged = 6, kStBreakdown = 7;
 
 __device__ __forceinline__ void finalize_body(SolveState* st, const double* __restrict__ partial, int nparts, int phase,
                                               double tol2, int maxit) {
-  __shared__ double red[32];
+  __shared__ double red[2][32];
   if (phase != FP_FF && phase != FP_TRUE && st->done) return;
-  // fixed-order reduction: thread t sums parts t, t+1024, ...; then a fixed tree
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+  // fixed-order reduction: thread t sums parts t, t+1024, ...; then a fixed
+  // tree. The flexible beta also needs the second set partial[nparts..2 nparts).
+  const bool two = (phase == FP_RZ_FLEX);
+  double s = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    s += partial[i];
+    if (two) s2 += partial[nparts + i];
+  }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int off = 16; off > 0; off >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s;
+    red[1][threadIdx.x >> 5] = s2;
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double tot = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  double tot = 0.0, tot2 = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    tot += red[0][w];
+    tot2 += red[1][w];
+  }
   switch (phase) {
     case FP_FF:
       st->ff = tot;
@@ -182,13 +196,9 @@ __device__ __forceinline__ void finalize_body(SolveState* st, const double* __re
       // flexible (Polak-Ribiere) beta = (z_new, r_new - r_old) / (z_old, r_old)
       //                              = -alpha (z_new, q) / rz_old;
       // partial[0..nparts) holds (r,z), partial[nparts..2 nparts) holds (q,z)
-      {
-        double zq = 0.0;
-        for (int i = 0; i < nparts; ++i) zq += partial[nparts + i];
-        st->zq = zq;
-        if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
-        else { st->beta = -st->alpha * zq / st->rz; st->rz_old = st->rz; st->rz = tot; }
-      }
+      st->zq = tot2;
+      if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
+      else { st->beta = -st->alpha * tot2 / st->rz; st->rz_old = st->rz; st->rz = tot; }
       break;
     case FP_TRUE:
       st->zq = tot;  // ||f - A u||^2 of the final iterate

@@ -95,6 +95,17 @@ struct Profiler {
   }
 };
 
+// Smallest pencils-per-tile the tuner tries (sizes the partial-sum buffer).
+constexpr int kMinTunePP = 2;
+
+// One radix sequence of the FFT of one direction, with its device twiddles.
+struct FftVar {
+  int len, nst;
+  int radix[kMaxStages], twoff[kMaxStages];
+  const double* twd;
+  const float* twf;
+};
+
 // Plan of one problem: host 1D data, device tables, launch geometry.
 struct Plan {
   mutable Profiler prof;
@@ -110,6 +121,11 @@ struct Plan {
   BandTab bt[3];
   WBandTab wb[3];  // variable-coefficient bands (IFFD_COEF_SEPARABLE_SIN)
   int PPd[3], ldtd[3], PPf[3], ldtf[3], PPs[3], ldts[3], PPv[3];
+  // FFT radix sequences of each direction (lengths L, and F for Bluestein) and
+  // the one selected per precision (index into fvar[a])
+  std::vector<FftVar> fvar[3];
+  int vsel_d[3] = {0, 0, 0}, vsel_f[3] = {0, 0, 0};
+  bool tuned = false;
   // exact FD tables
   const double* QT[3] = {nullptr, nullptr, nullptr};
   const double* Q[3] = {nullptr, nullptr, nullptr};
@@ -134,5 +150,9 @@ int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const if
                 iffd_plan** out);
 void plan_release(iffd_plan* h);
 StiffLaunch plan_stiff_launch(const Plan* P, int axis);
+template <typename T>
+void set_fft(AxisTab<T>* t, const FftVar& v);
+// Tunes the tiles and radix sequences of a plan on workspace ws (iffd_autotune).
+int plan_autotune(Plan* P, void* ws, cudaStream_t st);
 
 }  // namespace iffd
