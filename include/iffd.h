@@ -14,8 +14,9 @@
  *   caller, contiguous, with direction 1 (x) fastest -- the lexicographic order
  *   of eq. "tp-B-basis": entry (i_1, .., i_d) sits at i_1 + m_1 (i_2 + m_2 i_3).
  * - The library owns only the plan (handle) and its device tables (a few
- *   hundred KB). All large scratch memory is a caller-provided device buffer
- *   `ws` of at least iffd_workspace_bytes() bytes (256-byte aligned).
+ *   hundred KB, plus 8 N bytes of eigenvalue reciprocals for FP64 IFFD plans).
+ *   All large scratch memory is a caller-provided device buffer `ws` of at
+ *   least iffd_workspace_bytes() bytes (256-byte aligned).
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   Every call is asynchronous on that stream except iffd_setup (which
  *   synchronises it once after uploading the tables) and iffd_pcg_solve (which
@@ -101,7 +102,9 @@ int iffd_default_options(iffd_options* opt);
  * special basis of eq. "special_basis", V_out, Q_out, Lambda_out, D~_reg,
  * Lambda_reg of Lemma 3) -- plus the dense Q_k of eq. "eigendecomposition" when
  * opt->precond == IFFD_PRECOND_EXACT_FD -- and uploads them to the current
- * device. dirichlet[2k], dirichlet[2k+1] flag Dirichlet data at x_k = 0 / 1
+ * device. FP64 IFFD plans also keep 1 / (sum of the eigenvalues of all
+ * directions) for every DoF on the device (8 N bytes), so that the eigenvalue
+ * scaling is a multiply. dirichlet[2k], dirichlet[2k+1] flag Dirichlet data at x_k = 0 / 1
  * (must be 1, 1). opt may be NULL (defaults). stream: see conventions.
  * Errors: INVALID_ARG, UNSUPPORTED (n <= p, p > 16, non-{0,1} Dirichlet set,
  * transform too large for shared memory), SINGULAR, CUDA. *out is set only

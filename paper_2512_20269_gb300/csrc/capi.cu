@@ -277,6 +277,7 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const cha
   t->post = reinterpret_cast<const T*>(base + o.post);
   t->chirp = reinterpret_cast<const T*>(base + o.chirp);
   t->bhat = reinterpret_cast<const T*>(base + o.bhat);
+  t->rden = nullptr;
 }
 
 template <typename T>
@@ -798,10 +799,20 @@ int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const if
     }
     if (o.coef == IFFD_COEF_SEPARABLE_SIN) build_weighted_bands(&P->host[a]);
   }
-  const int rc = build_plan(P, stream);
+  int rc = build_plan(P, stream);
+  if (rc == IFFD_OK && o.precision == IFFD_PREC_FP64 && o.precond == IFFD_PRECOND_IFFD) {
+    // reciprocals of the summed eigenvalues for the FUSED pass (8 N bytes)
+    cudaError_t e = cudaMalloc(&P->rden, (size_t)P->dims.N * sizeof(double));
+    if (e == cudaSuccess)
+      e = launch_rden_fill(P->rden, P->dims, P->axd[d - 1].lam, P->axd[0].lam, P->axd[d == 3 ? 1 : 0].lam, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "eigenvalue reciprocals");
+    else P->axd[d - 1].rden = P->rden;
+  }
   if (rc != IFFD_OK) {
     const std::string msg = g_err;
     if (P->dev) cudaFree(P->dev);
+    if (P->rden) cudaFree(P->rden);
     if (P->host_state) cudaFreeHost(P->host_state);
     delete h;
     g_err = msg;
@@ -816,6 +827,7 @@ void plan_release(iffd_plan* h) {
   Plan* P = &h->P;
   P->prof.release();
   if (P->dev) cudaFree(P->dev);
+  if (P->rden) cudaFree(P->rden);
   if (P->host_state) cudaFreeHost(P->host_state);
   delete h;
 }

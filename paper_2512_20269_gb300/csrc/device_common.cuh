@@ -56,6 +56,10 @@ struct AxisTab {
   const T* tw;     // complex FFT twiddles (interleaved), per stage offsets twoff
   const T* chirp;  // Bluestein: c_j = exp(i pi j^2 / L), j < L (interleaved)
   const T* bhat;   // Bluestein: DFT_F of the chirp kernel, divided by F
+  // FP64 plans, last direction: 1 / (sum of the eigenvalues of all directions)
+  // per DoF (same layout as the data), used by the FUSED pass instead of a
+  // division; NULL elsewhere.
+  const double* rden;
 };
 
 // Pencil tiles. The pencils along direction `axis` are numbered q = 0..Q-1:

@@ -44,7 +44,10 @@ template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                 long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st);
 
-size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);  // F: FFT length (AxisTab::F)
+size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);
+// Fills AxisTab::rden of an FP64 plan (see device_common.cuh).
+cudaError_t launch_rden_fill(double* rden, const Dims& dims, const double* lamF, const double* lam0,
+                             const double* lam1, cudaStream_t st);  // F: FFT length (AxisTab::F)
 int precond_tiles(const Dims& dims, int axis, int PP);
 
 template <typename Tc, typename Tin, typename Tout>

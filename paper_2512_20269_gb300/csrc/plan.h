@@ -116,6 +116,7 @@ struct Plan {
   Dims dims{};
   Axis1D host[3];
   void* dev = nullptr;  // single allocation for all device tables
+  double* rden = nullptr;  // FP64 IFFD plans: N reciprocals of the summed eigenvalues
   AxisTab<double> axd[3];
   AxisTab<float> axf[3];
   BandTab bt[3];

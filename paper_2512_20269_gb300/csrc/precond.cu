@@ -349,13 +349,25 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
   }
 
   if (MODE == PM_FUSED) {
-    // divide by the summed eigenvalues of all directions
-    for (int e = tid; e < PP * m; e += blockDim.x) {
-      const int pc = e / m, i = e - pc * m;
-      if (pc >= g.nvalid) continue;  // padding pencils
-      Tc den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
-      if (dims.d == 3) den += __ldg(lamB + pib[pc]);
-      tile[pc * ldt + i] = tile[pc * ldt + i] / den;
+    // divide by the summed eigenvalues of all directions: by a multiply with
+    // the precomputed reciprocal (FP64 plans; read in the coalesced order of
+    // the tile load), else by a division
+    if (ax.rden != nullptr) {
+      for (int e = tid; e < PP * m; e += blockDim.x) {
+        int pc, i;
+        if (axis == 0) { pc = e / m; i = e - pc * m; }
+        else { i = e / PP; pc = e - i * PP; }
+        if (pc >= g.nvalid) continue;  // padding pencils
+        tile[pc * ldt + i] = tile[pc * ldt + i] * (Tc)__ldg(ax.rden + pbase[pc] + i * g.S);
+      }
+    } else {
+      for (int e = tid; e < PP * m; e += blockDim.x) {
+        const int pc = e / m, i = e - pc * m;
+        if (pc >= g.nvalid) continue;  // padding pencils
+        Tc den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
+        if (dims.d == 3) den += __ldg(lamB + pib[pc]);
+        tile[pc * ldt + i] = tile[pc * ldt + i] / den;
+      }
     }
     __syncthreads();
   }
@@ -512,6 +524,30 @@ precond_pass_batched(const PassDesc<Tc, Tin, Tout>* __restrict__ sys, const long
   const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
   precond_body<Tc, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.PP, sd.ldt, sd.ax, sd.lamA, sd.lamB,
                                           sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+}
+
+// rden[x + m0 (y + m1 z)] = 1 / (lam_F[i_F] + lam_0[x] (+ lam_1[y])): the
+// reciprocal of the summed eigenvalues, added in the order of the FUSED pass
+// (last direction F = d-1 first, then direction 0, then direction 1).
+__global__ void rden_fill(double* __restrict__ rden, Dims dims, const double* __restrict__ lamF,
+                          const double* __restrict__ lam0, const double* __restrict__ lam1) {
+  const long long m0 = dims.m[0], m1 = dims.m[1];
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < dims.N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long x = idx % m0, rest = idx / m0;
+    double den;
+    if (dims.d == 3) den = (__ldg(lamF + rest / m1) + __ldg(lam0 + x)) + __ldg(lam1 + rest % m1);
+    else den = __ldg(lamF + rest) + __ldg(lam0 + x);
+    rden[idx] = 1.0 / den;
+  }
+}
+
+cudaError_t launch_rden_fill(double* rden, const Dims& dims, const double* lamF, const double* lam0,
+                             const double* lam1, cudaStream_t st) {
+  long long g = (dims.N + kThreads - 1) / kThreads;
+  if (g > 8 * 152) g = 8 * 152;
+  rden_fill<<<(unsigned)g, kThreads, 0, st>>>(rden, dims, lamF, lam0, lam1);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ host launchers
