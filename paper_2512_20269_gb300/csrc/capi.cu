@@ -278,6 +278,12 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const cha
   t->chirp = reinterpret_cast<const T*>(base + o.chirp);
   t->bhat = reinterpret_cast<const T*>(base + o.bhat);
   t->rden = nullptr;
+  t->fm = make_fastdiv(A.m);
+  t->fL = make_fastdiv(L);
+  t->fF = make_fastdiv(F);
+  t->fN = make_fastdiv(A.n_reg);
+  t->fK = make_fastdiv(A.n_reg / 2 + 1);
+  t->fnout = make_fastdiv(A.n_out);
 }
 
 template <typename T>
@@ -291,9 +297,13 @@ const float* var_tw<float>(const FftVar& v) { return v.twf; }
 template <typename T>
 void set_fft(AxisTab<T>* t, const FftVar& v) {
   t->nst = v.nst;
+  int Ns = 1;
   for (int s = 0; s < kMaxStages; ++s) {
     t->radix[s] = s < v.nst ? v.radix[s] : 1;
     t->twoff[s] = s < v.nst ? v.twoff[s] : 0;
+    t->fnb[s] = make_fastdiv(v.len / t->radix[s]);
+    t->fNs[s] = make_fastdiv(Ns);
+    if (s < v.nst) Ns *= v.radix[s];
   }
   t->tw = var_tw<T>(v);
 }

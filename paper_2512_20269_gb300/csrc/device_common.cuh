@@ -32,6 +32,32 @@ __device__ __forceinline__ Cplx<T> mul_mi(Cplx<T> a) { return {a.y, -a.x}; }
 template <typename T>
 __device__ __forceinline__ Cplx<T> mul_pi(Cplx<T> a) { return {-a.y, a.x}; }
 
+// Quotient of a non-negative n < 2^31 by an invariant divisor d >= 1 through
+// one 64-bit multiply and a shift -- division by invariant integers using
+// multiplication (Granlund and Montgomery, PLDI 1994). With l = ceil(log2 d),
+// s = 31 + l and M = ceil(2^s / d) (< 2^32): M d = 2^s + e with 0 <= e < d,
+// so n M / 2^s = n / d + n e / (d 2^s), and the last term is below
+// n / 2^s < 2^-l <= 1/d, too small to reach the next integer:
+// floor(n M / 2^s) = floor(n / d).
+struct FastDiv {
+  unsigned M;
+  int s, d;
+  __host__ __device__ __forceinline__ int div(int n) const {
+    return (int)(((unsigned long long)(unsigned)n * M) >> s);
+  }
+  __host__ __device__ __forceinline__ int mod(int n) const { return n - div(n) * d; }
+};
+
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  f.d = d < 1 ? 1 : d;
+  int l = 0;
+  while ((1LL << l) < f.d) ++l;
+  f.s = 31 + l;
+  f.M = (unsigned)(((1ULL << f.s) + (unsigned long long)f.d - 1) / (unsigned long long)f.d);
+  return f;
+}
+
 // Logical shape of a tensor-product coefficient array: x (direction 1) fastest.
 struct Dims {
   int d;
@@ -54,6 +80,10 @@ struct AxisTab {
   const T* lam;    // m: Lambda_reg then Lambda_out
   const T* post;   // DST-II/III: 4 per k = 0..N/2;  DST-I: n_reg values 1/(2 D~)
   const T* tw;     // complex FFT twiddles (interleaved), per stage offsets twoff
+  // invariant divisors of the index arithmetic: m, L, F, n_reg, n_reg/2 + 1,
+  // n_out, and per FFT stage F / radix and the stage's Ns
+  FastDiv fm, fL, fF, fN, fK, fnout;
+  FastDiv fnb[kMaxStages], fNs[kMaxStages];
   const T* chirp;  // Bluestein: c_j = exp(i pi j^2 / L), j < L (interleaved)
   const T* bhat;   // Bluestein: DFT_F of the chirp kernel, divided by F
   // FP64 plans, last direction: 1 / (sum of the eigenvalues of all directions)

@@ -99,9 +99,9 @@ __device__ __forceinline__ void dft5(Cplx<T>* v) {
 }
 
 template <typename T, int R>
-__device__ __forceinline__ void butterfly(const Cplx<T>* in, Cplx<T>* out, int j, int nb, int Ns, const T* tw) {
+__device__ __forceinline__ void butterfly(const Cplx<T>* in, Cplx<T>* out, int j, int k, int nb, int Ns,
+                                          const T* tw) {
   Cplx<T> v[R];
-  const int k = j % Ns;
 #pragma unroll
   for (int q = 0; q < R; ++q) v[q] = in[j + q * nb];
   if (Ns > 1) {
@@ -134,31 +134,33 @@ __device__ Cplx<T>* fft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const Ax
   for (int s = 0; s < ax.nst; ++s) {
     const int r = ax.radix[s];
     const int nb = L / r;
+    const FastDiv fnb = ax.fnb[s], fNs = ax.fNs[s];
     const T* tw = ax.tw + 2 * ax.twoff[s];
     if (r == 8 || r == 4 || r == 2 || r == 3 || r == 5) {
       const int total = npairs * nb;
       for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        const int pr = w / nb;
+        const int pr = fnb.div(w);
         const int j = w - pr * nb;
+        const int k = fNs.mod(j);
         const Cplx<T>* in = src + (size_t)pr * L;
         Cplx<T>* out = dst + (size_t)pr * L;
         switch (r) {
-          case 8: butterfly<T, 8>(in, out, j, nb, Ns, tw); break;
-          case 4: butterfly<T, 4>(in, out, j, nb, Ns, tw); break;
-          case 2: butterfly<T, 2>(in, out, j, nb, Ns, tw); break;
-          case 3: butterfly<T, 3>(in, out, j, nb, Ns, tw); break;
-          default: butterfly<T, 5>(in, out, j, nb, Ns, tw); break;
+          case 8: butterfly<T, 8>(in, out, j, k, nb, Ns, tw); break;
+          case 4: butterfly<T, 4>(in, out, j, k, nb, Ns, tw); break;
+          case 2: butterfly<T, 2>(in, out, j, k, nb, Ns, tw); break;
+          case 3: butterfly<T, 3>(in, out, j, k, nb, Ns, tw); break;
+          default: butterfly<T, 5>(in, out, j, k, nb, Ns, tw); break;
         }
       }
     } else {
       const int NsR = Ns * r;
       const int total = npairs * L;
       for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        const int pr = w / L;
+        const int pr = ax.fF.div(w);
         const int o = w - pr * L;
-        const int t = o / nb;
+        const int t = fnb.div(o);
         const int j = o - t * nb;
-        const int k = j % Ns;
+        const int k = fNs.mod(j);
         const int step = k + t * Ns;
         const Cplx<T>* in = src + (size_t)pr * L;
         Cplx<T> acc = in[j];
@@ -195,7 +197,7 @@ __device__ Cplx<T>* dft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const Ax
   if (!ax.blu) return fft_block(bufA, bufB, npairs, ax);
   const int L = ax.L, F = ax.F;
   for (int w = threadIdx.x; w < npairs * F; w += blockDim.x) {
-    const int j = w % F;
+    const int j = ax.fF.mod(w);
     Cplx<T> v = {T(0), T(0)};
     if (j < L) {  // a_j = x_j conj(c_j); zero padding beyond L
       const Cplx<T> x = bufA[w], c = ldc(ax.chirp + 2 * j);
@@ -206,13 +208,13 @@ __device__ Cplx<T>* dft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const Ax
   __syncthreads();
   Cplx<T>* R = fft_block(bufA, bufB, npairs, ax);
   for (int w = threadIdx.x; w < npairs * F; w += blockDim.x) {
-    const Cplx<T> v = cmul(R[w], ldc(ax.bhat + 2 * (w % F)));
+    const Cplx<T> v = cmul(R[w], ldc(ax.bhat + 2 * ax.fF.mod(w)));
     R[w] = {v.x, -v.y};
   }
   __syncthreads();
   Cplx<T>* S = fft_block(R, R == bufA ? bufB : bufA, npairs, ax);
   for (int w = threadIdx.x; w < npairs * L; w += blockDim.x) {
-    const int pr = w / L, k = w - pr * L;
+    const int pr = ax.fL.div(w), k = w - pr * L;
     const Cplx<T> v = cmul(S[(size_t)pr * F + k], ldc(ax.chirp + 2 * k));
     S[(size_t)pr * F + k] = {v.x, -v.y};  // X_k = conj(c_k S_k)
   }
@@ -253,6 +255,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
                                              const double* __restrict__ dotv1, double* __restrict__ partial,
                                              long long tile_id, int ptile, int pstride, unsigned char* smem) {
   const int npairs = PP / 2;
+  const int lpp = 31 - __clz(PP);  // PP is a power of two
   const int L = ax.L;  // DFT length
   const int F = ax.F;  // stride of a sequence in shared memory
   const int m = ax.m;
@@ -272,8 +275,8 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
   // the valid pencil, e.g. undivided values in the fused pass).
   for (int e = tid; e < PP * m; e += blockDim.x) {
     int pc, i;
-    if (axis == 0) { pc = e / m; i = e - pc * m; }
-    else { i = e / PP; pc = e - i * PP; }
+    if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
+    else { i = e >> lpp; pc = e & (PP - 1); }
     tile[pc * ldt + i] = (pc < g.nvalid) ? (Tc)in[pbase[pc] + i * g.S] : Tc(0);
   }
   __syncthreads();
@@ -285,7 +288,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
     const int nw = ax.n_out;
     for (int job = warp; job < PP * nw; job += nwarps) {
-      const int pc = job / nw, k = job - pc * nw;
+      const int pc = ax.fnout.div(job), k = job - pc * nw;
       const Tc* row = tile + pc * ldt;
       Tc acc = Tc(0);
       for (int i = lane; i < ax.wlo; i += 32) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
@@ -295,7 +298,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     }
     // pack the regular part of two pencils into one complex sequence
     for (int w = tid; w < npairs * L; w += blockDim.x) {
-      const int pr = w / L, l = w - pr * L;
+      const int pr = ax.fL.div(w), l = w - pr * L;
       const Tc* ra = tile + (2 * pr) * ldt;
       const Tc* rb = ra + ldt;
       Tc va, vb;
@@ -316,7 +319,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     if (ax.kind == 1) {
       const int K = N / 2 + 1;
       for (int w = tid; w < npairs * K; w += blockDim.x) {
-        const int pr = w / K, k = w - pr * K;
+        const int pr = ax.fK.div(w), k = w - pr * K;
         Tc* ra = tile + (2 * pr) * ldt;
         Tc* rb = ra + ldt;
         const Cplx<Tc> zk = Z[(size_t)pr * F + k];
@@ -334,7 +337,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
       }
     } else {
       for (int w = tid; w < npairs * N; w += blockDim.x) {
-        const int pr = w / N, j = w - pr * N;
+        const int pr = ax.fN.div(w), j = w - pr * N;
         const Cplx<Tc> z = Z[(size_t)pr * F + j + 1];
         const Tc sc = __ldg(ax.post + j);
         tile[(2 * pr) * ldt + j] = -sc * z.y;
@@ -342,7 +345,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
       }
     }
     for (int w = tid; w < PP * ax.n_out; w += blockDim.x) {
-      const int pc = w / ax.n_out, k = w - pc * ax.n_out;
+      const int pc = ax.fnout.div(w), k = w - pc * ax.n_out;
       tile[pc * ldt + N + k] = outv[pc * kMaxNout + k];
     }
     __syncthreads();
@@ -355,14 +358,14 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     if (ax.rden != nullptr) {
       for (int e = tid; e < PP * m; e += blockDim.x) {
         int pc, i;
-        if (axis == 0) { pc = e / m; i = e - pc * m; }
-        else { i = e / PP; pc = e - i * PP; }
+        if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
+        else { i = e >> lpp; pc = e & (PP - 1); }
         if (pc >= g.nvalid) continue;  // padding pencils
         tile[pc * ldt + i] = tile[pc * ldt + i] * (Tc)__ldg(ax.rden + pbase[pc] + i * g.S);
       }
     } else {
       for (int e = tid; e < PP * m; e += blockDim.x) {
-        const int pc = e / m, i = e - pc * m;
+        const int pc = ax.fm.div(e), i = e - pc * m;
         if (pc >= g.nvalid) continue;  // padding pencils
         Tc den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
         if (dims.d == 3) den += __ldg(lamB + pib[pc]);
@@ -374,13 +377,13 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
 
   if (MODE == PM_BWD || MODE == PM_FUSED) {
     for (int w = tid; w < PP * ax.n_out; w += blockDim.x) {
-      const int pc = w / ax.n_out, k = w - pc * ax.n_out;
+      const int pc = ax.fnout.div(w), k = w - pc * ax.n_out;
       outv[pc * kMaxNout + k] = tile[pc * ldt + N + k];
     }
     if (ax.kind == 1) {
       const int K = N / 2 + 1;
       for (int w = tid; w < npairs * K; w += blockDim.x) {
-        const int pr = w / K, k = w - pr * K;
+        const int pr = ax.fK.div(w), k = w - pr * K;
         const Tc* za = tile + (2 * pr) * ldt;
         const Tc* zb = za + ldt;
         const Tc* t4 = ax.post + 4 * k;
@@ -401,7 +404,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     } else {
       const int n = N + 1;
       for (int w = tid; w < npairs * L; w += blockDim.x) {
-        const int pr = w / L, l = w - pr * L;
+        const int pr = ax.fL.div(w), l = w - pr * L;
         const Tc* za = tile + (2 * pr) * ldt;
         const Tc* zb = za + ldt;
         Tc va, vb;
@@ -422,7 +425,7 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     const Cplx<Tc>* Z = dft_block(bufA, bufB, npairs, ax);
     // scatter: x = V_reg w + W z_out
     for (int e = tid; e < PP * m; e += blockDim.x) {
-      const int pc = e / m, i = e - pc * m;
+      const int pc = ax.fm.div(e), i = e - pc * m;
       const int pr = pc >> 1;
       const bool isb = pc & 1;
       const Cplx<Tc>* Zp = Z + (size_t)pr * F;
@@ -459,8 +462,8 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
   double d0 = 0.0, d1 = 0.0;
   for (int e = tid; e < PP * m; e += blockDim.x) {
     int pc, i;
-    if (axis == 0) { pc = e / m; i = e - pc * m; }
-    else { i = e / PP; pc = e - i * PP; }
+    if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
+    else { i = e >> lpp; pc = e & (PP - 1); }
     if (pc < g.nvalid) {
       const long long off = pbase[pc] + i * g.S;
       const Tc v = tile[pc * ldt + i];
