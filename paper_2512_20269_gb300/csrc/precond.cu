@@ -283,18 +283,27 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
 
   const int N = ax.n_reg;
   if (MODE == PM_FWD || MODE == PM_FUSED) {
-    // remainder projections y_out = W^T r over the two support ranges of W
-    // (one warp per (pencil, column); the loops run over exactly n_out columns)
-    const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+    // remainder projections y_out = W^T r over the two support ranges of W:
+    // one group of 8 consecutive lanes per (pencil, column), reduced with three
+    // shuffles. Every lane runs the same number of rounds (inactive groups add
+    // zeros), so the full-warp shuffles never diverge.
     const int nw = ax.n_out;
-    for (int job = warp; job < PP * nw; job += nwarps) {
-      const int pc = ax.fnout.div(job), k = job - pc * nw;
-      const Tc* row = tile + pc * ldt;
+    const int grp = tid >> 3, sub = tid & 7, ngrp = blockDim.x >> 3;
+    for (int base = 0; base < PP * nw; base += ngrp) {
+      const int job = base + grp;
       Tc acc = Tc(0);
-      for (int i = lane; i < ax.wlo; i += 32) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
-      for (int i = ax.whi + lane; i < m; i += 32) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) outv[pc * kMaxNout + k] = acc;
+      int pc = 0, k = 0;
+      if (job < PP * nw) {
+        pc = ax.fnout.div(job);
+        k = job - pc * nw;
+        const Tc* row = tile + pc * ldt;
+        for (int i = sub; i < ax.wlo; i += 8) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
+        for (int i = ax.whi + sub; i < m; i += 8) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (sub == 0 && job < PP * nw) outv[pc * kMaxNout + k] = acc;
     }
     // pack the regular part of two pencils into one complex sequence
     for (int w = tid; w < npairs * L; w += blockDim.x) {
