@@ -6,10 +6,11 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - Problem (Section 2): d in {2,3} directions, n elements per direction on a
- *   uniform grid, degree p, maximal smoothness C^{p-1}, homogeneous Dirichlet
- *   data on both ends of every direction (D_k = {0,1}; other Dirichlet sets
- *   return IFFD_ERR_UNSUPPORTED). The basis of direction k has
- *   m_k = n_k + p - 2 functions; N = m_1 * ... * m_d.
+ *   uniform grid, degree p, maximal smoothness C^{p-1}; on each end of each
+ *   direction either homogeneous Dirichlet or natural (Neumann) conditions
+ *   (the Dirichlet set D_k of direction k is any subset of {0,1}; at least one
+ *   end of one direction must be Dirichlet, else A^ is singular). The basis of
+ *   direction k has m_k = n_k + p - |D_k| functions; N = m_1 * ... * m_d.
  * - Vectors are float64 arrays of N entries in DEVICE memory, owned by the
  *   caller, contiguous, with direction 1 (x) fastest -- the lexicographic order
  *   of eq. "tp-B-basis": entry (i_1, .., i_d) sits at i_1 + m_1 (i_2 + m_2 i_3).
@@ -41,7 +42,7 @@ typedef struct iffd_plan* iffd_handle;
 typedef enum {
   IFFD_OK = 0,
   IFFD_ERR_INVALID_ARG = 1,  /* null pointer, d not in {2,3}, p < 1, ... */
-  IFFD_ERR_UNSUPPORTED = 2,  /* n <= p, Dirichlet set other than {0,1}, size too large */
+  IFFD_ERR_UNSUPPORTED = 2,  /* n <= p, p > 16, n too small for the edge blocks, size too large */
   IFFD_ERR_SINGULAR = 3,     /* all-Neumann problem: A^ singular (Section 3) */
   IFFD_ERR_WORKSPACE = 4,    /* ws is NULL or misaligned */
   IFFD_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
@@ -104,11 +105,15 @@ int iffd_default_options(iffd_options* opt);
  * opt->precond == IFFD_PRECOND_EXACT_FD -- and uploads them to the current
  * device. FP64 IFFD plans also keep 1 / (sum of the eigenvalues of all
  * directions) for every DoF on the device (8 N bytes), so that the eigenvalue
- * scaling is a multiply. dirichlet[2k], dirichlet[2k+1] flag Dirichlet data at x_k = 0 / 1
- * (must be 1, 1). opt may be NULL (defaults). stream: see conventions.
- * Errors: INVALID_ARG, UNSUPPORTED (n <= p, p > 16, non-{0,1} Dirichlet set,
- * transform too large for shared memory), SINGULAR, CUDA. *out is set only
- * on success; release it with iffd_destroy. */
+ * scaling is a multiply. dirichlet[2k], dirichlet[2k+1] flag Dirichlet data
+ * at x_k = 0 / 1 (0: natural condition); the transform of each direction
+ * follows Table 1 for its (parity of p, D_k): DST-I / DST-II,III for
+ * D_k = {0,1}, the six other cases through a zero-padded DFT of length 2n or
+ * 4n. opt may be NULL (defaults). stream: see conventions.
+ * Errors: INVALID_ARG, UNSUPPORTED (n <= p, p > 16, n too small for the edge
+ * blocks of the special basis, transform too large for shared memory),
+ * SINGULAR (no Dirichlet end at all), CUDA. *out is set only on success;
+ * release it with iffd_destroy. */
 int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
                iffd_handle* out);
 
@@ -147,12 +152,11 @@ int iffd_get_dims(iffd_handle h, int axis, int* m, int* n_reg, int* n_out);
  *   M_band, K_band: m*(2p+1), band[i*(2p+1) + (j-i+p)] = M[i][j] (Section 3);
  *   lam: m, Lambda~ = [Lambda_reg (Lemma 3) | Lambda_out];
  *   dtilde: n_reg, diagonal of D~_reg (end of Section 6);
- *   VL: (p-1)*floor(p/2), left edge block of V_reg (row-major); the right block
- *       is its mirror image V_reg[m-1-r][n_reg-1-c] = VL[r][c] and the interior
- *       special function j is the B-spline j + floor((p-1)/2);
+ *   Vreg: m*n_reg, V_reg in the special basis of Section 6 (row-major, dense):
+ *       column j is special function j on the B-spline basis of S_{p,h,D};
  *   W: m*n_out, V_out Q_out (row-major). */
 int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double* lam, double* dtilde,
-                double* VL, double* W);
+                double* Vreg, double* W);
 
 /* Host-only variant of iffd_get_1d that needs no plan and no GPU: runs the
  * same 1D setup for n elements, degree p and the Dirichlet flags
@@ -160,7 +164,7 @@ int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double*
  * be NULL); every array pointer may be NULL (call once with NULLs to size the
  * buffers). Same layouts and errors as iffd_get_1d / iffd_setup. */
 int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
-                   double* K_band, double* lam, double* dtilde, double* VL, double* W);
+                   double* K_band, double* lam, double* dtilde, double* Vreg, double* W);
 
 /* Host-only: how the preconditioner passes of one direction carry its DST
  * (Table 1: DST-I for odd p, DST-II/III for even p, D = {0,1}) for the given

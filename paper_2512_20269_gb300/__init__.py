@@ -55,27 +55,30 @@ def host_axis(n: int, p: int, dirichlet=(1, 1)) -> dict:
     bw = 2 * p + 1
     out = {"m": m, "n_reg": nr, "n_out": no,
            "M_band": np.zeros(m * bw), "K_band": np.zeros(m * bw), "lam": np.zeros(m),
-           "dtilde": np.zeros(nr), "VL": np.zeros(max(1, (p - 1) * (p // 2))), "W": np.zeros(max(1, m * no))}
+           "dtilde": np.zeros(nr), "V_reg": np.zeros(m * nr), "W": np.zeros(max(1, m * no))}
     dp = lambda a: a.ctypes.data_as(_lib.c_double_p)
     check(lib.iffd_host_axis(n, p, dir_arr, None, None, None, dp(out["M_band"]), dp(out["K_band"]),
-                             dp(out["lam"]), dp(out["dtilde"]), dp(out["VL"]), dp(out["W"])), "iffd_host_axis")
+                             dp(out["lam"]), dp(out["dtilde"]), dp(out["V_reg"]), dp(out["W"])), "iffd_host_axis")
     out["M_band"] = out["M_band"].reshape(m, bw)
     out["K_band"] = out["K_band"].reshape(m, bw)
-    out["VL"] = out["VL"][:(p - 1) * (p // 2)].reshape(p - 1, p // 2)
+    out["V_reg"] = out["V_reg"].reshape(m, nr)
     out["W"] = out["W"][:m * no].reshape(m, no)
     return out
 
 
 class IFFDPlan:
-    """One problem (d, n per direction, p, Dirichlet on every face) on the current CUDA device.
+    """One problem (d, n per direction, p, boundary conditions) on the current CUDA device.
 
     Vectors are float64 CUDA tensors of N = prod(m_k) entries, direction 1 (x)
     fastest; a tensor of shape (m_d, ..., m_1) in C order has that layout.
+    `dirichlet`: one (at x_k = 0, at x_k = 1) flag pair per direction, 1 for
+    homogeneous Dirichlet data, 0 for the natural condition (default: Dirichlet
+    on every face).
     """
 
     def __init__(self, d: int, n, p: int, precision: str = "fp64", precond: str = "iffd", rtol: float = 1e-8,
                  maxit: int = 500, true_residual: bool = True, flexible: bool = False, coef: str = "const",
-                 coef_amp: float = 0.5, stream=None):
+                 coef_amp: float = 0.5, stream=None, dirichlet=None):
         import torch
         self._lib = _lib.load()
         n = [int(n)] * d if np.isscalar(n) else [int(x) for x in n]
@@ -92,7 +95,11 @@ class IFFDPlan:
         opt.coef_amp = coef_amp
         self.options = opt
         nn = (ctypes.c_int * d)(*n)
-        dd = (ctypes.c_int * (2 * d))(*([1] * (2 * d)))
+        flags = [1] * (2 * d) if dirichlet is None else [int(v) for pair in dirichlet for v in pair]
+        if len(flags) != 2 * d:
+            raise ValueError("dirichlet needs one (x=0, x=1) pair per direction")
+        self.dirichlet = [tuple(flags[2 * k:2 * k + 2]) for k in range(d)]
+        dd = (ctypes.c_int * (2 * d))(*flags)
         h = ctypes.c_void_p()
         check(self._lib.iffd_setup(d, nn, p, dd, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)),
               "iffd_setup")

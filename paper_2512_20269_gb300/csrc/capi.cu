@@ -57,7 +57,7 @@ static std::vector<T> cast_vec(const std::vector<double>& v) {
 }
 
 struct AxisOffsets {
-  size_t VL, W, lam, post, chirp, bhat;
+  size_t VL, VR, W, lam, post, chirp, bhat;
 };
 
 static bool register_radix(int r) { return r == 8 || r == 4 || r == 2 || r == 3 || r == 5; }
@@ -265,6 +265,11 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const cha
   t->o = A.o;
   t->nL = A.nL;
   t->rowsL = A.rowsL;
+  t->nR = A.nR;
+  t->rowsR = A.rowsR;
+  t->gq = A.gq;
+  t->gqc = A.gqc;
+  t->gqe = A.gqe;
   t->wlo = A.wlo;
   t->whi = A.whi;
   t->kind = A.kind;
@@ -272,6 +277,7 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const cha
   t->F = F;
   t->blu = (F > L) ? 1 : 0;
   t->VL = reinterpret_cast<const T*>(base + o.VL);
+  t->VR = reinterpret_cast<const T*>(base + o.VR);
   t->W = reinterpret_cast<const T*>(base + o.W);
   t->lam = reinterpret_cast<const T*>(base + o.lam);
   t->post = reinterpret_cast<const T*>(base + o.post);
@@ -329,13 +335,22 @@ static int pick_pp(int m, int F, size_t elt, int* PP, int* ldt) {
   return 1;
 }
 
+// Length of the complex DFT that carries one direction's transform (two
+// pencils per sequence): n_reg (DST-II/III, Makhoul order), 2 (n_reg + 1)
+// (DST-I, odd extension), 2 n q (generic Table 1 case, zero padding).
+static int dft_length(const Axis1D& A) {
+  if (A.kind == TK_DST23) return A.n_reg;
+  if (A.kind == TK_DST1) return 2 * (A.n_reg + 1);
+  return 2 * A.n * A.gq;
+}
+
 // Transform of one direction for one precision (element size elt): the DFT
 // length L, the FFT length F actually run (F > L: Bluestein) and the tile.
 // Bluestein is used when bluestein_length() picks it and its two length-F
 // buffers fit in shared memory; otherwise the direct length-L FFT. Returns 0
 // if neither fits.
 static int choose_transform(const Axis1D& A, size_t elt, int* L, int* F, int* PP, int* ldt) {
-  *L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
+  *L = dft_length(A);
   const int fb = bluestein_length(*L);
   if (fb > 0 && pick_pp(A.m, fb, elt, PP, ldt)) {
     *F = fb;
@@ -360,7 +375,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     // the DST of the regular part is carried by a complex DFT of length L
     // (two pencils per sequence; Makhoul order for DST-II/III, odd extension
     // for DST-I); lengths with large prime factors may run as Bluestein
-    pa[a].L = (A.kind == TK_DST23) ? A.n_reg : 2 * (A.n_reg + 1);
+    pa[a].L = dft_length(A);
     pa[a].F = bluestein_length(pa[a].L);
     std::vector<double> chirp, bhat;
     if (pa[a].F > 0) bluestein_tables(pa[a].L, pa[a].F, &chirp, &bhat);
@@ -376,25 +391,30 @@ static int build_plan(Plan* P, cudaStream_t stream) {
         pa[a].vars.push_back(std::move(fp));
       }
     }
-    const std::vector<double> post = post_table(A);
+    const std::vector<double> post = (A.kind == TK_GEN) ? A.gpost : post_table(A);
     pa[a].od.VL = tb.add_vec(A.VL);
+    pa[a].od.VR = tb.add_vec(A.VR);
     pa[a].od.W = tb.add_vec(A.W);
     pa[a].od.lam = tb.add_vec(A.lam);
     pa[a].od.post = tb.add_vec(post);
     pa[a].od.chirp = tb.add_vec(chirp);
     pa[a].od.bhat = tb.add_vec(bhat);
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
+    pa[a].of.VR = tb.add_vec(cast_vec<float>(A.VR));
     pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
     pa[a].of.lam = tb.add_vec(cast_vec<float>(A.lam));
     pa[a].of.post = tb.add_vec(cast_vec<float>(post));
     pa[a].of.chirp = tb.add_vec(cast_vec<float>(chirp));
     pa[a].of.bhat = tb.add_vec(cast_vec<float>(bhat));
-    // stiffness band tables; interior rows 2p-1 .. m-2p are symmetric Toeplitz
+    // stiffness band tables; interior rows are symmetric Toeplitz
     const int p = A.p, m = A.m, bw = 2 * p + 1;
     pa[a].Mb = tb.add_vec(A.Mband);
     pa[a].Kb = tb.add_vec(A.Kband);
     std::vector<double> mt(p + 1, 0.0), kt(p + 1, 0.0);
-    int ilo = 2 * p - 1, ihi = m - 2 * p + 1;
+    // rows coupled to a B-spline with repeated end knots are general band rows:
+    // the first 2p-1 rows at a Dirichlet end (its end B-spline is removed), 2p
+    // rows at a natural end
+    int ilo = 2 * p - (A.dir0 ? 1 : 0), ihi = m - 2 * p + (A.dir1 ? 1 : 0);
     if (ihi <= ilo) { ilo = 0; ihi = 0; }
     else {
       const int mid = (ilo + ihi) / 2;
@@ -888,7 +908,18 @@ int iffd_get_dims(iffd_handle h, int axis, int* m, int* n_reg, int* n_out) {
   return IFFD_OK;
 }
 
-int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double* lam, double* dtilde, double* VL,
+// Dense V_reg (m x n_reg, row-major) from the edge blocks and the interior map.
+static void dense_vreg(const Axis1D& A, double* V) {
+  const int m = A.m, nr = A.n_reg;
+  std::memset(V, 0, sizeof(double) * (size_t)m * nr);
+  for (int r = 0; r < A.rowsL; ++r)
+    for (int c = 0; c < A.nL; ++c) V[(size_t)r * nr + c] = A.VL[(size_t)r * A.nL + c];
+  for (int r = 0; r < A.rowsR; ++r)
+    for (int c = 0; c < A.nR; ++c) V[(size_t)(m - 1 - r) * nr + (nr - 1 - c)] = A.VR[(size_t)r * A.nR + c];
+  for (int j = A.nL; j < nr - A.nR; ++j) V[(size_t)(j + A.o) * nr + j] = 1.0;
+}
+
+int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double* lam, double* dtilde, double* Vreg,
                 double* W) {
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   const Axis1D& A = h->P.host[axis];
@@ -899,13 +930,13 @@ int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double*
   cp(K_band, A.Kband);
   cp(lam, A.lam);
   cp(dtilde, A.dtilde);
-  cp(VL, A.VL);
+  if (Vreg) dense_vreg(A, Vreg);
   cp(W, A.W);
   return IFFD_OK;
 }
 
 int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
-                   double* K_band, double* lam, double* dtilde, double* VL, double* W) {
+                   double* K_band, double* lam, double* dtilde, double* Vreg, double* W) {
   g_err.clear();
   if (!dirichlet) return fail(IFFD_ERR_INVALID_ARG, "dirichlet is NULL");
   Axis1D A;
@@ -921,7 +952,7 @@ int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* 
   cp(K_band, A.Kband);
   cp(lam, A.lam);
   cp(dtilde, A.dtilde);
-  cp(VL, A.VL);
+  if (Vreg) dense_vreg(A, Vreg);
   cp(W, A.W);
   return IFFD_OK;
 }

@@ -68,17 +68,21 @@ struct Dims {
 // Per-direction tables consumed by the transform passes (device pointers).
 template <typename T>
 struct AxisTab {
-  int m, n_reg, n_out, p, o, nL, rowsL, wlo, whi, kind;
+  int m, n_reg, n_out, p, o, nL, rowsL, nR, rowsR, wlo, whi, kind;
+  int gq, gqc, gqe;  // generic transform (kind 2): frequencies gq j - gqe (FWD), gq i - gqc (BWD)
   // L: length of the complex DFT that carries the DST (two pencils per
   // sequence). F: length of the FFT actually run, = L, or, when blu is set, the
   // 5-smooth Bluestein length F >= 2L - 1; shared-memory sequences have stride F.
   int L, F, blu, nst;
   int radix[kMaxStages];  // stages of the length-F FFT
   int twoff[kMaxStages];
-  const T* VL;     // rowsL * nL (row-major); the right block is its mirror image
+  const T* VL;     // rowsL * nL (row-major), left edge block
+  const T* VR;     // rowsR * nR (row-major), right edge block in mirrored form:
+                   // V_reg[m-1-r][n_reg-1-c] = VR[r][c]
   const T* W;      // m * n_out (row-major) = V_out Q_out
   const T* lam;    // m: Lambda_reg then Lambda_out
-  const T* post;   // DST-II/III: 4 per k = 0..N/2;  DST-I: n_reg values 1/(2 D~)
+  const T* post;   // DST-II/III: 4 per k = 0..N/2;  DST-I: n_reg values 1/(2 D~);
+                   // generic: w_j/D~_j (2 N), v_i (2 N), 1/D~_j (N)
   const T* tw;     // complex FFT twiddles (interleaved), per stage offsets twoff
   // invariant divisors of the index arithmetic: m, L, F, n_reg, n_reg/2 + 1,
   // n_out, and per FFT stage F / radix and the stage's Ns

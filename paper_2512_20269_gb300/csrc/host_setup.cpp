@@ -1,6 +1,7 @@
 // Host-side univariate IFFD setup (Sections 2, 4, 5 and 6 of the paper).
 //
-// Builds, for one parametric direction with D = {0,1}:
+// Builds, for one parametric direction with Dirichlet set D (any subset of
+// {0, 1}; the eight (parity of p, D) cases of Table 1):
 //   * banded M and K of S_{p,h,D} by Cox-de Boor + (p+1)-point Gauss (Section 2);
 //   * the edge blocks of V_reg in the special basis of Section 6 (eq.
 //     "special_basis"), obtained exactly by Boehm knot insertion: inserting the
@@ -11,8 +12,11 @@
 //     of eq. "eigendecomposition_out" by Cholesky + cyclic Jacobi;
 //   * Lambda_reg from Lemma 3 (with the factor (2 - 2cos t)/h^2 written as
 //     4 sin^2(t/2)/h^2) and D~_reg = D_reg Theta from the periodic symbols:
-//     D~_jj^2 = sigma_M(h alpha_j) * mean_i sin^2(x_i alpha_j), which equals the
-//     paper's numeric definition (U^T V_reg^T M V_reg U)^{1/2}.
+//     D~_jj^2 = sigma_M(h alpha_j) * mean_i sin^2(x_i alpha_j + beta), which
+//     equals the paper's numeric definition (U^T V_reg^T M V_reg U)^{1/2};
+//   * the parameters of the generic transform of the six cases other than
+//     D = {0,1}: U_ij = sin(pi (i - c)(j - e) / n + beta) (Table 1), evaluated
+//     through a zero-padded DFT of length 2n (c, e integers) or 4n.
 #include "host_setup.h"
 
 #include <algorithm>
@@ -288,10 +292,12 @@ void insert_knot(std::vector<double>* kn, std::vector<double>* c, int p, double 
   *c = nc;
 }
 
-// Banded M and K of S_{p,h,{0,1}} (B-splines 0 and n+p-1 removed), with an
-// optional weight w(x) under both integrals; (p+1)-point Gauss per element.
-void assemble_bands(int n, int p, double (*w)(double), std::vector<double>* Mb, std::vector<double>* Kb) {
-  const int m = n + p - 2, bw = 2 * p + 1, F = n + p;
+// Banded M and K of S_{p,h,D} (B-spline 0 removed if dir0, n+p-1 if dir1),
+// with an optional weight w(x) under both integrals; (p+1)-point Gauss per element.
+void assemble_bands(int n, int p, bool dir0, bool dir1, double (*w)(double), std::vector<double>* Mb,
+                    std::vector<double>* Kb) {
+  const int m = n + p - (dir0 ? 1 : 0) - (dir1 ? 1 : 0), bw = 2 * p + 1, F = n + p;
+  const int s0 = dir0 ? 1 : 0;
   const std::vector<double> kn = open_knots(n, p);
   std::vector<double> gx, gw;
   gauss_legendre(p + 1, &gx, &gw);
@@ -319,8 +325,8 @@ void assemble_bands(int n, int p, double (*w)(double), std::vector<double>* Mb, 
     for (int d = 0; d < bw; ++d) {
       const int j = i + d - p;
       if (j < 0 || j >= m) continue;
-      (*Mb)[(size_t)i * bw + d] = Mf[(size_t)(i + 1) * bw + d];
-      (*Kb)[(size_t)i * bw + d] = Kf[(size_t)(i + 1) * bw + d];
+      (*Mb)[(size_t)i * bw + d] = Mf[(size_t)(i + s0) * bw + d];
+      (*Kb)[(size_t)i * bw + d] = Kf[(size_t)(i + s0) * bw + d];
     }
 }
 
@@ -369,74 +375,171 @@ bool fft_factor(int L, std::vector<int>* radices) {
   return true;
 }
 
+namespace {
+
+// Edge block of the special basis at the end x = 0 for one end type (Section
+// 6, eq. "special_basis"): Dirichlet (dir) B~_i - B~_{dp-i}, i = 1..floor(p/2);
+// otherwise, p even, B~_i + B~_{1-i}, i = 1..p/2, and p odd, B~_0 and
+// B~_i + B~_{-i}, i = 1..(p-1)/2. Each combination of cardinal B-splines is
+// written in the open-knot basis exactly by inserting the knot 0 p times into
+// the uniform knot vector (Boehm). V[r * nfun + c]: coefficient of function c
+// on the reduced basis function r counted from the end (the B-spline at the
+// end itself is removed when dir). The right end is the mirror image.
+std::string edge_block(int p, bool dir, int* nfun, int* rows, std::vector<double>* V) {
+  const int half = p / 2;
+  const int dp = (p % 2 == 1) ? 0 : 1;
+  std::vector<std::vector<std::pair<double, int>>> combos;
+  if (dir) {
+    for (int i = 1; i <= half; ++i) combos.push_back({{1.0, i}, {-1.0, dp - i}});
+  } else if (p % 2 == 0) {
+    for (int i = 1; i <= half; ++i) combos.push_back({{1.0, i}, {1.0, 1 - i}});
+  } else {
+    combos.push_back({{1.0, 0}});
+    for (int i = 1; i <= (p - 1) / 2; ++i) combos.push_back({{1.0, i}, {1.0, -i}});
+  }
+  *nfun = (int)combos.size();
+  const int J0 = -3 * p - 4, J1 = 3 * p + 4;
+  const int s0 = dir ? 1 : 0;
+  std::vector<std::vector<double>> cols;
+  int maxrow = -1;
+  for (const auto& cb : combos) {
+    std::vector<double> knots;
+    for (int j = J0; j <= J1; ++j) knots.push_back(double(j));
+    std::vector<double> coef(knots.size() - p - 1, 0.0);
+    // B~_k is the uniform B-spline starting at knot k - floor(p/2) - 1
+    for (const auto& t : cb) coef[(t.second - half - 1) - J0] += t.first;
+    for (int r = 0; r < p; ++r) insert_knot(&knots, &coef, p, 0.0);
+    int z = 0;
+    while (knots[z] != 0.0) ++z;
+    // open B-spline with full index jf (counted from x = 0) <-> coef[z + jf]
+    if (dir && std::fabs(coef[z]) > 1e-13) return "special basis function does not vanish at a Dirichlet end";
+    std::vector<double> col;
+    for (int jf = s0; jf <= 2 * p + 2; ++jf) col.push_back(coef[z + jf]);
+    for (int r = 0; r < (int)col.size(); ++r)
+      if (std::fabs(col[r]) > 1e-13) maxrow = std::max(maxrow, r);
+    cols.push_back(col);
+  }
+  *rows = maxrow + 1;
+  if (*rows > 2 * p) return "special basis edge function is not local";
+  V->assign((size_t)(*rows) * (*nfun), 0.0);
+  for (int c = 0; c < *nfun; ++c)
+    for (int r = 0; r < *rows; ++r) (*V)[(size_t)r * (*nfun) + c] = cols[c][r];
+  return "";
+}
+
+// Rows of the constraint matrix G of eq. "reg_space" for the end x = 0 on the
+// reduced basis (counted from the end): derivatives of orders 2, 4, .. (Dirichlet
+// end) or 1, 3, .. (otherwise) up to p - 1 of the open B-splines at 0.
+void end_constraints(const std::vector<double>& kn, int p, bool dir, int m, std::vector<std::vector<double>>* G) {
+  std::vector<double> d(p + 1);
+  const int s0 = dir ? 1 : 0;
+  for (int ord = dir ? 2 : 1; ord <= p - 1; ord += 2) {
+    bspline_local(kn, p, 0, 0.0, ord, d.data());
+    std::vector<double> row(m, 0.0);
+    for (int jf = s0; jf <= p && jf - s0 < m; ++jf) row[jf - s0] = d[jf];
+    G->push_back(row);
+  }
+}
+
+}  // namespace
+
 std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
   std::ostringstream err;
   if (p < 1 || p > 16) { err << "degree p=" << p << " outside 1..16"; return err.str(); }
   if (n <= p) { err << "n=" << n << " must exceed p=" << p; return err.str(); }
-  if (!(dir0 && dir1)) return "only the Dirichlet set D = {0,1} is implemented on the device path";
   A->n = n;
   A->p = p;
-  A->m = n + p - 2;
+  A->dir0 = dir0;
+  A->dir1 = dir1;
+  A->m = n + p - (dir0 ? 1 : 0) - (dir1 ? 1 : 0);
   const int m = A->m;
-  const int bw = 2 * p + 1;
-  A->kind = (p % 2 == 1) ? TK_DST1 : TK_DST23;
-  A->n_reg = (p % 2 == 1) ? n - 1 : n;
-  A->n_out = m - A->n_reg;
 
-  // ---- banded M, K of S_{p,h}, Dirichlet B-splines 0 and n+p-1 removed
-  assemble_bands(n, p, nullptr, &A->Mband, &A->Kband);
+  // ---- banded M, K of S_{p,h,D}
+  assemble_bands(n, p, dir0, dir1, nullptr, &A->Mband, &A->Kband);
   const std::vector<double> kn = open_knots(n, p);
 
-  // ---- special basis edge block (Section 6, D = {0,1}) by knot insertion
-  const int half = p / 2;                 // floor(p/2)
-  const int dp = (p % 2 == 1) ? 0 : 1;    // delta_p
-  A->nL = half;
-  A->rowsL = p - 1;
-  A->o = (p - 1) / 2;
-  A->VL.assign((size_t)A->rowsL * A->nL, 0.0);
-  {
-    // cardinal knots tau_j = j (unit spacing; coefficients are scale free)
-    const int J0 = -3 * p - 4, J1 = 3 * p + 4;
-    for (int c = 0; c < A->nL; ++c) {
-      const int i = c + 1;
-      std::vector<double> knots;
-      for (int j = J0; j <= J1; ++j) knots.push_back(double(j));
-      std::vector<double> coef(knots.size() - p - 1, 0.0);
-      // B~_k is the uniform B-spline starting at knot k - floor(p/2) - 1
-      coef[(i - half - 1) - J0] += 1.0;
-      coef[(dp - i - half - 1) - J0] -= 1.0;
-      for (int r = 0; r < p; ++r) insert_knot(&knots, &coef, p, 0.0);
-      int z = 0;
-      while (knots[z] != 0.0) ++z;
-      // open B-spline with full index jf  <->  coef[z + jf]; reduced row = jf - 1
-      if (std::fabs(coef[z]) > 1e-13) {
-        err << "special basis function " << c << " does not vanish at 0";
-        return err.str();
-      }
-      for (int jf = p; jf < p + 3; ++jf)
-        if (std::fabs(coef[z + jf]) > 1e-13) {
-          err << "special basis function " << c << " is not local";
-          return err.str();
-        }
-      for (int r = 0; r < A->rowsL; ++r) A->VL[(size_t)r * A->nL + c] = coef[z + r + 1];
-    }
-  }
+  // ---- special basis: edge blocks (knot insertion) and the interior functions
+  std::string e = edge_block(p, dir0, &A->nL, &A->rowsL, &A->VL);
+  if (!e.empty()) return e;
+  e = edge_block(p, dir1, &A->nR, &A->rowsR, &A->VR);
+  if (!e.empty()) return e;
+  // interior special function i = floor(p/2)+1 .. n-ceil(p/2) is the open
+  // B-spline with full index i + floor((p-1)/2) (p odd) or i + p/2 - 1 (p even)
+  const int n_int = n - p;
+  A->n_reg = A->nL + n_int + A->nR;
+  A->n_out = m - A->n_reg;
+  const int first_full = (p / 2 + 1) + ((p % 2 == 1) ? (p - 1) / 2 : p / 2 - 1);
+  A->o = first_full - (dir0 ? 1 : 0) - A->nL;
+  // the device passes give every row of V_reg to one region: left block,
+  // interior, or right block
+  if (A->rowsL > A->nL + A->o || m - A->rowsR < A->nL + A->o + n_int || A->rowsL > m - A->rowsR)
+    return "n too small for the device layout of the special basis";
+
+  // ---- Table 1: nodes x_i = (i - c) h, alpha_j = (j - e) pi, beta
+  const bool odd = (p % 2 == 1);
+  double c, ee, beta;
+  if (odd) c = dir0 ? 0.0 : 1.0;
+  else c = 0.5;
+  if (dir0 && dir1) ee = 0.0;
+  else if (dir0 || dir1) ee = 0.5;
+  else ee = 1.0;
+  beta = (dir1 && !dir0) || (!dir0 && !dir1) ? 0.5 * kPi : 0.0;
+  if (dir0 && dir1) A->kind = odd ? TK_DST1 : TK_DST23;
+  else A->kind = TK_GEN;
+  A->gq = (c != std::floor(c) || ee != std::floor(ee)) ? 2 : 1;
+  A->gqc = (int)std::lround(A->gq * c);
+  A->gqe = (int)std::lround(A->gq * ee);
 
   // ---- Lambda_reg (Lemma 3) and D~_reg (periodic symbols)
   const double h = 1.0 / n;
   A->lam.assign(m, 0.0);
   A->dtilde.assign(A->n_reg, 0.0);
   for (int j = 0; j < A->n_reg; ++j) {
-    const double t = (j + 1) * kPi * h;  // h alpha_j, alpha_j = j pi (1-based j)
+    const double alpha = (j + 1 - ee) * kPi;
+    const double t = h * alpha;
     double sM = cardinal_half(2 * p + 1, 0), sK = cardinal_half(2 * p - 1, 0);
     for (int k = 1; k <= p; ++k) sM += 2.0 * cardinal_half(2 * p + 1, 2 * k) * std::cos(k * t);
     for (int k = 1; k <= p - 1; ++k) sK += 2.0 * cardinal_half(2 * p - 1, 2 * k) * std::cos(k * t);
     const double s2 = std::sin(0.5 * t);
     A->lam[j] = 4.0 * s2 * s2 / (h * h) * sK / sM;
-    // mean of sin^2(x_i alpha_j) over the 4n periodic nodes: 1/2, except the
-    // alternating mode h alpha_j = pi of even degree where it is 1.
-    const double meanq2 = (dp == 1 && j + 1 == n) ? 1.0 : 0.5;
+    // mean of sin^2(x_i alpha_j + beta) over the 4n periodic nodes x_i = (i - c') h,
+    // i = -2n+1..2n (c' = 0 for odd p, 1/2 for even p): 1/2 unless h alpha_j is a
+    // multiple of pi, where the sum is taken exactly
+    double meanq2 = 0.5;
+    const double jm = j + 1 - ee;
+    if (std::fabs(jm) < 1e-12 || std::fabs(jm - n) < 1e-12) {
+      double acc = 0.0;
+      for (int i = -2 * n + 1; i <= 2 * n; ++i) {
+        const double x = (i - (odd ? 0.0 : 0.5)) * h;
+        const double q = std::sin(x * alpha + beta);
+        acc += q * q;
+      }
+      meanq2 = acc / (4.0 * n);
+    }
     A->dtilde[j] = std::sqrt(sM * meanq2);
+    if (!(A->dtilde[j] > 0.0)) return "degenerate regular mode (D~ = 0)";
+  }
+  // generic transform (Table 1 cases other than D = {0,1}): with
+  // T(k) = sum_l s_l exp(+2 pi i l k / L), L = 2 n q, of the zero-padded real
+  // sequence s (entries l = 1..n_reg), sin(theta (i - c)(j - e) + beta) gives
+  //   FWD  y_j = Im(w_j T(q (j - e))) / D~_j,  w_j = exp(i (beta - pi c (j - e) / n)),
+  //   BWD  x_i = Im(v_i T(q (i - c))),         v_i = exp(i (beta - pi e (i - c) / n)),
+  // and the BWD input is pre-scaled by 1 / D~_j. Two real pencils share one
+  // complex sequence; separating them costs a factor 1/2, folded in here.
+  A->gpost.clear();
+  if (A->kind == TK_GEN) {
+    const int N = A->n_reg;
+    for (int j = 1; j <= N; ++j) {
+      const double ang = beta - kPi * c * (j - ee) / n;
+      A->gpost.push_back(0.5 * std::cos(ang) / A->dtilde[j - 1]);
+      A->gpost.push_back(0.5 * std::sin(ang) / A->dtilde[j - 1]);
+    }
+    for (int i = 1; i <= N; ++i) {
+      const double ang = beta - kPi * ee * (i - c) / n;
+      A->gpost.push_back(0.5 * std::cos(ang));
+      A->gpost.push_back(0.5 * std::sin(ang));
+    }
+    for (int j = 1; j <= N; ++j) A->gpost.push_back(1.0 / A->dtilde[j - 1]);
   }
 
   // ---- remainder space: V_out = M^{-1} G^T, then Q_out, Lambda_out
@@ -445,32 +548,32 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
   A->wlo = 0;
   A->whi = m;
   if (no > 0) {
-    const int nlo = no / 2;  // constraints per end (D = {0,1}: even orders 2..p-1)
-    std::vector<std::vector<double>> G;  // rows over the reduced basis
-    std::vector<double> d(p + 1);
-    for (int kk = 1; kk <= nlo; ++kk) {
-      bspline_local(kn, p, 0, 0.0, 2 * kk, d.data());
-      std::vector<double> row(m, 0.0);
-      for (int jf = 1; jf <= p && jf - 1 < m; ++jf) row[jf - 1] = d[jf];
-      G.push_back(row);
-    }
-    // orthonormalise the left rows (modified Gram-Schmidt), mirror to the right
-    for (int a = 0; a < nlo; ++a) {
-      for (int b = 0; b < a; ++b) {
-        double dot = 0;
-        for (int i = 0; i < m; ++i) dot += G[a][i] * G[b][i];
-        for (int i = 0; i < m; ++i) G[a][i] -= dot * G[b][i];
+    std::vector<std::vector<double>> G, GR;  // rows over the reduced basis
+    end_constraints(kn, p, dir0, m, &G);
+    end_constraints(kn, p, dir1, m, &GR);
+    // orthonormalise each end's rows (modified Gram-Schmidt; derivative values
+    // scale like h^-k), mirror the right end's rows
+    auto orthonormalise = [&](std::vector<std::vector<double>>& R) {
+      for (size_t a = 0; a < R.size(); ++a) {
+        for (size_t b = 0; b < a; ++b) {
+          double dot = 0;
+          for (int i = 0; i < m; ++i) dot += R[a][i] * R[b][i];
+          for (int i = 0; i < m; ++i) R[a][i] -= dot * R[b][i];
+        }
+        double nr = 0;
+        for (int i = 0; i < m; ++i) nr += R[a][i] * R[a][i];
+        nr = std::sqrt(nr);
+        for (int i = 0; i < m; ++i) R[a][i] /= nr;
       }
-      double nr = 0;
-      for (int i = 0; i < m; ++i) nr += G[a][i] * G[a][i];
-      nr = std::sqrt(nr);
-      for (int i = 0; i < m; ++i) G[a][i] /= nr;
-    }
-    for (int a = 0; a < nlo; ++a) {
+    };
+    orthonormalise(G);
+    orthonormalise(GR);
+    for (const auto& r : GR) {
       std::vector<double> row(m, 0.0);
-      for (int i = 0; i < m; ++i) row[m - 1 - i] = G[a][i];
+      for (int i = 0; i < m; ++i) row[m - 1 - i] = r[i];
       G.push_back(row);
     }
+    if ((int)G.size() != no) return "constraint count differs from n_out";
     std::vector<double> Lm;
     if (!band_cholesky(A->Mband, m, p, &Lm)) return "mass matrix is not positive definite";
     std::vector<double> Vout((size_t)m * no);  // column-major: Vout[i + k*m]
@@ -532,7 +635,9 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
   return "";
 }
 
-void build_weighted_bands(Axis1D* A) { assemble_bands(A->n, A->p, sin_2pi, &A->Msband, &A->Ksband); }
+void build_weighted_bands(Axis1D* A) {
+  assemble_bands(A->n, A->p, A->dir0, A->dir1, sin_2pi, &A->Msband, &A->Ksband);
+}
 
 std::string exact_fd_axis(const Axis1D& ax, std::vector<double>* Q, std::vector<double>* lam) {
   const int m = ax.m, p = ax.p, bw = 2 * p + 1;

@@ -13,19 +13,29 @@ namespace iffd {
 enum TransformKind : int {
   TK_DST1 = 0,   // p odd, D = {0,1}: U_reg = DST-I, U_reg^T = DST-I
   TK_DST23 = 1,  // p even, D = {0,1}: U_reg = DST-III, U_reg^T = DST-II
+  TK_GEN = 2,    // the other six cases of Table 1 (DST-III/IV, DCT-I..IV types):
+                 // U_ij = sin(pi (i - c)(j - e) / n + beta) via a zero-padded DFT
 };
 
 struct Axis1D {
   int n = 0, p = 0;          // elements, degree
-  int m = 0;                 // dim S_{p,h,D} = n + p - 2
+  bool dir0 = true, dir1 = true;  // Dirichlet data at x = 0 / x = 1
+  int m = 0;                 // dim S_{p,h,D} = n + p - |D|
   int n_reg = 0, n_out = 0;  // eq. "reg_space_dim"
   int kind = TK_DST23;
+  // TK_GEN: DFT length 2 n gq; frequency of output j is gq j - gqe (FWD) and
+  // of output i is gq i - gqc (BWD), i.e. q (j - e) and q (i - c).
+  int gq = 1, gqc = 0, gqe = 0;
+  // TK_GEN post factors: w_j / D~_j (2 n_reg, complex), v_i (2 n_reg, complex),
+  // 1 / D~_j (n_reg)
+  std::vector<double> gpost;
   // V_reg (Section 4): rows 0..rowsL-1 x cols 0..nL-1 is the left edge block,
-  // the interior special function j (nL <= j < n_reg - nL) is the B-spline with
-  // reduced index j + o, and the right edge block is the mirror image:
-  // V_reg[m-1-r][n_reg-1-c] = VL[r][c].
-  int nL = 0, rowsL = 0, o = 0;
+  // the interior special function j (nL <= j < n_reg - nR) is the B-spline with
+  // reduced index j + o, and the right edge block is the mirror image of VR:
+  // V_reg[m-1-r][n_reg-1-c] = VR[r][c] (c < nR, r < rowsR).
+  int nL = 0, rowsL = 0, o = 0, nR = 0, rowsR = 0;
   std::vector<double> VL;    // rowsL * nL, row-major
+  std::vector<double> VR;    // rowsR * nR, row-major (left-end form of the right block)
   // W = V_out Q_out (m x n_out, row-major), significant only on rows
   // [0, wlo) and [whi, m); the rows in between are below 1e-17 of max |W|.
   std::vector<double> W;

@@ -222,6 +222,19 @@ __device__ Cplx<T>* dft_block(Cplx<T>* bufA, Cplx<T>* bufB, int npairs, const Ax
   return S;
 }
 
+// Generic Table 1 transform (kind 2): output of frequency k of the two real
+// pencils a (x) and b (y) packed in the length-L sequence Zp,
+// T(k) = sum_l s_l exp(+2 pi i l k / L), times 2; Im(f T(k)) for the complex
+// post factor f (which carries the 1/2 of the separation).
+template <typename T>
+__device__ __forceinline__ void gen_im(const Cplx<T>* Zp, int k, int L, T fx, T fy, T& ya, T& yb) {
+  const Cplx<T> z1 = Zp[k == 0 ? 0 : L - k], z2 = Zp[k];
+  const T tax = z1.x + z2.x, tay = z1.y - z2.y;  // 2 T_a(k)
+  const T tbx = z1.y + z2.y, tby = z2.x - z1.x;  // 2 T_b(k)
+  ya = fma(fx, tay, fy * tax);
+  yb = fma(fx, tby, fy * tbx);
+}
+
 // y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1].
 template <typename T>
 __device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
@@ -230,10 +243,10 @@ __device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& a
     for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + i), row[r], s);
     return s;
   }
-  if (i >= ax.n_reg - ax.nL) {
+  if (i >= ax.n_reg - ax.nR) {
     const int c = ax.n_reg - 1 - i;
     T s = T(0);
-    for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + c), row[ax.m - 1 - r], s);
+    for (int r = 0; r < ax.rowsR; ++r) s = fma(__ldg(ax.VR + r * ax.nR + c), row[ax.m - 1 - r], s);
     return s;
   }
   return row[i + ax.o];
@@ -315,6 +328,9 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
         const int i = (l < (N + 1) / 2) ? 2 * l : 2 * (N - 1 - l) + 1;
         va = neg_if(reg_gather(ra, i, ax), i & 1);
         vb = neg_if(reg_gather(rb, i, ax), i & 1);
+      } else if (ax.kind == 2) {  // generic: y_reg at positions 1..N, zero padding
+        if (l >= 1 && l <= N) { va = reg_gather(ra, l - 1, ax); vb = reg_gather(rb, l - 1, ax); }
+        else { va = Tc(0); vb = Tc(0); }
       } else {  // DST-I: odd extension of length L = 2n
         const int n = N + 1;
         if (l == 0 || l == n) { va = Tc(0); vb = Tc(0); }
@@ -343,6 +359,15 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
           ra[k - 1] = fma(C, Ar, -E * Ai);
           rb[k - 1] = fma(C, Br, -E * Bi);
         }
+      }
+    } else if (ax.kind == 2) {
+      for (int w = tid; w < npairs * N; w += blockDim.x) {
+        const int pr = ax.fN.div(w), j = w - pr * N;
+        Tc ya, yb;
+        gen_im(Z + (size_t)pr * F, ax.gq * (j + 1) - ax.gqe, L, __ldg(ax.post + 2 * j), __ldg(ax.post + 2 * j + 1),
+               ya, yb);
+        tile[(2 * pr) * ldt + j] = ya;
+        tile[(2 * pr + 1) * ldt + j] = yb;
       }
     } else {
       for (int w = tid; w < npairs * N; w += blockDim.x) {
@@ -410,6 +435,19 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
           G[N - k] = {ar + bi, br - ai};
         }
       }
+    } else if (ax.kind == 2) {
+      for (int w = tid; w < npairs * L; w += blockDim.x) {
+        const int pr = ax.fL.div(w), l = w - pr * L;
+        const Tc* za = tile + (2 * pr) * ldt;
+        const Tc* zb = za + ldt;
+        Tc va = Tc(0), vb = Tc(0);
+        if (l >= 1 && l <= N) {
+          const Tc sc = __ldg(ax.post + 4 * N + l - 1);  // 1 / D~
+          va = sc * za[l - 1];
+          vb = sc * zb[l - 1];
+        }
+        bufA[(size_t)pr * F + l] = {va, vb};
+      }
     } else {
       const int n = N + 1;
       for (int w = tid; w < npairs * L; w += blockDim.x) {
@@ -443,6 +481,11 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
           const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
           const Cplx<Tc> z = Zp[l];
           return neg_if(isb ? z.y : z.x, j & 1);
+        } else if (ax.kind == 2) {
+          Tc xa, xb;
+          gen_im(Zp, ax.gq * (j + 1) - ax.gqc, L, __ldg(ax.post + 2 * N + 2 * j), __ldg(ax.post + 2 * N + 2 * j + 1),
+                 xa, xb);
+          return isb ? xb : xa;
         } else {
           const Cplx<Tc> z = Zp[j + 1];
           return isb ? z.x : -z.y;
@@ -452,10 +495,10 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
       if (i < ax.rowsL) {
         x = Tc(0);
         for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
-      } else if (i >= m - ax.rowsL) {
+      } else if (i >= m - ax.rowsR) {
         const int r = m - 1 - i;
         x = Tc(0);
-        for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + r * ax.nL + c), wreg(N - 1 - c), x);
+        for (int c = 0; c < ax.nR; ++c) x = fma(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
       } else {
         x = wreg(i - ax.o);
       }

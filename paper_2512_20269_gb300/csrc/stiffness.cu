@@ -7,7 +7,7 @@
 // (2D: the first stage runs on y and the last on x.) Seven banded products in
 // 3D, four in 2D. Interior rows of M and K are symmetric Toeplitz (uniform
 // knots), so one set of pair sums u_{i-k} + u_{i+k} feeds both M and K; the
-// first and last 2p-1 rows use the stored band.
+// boundary rows (2p-1 at a Dirichlet end, 2p at a natural end) use the stored band.
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -82,7 +82,7 @@ __device__ __forceinline__ void tile_coords(int axis, int e, int PP, int m, int&
 }
 
 // Work split of the compute loops: first every interior (Toeplitz) row of
-// every pencil, then the 2(2p-1) boundary rows, so that no warp mixes the two
+// every pencil, then the boundary rows, so that no warp mixes the two
 // code paths. Item e of a region of nr rows starting at row r0:
 __device__ __forceinline__ void region_coords(int axis, int e, int PP, int nr, int& pc, int& r) {
   if (axis == 0) { pc = e / nr; r = e - pc * nr; }
