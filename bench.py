@@ -334,12 +334,14 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
         from paper_2512_20269_gb300.serving import Server
         reqs = inputs.serving_requests()
         cap = args.serve_cap_dofs if args.serve_cap_dofs > 0 else None
-        srv = Server(budget_bytes=150 * (1 << 30), precision="fp32", iterations_per_step=2, max_inflight_dofs=cap)
+        srv = Server(budget_bytes=150 * (1 << 30), precision="fp32", iterations_per_step=args.serve_iters,
+                     max_inflight_dofs=cap)
         st = srv.run(reqs, max_wall_s=args.serve_seconds)
         line.update({"value": st["dof_per_s"], "ms_per_step": None, "dtype": "f64",
                      "config": {"workload": "serving_poisson_2000rps", "rate_rps": 2000, "arrival_window_s": 60,
                                 "run_wall_s": args.serve_seconds, "budget_bytes": 150 * (1 << 30),
-                                "precond": "IFFD, FP32 transforms", "seed": 4, "max_inflight_dofs": cap},
+                                "precond": "IFFD, FP32 transforms", "seed": 4, "max_inflight_dofs": cap,
+                                "iterations_per_step": args.serve_iters},
                      "serving": st})
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -359,6 +361,7 @@ def main():
                          "variable coefficient; batched: 512 uneven 3D problems; serving: Poisson request stream")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-autotune", action="store_true", help="batched: default launch geometry")
+    ap.add_argument("--serve-iters", type=int, default=2, help="serving: PCG iterations per engine step")
     ap.add_argument("--serve-cap-dofs", type=int, default=0,
                     help="serving: cap on the DoFs in flight (0 = HBM budget only)")
     args = ap.parse_args()

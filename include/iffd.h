@@ -284,15 +284,18 @@ typedef struct {
  * already enqueued on `stream` (so f may be produced there) and returns after
  * the step's work has finished. */
 int iffd_engine_create(const iffd_options* opt, size_t budget_bytes, void* stream, iffd_engine_handle* out);
-/* Workspace a request (d, n, p) takes from the arena (builds and caches the
- * plan of (d, n, p) if needed). */
-int iffd_engine_request_bytes(iffd_engine_handle e, int d, int n, int p, size_t* bytes);
-/* Admits a request if its workspace fits the arena now: f (right-hand side)
- * and u (solution, output) are caller-owned device arrays of N float64 that
- * must stay valid until the request completes. Returns IFFD_ERR_WORKSPACE if
- * the arena has no room now (resubmit after completions) and
- * IFFD_ERR_UNSUPPORTED if the request can never fit. */
-int iffd_engine_submit(iffd_engine_handle e, int d, int n, int p, const double* f, double* u, long long* id);
+/* Workspace a request (d, n, p, dirichlet as in iffd_engine_submit) takes from
+ * the arena (builds and caches the plan of the class if needed). */
+int iffd_engine_request_bytes(iffd_engine_handle e, int d, int n, int p, const int* dirichlet, size_t* bytes);
+/* Admits a request if its workspace fits the arena now: d directions with n
+ * elements each, degree p, dirichlet[2k], dirichlet[2k+1] the Dirichlet flags
+ * of direction k as in iffd_setup (NULL: Dirichlet on every face); f
+ * (right-hand side) and u (solution, output) are caller-owned device arrays
+ * of N float64 that must stay valid until the request completes. Returns
+ * IFFD_ERR_WORKSPACE if the arena has no room now (resubmit after
+ * completions) and IFFD_ERR_UNSUPPORTED if the request can never fit. */
+int iffd_engine_submit(iffd_engine_handle e, int d, int n, int p, const int* dirichlet, const double* f, double* u,
+                       long long* id);
 /* One step (see above); *active receives the number of requests still
  * iterating. Synchronises the engine's stream once (to read the states). */
 int iffd_engine_step(iffd_engine_handle e, int iterations, int* active);

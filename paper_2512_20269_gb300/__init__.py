@@ -261,15 +261,27 @@ class IFFDEngine:
         self._h = h
         self._keep = {}  # request id -> (f, u) tensors kept alive until completion
 
-    def request_bytes(self, d: int, n: int, p: int) -> int:
+    @staticmethod
+    def _flags(d, dirichlet):
+        if dirichlet is None:
+            return None
+        flags = [int(v) for pair in dirichlet for v in pair]
+        if len(flags) != 2 * d:
+            raise ValueError("dirichlet needs one (x=0, x=1) pair per direction")
+        return (ctypes.c_int * (2 * d))(*flags)
+
+    def request_bytes(self, d: int, n: int, p: int, dirichlet=None) -> int:
         nb = ctypes.c_size_t()
-        check(self._lib.iffd_engine_request_bytes(self._h, d, n, p, ctypes.byref(nb)), "iffd_engine_request_bytes")
+        check(self._lib.iffd_engine_request_bytes(self._h, d, n, p, self._flags(d, dirichlet), ctypes.byref(nb)),
+              "iffd_engine_request_bytes")
         return nb.value
 
-    def submit(self, d: int, n: int, p: int, f, u):
-        """Returns the request id, or None if the arena has no room right now."""
+    def submit(self, d: int, n: int, p: int, f, u, dirichlet=None):
+        """Returns the request id, or None if the arena has no room right now.
+        dirichlet: one (x=0, x=1) flag pair per direction (default: all Dirichlet)."""
         rid = ctypes.c_longlong()
-        rc = self._lib.iffd_engine_submit(self._h, d, n, p, _ptr(f), _ptr(u), ctypes.byref(rid))
+        rc = self._lib.iffd_engine_submit(self._h, d, n, p, self._flags(d, dirichlet), _ptr(f), _ptr(u),
+                                          ctypes.byref(rid))
         if rc == 4:  # IFFD_ERR_WORKSPACE: admission refused for now
             return None
         check(rc, "iffd_engine_submit")

@@ -71,8 +71,8 @@ SIGNATURES = [
     ("iffd_engine_create", ctypes.c_int, [ctypes.POINTER(iffd_options), ctypes.c_size_t, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     ("iffd_engine_request_bytes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                 c_size_t_p]),
-    ("iffd_engine_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 c_int_p, c_size_t_p]),
+    ("iffd_engine_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_int_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     ("iffd_engine_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p]),
     ("iffd_engine_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(iffd_completion), ctypes.c_int, c_int_p]),

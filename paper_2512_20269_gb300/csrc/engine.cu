@@ -137,7 +137,7 @@ struct Engine {
   int device = 0;
   char* arena_mem = nullptr;
   Arena arena;
-  std::map<std::tuple<int, int, int>, iffd_plan*> plans;
+  std::map<std::tuple<int, int, int, int>, iffd_plan*> plans;  // (d, n, p, Dirichlet flag bits)
   std::vector<Sys> active;
   std::vector<iffd_completion> done_list;
   long long next_id = 1;
@@ -647,16 +647,23 @@ int iffd_engine_create(const iffd_options* opt, size_t budget_bytes, void* strea
   return IFFD_OK;
 }
 
-static int engine_plan(iffd_engine* h, int d, int n, int p, iffd_plan** out) {
+// Plan of a request class; dirichlet: 2d flags (NULL: Dirichlet on every face).
+static int engine_plan(iffd_engine* h, int d, int n, int p, const int* dirichlet, iffd_plan** out) {
   Engine& E = h->E;
-  auto key = std::make_tuple(d, n, p);
+  if (d != 2 && d != 3) return fail(IFFD_ERR_INVALID_ARG, "d must be 2 or 3");
+  int dir[6] = {1, 1, 1, 1, 1, 1};
+  int bits = 0;
+  for (int k = 0; k < 2 * d; ++k) {
+    if (dirichlet) dir[k] = dirichlet[k] != 0;
+    bits |= dir[k] << k;
+  }
+  auto key = std::make_tuple(d, n, p, bits);
   auto it = E.plans.find(key);
   if (it != E.plans.end()) {
     *out = it->second;
     return IFFD_OK;
   }
   const int nn[3] = {n, n, n};
-  const int dir[6] = {1, 1, 1, 1, 1, 1};
   iffd_options o = E.opt;
   o.true_residual = 0;
   iffd_plan* P = nullptr;
@@ -667,21 +674,22 @@ static int engine_plan(iffd_engine* h, int d, int n, int p, iffd_plan** out) {
   return IFFD_OK;
 }
 
-int iffd_engine_request_bytes(iffd_engine_handle h, int d, int n, int p, size_t* bytes) {
+int iffd_engine_request_bytes(iffd_engine_handle h, int d, int n, int p, const int* dirichlet, size_t* bytes) {
   if (!h || !bytes) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
   iffd_plan* P = nullptr;
-  const int rc = engine_plan(h, d, n, p, &P);
+  const int rc = engine_plan(h, d, n, p, dirichlet, &P);
   if (rc) return rc;
   *bytes = al256(P->P.ws_bytes);
   return IFFD_OK;
 }
 
-int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const double* f, double* u, long long* id) {
+int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const int* dirichlet, const double* f, double* u,
+                       long long* id) {
   if (!h || !f || !u || !id) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
   if (f == u) return fail(IFFD_ERR_INVALID_ARG, "f and u must not alias");
   Engine& E = h->E;
   iffd_plan* P = nullptr;
-  int rc = engine_plan(h, d, n, p, &P);
+  int rc = engine_plan(h, d, n, p, dirichlet, &P);
   if (rc) return rc;
   const size_t need = al256(P->P.ws_bytes);
   if (need > E.arena.bytes) return fail(IFFD_ERR_UNSUPPORTED, "request needs more workspace than the whole budget");

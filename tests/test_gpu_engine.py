@@ -105,3 +105,25 @@ def test_engine_rejects_oversized_and_bad_requests():
         eng.submit(3, 64, 4, f, u)   # needs far more than 1 MiB
     with pytest.raises(IFFDError):
         eng.submit(3, 4, 5, f, u)    # n <= p
+
+
+def test_engine_mixed_boundaries_equal_alone():
+    """Requests with natural conditions on some faces (generic Table 1
+    transforms) share the engine's launches with Dirichlet requests and still
+    equal their stand-alone solves bitwise."""
+    torch = require_gpu()
+    from paper_2512_20269_gb300 import IFFDEngine, IFFDPlan
+    mix = [(3, 20, 4, ((1, 0), (0, 1), (0, 0))), (3, 20, 4, None), (2, 33, 3, ((0, 0), (1, 1))),
+           (3, 17, 5, ((0, 1), (1, 1), (1, 0)))]
+    eng = IFFDEngine(2 << 30, precision="fp32")
+    reqs = {}
+    for k, (d, n, p, dirichlet) in enumerate(mix):
+        plan = IFFDPlan(d, n, p, precision="fp32", true_residual=False, dirichlet=dirichlet)
+        f = torch.from_numpy(inputs.rhs(plan.shape, "normal", seed=600 + k)).cuda().reshape(-1)
+        u = torch.empty_like(f)
+        reqs[eng.submit(d, n, p, f, u, dirichlet=dirichlet)] = (plan, f, u)
+    done = dict(eng.run_to_completion(iterations_per_step=2))
+    for rid, (plan, f, u) in reqs.items():
+        ua, ia = plan.pcg_solve(f)
+        assert done[rid]["status"] == 0 and done[rid]["iters"] == ia["iters"]
+        assert torch.equal(u, ua.reshape(-1))
