@@ -285,12 +285,32 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
 
   // ---- load the tile. Padding pencils are zero: two pencils share one complex
   // FFT, so a padding partner must not carry data (its rounding would leak into
-  // the valid pencil, e.g. undivided values in the fused pass).
-  for (int e = tid; e < PP * m; e += blockDim.x) {
-    int pc, i;
-    if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
-    else { i = e >> lpp; pc = e & (PP - 1); }
-    tile[pc * ldt + i] = (pc < g.nvalid) ? (Tc)in[pbase[pc] + i * g.S] : Tc(0);
+  // the valid pencil, e.g. undivided values in the fused pass). Each thread
+  // issues four independent global loads before its shared-memory stores, so
+  // that enough loads are in flight to cover the DRAM latency.
+  {
+    constexpr int U = 4;
+    const int total = PP * m;
+    for (int e0 = tid; e0 < total; e0 += U * blockDim.x) {
+      Tin v[U];
+      int slot[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = Tin(0);
+        slot[u] = -1;
+        if (e < total) {
+          int pc, i;
+          if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
+          else { i = e >> lpp; pc = e & (PP - 1); }
+          slot[u] = pc * ldt + i;
+          if (pc < g.nvalid) v[u] = in[pbase[pc] + i * g.S];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (slot[u] >= 0) tile[slot[u]] = (Tc)v[u];
+    }
   }
   __syncthreads();
 
