@@ -124,7 +124,9 @@ int iffd_workspace_bytes(iffd_handle h, size_t* bytes);
  * counterpart; it fixes no kernel design): for every direction, the pencils
  * per tile (2..32, within 200 KB of shared memory) and the radix sequence of
  * the FFT (greedy radix 8, radix 4, or the greedy sequence reversed) of the
- * transform pass, and the pencils per tile of the stiffness sweep. Each
+ * transform pass, whether the pass runs as a persistent kernel that loads its
+ * next tile asynchronously (where the pass reads its own arithmetic type),
+ * and the pencils per tile of the stiffness sweep. Each
  * candidate runs the plan's kernel on the workspace ws (iffd_workspace_bytes,
  * contents overwritten) on `stream`; the fastest of three timed launches wins.
  * Passes whose default launch has fewer than 4 x 152 CTAs (too small to fill
@@ -137,11 +139,23 @@ int iffd_workspace_bytes(iffd_handle h, size_t* bytes);
  * Errors: INVALID_ARG, WORKSPACE (ws NULL or not 256-byte aligned), CUDA. */
 int iffd_autotune(iffd_handle h, void* ws, void* stream);
 
+/* Sets the launch geometry of direction `axis` by hand (the tuner's choices,
+ * see iffd_autotune): pencils per tile of its transform pass and of its
+ * stiffness sweep (2, 4, 8, 16 or 32; <= 0 keeps the current value) and the
+ * pipelined transform kernel (1 on, 0 off, < 0 unchanged). The geometry does
+ * not change any transformed value; it changes the grouping of the partial
+ * sums of the dot products. Errors: INVALID_ARG, UNSUPPORTED (does not fit in
+ * 200 KB of shared memory). Do not call while work of the plan is in flight. */
+int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencils_stiffness, int pipelined);
+
 /* Launch geometry of direction `axis` (any pointer may be NULL): pencils per
  * tile of its transform pass (for the plan's precision) and of its stiffness
- * sweep, and the radix sequence of its FFT (radices[0..*nstages), at most 12). */
+ * sweep, the radix sequence of its FFT (radices[0..*nstages), at most 12),
+ * and whether its transform passes run as the persistent pipelined kernel
+ * (*pipelined = 1: each CTA loads its next tile asynchronously while it
+ * transforms the current one). */
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
-                   int* nstages);
+                   int* nstages, int* pipelined);
 
 /* Sizes of direction `axis` (0-based): m = n + p - 2, n_reg and n_out of
  * eq. "reg_space_dim". */

@@ -189,13 +189,21 @@ class IFFDPlan:
         check(self._lib.iffd_autotune(self._h, self._ws_ptr, _stream_handle(stream)), "iffd_autotune")
         return self
 
+    def set_geometry(self, axis: int, pencils_transform: int = 0, pencils_stiffness: int = 0, pipelined=None):
+        """Set one direction's launch geometry by hand (iffd_set_geometry)."""
+        pl = -1 if pipelined is None else int(bool(pipelined))
+        check(self._lib.iffd_set_geometry(self._h, axis, int(pencils_transform), int(pencils_stiffness), pl),
+              "iffd_set_geometry")
+        return self
+
     def tiles(self, axis: int) -> dict:
         """Launch geometry of one direction (iffd_get_tiles)."""
-        pt, ps, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        pt, ps, ns, pl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         rad = (ctypes.c_int * 12)()
-        check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns)),
-              "iffd_get_tiles")
-        return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value])}
+        check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns),
+                                       ctypes.byref(pl)), "iffd_get_tiles")
+        return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value]),
+                "pipelined": bool(pl.value)}
 
     def profile_enable(self, on: bool = True):
         check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")

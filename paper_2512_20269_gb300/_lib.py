@@ -47,7 +47,8 @@ SIGNATURES = [
                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     ("iffd_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, c_size_t_p]),
     ("iffd_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    ("iffd_get_tiles", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]),
+    ("iffd_set_geometry", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("iffd_get_tiles", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p, c_int_p]),
     ("iffd_get_dims", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p]),
     ("iffd_get_1d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [c_double_p] * 6),
     ("iffd_host_axis", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/iffd.h"
@@ -323,12 +324,12 @@ static int default_var(const std::vector<FftVar>& fv, int len) {
   return -1;
 }
 
-// Default pencils per tile of a transform pass whose FFT has length F: 8
-// (FP64) or 16 (FP32) pencils, halved while the tile needs more than 110 KB of
-// shared memory (iffd_autotune may pick others).
+// Default pencils per tile of a transform pass whose FFT has length F: 8,
+// halved while the tile needs more than 110 KB of shared memory
+// (iffd_autotune may pick others).
 static int pick_pp(int m, int F, size_t elt, int* PP, int* ldt) {
   *ldt = m | 1;
-  int pp = (elt == sizeof(double)) ? 8 : 16;
+  int pp = 8;
   while (pp > 2 && precond_smem_bytes(pp, *ldt, F, elt) > 110 * 1024) pp /= 2;
   if (precond_smem_bytes(pp, *ldt, F, elt) > 220 * 1024) return 0;
   *PP = pp;
@@ -591,6 +592,7 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
   L.dot1 = nullptr;
   L.partial = nullptr;
   L.done = done;
+  L.pipe = std::is_same<Tc, double>::value ? P->pipe_d[axis] : P->pipe_f[axis];
   return L;
 }
 template PassLaunch<double> make_pass<double>(const Plan*, int, const AxisTab<double>*, const int*, const int*,

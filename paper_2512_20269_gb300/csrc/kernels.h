@@ -22,6 +22,7 @@ struct PassLaunch {
   const double* dot1;  // optional: partial (dot1, out) per CTA
   double* partial;
   const int* done;     // optional early-exit flag (PCG)
+  int pipe;            // 1: persistent two-stage pipelined kernel (same input and arithmetic type only)
 };
 
 // Per-system descriptor of one batched transform pass.
@@ -44,7 +45,8 @@ template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                 long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st);
 
-size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);
+size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);       // F: FFT length (AxisTab::F)
+size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt);  // pipelined kernel: one more tile
 // Fills AxisTab::rden of an FP64 plan (see device_common.cuh).
 cudaError_t launch_rden_fill(double* rden, const Dims& dims, const double* lamF, const double* lam0,
                              const double* lam1, cudaStream_t st);  // F: FFT length (AxisTab::F)

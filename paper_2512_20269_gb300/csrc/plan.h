@@ -126,6 +126,9 @@ struct Plan {
   // the one selected per precision (index into fvar[a])
   std::vector<FftVar> fvar[3];
   int vsel_d[3] = {0, 0, 0}, vsel_f[3] = {0, 0, 0};
+  // 1: the direction's transform passes run as the persistent pipelined kernel
+  // (where input and arithmetic types agree); chosen by the tuner
+  int pipe_d[3] = {0, 0, 0}, pipe_f[3] = {0, 0, 0};
   bool tuned = false;
   // exact FD tables
   const double* QT[3] = {nullptr, nullptr, nullptr};

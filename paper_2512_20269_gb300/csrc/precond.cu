@@ -15,6 +15,12 @@
 //        V_out Q_out z_out.
 // All arithmetic is in Tc (double, or float for the reduced-precision
 // transform variant); Tin/Tout are the global storage types.
+#include <cuda_pipeline.h>
+
+#include <algorithm>
+
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -259,30 +265,17 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Body of one CTA of a transform pass: tile `tile` of the pencils along `axis`.
+// A transform pass processes tiles of PP pencils along `axis` (tile_setup):
+// load the tile into shared memory, transform it (compute_tile), store it.
 // Partial dot products go to partial[ptile] (and partial[pstride + ptile]).
-template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
-__device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dims& dims, int axis, int PP, int ldt,
-                                             const AxisTab<Tc>& ax, const Tc* __restrict__ lamA,
-                                             const Tc* __restrict__ lamB, const double* __restrict__ dotv0,
-                                             const double* __restrict__ dotv1, double* __restrict__ partial,
-                                             long long tile_id, int ptile, int pstride, unsigned char* smem) {
-  const int npairs = PP / 2;
-  const int lpp = 31 - __clz(PP);  // PP is a power of two
-  const int L = ax.L;  // DFT length
-  const int F = ax.F;  // stride of a sequence in shared memory
+
+// Synchronous tile load (the caller synchronises afterwards).
+template <typename Tc, typename Tin>
+__device__ __forceinline__ void load_tile(const Tin* __restrict__ in, Tc* tile, int axis, int PP, int ldt,
+                                          const AxisTab<Tc>& ax, const long long* pbase, const TileInfo& g) {
+  const int lpp = 31 - __clz(PP);
   const int m = ax.m;
-  Cplx<Tc>* bufA = reinterpret_cast<Cplx<Tc>*>(smem);
-  Cplx<Tc>* bufB = bufA + (size_t)npairs * F;
-  Tc* tile = reinterpret_cast<Tc*>(bufB + (size_t)npairs * F);
-  Tc* outv = tile + (size_t)PP * ldt;  // PP * kMaxNout
-
-  __shared__ long long pbase[64];
-  __shared__ int pia[64], pib[64];
-  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
   const int tid = threadIdx.x;
-  __syncthreads();
-
   // ---- load the tile. Padding pencils are zero: two pencils share one complex
   // FFT, so a padding partner must not carry data (its rounding would leak into
   // the valid pencil, e.g. undivided values in the fused pass). Each thread
@@ -312,8 +305,23 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
         if (slot[u] >= 0) tile[slot[u]] = (Tc)v[u];
     }
   }
-  __syncthreads();
+}
 
+// The transform of one loaded tile, in place in `tile` (bufA, bufB: FFT
+// sequences; outv: remainder coefficients). Starts after and ends with a
+// block-wide synchronisation.
+template <typename Tc, int MODE>
+__device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>* bufB, Tc* outv, const Dims& dims,
+                                             int axis, int PP, int ldt, const AxisTab<Tc>& ax,
+                                             const Tc* __restrict__ lamA, const Tc* __restrict__ lamB,
+                                             const long long* pbase, const int* pia, const int* pib,
+                                             const TileInfo& g) {
+  const int npairs = PP / 2;
+  const int lpp = 31 - __clz(PP);  // PP is a power of two
+  const int L = ax.L;  // DFT length
+  const int F = ax.F;  // stride of a sequence in shared memory
+  const int m = ax.m;
+  const int tid = threadIdx.x;
   const int N = ax.n_reg;
   if (MODE == PM_FWD || MODE == PM_FUSED) {
     // remainder projections y_out = W^T r over the two support ranges of W:
@@ -530,6 +538,17 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
     __syncthreads();
   }
 
+}
+
+// Store the tile (and the partial dot products of the last pass of a PCG step).
+template <typename Tc, typename Tout, int NDOT>
+__device__ __forceinline__ void store_tile(const Tc* tile, Tout* __restrict__ out, int axis, int PP, int ldt,
+                                           const AxisTab<Tc>& ax, const long long* pbase, const TileInfo& g,
+                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                           double* __restrict__ partial, int ptile, int pstride) {
+  const int lpp = 31 - __clz(PP);
+  const int m = ax.m;
+  const int tid = threadIdx.x;
   // ---- store (and, on the last pass of a PCG step, partial dot products)
   double d0 = 0.0, d1 = 0.0;
   for (int e = tid; e < PP * m; e += blockDim.x) {
@@ -559,6 +578,29 @@ __device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dim
   }
 }
 
+// Body of one CTA of a (non-persistent) transform pass: tile `tile_id`.
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+__device__ __forceinline__ void precond_body(const Tin* in, Tout* out, const Dims& dims, int axis, int PP, int ldt,
+                                             const AxisTab<Tc>& ax, const Tc* __restrict__ lamA,
+                                             const Tc* __restrict__ lamB, const double* __restrict__ dotv0,
+                                             const double* __restrict__ dotv1, double* __restrict__ partial,
+                                             long long tile_id, int ptile, int pstride, unsigned char* smem) {
+  const int npairs = PP / 2;
+  const int F = ax.F;
+  Cplx<Tc>* bufA = reinterpret_cast<Cplx<Tc>*>(smem);
+  Cplx<Tc>* bufB = bufA + (size_t)npairs * F;
+  Tc* tile = reinterpret_cast<Tc*>(bufB + (size_t)npairs * F);
+  Tc* outv = tile + (size_t)PP * ldt;  // PP * kMaxNout
+  __shared__ long long pbase[64];
+  __shared__ int pia[64], pib[64];
+  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
+  __syncthreads();
+  load_tile<Tc, Tin>(in, tile, axis, PP, ldt, ax, pbase, g);
+  __syncthreads();
+  compute_tile<Tc, MODE>(tile, bufA, bufB, outv, dims, axis, PP, ldt, ax, lamA, lamB, pbase, pia, pib, g);
+  store_tile<Tc, Tout, NDOT>(tile, out, axis, PP, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
+}
+
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
 precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, AxisTab<Tc> ax,
@@ -569,6 +611,70 @@ precond_pass(const Tin* in, Tout* out, Dims dims, int axis, int PP, int ldt, Axi
   extern __shared__ __align__(16) unsigned char smem[];
   precond_body<Tc, Tin, Tout, MODE, NDOT>(in, out, dims, axis, PP, ldt, ax, lamA, lamB, dotv0, dotv1, partial,
                                           blockIdx.x, blockIdx.x, gridDim.x, smem);
+}
+
+// Asynchronous tile load: one cp.async element copy per DoF (padding pencils
+// are written as zeros); the caller commits the copy group.
+template <typename Tc>
+__device__ __forceinline__ void load_tile_async(const Tc* __restrict__ in, Tc* tile, int axis, int PP, int ldt,
+                                                const AxisTab<Tc>& ax, const long long* pbase, const TileInfo& g) {
+  const int lpp = 31 - __clz(PP);
+  const int m = ax.m;
+  for (int e = threadIdx.x; e < PP * m; e += blockDim.x) {
+    int pc, i;
+    if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
+    else { i = e >> lpp; pc = e & (PP - 1); }
+    Tc* dst = tile + pc * ldt + i;
+    if (pc < g.nvalid) __pipeline_memcpy_async(dst, in + pbase[pc] + i * g.S, sizeof(Tc));
+    else *dst = Tc(0);
+  }
+}
+
+// Persistent transform pass with a two-stage pipeline: each CTA walks the
+// tiles t = blockIdx.x, + gridDim.x, ...; while it transforms tile t the
+// copies of its next tile are already in flight into the second tile buffer.
+// Same arithmetic and partial sums as precond_pass (only the loading differs).
+template <typename Tc, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_pass_pipe(const Tc* in, Tc* out, Dims dims, int axis, int PP, int ldt, AxisTab<Tc> ax,
+                  const Tc* __restrict__ lamA, const Tc* __restrict__ lamB, const double* __restrict__ dotv0,
+                  const double* __restrict__ dotv1, double* __restrict__ partial, int ntiles,
+                  const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int npairs = PP / 2, F = ax.F;
+  Cplx<Tc>* bufA = reinterpret_cast<Cplx<Tc>*>(smem);
+  Cplx<Tc>* bufB = bufA + (size_t)npairs * F;
+  Tc* tiles = reinterpret_cast<Tc*>(bufB + (size_t)npairs * F);  // two tile buffers
+  Tc* outv = tiles + (size_t)2 * PP * ldt;                          // PP * kMaxNout
+  __shared__ long long pbase[2][64];
+  __shared__ int pia[2][64], pib[2][64];
+  int t = blockIdx.x;
+  if (t >= ntiles) return;  // the same for every thread of the CTA
+  TileInfo g = tile_setup(dims, axis, PP, t, pbase[0], pia[0], pib[0]);
+  __syncthreads();
+  load_tile_async<Tc>(in, tiles, axis, PP, ldt, ax, pbase[0], g);
+  __pipeline_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    const int nx = cur ^ 1;
+    TileInfo gn = g;
+    if (tn < ntiles) gn = tile_setup(dims, axis, PP, tn, pbase[nx], pia[nx], pib[nx]);
+    __syncthreads();  // pbase[nx] written
+    if (tn < ntiles) load_tile_async<Tc>(in, tiles + (size_t)nx * PP * ldt, axis, PP, ldt, ax, pbase[nx], gn);
+    __pipeline_commit();
+    __pipeline_wait_prior(1);  // this thread's copies of tile t have landed
+    __syncthreads();           // and every thread's
+    Tc* tile = tiles + (size_t)cur * PP * ldt;
+    compute_tile<Tc, MODE>(tile, bufA, bufB, outv, dims, axis, PP, ldt, ax, lamA, lamB, pbase[cur], pia[cur],
+                           pib[cur], g);
+    store_tile<Tc, Tc, NDOT>(tile, out, axis, PP, ldt, ax, pbase[cur], g, dotv0, dotv1, partial, t, ntiles);
+    __syncthreads();  // tile buffer and pbase of `cur` are free for tile t + 2 gridDim.x
+    g = gn;
+    cur = nx;
+  }
+  __pipeline_wait_prior(0);
 }
 
 // Batched pass: the grid covers the tiles of many independent systems; CTA b
@@ -634,8 +740,42 @@ size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt) {
 
 int precond_tiles(const Dims& dims, int axis, int PP) { return (int)host_num_tiles(dims, axis, PP); }
 
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+  }
+  return n;
+}
+
+size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt) {
+  return precond_smem_bytes(PP, ldt, F, elt) + (size_t)PP * ldt * elt;
+}
+
+template <typename Tc, int MODE, int NDOT>
+static cudaError_t launch_pipe_t(const PassLaunch<Tc>& P, const Tc* in, Tc* out, cudaStream_t st) {
+  auto kern = precond_pass_pipe<Tc, MODE, NDOT>;
+  const size_t sm = precond_smem_bytes_pipe(P.PP, P.ldt, P.ax.F, sizeof(Tc));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int tiles = precond_tiles(P.dims, P.axis, P.PP);
+  const int grid = std::min(tiles, per_sm * sm_count());
+  kern<<<grid, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.PP, P.ldt, P.ax, P.lamA, P.lamB, P.dot0, P.dot1,
+                                   P.partial, tiles, P.done);
+  return cudaGetLastError();
+}
+
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value) {
+    if (P.pipe) return launch_pipe_t<Tc, MODE, NDOT>(P, in, out, st);
+  }
   auto kern = precond_pass<Tc, Tin, Tout, MODE, NDOT>;
   const size_t sm = precond_smem_bytes(P.PP, P.ldt, P.ax.F, sizeof(Tc));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

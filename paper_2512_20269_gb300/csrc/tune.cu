@@ -43,6 +43,7 @@ struct Key {
 struct Choice {
   int pp;
   std::vector<int> radix;  // transform passes only
+  int pipe = 0;            // transform passes only: pipelined persistent kernel
 };
 
 std::mutex g_mu;
@@ -102,6 +103,9 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
   int* PPs = f64 ? P->PPd : P->PPf;
   int* ldts = f64 ? P->ldtd : P->ldtf;
   int* vsel = f64 ? P->vsel_d : P->vsel_f;
+  int* pipes = f64 ? P->pipe_d : P->pipe_f;
+  // the timed pass reads Tc except FP32's first direction (FP64 input)
+  const bool pipe_ok = f64 || a > 0;
   AxisTab<Tc>& ax = tabs[a];
   const int mode = (a == P->d - 1) ? PM_FUSED : PM_FWD;
   const Key key{0, f64 ? IFFD_PREC_FP64 : IFFD_PREC_FP32_TRANSFORM, P->d, a, ax.m, ax.F, P->p,
@@ -109,10 +113,11 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
   std::vector<int> vars;
   for (size_t i = 0; i < P->fvar[a].size(); ++i)
     if (P->fvar[a][i].len == ax.F) vars.push_back((int)i);
-  auto apply = [&](int vi, int pp) {
+  auto apply = [&](int vi, int pp, int pipe) {
     vsel[a] = vi;
     set_fft(&ax, P->fvar[a][vi]);
     PPs[a] = pp;
+    pipes[a] = pipe;
   };
   if (precond_tiles(P->dims, a, PPs[a]) < kMinTuneTiles) return IFFD_OK;
   {
@@ -121,7 +126,7 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
     if (it != g_cache.end()) {
       for (int vi : vars)
         if (var_radices(P->fvar[a][vi]) == it->second.radix) {
-          apply(vi, it->second.pp);
+          apply(vi, it->second.pp, it->second.pipe);
           return IFFD_OK;
         }
     }
@@ -130,11 +135,14 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
   double* z = reinterpret_cast<double*>(ws + P->off_z);
   float* tf = reinterpret_cast<float*>(ws + P->off_tf);
   float best = 1e30f;
-  int best_v = vsel[a], best_pp = PPs[a];
+  int best_v = vsel[a], best_pp = PPs[a], best_pipe = pipes[a];
   for (int vi : vars)
-    for (int pp : kCandPP) {
-      if (precond_smem_bytes(pp, ldts[a], ax.F, sizeof(Tc)) > kMaxTuneSmem) continue;
-      apply(vi, pp);
+    for (int pp : kCandPP)
+      for (int pipe = 0; pipe <= (pipe_ok ? 1 : 0); ++pipe) {
+      const size_t need = pipe ? precond_smem_bytes_pipe(pp, ldts[a], ax.F, sizeof(Tc))
+                               : precond_smem_bytes(pp, ldts[a], ax.F, sizeof(Tc));
+      if (need > kMaxTuneSmem) continue;
+      apply(vi, pp, pipe);
       const PassLaunch<Tc> L = make_pass<Tc>(P, a, tabs, PPs, ldts, nullptr);
       float ms = 0.f;
       int rc;
@@ -152,11 +160,12 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
         best = ms;
         best_v = vi;
         best_pp = pp;
+        best_pipe = pipe;
       }
     }
-  apply(best_v, best_pp);
+  apply(best_v, best_pp, best_pipe);
   std::lock_guard<std::mutex> lk(g_mu);
-  g_cache[key] = Choice{best_pp, var_radices(P->fvar[a][best_v])};
+  g_cache[key] = Choice{best_pp, var_radices(P->fvar[a][best_v]), best_pipe};
   return IFFD_OK;
 }
 
@@ -264,8 +273,44 @@ int iffd_autotune(iffd_handle h, void* ws, void* stream) {
   return plan_autotune(&h->P, ws, static_cast<cudaStream_t>(stream));
 }
 
+int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencils_stiffness, int pipelined) {
+  g_err.clear();
+  if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
+  Plan& P = h->P;
+  const bool f64 = P.opt.precision == IFFD_PREC_FP64;
+  auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
+  if (pencils_transform > 0) {
+    if (!pow2(pencils_transform)) return fail(IFFD_ERR_INVALID_ARG, "pencils per tile must be 2, 4, 8, 16 or 32");
+    const int ldt = f64 ? P.ldtd[axis] : P.ldtf[axis];
+    const int F = f64 ? P.axd[axis].F : P.axf[axis].F;
+    const size_t elt = f64 ? sizeof(double) : sizeof(float);
+    const int pipe = pipelined > 0 ? 1 : (pipelined == 0 ? 0 : (f64 ? P.pipe_d[axis] : P.pipe_f[axis]));
+    const size_t need = pipe ? precond_smem_bytes_pipe(pencils_transform, ldt, F, elt)
+                             : precond_smem_bytes(pencils_transform, ldt, F, elt);
+    if (need > kMaxTuneSmem) return fail(IFFD_ERR_UNSUPPORTED, "tile does not fit in shared memory");
+    (f64 ? P.PPd : P.PPf)[axis] = pencils_transform;
+  }
+  if (pipelined >= 0) {
+    const int PP = f64 ? P.PPd[axis] : P.PPf[axis];
+    const int ldt = f64 ? P.ldtd[axis] : P.ldtf[axis];
+    const int F = f64 ? P.axd[axis].F : P.axf[axis].F;
+    const size_t elt = f64 ? sizeof(double) : sizeof(float);
+    if (pipelined && precond_smem_bytes_pipe(PP, ldt, F, elt) > kMaxTuneSmem)
+      return fail(IFFD_ERR_UNSUPPORTED, "pipelined tile does not fit in shared memory");
+    (f64 ? P.pipe_d : P.pipe_f)[axis] = pipelined ? 1 : 0;
+  }
+  if (pencils_stiffness > 0) {
+    if (!pow2(pencils_stiffness)) return fail(IFFD_ERR_INVALID_ARG, "pencils per tile must be 2, 4, 8, 16 or 32");
+    const bool var = P.opt.coef == IFFD_COEF_SEPARABLE_SIN;
+    if ((size_t)(var ? 4 : 2) * pencils_stiffness * P.ldts[axis] * sizeof(double) > kMaxTuneSmem)
+      return fail(IFFD_ERR_UNSUPPORTED, "stiffness tile does not fit in shared memory");
+    (var ? P.PPv : P.PPs)[axis] = pencils_stiffness;
+  }
+  return IFFD_OK;
+}
+
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
-                   int* nstages) {
+                   int* nstages, int* pipelined) {
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   const Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
@@ -274,6 +319,7 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
     *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
   const int nst = f64 ? P.axd[axis].nst : P.axf[axis].nst;
   if (nstages) *nstages = nst;
+  if (pipelined) *pipelined = f64 ? P.pipe_d[axis] : P.pipe_f[axis];
   if (radices)
     for (int s = 0; s < nst; ++s) radices[s] = f64 ? P.axd[axis].radix[s] : P.axf[axis].radix[s];
   return IFFD_OK;
