@@ -27,19 +27,30 @@ from fractions import Fraction
 import numpy as np
 
 
-def open_knots(n: int, p: int) -> np.ndarray:
+def open_knots(n: int, p: int, rep=None) -> np.ndarray:
     """p-open knot vector on the uniform grid z_k = k/n (Section 2):
-    p+1 copies of 0, the interior breakpoints 1/n..(n-1)/n, p+1 copies of 1."""
-    interior = [k / n for k in range(1, n)]
+    p+1 copies of 0, the interior breakpoints 1/n..(n-1)/n, p+1 copies of 1.
+    ``rep`` = {k: extra} repeats the interior breakpoint k/n extra more times
+    (reduced regularity C^{p-1-extra} there, Remark "reduced_regularity")."""
+    rep = rep or {}
+    interior = []
+    for k in range(1, n):
+        interior += [k / n] * (1 + int(rep.get(k, 0)))
     return np.array([0.0] * (p + 1) + interior + [1.0] * (p + 1), dtype=np.float64)
 
 
-def _element_span(p: int, e: int) -> int:
-    """Index s with xi_s = z_e < xi_{s+1} = z_{e+1} for element e (0-based)."""
-    return p + e
+def n_basis(n: int, p: int, rep=None) -> int:
+    """Number of B-splines of S_{p,h} with the repeated knots ``rep``."""
+    return n + p + sum(int(v) for v in (rep or {}).values())
 
 
-def bspline_table(knots: np.ndarray, q: int, e: int, x: np.ndarray, p: int) -> dict:
+def _element_span(knots: np.ndarray, e: int, n: int) -> int:
+    """Index s with xi_s = z_e < xi_{s+1} = z_{e+1} for element e (0-based):
+    the last knot equal to z_e."""
+    return int(np.searchsorted(knots, e / n, side="right")) - 1
+
+
+def bspline_table(knots: np.ndarray, q: int, e: int, x: np.ndarray, p: int, n: int | None = None) -> dict:
     """Cox-de Boor recursion up to degree q on element e of a degree-p knot vector.
 
     Returns {i: B_{q,i}(x)} for the B-splines of degree q that can be nonzero on
@@ -48,7 +59,8 @@ def bspline_table(knots: np.ndarray, q: int, e: int, x: np.ndarray, p: int) -> d
     piece). Summands with a vanishing denominator are dropped (Section 2).
     """
     x = np.asarray(x, dtype=np.float64)
-    s = _element_span(p, e)
+    n = _n_elements(knots, p) if n is None else n
+    s = _element_span(knots, e, n)
     vals = {s: np.ones_like(x)}
     for d in range(1, q + 1):
         new = {}
@@ -65,18 +77,26 @@ def bspline_table(knots: np.ndarray, q: int, e: int, x: np.ndarray, p: int) -> d
     return vals
 
 
-def bspline_derivs(knots: np.ndarray, p: int, e: int, x: np.ndarray, k: int) -> np.ndarray:
-    """k-th derivative of B_{p,e}, ..., B_{p,e+p} at points x of element e.
+def _n_elements(knots: np.ndarray, p: int) -> int:
+    """Number of (uniform) elements of a knot vector built by open_knots."""
+    return len(np.unique(knots)) - 1
 
-    Returns an array of shape (len(x), p+1); column j is B_{p,e+j}^{(k)}.
+
+def bspline_derivs(knots: np.ndarray, p: int, e: int, x: np.ndarray, k: int) -> np.ndarray:
+    """k-th derivative of the p+1 B-splines nonzero on element e, at points x
+    of the element: B_{p,s-p}, ..., B_{p,s} with s the element's span (s = p + e
+    without repeated knots).
+
+    Returns an array of shape (len(x), p+1); column j is B_{p,s-p+j}^{(k)}.
     For k > p all derivatives vanish.
     """
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     out = np.zeros((x.size, p + 1))
     if k > p:
         return out
-    s = _element_span(p, e)
-    cur = bspline_table(knots, p - k, e, x, p)  # degree p-k values
+    n = _n_elements(knots, p)
+    s = _element_span(knots, e, n)
+    cur = bspline_table(knots, p - k, e, x, p, n)  # degree p-k values
     for d in range(p - k + 1, p + 1):
         new = {}
         for i in range(s - d, s + 1):
@@ -90,7 +110,7 @@ def bspline_derivs(knots: np.ndarray, p: int, e: int, x: np.ndarray, k: int) -> 
             new[i] = acc
         cur = new
     for j in range(p + 1):
-        out[:, j] = cur.get(e + j, np.zeros_like(x))
+        out[:, j] = cur.get(s - p + j, np.zeros_like(x))
     return out
 
 
@@ -100,16 +120,17 @@ def gauss_rule(npts: int, a: float, b: float):
     return 0.5 * (b - a) * t + 0.5 * (a + b), 0.5 * (b - a) * w
 
 
-def assemble_full(n: int, p: int, weight=None, nq: int | None = None):
-    """Full (n+p) x (n+p) mass and stiffness matrices of S_{p,h}.
+def assemble_full(n: int, p: int, weight=None, nq: int | None = None, rep=None):
+    """Full mass and stiffness matrices of S_{p,h} (n + p B-splines, plus one
+    per repeated knot of ``rep``).
 
     M_ij = int_0^1 a(x) B_i(x) B_j(x) dx,  K_ij = int_0^1 a(x) B_i'(x) B_j'(x) dx,
     with a = 1 unless ``weight`` is given, integrated element by element with
     an nq-point Gauss rule (nq = p+1 by default).
     """
-    knots = open_knots(n, p)
+    knots = open_knots(n, p, rep)
     nq = p + 1 if nq is None else nq
-    size = n + p
+    size = n_basis(n, p, rep)
     M = np.zeros((size, size))
     K = np.zeros((size, size))
     for e in range(n):
@@ -118,26 +139,28 @@ def assemble_full(n: int, p: int, weight=None, nq: int | None = None):
             wg = wg * weight(xg)
         B = bspline_derivs(knots, p, e, xg, 0)
         dB = bspline_derivs(knots, p, e, xg, 1)
-        M[e:e + p + 1, e:e + p + 1] += B.T @ (wg[:, None] * B)
-        K[e:e + p + 1, e:e + p + 1] += dB.T @ (wg[:, None] * dB)
+        s0 = _element_span(knots, e, n) - p
+        M[s0:s0 + p + 1, s0:s0 + p + 1] += B.T @ (wg[:, None] * B)
+        K[s0:s0 + p + 1, s0:s0 + p + 1] += dB.T @ (wg[:, None] * dB)
     return M, K
 
 
-def kept_indices(n: int, p: int, dirichlet=(0, 1)) -> np.ndarray:
-    """Indices of the B-splines kept in S_{p,h,D}: B_0 is dropped when 0 is in D
-    and B_{n+p-1} when 1 is in D (the only ones that do not vanish there)."""
-    idx = list(range(n + p))
+def kept_indices(n: int, p: int, dirichlet=(0, 1), rep=None) -> np.ndarray:
+    """Indices of the B-splines kept in S_{p,h,D}: the first is dropped when 0
+    is in D and the last when 1 is in D (the only ones that do not vanish there)."""
+    size = n_basis(n, p, rep)
+    idx = list(range(size))
     if 1 in dirichlet:
-        idx.remove(n + p - 1)
+        idx.remove(size - 1)
     if 0 in dirichlet:
         idx.remove(0)
     return np.array(idx, dtype=np.int64)
 
 
-def mass_stiffness(n: int, p: int, dirichlet=(0, 1), weight=None):
-    """M and K of S_{p,h,D} (size m = n + p - |D|)."""
-    M, K = assemble_full(n, p, weight)
-    keep = kept_indices(n, p, dirichlet)
+def mass_stiffness(n: int, p: int, dirichlet=(0, 1), weight=None, rep=None):
+    """M and K of S_{p,h,D} (size m = n + p - |D|, plus the repeated knots)."""
+    M, K = assemble_full(n, p, weight, rep=rep)
+    keep = kept_indices(n, p, dirichlet, rep)
     return M[np.ix_(keep, keep)], K[np.ix_(keep, keep)]
 
 

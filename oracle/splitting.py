@@ -175,15 +175,17 @@ def special_basis_combinations(n: int, p: int, dirichlet):
     return combos
 
 
-def cardinal_coefficients(n: int, p: int) -> tuple[np.ndarray, list]:
+def cardinal_coefficients(n: int, p: int, rep=None) -> tuple[np.ndarray, list]:
     """Coefficients of every active cardinal B-spline B~_k (restricted to [0,1])
-    in the full open-knot basis of S_{p,h}, by exact L2 projection."""
-    knots = open_knots(n, p)
+    in the full open-knot basis of S_{p,h} (with the repeated knots ``rep``),
+    by exact L2 projection (the cardinal B-splines are C^{p-1} piecewise
+    polynomials on the same elements, hence in the space)."""
+    knots = open_knots(n, p, rep)
     h = 1.0 / n
     ks = list(cardinal_index_range(n, p))
-    Mfull, _ = assemble_full(n, p)
+    Mfull, _ = assemble_full(n, p, rep=rep)
     nq = p + 1
-    E = np.zeros((len(ks), n + p))
+    E = np.zeros((len(ks), Mfull.shape[0]))
     xs, ws = [], []
     for e in range(n):
         xg, wg = gauss_rule(nq, e / n, (e + 1) / n)
@@ -196,23 +198,27 @@ def cardinal_coefficients(n: int, p: int) -> tuple[np.ndarray, list]:
     for e in range(n):
         sl = slice(e * nq, (e + 1) * nq)
         B = bspline_derivs(knots, p, e, xs[sl], 0)   # (nq, p+1)
-        E[:, e:e + p + 1] += (card[:, sl] * ws[None, sl]) @ B
+        s0 = int(np.searchsorted(knots, e / n, side="right")) - 1 - p
+        E[:, s0:s0 + p + 1] += (card[:, sl] * ws[None, sl]) @ B
     coef = np.linalg.solve(Mfull, E.T).T       # rows: cardinal k
     return coef, ks
 
 
-def V_reg_matrix(n: int, p: int, dirichlet, return_dropped: bool = False):
-    """V_reg: coordinates of the special basis in the kept B-spline basis."""
+def V_reg_matrix(n: int, p: int, dirichlet, return_dropped: bool = False, rep=None):
+    """V_reg: coordinates of the special basis in the kept B-spline basis
+    (with the repeated knots ``rep``: the regular space is unchanged,
+    Remark "reduced_regularity", only its coordinates change)."""
     D = normalize_dirichlet(dirichlet)
-    coef, ks = cardinal_coefficients(n, p)
+    coef, ks = cardinal_coefficients(n, p, rep)
     row = {k: r for r, k in enumerate(ks)}
     combos = special_basis_combinations(n, p, D)
-    full = np.zeros((n + p, len(combos)))
+    size = coef.shape[1]
+    full = np.zeros((size, len(combos)))
     for j, c in enumerate(combos):
         for v, k in c:
             full[:, j] += v * coef[row[k]]
-    keep = kept_indices(n, p, D)
-    dropped = np.setdiff1d(np.arange(n + p), keep)
+    keep = kept_indices(n, p, D, rep)
+    dropped = np.setdiff1d(np.arange(size), keep)
     V = full[keep, :]
     if return_dropped:
         return V, full[dropped, :]
@@ -251,14 +257,16 @@ class AxisSplit:
         return self.V_out.shape[1]
 
 
-def axis_split(n: int, p: int, dirichlet=(0, 1)) -> AxisSplit:
-    """Build Q~ and Lambda~ of one direction (Sections 4 and 6)."""
+def axis_split(n: int, p: int, dirichlet=(0, 1), rep=None) -> AxisSplit:
+    """Build Q~ and Lambda~ of one direction (Sections 4 and 6); ``rep`` =
+    {k: extra} repeats interior knots (Remark "reduced_regularity": the regular
+    space and its transform are unchanged, S^out grows by one per extra knot)."""
     D = normalize_dirichlet(dirichlet)
-    Mf, Kf = assemble_full(n, p)
-    keep = kept_indices(n, p, D)
+    Mf, Kf = assemble_full(n, p, rep=rep)
+    keep = kept_indices(n, p, D, rep)
     M = Mf[np.ix_(keep, keep)]
     K = Kf[np.ix_(keep, keep)]
-    V = V_reg_matrix(n, p, D)
+    V = V_reg_matrix(n, p, D, rep=rep)
     U = U_reg(n, p, D)
     # D~_reg = (U^T V_reg^T M V_reg U)^{1/2} (end of Section 6). Lambda_reg from
     # Lemma 3: the numeric diag(U^T V_reg^T K V_reg U) / D~^2 of eq. "Lambda reg"

@@ -164,3 +164,81 @@ def test_prop1_bound_bounded_in_h_and_p():
             ratios.append(operators.prop1_bound(s.K, Kt))
         assert max(ratios) < 4.0, (p, ratios)
         assert ratios[-1] <= ratios[0] * 1.05 + 1e-12, (p, ratios)
+
+
+# ------------------------------------------- reduced regularity (Remark)
+REP_CASES = [(16, 3, (0, 1), {8: 2}), (16, 4, (0, 1), {5: 1, 11: 3}), (17, 2, (0,), {9: 1}),
+             (20, 5, (), {10: 4}), (18, 6, (1,), {6: 2, 12: 5}), (15, 1, (0, 1), {})]
+
+
+@pytest.mark.parametrize("n,p,D,rep", REP_CASES)
+def test_reduced_regularity_dimensions(n, p, D, rep):
+    """Remark "reduced_regularity": S^reg does not change when interior knots
+    are repeated, and every added knot adds one function to S^out."""
+    base = splitting.axis_split(n, p, D)
+    s = splitting.axis_split(n, p, D, rep=rep)
+    extra = sum(rep.values())
+    assert s.m == base.m + extra
+    assert s.n_reg == base.n_reg
+    assert s.n_out == base.n_out + extra
+
+
+@pytest.mark.parametrize("n,p,D,rep", REP_CASES[:5])
+def test_reduced_regularity_regular_space_unchanged(n, p, D, rep):
+    """The special functions written in the basis with repeated knots (V_reg,
+    by L2 projection) are the same functions: evaluated through the B-splines
+    they equal the cardinal combinations at points of every element."""
+    s = splitting.axis_split(n, p, D, rep=rep)
+    knots = splines.open_knots(n, p, rep)
+    keep = splines.kept_indices(n, p, D, rep)
+    size = splines.n_basis(n, p, rep)
+    combos = splitting.special_basis_combinations(n, p, D)
+    full = np.zeros((size, s.n_reg))
+    full[keep] = s.V_reg
+    h = 1.0 / n
+    worst = 0.0
+    for e in range(n):
+        x = e * h + h * np.array([0.13, 0.5, 0.91])
+        B = splines.bspline_derivs(knots, p, e, x, 0)
+        s0 = int(np.searchsorted(knots, e / n, side="right")) - 1 - p
+        vals = B @ full[s0:s0 + p + 1]
+        ref = np.zeros_like(vals)
+        for j, c in enumerate(combos):
+            for v, k in c:
+                ref[:, j] += v * splines.cardinal_bspline(p, (x - splitting.node(k, n, p)) / h)
+        worst = max(worst, np.abs(vals - ref).max())
+    assert worst < 1e-12
+
+
+@pytest.mark.parametrize("n,p,D,rep", REP_CASES[:5])
+def test_reduced_regularity_identities(n, p, D, rep):
+    """P1 and P7 with repeated knots: partition of unity, K 1 = 0, Q~^T M Q~ = I,
+    Q~^T K~ Q~ = Lambda~, V_reg^T M V_out = 0."""
+    Mf, Kf = splines.assemble_full(n, p, rep=rep)
+    assert abs(Mf.sum() - 1.0) < 1e-13
+    assert np.abs(Kf @ np.ones(Kf.shape[0])).max() < 1e-10 * np.abs(Kf).max()
+    s = splitting.axis_split(n, p, D, rep=rep)
+    m = s.m
+    np.testing.assert_allclose(s.Qt.T @ s.M @ s.Qt, np.eye(m), atol=1e-11)
+    Kt = splitting.ktilde_basis_free(s.M, s.K, s.V_reg)
+    np.testing.assert_allclose(s.Qt.T @ Kt @ s.Qt, np.diag(s.lamt), atol=1e-10 * np.abs(s.lamt).max())
+    assert np.abs(s.V_reg.T @ s.M @ s.V_out).max() < 1e-11 * np.abs(s.V_reg).max() * np.abs(s.V_out).max() * m
+
+
+def test_reduced_regularity_condition_bounded():
+    """IFFD stays a good preconditioner with a C^0 line (the plate-with-hole
+    situation of Section 7): kappa(P^{-1} A^) in 2D with a knot of full
+    multiplicity at x = 1/2 stays bounded as h shrinks (and close to its value
+    without the repeated knot, 1.25)."""
+    from oracle import operators
+    import scipy.sparse
+    ks = []
+    for n in (16, 32):
+        p = 3
+        rep = {n // 2: p - 1}
+        sx = splitting.axis_split(n, p, (0, 1), rep=rep)
+        sy = splitting.axis_split(n, p, (0, 1))
+        MK = [(scipy.sparse.csr_matrix(sx.M), scipy.sparse.csr_matrix(sx.K)),
+              (scipy.sparse.csr_matrix(sy.M), scipy.sparse.csr_matrix(sy.K))]
+        ks.append(operators.kappa_lanczos([sx, sy], (sy.m, sx.m), lambda v: operators.stiffness_apply(v, MK)))
+    assert ks[1] <= ks[0] + 0.05 and ks[1] < 1.5, ks  # measured: 1.30 (n = 16), 1.25 (n = 32)
