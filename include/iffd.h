@@ -117,6 +117,24 @@ int iffd_default_options(iffd_options* opt);
 int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
                iffd_handle* out);
 
+/* iffd_setup with repeated interior knots (reduced regularity, Remark
+ * "reduced_regularity" of Section 4). nrep[k] (k < d) is the number of
+ * repeated breakpoints of direction k; reps lists them as (knot, extra) int
+ * pairs, direction 0 first: the breakpoint knot/n_k (1 <= knot <= n_k - 1)
+ * appears 1 + extra times in the knot vector (1 <= extra <= p - 1), so the
+ * splines are C^{p-1-extra} there, and m_k = n_k + p + sum extra - |D_k|.
+ * The regular space S^reg and its transform are those without repeated knots;
+ * S^out grows by `extra` per repeated breakpoint (the jumps of the derivatives
+ * of orders p - extra .. p - 1). V_reg gets a small dense block around every
+ * repeated breakpoint, and the stiffness sweeps of such a direction use
+ * general band rows throughout. nrep NULL: no repeated knots (iffd_setup).
+ * Host arrays, read during the call only. Errors: as iffd_setup, plus
+ * INVALID_ARG (negative count, reps NULL with a positive count) and
+ * UNSUPPORTED (knot or extra out of range, a knot listed twice, a repeated
+ * breakpoint too close to an end for the edge blocks, n_out above 16). */
+int iffd_setup_knots(int d, const int* n_elems, int p, const int* dirichlet, const int* nrep, const int* reps,
+                     const iffd_options* opt, void* stream, iffd_handle* out);
+
 /* Device workspace needed by every call on this plan, in bytes. */
 int iffd_workspace_bytes(iffd_handle h, size_t* bytes);
 
@@ -157,8 +175,8 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
                    int* nstages, int* pipelined);
 
-/* Sizes of direction `axis` (0-based): m = n + p - 2, n_reg and n_out of
- * eq. "reg_space_dim". */
+/* Sizes of direction `axis` (0-based): m = n + p - |D| (plus the extra
+ * multiplicities of repeated knots), n_reg and n_out of eq. "reg_space_dim". */
 int iffd_get_dims(iffd_handle h, int axis, int* m, int* n_reg, int* n_out);
 
 /* Copies the host-side 1D data of direction `axis` into caller HOST buffers
@@ -179,6 +197,12 @@ int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double*
  * buffers). Same layouts and errors as iffd_get_1d / iffd_setup. */
 int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
                    double* K_band, double* lam, double* dtilde, double* Vreg, double* W);
+
+/* iffd_host_axis with nrep repeated interior breakpoints, listed as
+ * (knot, extra) int pairs in reps (see iffd_setup_knots). Needs no GPU. */
+int iffd_host_axis_knots(int n, int p, const int* dirichlet, int nrep, const int* reps, int* m, int* n_reg,
+                         int* n_out, double* M_band, double* K_band, double* lam, double* dtilde, double* Vreg,
+                         double* W);
 
 /* Host-only: how the preconditioner passes of one direction carry its DST
  * (Table 1: DST-I for odd p, DST-II/III for even p, D = {0,1}) for the given

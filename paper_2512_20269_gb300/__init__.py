@@ -44,21 +44,33 @@ def host_transform(n: int, p: int, precision: str = "fp64", dirichlet=(1, 1)) ->
     return {"L": L.value, "F": F.value, "bluestein": F.value > L.value, "pencils": pp.value}
 
 
-def host_axis(n: int, p: int, dirichlet=(1, 1)) -> dict:
-    """1D tables of one direction computed by the library's host setup (no GPU)."""
+def _rep_pairs(rep) -> list:
+    """{knot: extra} or [(knot, extra), ...] -> flat [knot, extra, ...]."""
+    items = sorted(rep.items()) if isinstance(rep, dict) else [tuple(t) for t in (rep or [])]
+    return [int(v) for kv in items for v in kv]
+
+
+def host_axis(n: int, p: int, dirichlet=(1, 1), rep=None) -> dict:
+    """1D tables of one direction computed by the library's host setup (no GPU).
+    `rep` = {knot: extra}: breakpoint knot/n repeated `extra` more times
+    (reduced regularity)."""
     lib = _lib.load()
     dir_arr = (ctypes.c_int * 2)(*dirichlet)
+    flat = _rep_pairs(rep)
+    nrep = len(flat) // 2
+    rep_arr = (ctypes.c_int * max(1, len(flat)))(*flat)
     m, nr, no = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    check(lib.iffd_host_axis(n, p, dir_arr, ctypes.byref(m), ctypes.byref(nr), ctypes.byref(no),
-                             None, None, None, None, None, None), "iffd_host_axis")
+    check(lib.iffd_host_axis_knots(n, p, dir_arr, nrep, rep_arr, ctypes.byref(m), ctypes.byref(nr),
+                                   ctypes.byref(no), None, None, None, None, None, None), "iffd_host_axis_knots")
     m, nr, no = m.value, nr.value, no.value
     bw = 2 * p + 1
     out = {"m": m, "n_reg": nr, "n_out": no,
            "M_band": np.zeros(m * bw), "K_band": np.zeros(m * bw), "lam": np.zeros(m),
            "dtilde": np.zeros(nr), "V_reg": np.zeros(m * nr), "W": np.zeros(max(1, m * no))}
     dp = lambda a: a.ctypes.data_as(_lib.c_double_p)
-    check(lib.iffd_host_axis(n, p, dir_arr, None, None, None, dp(out["M_band"]), dp(out["K_band"]),
-                             dp(out["lam"]), dp(out["dtilde"]), dp(out["V_reg"]), dp(out["W"])), "iffd_host_axis")
+    check(lib.iffd_host_axis_knots(n, p, dir_arr, nrep, rep_arr, None, None, None, dp(out["M_band"]),
+                                   dp(out["K_band"]), dp(out["lam"]), dp(out["dtilde"]), dp(out["V_reg"]),
+                                   dp(out["W"])), "iffd_host_axis_knots")
     out["M_band"] = out["M_band"].reshape(m, bw)
     out["K_band"] = out["K_band"].reshape(m, bw)
     out["V_reg"] = out["V_reg"].reshape(m, nr)
@@ -73,12 +85,13 @@ class IFFDPlan:
     fastest; a tensor of shape (m_d, ..., m_1) in C order has that layout.
     `dirichlet`: one (at x_k = 0, at x_k = 1) flag pair per direction, 1 for
     homogeneous Dirichlet data, 0 for the natural condition (default: Dirichlet
-    on every face).
+    on every face). `knots`: per direction, None or {knot: extra} repeated
+    interior breakpoints (reduced regularity, iffd_setup_knots).
     """
 
     def __init__(self, d: int, n, p: int, precision: str = "fp64", precond: str = "iffd", rtol: float = 1e-8,
                  maxit: int = 500, true_residual: bool = True, flexible: bool = False, coef: str = "const",
-                 coef_amp: float = 0.5, stream=None, dirichlet=None):
+                 coef_amp: float = 0.5, stream=None, dirichlet=None, knots=None):
         import torch
         self._lib = _lib.load()
         n = [int(n)] * d if np.isscalar(n) else [int(x) for x in n]
@@ -101,8 +114,19 @@ class IFFDPlan:
         self.dirichlet = [tuple(flags[2 * k:2 * k + 2]) for k in range(d)]
         dd = (ctypes.c_int * (2 * d))(*flags)
         h = ctypes.c_void_p()
-        check(self._lib.iffd_setup(d, nn, p, dd, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)),
-              "iffd_setup")
+        if knots is None:
+            check(self._lib.iffd_setup(d, nn, p, dd, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)),
+                  "iffd_setup")
+        else:
+            if len(knots) != d:
+                raise ValueError("knots needs one entry per direction")
+            flat = [_rep_pairs(k) for k in knots]
+            nrep = (ctypes.c_int * d)(*[len(f) // 2 for f in flat])
+            allp = [v for f in flat for v in f]
+            reps = (ctypes.c_int * max(1, len(allp)))(*allp)
+            check(self._lib.iffd_setup_knots(d, nn, p, dd, nrep, reps, ctypes.byref(opt), _stream_handle(stream),
+                                             ctypes.byref(h)), "iffd_setup_knots")
+        self.knots = knots
         self._h = h
         self.m = []
         for a in range(d):
@@ -129,17 +153,23 @@ class IFFDPlan:
         return torch.empty(self.shape, dtype=torch.float64, device="cuda")
 
     def get_1d(self, axis: int) -> dict:
-        m = self.m[axis]
-        p = self.p
-        bw = 2 * p + 1
-        no = m - (self.n[axis] - 1 if p % 2 else self.n[axis])
+        """Host copies of the 1D tables of direction `axis` (iffd_get_1d):
+        banded M and K, Lambda~, D~_reg, dense V_reg (m x n_reg) and
+        W = V_out Q_out (m x n_out)."""
+        m, nr, no = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self._lib.iffd_get_dims(self._h, axis, ctypes.byref(m), ctypes.byref(nr), ctypes.byref(no)),
+              "iffd_get_dims")
+        m, nr, no = m.value, nr.value, no.value
+        bw = 2 * self.p + 1
         out = {"M_band": np.zeros(m * bw), "K_band": np.zeros(m * bw), "lam": np.zeros(m),
-               "dtilde": np.zeros(m - no), "VL": np.zeros(max(1, (p - 1) * (p // 2))), "W": np.zeros(max(1, m * no))}
+               "dtilde": np.zeros(nr), "V_reg": np.zeros(m * nr), "W": np.zeros(max(1, m * no))}
         dp = lambda a: a.ctypes.data_as(_lib.c_double_p)
         check(self._lib.iffd_get_1d(self._h, axis, dp(out["M_band"]), dp(out["K_band"]), dp(out["lam"]),
-                                    dp(out["dtilde"]), dp(out["VL"]), dp(out["W"])), "iffd_get_1d")
+                                    dp(out["dtilde"]), dp(out["V_reg"]), dp(out["W"])), "iffd_get_1d")
         out["M_band"] = out["M_band"].reshape(m, bw)
         out["K_band"] = out["K_band"].reshape(m, bw)
+        out["V_reg"] = out["V_reg"].reshape(m, nr)
+        out["W"] = out["W"][:m * no].reshape(m, no)
         return out
 
     # -- C ABI calls

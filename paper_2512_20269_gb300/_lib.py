@@ -45,6 +45,9 @@ SIGNATURES = [
     ("iffd_default_options", ctypes.c_int, [ctypes.POINTER(iffd_options)]),
     ("iffd_setup", ctypes.c_int, [ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, ctypes.POINTER(iffd_options),
                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("iffd_setup_knots", ctypes.c_int, [ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, c_int_p, c_int_p,
+                                        ctypes.POINTER(iffd_options), ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
     ("iffd_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, c_size_t_p]),
     ("iffd_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("iffd_set_geometry", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -53,6 +56,8 @@ SIGNATURES = [
     ("iffd_get_1d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [c_double_p] * 6),
     ("iffd_host_axis", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_int_p, c_int_p]
      + [c_double_p] * 6),
+    ("iffd_host_axis_knots", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, c_int_p,
+                                            c_int_p, c_int_p] + [c_double_p] * 6),
     ("iffd_host_transform", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, c_int_p,
                                            c_int_p]),
     ("iffd_apply_preconditioner", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

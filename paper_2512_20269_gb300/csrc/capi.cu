@@ -58,7 +58,7 @@ static std::vector<T> cast_vec(const std::vector<double>& v) {
 }
 
 struct AxisOffsets {
-  size_t VL, VR, W, lam, post, chirp, bhat;
+  size_t VL, VR, W, lam, post, chirp, bhat, VB, blk;
 };
 
 static bool register_radix(int r) { return r == 8 || r == 4 || r == 2 || r == 3 || r == 5; }
@@ -279,6 +279,9 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const cha
   t->blu = (F > L) ? 1 : 0;
   t->VL = reinterpret_cast<const T*>(base + o.VL);
   t->VR = reinterpret_cast<const T*>(base + o.VR);
+  t->nblk = (int)(A.blk.size() / 6);
+  t->blk = reinterpret_cast<const int*>(base + o.blk);
+  t->VB = reinterpret_cast<const T*>(base + o.VB);
   t->W = reinterpret_cast<const T*>(base + o.W);
   t->lam = reinterpret_cast<const T*>(base + o.lam);
   t->post = reinterpret_cast<const T*>(base + o.post);
@@ -400,6 +403,10 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     pa[a].od.post = tb.add_vec(post);
     pa[a].od.chirp = tb.add_vec(chirp);
     pa[a].od.bhat = tb.add_vec(bhat);
+    pa[a].od.VB = tb.add_vec(A.VB);
+    pa[a].od.blk = tb.add_vec(A.blk);
+    pa[a].of.blk = pa[a].od.blk;
+    pa[a].of.VB = tb.add_vec(cast_vec<float>(A.VB));
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
     pa[a].of.VR = tb.add_vec(cast_vec<float>(A.VR));
     pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
@@ -415,8 +422,9 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     // rows coupled to a B-spline with repeated end knots are general band rows:
     // the first 2p-1 rows at a Dirichlet end (its end B-spline is removed), 2p
     // rows at a natural end
+    // (with repeated knots every row is a general band row)
     int ilo = 2 * p - (A.dir0 ? 1 : 0), ihi = m - 2 * p + (A.dir1 ? 1 : 0);
-    if (ihi <= ilo) { ilo = 0; ihi = 0; }
+    if (ihi <= ilo || !A.reps.empty()) { ilo = 0; ihi = 0; }
     else {
       const int mid = (ilo + ihi) / 2;
       for (int k = 0; k <= p; ++k) {
@@ -791,7 +799,7 @@ int record_error(int code, const std::string& msg) { return fail(code, msg); }
 namespace iffd {
 
 int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, cudaStream_t stream,
-                iffd_plan** outp) {
+                iffd_plan** outp, const int* nrep, const int* reps) {
   if (!outp || !n_elems || !dirichlet) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
   if (d != 2 && d != 3) return fail(IFFD_ERR_INVALID_ARG, "d must be 2 or 3");
   if (p < 1) return fail(IFFD_ERR_INVALID_ARG, "p must be >= 1");
@@ -818,9 +826,13 @@ int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const if
     delete h;
     return fail(IFFD_ERR_CUDA, "no CUDA device");
   }
+  const int* rp = reps;
   for (int a = 0; a < d; ++a) {
     P->n[a] = n_elems[a];
-    std::string err = build_axis(n_elems[a], p, dirichlet[2 * a] != 0, dirichlet[2 * a + 1] != 0, &P->host[a]);
+    std::vector<std::pair<int, int>> ra;
+    for (int r = 0; nrep && r < nrep[a]; ++r, rp += 2) ra.push_back({rp[0], rp[1]});
+    std::string err =
+        build_axis(n_elems[a], p, dirichlet[2 * a] != 0, dirichlet[2 * a + 1] != 0, &P->host[a], ra);
     if (!err.empty()) {
       delete h;
       return fail(IFFD_ERR_UNSUPPORTED, err);
@@ -884,15 +896,29 @@ int iffd_default_options(iffd_options* opt) {
   return IFFD_OK;
 }
 
-int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
-               iffd_handle* out) {
+int iffd_setup_knots(int d, const int* n_elems, int p, const int* dirichlet, const int* nrep, const int* reps,
+                     const iffd_options* opt, void* stream, iffd_handle* out) {
   g_err.clear();
   if (!out) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (nrep) {
+    if (d != 2 && d != 3) return fail(IFFD_ERR_INVALID_ARG, "d must be 2 or 3");
+    int total = 0;
+    for (int a = 0; a < d; ++a) {
+      if (nrep[a] < 0) return fail(IFFD_ERR_INVALID_ARG, "negative repeated-knot count");
+      total += nrep[a];
+    }
+    if (total > 0 && !reps) return fail(IFFD_ERR_INVALID_ARG, "reps is NULL");
+  }
   iffd_plan* h = nullptr;
-  const int rc = plan_create(d, n_elems, p, dirichlet, opt, static_cast<cudaStream_t>(stream), &h);
+  const int rc = plan_create(d, n_elems, p, dirichlet, opt, static_cast<cudaStream_t>(stream), &h, nrep, reps);
   if (rc != IFFD_OK) return rc;
   *out = h;
   return IFFD_OK;
+}
+
+int iffd_setup(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, void* stream,
+               iffd_handle* out) {
+  return iffd_setup_knots(d, n_elems, p, dirichlet, nullptr, nullptr, opt, stream, out);
 }
 
 int iffd_workspace_bytes(iffd_handle h, size_t* bytes) {
@@ -910,16 +936,8 @@ int iffd_get_dims(iffd_handle h, int axis, int* m, int* n_reg, int* n_out) {
   return IFFD_OK;
 }
 
-// Dense V_reg (m x n_reg, row-major) from the edge blocks and the interior map.
-static void dense_vreg(const Axis1D& A, double* V) {
-  const int m = A.m, nr = A.n_reg;
-  std::memset(V, 0, sizeof(double) * (size_t)m * nr);
-  for (int r = 0; r < A.rowsL; ++r)
-    for (int c = 0; c < A.nL; ++c) V[(size_t)r * nr + c] = A.VL[(size_t)r * A.nL + c];
-  for (int r = 0; r < A.rowsR; ++r)
-    for (int c = 0; c < A.nR; ++c) V[(size_t)(m - 1 - r) * nr + (nr - 1 - c)] = A.VR[(size_t)r * A.nR + c];
-  for (int j = A.nL; j < nr - A.nR; ++j) V[(size_t)(j + A.o) * nr + j] = 1.0;
-}
+// Dense V_reg (m x n_reg, row-major) as the device passes apply it.
+static void dense_vreg(const Axis1D& A, double* V) { expand_vreg(A, V); }
 
 int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double* lam, double* dtilde, double* Vreg,
                 double* W) {
@@ -937,12 +955,16 @@ int iffd_get_1d(iffd_handle h, int axis, double* M_band, double* K_band, double*
   return IFFD_OK;
 }
 
-int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
-                   double* K_band, double* lam, double* dtilde, double* Vreg, double* W) {
+int iffd_host_axis_knots(int n, int p, const int* dirichlet, int nrep, const int* reps, int* m, int* n_reg,
+                         int* n_out, double* M_band, double* K_band, double* lam, double* dtilde, double* Vreg,
+                         double* W) {
   g_err.clear();
   if (!dirichlet) return fail(IFFD_ERR_INVALID_ARG, "dirichlet is NULL");
+  if (nrep < 0 || (nrep > 0 && !reps)) return fail(IFFD_ERR_INVALID_ARG, "bad repeated-knot list");
+  std::vector<std::pair<int, int>> ra;
+  for (int r = 0; r < nrep; ++r) ra.push_back({reps[2 * r], reps[2 * r + 1]});
   Axis1D A;
-  const std::string err = build_axis(n, p, dirichlet[0] != 0, dirichlet[1] != 0, &A);
+  const std::string err = build_axis(n, p, dirichlet[0] != 0, dirichlet[1] != 0, &A, ra);
   if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
   if (m) *m = A.m;
   if (n_reg) *n_reg = A.n_reg;
@@ -957,6 +979,11 @@ int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* 
   if (Vreg) dense_vreg(A, Vreg);
   cp(W, A.W);
   return IFFD_OK;
+}
+
+int iffd_host_axis(int n, int p, const int* dirichlet, int* m, int* n_reg, int* n_out, double* M_band,
+                   double* K_band, double* lam, double* dtilde, double* Vreg, double* W) {
+  return iffd_host_axis_knots(n, p, dirichlet, 0, nullptr, m, n_reg, n_out, M_band, K_band, lam, dtilde, Vreg, W);
 }
 
 int iffd_host_transform(int n, int p, const int* dirichlet, int precision, int* L, int* F, int* pencils) {

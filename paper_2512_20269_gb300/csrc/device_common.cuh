@@ -79,6 +79,12 @@ struct AxisTab {
   const T* VL;     // rowsL * nL (row-major), left edge block
   const T* VR;     // rowsR * nR (row-major), right edge block in mirrored form:
                    // V_reg[m-1-r][n_reg-1-c] = VR[r][c]
+  // interior blocks of V_reg around repeated knots (reduced regularity; nblk
+  // = 0 without): 6 ints per block (columns c0..c1-1, rows r0..r1-1, identity
+  // offset after the block, offset of its row-major values in VB)
+  int nblk;
+  const int* blk;
+  const T* VB;
   const T* W;      // m * n_out (row-major) = V_out Q_out
   const T* lam;    // m: Lambda_reg then Lambda_out
   const T* post;   // DST-II/III: 4 per k = 0..N/2;  DST-I: n_reg values 1/(2 D~);

@@ -3,12 +3,15 @@
 // Builds, for one parametric direction with Dirichlet set D (any subset of
 // {0, 1}; the eight (parity of p, D) cases of Table 1):
 //   * banded M and K of S_{p,h,D} by Cox-de Boor + (p+1)-point Gauss (Section 2);
-//   * the edge blocks of V_reg in the special basis of Section 6 (eq.
-//     "special_basis"), obtained exactly by Boehm knot insertion: inserting the
-//     knot 0 p times into the uniform (cardinal) knot vector turns every cardinal
-//     B-spline into a combination of the open-knot B-splines;
-//   * V_out = M^{-1} G^T, G the derivative functionals of eq. "reg_space" (its
-//     columns span the L2-orthogonal complement of S^reg), and Q_out, Lambda_out
+//   * V_reg in the special basis of Section 6 (eq. "special_basis"), obtained
+//     exactly by Boehm knot insertion: inserting the knots 0 and 1 p times (and
+//     every repeated interior knot its extra times) into the uniform (cardinal)
+//     knot vector turns every cardinal B-spline into a combination of the
+//     open-knot B-splines; stored as edge blocks, identity runs and, around
+//     repeated knots (Remark "reduced_regularity"), small dense blocks;
+//   * V_out = M^{-1} G^T, G the derivative functionals of eq. "reg_space" and,
+//     at repeated knots, the derivative jumps that S^reg forbids (its columns
+//     span the L2-orthogonal complement of S^reg), and Q_out, Lambda_out
 //     of eq. "eigendecomposition_out" by Cholesky + cyclic Jacobi;
 //   * Lambda_reg from Lemma 3 (with the factor (2 - 2cos t)/h^2 written as
 //     4 sin^2(t/2)/h^2) and D~_reg = D_reg Theta from the periodic symbols:
@@ -63,19 +66,39 @@ void gauss_legendre(int q, std::vector<double>* x, std::vector<double>* w) {
   }
 }
 
-// Open uniform knot vector xi_0..xi_{n+2p} on [0,1].
-std::vector<double> open_knots(int n, int p) {
+// p-open knot vector on the uniform grid z_k = k/n (Section 2): p+1 copies
+// of 0, the interior breakpoints, p+1 copies of 1. A breakpoint k listed in
+// `reps` as (k, e) appears 1 + e times (reduced regularity C^{p-1-e} there,
+// Remark "reduced_regularity").
+// With unit_h the knots are given in units of h (the integers 0..n).
+std::vector<double> open_knots(int n, int p, const std::vector<std::pair<int, int>>& reps = {},
+                               bool unit_h = false) {
+  const double scale = unit_h ? 1.0 : double(n);
   std::vector<double> k;
   for (int i = 0; i <= p; ++i) k.push_back(0.0);
-  for (int i = 1; i < n; ++i) k.push_back(double(i) / n);
-  for (int i = 0; i <= p; ++i) k.push_back(1.0);
+  size_t r = 0;
+  for (int i = 1; i < n; ++i) {
+    int copies = 1;
+    while (r < reps.size() && reps[r].first < i) ++r;
+    if (r < reps.size() && reps[r].first == i) copies += reps[r].second;
+    for (int c = 0; c < copies; ++c) k.push_back(double(i) / scale);
+  }
+  for (int i = 0; i <= p; ++i) k.push_back(double(n) / scale);
   return k;
 }
 
-// Values (order 0) or derivatives (order r) of B_{p,e..e+p} at x on element e.
-// Cox-de Boor for degree p-r, then r steps of the derivative recursion.
-void bspline_local(const std::vector<double>& kn, int p, int e, double x, int r, double* out) {
-  const int s = p + e;
+// Span of element e: the last index s with xi_s = e/n, so that xi_s <= x <
+// xi_{s+1} on the element and B_{p,s-p..s} are the B-splines nonzero there
+// (s = p + e without repeated knots).
+int element_span(const std::vector<double>& kn, int n, int e) {
+  const double z = double(e) / n;
+  return int(std::upper_bound(kn.begin(), kn.end(), z) - kn.begin()) - 1;
+}
+
+// Values (order 0) or derivatives (order r) of B_{p,s-p..s} at x on the
+// element of span s. Cox-de Boor for degree p-r, then r steps of the
+// derivative recursion; terms with a vanishing knot difference are dropped.
+void bspline_local(const std::vector<double>& kn, int p, int s, double x, int r, double* out) {
   std::vector<double> cur(p + 2, 0.0), nxt(p + 2, 0.0);
   // cur[t] holds B_{d, s-d+t}, t = 0..d
   cur[0] = 1.0;
@@ -292,28 +315,31 @@ void insert_knot(std::vector<double>* kn, std::vector<double>* c, int p, double 
   *c = nc;
 }
 
-// Banded M and K of S_{p,h,D} (B-spline 0 removed if dir0, n+p-1 if dir1),
-// with an optional weight w(x) under both integrals; (p+1)-point Gauss per element.
-void assemble_bands(int n, int p, bool dir0, bool dir1, double (*w)(double), std::vector<double>* Mb,
-                    std::vector<double>* Kb) {
-  const int m = n + p - (dir0 ? 1 : 0) - (dir1 ? 1 : 0), bw = 2 * p + 1, F = n + p;
+// Banded M and K of S_{p,h,D} on the knot vector kn (B-spline 0 removed if
+// dir0, the last one if dir1), with an optional weight w(x) under both
+// integrals; (p+1)-point Gauss per element. B_i and B_j share an element only
+// if |i - j| <= p, also with repeated knots, so the half bandwidth is p.
+void assemble_bands(int n, int p, const std::vector<double>& kn, bool dir0, bool dir1, double (*w)(double),
+                    std::vector<double>* Mb, std::vector<double>* Kb) {
+  const int F = (int)kn.size() - p - 1, bw = 2 * p + 1;
+  const int m = F - (dir0 ? 1 : 0) - (dir1 ? 1 : 0);
   const int s0 = dir0 ? 1 : 0;
-  const std::vector<double> kn = open_knots(n, p);
   std::vector<double> gx, gw;
   gauss_legendre(p + 1, &gx, &gw);
   std::vector<double> Mf((size_t)F * bw, 0.0), Kf((size_t)F * bw, 0.0);
   std::vector<double> B(p + 1), dB(p + 1);
   for (int e = 0; e < n; ++e) {
     const double a = double(e) / n, b = double(e + 1) / n;
+    const int sp = element_span(kn, n, e);
     for (int g = 0; g <= p; ++g) {
       const double x = 0.5 * (b - a) * gx[g] + 0.5 * (a + b);
       double wt = 0.5 * (b - a) * gw[g];
       if (w) wt *= w(x);
-      bspline_local(kn, p, e, x, 0, B.data());
-      bspline_local(kn, p, e, x, 1, dB.data());
+      bspline_local(kn, p, sp, x, 0, B.data());
+      bspline_local(kn, p, sp, x, 1, dB.data());
       for (int s = 0; s <= p; ++s)
         for (int t = 0; t <= p; ++t) {
-          const int i = e + s, j = e + t;
+          const int i = sp - p + s, j = sp - p + t;
           Mf[(size_t)i * bw + (j - i + p)] += wt * B[s] * B[t];
           Kf[(size_t)i * bw + (j - i + p)] += wt * dB[s] * dB[t];
         }
@@ -377,103 +403,331 @@ bool fft_factor(int L, std::vector<int>* radices) {
 
 namespace {
 
-// Edge block of the special basis at the end x = 0 for one end type (Section
-// 6, eq. "special_basis"): Dirichlet (dir) B~_i - B~_{dp-i}, i = 1..floor(p/2);
-// otherwise, p even, B~_i + B~_{1-i}, i = 1..p/2, and p odd, B~_0 and
-// B~_i + B~_{-i}, i = 1..(p-1)/2. Each combination of cardinal B-splines is
-// written in the open-knot basis exactly by inserting the knot 0 p times into
-// the uniform knot vector (Boehm). V[r * nfun + c]: coefficient of function c
-// on the reduced basis function r counted from the end (the B-spline at the
-// end itself is removed when dir). The right end is the mirror image.
-std::string edge_block(int p, bool dir, int* nfun, int* rows, std::vector<double>* V) {
+// A combination sum_t c_t N_{a_t} of uniform B-splines of degree p; N_a has
+// the knots a, a+1, .., a+p+1 (units of h). The cardinal B-spline B~_k of
+// eq. "Btilde" is N_{k - floor(p/2) - 1}.
+using Combo = std::vector<std::pair<double, int>>;
+using SparseCol = std::vector<std::pair<int, double>>;  // (index, value), increasing index
+
+// Edge functions of the special basis at the end x = 0 (Section 6, eq.
+// "special_basis"), counted from the end: at a Dirichlet end B~_i - B~_{dp-i},
+// i = 1..floor(p/2); at a natural end, p even, B~_i + B~_{1-i}, i = 1..p/2,
+// and p odd, B~_0 and B~_i + B~_{-i}, i = 1..(p-1)/2. The functions at x = 1
+// are their mirror images.
+std::vector<Combo> edge_combos(int p, bool dir) {
   const int half = p / 2;
   const int dp = (p % 2 == 1) ? 0 : 1;
-  std::vector<std::vector<std::pair<double, int>>> combos;
+  std::vector<std::vector<std::pair<double, int>>> card;
   if (dir) {
-    for (int i = 1; i <= half; ++i) combos.push_back({{1.0, i}, {-1.0, dp - i}});
+    for (int i = 1; i <= half; ++i) card.push_back({{1.0, i}, {-1.0, dp - i}});
   } else if (p % 2 == 0) {
-    for (int i = 1; i <= half; ++i) combos.push_back({{1.0, i}, {1.0, 1 - i}});
+    for (int i = 1; i <= half; ++i) card.push_back({{1.0, i}, {1.0, 1 - i}});
   } else {
-    combos.push_back({{1.0, 0}});
-    for (int i = 1; i <= (p - 1) / 2; ++i) combos.push_back({{1.0, i}, {1.0, -i}});
+    card.push_back({{1.0, 0}});
+    for (int i = 1; i <= (p - 1) / 2; ++i) card.push_back({{1.0, i}, {1.0, -i}});
   }
-  *nfun = (int)combos.size();
-  const int J0 = -3 * p - 4, J1 = 3 * p + 4;
-  const int s0 = dir ? 1 : 0;
-  std::vector<std::vector<double>> cols;
-  int maxrow = -1;
-  for (const auto& cb : combos) {
-    std::vector<double> knots;
-    for (int j = J0; j <= J1; ++j) knots.push_back(double(j));
-    std::vector<double> coef(knots.size() - p - 1, 0.0);
-    // B~_k is the uniform B-spline starting at knot k - floor(p/2) - 1
-    for (const auto& t : cb) coef[(t.second - half - 1) - J0] += t.first;
-    for (int r = 0; r < p; ++r) insert_knot(&knots, &coef, p, 0.0);
-    int z = 0;
-    while (knots[z] != 0.0) ++z;
-    // open B-spline with full index jf (counted from x = 0) <-> coef[z + jf]
-    if (dir && std::fabs(coef[z]) > 1e-13) return "special basis function does not vanish at a Dirichlet end";
-    std::vector<double> col;
-    for (int jf = s0; jf <= 2 * p + 2; ++jf) col.push_back(coef[z + jf]);
-    for (int r = 0; r < (int)col.size(); ++r)
-      if (std::fabs(col[r]) > 1e-13) maxrow = std::max(maxrow, r);
-    cols.push_back(col);
+  std::vector<Combo> out;
+  for (auto& c : card) {
+    Combo cb;
+    for (auto& t : c) cb.push_back({t.first, t.second - half - 1});
+    out.push_back(cb);
   }
-  *rows = maxrow + 1;
-  if (*rows > 2 * p) return "special basis edge function is not local";
-  V->assign((size_t)(*rows) * (*nfun), 0.0);
-  for (int c = 0; c < *nfun; ++c)
-    for (int r = 0; r < *rows; ++r) (*V)[(size_t)r * (*nfun) + c] = cols[c][r];
+  return out;
+}
+
+// Coefficients of the restriction to [0, 1] of the combination cb in the
+// open-knot basis whose knot vector, in units of h, is G (repeated interior
+// breakpoints `reps`). Exact up to rounding by Boehm insertion: inserting the
+// breakpoints 0 and n p times each and every repeated breakpoint k e_k times
+// into the uniform knots turns cb into a combination of B-splines that are,
+// inside [0, n], those of G (outside they vanish on [0, n]). Breakpoints
+// outside the support change no coefficient; the ones in it, its ends
+// included, are inserted so that the multiplicities match those of G. The
+// uniform knots are padded by p + 2 on each side so that every insertion
+// stays inside them. Returns (full B-spline index, coefficient), entries below
+// 1e-13 of the largest dropped.
+std::string restrict_combo(int n, int p, const Combo& cb, const std::vector<double>& G,
+                           const std::vector<std::pair<int, int>>& reps, SparseCol* col) {
+  int lo = cb[0].second, hi = cb[0].second + p + 1;
+  for (const auto& t : cb) {
+    lo = std::min(lo, t.second);
+    hi = std::max(hi, t.second + p + 1);
+  }
+  const int J0 = lo - p - 2, J1 = hi + p + 2;
+  std::vector<double> knots;
+  for (int j = J0; j <= J1; ++j) knots.push_back(double(j));
+  std::vector<double> coef(knots.size() - p - 1, 0.0);
+  for (const auto& t : cb) coef[t.second - J0] += t.first;
+  auto ins = [&](int t, int times) {
+    if (t < lo || t > hi) return;
+    for (int r = 0; r < times; ++r) insert_knot(&knots, &coef, p, double(t));
+  };
+  ins(0, p);
+  ins(n, p);
+  for (const auto& r : reps) ins(r.first, r.second);
+  double cmax = 0.0;
+  for (double c : coef) cmax = std::max(cmax, std::fabs(c));
+  col->clear();
+  for (int w = 0; w < (int)coef.size(); ++w) {
+    if (!(std::fabs(coef[w]) > 1e-13 * cmax)) continue;
+    const double a = knots[w], b = knots[w + p + 1];
+    if (b <= 0.0 || a >= double(n)) continue;  // vanishes on [0, n]
+    if (a < 0.0 || b > double(n)) return "special function does not restrict to the open-knot basis";
+    const int w0 = int(std::lower_bound(knots.begin(), knots.end(), a) - knots.begin());
+    const int j = int(std::lower_bound(G.begin(), G.end(), a) - G.begin()) + (w - w0);
+    if (j + p + 1 >= (int)G.size()) return "special function outside the open-knot basis";
+    for (int q = 0; q <= p + 1; ++q)
+      if (G[j + q] != knots[w + q]) return "special function: knot sequences do not match";
+    col->push_back({j, coef[w]});
+  }
   return "";
 }
 
-// Rows of the constraint matrix G of eq. "reg_space" for the end x = 0 on the
-// reduced basis (counted from the end): derivatives of orders 2, 4, .. (Dirichlet
-// end) or 1, 3, .. (otherwise) up to p - 1 of the open B-splines at 0.
-void end_constraints(const std::vector<double>& kn, int p, bool dir, int m, std::vector<std::vector<double>>* G) {
+// Derivative of order ord at x of the B-splines of the element of span sp, as a
+// row over the reduced basis (full index - s0; removed functions skipped),
+// scaled by sign and added to row.
+void add_functional(const std::vector<double>& kn, int p, int sp, double x, int ord, int s0, int m, double sign,
+                    std::vector<double>* row) {
   std::vector<double> d(p + 1);
-  const int s0 = dir ? 1 : 0;
-  for (int ord = dir ? 2 : 1; ord <= p - 1; ord += 2) {
-    bspline_local(kn, p, 0, 0.0, ord, d.data());
-    std::vector<double> row(m, 0.0);
-    for (int jf = s0; jf <= p && jf - s0 < m; ++jf) row[jf - s0] = d[jf];
-    G->push_back(row);
+  bspline_local(kn, p, sp, x, ord, d.data());
+  for (int t = 0; t <= p; ++t) {
+    const int r = sp - p + t - s0;
+    if (r >= 0 && r < m) (*row)[r] += sign * d[t];
   }
+}
+
+// The transform passes apply V_reg through the compressed form of Axis1D:
+// gather (y_j = sum_i V_reg[i][j] r_i, one output per column) and scatter
+// (x_i = sum_j V_reg[i][j] w_j, one output per row). These two functions
+// restate the kernels' column and row rules on the host.
+void device_col(const Axis1D& A, int j, SparseCol* out) {
+  out->clear();
+  if (j < A.nL) {
+    for (int r = 0; r < A.rowsL; ++r) out->push_back({r, A.VL[(size_t)r * A.nL + j]});
+    return;
+  }
+  if (j >= A.n_reg - A.nR) {
+    const int c = A.n_reg - 1 - j;
+    for (int r = A.rowsR - 1; r >= 0; --r) out->push_back({A.m - 1 - r, A.VR[(size_t)r * A.nR + c]});
+    return;
+  }
+  int o = A.o;
+  for (size_t b = 0; b < A.blk.size(); b += 6) {
+    const int c0 = A.blk[b], c1 = A.blk[b + 1], r0 = A.blk[b + 2], r1 = A.blk[b + 3], vo = A.blk[b + 5];
+    if (j < c0) break;
+    if (j < c1) {
+      for (int r = r0; r < r1; ++r) out->push_back({r, A.VB[(size_t)vo + (size_t)(r - r0) * (c1 - c0) + (j - c0)]});
+      return;
+    }
+    o = A.blk[b + 4];
+  }
+  out->push_back({j + o, 1.0});
+}
+
+void device_row(const Axis1D& A, int i, SparseCol* out) {
+  out->clear();
+  if (i < A.rowsL) {
+    for (int c = 0; c < A.nL; ++c) out->push_back({c, A.VL[(size_t)i * A.nL + c]});
+    return;
+  }
+  if (i >= A.m - A.rowsR) {
+    const int r = A.m - 1 - i;
+    for (int c = A.nR - 1; c >= 0; --c) out->push_back({A.n_reg - 1 - c, A.VR[(size_t)r * A.nR + c]});
+    return;
+  }
+  int o = A.o;
+  for (size_t b = 0; b < A.blk.size(); b += 6) {
+    const int c0 = A.blk[b], c1 = A.blk[b + 1], r0 = A.blk[b + 2], r1 = A.blk[b + 3], vo = A.blk[b + 5];
+    if (i < r0) break;
+    if (i < r1) {
+      for (int c = c0; c < c1; ++c) out->push_back({c, A.VB[(size_t)vo + (size_t)(i - r0) * (c1 - c0) + (c - c0)]});
+      return;
+    }
+    o = A.blk[b + 4];
+  }
+  out->push_back({i - o, 1.0});
+}
+
+// Two sparse vectors agree to 1e-13 (entries missing in one count as 0).
+bool same_sparse(const SparseCol& a, const SparseCol& b) {
+  size_t x = 0, y = 0;
+  while (x < a.size() || y < b.size()) {
+    double d;
+    if (y >= b.size() || (x < a.size() && a[x].first < b[y].first)) d = a[x++].second;
+    else if (x >= a.size() || b[y].first < a[x].first) d = b[y++].second;
+    else d = a[x++].second - b[y++].second;
+    if (!(std::fabs(d) <= 1e-13)) return false;
+  }
+  return true;
 }
 
 }  // namespace
 
-std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
+std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A,
+                       const std::vector<std::pair<int, int>>& reps_in) {
   std::ostringstream err;
   if (p < 1 || p > 16) { err << "degree p=" << p << " outside 1..16"; return err.str(); }
   if (n <= p) { err << "n=" << n << " must exceed p=" << p; return err.str(); }
+  std::vector<std::pair<int, int>> reps(reps_in);
+  std::sort(reps.begin(), reps.end());
+  int extra = 0;
+  for (size_t r = 0; r < reps.size(); ++r) {
+    if (reps[r].first < 1 || reps[r].first > n - 1) { err << "repeated knot " << reps[r].first << " outside 1..n-1"; return err.str(); }
+    if (reps[r].second < 1 || reps[r].second > p - 1) {
+      err << "extra multiplicity " << reps[r].second << " outside 1..p-1"; return err.str();
+    }
+    if (r > 0 && reps[r].first == reps[r - 1].first) { err << "knot " << reps[r].first << " repeated twice"; return err.str(); }
+    extra += reps[r].second;
+  }
   A->n = n;
   A->p = p;
   A->dir0 = dir0;
   A->dir1 = dir1;
-  A->m = n + p - (dir0 ? 1 : 0) - (dir1 ? 1 : 0);
+  A->reps = reps;
+  A->m = n + p + extra - (dir0 ? 1 : 0) - (dir1 ? 1 : 0);
   const int m = A->m;
+  const int s0 = dir0 ? 1 : 0;
 
   // ---- banded M, K of S_{p,h,D}
-  assemble_bands(n, p, dir0, dir1, nullptr, &A->Mband, &A->Kband);
-  const std::vector<double> kn = open_knots(n, p);
+  const std::vector<double> kn = open_knots(n, p, reps);
+  assemble_bands(n, p, kn, dir0, dir1, nullptr, &A->Mband, &A->Kband);
 
-  // ---- special basis: edge blocks (knot insertion) and the interior functions
-  std::string e = edge_block(p, dir0, &A->nL, &A->rowsL, &A->VL);
-  if (!e.empty()) return e;
-  e = edge_block(p, dir1, &A->nR, &A->rowsR, &A->VR);
-  if (!e.empty()) return e;
-  // interior special function i = floor(p/2)+1 .. n-ceil(p/2) is the open
-  // B-spline with full index i + floor((p-1)/2) (p odd) or i + p/2 - 1 (p even)
+  // ---- special basis (Section 6) in the open-knot basis. With repeated knots
+  // the regular space is the same (Remark "reduced_regularity"); only the
+  // coordinates of its functions change. Column j of V_reg: the left edge
+  // functions, the interior cardinal B-splines N_0 .. N_{n-p-1}, and the right
+  // edge functions (mirror images: computed at x = 0 on the mirrored knots).
+  const std::vector<double> kh = open_knots(n, p, reps, true);  // knots in units of h
+  std::vector<std::pair<int, int>> mreps;
+  for (auto it = reps.rbegin(); it != reps.rend(); ++it) mreps.push_back({n - it->first, it->second});
+  const std::vector<double> khm = open_knots(n, p, mreps, true);
+  const int F = (int)kh.size() - p - 1;
+  const std::vector<Combo> left = edge_combos(p, dir0), right = edge_combos(p, dir1);
+  A->nL = (int)left.size();
+  A->nR = (int)right.size();
   const int n_int = n - p;
   A->n_reg = A->nL + n_int + A->nR;
   A->n_out = m - A->n_reg;
-  const int first_full = (p / 2 + 1) + ((p % 2 == 1) ? (p - 1) / 2 : p / 2 - 1);
-  A->o = first_full - (dir0 ? 1 : 0) - A->nL;
-  // the device passes give every row of V_reg to one region: left block,
-  // interior, or right block
-  if (A->rowsL > A->nL + A->o || m - A->rowsR < A->nL + A->o + n_int || A->rowsL > m - A->rowsR)
-    return "n too small for the device layout of the special basis";
+  const int nr = A->n_reg;
+  std::vector<SparseCol> cols(nr);  // V_reg by columns, reduced row indices
+  SparseCol full;
+  for (int j = 0; j < nr; ++j) {
+    const bool is_right = j >= nr - A->nR;
+    std::string e;
+    if (j < A->nL) e = restrict_combo(n, p, left[j], kh, reps, &full);
+    else if (is_right) e = restrict_combo(n, p, right[nr - 1 - j], khm, mreps, &full);
+    else e = restrict_combo(n, p, Combo{{1.0, j - A->nL}}, kh, reps, &full);
+    if (!e.empty()) return e;
+    for (const auto& t : full) {
+      const int jf = is_right ? F - 1 - t.first : t.first;  // full index on kh
+      if ((dir0 && jf == 0) || (dir1 && jf == F - 1)) return "special basis function does not vanish at a Dirichlet end";
+      cols[j].push_back({jf - s0, t.second});
+    }
+    std::sort(cols[j].begin(), cols[j].end());
+  }
+  // compressed form used by the device passes: edge blocks, identity runs
+  // (column j is the B-spline with reduced index j + offset) and dense blocks
+  // over the runs of other interior columns (around repeated knots). A run
+  // that touches an edge block (no identity column between them, or shared
+  // rows) joins it; if the two edge blocks then overlap, the left block takes
+  // all of V_reg (small n only).
+  struct Run { int c0, c1, r0, r1; };
+  std::vector<Run> runs;
+  for (int j = A->nL; j < nr - A->nR; ++j) {
+    if (cols[j].empty()) return "special basis function vanishes";
+    const bool unit = cols[j].size() == 1 && cols[j][0].second == 1.0;
+    if (unit) continue;
+    if (runs.empty() || runs.back().c1 != j) runs.push_back({j, j + 1, cols[j].front().first, cols[j].back().first + 1});
+    Run& r = runs.back();
+    r.c1 = j + 1;
+    r.r0 = std::min(r.r0, cols[j].front().first);
+    r.r1 = std::max(r.r1, cols[j].back().first + 1);
+  }
+  A->rowsL = 0;
+  for (int j = 0; j < A->nL; ++j)
+    for (const auto& t : cols[j]) A->rowsL = std::max(A->rowsL, t.first + 1);
+  A->rowsR = 0;
+  for (int j = nr - A->nR; j < nr; ++j)
+    for (const auto& t : cols[j]) A->rowsR = std::max(A->rowsR, m - t.first);
+  size_t first = 0, last = runs.size();
+  while (first < last && (runs[first].c0 == A->nL || runs[first].r0 < A->rowsL)) {
+    A->nL = runs[first].c1;
+    A->rowsL = std::max(A->rowsL, runs[first].r1);
+    ++first;
+  }
+  while (last > first && (runs[last - 1].c1 == nr - A->nR || runs[last - 1].r1 > m - A->rowsR)) {
+    A->nR = nr - runs[last - 1].c0;
+    A->rowsR = std::max(A->rowsR, m - runs[last - 1].r0);
+    --last;
+  }
+  if (A->rowsL > m - A->rowsR || A->nL > nr - A->nR) {
+    A->nL = nr;
+    A->rowsL = m;
+    A->nR = 0;
+    A->rowsR = 0;
+    first = last = runs.size();
+  }
+  A->VL.assign((size_t)A->rowsL * A->nL, 0.0);
+  for (int j = 0; j < A->nL; ++j)
+    for (const auto& t : cols[j]) {
+      if (t.first >= A->rowsL) return "unexpected structure of V_reg";
+      A->VL[(size_t)t.first * A->nL + j] = t.second;
+    }
+  A->VR.assign((size_t)A->rowsR * A->nR, 0.0);
+  for (int j = nr - A->nR; j < nr; ++j)
+    for (const auto& t : cols[j]) {
+      if (m - 1 - t.first >= A->rowsR) return "unexpected structure of V_reg";
+      A->VR[(size_t)(m - 1 - t.first) * A->nR + (nr - 1 - j)] = t.second;
+    }
+  // identity offsets: o before the first block, then the offset after each block
+  A->blk.clear();
+  A->VB.clear();
+  A->o = 0;
+  bool have_o = false;
+  int cur = 0;
+  size_t next = first;
+  for (int j = A->nL; j < nr - A->nR; ++j) {
+    if (next < last && j == runs[next].c0) {
+      const Run& r = runs[next];
+      const int vo = (int)A->VB.size();
+      A->VB.resize(A->VB.size() + (size_t)(r.r1 - r.r0) * (r.c1 - r.c0), 0.0);
+      for (int c = r.c0; c < r.c1; ++c)
+        for (const auto& t : cols[c]) A->VB[(size_t)vo + (size_t)(t.first - r.r0) * (r.c1 - r.c0) + (c - r.c0)] = t.second;
+      // offset of the identity columns after the block (the block's own if none follow)
+      int after = cur;
+      if (r.c1 < nr - A->nR) after = cols[r.c1][0].first - r.c1;
+      A->blk.insert(A->blk.end(), {r.c0, r.c1, r.r0, r.r1, after, vo});
+      cur = after;
+      have_o = true;
+      j = r.c1 - 1;
+      ++next;
+      continue;
+    }
+    const int off = cols[j][0].first - j;
+    if (!have_o) {
+      A->o = cur = off;
+      have_o = true;
+    } else if (off != cur) {
+      return "unexpected structure of V_reg";
+    }
+  }
+  // the device rules must reproduce V_reg column by column and row by row
+  std::vector<SparseCol> rows(m);
+  for (int j = 0; j < nr; ++j)
+    for (const auto& t : cols[j]) rows[t.first].push_back({j, t.second});
+  SparseCol dv;
+  for (int j = 0; j < nr; ++j) {
+    device_col(*A, j, &dv);
+    for (const auto& t : dv)
+      if (t.first < 0 || t.first >= m) return "n too small for the device layout of the special basis";
+    if (!same_sparse(dv, cols[j])) return "n too small for the device layout of the special basis";
+  }
+  for (int i = 0; i < m; ++i) {
+    device_row(*A, i, &dv);
+    for (const auto& t : dv)
+      if (t.first < 0 || t.first >= nr) return "n too small for the device layout of the special basis";
+    if (!same_sparse(dv, rows[i])) return "n too small for the device layout of the special basis";
+  }
 
   // ---- Table 1: nodes x_i = (i - c) h, alpha_j = (j - e) pi, beta
   const bool odd = (p % 2 == 1);
@@ -548,30 +802,48 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
   A->wlo = 0;
   A->whi = m;
   if (no > 0) {
-    std::vector<std::vector<double>> G, GR;  // rows over the reduced basis
-    end_constraints(kn, p, dir0, m, &G);
-    end_constraints(kn, p, dir1, m, &GR);
-    // orthonormalise each end's rows (modified Gram-Schmidt; derivative values
-    // scale like h^-k), mirror the right end's rows
-    auto orthonormalise = [&](std::vector<std::vector<double>>& R) {
+    // rows of G over the reduced basis (eq. "reg_space"): derivatives of the
+    // even orders 2, 4, .. (Dirichlet end) or the odd orders 1, 3, .. (natural
+    // end) up to p - 1 at each end, and, at a breakpoint k repeated e times,
+    // the jumps of the derivatives of orders p - e .. p - 1 (functions of
+    // S^reg are C^{p-1} there). Each group is orthonormalised (modified
+    // Gram-Schmidt; derivative values scale like h^-k).
+    std::vector<std::vector<double>> G;
+    auto orthonormalise_into = [&](std::vector<std::vector<double>> R) {
       for (size_t a = 0; a < R.size(); ++a) {
         for (size_t b = 0; b < a; ++b) {
           double dot = 0;
           for (int i = 0; i < m; ++i) dot += R[a][i] * R[b][i];
           for (int i = 0; i < m; ++i) R[a][i] -= dot * R[b][i];
         }
-        double nr = 0;
-        for (int i = 0; i < m; ++i) nr += R[a][i] * R[a][i];
-        nr = std::sqrt(nr);
-        for (int i = 0; i < m; ++i) R[a][i] /= nr;
+        double nr2 = 0;
+        for (int i = 0; i < m; ++i) nr2 += R[a][i] * R[a][i];
+        const double nrm = std::sqrt(nr2);
+        for (int i = 0; i < m; ++i) R[a][i] /= nrm;
+        G.push_back(R[a]);
       }
     };
-    orthonormalise(G);
-    orthonormalise(GR);
-    for (const auto& r : GR) {
-      std::vector<double> row(m, 0.0);
-      for (int i = 0; i < m; ++i) row[m - 1 - i] = r[i];
-      G.push_back(row);
+    const int sp0 = element_span(kn, n, 0), sp1 = element_span(kn, n, n - 1);
+    for (int end = 0; end < 2; ++end) {
+      const bool dir = end == 0 ? dir0 : dir1;
+      std::vector<std::vector<double>> R;
+      for (int ord = dir ? 2 : 1; ord <= p - 1; ord += 2) {
+        std::vector<double> row(m, 0.0);
+        add_functional(kn, p, end == 0 ? sp0 : sp1, end == 0 ? 0.0 : 1.0, ord, s0, m, 1.0, &row);
+        R.push_back(row);
+      }
+      orthonormalise_into(R);
+    }
+    for (const auto& rk : reps) {
+      std::vector<std::vector<double>> R;
+      const double x = double(rk.first) / n;
+      for (int ord = p - rk.second; ord <= p - 1; ++ord) {
+        std::vector<double> row(m, 0.0);
+        add_functional(kn, p, element_span(kn, n, rk.first), x, ord, s0, m, 1.0, &row);
+        add_functional(kn, p, element_span(kn, n, rk.first - 1), x, ord, s0, m, -1.0, &row);
+        R.push_back(row);
+      }
+      orthonormalise_into(R);
     }
     if ((int)G.size() != no) return "constraint count differs from n_out";
     std::vector<double> Lm;
@@ -620,23 +892,32 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A) {
         if (std::fabs(A->W[(size_t)i * no + k]) > 1e-17 * wmax) return false;
       return true;
     };
-    const int mid = m / 2;
-    if (small(mid)) {
-      int lo_i = mid, hi_i = mid;
-      while (lo_i > 0 && small(lo_i - 1)) --lo_i;
-      while (hi_i < m && small(hi_i)) ++hi_i;
-      A->wlo = lo_i;
-      A->whi = hi_i;
-    } else {
-      A->wlo = m;
-      A->whi = m;
+    // the longest run of such rows is skipped by the passes
+    int best_lo = m, best_len = 0;
+    for (int i = 0; i < m;) {
+      if (!small(i)) { ++i; continue; }
+      int k = i;
+      while (k < m && small(k)) ++k;
+      if (k - i > best_len) { best_len = k - i; best_lo = i; }
+      i = k;
     }
+    A->wlo = best_lo;
+    A->whi = best_lo + best_len;
   }
   return "";
 }
 
+void expand_vreg(const Axis1D& A, double* V) {
+  std::fill(V, V + (size_t)A.m * A.n_reg, 0.0);
+  SparseCol c;
+  for (int j = 0; j < A.n_reg; ++j) {
+    device_col(A, j, &c);
+    for (const auto& t : c) V[(size_t)t.first * A.n_reg + j] = t.second;
+  }
+}
+
 void build_weighted_bands(Axis1D* A) {
-  assemble_bands(A->n, A->p, A->dir0, A->dir1, sin_2pi, &A->Msband, &A->Ksband);
+  assemble_bands(A->n, A->p, open_knots(A->n, A->p, A->reps), A->dir0, A->dir1, sin_2pi, &A->Msband, &A->Ksband);
 }
 
 std::string exact_fd_axis(const Axis1D& ax, std::vector<double>* Q, std::vector<double>* lam) {

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace iffd {
@@ -20,7 +21,10 @@ enum TransformKind : int {
 struct Axis1D {
   int n = 0, p = 0;          // elements, degree
   bool dir0 = true, dir1 = true;  // Dirichlet data at x = 0 / x = 1
-  int m = 0;                 // dim S_{p,h,D} = n + p - |D|
+  // repeated interior breakpoints (k, e): z_k = k/n appears 1 + e times in the
+  // knot vector (continuity C^{p-1-e} there; Remark "reduced_regularity")
+  std::vector<std::pair<int, int>> reps;
+  int m = 0;                 // dim S_{p,h,D} = n + p + sum e - |D|
   int n_reg = 0, n_out = 0;  // eq. "reg_space_dim"
   int kind = TK_DST23;
   // TK_GEN: DFT length 2 n gq; frequency of output j is gq j - gqe (FWD) and
@@ -30,12 +34,18 @@ struct Axis1D {
   // 1 / D~_j (n_reg)
   std::vector<double> gpost;
   // V_reg (Section 4): rows 0..rowsL-1 x cols 0..nL-1 is the left edge block,
-  // the interior special function j (nL <= j < n_reg - nR) is the B-spline with
-  // reduced index j + o, and the right edge block is the mirror image of VR:
-  // V_reg[m-1-r][n_reg-1-c] = VR[r][c] (c < nR, r < rowsR).
+  // the right edge block is the mirror image of VR: V_reg[m-1-r][n_reg-1-c] =
+  // VR[r][c] (c < nR, r < rowsR). An interior special function j (nL <= j <
+  // n_reg - nR) is either the B-spline with reduced index j + offset, where
+  // the offset is o before the first interior block and blk[6b+4] after block
+  // b, or a column of an interior block b: columns [blk[6b], blk[6b+1]) x rows
+  // [blk[6b+2], blk[6b+3]), dense row-major at VB + blk[6b+5]. Interior blocks
+  // exist only around repeated knots; blocks are ordered by columns and rows.
   int nL = 0, rowsL = 0, o = 0, nR = 0, rowsR = 0;
   std::vector<double> VL;    // rowsL * nL, row-major
   std::vector<double> VR;    // rowsR * nR, row-major (left-end form of the right block)
+  std::vector<int> blk;      // 6 per interior block: c0, c1, r0, r1, offset after, VB offset
+  std::vector<double> VB;
   // W = V_out Q_out (m x n_out, row-major), significant only on rows
   // [0, wlo) and [whi, m); the rows in between are below 1e-17 of max |W|.
   std::vector<double> W;
@@ -53,8 +63,14 @@ struct Axis1D {
 // same (p+1)-point Gauss rule per element as M and K (bands as above).
 void build_weighted_bands(Axis1D* A);
 
-// Builds all of the above. Returns an empty string on success, else a message.
-std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* out);
+// Builds all of the above. reps: repeated interior breakpoints (k, e), 1 <= k
+// <= n-1, 1 <= e <= p-1, each k at most once. Returns an empty string on
+// success, else a message.
+std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* out,
+                       const std::vector<std::pair<int, int>>& reps = {});
+
+// Dense V_reg (m x n_reg, row-major) as the device passes apply it.
+void expand_vreg(const Axis1D& A, double* V);
 
 // Exact generalized eigendecomposition K q = lambda M q, Q^T M Q = I
 // (dense, column-major Q: Q[i + j*m] = q_j[i]). Returns "" on success.

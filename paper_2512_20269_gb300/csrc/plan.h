@@ -150,8 +150,10 @@ struct iffd_plan {
 namespace iffd {
 
 // Builds a plan (host 1D setup + device tables) on the current device.
+// nrep[k] repeated knots for direction k, listed as (knot, extra) pairs in
+// reps, direction by direction; both may be NULL (no repeated knots).
 int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, cudaStream_t stream,
-                iffd_plan** out);
+                iffd_plan** out, const int* nrep = nullptr, const int* reps = nullptr);
 void plan_release(iffd_plan* h);
 StiffLaunch plan_stiff_launch(const Plan* P, int axis);
 template <typename T>

@@ -255,7 +255,21 @@ __device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& a
     for (int r = 0; r < ax.rowsR; ++r) s = fma(__ldg(ax.VR + r * ax.nR + c), row[ax.m - 1 - r], s);
     return s;
   }
-  return row[i + ax.o];
+  int o = ax.o;
+  for (int b = 0; b < ax.nblk; ++b) {  // interior blocks (repeated knots only)
+    const int* B = ax.blk + 6 * b;
+    const int c0 = __ldg(B), c1 = __ldg(B + 1);
+    if (i < c0) break;
+    if (i < c1) {
+      const int r0 = __ldg(B + 2), r1 = __ldg(B + 3), w = c1 - c0;
+      const T* V = ax.VB + __ldg(B + 5) + (i - c0);
+      T s = T(0);
+      for (int r = r0; r < r1; ++r) s = fma(__ldg(V + (r - r0) * w), row[r], s);
+      return s;
+    }
+    o = __ldg(B + 4);
+  }
+  return row[i + o];
 }
 
 template <typename T>
@@ -528,7 +542,23 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         x = Tc(0);
         for (int c = 0; c < ax.nR; ++c) x = fma(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
       } else {
-        x = wreg(i - ax.o);
+        int o = ax.o;
+        bool inblk = false;
+        for (int b = 0; b < ax.nblk; ++b) {  // interior blocks (repeated knots only)
+          const int* B = ax.blk + 6 * b;
+          const int r0 = __ldg(B + 2), r1 = __ldg(B + 3);
+          if (i < r0) break;
+          if (i < r1) {
+            const int c0 = __ldg(B), c1 = __ldg(B + 1);
+            const Tc* V = ax.VB + __ldg(B + 5) + (i - r0) * (c1 - c0);
+            x = Tc(0);
+            for (int c = c0; c < c1; ++c) x = fma(__ldg(V + (c - c0)), wreg(c), x);
+            inblk = true;
+            break;
+          }
+          o = __ldg(B + 4);
+        }
+        if (!inblk) x = wreg(i - o);
       }
       if (i < ax.wlo || i >= ax.whi) {
         for (int k = 0; k < ax.n_out; ++k) x = fma(__ldg(ax.W + i * ax.n_out + k), outv[pc * kMaxNout + k], x);

@@ -2,6 +2,7 @@
 declared in include/iffd.h, and its host-side 1D setup (no GPU involved)
 matches the oracle's independent construction of the same objects."""
 
+import ctypes
 import os
 import re
 
@@ -138,3 +139,64 @@ def test_transform_planner(lib, n, p):
     # direct FFT while FP32 runs Bluestein
     if (n, p) == (1939, 3):
         assert not host_transform(n, p, "fp64")["bluestein"] and host_transform(n, p, "fp32")["bluestein"]
+
+
+# repeated interior knots (Remark "reduced_regularity"): interior knots, knots
+# next to an end (their block joins the edge block), several knots, the
+# largest multiplicity, and tiny n where V_reg is kept as one dense block
+REP_HOST_CASES = [
+    (16, 3, (1, 1), {8: 2}), (16, 4, (1, 1), {5: 1, 11: 3}), (17, 2, (1, 0), {9: 1}),
+    (20, 5, (0, 0), {10: 4}), (18, 6, (0, 1), {6: 2, 12: 5}), (40, 4, (1, 1), {20: 1}),
+    (64, 3, (1, 1), {10: 1, 11: 2, 40: 1}), (30, 8, (1, 0), {15: 7}), (16, 4, (1, 1), {1: 1}),
+    (16, 4, (1, 1), {2: 3}), (16, 3, (0, 0), {15: 2}), (8, 7, (1, 1), {4: 6}),
+    (10, 3, (1, 1), {k: 1 for k in range(1, 10)}), (5, 4, (1, 1), {}), (3, 2, (1, 0), {}), (9, 8, (0, 1), {}),
+]
+
+
+@pytest.mark.parametrize("n,p,D,rep", REP_HOST_CASES)
+def test_host_setup_reduced_regularity_matches_oracle(lib, n, p, D, rep):
+    """With repeated knots: banded M/K on the knot vector with repeats, V_reg
+    (knot insertion, as the device passes apply it, vs the oracle's L2
+    projection), the unchanged Lambda_reg and D~_reg, and the remainder
+    operator including the jump constraints at the repeated knots."""
+    from paper_2512_20269_gb300 import host_axis
+    h = host_axis(n, p, D, rep)
+    s = splitting.axis_split(n, p, tuple(k for k, v in zip((0, 1), D) if v), rep=rep)
+    m, bw = s.m, 2 * p + 1
+    assert (h["m"], h["n_reg"], h["n_out"]) == (s.m, s.n_reg, s.n_out)
+    M = np.zeros((m, m))
+    K = np.zeros((m, m))
+    for i in range(m):
+        for dd in range(bw):
+            j = i + dd - p
+            if 0 <= j < m:
+                M[i, j] = h["M_band"][i, dd]
+                K[i, j] = h["K_band"][i, dd]
+    np.testing.assert_allclose(M, s.M, atol=1e-14 * np.abs(s.M).max())
+    np.testing.assert_allclose(K, s.K, atol=1e-13 * np.abs(s.K).max())
+    np.testing.assert_allclose(h["V_reg"], s.V_reg, atol=1e-12)
+    nr = h["n_reg"]
+    lam_scale = np.abs(s.lam_reg).max()
+    np.testing.assert_allclose(h["lam"][:nr], s.lam_reg, rtol=1e-12, atol=1e-13 * lam_scale)
+    np.testing.assert_allclose(h["dtilde"], s.Dt, rtol=1e-12)
+    if s.n_out:
+        lo, W = h["lam"][nr:], h["W"]
+        A1 = W @ np.diag(1 / lo) @ W.T
+        Wo = s.V_out @ s.Q_out
+        A2 = Wo @ np.diag(1 / s.lam_out) @ Wo.T
+        np.testing.assert_allclose(A1, A2, atol=1e-11 * np.abs(A2).max())
+        np.testing.assert_allclose(lo, s.lam_out, rtol=1e-11)
+
+
+@pytest.mark.parametrize("rep,msg", [({0: 1}, b"outside"), ({16: 1}, b"outside"), ({5: 4}, b"outside 1..p-1"),
+                                     ({5: 0}, b"outside 1..p-1")])
+def test_reduced_regularity_input_errors(lib, rep, msg):
+    from paper_2512_20269_gb300 import IFFDError, host_axis
+    with pytest.raises(IFFDError):
+        host_axis(16, 4, (1, 1), rep)
+    assert msg in lib.iffd_last_error()
+    d = (ctypes.c_int * 2)(1, 1)
+    reps = (ctypes.c_int * 4)(5, 1, 5, 2)  # the same knot twice
+    assert lib.iffd_host_axis_knots(16, 4, d, 2, reps, None, None, None, None, None, None, None, None, None) == 2
+    assert lib.iffd_host_axis_knots(16, 4, d, 1, None, None, None, None, None, None, None, None, None, None) == 1
+    assert lib.iffd_host_axis_knots(16, 4, d, -1, reps, None, None, None, None, None, None, None, None, None) == 1
