@@ -143,8 +143,9 @@ int iffd_workspace_bytes(iffd_handle h, size_t* bytes);
  * per tile (2..32, within 200 KB of shared memory) and the radix sequence of
  * the FFT (greedy radix 8, radix 4, or the greedy sequence reversed) of the
  * transform pass, whether the pass runs as a persistent kernel that loads its
- * next tile asynchronously (where the pass reads its own arithmetic type),
- * and the pencils per tile of the stiffness sweep. Each
+ * next tile asynchronously (where the pass reads its own arithmetic type) or,
+ * for FP32 transforms where it applies, as the warp-FFT pass, and the pencils
+ * per tile of the stiffness sweep. Each
  * candidate runs the plan's kernel on the workspace ws (iffd_workspace_bytes,
  * contents overwritten) on `stream`; the fastest of three timed launches wins.
  * Passes whose default launch has fewer than 4 x 152 CTAs (too small to fill
@@ -160,18 +161,26 @@ int iffd_autotune(iffd_handle h, void* ws, void* stream);
 /* Sets the launch geometry of direction `axis` by hand (the tuner's choices,
  * see iffd_autotune): pencils per tile of its transform pass and of its
  * stiffness sweep (2, 4, 8, 16 or 32; <= 0 keeps the current value) and the
- * pipelined transform kernel (1 on, 0 off, < 0 unchanged). The geometry does
- * not change any transformed value; it changes the grouping of the partial
- * sums of the dot products. Errors: INVALID_ARG, UNSUPPORTED (does not fit in
- * 200 KB of shared memory). Do not call while work of the plan is in flight. */
+ * schedule of its transform passes: `pipelined` 1 = persistent pipelined
+ * kernel, 0 = one tile per CTA, 2 = the warp-FFT pass (FP32 transforms only,
+ * DST-II/III directions -- even p, D = {0,1} -- with n_reg = 64, 128, 256 or
+ * 512: each pencil pair is transformed by the lanes of one warp, register
+ * butterflies, fixed tile; the default for such directions), < 0 unchanged.
+ * Setting a tile size or pipelined 0/1 on an FP32 plan selects the block
+ * kernel. The block-kernel geometry does not change any transformed value; it
+ * changes the grouping of the partial sums of the dot products (the warp-FFT
+ * pass rounds differently, within the FP32 tolerance). Errors: INVALID_ARG,
+ * UNSUPPORTED (does not fit in 200 KB of shared memory; warp-FFT pass not
+ * available for this direction). Do not call while work of the plan is in
+ * flight. */
 int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencils_stiffness, int pipelined);
 
 /* Launch geometry of direction `axis` (any pointer may be NULL): pencils per
  * tile of its transform pass (for the plan's precision) and of its stiffness
  * sweep, the radix sequence of its FFT (radices[0..*nstages), at most 12),
- * and whether its transform passes run as the persistent pipelined kernel
- * (*pipelined = 1: each CTA loads its next tile asynchronously while it
- * transforms the current one). */
+ * and the schedule of its transform passes (*pipelined = 1: persistent
+ * pipelined kernel, each CTA loads its next tile asynchronously while it
+ * transforms the current one; 2: FP32 warp-FFT pass; 0: one tile per CTA). */
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
                    int* nstages, int* pipelined);
 

@@ -219,9 +219,11 @@ class IFFDPlan:
         check(self._lib.iffd_autotune(self._h, self._ws_ptr, _stream_handle(stream)), "iffd_autotune")
         return self
 
-    def set_geometry(self, axis: int, pencils_transform: int = 0, pencils_stiffness: int = 0, pipelined=None):
-        """Set one direction's launch geometry by hand (iffd_set_geometry)."""
-        pl = -1 if pipelined is None else int(bool(pipelined))
+    def set_geometry(self, axis: int, pencils_transform: int = 0, pencils_stiffness: int = 0, pipelined=None,
+                     warp: bool = False):
+        """Set one direction's launch geometry by hand (iffd_set_geometry).
+        `warp`: run the FP32 warp-FFT transform pass (its tile is fixed)."""
+        pl = 2 if warp else (-1 if pipelined is None else int(bool(pipelined)))
         check(self._lib.iffd_set_geometry(self._h, axis, int(pencils_transform), int(pencils_stiffness), pl),
               "iffd_set_geometry")
         return self
@@ -233,7 +235,7 @@ class IFFDPlan:
         check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns),
                                        ctypes.byref(pl)), "iffd_get_tiles")
         return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value]),
-                "pipelined": bool(pl.value)}
+                "pipelined": pl.value == 1, "warp": pl.value == 2}
 
     def profile_enable(self, on: bool = True):
         check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")

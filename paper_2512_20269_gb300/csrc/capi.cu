@@ -373,6 +373,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     std::vector<FftPlan> vars;         // radix sequences of length L (and F)
     std::vector<size_t> var_d, var_f;  // their twiddle tables (FP64, FP32)
     int ilo, ihi;
+    size_t wt;                         // FP32 warp-FFT twiddles (DST-II/III directions)
   } pa[3];
   for (int a = 0; a < P->d; ++a) {
     const Axis1D& A = P->host[a];
@@ -407,6 +408,18 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     pa[a].od.blk = tb.add_vec(A.blk);
     pa[a].of.blk = pa[a].od.blk;
     pa[a].of.VB = tb.add_vec(cast_vec<float>(A.VB));
+    {
+      // exp(-2 pi i e / N), e < N, for the warp-FFT pass of length N = n_reg
+      std::vector<float> wt;
+      const int Nw = A.n_reg;
+      if (A.kind == TK_DST23 && (Nw == 64 || Nw == 128 || Nw == 256 || Nw == 512))
+        for (int e = 0; e < Nw; ++e) {
+          const double ang = -2.0 * 3.14159265358979323846264338327950288 * e / Nw;
+          wt.push_back((float)std::cos(ang));
+          wt.push_back((float)std::sin(ang));
+        }
+      pa[a].wt = tb.add_vec(wt);
+    }
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
     pa[a].of.VR = tb.add_vec(cast_vec<float>(A.VR));
     pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
@@ -503,6 +516,8 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     fill_axistab(&P->axf[a], A, L, F, base, pa[a].of);
     P->vsel_f[a] = default_var(P->fvar[a], F);
     set_fft(&P->axf[a], P->fvar[a][P->vsel_f[a]]);
+    P->wtab[a] = reinterpret_cast<const float2*>(base + pa[a].wt);
+    P->warp_f[a] = wpass_len(P->axf[a]) > 0 ? 1 : 0;
     BandTab& b = P->bt[a];
     b.m = A.m;
     b.p = A.p;
@@ -601,7 +616,34 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
   L.partial = nullptr;
   L.done = done;
   L.pipe = std::is_same<Tc, double>::value ? P->pipe_d[axis] : P->pipe_f[axis];
+  L.wN = 0;
+  L.wt = nullptr;
+  if constexpr (std::is_same<Tc, float>::value) {
+    const F32Geom g = f32_geom(*P, axis);
+    if (g.wN) {
+      L.PP = g.PP;
+      L.ldt = g.ldt;
+      L.wN = g.wN;
+      L.wt = g.wt;
+      L.pipe = 0;
+    }
+  }
   return L;
+}
+
+F32Geom f32_geom(const Plan& P, int a) {
+  F32Geom g{P.PPf[a], P.ldtf[a], 0, nullptr, 0};
+  const int wN = P.warp_f[a] ? wpass_len(P.axf[a]) : 0;
+  if (wN) {
+    g.wN = wN;
+    g.wt = P.wtab[a];
+    g.PP = wpass_pencils(wN);
+    g.ldt = P.axf[a].m | 1;
+    g.smem = wpass_smem_bytes(wN, g.ldt);
+  } else {
+    g.smem = precond_smem_bytes(g.PP, g.ldt, P.axf[a].F, sizeof(float));
+  }
+  return g;
 }
 template PassLaunch<double> make_pass<double>(const Plan*, int, const AxisTab<double>*, const int*, const int*,
                                               const int*);

@@ -245,6 +245,15 @@ PassDesc<Tc, Tc, Tc> pdesc_same(const Plan& P, int axis, const AxisTab<Tc>* tabs
   d.lamA = tabs[0].lam;
   d.lamB = (P.d == 3) ? tabs[1].lam : tabs[0].lam;
   d.done = done;
+  d.wN = 0;
+  d.wt = nullptr;
+  if constexpr (std::is_same<Tc, float>::value) {
+    const F32Geom g = f32_geom(P, axis);
+    d.PP = g.PP;
+    d.ldt = g.ldt;
+    d.wN = g.wN;
+    d.wt = g.wt;
+  }
   return d;
 }
 
@@ -296,11 +305,11 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       PassDesc<float, double, float> D{};
       auto T = pdesc_same<float>(P, 0, P.axf, P.PPf, P.ldtf, done);
       D.dims = T.dims; D.axis = 0; D.PP = T.PP; D.ldt = T.ldt; D.ax = T.ax; D.lamA = T.lamA; D.lamB = T.lamB;
+      D.wN = T.wN; D.wt = T.wt;
       D.done = done;
       D.in = vr(*s);
       D.out = vtf(*s);
-      seq->f_first.add(D, precond_tiles(P.dims, 0, P.PPf[0]),
-                       precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].F, sizeof(float)));
+      seq->f_first.add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
     }
     const int axes[3] = {1, d - 1, 1};
     for (int k = 0; k < 3; ++k) {
@@ -309,21 +318,20 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       auto D = pdesc_same<float>(P, a, P.axf, P.PPf, P.ldtf, done);
       D.in = vtf(*s);
       D.out = vtf(*s);
-      seq->f_mid[k].add(D, precond_tiles(P.dims, a, P.PPf[a]),
-                        precond_smem_bytes(P.PPf[a], P.ldtf[a], P.axf[a].F, sizeof(float)));
+      seq->f_mid[k].add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem);
     }
     {
       PassDesc<float, float, double> D{};
       auto T = pdesc_same<float>(P, 0, P.axf, P.PPf, P.ldtf, done);
       D.dims = T.dims; D.axis = 0; D.PP = T.PP; D.ldt = T.ldt; D.ax = T.ax; D.lamA = T.lamA; D.lamB = T.lamB;
+      D.wN = T.wN; D.wt = T.wt;
       D.done = done;
       D.in = vtf(*s);
       D.out = vz(*s);
       D.dot0 = vr(*s);
       D.dot1 = use_q ? vq(*s) : nullptr;
       D.partial = vpart(*s);
-      seq->f_last.add(D, precond_tiles(P.dims, 0, P.PPf[0]),
-                      precond_smem_bytes(P.PPf[0], P.ldtf[0], P.axf[0].F, sizeof(float)));
+      seq->f_last.add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
     }
   }
 }
@@ -395,8 +403,8 @@ int run_init(Engine* E, const std::vector<const Sys*>& sys) {
     vl.desc.push_back(v);
     vl.prefix.push_back(vl.prefix.back() + vec_grid(P.dims.N));
     fff.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
-    const int* PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? P.PPf : P.PPd;
-    frz0.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0[0])});
+    const int PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_geom(P, 0).PP : P.PPd[0];
+    frz0.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0)});
   }
   PrecondSeq pc;
   build_precond(sys, 1, false, &pc);
@@ -500,8 +508,8 @@ void build_lane(const Engine* E, const std::vector<const Sys*>& sys, IterSeq* ou
     it.upd.desc.push_back(v);
     it.upd.prefix.push_back(it.upd.prefix.back() + vec_grid(P.dims.N));
     it.frr.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
-    const int* PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? P.PPf : P.PPd;
-    it.frz.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0[0])});
+    const int PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_geom(P, 0).PP : P.PPd[0];
+    it.frz.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0)});
   }
   // A system's three sweeps must run in stage order. Groups are created in the
   // order systems are met (a 2D system creates no MID group), so order them by
@@ -519,7 +527,7 @@ std::pair<int, int> lane_key(const Sys& s) {
   const bool f32 = P.opt.precision == IFFD_PREC_FP32_TRANSFORM;
   size_t sm = 0;
   for (int a = 0; a < P.d; ++a)
-    sm = std::max(sm, f32 ? precond_smem_bytes(P.PPf[a], P.ldtf[a], P.axf[a].F, sizeof(float))
+    sm = std::max(sm, f32 ? f32_geom(P, a).smem
                           : precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].F, sizeof(double)));
   const int occ = (int)std::min<size_t>(4, std::max<size_t>(1, (227 * 1024) / std::max<size_t>(sm, 1)));
   return {occ, P.p};

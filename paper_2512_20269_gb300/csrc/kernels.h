@@ -23,6 +23,8 @@ struct PassLaunch {
   double* partial;
   const int* done;     // optional early-exit flag (PCG)
   int pipe;            // 1: persistent two-stage pipelined kernel (same input and arithmetic type only)
+  int wN;              // FP32 only: > 0 runs the warp-FFT pass of length wN (PP, ldt as wpass_pencils)
+  const float2* wt;    // its twiddles exp(-2 pi i e / wN), e < wN
 };
 
 // Per-system descriptor of one batched transform pass.
@@ -39,6 +41,8 @@ struct PassDesc {
   const double* dot1;
   double* partial;
   const int* done;
+  int wN;            // as PassLaunch
+  const float2* wt;
 };
 
 template <typename Tc, typename Tin, typename Tout>
@@ -51,6 +55,12 @@ size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt);  // pipeline
 cudaError_t launch_rden_fill(double* rden, const Dims& dims, const double* lamF, const double* lam0,
                              const double* lam1, cudaStream_t st);  // F: FFT length (AxisTab::F)
 int precond_tiles(const Dims& dims, int axis, int PP);
+// FP32 warp-FFT passes (DST-II/III directions of length 64, 128, 256 or 512):
+// the length the pass runs at for a direction with these tables (0: not
+// eligible), its pencils per tile, and its shared memory for tile row length ldt.
+int wpass_len(const AxisTab<float>& ax);
+int wpass_pencils(int N);
+size_t wpass_smem_bytes(int N, int ldt);
 
 template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);

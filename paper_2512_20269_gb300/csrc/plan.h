@@ -129,6 +129,11 @@ struct Plan {
   // 1: the direction's transform passes run as the persistent pipelined kernel
   // (where input and arithmetic types agree); chosen by the tuner
   int pipe_d[3] = {0, 0, 0}, pipe_f[3] = {0, 0, 0};
+  // FP32 transforms: 1 where the direction runs the warp-FFT pass (only if
+  // wpass_len(axf[a]) > 0; on by default, off once a tile size is set by
+  // hand or the tuner finds the block kernel faster), and its twiddle table
+  int warp_f[3] = {0, 0, 0};
+  const float2* wtab[3] = {nullptr, nullptr, nullptr};
   bool tuned = false;
   // exact FD tables
   const double* QT[3] = {nullptr, nullptr, nullptr};
@@ -155,6 +160,15 @@ namespace iffd {
 int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, cudaStream_t stream,
                 iffd_plan** out, const int* nrep = nullptr, const int* reps = nullptr);
 void plan_release(iffd_plan* h);
+// Launch geometry of the FP32 transform passes of direction a: pencils per
+// tile, tile row length, warp-FFT length (0: block kernel) and its twiddles,
+// shared memory of one (non-pipelined) CTA.
+struct F32Geom {
+  int PP, ldt, wN;
+  const float2* wt;
+  size_t smem;
+};
+F32Geom f32_geom(const Plan& P, int a);
 StiffLaunch plan_stiff_launch(const Plan* P, int axis);
 template <typename T>
 void set_fft(AxisTab<T>* t, const FftVar& v);

@@ -279,6 +279,12 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+}  // namespace iffd
+
+#include "precond_warp.cuh"
+
+namespace iffd {
+
 // A transform pass processes tiles of PP pencils along `axis` (tile_setup):
 // load the tile into shared memory, transform it (compute_tile), store it.
 // Partial dot products go to partial[ptile] (and partial[pstride + ptile]).
@@ -733,6 +739,29 @@ precond_pass_batched(const PassDesc<Tc, Tin, Tout>* __restrict__ sys, const long
   if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
   const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
   const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
+  if constexpr (std::is_same<Tc, float>::value) {
+    if (sd.wN != 0) {
+      switch (sd.wN) {
+        case 64:
+          wpass_body<64, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
+                                                sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+          break;
+        case 128:
+          wpass_body<128, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
+                                                 sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+          break;
+        case 256:
+          wpass_body<256, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
+                                                 sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+          break;
+        default:
+          wpass_body<512, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
+                                                 sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+          break;
+      }
+      return;
+    }
+  }
   precond_body<Tc, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.PP, sd.ldt, sd.ax, sd.lamA, sd.lamB,
                                           sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
 }
@@ -801,8 +830,53 @@ static cudaError_t launch_pipe_t(const PassLaunch<Tc>& P, const Tc* in, Tc* out,
   return cudaGetLastError();
 }
 
+int wpass_len(const AxisTab<float>& ax) {
+  const int N = ax.n_reg;
+  if (ax.kind != 1 || ax.blu || ax.L != N || ax.F != N) return 0;
+  return (N == 64 || N == 128 || N == 256 || N == 512) ? N : 0;
+}
+
+int wpass_pencils(int N) {
+  switch (N) {
+    case 64: return warp_pencils<64>();
+    case 128: return warp_pencils<128>();
+    case 256: return warp_pencils<256>();
+    default: return warp_pencils<512>();
+  }
+}
+
+size_t wpass_smem_bytes(int N, int ldt) {
+  const int PP = wpass_pencils(N);
+  return (size_t)PP * ldt * sizeof(float) + (size_t)(PP / 2) * wpad(N) * sizeof(Cplx<float>) +
+         (size_t)PP * kMaxNout * sizeof(float);
+}
+
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+static cudaError_t launch_wpass_n(const PassLaunch<float>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  auto kern = precond_wpass<N, Tin, Tout, MODE, NDOT>;
+  const size_t sm = wpass_smem_bytes(N, P.ldt);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
+  kern<<<tiles, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.ldt, P.ax, P.wt, P.lamA, P.lamB, P.dot0, P.dot1,
+                                    P.partial, P.done);
+  return cudaGetLastError();
+}
+
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  if constexpr (std::is_same<Tc, float>::value) {
+    if (P.wN != 0) {
+      if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
+      switch (P.wN) {
+        case 64: return launch_wpass_n<64, Tin, Tout, MODE, NDOT>(P, in, out, st);
+        case 128: return launch_wpass_n<128, Tin, Tout, MODE, NDOT>(P, in, out, st);
+        case 256: return launch_wpass_n<256, Tin, Tout, MODE, NDOT>(P, in, out, st);
+        case 512: return launch_wpass_n<512, Tin, Tout, MODE, NDOT>(P, in, out, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
   if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value) {
     if (P.pipe) return launch_pipe_t<Tc, MODE, NDOT>(P, in, out, st);
   }

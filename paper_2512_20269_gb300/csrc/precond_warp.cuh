@@ -1,0 +1,411 @@
+// FP32 transform passes with warp-local FFTs (included by precond.cu, after the
+// small DFTs, reg_gather and the tile helpers).
+//
+// Same operator as precond_pass (Q~^T, Q~, or both with the eigenvalue scaling,
+// eq. "preconditioner"), for the DST-II / DST-III directions of Table 1 (even
+// p, D = {0,1}) whose length N = n_reg is 64, 128, 256 or 512. The block-wide
+// kernel spends most of its instructions on run-time index arithmetic and on
+// shared-memory round trips between its steps; with FP32 arithmetic that, not
+// the FFT, limits it. Here a pencil pair belongs to LS lanes of one warp from
+// the edge gather to the output: the gather and Makhoul's reordering feed the
+// first FFT stage directly, every stage reads its R = N / LS values per lane
+// into registers, synchronises the warp and writes them back in place, and the
+// separation / twiddle / D~^{-1} step writes the results into the tile. All
+// sizes and the radix sequence (8, 8, then 8, 4 or 2) are compile-time
+// constants; the only block-wide steps are the coalesced tile load and store.
+#pragma once
+
+namespace iffd {
+
+// Complex values per lane (R) and lanes per sequence (LS) for length N; a warp
+// holds 32 / LS sequences, a CTA of 8 warps 8 * 32 / LS pencil pairs.
+template <int N>
+struct WarpFft;
+template <>
+struct WarpFft<64> {
+  static constexpr int R = 8, LS = 8;
+};
+template <>
+struct WarpFft<128> {
+  static constexpr int R = 8, LS = 16;
+};
+template <>
+struct WarpFft<256> {
+  static constexpr int R = 8, LS = 32;
+};
+template <>
+struct WarpFft<512> {
+  static constexpr int R = 16, LS = 32;
+};
+
+template <int N>
+__host__ __device__ constexpr int warp_pencils() {
+  return 2 * (kThreads / 32) * (32 / WarpFft<N>::LS);
+}
+
+// Sequence buffers skip one complex slot after every 8, so that the strided
+// stores of the early stages spread over the banks.
+__host__ __device__ constexpr int wpad(int i) { return i + (i >> 3); }
+template <int N>
+__host__ __device__ constexpr int wbuf_len() {
+  return N + N / 8;
+}
+
+template <int r>
+__device__ __forceinline__ void wdft(Cplx<float>* v) {
+  if constexpr (r == 2) dft2(v);
+  else if constexpr (r == 4) dft4(v);
+  else dft8(v);
+}
+
+// One Stockham stage of radix r and span Ns on the sequence in buf (the same
+// index map as fft_block): butterfly j takes in[j + q N/r], twiddles input q by
+// exp(-2 pi i q k / (Ns r)), k = j mod Ns (table wt[e] = exp(-2 pi i e / N)),
+// and writes out[(j - k) r + k + t Ns]. Lane ls runs butterflies ls + LS u.
+template <int N, int r, int Ns>
+__device__ __forceinline__ void wstage(Cplx<float>* buf, int ls, const float2* __restrict__ wt) {
+  constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, nb = N / r, BPL = R / r;
+  static_assert(N % r == 0 && R % r == 0 && nb == LS * BPL, "stage does not tile the warp");
+  Cplx<float> v[BPL][r];
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) {
+    const int j = ls + LS * u;
+#pragma unroll
+    for (int q = 0; q < r; ++q) v[u][q] = buf[wpad(j + q * nb)];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) {
+    const int j = ls + LS * u;
+    const int k = j & (Ns - 1);
+    if constexpr (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < r; ++q) {
+        const float2 w = __ldg(wt + q * k * (N / (Ns * r)));
+        v[u][q] = cmul(v[u][q], Cplx<float>{w.x, w.y});
+      }
+    }
+    wdft<r>(v[u]);
+    const int base = (j - k) * r + k;
+#pragma unroll
+    for (int t = 0; t < r; ++t) buf[wpad(base + t * Ns)] = v[u][t];
+  }
+  __syncwarp();
+}
+
+// The stages after the first (span Ns = 8).
+template <int N>
+__device__ __forceinline__ void wfft_rest(Cplx<float>* buf, int ls, const float2* __restrict__ wt) {
+  wstage<N, 8, 8>(buf, ls, wt);
+  if constexpr (N == 128) wstage<N, 2, 64>(buf, ls, wt);
+  if constexpr (N == 256) wstage<N, 4, 64>(buf, ls, wt);
+  if constexpr (N == 512) wstage<N, 8, 64>(buf, ls, wt);
+}
+
+// First stage (radix 8, span 1, no twiddles) with the inputs supplied by
+// src(l) (sequence element l).
+template <int N, typename Src>
+__device__ __forceinline__ void wstage_first(Cplx<float>* buf, int ls, Src src) {
+  constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, r = 8, nb = N / r, BPL = R / r;
+  Cplx<float> v[BPL][r];
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) {
+    const int j = ls + LS * u;
+#pragma unroll
+    for (int q = 0; q < r; ++q) v[u][q] = src(j + q * nb);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) {
+    const int j = ls + LS * u;
+    dft8(v[u]);
+#pragma unroll
+    for (int t = 0; t < r; ++t) buf[wpad(j * r + t)] = v[u][t];
+  }
+  __syncwarp();
+}
+
+// Sum over the LS lanes of one sequence group (aligned, power of two).
+template <int LS>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int off = LS / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// V_reg row rule of the scatter (x_i = sum_j V_reg[i][j] w_j): edge blocks,
+// interior blocks, identity runs (see AxisTab).
+template <typename WReg>
+__device__ __forceinline__ float wscatter_row(int i, const AxisTab<float>& ax, WReg wreg) {
+  const int m = ax.m, N = ax.n_reg;
+  if (i < ax.rowsL) {
+    float x = 0.f;
+    for (int c = 0; c < ax.nL; ++c) x = fmaf(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
+    return x;
+  }
+  if (i >= m - ax.rowsR) {
+    const int r = m - 1 - i;
+    float x = 0.f;
+    for (int c = 0; c < ax.nR; ++c) x = fmaf(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
+    return x;
+  }
+  int o = ax.o;
+  for (int b = 0; b < ax.nblk; ++b) {
+    const int* B = ax.blk + 6 * b;
+    const int r0 = __ldg(B + 2), r1 = __ldg(B + 3);
+    if (i < r0) break;
+    if (i < r1) {
+      const int c0 = __ldg(B), c1 = __ldg(B + 1);
+      const float* V = ax.VB + __ldg(B + 5) + (i - r0) * (c1 - c0);
+      float x = 0.f;
+      for (int c = c0; c < c1; ++c) x = fmaf(__ldg(V + (c - c0)), wreg(c), x);
+      return x;
+    }
+    o = __ldg(B + 4);
+  }
+  return wreg(i - o);
+}
+
+// One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
+                                           int axis, int ldt, const AxisTab<float>& ax, const float2* __restrict__ wt,
+                                           const float* __restrict__ lamA, const float* __restrict__ lamB,
+                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                           double* __restrict__ partial, long long tile_id, int ptile, int pstride,
+                                           unsigned char* smem) {
+  constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
+  const int m = ax.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* tile = reinterpret_cast<float*>(smem);
+  Cplx<float>* wbuf = reinterpret_cast<Cplx<float>*>(tile + (size_t)PP * ldt);
+  float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
+  __shared__ long long pbase[PP];
+  __shared__ int pia[PP], pib[PP];
+  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
+  __syncthreads();
+
+  // ---- coalesced tile load (padding pencils are zero)
+  if (axis == 0) {
+    for (int pc = warp; pc < PP; pc += kThreads / 32) {
+      float* row = tile + pc * ldt;
+      if (pc < g.nvalid) {
+        const Tin* src = in + pbase[pc];
+#pragma unroll 4
+        for (int i = lane; i < m; i += 32) row[i] = (float)src[i];
+      } else {
+        for (int i = lane; i < m; i += 32) row[i] = 0.f;
+      }
+    }
+  } else {
+    constexpr int RS = kThreads / PP;  // rows per sweep
+    const int pc = tid & (PP - 1);
+    const bool valid = pc < g.nvalid;
+    const Tin* src = in + pbase[pc];
+    const long long step = g.S * RS;
+    int i = tid / PP;
+    const Tin* p = src + i * g.S;
+    for (; i + 3 * RS < m; i += 4 * RS, p += 4 * step) {
+      Tin v0 = Tin(0), v1 = Tin(0), v2 = Tin(0), v3 = Tin(0);
+      if (valid) {
+        v0 = p[0];
+        v1 = p[step];
+        v2 = p[2 * step];
+        v3 = p[3 * step];
+      }
+      tile[pc * ldt + i] = (float)v0;
+      tile[pc * ldt + i + RS] = (float)v1;
+      tile[pc * ldt + i + 2 * RS] = (float)v2;
+      tile[pc * ldt + i + 3 * RS] = (float)v3;
+    }
+    for (; i < m; i += RS, p += step) tile[pc * ldt + i] = valid ? (float)p[0] : 0.f;
+  }
+  __syncthreads();
+
+  // ---- warp-local transform of pencil pair pr (pencils 2 pr, 2 pr + 1)
+  const int grp = lane / LS, ls = lane % LS;
+  const int pr = warp * G + grp;
+  float* ra = tile + (2 * pr) * ldt;
+  float* rb = ra + ldt;
+  float* ova = outv + (2 * pr) * kMaxNout;
+  float* ovb = ova + kMaxNout;
+  Cplx<float>* buf = wbuf + (size_t)pr * wbuf_len<N>();
+  const int nw = ax.n_out;
+
+  if (MODE == PM_FWD || MODE == PM_FUSED) {
+    // y_out = W^T r over the support rows of W
+    for (int k = 0; k < nw; ++k) {
+      float sa = 0.f, sb = 0.f;
+      for (int i = ls; i < ax.wlo; i += LS) {
+        const float w = __ldg(ax.W + i * nw + k);
+        sa = fmaf(w, ra[i], sa);
+        sb = fmaf(w, rb[i], sb);
+      }
+      for (int i = ax.whi + ls; i < m; i += LS) {
+        const float w = __ldg(ax.W + i * nw + k);
+        sa = fmaf(w, ra[i], sa);
+        sb = fmaf(w, rb[i], sb);
+      }
+      sa = group_sum<LS>(sa);
+      sb = group_sum<LS>(sb);
+      if (ls == 0) {
+        ova[k] = sa;
+        ovb[k] = sb;
+      }
+    }
+    // Makhoul order of u_i = (-1)^i y_i, y = V_reg^T r, as the first stage's input
+    wstage_first<N>(buf, ls, [&](int l) {
+      const int i = (l < N / 2) ? 2 * l : 2 * (N - 1 - l) + 1;
+      return Cplx<float>{neg_if(reg_gather(ra, i, ax), i & 1), neg_if(reg_gather(rb, i, ax), i & 1)};
+    });
+    wfft_rest<N>(buf, ls, wt);
+    // separation, twiddle and D~^{-1}: outputs N-1-k and k-1 from Z[k], Z[N-k]
+    for (int k = ls; k <= N / 2; k += LS) {
+      const Cplx<float> zk = buf[wpad(k)];
+      const Cplx<float> zm = buf[wpad(k == 0 ? 0 : N - k)];
+      const float Ar = zk.x + zm.x, Ai = zk.y - zm.y;
+      const float Br = zk.y + zm.y, Bi = zm.x - zk.x;
+      const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
+      ra[N - 1 - k] = fmaf(t.x, Ar, t.y * Ai);
+      rb[N - 1 - k] = fmaf(t.x, Br, t.y * Bi);
+      if (k > 0 && 2 * k != N) {
+        ra[k - 1] = fmaf(t.z, Ar, -t.w * Ai);
+        rb[k - 1] = fmaf(t.z, Br, -t.w * Bi);
+      }
+    }
+    __syncwarp();
+    for (int k = ls; k < nw; k += LS) {
+      ra[N + k] = ova[k];
+      rb[N + k] = ovb[k];
+    }
+    __syncwarp();
+  }
+
+  if (MODE == PM_FUSED) {
+    // divide by the summed eigenvalues of all directions
+    const int pa = 2 * pr, pb = pa + 1;
+    const float la = __ldg(lamA + pia[pa]), lb = __ldg(lamA + pia[pb]);
+    const float ma = (dims.d == 3) ? __ldg(lamB + pib[pa]) : 0.f;
+    const float mb = (dims.d == 3) ? __ldg(lamB + pib[pb]) : 0.f;
+    for (int i = ls; i < m; i += LS) {
+      const float li = __ldg(ax.lam + i);
+      float da = li + la, db = li + lb;
+      if (dims.d == 3) {
+        da += ma;
+        db += mb;
+      }
+      ra[i] = ra[i] / da;
+      rb[i] = rb[i] / db;
+    }
+    __syncwarp();
+  }
+
+  if (MODE == PM_BWD || MODE == PM_FUSED) {
+    for (int k = ls; k < nw; k += LS) {
+      ova[k] = ra[N + k];
+      ovb[k] = rb[N + k];
+    }
+    // inverse of the separation: G[k], G[N-k] from rows N-1-k and k-1
+    for (int k = ls; k <= N / 2; k += LS) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
+      if (k == 0 || 2 * k == N) {
+        const float s = t.x + t.x;
+        buf[wpad(k)] = {s * ra[N - 1 - k], s * rb[N - 1 - k]};
+      } else {
+        const float ar = fmaf(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
+        const float ai = fmaf(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
+        const float br = fmaf(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
+        const float bi = fmaf(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+        buf[wpad(k)] = {ar - bi, ai + br};
+        buf[wpad(N - k)] = {ar + bi, br - ai};
+      }
+    }
+    __syncwarp();
+    wstage<N, 8, 1>(buf, ls, wt);
+    wfft_rest<N>(buf, ls, wt);
+    // x = V_reg w + W z_out, row by row (DST-III output j is +-Re/Im Z[l(j)])
+    for (int i = ls; i < m; i += LS) {
+      auto wa = [&](int j) {
+        const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+        return neg_if(buf[wpad(l)].x, j & 1);
+      };
+      auto wb = [&](int j) {
+        const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+        return neg_if(buf[wpad(l)].y, j & 1);
+      };
+      float xa = wscatter_row(i, ax, wa), xb = wscatter_row(i, ax, wb);
+      if (i < ax.wlo || i >= ax.whi) {
+        for (int k = 0; k < nw; ++k) {
+          const float w = __ldg(ax.W + i * nw + k);
+          xa = fmaf(w, ova[k], xa);
+          xb = fmaf(w, ovb[k], xb);
+        }
+      }
+      ra[i] = xa;
+      rb[i] = xb;
+    }
+  }
+  __syncthreads();
+
+  // ---- coalesced store (and the partial dot products of a PCG step)
+  double d0 = 0.0, d1 = 0.0;
+  if (axis == 0) {
+    for (int pc = warp; pc < g.nvalid; pc += kThreads / 32) {
+      const float* row = tile + pc * ldt;
+      Tout* dst = out + pbase[pc];
+      const long long off0 = pbase[pc];
+      for (int i = lane; i < m; i += 32) {
+        const Tout v = (Tout)row[i];
+        dst[i] = v;
+        if (NDOT >= 1) d0 = fma(__ldg(dotv0 + off0 + i), (double)v, d0);
+        if (NDOT >= 2) d1 = fma(__ldg(dotv1 + off0 + i), (double)v, d1);
+      }
+    }
+  } else {
+    constexpr int RS = kThreads / PP;
+    const int pc = tid & (PP - 1);
+    if (pc < g.nvalid) {
+      const long long step = g.S * RS;
+      int i = tid / PP;
+      long long off = pbase[pc] + i * g.S;
+      for (; i < m; i += RS, off += step) {
+        const Tout v = (Tout)tile[pc * ldt + i];
+        out[off] = v;
+        if (NDOT >= 1) d0 = fma(__ldg(dotv0 + off), (double)v, d0);
+        if (NDOT >= 2) d1 = fma(__ldg(dotv1 + off), (double)v, d1);
+      }
+    }
+  }
+  if (NDOT >= 1) {
+    __shared__ double red[2][kThreads / 32];
+    d0 = warp_sum(d0);
+    d1 = warp_sum(d1);
+    if (lane == 0) {
+      red[0][warp] = d0;
+      red[1][warp] = d1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        s0 += red[0][w];
+        s1 += red[1][w];
+      }
+      partial[ptile] = s0;
+      if (NDOT >= 2) partial[pstride + ptile] = s1;
+    }
+  }
+}
+
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<float> ax, const float2* wt,
+              const float* __restrict__ lamA, const float* __restrict__ lamB, const double* __restrict__ dotv0,
+              const double* __restrict__ dotv1, double* __restrict__ partial, const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  wpass_body<N, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
+                                       blockIdx.x, blockIdx.x, gridDim.x, smem);
+}
+
+}  // namespace iffd

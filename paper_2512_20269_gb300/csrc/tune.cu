@@ -44,6 +44,7 @@ struct Choice {
   int pp;
   std::vector<int> radix;  // transform passes only
   int pipe = 0;            // transform passes only: pipelined persistent kernel
+  int warp = 0;            // FP32 transform passes only: warp-FFT pass
 };
 
 std::mutex g_mu;
@@ -113,11 +114,12 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
   std::vector<int> vars;
   for (size_t i = 0; i < P->fvar[a].size(); ++i)
     if (P->fvar[a][i].len == ax.F) vars.push_back((int)i);
-  auto apply = [&](int vi, int pp, int pipe) {
+  auto apply = [&](int vi, int pp, int pipe, int warp) {
     vsel[a] = vi;
     set_fft(&ax, P->fvar[a][vi]);
     PPs[a] = pp;
     pipes[a] = pipe;
+    if constexpr (!f64) P->warp_f[a] = warp;
   };
   if (precond_tiles(P->dims, a, PPs[a]) < kMinTuneTiles) return IFFD_OK;
   {
@@ -126,7 +128,7 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
     if (it != g_cache.end()) {
       for (int vi : vars)
         if (var_radices(P->fvar[a][vi]) == it->second.radix) {
-          apply(vi, it->second.pp, it->second.pipe);
+          apply(vi, it->second.pp, it->second.pipe, it->second.warp);
           return IFFD_OK;
         }
     }
@@ -135,37 +137,48 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
   double* z = reinterpret_cast<double*>(ws + P->off_z);
   float* tf = reinterpret_cast<float*>(ws + P->off_tf);
   float best = 1e30f;
-  int best_v = vsel[a], best_pp = PPs[a], best_pipe = pipes[a];
+  int best_v = vsel[a], best_pp = PPs[a], best_pipe = pipes[a], best_warp = 0;
+  auto time_pass = [&](float* ms) -> int {
+    const PassLaunch<Tc> L = make_pass<Tc>(P, a, tabs, PPs, ldts, nullptr);
+    if constexpr (f64) {
+      return time_best([&] { return launch_pass<double, double, double>(L, mode, 0, a == 0 ? r : z, z, st); }, st,
+                       tm, ms);
+    } else {
+      if (a == 0)
+        return time_best([&] { return launch_pass<float, double, float>(L, mode, 0, r, tf, st); }, st, tm, ms);
+      return time_best([&] { return launch_pass<float, float, float>(L, mode, 0, tf, tf, st); }, st, tm, ms);
+    }
+  };
+  if constexpr (!f64) {
+    if (wpass_len(ax) > 0) {  // the warp-FFT pass (its geometry is fixed)
+      apply(vsel[a], PPs[a], 0, 1);
+      float ms = 0.f;
+      if (int rc = time_pass(&ms)) return rc;
+      best = ms;
+      best_warp = 1;
+      best_pipe = 0;
+    }
+  }
   for (int vi : vars)
     for (int pp : kCandPP)
       for (int pipe = 0; pipe <= (pipe_ok ? 1 : 0); ++pipe) {
       const size_t need = pipe ? precond_smem_bytes_pipe(pp, ldts[a], ax.F, sizeof(Tc))
                                : precond_smem_bytes(pp, ldts[a], ax.F, sizeof(Tc));
       if (need > kMaxTuneSmem) continue;
-      apply(vi, pp, pipe);
-      const PassLaunch<Tc> L = make_pass<Tc>(P, a, tabs, PPs, ldts, nullptr);
+      apply(vi, pp, pipe, 0);
       float ms = 0.f;
-      int rc;
-      if constexpr (f64) {
-        rc = time_best([&] { return launch_pass<double, double, double>(L, mode, 0, a == 0 ? r : z, z, st); }, st,
-                       tm, &ms);
-      } else {
-        if (a == 0)
-          rc = time_best([&] { return launch_pass<float, double, float>(L, mode, 0, r, tf, st); }, st, tm, &ms);
-        else
-          rc = time_best([&] { return launch_pass<float, float, float>(L, mode, 0, tf, tf, st); }, st, tm, &ms);
-      }
-      if (rc) return rc;
+      if (int rc = time_pass(&ms)) return rc;
       if (ms < best) {
         best = ms;
         best_v = vi;
         best_pp = pp;
         best_pipe = pipe;
+        best_warp = 0;
       }
     }
-  apply(best_v, best_pp, best_pipe);
+  apply(best_v, best_pp, best_pipe, best_warp);
   std::lock_guard<std::mutex> lk(g_mu);
-  g_cache[key] = Choice{best_pp, var_radices(P->fvar[a][best_v]), best_pipe};
+  g_cache[key] = Choice{best_pp, var_radices(P->fvar[a][best_v]), best_pipe, best_warp};
   return IFFD_OK;
 }
 
@@ -279,6 +292,19 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
   auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
+  if (pipelined == 2) {
+    if (f64 || wpass_len(P.axf[axis]) == 0)
+      return fail(IFFD_ERR_UNSUPPORTED, "the warp-FFT pass needs FP32 transforms and a DST-II/III direction of "
+                                        "length 64, 128, 256 or 512");
+    if (pencils_transform > 0) return fail(IFFD_ERR_INVALID_ARG, "the warp-FFT pass has a fixed tile");
+    P.warp_f[axis] = 1;
+    P.pipe_f[axis] = 0;
+    pipelined = -1;
+  } else if (pipelined > 2) {
+    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1 or 2 (or < 0)");
+  } else if (!f64 && (pencils_transform > 0 || pipelined >= 0)) {
+    P.warp_f[axis] = 0;  // a block-kernel geometry set by hand
+  }
   if (pencils_transform > 0) {
     if (!pow2(pencils_transform)) return fail(IFFD_ERR_INVALID_ARG, "pencils per tile must be 2, 4, 8, 16 or 32");
     const int ldt = f64 ? P.ldtd[axis] : P.ldtf[axis];
@@ -314,12 +340,12 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   const Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
-  if (pencils_transform) *pencils_transform = f64 ? P.PPd[axis] : P.PPf[axis];
+  if (pencils_transform) *pencils_transform = f64 ? P.PPd[axis] : f32_geom(P, axis).PP;
   if (pencils_stiffness)
     *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
   const int nst = f64 ? P.axd[axis].nst : P.axf[axis].nst;
   if (nstages) *nstages = nst;
-  if (pipelined) *pipelined = f64 ? P.pipe_d[axis] : P.pipe_f[axis];
+  if (pipelined) *pipelined = f64 ? P.pipe_d[axis] : (f32_geom(P, axis).wN ? 2 : P.pipe_f[axis]);
   if (radices)
     for (int s = 0; s < nst; ++s) radices[s] = f64 ? P.axd[axis].radix[s] : P.axf[axis].radix[s];
   return IFFD_OK;

@@ -15,8 +15,9 @@ pytestmark = pytest.mark.gpu
 
 # A 2D system comes before 3D systems of the same degree (p = 4, 7): the 2D one
 # has no middle sweep, so this checks that every system's sweeps run in order.
+# (3, 64, 4) and (2, 128, 6) run their FP32 transforms as the warp-FFT pass.
 MIX = [(2, 30, 4), (3, 16, 2), (3, 24, 3), (3, 32, 4), (3, 16, 5), (3, 24, 6), (2, 64, 3), (3, 48, 4), (2, 40, 2),
-       (2, 33, 7), (3, 15, 7)]
+       (2, 33, 7), (3, 15, 7), (3, 64, 4), (2, 128, 6)]
 
 
 def _alone(torch, d, n, p, f, precision):
