@@ -271,8 +271,8 @@ static void fill_axistab(AxisTab<T>* t, const Axis1D& A, int L, int F, const cha
   t->gq = A.gq;
   t->gqc = A.gqc;
   t->gqe = A.gqe;
-  t->wlo = A.wlo;
-  t->whi = A.whi;
+  t->wlo = std::is_same<T, float>::value ? A.wlo_f : A.wlo;
+  t->whi = std::is_same<T, float>::value ? A.whi_f : A.whi;
   t->kind = A.kind;
   t->L = L;
   t->F = F;
@@ -517,7 +517,13 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     P->vsel_f[a] = default_var(P->fvar[a], F);
     set_fft(&P->axf[a], P->fvar[a][P->vsel_f[a]]);
     P->wtab[a] = reinterpret_cast<const float2*>(base + pa[a].wt);
-    P->warp_f[a] = wpass_len(P->axf[a]) > 0 ? 1 : 0;
+    P->warp_f[a] = 0;
+    if (const int wN = wpass_len(P->axf[a])) {
+      // the warp-FFT pass by default, unless its larger tiles leave the GPU
+      // underfilled where the block kernel's would not
+      const int tw = precond_tiles(P->dims, a, wpass_pencils(wN)), tb = precond_tiles(P->dims, a, P->PPf[a]);
+      P->warp_f[a] = (tw >= 152 || tb < 152) ? 1 : 0;
+    }
     BandTab& b = P->bt[a];
     b.m = A.m;
     b.p = A.p;
@@ -633,7 +639,7 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
 
 F32Geom f32_geom(const Plan& P, int a) {
   F32Geom g{P.PPf[a], P.ldtf[a], 0, nullptr, 0};
-  const int wN = P.warp_f[a] ? wpass_len(P.axf[a]) : 0;
+  const int wN = (P.warp_f[a] && P.dims.N / P.axf[a].m < (1LL << 31)) ? wpass_len(P.axf[a]) : 0;
   if (wN) {
     g.wN = wN;
     g.wt = P.wtab[a];

@@ -799,8 +799,8 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A,
   // ---- remainder space: V_out = M^{-1} G^T, then Q_out, Lambda_out
   const int no = A->n_out;
   A->W.assign((size_t)m * no, 0.0);
-  A->wlo = 0;
-  A->whi = m;
+  A->wlo = A->wlo_f = 0;
+  A->whi = A->whi_f = m;
   if (no > 0) {
     // rows of G over the reduced basis (eq. "reg_space"): derivatives of the
     // even orders 2, 4, .. (Dirichlet end) or the odd orders 1, 3, .. (natural
@@ -885,24 +885,29 @@ std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* A,
         wmax = std::max(wmax, std::fabs(s));
       }
     for (int k = 0; k < no; ++k) A->lam[A->n_reg + k] = lo[k];
-    // support: the maximal block of rows around the middle whose entries are all
-    // below 1e-17 max|W| is dropped (W decays geometrically away from both ends)
-    auto small = [&](int i) {
-      for (int k = 0; k < no; ++k)
-        if (std::fabs(A->W[(size_t)i * no + k]) > 1e-17 * wmax) return false;
-      return true;
+    // support: the longest run of rows whose entries are all below tol max|W|
+    // is skipped by the passes (W decays geometrically away from both ends and
+    // from repeated knots); tol = 1e-17 for FP64 passes, 1e-10 for FP32 ones
+    // (far below FP32 rounding: at most m 1e-10 of the result's scale)
+    auto support = [&](double tol, int* wlo, int* whi) {
+      auto small = [&](int i) {
+        for (int k = 0; k < no; ++k)
+          if (std::fabs(A->W[(size_t)i * no + k]) > tol * wmax) return false;
+        return true;
+      };
+      int best_lo = m, best_len = 0;
+      for (int i = 0; i < m;) {
+        if (!small(i)) { ++i; continue; }
+        int k = i;
+        while (k < m && small(k)) ++k;
+        if (k - i > best_len) { best_len = k - i; best_lo = i; }
+        i = k;
+      }
+      *wlo = best_lo;
+      *whi = best_lo + best_len;
     };
-    // the longest run of such rows is skipped by the passes
-    int best_lo = m, best_len = 0;
-    for (int i = 0; i < m;) {
-      if (!small(i)) { ++i; continue; }
-      int k = i;
-      while (k < m && small(k)) ++k;
-      if (k - i > best_len) { best_len = k - i; best_lo = i; }
-      i = k;
-    }
-    A->wlo = best_lo;
-    A->whi = best_lo + best_len;
+    support(1e-17, &A->wlo, &A->whi);
+    support(1e-10, &A->wlo_f, &A->whi_f);
   }
   return "";
 }

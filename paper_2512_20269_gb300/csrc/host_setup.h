@@ -50,6 +50,7 @@ struct Axis1D {
   // [0, wlo) and [whi, m); the rows in between are below 1e-17 of max |W|.
   std::vector<double> W;
   int wlo = 0, whi = 0;
+  int wlo_f = 0, whi_f = 0;  // the same for FP32 passes (rows below 1e-10 of max |W|)
   std::vector<double> lam;    // Lambda~ diagonal: Lambda_reg (n_reg) then Lambda_out (n_out)
   std::vector<double> dtilde; // D~_reg diagonal (n_reg)
   // Banded mass / stiffness of S_{p,h,D}: band[i*(2p+1) + (j-i+p)] = A[i][j].

@@ -51,6 +51,14 @@ __host__ __device__ constexpr int wbuf_len() {
   return N + N / 8;
 }
 
+// Complex values in the sequence buffers are float2 (8-byte aligned, one
+// 64-bit shared-memory access each).
+__device__ __forceinline__ Cplx<float> wld(const float2* b, int i) {
+  const float2 t = b[i];
+  return {t.x, t.y};
+}
+__device__ __forceinline__ void wst(float2* b, int i, Cplx<float> v) { b[i] = make_float2(v.x, v.y); }
+
 template <int r>
 __device__ __forceinline__ void wdft(Cplx<float>* v) {
   if constexpr (r == 2) dft2(v);
@@ -63,7 +71,7 @@ __device__ __forceinline__ void wdft(Cplx<float>* v) {
 // exp(-2 pi i q k / (Ns r)), k = j mod Ns (table wt[e] = exp(-2 pi i e / N)),
 // and writes out[(j - k) r + k + t Ns]. Lane ls runs butterflies ls + LS u.
 template <int N, int r, int Ns>
-__device__ __forceinline__ void wstage(Cplx<float>* buf, int ls, const float2* __restrict__ wt) {
+__device__ __forceinline__ void wstage(float2* buf, int ls, const float2* __restrict__ wt) {
   constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, nb = N / r, BPL = R / r;
   static_assert(N % r == 0 && R % r == 0 && nb == LS * BPL, "stage does not tile the warp");
   Cplx<float> v[BPL][r];
@@ -71,7 +79,7 @@ __device__ __forceinline__ void wstage(Cplx<float>* buf, int ls, const float2* _
   for (int u = 0; u < BPL; ++u) {
     const int j = ls + LS * u;
 #pragma unroll
-    for (int q = 0; q < r; ++q) v[u][q] = buf[wpad(j + q * nb)];
+    for (int q = 0; q < r; ++q) v[u][q] = wld(buf, wpad(j + q * nb));
   }
   __syncwarp();
 #pragma unroll
@@ -88,14 +96,14 @@ __device__ __forceinline__ void wstage(Cplx<float>* buf, int ls, const float2* _
     wdft<r>(v[u]);
     const int base = (j - k) * r + k;
 #pragma unroll
-    for (int t = 0; t < r; ++t) buf[wpad(base + t * Ns)] = v[u][t];
+    for (int t = 0; t < r; ++t) wst(buf, wpad(base + t * Ns), v[u][t]);
   }
   __syncwarp();
 }
 
 // The stages after the first (span Ns = 8).
 template <int N>
-__device__ __forceinline__ void wfft_rest(Cplx<float>* buf, int ls, const float2* __restrict__ wt) {
+__device__ __forceinline__ void wfft_rest(float2* buf, int ls, const float2* __restrict__ wt) {
   wstage<N, 8, 8>(buf, ls, wt);
   if constexpr (N == 128) wstage<N, 2, 64>(buf, ls, wt);
   if constexpr (N == 256) wstage<N, 4, 64>(buf, ls, wt);
@@ -103,16 +111,16 @@ __device__ __forceinline__ void wfft_rest(Cplx<float>* buf, int ls, const float2
 }
 
 // First stage (radix 8, span 1, no twiddles) with the inputs supplied by
-// src(l) (sequence element l).
+// src(j, q) (sequence element j + q N/8; j < N/8, q a constant once unrolled).
 template <int N, typename Src>
-__device__ __forceinline__ void wstage_first(Cplx<float>* buf, int ls, Src src) {
+__device__ __forceinline__ void wstage_first(float2* buf, int ls, Src src) {
   constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, r = 8, nb = N / r, BPL = R / r;
   Cplx<float> v[BPL][r];
 #pragma unroll
   for (int u = 0; u < BPL; ++u) {
     const int j = ls + LS * u;
 #pragma unroll
-    for (int q = 0; q < r; ++q) v[u][q] = src(j + q * nb);
+    for (int q = 0; q < r; ++q) v[u][q] = src(j, q);
   }
   __syncwarp();
 #pragma unroll
@@ -120,7 +128,7 @@ __device__ __forceinline__ void wstage_first(Cplx<float>* buf, int ls, Src src) 
     const int j = ls + LS * u;
     dft8(v[u]);
 #pragma unroll
-    for (int t = 0; t < r; ++t) buf[wpad(j * r + t)] = v[u][t];
+    for (int t = 0; t < r; ++t) wst(buf, wpad(j * r + t), v[u][t]);
   }
   __syncwarp();
 }
@@ -166,6 +174,38 @@ __device__ __forceinline__ float wscatter_row(int i, const AxisTab<float>& ax, W
   return wreg(i - o);
 }
 
+// tile_setup with 32-bit quotients (the host limits these passes to fewer
+// than 2^31 pencils per direction).
+__device__ __forceinline__ TileInfo wtile_setup(const Dims& dims, int axis, int PP, long long tile, long long* pbase,
+                                                int* pia, int* pib) {
+  const unsigned m0 = dims.m[0], m1 = dims.m[1];
+  const unsigned Q = (unsigned)(dims.N / dims.m[axis]);
+  const unsigned q0 = (unsigned)tile * (unsigned)PP;
+  TileInfo t;
+  t.nvalid = (int)min((unsigned)PP, Q - q0);
+  t.S = (axis == 0) ? 1 : ((axis == 1) ? (long long)m0 : (long long)m0 * m1);
+  for (int pc = threadIdx.x; pc < PP; pc += blockDim.x) {
+    unsigned q = q0 + pc;
+    if (q >= Q) q = Q - 1;
+    long long base;
+    unsigned ia, ib;
+    if (axis == 0) {
+      base = (long long)q * m0;
+      ib = q / m1;
+      ia = q - ib * m1;
+    } else {
+      const unsigned rest = q / m0, x = q - rest * m0;
+      ia = x;
+      ib = rest;
+      base = x + (long long)rest * ((axis == 1) ? (long long)m0 * m1 : (long long)m0);
+    }
+    pbase[pc] = base;
+    pia[pc] = (int)ia;
+    pib[pc] = (int)ib;
+  }
+  return t;
+}
+
 // One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
 template <int N, typename Tin, typename Tout, int MODE, int NDOT>
 __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
@@ -178,11 +218,11 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
   const int m = ax.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* tile = reinterpret_cast<float*>(smem);
-  Cplx<float>* wbuf = reinterpret_cast<Cplx<float>*>(tile + (size_t)PP * ldt);
+  float2* wbuf = reinterpret_cast<float2*>(tile + (size_t)PP * ldt);
   float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
   __shared__ long long pbase[PP];
   __shared__ int pia[PP], pib[PP];
-  const TileInfo g = tile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
+  const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
   __syncthreads();
 
   // ---- coalesced tile load (padding pencils are zero)
@@ -229,40 +269,65 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
   float* rb = ra + ldt;
   float* ova = outv + (2 * pr) * kMaxNout;
   float* ovb = ova + kMaxNout;
-  Cplx<float>* buf = wbuf + (size_t)pr * wbuf_len<N>();
+  float2* buf = wbuf + (size_t)pr * wbuf_len<N>();
   const int nw = ax.n_out;
 
   if (MODE == PM_FWD || MODE == PM_FUSED) {
-    // y_out = W^T r over the support rows of W
-    for (int k = 0; k < nw; ++k) {
-      float sa = 0.f, sb = 0.f;
-      for (int i = ls; i < ax.wlo; i += LS) {
-        const float w = __ldg(ax.W + i * nw + k);
-        sa = fmaf(w, ra[i], sa);
-        sb = fmaf(w, rb[i], sb);
-      }
-      for (int i = ax.whi + ls; i < m; i += LS) {
-        const float w = __ldg(ax.W + i * nw + k);
-        sa = fmaf(w, ra[i], sa);
-        sb = fmaf(w, rb[i], sb);
-      }
-      sa = group_sum<LS>(sa);
-      sb = group_sum<LS>(sb);
-      if (ls == 0) {
-        ova[k] = sa;
-        ovb[k] = sb;
-      }
+    // y_out = W^T r over the support rows of W, all columns per row read
+    {
+      float sa[kMaxNout], sb[kMaxNout];
+#pragma unroll
+      for (int k = 0; k < kMaxNout; ++k) sa[k] = sb[k] = 0.f;
+      auto rows = [&](int i0, int i1) {
+        for (int i = i0 + ls; i < i1; i += LS) {
+          const float xa = ra[i], xb = rb[i];
+          const float* w = ax.W + i * nw;
+#pragma unroll
+          for (int k = 0; k < kMaxNout; ++k)
+            if (k < nw) {
+              const float wk = __ldg(w + k);
+              sa[k] = fmaf(wk, xa, sa[k]);
+              sb[k] = fmaf(wk, xb, sb[k]);
+            }
+        }
+      };
+      rows(0, ax.wlo);
+      rows(ax.whi, m);
+#pragma unroll
+      for (int k = 0; k < kMaxNout; ++k)
+        if (k < nw) {
+          const float ya = group_sum<LS>(sa[k]), yb = group_sum<LS>(sb[k]);
+          if (ls == 0) {
+            ova[k] = ya;
+            ovb[k] = yb;
+          }
+        }
     }
-    // Makhoul order of u_i = (-1)^i y_i, y = V_reg^T r, as the first stage's input
-    wstage_first<N>(buf, ls, [&](int l) {
-      const int i = (l < N / 2) ? 2 * l : 2 * (N - 1 - l) + 1;
-      return Cplx<float>{neg_if(reg_gather(ra, i, ax), i & 1), neg_if(reg_gather(rb, i, ax), i & 1)};
+    // Makhoul order of u_i = (-1)^i y_i, y = V_reg^T r, as the first stage's
+    // input: element l = j + q N/8 lies in the first half exactly when q < 4
+    // (edge functions, i < nL <= 8 or i >= N - nR, sit only in the first and
+    // last eighths of each half, q = 0, 3, 4, 7, since N / 8 >= 8; interior
+    // blocks, and edge blocks widened by repeated knots, may sit anywhere)
+    const bool blocks = ax.nblk > 0 || ax.nL > 8 || ax.nR > 8;
+    wstage_first<N>(buf, ls, [&](int j, int q) {
+      const int l = j + q * (N / 8);
+      const bool hi = q >= 4;
+      const int i = hi ? 2 * (N - 1 - l) + 1 : 2 * l;
+      float ya, yb;
+      if ((q == 0 || q == 3 || q == 4 || q == 7 || blocks) && (i < ax.nL || i >= N - ax.nR || blocks)) {
+        ya = reg_gather(ra, i, ax);
+        yb = reg_gather(rb, i, ax);
+      } else {
+        ya = ra[i + ax.o];
+        yb = rb[i + ax.o];
+      }
+      return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
     });
     wfft_rest<N>(buf, ls, wt);
     // separation, twiddle and D~^{-1}: outputs N-1-k and k-1 from Z[k], Z[N-k]
     for (int k = ls; k <= N / 2; k += LS) {
-      const Cplx<float> zk = buf[wpad(k)];
-      const Cplx<float> zm = buf[wpad(k == 0 ? 0 : N - k)];
+      const Cplx<float> zk = wld(buf, wpad(k));
+      const Cplx<float> zm = wld(buf, wpad(k == 0 ? 0 : N - k));
       const float Ar = zk.x + zm.x, Ai = zk.y - zm.y;
       const float Br = zk.y + zm.y, Bi = zm.x - zk.x;
       const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
@@ -310,14 +375,14 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
       const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
       if (k == 0 || 2 * k == N) {
         const float s = t.x + t.x;
-        buf[wpad(k)] = {s * ra[N - 1 - k], s * rb[N - 1 - k]};
+        buf[wpad(k)] = make_float2(s * ra[N - 1 - k], s * rb[N - 1 - k]);
       } else {
         const float ar = fmaf(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
         const float ai = fmaf(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
         const float br = fmaf(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
         const float bi = fmaf(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
-        buf[wpad(k)] = {ar - bi, ai + br};
-        buf[wpad(N - k)] = {ar + bi, br - ai};
+        buf[wpad(k)] = make_float2(ar - bi, ai + br);
+        buf[wpad(N - k)] = make_float2(ar + bi, br - ai);
       }
     }
     __syncwarp();

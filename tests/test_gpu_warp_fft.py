@@ -28,6 +28,7 @@ def _rel(a, b):
 CASES = [
     (2, (64, 64), 4, None), (2, (128, 40), 2, None), (3, (64, 64, 64), 4, None), (3, (256, 37, 20), 6, None),
     (2, (512, 24), 4, None), (3, (128, 64, 30), 8, None), (2, (64, 128), 4, ({32: 1}, {20: 2, 100: 1})),
+    (2, (64, 128), 6, ({1: 1}, {126: 3})),
 ]
 
 
@@ -39,6 +40,8 @@ def test_warp_pass_matches_oracle_and_block_kernel(d, ns, p, knots):
     kw = {} if knots is None else {"knots": list(knots)}
     plan = IFFDPlan(d, list(ns), p, precision="fp32", **kw)
     warp_axes = [a for a in range(d) if ns[a] in (64, 128, 256, 512)]
+    for a in warp_axes:
+        plan.set_geometry(a, warp=True)
     for a in range(d):
         assert plan.tiles(a)["warp"] == (a in warp_axes)
     block = IFFDPlan(d, list(ns), p, precision="fp32", **kw)
@@ -68,6 +71,16 @@ def test_warp_pass_pcg():
     _, i32 = plan.pcg_solve(f)
     assert i32["status"] == 0 and i32["true_rel_res"] <= 1.1e-8
     assert i32["iters"] <= i64["iters"] + 2
+
+
+def test_warp_pass_default_fills_the_gpu():
+    """The warp-FFT pass is the default where its tiles (16 to 64 pencils)
+    still fill the GPU, or where the block kernel's would not either."""
+    require_gpu()
+    from paper_2512_20269_gb300 import IFFDPlan
+    assert all(IFFDPlan(3, 128, 4, precision="fp32").tiles(a)["warp"] for a in range(3))  # 529 tiles
+    assert not any(IFFDPlan(3, 64, 4, precision="fp32").tiles(a)["warp"] for a in range(3))  # 68 tiles
+    assert IFFDPlan(2, 512, 4, precision="fp32").tiles(0)["warp"]  # 33 tiles, block kernel 65
 
 
 def test_warp_geometry_switches():
