@@ -69,8 +69,11 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
     per_pass = 2.5 * math.log2(n) + 2 * n_out
     if kind.startswith("precond"):
         if precision == "fp32":
-            byt = {"precond_fwd": 6.0, "precond_fused": 8.0, "precond_bwd": 6.0}[kind] * 1.0
-            # FP32 intermediates: (8+4)/2 or (4+4) B per DoF; averaged per launch kind
+            # FP32 intermediates: the first FWD pass reads FP64 and writes FP32
+            # (12 B/DoF), the last BWD pass the reverse (12), the others read
+            # and write FP32 (8); per launch kind averaged over its directions
+            edge = (12.0 + 8.0 * (d - 2)) / (d - 1)
+            byt = {"precond_fwd": edge, "precond_fused": 8.0, "precond_bwd": edge}[kind]
             return byt * N, "B", "hbm"
         fl = per_pass * N if kind != "precond_fused" else (2 * per_pass + 3) * N
         return fl, "flop", "alu"
@@ -507,6 +510,34 @@ def main():
                               "true_rel_res": ichk["true_rel_res"]}
             del pv, pchk
 
+    # ---------------- preconditioner applies per second (inputs resident)
+    # algorithmic bytes per DoF of one apply: FP64, 16 per pass and 24 for the
+    # fused pass (it also reads 1/sum(lambda)); FP32 transforms, 12 for the
+    # first and last pass and 8 for the others
+    apply_stats = {}
+    if not args.no_variants:
+        for name, prec in (("fp64", "fp64"), ("fp32_transform", "fp32")):
+            pa = IFFDPlan(w.d, w.n, w.p, precision=prec, true_residual=False).autotune()
+            zz = pa.empty()
+            for _ in range(3):
+                pa.apply_preconditioner(f, zz)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            reps = 20
+            a.record(stream)
+            for _ in range(reps):
+                pa.apply_preconditioner(f, zz)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ams = a.elapsed_time(b) / reps
+            bpd = (16.0 * (2 * w.d - 2) + 24.0) if prec == "fp64" else (24.0 + 8.0 * (2 * w.d - 3))
+            gbs = bpd * w.N / (ams / 1e3) / 1e9
+            apply_stats[name] = {"ms": ams, "applies_per_s": 1e3 / ams, "alg_bytes_per_dof": bpd,
+                                 "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                                 "tiles": [pa.tiles(k) for k in range(w.d)]}
+            del pa, zz
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -523,7 +554,7 @@ def main():
                 "geometry": "iffd_autotune (tiles and radix sequences tuned in setup, excluded from timing)",
                 "tiles": [plan.tiles(a) for a in range(w.d)],
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clk,
-                "variants": variants, "kernels": rooflines,
+                "variants": variants, "precond_apply": apply_stats, "kernels": rooflines,
                 "hbm_frac_of_solve": None}
         # fraction of HBM peak of the whole solve at the method's algorithmic traffic
         # (176 B/DoF per PCG iteration, see the design notes)

@@ -193,6 +193,7 @@ struct PassLaunchB {
   std::vector<long long> prefix{0};
   size_t smem = 0;
   int mode = PM_FWD, ndot = 0;
+  int wN = 0;  // > 0: every system runs the FP32 warp-FFT pass of this length
   size_t off_desc = 0, off_prefix = 0;
   void add(const PassDesc<Tc, Tin, Tout>& d, int tiles, size_t sm) {
     desc.push_back(d);
@@ -227,11 +228,27 @@ struct PrecondSeq {
   bool fp32 = false;
   // FP64 passes
   std::vector<PassLaunchB<double, double, double>> d64;
-  // FP32 passes: first (r -> tf), middle (tf -> tf), last (tf -> z)
-  PassLaunchB<float, double, float> f_first;
-  std::vector<PassLaunchB<float, float, float>> f_mid;
-  PassLaunchB<float, float, double> f_last;
+  // FP32 passes: first (r -> tf), middle (tf -> tf), last (tf -> z); one
+  // launch per kernel: key 0 the block kernel, key N the warp-FFT pass of
+  // length N (systems of one pass are independent, so splitting a pass into
+  // launches does not change any result)
+  std::map<int, PassLaunchB<float, double, float>> f_first;
+  std::vector<std::map<int, PassLaunchB<float, float, float>>> f_mid;
+  std::map<int, PassLaunchB<float, float, double>> f_last;
 };
+
+template <typename L>
+L& pass_slot(std::map<int, L>& m, int wN, int mode, int ndot) {
+  auto it = m.find(wN);
+  if (it == m.end()) {
+    L l;
+    l.mode = mode;
+    l.ndot = ndot;
+    l.wN = wN;
+    it = m.emplace(wN, std::move(l)).first;
+  }
+  return it->second;
+}
 
 template <typename Tc>
 PassDesc<Tc, Tc, Tc> pdesc_same(const Plan& P, int axis, const AxisTab<Tc>* tabs, const int* PPs, const int* ldts,
@@ -288,15 +305,10 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
     }
     return;
   }
-  seq->f_first = {};
-  seq->f_first.mode = PM_FWD;
+  seq->f_first.clear();
   seq->f_mid.assign(3, {});
-  seq->f_mid[0].mode = PM_FWD;    // axis 1 (3D)
-  seq->f_mid[1].mode = PM_FUSED;  // last axis
-  seq->f_mid[2].mode = PM_BWD;    // axis 1 (3D)
-  seq->f_last = {};
-  seq->f_last.mode = PM_BWD;
-  seq->f_last.ndot = ndot;
+  seq->f_last.clear();
+  const int mid_modes[3] = {PM_FWD, PM_FUSED, PM_BWD};  // axis 1 (3D), last axis, axis 1 (3D)
   for (const Sys* s : sys) {
     const Plan& P = s->plan->P;
     const int* done = &vst(*s)->done;
@@ -309,7 +321,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.done = done;
       D.in = vr(*s);
       D.out = vtf(*s);
-      seq->f_first.add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
+      pass_slot(seq->f_first, D.wN, PM_FWD, 0).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
     }
     const int axes[3] = {1, d - 1, 1};
     for (int k = 0; k < 3; ++k) {
@@ -318,7 +330,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       auto D = pdesc_same<float>(P, a, P.axf, P.PPf, P.ldtf, done);
       D.in = vtf(*s);
       D.out = vtf(*s);
-      seq->f_mid[k].add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem);
+      pass_slot(seq->f_mid[k], D.wN, mid_modes[k], 0).add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem);
     }
     {
       PassDesc<float, float, double> D{};
@@ -331,7 +343,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.dot0 = vr(*s);
       D.dot1 = use_q ? vq(*s) : nullptr;
       D.partial = vpart(*s);
-      seq->f_last.add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
+      pass_slot(seq->f_last, D.wN, PM_BWD, ndot).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
     }
   }
 }
@@ -346,15 +358,25 @@ void stage_precond(Staging& sg, PrecondSeq& q) {
   if (!q.fp32) {
     for (auto& l : q.d64) stage_pass(sg, l);
   } else {
-    stage_pass(sg, q.f_first);
-    for (auto& l : q.f_mid) stage_pass(sg, l);
-    stage_pass(sg, q.f_last);
+    for (auto& kv : q.f_first) stage_pass(sg, kv.second);
+    for (auto& m : q.f_mid)
+      for (auto& kv : m) stage_pass(sg, kv.second);
+    for (auto& kv : q.f_last) stage_pass(sg, kv.second);
   }
 }
 
 template <typename Tc, typename Tin, typename Tout>
 int run_pass(Engine* E, char* base, PassLaunchB<Tc, Tin, Tout>& l, cudaStream_t st) {
   if (l.desc.empty()) return IFFD_OK;
+  if constexpr (std::is_same<Tc, float>::value) {
+    if (l.wN) {
+      IFFD_CUDA((launch_wpass_batched<Tin, Tout>(at<PassDesc<Tc, Tin, Tout>>(base, l.off_desc),
+                                                 at<long long>(base, l.off_prefix), (int)l.desc.size(),
+                                                 l.prefix.back(), l.smem, l.wN, l.mode, l.ndot, st)));
+      if (l.prefix.back() > 0) ++E->launches;
+      return IFFD_OK;
+    }
+  }
   IFFD_CUDA((launch_pass_batched<Tc, Tin, Tout>(at<PassDesc<Tc, Tin, Tout>>(base, l.off_desc),
                                                 at<long long>(base, l.off_prefix), (int)l.desc.size(),
                                                 l.prefix.back(), l.smem, l.mode, l.ndot, st)));
@@ -369,10 +391,14 @@ int run_precond_seq(Engine* E, char* base, PrecondSeq& q, cudaStream_t st) {
       if ((rc = run_pass(E, base, l, st))) return rc;
     return IFFD_OK;
   }
-  if ((rc = run_pass(E, base, q.f_first, st))) return rc;
-  for (auto& l : q.f_mid)
-    if ((rc = run_pass(E, base, l, st))) return rc;
-  return run_pass(E, base, q.f_last, st);
+  for (auto& kv : q.f_first)
+    if ((rc = run_pass(E, base, kv.second, st))) return rc;
+  for (auto& m : q.f_mid)
+    for (auto& kv : m)
+      if ((rc = run_pass(E, base, kv.second, st))) return rc;
+  for (auto& kv : q.f_last)
+    if ((rc = run_pass(E, base, kv.second, st))) return rc;
+  return IFFD_OK;
 }
 
 int run_fin(Engine* E, char* base, FinLaunchB& f, cudaStream_t st) {
@@ -562,9 +588,10 @@ int build_iteration(Engine* E) {
       IFFD_CUDA(launch_stiff_batched(l.p, l.stage, nullptr, nullptr, 0, 0, l.smem, E->st));
     IterSeq dry = it;
     for (auto& l : dry.pc.d64) l.prefix.assign(l.prefix.size(), 0);
-    dry.pc.f_first.prefix.assign(dry.pc.f_first.prefix.size(), 0);
-    for (auto& l : dry.pc.f_mid) l.prefix.assign(l.prefix.size(), 0);
-    dry.pc.f_last.prefix.assign(dry.pc.f_last.prefix.size(), 0);
+    for (auto& kv : dry.pc.f_first) kv.second.prefix.assign(kv.second.prefix.size(), 0);
+    for (auto& m : dry.pc.f_mid)
+      for (auto& kv : m) kv.second.prefix.assign(kv.second.prefix.size(), 0);
+    for (auto& kv : dry.pc.f_last) kv.second.prefix.assign(kv.second.prefix.size(), 0);
     const int rc = run_precond_seq(E, base, dry.pc, E->st);
     if (rc) return rc;
   }

@@ -49,6 +49,11 @@ template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                 long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st);
 
+// Batched warp-FFT passes: every system of the launch has wN == N.
+template <typename Tin, typename Tout>
+cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                 long long total_tiles, size_t smem, int N, int mode, int ndot, cudaStream_t st);
+
 size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);       // F: FFT length (AxisTab::F)
 size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt);  // pipelined kernel: one more tile
 // Fills AxisTab::rden of an FP64 plan (see device_common.cuh).

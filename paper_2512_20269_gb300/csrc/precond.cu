@@ -739,31 +739,37 @@ precond_pass_batched(const PassDesc<Tc, Tin, Tout>* __restrict__ sys, const long
   if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
   const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
   const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
-  if constexpr (std::is_same<Tc, float>::value) {
-    if (sd.wN != 0) {
-      switch (sd.wN) {
-        case 64:
-          wpass_body<64, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
-                                                sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
-          break;
-        case 128:
-          wpass_body<128, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
-                                                 sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
-          break;
-        case 256:
-          wpass_body<256, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
-                                                 sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
-          break;
-        default:
-          wpass_body<512, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
-                                                 sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
-          break;
-      }
-      return;
-    }
-  }
   precond_body<Tc, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.PP, sd.ldt, sd.ax, sd.lamA, sd.lamB,
                                           sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+}
+
+// Batched warp-FFT pass: every system of the launch runs the warp-FFT pass of
+// length N (a separate kernel from the block one, so that neither carries the
+// other's register allocation).
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const long long* __restrict__ tile_prefix,
+                      int nsys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ PassDesc<float, Tin, Tout> sd;
+  __shared__ int s_sys;
+  if (threadIdx.x == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {  // last s with tile_prefix[s] <= b
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_sys = lo;
+    sd = sys[lo];
+  }
+  __syncthreads();
+  if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
+  const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
+  const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
+  wpass_body<N, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA, sd.lamB,
+                                       sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
 }
 
 // rden[x + m0 (y + m1 z)] = 1 / (lam_F[i_F] + lam_0[x] (+ lam_1[y])): the
@@ -924,6 +930,50 @@ cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long l
   if (ndot == 1) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
   return launch_batched_t<Tc, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
 }
+
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+static cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                     long long total_tiles, size_t smem, cudaStream_t st) {
+  auto kern = precond_wpass_batched<N, Tin, Tout, MODE, NDOT>;
+  static size_t smem_set = 0;  // attribute is raised only when needed (not inside a graph capture)
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  if (total_tiles <= 0) return cudaSuccess;
+  kern<<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
+  return cudaGetLastError();
+}
+
+template <int N, typename Tin, typename Tout>
+static cudaError_t launch_wbatched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                     long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st) {
+  if (mode == PM_FWD) return launch_wbatched_t<N, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (mode == PM_FUSED)
+    return launch_wbatched_t<N, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (ndot == 0) return launch_wbatched_t<N, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (ndot == 1) return launch_wbatched_t<N, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  return launch_wbatched_t<N, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                 long long total_tiles, size_t smem, int N, int mode, int ndot, cudaStream_t st) {
+  switch (N) {
+    case 64: return launch_wbatched_n<64, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
+    case 128: return launch_wbatched_n<128, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
+    case 256: return launch_wbatched_n<256, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
+    case 512: return launch_wbatched_n<512, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_wpass_batched<double, float>(const PassDesc<float, double, float>*, const long long*, int,
+                                                         long long, size_t, int, int, int, cudaStream_t);
+template cudaError_t launch_wpass_batched<float, float>(const PassDesc<float, float, float>*, const long long*, int,
+                                                        long long, size_t, int, int, int, cudaStream_t);
+template cudaError_t launch_wpass_batched<float, double>(const PassDesc<float, float, double>*, const long long*, int,
+                                                         long long, size_t, int, int, int, cudaStream_t);
 
 #define IFFD_INST_BATCHED(Tc, Tin, Tout)                                                                      \
   template cudaError_t launch_pass_batched<Tc, Tin, Tout>(const PassDesc<Tc, Tin, Tout>*, const long long*, int, \
