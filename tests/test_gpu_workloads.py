@@ -80,7 +80,12 @@ def test_cube_n256_p4_full():
     zo = oracle_precond(f, w.n, w.p)
     assert rel_max_err(z, zo) <= 1e-12
     assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
-    del z, zo
+    # FP32 transforms (the warp-FFT pass on every direction at this size)
+    plan32 = IFFDPlan(w.d, w.n, w.p, precision="fp32")
+    assert all(plan32.tiles(a)["warp"] for a in range(w.d))
+    z32 = plan32.apply_preconditioner(fg).cpu().numpy()
+    assert np.linalg.norm(z32 - zo) <= 1e-5 * np.linalg.norm(zo)
+    del z, zo, z32
     Au = plan.apply_stiffness(fg).cpu().numpy()
     assert rel_max_err(Au, oracle_stiffness(f, w.n, w.p)) <= 1e-13
     del Au
@@ -90,3 +95,7 @@ def test_cube_n256_p4_full():
     res = np.linalg.norm(f - oracle_stiffness(u, w.n, w.p)) / np.linalg.norm(f)
     assert res <= 1.1e-8
     assert abs(res - info["true_rel_res"]) <= 1e-10
+    u32, i32 = plan32.pcg_solve(fg)
+    assert i32["status"] == 0 and i32["iters"] <= info["iters"] + 2
+    res32 = np.linalg.norm(f - oracle_stiffness(u32.cpu().numpy(), w.n, w.p)) / np.linalg.norm(f)
+    assert res32 <= 1.1e-8
