@@ -304,22 +304,47 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
         }
     }
     // Makhoul order of u_i = (-1)^i y_i, y = V_reg^T r, as the first stage's
-    // input: element l = j + q N/8 lies in the first half exactly when q < 4
-    // (edge functions, i < nL <= 8 or i >= N - nR, sit only in the first and
-    // last eighths of each half, q = 0, 3, 4, 7, since N / 8 >= 8; interior
-    // blocks, and edge blocks widened by repeated knots, may sit anywhere)
-    const bool blocks = ax.nblk > 0 || ax.nL > 8 || ax.nR > 8;
+    // input: element l = j + q N/8 lies in the first half exactly when q < 4.
+    // Without interior blocks (and with at most 4 edge functions per lane) the
+    // edge values y_i (i < nL, i >= N - nR) are computed first and stored
+    // in the rows an identity column would use, row i + o: those rows belong to
+    // no other column and have been read already (by the edge dot products and
+    // W^T r), so the gather below is one branch-free read per element.
+    const int ne = ax.nL + ax.nR;
+    const bool uniform = ax.nblk == 0 && 2 * ne <= 4 * LS;
+    if (uniform) {
+      // every lane reads its (at most 4) edge values before any lane writes
+      float ev[4];
+      int slot[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int t = ls + r * LS;
+        slot[r] = -1;
+        ev[r] = 0.f;
+        if (t < 2 * ne) {
+          const int c = t < ne ? t : t - ne;
+          const int i = c < ax.nL ? c : N - ax.nR + (c - ax.nL);
+          ev[r] = reg_gather(t < ne ? ra : rb, i, ax);
+          slot[r] = (t < ne ? 0 : ldt) + i + ax.o;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (slot[r] >= 0) ra[slot[r]] = ev[r];
+      __syncwarp();
+    }
     wstage_first<N>(buf, ls, [&](int j, int q) {
       const int l = j + q * (N / 8);
       const bool hi = q >= 4;
       const int i = hi ? 2 * (N - 1 - l) + 1 : 2 * l;
       float ya, yb;
-      if ((q == 0 || q == 3 || q == 4 || q == 7 || blocks) && (i < ax.nL || i >= N - ax.nR || blocks)) {
-        ya = reg_gather(ra, i, ax);
-        yb = reg_gather(rb, i, ax);
-      } else {
+      if (uniform) {
         ya = ra[i + ax.o];
         yb = rb[i + ax.o];
+      } else {
+        ya = reg_gather(ra, i, ax);
+        yb = reg_gather(rb, i, ax);
       }
       return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
     });
@@ -398,7 +423,14 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
         const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
         return neg_if(buf[wpad(l)].y, j & 1);
       };
-      float xa = wscatter_row(i, ax, wa), xb = wscatter_row(i, ax, wb);
+      float xa, xb;
+      if (ax.nblk == 0 && i >= ax.rowsL && i < m - ax.rowsR) {  // identity rows
+        xa = wa(i - ax.o);
+        xb = wb(i - ax.o);
+      } else {
+        xa = wscatter_row(i, ax, wa);
+        xb = wscatter_row(i, ax, wb);
+      }
       if (i < ax.wlo || i >= ax.whi) {
         for (int k = 0; k < nw; ++k) {
           const float w = __ldg(ax.W + i * nw + k);
