@@ -165,7 +165,9 @@ int iffd_autotune(iffd_handle h, void* ws, void* stream);
  * kernel, 0 = one tile per CTA, 2 = the warp-FFT pass (FP32 transforms only,
  * DST-II/III directions -- even p, D = {0,1} -- with n_reg = 64, 128, 256 or
  * 512: each pencil pair is transformed by the lanes of one warp, register
- * butterflies, fixed tile; the default for such directions), < 0 unchanged.
+ * butterflies, fixed tile; the default for such directions), 3 = the
+ * warp-FFT pass as a persistent kernel that loads its next tile
+ * asynchronously (passes with FP32 input), < 0 unchanged.
  * Setting a tile size or pipelined 0/1 on an FP32 plan selects the block
  * kernel. The block-kernel geometry does not change any transformed value; it
  * changes the grouping of the partial sums of the dot products (the warp-FFT
@@ -180,7 +182,8 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
  * sweep, the radix sequence of its FFT (radices[0..*nstages), at most 12),
  * and the schedule of its transform passes (*pipelined = 1: persistent
  * pipelined kernel, each CTA loads its next tile asynchronously while it
- * transforms the current one; 2: FP32 warp-FFT pass; 0: one tile per CTA). */
+ * transforms the current one; 2: FP32 warp-FFT pass; 3: the same,
+ * persistent and pipelined; 0: one tile per CTA). */
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
                    int* nstages, int* pipelined);
 

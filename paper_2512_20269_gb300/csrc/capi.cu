@@ -631,7 +631,7 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
       L.ldt = g.ldt;
       L.wN = g.wN;
       L.wt = g.wt;
-      L.pipe = 0;
+      L.pipe = P->pipe_f[axis];  // the pipelined warp kernel (passes with FP32 input)
     }
   }
   return L;

@@ -857,8 +857,28 @@ size_t wpass_smem_bytes(int N, int ldt) {
          (size_t)PP * kMaxNout * sizeof(float);
 }
 
+template <int N, typename Tout, int MODE, int NDOT>
+static cudaError_t launch_wpass_pipe_n(const PassLaunch<float>& P, const float* in, Tout* out, cudaStream_t st) {
+  auto kern = precond_wpass_pipe<N, Tout, MODE, NDOT>;
+  const size_t sm = wpass_smem_bytes(N, P.ldt) + (size_t)warp_pencils<N>() * P.ldt * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
+  const int grid = std::min(tiles, per_sm * sm_count());
+  kern<<<grid, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.ldt, P.ax, P.wt, P.lamA, P.lamB, P.dot0, P.dot1,
+                                   P.partial, tiles, P.done);
+  return cudaGetLastError();
+}
+
 template <int N, typename Tin, typename Tout, int MODE, int NDOT>
 static cudaError_t launch_wpass_n(const PassLaunch<float>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  if constexpr (std::is_same<Tin, float>::value) {
+    if (P.pipe) return launch_wpass_pipe_n<N, Tout, MODE, NDOT>(P, in, out, st);
+  }
   auto kern = precond_wpass<N, Tin, Tout, MODE, NDOT>;
   const size_t sm = wpass_smem_bytes(N, P.ldt);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -206,25 +206,15 @@ __device__ __forceinline__ TileInfo wtile_setup(const Dims& dims, int axis, int 
   return t;
 }
 
-// One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
-template <int N, typename Tin, typename Tout, int MODE, int NDOT>
-__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
-                                           int axis, int ldt, const AxisTab<float>& ax, const float2* __restrict__ wt,
-                                           const float* __restrict__ lamA, const float* __restrict__ lamB,
-                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
-                                           double* __restrict__ partial, long long tile_id, int ptile, int pstride,
-                                           unsigned char* smem) {
+// The three steps of one tile: coalesced load into `tile` (row length ldt),
+// warp-local transform, coalesced store. Each is called by the whole CTA.
+template <int N, typename Tin>
+__device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, float* tile, int axis, int ldt,
+                                           const AxisTab<float>& ax, const long long* pbase, const TileInfo& g) {
   constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
   const int m = ax.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float* tile = reinterpret_cast<float*>(smem);
-  float2* wbuf = reinterpret_cast<float2*>(tile + (size_t)PP * ldt);
-  float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
-  __shared__ long long pbase[PP];
-  __shared__ int pia[PP], pib[PP];
-  const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
-  __syncthreads();
-
+  (void)LS; (void)G; (void)tid; (void)warp; (void)lane;
   // ---- coalesced tile load (padding pencils are zero)
   if (axis == 0) {
     for (int pc = warp; pc < PP; pc += kThreads / 32) {
@@ -260,8 +250,17 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
     }
     for (; i < m; i += RS, p += step) tile[pc * ldt + i] = valid ? (float)p[0] : 0.f;
   }
-  __syncthreads();
+}
 
+template <int N, int MODE>
+__device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* outv, const Dims& dims, int ldt,
+                                           const AxisTab<float>& ax, const float2* __restrict__ wt,
+                                           const float* __restrict__ lamA, const float* __restrict__ lamB,
+                                           const int* pia, const int* pib) {
+  constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
+  const int m = ax.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  (void)LS; (void)G; (void)tid; (void)warp; (void)lane;
   // ---- warp-local transform of pencil pair pr (pencils 2 pr, 2 pr + 1)
   const int grp = lane / LS, ls = lane % LS;
   const int pr = warp * G + grp;
@@ -273,18 +272,16 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
   const int nw = ax.n_out;
 
   if (MODE == PM_FWD || MODE == PM_FUSED) {
-    // y_out = W^T r over the support rows of W, all columns per row read
-    {
-      float sa[kMaxNout], sb[kMaxNout];
-#pragma unroll
-      for (int k = 0; k < kMaxNout; ++k) sa[k] = sb[k] = 0.f;
+    // y_out = W^T r over the support rows of W, four columns per row read
+    for (int k0 = 0; k0 < nw; k0 += 4) {
+      float sa[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f};
       auto rows = [&](int i0, int i1) {
         for (int i = i0 + ls; i < i1; i += LS) {
           const float xa = ra[i], xb = rb[i];
-          const float* w = ax.W + i * nw;
+          const float* w = ax.W + i * nw + k0;
 #pragma unroll
-          for (int k = 0; k < kMaxNout; ++k)
-            if (k < nw) {
+          for (int k = 0; k < 4; ++k)
+            if (k0 + k < nw) {
               const float wk = __ldg(w + k);
               sa[k] = fmaf(wk, xa, sa[k]);
               sb[k] = fmaf(wk, xb, sb[k]);
@@ -294,12 +291,12 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
       rows(0, ax.wlo);
       rows(ax.whi, m);
 #pragma unroll
-      for (int k = 0; k < kMaxNout; ++k)
-        if (k < nw) {
+      for (int k = 0; k < 4; ++k)
+        if (k0 + k < nw) {
           const float ya = group_sum<LS>(sa[k]), yb = group_sum<LS>(sb[k]);
           if (ls == 0) {
-            ova[k] = ya;
-            ovb[k] = yb;
+            ova[k0 + k] = ya;
+            ovb[k0 + k] = yb;
           }
         }
     }
@@ -442,8 +439,17 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
       rb[i] = xb;
     }
   }
-  __syncthreads();
+}
 
+template <int N, typename Tout, int NDOT>
+__device__ __forceinline__ void wstore_tile(const float* tile, Tout* __restrict__ out, int axis, int ldt,
+                                            const AxisTab<float>& ax, const long long* pbase, const TileInfo& g,
+                                            const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                            double* __restrict__ partial, int ptile, int pstride) {
+  constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
+  const int m = ax.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  (void)LS; (void)G; (void)tid; (void)warp; (void)lane;
   // ---- coalesced store (and the partial dot products of a PCG step)
   double d0 = 0.0, d1 = 0.0;
   if (axis == 0) {
@@ -494,6 +500,29 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
   }
 }
 
+// One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
+                                           int axis, int ldt, const AxisTab<float>& ax, const float2* __restrict__ wt,
+                                           const float* __restrict__ lamA, const float* __restrict__ lamB,
+                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                           double* __restrict__ partial, long long tile_id, int ptile, int pstride,
+                                           unsigned char* smem) {
+  constexpr int PP = warp_pencils<N>();
+  float* tile = reinterpret_cast<float*>(smem);
+  float2* wbuf = reinterpret_cast<float2*>(tile + (size_t)PP * ldt);
+  float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
+  __shared__ long long pbase[PP];
+  __shared__ int pia[PP], pib[PP];
+  const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
+  __syncthreads();
+  wload_tile<N, Tin>(in, tile, axis, ldt, ax, pbase, g);
+  __syncthreads();
+  wtransform<N, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+  __syncthreads();
+  wstore_tile<N, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
+}
+
 template <int N, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
 precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<float> ax, const float2* wt,
@@ -503,6 +532,84 @@ precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<fl
   extern __shared__ __align__(16) unsigned char smem[];
   wpass_body<N, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
                                        blockIdx.x, blockIdx.x, gridDim.x, smem);
+}
+
+// Asynchronous tile load (FP32 input): one 4-byte cp.async per element,
+// padding pencils written as zeros; the caller commits the copy group.
+template <int N>
+__device__ __forceinline__ void wload_tile_async(const float* __restrict__ in, float* tile, int axis, int ldt,
+                                                 const AxisTab<float>& ax, const long long* pbase,
+                                                 const TileInfo& g) {
+  constexpr int PP = warp_pencils<N>();
+  const int m = ax.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (axis == 0) {
+    for (int pc = warp; pc < PP; pc += kThreads / 32) {
+      float* row = tile + pc * ldt;
+      if (pc < g.nvalid) {
+        const float* src = in + pbase[pc];
+        for (int i = lane; i < m; i += 32) __pipeline_memcpy_async(row + i, src + i, sizeof(float));
+      } else {
+        for (int i = lane; i < m; i += 32) row[i] = 0.f;
+      }
+    }
+  } else {
+    constexpr int RS = kThreads / PP;
+    const int pc = tid & (PP - 1);
+    const bool valid = pc < g.nvalid;
+    const float* src = in + pbase[pc];
+    for (int i = tid / PP; i < m; i += RS) {
+      float* dst = tile + pc * ldt + i;
+      if (valid) __pipeline_memcpy_async(dst, src + i * g.S, sizeof(float));
+      else *dst = 0.f;
+    }
+  }
+}
+
+// Persistent warp-FFT pass (FP32 input) with a two-stage pipeline: each CTA
+// walks the tiles t = blockIdx.x, + gridDim.x, ...; while it transforms and
+// stores tile t, the copies of its next tile are in flight into the second
+// tile buffer. Same arithmetic and partial sums as precond_wpass.
+template <int N, typename Tout, int MODE, int NDOT>
+__global__ void __launch_bounds__(kThreads)
+precond_wpass_pipe(const float* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<float> ax, const float2* wt,
+                   const float* __restrict__ lamA, const float* __restrict__ lamB, const double* __restrict__ dotv0,
+                   const double* __restrict__ dotv1, double* __restrict__ partial, int ntiles,
+                   const int* __restrict__ done) {
+  if (done != nullptr && *((volatile const int*)done)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int PP = warp_pencils<N>();
+  float* tiles = reinterpret_cast<float*>(smem);  // two tile buffers
+  float2* wbuf = reinterpret_cast<float2*>(tiles + (size_t)2 * PP * ldt);
+  float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());
+  __shared__ long long pbase[2][PP];
+  __shared__ int pia[2][PP], pib[2][PP];
+  int t = blockIdx.x;
+  if (t >= ntiles) return;  // the same for every thread of the CTA
+  TileInfo g = wtile_setup(dims, axis, PP, t, pbase[0], pia[0], pib[0]);
+  __syncthreads();
+  wload_tile_async<N>(in, tiles, axis, ldt, ax, pbase[0], g);
+  __pipeline_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    const int nx = cur ^ 1;
+    TileInfo gn = g;
+    if (tn < ntiles) gn = wtile_setup(dims, axis, PP, tn, pbase[nx], pia[nx], pib[nx]);
+    __syncthreads();  // pbase[nx] written
+    if (tn < ntiles) wload_tile_async<N>(in, tiles + (size_t)nx * PP * ldt, axis, ldt, ax, pbase[nx], gn);
+    __pipeline_commit();
+    __pipeline_wait_prior(1);  // this thread's copies of tile t have landed
+    __syncthreads();           // and every thread's
+    float* tile = tiles + (size_t)cur * PP * ldt;
+    wtransform<N, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia[cur], pib[cur]);
+    __syncthreads();
+    wstore_tile<N, Tout, NDOT>(tile, out, axis, ldt, ax, pbase[cur], g, dotv0, dotv1, partial, t, ntiles);
+    __syncthreads();  // tile buffer and pbase of `cur` are free for tile t + 2 gridDim.x
+    g = gn;
+    cur = nx;
+  }
+  __pipeline_wait_prior(0);
 }
 
 }  // namespace iffd

@@ -99,3 +99,25 @@ def test_warp_geometry_switches():
         IFFDPlan(2, 64, 4).set_geometry(0, warp=True)  # FP64 plan
     with pytest.raises(IFFDError):
         IFFDPlan(2, 64, 3, precision="fp32").set_geometry(0, warp=True)  # odd p: DST-I
+
+
+@pytest.mark.parametrize("d,ns,p", [(3, (256, 64, 128), 4), (2, (512, 128), 6), (3, (64, 64, 40), 2)])
+def test_pipelined_warp_pass_equals_plain(d, ns, p):
+    """The persistent warp-FFT kernel that loads its next tile asynchronously
+    does the same arithmetic as the plain one: bitwise equal results."""
+    torch = require_gpu()
+    from paper_2512_20269_gb300 import IFFDPlan
+    plain = IFFDPlan(d, list(ns), p, precision="fp32")
+    pipe = IFFDPlan(d, list(ns), p, precision="fp32")
+    for a in range(d):
+        if ns[a] in (64, 128, 256, 512):
+            plain.set_geometry(a, warp=True, pipelined=False)
+            pipe.set_geometry(a, warp=True, pipelined=True)
+            t = pipe.tiles(a)
+            assert t["warp"] and t["pipelined"]
+    r = _gpu(torch, inputs.rhs(plain.shape, "normal", seed=61 + p))
+    assert torch.equal(plain.apply_preconditioner(r), pipe.apply_preconditioner(r))
+    u0, i0 = plain.pcg_solve(r)
+    u1, i1 = pipe.pcg_solve(r)
+    assert i0["iters"] == i1["iters"] and torch.equal(u0, u1)
+    assert i1["true_rel_res"] <= 1.1e-8
