@@ -557,7 +557,8 @@ def main():
                 "variants": variants, "precond_apply": apply_stats, "kernels": rooflines,
                 "hbm_frac_of_solve": None}
         # fraction of HBM peak of the whole solve at the method's algorithmic traffic
-        # (176 B/DoF per PCG iteration, see the design notes)
+        # (176 B/DoF per PCG iteration: 96 preconditioner + 32 stiffness with the
+        # direction update + 48 for the x, r update; 96 for the initial apply)
         line["hbm_frac_of_solve"] = (176.0 * w.N * iters + 96.0 * w.N) / (ms / args.steps / 1e3) / 1e9 / hbm_peak
         print(json.dumps(line), flush=True)
     if dist is not None:

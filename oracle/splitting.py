@@ -9,7 +9,7 @@ matrix of Table 1, D~_reg its normalisation, Q_out / Lambda_out the remainder
 eigenpairs, and Q~ = [V_reg U D~^{-1}, V_out Q_out], Lambda~ = blkdiag(Lambda_reg,
 Lambda_out).
 
-Readings of the paper taken here (each one is listed in the design doc):
+Readings of the paper taken here:
 
 * Neumann ends carry the odd-derivative conditions of all orders <= p-1
   (eq. "reg_space"; the printed range k = 0..floor(p/2) overshoots p-1).

@@ -1,7 +1,7 @@
 """GPU parity: every CUDA path through the C ABI against the CPU oracle on the
 same seeded inputs.
 
-Tolerances (stated in the design doc):
+Tolerances:
 * FP64 preconditioner apply and exact FD: max |z - z_oracle| <= 1e-12 max |z_oracle|;
 * FP32-transform preconditioner: 1e-5 (relative 2-norm);
 * stiffness: 1e-13 max-norm relative;
