@@ -74,12 +74,17 @@ template <int N, int r, int Ns>
 __device__ __forceinline__ void wstage(float2* buf, int ls, const float2* __restrict__ wt) {
   constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, nb = N / r, BPL = R / r;
   static_assert(N % r == 0 && R % r == 0 && nb == LS * BPL, "stage does not tile the warp");
+  // with nb and Ns multiples of 8 (Ns = 1 only with r = 8), the padded index
+  // is linear in q and t: wpad(j + q nb) = wpad(j) + q (nb + nb / 8), and
+  // wpad(base + t Ns) = wpad(base) + t (Ns + Ns / 8) (+ t when Ns = 1)
+  static_assert(nb % 8 == 0 && (Ns % 8 == 0 || (Ns == 1 && r == 8)), "padded index not linear");
+  constexpr int qstep = nb + nb / 8, tstep = (Ns == 1) ? 1 : Ns + Ns / 8;
   Cplx<float> v[BPL][r];
 #pragma unroll
   for (int u = 0; u < BPL; ++u) {
-    const int j = ls + LS * u;
+    const float2* bj = buf + wpad(ls + LS * u);
 #pragma unroll
-    for (int q = 0; q < r; ++q) v[u][q] = wld(buf, wpad(j + q * nb));
+    for (int q = 0; q < r; ++q) v[u][q] = wld(bj, q * qstep);
   }
   __syncwarp();
 #pragma unroll
@@ -94,9 +99,9 @@ __device__ __forceinline__ void wstage(float2* buf, int ls, const float2* __rest
       }
     }
     wdft<r>(v[u]);
-    const int base = (j - k) * r + k;
+    float2* bb = buf + wpad((j - k) * r + k);
 #pragma unroll
-    for (int t = 0; t < r; ++t) wst(buf, wpad(base + t * Ns), v[u][t]);
+    for (int t = 0; t < r; ++t) wst(bb, t * tstep, v[u][t]);
   }
   __syncwarp();
 }
@@ -127,8 +132,9 @@ __device__ __forceinline__ void wstage_first(float2* buf, int ls, Src src) {
   for (int u = 0; u < BPL; ++u) {
     const int j = ls + LS * u;
     dft8(v[u]);
+    float2* bb = buf + wpad(j * r);  // wpad(8 j + t) = wpad(8 j) + t
 #pragma unroll
-    for (int t = 0; t < r; ++t) wst(buf, wpad(j * r + t), v[u][t]);
+    for (int t = 0; t < r; ++t) wst(bb, t, v[u][t]);
   }
   __syncwarp();
 }
