@@ -57,18 +57,19 @@ __device__ __forceinline__ void dft8(Cplx<T>* v) {
   Cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
   dft4(e);
   dft4(o);
-  // o_t *= exp(-2 pi i t / 8)
-  const Cplx<T> o1 = {(o[1].x + o[1].y) * r, (o[1].y - o[1].x) * r};
+  // o_t *= exp(-2 pi i t / 8): o_1 = r (s1x, s1y), o_3 = r (s3x, -s3y) with
+  // r = 1/sqrt(2), the factor r folded into the output FMAs
+  const T s1x = o[1].x + o[1].y, s1y = o[1].y - o[1].x;
+  const T s3x = o[3].y - o[3].x, s3y = o[3].x + o[3].y;
   const Cplx<T> o2 = mul_mi(o[2]);
-  const Cplx<T> o3 = {(o[3].y - o[3].x) * r, -(o[3].x + o[3].y) * r};
   v[0] = cadd(e[0], o[0]);
   v[4] = csub(e[0], o[0]);
-  v[1] = cadd(e[1], o1);
-  v[5] = csub(e[1], o1);
+  v[1] = {fma(r, s1x, e[1].x), fma(r, s1y, e[1].y)};
+  v[5] = {fma(-r, s1x, e[1].x), fma(-r, s1y, e[1].y)};
   v[2] = cadd(e[2], o2);
   v[6] = csub(e[2], o2);
-  v[3] = cadd(e[3], o3);
-  v[7] = csub(e[3], o3);
+  v[3] = {fma(r, s3x, e[3].x), fma(-r, s3y, e[3].y)};
+  v[7] = {fma(-r, s3x, e[3].x), fma(r, s3y, e[3].y)};
 }
 
 template <typename T>
