@@ -223,10 +223,7 @@ class IFFDPlan:
                      warp: bool = False):
         """Set one direction's launch geometry by hand (iffd_set_geometry).
         `warp`: run the FP32 warp-FFT transform pass (its tile is fixed)."""
-        if warp:
-            pl = 3 if pipelined else 2
-        else:
-            pl = -1 if pipelined is None else int(bool(pipelined))
+        pl = 2 if warp else (-1 if pipelined is None else int(bool(pipelined)))
         check(self._lib.iffd_set_geometry(self._h, axis, int(pencils_transform), int(pencils_stiffness), pl),
               "iffd_set_geometry")
         return self
@@ -238,7 +235,7 @@ class IFFDPlan:
         check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns),
                                        ctypes.byref(pl)), "iffd_get_tiles")
         return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value]),
-                "pipelined": pl.value in (1, 3), "warp": pl.value in (2, 3)}
+                "pipelined": pl.value == 1, "warp": pl.value == 2}
 
     def profile_enable(self, on: bool = True):
         check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")

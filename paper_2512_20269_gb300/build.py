@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libiffd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host_setup.cpp", "precond.cu", "stiffness.cu", "pcg.cu", "fd.cu", "capi.cu", "noalloc.cu", "varcoef.cu", "engine.cu",
+SOURCES = ["host_setup.cpp", "precond.cu", "precond_warp64.cu", "precond_warp128.cu", "precond_warp256.cu",
+           "precond_warp512.cu", "stiffness.cu", "pcg.cu", "fd.cu", "capi.cu", "noalloc.cu", "varcoef.cu", "engine.cu",
            "tune.cu"]
 
 
@@ -47,7 +48,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     extra = list(extra or [])
     if verbose:
         extra += ["-Xptxas", "-v"]
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, len(SOURCES))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]

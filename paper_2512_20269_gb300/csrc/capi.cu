@@ -409,10 +409,11 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     pa[a].of.blk = pa[a].od.blk;
     pa[a].of.VB = tb.add_vec(cast_vec<float>(A.VB));
     {
-      // exp(-2 pi i e / N), e < N, for the warp-FFT pass of length N = n_reg
+      // exp(-2 pi i e / N), e < N, for the warp-FFT pass of FFT length N
+      // (n_reg for DST-II/III, 2 (n_reg + 1) for DST-I)
       std::vector<float> wt;
-      const int Nw = A.n_reg;
-      if (A.kind == TK_DST23 && (Nw == 64 || Nw == 128 || Nw == 256 || Nw == 512))
+      const int Nw = (A.kind == TK_DST23) ? A.n_reg : (A.kind == TK_DST1 ? 2 * (A.n_reg + 1) : 0);
+      if (Nw == 64 || Nw == 128 || Nw == 256 || Nw == 512)
         for (int e = 0; e < Nw; ++e) {
           const double ang = -2.0 * 3.14159265358979323846264338327950288 * e / Nw;
           wt.push_back((float)std::cos(ang));
@@ -631,7 +632,7 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
       L.ldt = g.ldt;
       L.wN = g.wN;
       L.wt = g.wt;
-      L.pipe = P->pipe_f[axis];  // the pipelined warp kernel (passes with FP32 input)
+      L.pipe = 0;
     }
   }
   return L;

@@ -193,7 +193,8 @@ struct PassLaunchB {
   std::vector<long long> prefix{0};
   size_t smem = 0;
   int mode = PM_FWD, ndot = 0;
-  int wN = 0;  // > 0: every system runs the FP32 warp-FFT pass of this length
+  int wN = 0;     // > 0: every system runs the FP32 warp-FFT pass of this length
+  int wkind = 0;  // and this transform kind (AxisTab::kind)
   size_t off_desc = 0, off_prefix = 0;
   void add(const PassDesc<Tc, Tin, Tout>& d, int tiles, size_t sm) {
     desc.push_back(d);
@@ -231,21 +232,23 @@ struct PrecondSeq {
   // FP32 passes: first (r -> tf), middle (tf -> tf), last (tf -> z); one
   // launch per kernel: key 0 the block kernel, key N the warp-FFT pass of
   // length N (systems of one pass are independent, so splitting a pass into
-  // launches does not change any result)
+  // launches does not change any result); key 2 N + (kind == 1) for the warp pass
   std::map<int, PassLaunchB<float, double, float>> f_first;
   std::vector<std::map<int, PassLaunchB<float, float, float>>> f_mid;
   std::map<int, PassLaunchB<float, float, double>> f_last;
 };
 
 template <typename L>
-L& pass_slot(std::map<int, L>& m, int wN, int mode, int ndot) {
-  auto it = m.find(wN);
+L& pass_slot(std::map<int, L>& m, int wN, int wkind, int mode, int ndot) {
+  const int key = wN ? 2 * wN + (wkind == 1 ? 1 : 0) : 0;
+  auto it = m.find(key);
   if (it == m.end()) {
     L l;
     l.mode = mode;
     l.ndot = ndot;
     l.wN = wN;
-    it = m.emplace(wN, std::move(l)).first;
+    l.wkind = wkind;
+    it = m.emplace(key, std::move(l)).first;
   }
   return it->second;
 }
@@ -321,7 +324,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.done = done;
       D.in = vr(*s);
       D.out = vtf(*s);
-      pass_slot(seq->f_first, D.wN, PM_FWD, 0).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
+      pass_slot(seq->f_first, D.wN, D.ax.kind, PM_FWD, 0).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
     }
     const int axes[3] = {1, d - 1, 1};
     for (int k = 0; k < 3; ++k) {
@@ -330,7 +333,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       auto D = pdesc_same<float>(P, a, P.axf, P.PPf, P.ldtf, done);
       D.in = vtf(*s);
       D.out = vtf(*s);
-      pass_slot(seq->f_mid[k], D.wN, mid_modes[k], 0).add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem);
+      pass_slot(seq->f_mid[k], D.wN, D.ax.kind, mid_modes[k], 0).add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem);
     }
     {
       PassDesc<float, float, double> D{};
@@ -343,7 +346,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.dot0 = vr(*s);
       D.dot1 = use_q ? vq(*s) : nullptr;
       D.partial = vpart(*s);
-      pass_slot(seq->f_last, D.wN, PM_BWD, ndot).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
+      pass_slot(seq->f_last, D.wN, D.ax.kind, PM_BWD, ndot).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
     }
   }
 }
@@ -372,7 +375,7 @@ int run_pass(Engine* E, char* base, PassLaunchB<Tc, Tin, Tout>& l, cudaStream_t 
     if (l.wN) {
       IFFD_CUDA((launch_wpass_batched<Tin, Tout>(at<PassDesc<Tc, Tin, Tout>>(base, l.off_desc),
                                                  at<long long>(base, l.off_prefix), (int)l.desc.size(),
-                                                 l.prefix.back(), l.smem, l.wN, l.mode, l.ndot, st)));
+                                                 l.prefix.back(), l.smem, l.wN, l.wkind, l.mode, l.ndot, st)));
       if (l.prefix.back() > 0) ++E->launches;
       return IFFD_OK;
     }

@@ -49,10 +49,22 @@ template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                 long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st);
 
-// Batched warp-FFT passes: every system of the launch has wN == N.
+// Batched warp-FFT passes: every system of the launch has wN == N and
+// transform kind `kind` (AxisTab::kind: 1 DST-II/III, 0 DST-I).
 template <typename Tin, typename Tout>
 cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                 long long total_tiles, size_t smem, int N, int mode, int ndot, cudaStream_t st);
+                                 long long total_tiles, size_t smem, int N, int kind, int mode, int ndot,
+                                 cudaStream_t st);
+
+// Per FFT length N (one translation unit each): the warp-FFT pass of one
+// direction, and its batched form (every system of the launch has wN == N and
+// transform kind `kind`).
+template <int N, typename Tin, typename Tout>
+cudaError_t launch_wpass(const PassLaunch<float>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
+template <int N, typename Tin, typename Tout>
+cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                   long long total_tiles, size_t smem, int kind, int mode, int ndot,
+                                   cudaStream_t st);
 
 size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);       // F: FFT length (AxisTab::F)
 size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt);  // pipelined kernel: one more tile
@@ -60,7 +72,8 @@ size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt);  // pipeline
 cudaError_t launch_rden_fill(double* rden, const Dims& dims, const double* lamF, const double* lam0,
                              const double* lam1, cudaStream_t st);  // F: FFT length (AxisTab::F)
 int precond_tiles(const Dims& dims, int axis, int PP);
-// FP32 warp-FFT passes (DST-II/III directions of length 64, 128, 256 or 512):
+// FP32 warp-FFT passes (D = {0,1} directions whose FFT length is 64, 128, 256
+// or 512: DST-II/III with n_reg of that length, DST-I with 2 (n_reg + 1)):
 // the length the pass runs at for a direction with these tables (0: not
 // eligible), its pencils per tile, and its shared memory for tile row length ldt.
 int wpass_len(const AxisTab<float>& ax);

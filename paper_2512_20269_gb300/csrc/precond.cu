@@ -23,54 +23,10 @@
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "precond_dev.cuh"
+#include "precond_warp_geom.h"
 
 namespace iffd {
-
-template <typename T>
-__device__ __forceinline__ Cplx<T> ldc(const T* p) {
-  return {__ldg(p), __ldg(p + 1)};
-}
-
-// ------------------------------------------------------------- small DFTs
-// Forward DFTs y_t = sum_q v_q exp(-2 pi i q t / R) in registers.
-template <typename T>
-__device__ __forceinline__ void dft2(Cplx<T>* v) {
-  const Cplx<T> a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-
-template <typename T>
-__device__ __forceinline__ void dft4(Cplx<T>* v) {
-  const Cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  const Cplx<T> t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
-  v[0] = cadd(t0, t2);
-  v[2] = csub(t0, t2);
-  v[1] = cadd(t1, mul_mi(t3));
-  v[3] = csub(t1, mul_mi(t3));
-}
-
-template <typename T>
-__device__ __forceinline__ void dft8(Cplx<T>* v) {
-  const T r = T(0.70710678118654752440084436210484903928);
-  Cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
-  Cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
-  dft4(e);
-  dft4(o);
-  // o_t *= exp(-2 pi i t / 8): o_1 = r (s1x, s1y), o_3 = r (s3x, -s3y) with
-  // r = 1/sqrt(2), the factor r folded into the output FMAs
-  const T s1x = o[1].x + o[1].y, s1y = o[1].y - o[1].x;
-  const T s3x = o[3].y - o[3].x, s3y = o[3].x + o[3].y;
-  const Cplx<T> o2 = mul_mi(o[2]);
-  v[0] = cadd(e[0], o[0]);
-  v[4] = csub(e[0], o[0]);
-  v[1] = {fma(r, s1x, e[1].x), fma(r, s1y, e[1].y)};
-  v[5] = {fma(-r, s1x, e[1].x), fma(-r, s1y, e[1].y)};
-  v[2] = cadd(e[2], o2);
-  v[6] = csub(e[2], o2);
-  v[3] = {fma(r, s3x, e[3].x), fma(-r, s3y, e[3].y)};
-  v[7] = {fma(-r, s3x, e[3].x), fma(r, s3y, e[3].y)};
-}
 
 template <typename T>
 __device__ __forceinline__ void dft3(Cplx<T>* v) {
@@ -242,49 +198,6 @@ __device__ __forceinline__ void gen_im(const Cplx<T>* Zp, int k, int L, T fx, T 
   yb = fma(fx, tby, fy * tbx);
 }
 
-// y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1].
-template <typename T>
-__device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
-  if (i < ax.nL) {
-    T s = T(0);
-    for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + i), row[r], s);
-    return s;
-  }
-  if (i >= ax.n_reg - ax.nR) {
-    const int c = ax.n_reg - 1 - i;
-    T s = T(0);
-    for (int r = 0; r < ax.rowsR; ++r) s = fma(__ldg(ax.VR + r * ax.nR + c), row[ax.m - 1 - r], s);
-    return s;
-  }
-  int o = ax.o;
-  for (int b = 0; b < ax.nblk; ++b) {  // interior blocks (repeated knots only)
-    const int* B = ax.blk + 6 * b;
-    const int c0 = __ldg(B), c1 = __ldg(B + 1);
-    if (i < c0) break;
-    if (i < c1) {
-      const int r0 = __ldg(B + 2), r1 = __ldg(B + 3), w = c1 - c0;
-      const T* V = ax.VB + __ldg(B + 5) + (i - c0);
-      T s = T(0);
-      for (int r = r0; r < r1; ++r) s = fma(__ldg(V + (r - r0) * w), row[r], s);
-      return s;
-    }
-    o = __ldg(B + 4);
-  }
-  return row[i + o];
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
-
-}  // namespace iffd
-
-#include "precond_warp.cuh"
-
-namespace iffd {
 
 // A transform pass processes tiles of PP pencils along `axis` (tile_setup):
 // load the tile into shared memory, transform it (compute_tile), store it.
@@ -744,35 +657,6 @@ precond_pass_batched(const PassDesc<Tc, Tin, Tout>* __restrict__ sys, const long
                                           sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
 }
 
-// Batched warp-FFT pass: every system of the launch runs the warp-FFT pass of
-// length N (a separate kernel from the block one, so that neither carries the
-// other's register allocation).
-template <int N, typename Tin, typename Tout, int MODE, int NDOT>
-__global__ void __launch_bounds__(kThreads)
-precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const long long* __restrict__ tile_prefix,
-                      int nsys) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ PassDesc<float, Tin, Tout> sd;
-  __shared__ int s_sys;
-  if (threadIdx.x == 0) {
-    const long long b = blockIdx.x;
-    int lo = 0, hi = nsys - 1;
-    while (lo < hi) {  // last s with tile_prefix[s] <= b
-      const int mid = (lo + hi + 1) >> 1;
-      if (tile_prefix[mid] <= b) lo = mid;
-      else hi = mid - 1;
-    }
-    s_sys = lo;
-    sd = sys[lo];
-  }
-  __syncthreads();
-  if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
-  const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
-  const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
-  wpass_body<N, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA, sd.lamB,
-                                       sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
-}
-
 // rden[x + m0 (y + m1 z)] = 1 / (lam_F[i_F] + lam_0[x] (+ lam_1[y])): the
 // reciprocal of the summed eigenvalues, added in the order of the FUSED pass
 // (last direction F = d-1 first, then direction 0, then direction 1).
@@ -838,8 +722,11 @@ static cudaError_t launch_pipe_t(const PassLaunch<Tc>& P, const Tc* in, Tc* out,
 }
 
 int wpass_len(const AxisTab<float>& ax) {
-  const int N = ax.n_reg;
-  if (ax.kind != 1 || ax.blu || ax.L != N || ax.F != N) return 0;
+  int N = 0;
+  if (ax.kind == 1) N = ax.n_reg;                 // DST-II/III: Makhoul, length n_reg
+  else if (ax.kind == 0) N = 2 * (ax.n_reg + 1);  // DST-I: odd extension
+  else return 0;
+  if (ax.blu || ax.L != N || ax.F != N) return 0;
   return (N == 64 || N == 128 || N == 256 || N == 512) ? N : 0;
 }
 
@@ -858,48 +745,16 @@ size_t wpass_smem_bytes(int N, int ldt) {
          (size_t)PP * kMaxNout * sizeof(float);
 }
 
-template <int N, typename Tout, int MODE, int NDOT>
-static cudaError_t launch_wpass_pipe_n(const PassLaunch<float>& P, const float* in, Tout* out, cudaStream_t st) {
-  auto kern = precond_wpass_pipe<N, Tout, MODE, NDOT>;
-  const size_t sm = wpass_smem_bytes(N, P.ldt) + (size_t)warp_pencils<N>() * P.ldt * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
-  const int grid = std::min(tiles, per_sm * sm_count());
-  kern<<<grid, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.ldt, P.ax, P.wt, P.lamA, P.lamB, P.dot0, P.dot1,
-                                   P.partial, tiles, P.done);
-  return cudaGetLastError();
-}
-
-template <int N, typename Tin, typename Tout, int MODE, int NDOT>
-static cudaError_t launch_wpass_n(const PassLaunch<float>& P, const Tin* in, Tout* out, cudaStream_t st) {
-  if constexpr (std::is_same<Tin, float>::value) {
-    if (P.pipe) return launch_wpass_pipe_n<N, Tout, MODE, NDOT>(P, in, out, st);
-  }
-  auto kern = precond_wpass<N, Tin, Tout, MODE, NDOT>;
-  const size_t sm = wpass_smem_bytes(N, P.ldt);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
-  kern<<<tiles, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.ldt, P.ax, P.wt, P.lamA, P.lamB, P.dot0, P.dot1,
-                                    P.partial, P.done);
-  return cudaGetLastError();
-}
-
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
   if constexpr (std::is_same<Tc, float>::value) {
     if (P.wN != 0) {
       if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
       switch (P.wN) {
-        case 64: return launch_wpass_n<64, Tin, Tout, MODE, NDOT>(P, in, out, st);
-        case 128: return launch_wpass_n<128, Tin, Tout, MODE, NDOT>(P, in, out, st);
-        case 256: return launch_wpass_n<256, Tin, Tout, MODE, NDOT>(P, in, out, st);
-        case 512: return launch_wpass_n<512, Tin, Tout, MODE, NDOT>(P, in, out, st);
+        case 64: return launch_wpass<64, Tin, Tout>(P, MODE, NDOT, in, out, st);
+        case 128: return launch_wpass<128, Tin, Tout>(P, MODE, NDOT, in, out, st);
+        case 256: return launch_wpass<256, Tin, Tout>(P, MODE, NDOT, in, out, st);
+        case 512: return launch_wpass<512, Tin, Tout>(P, MODE, NDOT, in, out, st);
         default: return cudaErrorInvalidValue;
       }
     }
@@ -917,13 +772,36 @@ cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cud
   return cudaGetLastError();
 }
 
+// Only the (arithmetic, input, output) type and mode combinations the
+// preconditioners use are instantiated: FP64 throughout (every mode); FP32
+// transforms with FP64 input (forward passes of the first direction), FP32
+// in and out (forward, fused, backward without dot products), FP64 output
+// (backward passes of the first direction, with 0..2 dot products).
 template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
-  if (mode == PM_FWD) return launch_pass_t<Tc, Tin, Tout, PM_FWD, 0>(P, in, out, st);
-  if (mode == PM_FUSED) return launch_pass_t<Tc, Tin, Tout, PM_FUSED, 0>(P, in, out, st);
-  if (ndot == 0) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 0>(P, in, out, st);
-  if (ndot == 1) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 1>(P, in, out, st);
-  return launch_pass_t<Tc, Tin, Tout, PM_BWD, 2>(P, in, out, st);
+  constexpr bool in64 = std::is_same<Tc, float>::value && std::is_same<Tin, double>::value;
+  constexpr bool out64 = std::is_same<Tc, float>::value && std::is_same<Tout, double>::value;
+  constexpr bool f32 = std::is_same<Tc, float>::value && !in64 && !out64;
+  if constexpr (in64) {
+    if (mode != PM_FWD) return cudaErrorInvalidValue;
+    return launch_pass_t<Tc, Tin, Tout, PM_FWD, 0>(P, in, out, st);
+  } else if constexpr (out64) {
+    if (mode != PM_BWD) return cudaErrorInvalidValue;
+    if (ndot == 0) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 0>(P, in, out, st);
+    if (ndot == 1) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 1>(P, in, out, st);
+    return launch_pass_t<Tc, Tin, Tout, PM_BWD, 2>(P, in, out, st);
+  } else if constexpr (f32) {
+    if (ndot != 0) return cudaErrorInvalidValue;
+    if (mode == PM_FWD) return launch_pass_t<Tc, Tin, Tout, PM_FWD, 0>(P, in, out, st);
+    if (mode == PM_FUSED) return launch_pass_t<Tc, Tin, Tout, PM_FUSED, 0>(P, in, out, st);
+    return launch_pass_t<Tc, Tin, Tout, PM_BWD, 0>(P, in, out, st);
+  } else {
+    if (mode == PM_FWD) return launch_pass_t<Tc, Tin, Tout, PM_FWD, 0>(P, in, out, st);
+    if (mode == PM_FUSED) return launch_pass_t<Tc, Tin, Tout, PM_FUSED, 0>(P, in, out, st);
+    if (ndot == 0) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 0>(P, in, out, st);
+    if (ndot == 1) return launch_pass_t<Tc, Tin, Tout, PM_BWD, 1>(P, in, out, st);
+    return launch_pass_t<Tc, Tin, Tout, PM_BWD, 2>(P, in, out, st);
+  }
 }
 
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
@@ -944,57 +822,51 @@ static cudaError_t launch_batched_t(const PassDesc<Tc, Tin, Tout>* sys, const lo
 template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                 long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st) {
-  if (mode == PM_FWD) return launch_batched_t<Tc, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (mode == PM_FUSED)
-    return launch_batched_t<Tc, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (ndot == 0) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (ndot == 1) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  return launch_batched_t<Tc, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
-}
-
-template <int N, typename Tin, typename Tout, int MODE, int NDOT>
-static cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                     long long total_tiles, size_t smem, cudaStream_t st) {
-  auto kern = precond_wpass_batched<N, Tin, Tout, MODE, NDOT>;
-  static size_t smem_set = 0;  // attribute is raised only when needed (not inside a graph capture)
-  if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
+  constexpr bool in64 = std::is_same<Tc, float>::value && std::is_same<Tin, double>::value;
+  constexpr bool out64 = std::is_same<Tc, float>::value && std::is_same<Tout, double>::value;
+  constexpr bool f32 = std::is_same<Tc, float>::value && !in64 && !out64;
+  if constexpr (in64) {  // the same combinations as launch_pass
+    if (mode != PM_FWD) return cudaErrorInvalidValue;
+    return launch_batched_t<Tc, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  } else if constexpr (out64) {
+    if (mode != PM_BWD) return cudaErrorInvalidValue;
+    if (ndot == 0) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    if (ndot == 1) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    return launch_batched_t<Tc, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  } else if constexpr (f32) {
+    if (ndot != 0) return cudaErrorInvalidValue;
+    if (mode == PM_FWD) return launch_batched_t<Tc, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    if (mode == PM_FUSED)
+      return launch_batched_t<Tc, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    return launch_batched_t<Tc, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  } else {
+    if (mode == PM_FWD) return launch_batched_t<Tc, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    if (mode == PM_FUSED)
+      return launch_batched_t<Tc, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    if (ndot == 0) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    if (ndot == 1) return launch_batched_t<Tc, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
+    return launch_batched_t<Tc, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
   }
-  if (total_tiles <= 0) return cudaSuccess;
-  kern<<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
-  return cudaGetLastError();
-}
-
-template <int N, typename Tin, typename Tout>
-static cudaError_t launch_wbatched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                     long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st) {
-  if (mode == PM_FWD) return launch_wbatched_t<N, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (mode == PM_FUSED)
-    return launch_wbatched_t<N, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (ndot == 0) return launch_wbatched_t<N, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (ndot == 1) return launch_wbatched_t<N, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  return launch_wbatched_t<N, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
 }
 
 template <typename Tin, typename Tout>
 cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                 long long total_tiles, size_t smem, int N, int mode, int ndot, cudaStream_t st) {
+                                 long long total_tiles, size_t smem, int N, int kind, int mode, int ndot,
+                                 cudaStream_t st) {
   switch (N) {
-    case 64: return launch_wbatched_n<64, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
-    case 128: return launch_wbatched_n<128, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
-    case 256: return launch_wbatched_n<256, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
-    case 512: return launch_wbatched_n<512, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, mode, ndot, st);
+    case 64: return launch_wpass_batched_n<64, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
+    case 128: return launch_wpass_batched_n<128, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
+    case 256: return launch_wpass_batched_n<256, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
+    case 512: return launch_wpass_batched_n<512, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_wpass_batched<double, float>(const PassDesc<float, double, float>*, const long long*, int,
-                                                         long long, size_t, int, int, int, cudaStream_t);
+                                                         long long, size_t, int, int, int, int, cudaStream_t);
 template cudaError_t launch_wpass_batched<float, float>(const PassDesc<float, float, float>*, const long long*, int,
-                                                        long long, size_t, int, int, int, cudaStream_t);
+                                                        long long, size_t, int, int, int, int, cudaStream_t);
 template cudaError_t launch_wpass_batched<float, double>(const PassDesc<float, float, double>*, const long long*, int,
-                                                         long long, size_t, int, int, int, cudaStream_t);
+                                                         long long, size_t, int, int, int, int, cudaStream_t);
 
 #define IFFD_INST_BATCHED(Tc, Tin, Tout)                                                                      \
   template cudaError_t launch_pass_batched<Tc, Tin, Tout>(const PassDesc<Tc, Tin, Tout>*, const long long*, int, \

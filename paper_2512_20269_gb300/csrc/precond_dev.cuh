@@ -1,0 +1,94 @@
+// Device helpers shared by the block-wide transform passes (precond.cu) and
+// the warp-FFT passes (precond_warp.cuh): small register DFTs, the V_reg^T
+// gather of one pencil, a warp sum.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace iffd {
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> ldc(const T* p) {
+  return {__ldg(p), __ldg(p + 1)};
+}
+
+// ------------------------------------------------------------- small DFTs
+// Forward DFTs y_t = sum_q v_q exp(-2 pi i q t / R) in registers.
+template <typename T>
+__device__ __forceinline__ void dft2(Cplx<T>* v) {
+  const Cplx<T> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft4(Cplx<T>* v) {
+  const Cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  const Cplx<T> t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, mul_mi(t3));
+  v[3] = csub(t1, mul_mi(t3));
+}
+
+template <typename T>
+__device__ __forceinline__ void dft8(Cplx<T>* v) {
+  const T r = T(0.70710678118654752440084436210484903928);
+  Cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+  Cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+  dft4(e);
+  dft4(o);
+  // o_t *= exp(-2 pi i t / 8): o_1 = r (s1x, s1y), o_3 = r (s3x, -s3y) with
+  // r = 1/sqrt(2), the factor r folded into the output FMAs
+  const T s1x = o[1].x + o[1].y, s1y = o[1].y - o[1].x;
+  const T s3x = o[3].y - o[3].x, s3y = o[3].x + o[3].y;
+  const Cplx<T> o2 = mul_mi(o[2]);
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = {fma(r, s1x, e[1].x), fma(r, s1y, e[1].y)};
+  v[5] = {fma(-r, s1x, e[1].x), fma(-r, s1y, e[1].y)};
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = {fma(r, s3x, e[3].x), fma(-r, s3y, e[3].y)};
+  v[7] = {fma(-r, s3x, e[3].x), fma(r, s3y, e[3].y)};
+}
+
+// y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1].
+template <typename T>
+__device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
+  if (i < ax.nL) {
+    T s = T(0);
+    for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + i), row[r], s);
+    return s;
+  }
+  if (i >= ax.n_reg - ax.nR) {
+    const int c = ax.n_reg - 1 - i;
+    T s = T(0);
+    for (int r = 0; r < ax.rowsR; ++r) s = fma(__ldg(ax.VR + r * ax.nR + c), row[ax.m - 1 - r], s);
+    return s;
+  }
+  int o = ax.o;
+  for (int b = 0; b < ax.nblk; ++b) {  // interior blocks (repeated knots only)
+    const int* B = ax.blk + 6 * b;
+    const int c0 = __ldg(B), c1 = __ldg(B + 1);
+    if (i < c0) break;
+    if (i < c1) {
+      const int r0 = __ldg(B + 2), r1 = __ldg(B + 3), w = c1 - c0;
+      const T* V = ax.VB + __ldg(B + 5) + (i - c0);
+      T s = T(0);
+      for (int r = r0; r < r1; ++r) s = fma(__ldg(V + (r - r0) * w), row[r], s);
+      return s;
+    }
+    o = __ldg(B + 4);
+  }
+  return row[i + o];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+}  // namespace iffd

@@ -2,8 +2,9 @@
 // small DFTs, reg_gather and the tile helpers).
 //
 // Same operator as precond_pass (Q~^T, Q~, or both with the eigenvalue scaling,
-// eq. "preconditioner"), for the DST-II / DST-III directions of Table 1 (even
-// p, D = {0,1}) whose length N = n_reg is 64, 128, 256 or 512. The block-wide
+// eq. "preconditioner"), for the D = {0,1} directions of Table 1 whose FFT
+// length N is 64, 128, 256 or 512: DST-II / DST-III (even p, N = n_reg, with
+// Makhoul's reordering) and DST-I (odd p, N = 2 (n_reg + 1), odd extension). The block-wide
 // kernel spends most of its instructions on run-time index arithmetic and on
 // shared-memory round trips between its steps; with FP32 arithmetic that, not
 // the FFT, limits it. Here a pencil pair belongs to LS lanes of one warp from
@@ -15,41 +16,15 @@
 // constants; the only block-wide steps are the coalesced tile load and store.
 #pragma once
 
+#include <algorithm>
+#include <type_traits>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "precond_dev.cuh"
+#include "precond_warp_geom.h"
+
 namespace iffd {
-
-// Complex values per lane (R) and lanes per sequence (LS) for length N; a warp
-// holds 32 / LS sequences, a CTA of 8 warps 8 * 32 / LS pencil pairs.
-template <int N>
-struct WarpFft;
-template <>
-struct WarpFft<64> {
-  static constexpr int R = 8, LS = 8;
-};
-template <>
-struct WarpFft<128> {
-  static constexpr int R = 8, LS = 16;
-};
-template <>
-struct WarpFft<256> {
-  static constexpr int R = 8, LS = 32;
-};
-template <>
-struct WarpFft<512> {
-  static constexpr int R = 16, LS = 32;
-};
-
-template <int N>
-__host__ __device__ constexpr int warp_pencils() {
-  return 2 * (kThreads / 32) * (32 / WarpFft<N>::LS);
-}
-
-// Sequence buffers skip one complex slot after every 8, so that the strided
-// stores of the early stages spread over the banks.
-__host__ __device__ constexpr int wpad(int i) { return i + (i >> 3); }
-template <int N>
-__host__ __device__ constexpr int wbuf_len() {
-  return N + N / 8;
-}
 
 // Complex values in the sequence buffers are float2 (8-byte aligned, one
 // 64-bit shared-memory access each).
@@ -258,7 +233,9 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, float* ti
   }
 }
 
-template <int N, int MODE>
+// KIND 1: DST-II / DST-III (even p), FFT length N = n_reg in Makhoul's order;
+// KIND 0: DST-I (odd p), FFT length N = 2 (n_reg + 1) of the odd extension.
+template <int N, int KIND, int MODE>
 __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* outv, const Dims& dims, int ldt,
                                            const AxisTab<float>& ax, const float2* __restrict__ wt,
                                            const float* __restrict__ lamA, const float* __restrict__ lamB,
@@ -276,6 +253,7 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
   float* ovb = ova + kMaxNout;
   float2* buf = wbuf + (size_t)pr * wbuf_len<N>();
   const int nw = ax.n_out;
+  constexpr int NR = (KIND == 1) ? N : N / 2 - 1;  // n_reg
 
   if (MODE == PM_FWD || MODE == PM_FUSED) {
     // y_out = W^T r over the support rows of W, four columns per row read
@@ -326,7 +304,7 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
         ev[r] = 0.f;
         if (t < 2 * ne) {
           const int c = t < ne ? t : t - ne;
-          const int i = c < ax.nL ? c : N - ax.nR + (c - ax.nL);
+          const int i = c < ax.nL ? c : NR - ax.nR + (c - ax.nL);
           ev[r] = reg_gather(t < ne ? ra : rb, i, ax);
           slot[r] = (t < ne ? 0 : ldt) + i + ax.o;
         }
@@ -337,39 +315,69 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
         if (slot[r] >= 0) ra[slot[r]] = ev[r];
       __syncwarp();
     }
-    wstage_first<N>(buf, ls, [&](int j, int q) {
-      const int l = j + q * (N / 8);
-      const bool hi = q >= 4;
-      const int i = hi ? 2 * (N - 1 - l) + 1 : 2 * l;
-      float ya, yb;
-      if (uniform) {
-        ya = ra[i + ax.o];
-        yb = rb[i + ax.o];
-      } else {
-        ya = reg_gather(ra, i, ax);
-        yb = reg_gather(rb, i, ax);
+    if constexpr (KIND == 1) {
+      wstage_first<N>(buf, ls, [&](int j, int q) {
+        const int l = j + q * (N / 8);
+        const bool hi = q >= 4;
+        const int i = hi ? 2 * (N - 1 - l) + 1 : 2 * l;
+        float ya, yb;
+        if (uniform) {
+          ya = ra[i + ax.o];
+          yb = rb[i + ax.o];
+        } else {
+          ya = reg_gather(ra, i, ax);
+          yb = reg_gather(rb, i, ax);
+        }
+        return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
+      });
+      wfft_rest<N>(buf, ls, wt);
+      // separation, twiddle and D~^{-1}: outputs N-1-k and k-1 from Z[k], Z[N-k]
+      for (int k = ls; k <= N / 2; k += LS) {
+        const Cplx<float> zk = wld(buf, wpad(k));
+        const Cplx<float> zm = wld(buf, wpad(k == 0 ? 0 : N - k));
+        const float Ar = zk.x + zm.x, Ai = zk.y - zm.y;
+        const float Br = zk.y + zm.y, Bi = zm.x - zk.x;
+        const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
+        ra[N - 1 - k] = fmaf(t.x, Ar, t.y * Ai);
+        rb[N - 1 - k] = fmaf(t.x, Br, t.y * Bi);
+        if (k > 0 && 2 * k != N) {
+          ra[k - 1] = fmaf(t.z, Ar, -t.w * Ai);
+          rb[k - 1] = fmaf(t.z, Br, -t.w * Bi);
+        }
       }
-      return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
-    });
-    wfft_rest<N>(buf, ls, wt);
-    // separation, twiddle and D~^{-1}: outputs N-1-k and k-1 from Z[k], Z[N-k]
-    for (int k = ls; k <= N / 2; k += LS) {
-      const Cplx<float> zk = wld(buf, wpad(k));
-      const Cplx<float> zm = wld(buf, wpad(k == 0 ? 0 : N - k));
-      const float Ar = zk.x + zm.x, Ai = zk.y - zm.y;
-      const float Br = zk.y + zm.y, Bi = zm.x - zk.x;
-      const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
-      ra[N - 1 - k] = fmaf(t.x, Ar, t.y * Ai);
-      rb[N - 1 - k] = fmaf(t.x, Br, t.y * Bi);
-      if (k > 0 && 2 * k != N) {
-        ra[k - 1] = fmaf(t.z, Ar, -t.w * Ai);
-        rb[k - 1] = fmaf(t.z, Br, -t.w * Bi);
+    } else {
+      // odd extension of length N = 2n: 0, y_0 .. y_{n-2}, 0, -y_{n-2} .. -y_0;
+      // element l = j + q N/8 is in the second half exactly when q >= 4, and
+      // the zeros are l = 0 and l = n (j = 0 with q = 0 or 4)
+      wstage_first<N>(buf, ls, [&](int j, int q) {
+        const int l = j + q * (N / 8);
+        const bool hi = q >= 4;
+        const int i = hi ? N - 1 - l : l - 1;
+        float ya = 0.f, yb = 0.f;
+        if (!((q == 0 || q == 4) && j == 0)) {
+          if (uniform) {
+            ya = ra[i + ax.o];
+            yb = rb[i + ax.o];
+          } else {
+            ya = reg_gather(ra, i, ax);
+            yb = reg_gather(rb, i, ax);
+          }
+        }
+        return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
+      });
+      wfft_rest<N>(buf, ls, wt);
+      // DST-I output j is -Im Z[j+1] (pencil a) and Re Z[j+1] (pencil b), times 1/(2 D~_j)
+      for (int j = ls; j < NR; j += LS) {
+        const Cplx<float> z = wld(buf, wpad(j + 1));
+        const float sc = __ldg(ax.post + j);
+        ra[j] = -sc * z.y;
+        rb[j] = sc * z.x;
       }
     }
     __syncwarp();
     for (int k = ls; k < nw; k += LS) {
-      ra[N + k] = ova[k];
-      rb[N + k] = ovb[k];
+      ra[NR + k] = ova[k];
+      rb[NR + k] = ovb[k];
     }
     __syncwarp();
   }
@@ -395,36 +403,59 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
 
   if (MODE == PM_BWD || MODE == PM_FUSED) {
     for (int k = ls; k < nw; k += LS) {
-      ova[k] = ra[N + k];
-      ovb[k] = rb[N + k];
+      ova[k] = ra[NR + k];
+      ovb[k] = rb[NR + k];
     }
-    // inverse of the separation: G[k], G[N-k] from rows N-1-k and k-1
-    for (int k = ls; k <= N / 2; k += LS) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
-      if (k == 0 || 2 * k == N) {
-        const float s = t.x + t.x;
-        buf[wpad(k)] = make_float2(s * ra[N - 1 - k], s * rb[N - 1 - k]);
-      } else {
-        const float ar = fmaf(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
-        const float ai = fmaf(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
-        const float br = fmaf(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
-        const float bi = fmaf(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
-        buf[wpad(k)] = make_float2(ar - bi, ai + br);
-        buf[wpad(N - k)] = make_float2(ar + bi, br - ai);
+    if constexpr (KIND == 1) {
+      // inverse of the separation: G[k], G[N-k] from rows N-1-k and k-1
+      for (int k = ls; k <= N / 2; k += LS) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
+        if (k == 0 || 2 * k == N) {
+          const float s = t.x + t.x;
+          buf[wpad(k)] = make_float2(s * ra[N - 1 - k], s * rb[N - 1 - k]);
+        } else {
+          const float ar = fmaf(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
+          const float ai = fmaf(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
+          const float br = fmaf(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
+          const float bi = fmaf(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+          buf[wpad(k)] = make_float2(ar - bi, ai + br);
+          buf[wpad(N - k)] = make_float2(ar + bi, br - ai);
+        }
+      }
+    } else {
+      // odd extension of the scaled input w_j / (2 D~_j)
+      for (int l = ls; l < N; l += LS) {
+        float va = 0.f, vb = 0.f;
+        if (l != 0 && l != N / 2) {
+          const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
+          const float sc = (l < N / 2) ? __ldg(ax.post + jj) : -__ldg(ax.post + jj);
+          va = sc * ra[jj];
+          vb = sc * rb[jj];
+        }
+        buf[wpad(l)] = make_float2(va, vb);
       }
     }
     __syncwarp();
     wstage<N, 8, 1>(buf, ls, wt);
     wfft_rest<N>(buf, ls, wt);
-    // x = V_reg w + W z_out, row by row (DST-III output j is +-Re/Im Z[l(j)])
+    // x = V_reg w + W z_out, row by row (DST-III output j is +-Re/Im Z[l(j)];
+    // DST-I output j is -Im Z[j+1] / Re Z[j+1])
     for (int i = ls; i < m; i += LS) {
       auto wa = [&](int j) {
-        const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
-        return neg_if(buf[wpad(l)].x, j & 1);
+        if constexpr (KIND == 1) {
+          const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+          return neg_if(buf[wpad(l)].x, j & 1);
+        } else {
+          return -buf[wpad(j + 1)].y;
+        }
       };
       auto wb = [&](int j) {
-        const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
-        return neg_if(buf[wpad(l)].y, j & 1);
+        if constexpr (KIND == 1) {
+          const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+          return neg_if(buf[wpad(l)].y, j & 1);
+        } else {
+          return buf[wpad(j + 1)].x;
+        }
       };
       float xa, xb;
       if (ax.nblk == 0 && i >= ax.rowsL && i < m - ax.rowsR) {  // identity rows
@@ -507,7 +538,7 @@ __device__ __forceinline__ void wstore_tile(const float* tile, Tout* __restrict_
 }
 
 // One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
-template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
                                            int axis, int ldt, const AxisTab<float>& ax, const float2* __restrict__ wt,
                                            const float* __restrict__ lamA, const float* __restrict__ lamB,
@@ -524,98 +555,176 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
   __syncthreads();
   wload_tile<N, Tin>(in, tile, axis, ldt, ax, pbase, g);
   __syncthreads();
-  wtransform<N, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+  wtransform<N, KIND, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
   __syncthreads();
   wstore_tile<N, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
 }
 
-template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
 precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<float> ax, const float2* wt,
               const float* __restrict__ lamA, const float* __restrict__ lamB, const double* __restrict__ dotv0,
               const double* __restrict__ dotv1, double* __restrict__ partial, const int* __restrict__ done) {
   if (done != nullptr && *((volatile const int*)done)) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  wpass_body<N, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
-                                       blockIdx.x, blockIdx.x, gridDim.x, smem);
+  wpass_body<N, KIND, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
+                                             blockIdx.x, blockIdx.x, gridDim.x, smem);
 }
 
-// Asynchronous tile load (FP32 input): one 4-byte cp.async per element,
-// padding pencils written as zeros; the caller commits the copy group.
-template <int N>
-__device__ __forceinline__ void wload_tile_async(const float* __restrict__ in, float* tile, int axis, int ldt,
-                                                 const AxisTab<float>& ax, const long long* pbase,
-                                                 const TileInfo& g) {
-  constexpr int PP = warp_pencils<N>();
-  const int m = ax.m;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (axis == 0) {
-    for (int pc = warp; pc < PP; pc += kThreads / 32) {
-      float* row = tile + pc * ldt;
-      if (pc < g.nvalid) {
-        const float* src = in + pbase[pc];
-        for (int i = lane; i < m; i += 32) __pipeline_memcpy_async(row + i, src + i, sizeof(float));
-      } else {
-        for (int i = lane; i < m; i += 32) row[i] = 0.f;
-      }
-    }
-  } else {
-    constexpr int RS = kThreads / PP;
-    const int pc = tid & (PP - 1);
-    const bool valid = pc < g.nvalid;
-    const float* src = in + pbase[pc];
-    for (int i = tid / PP; i < m; i += RS) {
-      float* dst = tile + pc * ldt + i;
-      if (valid) __pipeline_memcpy_async(dst, src + i * g.S, sizeof(float));
-      else *dst = 0.f;
-    }
+// ---------------------------------------------------------------- launchers
+inline int warp_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
   }
+  return n;
 }
 
-// Persistent warp-FFT pass (FP32 input) with a two-stage pipeline: each CTA
-// walks the tiles t = blockIdx.x, + gridDim.x, ...; while it transforms and
-// stores tile t, the copies of its next tile are in flight into the second
-// tile buffer. Same arithmetic and partial sums as precond_wpass.
-template <int N, typename Tout, int MODE, int NDOT>
+// Batched warp-FFT pass: every system of the launch runs the warp-FFT pass of
+// length N (a separate kernel from the block one, so that neither carries the
+// other's register allocation).
+template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
-precond_wpass_pipe(const float* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<float> ax, const float2* wt,
-                   const float* __restrict__ lamA, const float* __restrict__ lamB, const double* __restrict__ dotv0,
-                   const double* __restrict__ dotv1, double* __restrict__ partial, int ntiles,
-                   const int* __restrict__ done) {
-  if (done != nullptr && *((volatile const int*)done)) return;
+precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const long long* __restrict__ tile_prefix,
+                      int nsys) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int PP = warp_pencils<N>();
-  float* tiles = reinterpret_cast<float*>(smem);  // two tile buffers
-  float2* wbuf = reinterpret_cast<float2*>(tiles + (size_t)2 * PP * ldt);
-  float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());
-  __shared__ long long pbase[2][PP];
-  __shared__ int pia[2][PP], pib[2][PP];
-  int t = blockIdx.x;
-  if (t >= ntiles) return;  // the same for every thread of the CTA
-  TileInfo g = wtile_setup(dims, axis, PP, t, pbase[0], pia[0], pib[0]);
-  __syncthreads();
-  wload_tile_async<N>(in, tiles, axis, ldt, ax, pbase[0], g);
-  __pipeline_commit();
-  int cur = 0;
-  for (; t < ntiles; t += gridDim.x) {
-    const int tn = t + gridDim.x;
-    const int nx = cur ^ 1;
-    TileInfo gn = g;
-    if (tn < ntiles) gn = wtile_setup(dims, axis, PP, tn, pbase[nx], pia[nx], pib[nx]);
-    __syncthreads();  // pbase[nx] written
-    if (tn < ntiles) wload_tile_async<N>(in, tiles + (size_t)nx * PP * ldt, axis, ldt, ax, pbase[nx], gn);
-    __pipeline_commit();
-    __pipeline_wait_prior(1);  // this thread's copies of tile t have landed
-    __syncthreads();           // and every thread's
-    float* tile = tiles + (size_t)cur * PP * ldt;
-    wtransform<N, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia[cur], pib[cur]);
-    __syncthreads();
-    wstore_tile<N, Tout, NDOT>(tile, out, axis, ldt, ax, pbase[cur], g, dotv0, dotv1, partial, t, ntiles);
-    __syncthreads();  // tile buffer and pbase of `cur` are free for tile t + 2 gridDim.x
-    g = gn;
-    cur = nx;
+  __shared__ PassDesc<float, Tin, Tout> sd;
+  __shared__ int s_sys;
+  if (threadIdx.x == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {  // last s with tile_prefix[s] <= b
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_sys = lo;
+    sd = sys[lo];
   }
-  __pipeline_wait_prior(0);
+  __syncthreads();
+  if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
+  const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
+  const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
+  wpass_body<N, KIND, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA, sd.lamB,
+                                       sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
 }
+
+template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_wpass_n(const PassLaunch<float>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  auto kern = precond_wpass<N, KIND, Tin, Tout, MODE, NDOT>;
+  const size_t sm = wpass_smem_bytes(N, P.ldt);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
+  kern<<<tiles, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.ldt, P.ax, P.wt, P.lamA, P.lamB, P.dot0, P.dot1,
+                                    P.partial, P.done);
+  return cudaGetLastError();
+}
+
+template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                     long long total_tiles, size_t smem, cudaStream_t st) {
+  auto kern = precond_wpass_batched<N, KIND, Tin, Tout, MODE, NDOT>;
+  static size_t smem_set = 0;  // attribute is raised only when needed (not inside a graph capture)
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  if (total_tiles <= 0) return cudaSuccess;
+  kern<<<(unsigned)total_tiles, kThreads, smem, st>>>(sys, tile_prefix, nsys);
+  return cudaGetLastError();
+}
+
+template <int N, int KIND, typename Tin, typename Tout>
+cudaError_t launch_wbatched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                     long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st) {
+  if (mode == PM_FWD)
+    return launch_wbatched_t<N, KIND, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (mode == PM_FUSED)
+    return launch_wbatched_t<N, KIND, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (ndot == 0)
+    return launch_wbatched_t<N, KIND, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if (ndot == 1)
+    return launch_wbatched_t<N, KIND, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  return launch_wbatched_t<N, KIND, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
+}
+
+
+// Only the (input, output) type and mode combinations the FP32 preconditioner
+// uses exist: FP64 -> FP32 forward passes (first direction), FP32 -> FP32
+// forward, fused and backward passes (ndot 0), FP32 -> FP64 backward passes
+// (last direction, ndot 0..2).
+template <typename Tin, typename Tout>
+constexpr bool wpass_combo_ok(int mode, int ndot) {
+  if (std::is_same<Tin, double>::value) return mode == PM_FWD;
+  if (std::is_same<Tout, double>::value) return mode == PM_BWD;
+  return ndot == 0;
+}
+
+template <int N, typename Tin, typename Tout>
+cudaError_t launch_wpass(const PassLaunch<float>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
+  if (!wpass_combo_ok<Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
+  const bool k1 = P.ax.kind == 1;
+#define IFFD_WL(MODE, NDOT)                                                                            \
+  return k1 ? launch_wpass_n<N, 1, Tin, Tout, MODE, NDOT>(P, in, out, st)                              \
+            : launch_wpass_n<N, 0, Tin, Tout, MODE, NDOT>(P, in, out, st);
+  if constexpr (std::is_same<Tin, double>::value) {
+    IFFD_WL(PM_FWD, 0)
+  } else if constexpr (std::is_same<Tout, double>::value) {
+    if (ndot == 0) { IFFD_WL(PM_BWD, 0) }
+    if (ndot == 1) { IFFD_WL(PM_BWD, 1) }
+    IFFD_WL(PM_BWD, 2)
+  } else {
+    if (mode == PM_FWD) { IFFD_WL(PM_FWD, 0) }
+    if (mode == PM_FUSED) { IFFD_WL(PM_FUSED, 0) }
+    IFFD_WL(PM_BWD, 0)
+  }
+#undef IFFD_WL
+}
+
+template <int N, typename Tin, typename Tout>
+cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                                   long long total_tiles, size_t smem, int kind, int mode, int ndot,
+                                   cudaStream_t st) {
+  if (!wpass_combo_ok<Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
+  const bool k1 = kind == 1;
+#define IFFD_WB(MODE, NDOT)                                                                                   \
+  return k1 ? launch_wbatched_t<N, 1, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st)  \
+            : launch_wbatched_t<N, 0, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  if constexpr (std::is_same<Tin, double>::value) {
+    IFFD_WB(PM_FWD, 0)
+  } else if constexpr (std::is_same<Tout, double>::value) {
+    if (ndot == 0) { IFFD_WB(PM_BWD, 0) }
+    if (ndot == 1) { IFFD_WB(PM_BWD, 1) }
+    IFFD_WB(PM_BWD, 2)
+  } else {
+    if (mode == PM_FWD) { IFFD_WB(PM_FWD, 0) }
+    if (mode == PM_FUSED) { IFFD_WB(PM_FUSED, 0) }
+    IFFD_WB(PM_BWD, 0)
+  }
+#undef IFFD_WB
+}
+
+// Explicit instantiation of one FFT length (one translation unit each, so
+// that they compile in parallel).
+#define IFFD_WARP_INSTANTIATE(NN)                                                                              \
+  template cudaError_t launch_wpass<NN, double, float>(const PassLaunch<float>&, int, int, const double*, float*, \
+                                                       cudaStream_t);                                           \
+  template cudaError_t launch_wpass<NN, float, float>(const PassLaunch<float>&, int, int, const float*, float*,   \
+                                                      cudaStream_t);                                            \
+  template cudaError_t launch_wpass<NN, float, double>(const PassLaunch<float>&, int, int, const float*, double*, \
+                                                       cudaStream_t);                                           \
+  template cudaError_t launch_wpass_batched_n<NN, double, float>(const PassDesc<float, double, float>*,            \
+                                                                 const long long*, int, long long, size_t, int,   \
+                                                                 int, int, cudaStream_t);                         \
+  template cudaError_t launch_wpass_batched_n<NN, float, float>(const PassDesc<float, float, float>*,              \
+                                                                const long long*, int, long long, size_t, int,    \
+                                                                int, int, cudaStream_t);                          \
+  template cudaError_t launch_wpass_batched_n<NN, float, double>(const PassDesc<float, float, double>*,            \
+                                                                 const long long*, int, long long, size_t, int,   \
+                                                                 int, int, cudaStream_t);
 
 }  // namespace iffd

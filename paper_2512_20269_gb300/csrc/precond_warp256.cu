@@ -1,0 +1,6 @@
+// FP32 warp-FFT passes of FFT length 256 (kernels in precond_warp.cuh).
+#include "precond_warp.cuh"
+
+namespace iffd {
+IFFD_WARP_INSTANTIATE(256)
+}  // namespace iffd

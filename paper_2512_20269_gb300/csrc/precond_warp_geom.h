@@ -1,0 +1,43 @@
+// Compile-time geometry of the FP32 warp-FFT passes (precond_warp.cuh), shared
+// with the host code that sizes their launches (precond.cu).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace iffd {
+
+// Complex values per lane (R) and lanes per sequence (LS) for length N; a warp
+// holds 32 / LS sequences, a CTA of 8 warps 8 * 32 / LS pencil pairs.
+template <int N>
+struct WarpFft;
+template <>
+struct WarpFft<64> {
+  static constexpr int R = 8, LS = 8;
+};
+template <>
+struct WarpFft<128> {
+  static constexpr int R = 8, LS = 16;
+};
+template <>
+struct WarpFft<256> {
+  static constexpr int R = 8, LS = 32;
+};
+template <>
+struct WarpFft<512> {
+  static constexpr int R = 16, LS = 32;
+};
+
+template <int N>
+__host__ __device__ constexpr int warp_pencils() {
+  return 2 * (kThreads / 32) * (32 / WarpFft<N>::LS);
+}
+
+// Sequence buffers skip one complex slot after every 8, so that the strided
+// stores of the early stages spread over the banks.
+__host__ __device__ constexpr int wpad(int i) { return i + (i >> 3); }
+template <int N>
+__host__ __device__ constexpr int wbuf_len() {
+  return N + N / 8;
+}
+
+}  // namespace iffd

@@ -150,17 +150,13 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
     }
   };
   if constexpr (!f64) {
-    if (wpass_len(ax) > 0) {  // the warp-FFT pass (fixed tile), plain or pipelined
-      for (int pipe = 0; pipe <= (pipe_ok ? 1 : 0); ++pipe) {
-        apply(vsel[a], PPs[a], pipe, 1);
-        float ms = 0.f;
-        if (int rc = time_pass(&ms)) return rc;
-        if (ms < best) {
-          best = ms;
-          best_warp = 1;
-          best_pipe = pipe;
-        }
-      }
+    if (wpass_len(ax) > 0) {  // the warp-FFT pass (its tile is fixed)
+      apply(vsel[a], PPs[a], 0, 1);
+      float ms = 0.f;
+      if (int rc = time_pass(&ms)) return rc;
+      best = ms;
+      best_warp = 1;
+      best_pipe = 0;
     }
   }
   for (int vi : vars)
@@ -296,16 +292,16 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
   auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
-  if (pipelined == 2 || pipelined == 3) {
+  if (pipelined == 2) {
     if (f64 || wpass_len(P.axf[axis]) == 0)
       return fail(IFFD_ERR_UNSUPPORTED, "the warp-FFT pass needs FP32 transforms and a DST-II/III direction of "
                                         "length 64, 128, 256 or 512");
     if (pencils_transform > 0) return fail(IFFD_ERR_INVALID_ARG, "the warp-FFT pass has a fixed tile");
     P.warp_f[axis] = 1;
-    P.pipe_f[axis] = pipelined == 3 ? 1 : 0;
+    P.pipe_f[axis] = 0;
     pipelined = -1;
-  } else if (pipelined > 3) {
-    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1, 2 or 3 (or < 0)");
+  } else if (pipelined > 2) {
+    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1 or 2 (or < 0)");
   } else if (!f64 && (pencils_transform > 0 || pipelined >= 0)) {
     P.warp_f[axis] = 0;  // a block-kernel geometry set by hand
   }
@@ -349,7 +345,7 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
     *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
   const int nst = f64 ? P.axd[axis].nst : P.axf[axis].nst;
   if (nstages) *nstages = nst;
-  if (pipelined) *pipelined = f64 ? P.pipe_d[axis] : (f32_geom(P, axis).wN ? 2 + P.pipe_f[axis] : P.pipe_f[axis]);
+  if (pipelined) *pipelined = f64 ? P.pipe_d[axis] : (f32_geom(P, axis).wN ? 2 : P.pipe_f[axis]);
   if (radices)
     for (int s = 0; s < nst; ++s) radices[s] = f64 ? P.axd[axis].radix[s] : P.axf[axis].radix[s];
   return IFFD_OK;
