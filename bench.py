@@ -65,7 +65,9 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
     M u and K u from one set of pair sums, 5p + 2 flops, plus 2 for the fused
     direction update p = z + beta p; middle sweep M T1, K T1 (shared pairs) and
     M T2 plus the sum, 8p + 4; last sweep K T1 + M T2, 6p + 3, plus 2 for the
-    fused dot product. PCG update 48 B/DoF."""
+    fused dot product. The backward pass along x also forms the PCG dot product
+    (r, z) of its output (2 flops per DoF), so the backward kind, averaged over
+    its d - 1 directions, adds 2 / (d - 1). PCG update 48 B/DoF."""
     per_pass = 2.5 * math.log2(n) + 2 * n_out
     if kind.startswith("precond"):
         if precision == "fp32":
@@ -75,7 +77,12 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
             edge = (12.0 + 8.0 * (d - 2)) / (d - 1)
             byt = {"precond_fwd": edge, "precond_fused": 8.0, "precond_bwd": edge}[kind]
             return byt * N, "B", "hbm"
-        fl = per_pass * N if kind != "precond_fused" else (2 * per_pass + 3) * N
+        if kind == "precond_fused":
+            fl = (2 * per_pass + 3) * N
+        elif kind == "precond_bwd":
+            fl = (per_pass + 2.0 / (d - 1)) * N
+        else:
+            fl = per_pass * N
         return fl, "flop", "alu"
     if kind.startswith("stiff"):
         per = {"stiff_first": 5 * p + 4, "stiff_mid": 8 * p + 4, "stiff_last": 6 * p + 5}[kind]
