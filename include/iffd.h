@@ -162,15 +162,16 @@ int iffd_autotune(iffd_handle h, void* ws, void* stream);
  * see iffd_autotune): pencils per tile of its transform pass and of its
  * stiffness sweep (2, 4, 8, 16 or 32; <= 0 keeps the current value) and the
  * schedule of its transform passes: `pipelined` 1 = persistent pipelined
- * kernel, 0 = one tile per CTA, 2 = the warp-FFT pass (FP32 transforms only,
- * D = {0,1} directions whose FFT length is 64, 128, 256 or 512: DST-II/III
+ * kernel, 0 = one tile per CTA, 2 = the warp-FFT pass (D = {0,1} directions
+ * whose FFT length is 64, 128, 256 or 512, FP64 plans up to 256: DST-II/III
  * with n_reg of that length, DST-I with 2 (n_reg + 1); each pencil pair is
- * transformed by the lanes of one warp, register
- * butterflies, fixed tile; the default for such directions), < 0 unchanged.
- * Setting a tile size or pipelined 0/1 on an FP32 plan selects the block
+ * transformed by the lanes of one warp, register butterflies, fixed tile;
+ * the default for such directions of FP32 plans, opt-in for FP64 plans),
+ * < 0 unchanged. Setting a tile size or pipelined 0/1 selects the block
  * kernel. The block-kernel geometry does not change any transformed value; it
  * changes the grouping of the partial sums of the dot products (the warp-FFT
- * pass rounds differently, within the FP32 tolerance). Errors: INVALID_ARG,
+ * pass rounds differently, within the FP32 or FP64 tolerance). The batched
+ * engine runs FP64 systems on the block kernel. Errors: INVALID_ARG,
  * UNSUPPORTED (does not fit in 200 KB of shared memory; warp-FFT pass not
  * available for this direction). Do not call while work of the plan is in
  * flight. */
@@ -181,7 +182,7 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
  * sweep, the radix sequence of its FFT (radices[0..*nstages), at most 12),
  * and the schedule of its transform passes (*pipelined = 1: persistent
  * pipelined kernel, each CTA loads its next tile asynchronously while it
- * transforms the current one; 2: FP32 warp-FFT pass; 0: one tile per CTA). */
+ * transforms the current one; 2: warp-FFT pass; 0: one tile per CTA). */
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
                    int* nstages, int* pipelined);
 

@@ -222,7 +222,8 @@ class IFFDPlan:
     def set_geometry(self, axis: int, pencils_transform: int = 0, pencils_stiffness: int = 0, pipelined=None,
                      warp: bool = False):
         """Set one direction's launch geometry by hand (iffd_set_geometry).
-        `warp`: run the FP32 warp-FFT transform pass (its tile is fixed)."""
+        `warp`: run the warp-FFT transform pass (its tile is fixed; the FP32
+        default where eligible, opt-in for FP64 plans up to FFT length 256)."""
         pl = 2 if warp else (-1 if pipelined is None else int(bool(pipelined)))
         check(self._lib.iffd_set_geometry(self._h, axis, int(pencils_transform), int(pencils_stiffness), pl),
               "iffd_set_geometry")

@@ -373,7 +373,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     std::vector<FftPlan> vars;         // radix sequences of length L (and F)
     std::vector<size_t> var_d, var_f;  // their twiddle tables (FP64, FP32)
     int ilo, ihi;
-    size_t wt;                         // FP32 warp-FFT twiddles (DST-II/III directions)
+    size_t wt, wt_d;                   // warp-FFT twiddles, FP32 and FP64 (D = {0,1} directions)
   } pa[3];
   for (int a = 0; a < P->d; ++a) {
     const Axis1D& A = P->host[a];
@@ -411,15 +411,16 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     {
       // exp(-2 pi i e / N), e < N, for the warp-FFT pass of FFT length N
       // (n_reg for DST-II/III, 2 (n_reg + 1) for DST-I)
-      std::vector<float> wt;
+      std::vector<double> wt;
       const int Nw = (A.kind == TK_DST23) ? A.n_reg : (A.kind == TK_DST1 ? 2 * (A.n_reg + 1) : 0);
       if (Nw == 64 || Nw == 128 || Nw == 256 || Nw == 512)
         for (int e = 0; e < Nw; ++e) {
-          const double ang = -2.0 * 3.14159265358979323846264338327950288 * e / Nw;
-          wt.push_back((float)std::cos(ang));
-          wt.push_back((float)std::sin(ang));
+          const double ang = -2.0 * kPi * e / Nw;
+          wt.push_back(std::cos(ang));
+          wt.push_back(std::sin(ang));
         }
-      pa[a].wt = tb.add_vec(wt);
+      pa[a].wt = tb.add_vec(cast_vec<float>(wt));
+      pa[a].wt_d = tb.add_vec(wt);
     }
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
     pa[a].of.VR = tb.add_vec(cast_vec<float>(A.VR));
@@ -518,7 +519,9 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     P->vsel_f[a] = default_var(P->fvar[a], F);
     set_fft(&P->axf[a], P->fvar[a][P->vsel_f[a]]);
     P->wtab[a] = reinterpret_cast<const float2*>(base + pa[a].wt);
+    P->wtab_d[a] = reinterpret_cast<const double2*>(base + pa[a].wt_d);
     P->warp_f[a] = 0;
+    P->warp_d[a] = 0;
     if (const int wN = wpass_len(P->axf[a])) {
       // the warp-FFT pass by default, unless its larger tiles leave the GPU
       // underfilled where the block kernel's would not
@@ -634,8 +637,20 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
       L.wt = g.wt;
       L.pipe = 0;
     }
+  } else {
+    if (const int wN = f64_warp_len(*P, axis)) {
+      L.PP = wpass_pencils(wN);
+      L.ldt = P->axd[axis].m | 1;
+      L.wN = wN;
+      L.wt = P->wtab_d[axis];
+      L.pipe = 0;
+    }
   }
   return L;
+}
+
+int f64_warp_len(const Plan& P, int a) {
+  return (P.warp_d[a] && P.dims.N / P.axd[a].m < (1LL << 31)) ? wpass_len(P.axd[a]) : 0;
 }
 
 F32Geom f32_geom(const Plan& P, int a) {

@@ -16,6 +16,21 @@ struct Cplx {
   T x, y;
 };
 
+// The vector type of one complex value in shared-memory sequence buffers and
+// twiddle tables (one 64- or 128-bit access).
+template <typename T>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> {
+  using type = float2;
+};
+template <>
+struct Vec2Of<double> {
+  using type = double2;
+};
+template <typename T>
+using vec2_t = typename Vec2Of<T>::type;
+
 template <typename T>
 __device__ __forceinline__ Cplx<T> cadd(Cplx<T> a, Cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T>

@@ -23,8 +23,8 @@ struct PassLaunch {
   double* partial;
   const int* done;     // optional early-exit flag (PCG)
   int pipe;            // 1: persistent two-stage pipelined kernel (same input and arithmetic type only)
-  int wN;              // FP32 only: > 0 runs the warp-FFT pass of length wN (PP, ldt as wpass_pencils)
-  const float2* wt;    // its twiddles exp(-2 pi i e / wN), e < wN
+  int wN;              // > 0 runs the warp-FFT pass of length wN (PP, ldt as wpass_pencils)
+  const vec2_t<Tc>* wt;  // its twiddles exp(-2 pi i e / wN), e < wN
 };
 
 // Per-system descriptor of one batched transform pass.
@@ -42,7 +42,7 @@ struct PassDesc {
   double* partial;
   const int* done;
   int wN;            // as PassLaunch
-  const float2* wt;
+  const vec2_t<Tc>* wt;
 };
 
 template <typename Tc, typename Tin, typename Tout>
@@ -59,8 +59,8 @@ cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const lo
 // Per FFT length N (one translation unit each): the warp-FFT pass of one
 // direction, and its batched form (every system of the launch has wN == N and
 // transform kind `kind`).
-template <int N, typename Tin, typename Tout>
-cudaError_t launch_wpass(const PassLaunch<float>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
+template <int N, typename Tc, typename Tin, typename Tout>
+cudaError_t launch_wpass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
 template <int N, typename Tin, typename Tout>
 cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                    long long total_tiles, size_t smem, int kind, int mode, int ndot,
@@ -72,13 +72,15 @@ size_t precond_smem_bytes_pipe(int PP, int ldt, int F, size_t elt);  // pipeline
 cudaError_t launch_rden_fill(double* rden, const Dims& dims, const double* lamF, const double* lam0,
                              const double* lam1, cudaStream_t st);  // F: FFT length (AxisTab::F)
 int precond_tiles(const Dims& dims, int axis, int PP);
-// FP32 warp-FFT passes (D = {0,1} directions whose FFT length is 64, 128, 256
-// or 512: DST-II/III with n_reg of that length, DST-I with 2 (n_reg + 1)):
-// the length the pass runs at for a direction with these tables (0: not
-// eligible), its pencils per tile, and its shared memory for tile row length ldt.
+// Warp-FFT passes (D = {0,1} directions whose FFT length is 64, 128, 256 or
+// 512 -- FP64: 64, 128 or 256: DST-II/III with n_reg of that length, DST-I
+// with 2 (n_reg + 1)): the length the pass runs at for a direction with these
+// tables (0: not eligible), its pencils per tile, and its shared memory for
+// tile row length ldt and arithmetic of elt bytes.
 int wpass_len(const AxisTab<float>& ax);
+int wpass_len(const AxisTab<double>& ax);
 int wpass_pencils(int N);
-size_t wpass_smem_bytes(int N, int ldt);
+size_t wpass_smem_bytes(int N, int ldt, size_t elt = sizeof(float));
 
 template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);

@@ -134,6 +134,10 @@ struct Plan {
   // hand or the tuner finds the block kernel faster), and its twiddle table
   int warp_f[3] = {0, 0, 0};
   const float2* wtab[3] = {nullptr, nullptr, nullptr};
+  // FP64 transforms: the same for the FP64 warp-FFT pass (wpass_len(axd[a]) > 0;
+  // off by default, chosen by hand or by the tuner) and its FP64 twiddles
+  int warp_d[3] = {0, 0, 0};
+  const double2* wtab_d[3] = {nullptr, nullptr, nullptr};
   bool tuned = false;
   // exact FD tables
   const double* QT[3] = {nullptr, nullptr, nullptr};
@@ -169,6 +173,8 @@ struct F32Geom {
   size_t smem;
 };
 F32Geom f32_geom(const Plan& P, int a);
+// FFT length of direction a's FP64 warp-FFT pass (0: the block kernel runs).
+int f64_warp_len(const Plan& P, int a);
 StiffLaunch plan_stiff_launch(const Plan* P, int axis);
 template <typename T>
 void set_fft(AxisTab<T>* t, const FftVar& v);

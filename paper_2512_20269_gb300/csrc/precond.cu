@@ -721,14 +721,18 @@ static cudaError_t launch_pipe_t(const PassLaunch<Tc>& P, const Tc* in, Tc* out,
   return cudaGetLastError();
 }
 
-int wpass_len(const AxisTab<float>& ax) {
+template <typename T>
+static int wpass_len_t(const AxisTab<T>& ax, int nmax) {
   int N = 0;
   if (ax.kind == 1) N = ax.n_reg;                 // DST-II/III: Makhoul, length n_reg
   else if (ax.kind == 0) N = 2 * (ax.n_reg + 1);  // DST-I: odd extension
   else return 0;
-  if (ax.blu || ax.L != N || ax.F != N) return 0;
+  if (ax.blu || ax.L != N || ax.F != N || N > nmax) return 0;
   return (N == 64 || N == 128 || N == 256 || N == 512) ? N : 0;
 }
+int wpass_len(const AxisTab<float>& ax) { return wpass_len_t(ax, 512); }
+// FP64: a length-512 tile (141 KB of shared memory) would leave one CTA per SM
+int wpass_len(const AxisTab<double>& ax) { return wpass_len_t(ax, 256); }
 
 int wpass_pencils(int N) {
   switch (N) {
@@ -739,24 +743,23 @@ int wpass_pencils(int N) {
   }
 }
 
-size_t wpass_smem_bytes(int N, int ldt) {
+size_t wpass_smem_bytes(int N, int ldt, size_t elt) {
   const int PP = wpass_pencils(N);
-  return (size_t)PP * ldt * sizeof(float) + (size_t)(PP / 2) * wpad(N) * sizeof(Cplx<float>) +
-         (size_t)PP * kMaxNout * sizeof(float);
+  return (size_t)PP * ldt * elt + (size_t)(PP / 2) * wpad(N) * 2 * elt + (size_t)PP * kMaxNout * elt;
 }
 
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
-  if constexpr (std::is_same<Tc, float>::value) {
-    if (P.wN != 0) {
-      if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
-      switch (P.wN) {
-        case 64: return launch_wpass<64, Tin, Tout>(P, MODE, NDOT, in, out, st);
-        case 128: return launch_wpass<128, Tin, Tout>(P, MODE, NDOT, in, out, st);
-        case 256: return launch_wpass<256, Tin, Tout>(P, MODE, NDOT, in, out, st);
-        case 512: return launch_wpass<512, Tin, Tout>(P, MODE, NDOT, in, out, st);
-        default: return cudaErrorInvalidValue;
-      }
+  if (P.wN != 0) {
+    if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
+    switch (P.wN) {
+      case 64: return launch_wpass<64, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
+      case 128: return launch_wpass<128, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
+      case 256: return launch_wpass<256, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
+      case 512:
+        if constexpr (std::is_same<Tc, float>::value) return launch_wpass<512, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
+        else return cudaErrorInvalidValue;
+      default: return cudaErrorInvalidValue;
     }
   }
   if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value) {

@@ -1,5 +1,5 @@
-// FP32 transform passes with warp-local FFTs (included by precond.cu, after the
-// small DFTs, reg_gather and the tile helpers).
+// Transform passes with warp-local FFTs, FP32 or FP64 arithmetic T (one
+// translation unit per FFT length includes this header).
 //
 // Same operator as precond_pass (Q~^T, Q~, or both with the eigenvalue scaling,
 // eq. "preconditioner"), for the D = {0,1} directions of Table 1 whose FFT
@@ -7,7 +7,8 @@
 // Makhoul's reordering) and DST-I (odd p, N = 2 (n_reg + 1), odd extension). The block-wide
 // kernel spends most of its instructions on run-time index arithmetic and on
 // shared-memory round trips between its steps; with FP32 arithmetic that, not
-// the FFT, limits it. Here a pencil pair belongs to LS lanes of one warp from
+// the FFT, limits it, and in FP64 its block-wide barriers between the steps
+// leave part of the FP64 pipe idle. Here a pencil pair belongs to LS lanes of one warp from
 // the edge gather to the output: the gather and Makhoul's reordering feed the
 // first FFT stage directly, every stage reads its R = N / LS values per lane
 // into registers, synchronises the warp and writes them back in place, and the
@@ -26,16 +27,33 @@
 
 namespace iffd {
 
-// Complex values in the sequence buffers are float2 (8-byte aligned, one
-// 64-bit shared-memory access each).
-__device__ __forceinline__ Cplx<float> wld(const float2* b, int i) {
-  const float2 t = b[i];
+// Complex values in the sequence buffers are float2 / double2 (one 64- or
+// 128-bit shared-memory access each).
+template <typename T>
+__device__ __forceinline__ Cplx<T> wld(const vec2_t<T>* b, int i) {
+  const vec2_t<T> t = b[i];
   return {t.x, t.y};
 }
-__device__ __forceinline__ void wst(float2* b, int i, Cplx<float> v) { b[i] = make_float2(v.x, v.y); }
+template <typename T>
+__device__ __forceinline__ void wst(vec2_t<T>* b, int i, Cplx<T> v) { b[i] = vec2_t<T>{v.x, v.y}; }
 
-template <int r>
-__device__ __forceinline__ void wdft(Cplx<float>* v) {
+// The four post-processing factors of DST-II/III output pair k (AxisTab::post).
+template <typename T>
+struct Post4 {
+  T x, y, z, w;
+};
+__device__ __forceinline__ Post4<float> ldpost(const float* p, int k) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
+  return {t.x, t.y, t.z, t.w};
+}
+__device__ __forceinline__ Post4<double> ldpost(const double* p, int k) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p) + 2 * k);
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 2 * k + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+
+template <int r, typename T>
+__device__ __forceinline__ void wdft(Cplx<T>* v) {
   if constexpr (r == 2) dft2(v);
   else if constexpr (r == 4) dft4(v);
   else dft8(v);
@@ -45,8 +63,8 @@ __device__ __forceinline__ void wdft(Cplx<float>* v) {
 // index map as fft_block): butterfly j takes in[j + q N/r], twiddles input q by
 // exp(-2 pi i q k / (Ns r)), k = j mod Ns (table wt[e] = exp(-2 pi i e / N)),
 // and writes out[(j - k) r + k + t Ns]. Lane ls runs butterflies ls + LS u.
-template <int N, int r, int Ns>
-__device__ __forceinline__ void wstage(float2* buf, int ls, const float2* __restrict__ wt) {
+template <typename T, int N, int r, int Ns>
+__device__ __forceinline__ void wstage(vec2_t<T>* buf, int ls, const vec2_t<T>* __restrict__ wt) {
   constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, nb = N / r, BPL = R / r;
   static_assert(N % r == 0 && R % r == 0 && nb == LS * BPL, "stage does not tile the warp");
   // with nb and Ns multiples of 8 (Ns = 1 only with r = 8), the padded index
@@ -54,12 +72,12 @@ __device__ __forceinline__ void wstage(float2* buf, int ls, const float2* __rest
   // wpad(base + t Ns) = wpad(base) + t (Ns + Ns / 8) (+ t when Ns = 1)
   static_assert(nb % 8 == 0 && (Ns % 8 == 0 || (Ns == 1 && r == 8)), "padded index not linear");
   constexpr int qstep = nb + nb / 8, tstep = (Ns == 1) ? 1 : Ns + Ns / 8;
-  Cplx<float> v[BPL][r];
+  Cplx<T> v[BPL][r];
 #pragma unroll
   for (int u = 0; u < BPL; ++u) {
-    const float2* bj = buf + wpad(ls + LS * u);
+    const vec2_t<T>* bj = buf + wpad(ls + LS * u);
 #pragma unroll
-    for (int q = 0; q < r; ++q) v[u][q] = wld(bj, q * qstep);
+    for (int q = 0; q < r; ++q) v[u][q] = wld<T>(bj, q * qstep);
   }
   __syncwarp();
 #pragma unroll
@@ -69,33 +87,33 @@ __device__ __forceinline__ void wstage(float2* buf, int ls, const float2* __rest
     if constexpr (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < r; ++q) {
-        const float2 w = __ldg(wt + q * k * (N / (Ns * r)));
-        v[u][q] = cmul(v[u][q], Cplx<float>{w.x, w.y});
+        const vec2_t<T> w = __ldg(wt + q * k * (N / (Ns * r)));
+        v[u][q] = cmul(v[u][q], Cplx<T>{w.x, w.y});
       }
     }
     wdft<r>(v[u]);
-    float2* bb = buf + wpad((j - k) * r + k);
+    vec2_t<T>* bb = buf + wpad((j - k) * r + k);
 #pragma unroll
-    for (int t = 0; t < r; ++t) wst(bb, t * tstep, v[u][t]);
+    for (int t = 0; t < r; ++t) wst<T>(bb, t * tstep, v[u][t]);
   }
   __syncwarp();
 }
 
 // The stages after the first (span Ns = 8).
-template <int N>
-__device__ __forceinline__ void wfft_rest(float2* buf, int ls, const float2* __restrict__ wt) {
-  wstage<N, 8, 8>(buf, ls, wt);
-  if constexpr (N == 128) wstage<N, 2, 64>(buf, ls, wt);
-  if constexpr (N == 256) wstage<N, 4, 64>(buf, ls, wt);
-  if constexpr (N == 512) wstage<N, 8, 64>(buf, ls, wt);
+template <typename T, int N>
+__device__ __forceinline__ void wfft_rest(vec2_t<T>* buf, int ls, const vec2_t<T>* __restrict__ wt) {
+  wstage<T, N, 8, 8>(buf, ls, wt);
+  if constexpr (N == 128) wstage<T, N, 2, 64>(buf, ls, wt);
+  if constexpr (N == 256) wstage<T, N, 4, 64>(buf, ls, wt);
+  if constexpr (N == 512) wstage<T, N, 8, 64>(buf, ls, wt);
 }
 
 // First stage (radix 8, span 1, no twiddles) with the inputs supplied by
 // src(j, q) (sequence element j + q N/8; j < N/8, q a constant once unrolled).
-template <int N, typename Src>
-__device__ __forceinline__ void wstage_first(float2* buf, int ls, Src src) {
+template <typename T, int N, typename Src>
+__device__ __forceinline__ void wstage_first(vec2_t<T>* buf, int ls, Src src) {
   constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, r = 8, nb = N / r, BPL = R / r;
-  Cplx<float> v[BPL][r];
+  Cplx<T> v[BPL][r];
 #pragma unroll
   for (int u = 0; u < BPL; ++u) {
     const int j = ls + LS * u;
@@ -107,16 +125,16 @@ __device__ __forceinline__ void wstage_first(float2* buf, int ls, Src src) {
   for (int u = 0; u < BPL; ++u) {
     const int j = ls + LS * u;
     dft8(v[u]);
-    float2* bb = buf + wpad(j * r);  // wpad(8 j + t) = wpad(8 j) + t
+    vec2_t<T>* bb = buf + wpad(j * r);  // wpad(8 j + t) = wpad(8 j) + t
 #pragma unroll
-    for (int t = 0; t < r; ++t) wst(bb, t, v[u][t]);
+    for (int t = 0; t < r; ++t) wst<T>(bb, t, v[u][t]);
   }
   __syncwarp();
 }
 
 // Sum over the LS lanes of one sequence group (aligned, power of two).
-template <int LS>
-__device__ __forceinline__ float group_sum(float v) {
+template <int LS, typename T>
+__device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
   for (int off = LS / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -124,18 +142,18 @@ __device__ __forceinline__ float group_sum(float v) {
 
 // V_reg row rule of the scatter (x_i = sum_j V_reg[i][j] w_j): edge blocks,
 // interior blocks, identity runs (see AxisTab).
-template <typename WReg>
-__device__ __forceinline__ float wscatter_row(int i, const AxisTab<float>& ax, WReg wreg) {
+template <typename T, typename WReg>
+__device__ __forceinline__ T wscatter_row(int i, const AxisTab<T>& ax, WReg wreg) {
   const int m = ax.m, N = ax.n_reg;
   if (i < ax.rowsL) {
-    float x = 0.f;
-    for (int c = 0; c < ax.nL; ++c) x = fmaf(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
+    T x = T(0);
+    for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
     return x;
   }
   if (i >= m - ax.rowsR) {
     const int r = m - 1 - i;
-    float x = 0.f;
-    for (int c = 0; c < ax.nR; ++c) x = fmaf(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
+    T x = T(0);
+    for (int c = 0; c < ax.nR; ++c) x = fma(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
     return x;
   }
   int o = ax.o;
@@ -145,9 +163,9 @@ __device__ __forceinline__ float wscatter_row(int i, const AxisTab<float>& ax, W
     if (i < r0) break;
     if (i < r1) {
       const int c0 = __ldg(B), c1 = __ldg(B + 1);
-      const float* V = ax.VB + __ldg(B + 5) + (i - r0) * (c1 - c0);
-      float x = 0.f;
-      for (int c = c0; c < c1; ++c) x = fmaf(__ldg(V + (c - c0)), wreg(c), x);
+      const T* V = ax.VB + __ldg(B + 5) + (i - r0) * (c1 - c0);
+      T x = T(0);
+      for (int c = c0; c < c1; ++c) x = fma(__ldg(V + (c - c0)), wreg(c), x);
       return x;
     }
     o = __ldg(B + 4);
@@ -189,9 +207,9 @@ __device__ __forceinline__ TileInfo wtile_setup(const Dims& dims, int axis, int 
 
 // The three steps of one tile: coalesced load into `tile` (row length ldt),
 // warp-local transform, coalesced store. Each is called by the whole CTA.
-template <int N, typename Tin>
-__device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, float* tile, int axis, int ldt,
-                                           const AxisTab<float>& ax, const long long* pbase, const TileInfo& g) {
+template <int N, typename T, typename Tin>
+__device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, T* tile, int axis, int ldt,
+                                           const AxisTab<T>& ax, const long long* pbase, const TileInfo& g) {
   constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
   const int m = ax.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -199,13 +217,13 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, float* ti
   // ---- coalesced tile load (padding pencils are zero)
   if (axis == 0) {
     for (int pc = warp; pc < PP; pc += kThreads / 32) {
-      float* row = tile + pc * ldt;
+      T* row = tile + pc * ldt;
       if (pc < g.nvalid) {
         const Tin* src = in + pbase[pc];
 #pragma unroll 4
-        for (int i = lane; i < m; i += 32) row[i] = (float)src[i];
+        for (int i = lane; i < m; i += 32) row[i] = (T)src[i];
       } else {
-        for (int i = lane; i < m; i += 32) row[i] = 0.f;
+        for (int i = lane; i < m; i += 32) row[i] = T(0);
       }
     }
   } else {
@@ -224,21 +242,21 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, float* ti
         v2 = p[2 * step];
         v3 = p[3 * step];
       }
-      tile[pc * ldt + i] = (float)v0;
-      tile[pc * ldt + i + RS] = (float)v1;
-      tile[pc * ldt + i + 2 * RS] = (float)v2;
-      tile[pc * ldt + i + 3 * RS] = (float)v3;
+      tile[pc * ldt + i] = (T)v0;
+      tile[pc * ldt + i + RS] = (T)v1;
+      tile[pc * ldt + i + 2 * RS] = (T)v2;
+      tile[pc * ldt + i + 3 * RS] = (T)v3;
     }
-    for (; i < m; i += RS, p += step) tile[pc * ldt + i] = valid ? (float)p[0] : 0.f;
+    for (; i < m; i += RS, p += step) tile[pc * ldt + i] = valid ? (T)p[0] : T(0);
   }
 }
 
 // KIND 1: DST-II / DST-III (even p), FFT length N = n_reg in Makhoul's order;
 // KIND 0: DST-I (odd p), FFT length N = 2 (n_reg + 1) of the odd extension.
-template <int N, int KIND, int MODE>
-__device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* outv, const Dims& dims, int ldt,
-                                           const AxisTab<float>& ax, const float2* __restrict__ wt,
-                                           const float* __restrict__ lamA, const float* __restrict__ lamB,
+template <typename T, int N, int KIND, int MODE>
+__device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, const Dims& dims, int ldt,
+                                           const AxisTab<T>& ax, const vec2_t<T>* __restrict__ wt,
+                                           const T* __restrict__ lamA, const T* __restrict__ lamB,
                                            const int* pia, const int* pib) {
   constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
   const int m = ax.m;
@@ -247,28 +265,28 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
   // ---- warp-local transform of pencil pair pr (pencils 2 pr, 2 pr + 1)
   const int grp = lane / LS, ls = lane % LS;
   const int pr = warp * G + grp;
-  float* ra = tile + (2 * pr) * ldt;
-  float* rb = ra + ldt;
-  float* ova = outv + (2 * pr) * kMaxNout;
-  float* ovb = ova + kMaxNout;
-  float2* buf = wbuf + (size_t)pr * wbuf_len<N>();
+  T* ra = tile + (2 * pr) * ldt;
+  T* rb = ra + ldt;
+  T* ova = outv + (2 * pr) * kMaxNout;
+  T* ovb = ova + kMaxNout;
+  vec2_t<T>* buf = wbuf + (size_t)pr * wbuf_len<N>();
   const int nw = ax.n_out;
   constexpr int NR = (KIND == 1) ? N : N / 2 - 1;  // n_reg
 
   if (MODE == PM_FWD || MODE == PM_FUSED) {
     // y_out = W^T r over the support rows of W, four columns per row read
     for (int k0 = 0; k0 < nw; k0 += 4) {
-      float sa[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f};
+      T sa[4] = {T(0), T(0), T(0), T(0)}, sb[4] = {T(0), T(0), T(0), T(0)};
       auto rows = [&](int i0, int i1) {
         for (int i = i0 + ls; i < i1; i += LS) {
-          const float xa = ra[i], xb = rb[i];
-          const float* w = ax.W + i * nw + k0;
+          const T xa = ra[i], xb = rb[i];
+          const T* w = ax.W + i * nw + k0;
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             if (k0 + k < nw) {
-              const float wk = __ldg(w + k);
-              sa[k] = fmaf(wk, xa, sa[k]);
-              sb[k] = fmaf(wk, xb, sb[k]);
+              const T wk = __ldg(w + k);
+              sa[k] = fma(wk, xa, sa[k]);
+              sb[k] = fma(wk, xb, sb[k]);
             }
         }
       };
@@ -277,7 +295,7 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         if (k0 + k < nw) {
-          const float ya = group_sum<LS>(sa[k]), yb = group_sum<LS>(sb[k]);
+          const T ya = group_sum<LS>(sa[k]), yb = group_sum<LS>(sb[k]);
           if (ls == 0) {
             ova[k0 + k] = ya;
             ovb[k0 + k] = yb;
@@ -295,13 +313,13 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
     const bool uniform = ax.nblk == 0 && 2 * ne <= 4 * LS;
     if (uniform) {
       // every lane reads its (at most 4) edge values before any lane writes
-      float ev[4];
+      T ev[4];
       int slot[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int t = ls + r * LS;
         slot[r] = -1;
-        ev[r] = 0.f;
+        ev[r] = T(0);
         if (t < 2 * ne) {
           const int c = t < ne ? t : t - ne;
           const int i = c < ax.nL ? c : NR - ax.nR + (c - ax.nL);
@@ -316,11 +334,11 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
       __syncwarp();
     }
     if constexpr (KIND == 1) {
-      wstage_first<N>(buf, ls, [&](int j, int q) {
+      wstage_first<T, N>(buf, ls, [&](int j, int q) {
         const int l = j + q * (N / 8);
         const bool hi = q >= 4;
         const int i = hi ? 2 * (N - 1 - l) + 1 : 2 * l;
-        float ya, yb;
+        T ya, yb;
         if (uniform) {
           ya = ra[i + ax.o];
           yb = rb[i + ax.o];
@@ -328,32 +346,32 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
           ya = reg_gather(ra, i, ax);
           yb = reg_gather(rb, i, ax);
         }
-        return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
+        return Cplx<T>{neg_if(ya, hi), neg_if(yb, hi)};
       });
-      wfft_rest<N>(buf, ls, wt);
+      wfft_rest<T, N>(buf, ls, wt);
       // separation, twiddle and D~^{-1}: outputs N-1-k and k-1 from Z[k], Z[N-k]
       for (int k = ls; k <= N / 2; k += LS) {
-        const Cplx<float> zk = wld(buf, wpad(k));
-        const Cplx<float> zm = wld(buf, wpad(k == 0 ? 0 : N - k));
-        const float Ar = zk.x + zm.x, Ai = zk.y - zm.y;
-        const float Br = zk.y + zm.y, Bi = zm.x - zk.x;
-        const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
-        ra[N - 1 - k] = fmaf(t.x, Ar, t.y * Ai);
-        rb[N - 1 - k] = fmaf(t.x, Br, t.y * Bi);
+        const Cplx<T> zk = wld<T>(buf, wpad(k));
+        const Cplx<T> zm = wld<T>(buf, wpad(k == 0 ? 0 : N - k));
+        const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
+        const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
+        const Post4<T> t = ldpost(ax.post, k);
+        ra[N - 1 - k] = fma(t.x, Ar, t.y * Ai);
+        rb[N - 1 - k] = fma(t.x, Br, t.y * Bi);
         if (k > 0 && 2 * k != N) {
-          ra[k - 1] = fmaf(t.z, Ar, -t.w * Ai);
-          rb[k - 1] = fmaf(t.z, Br, -t.w * Bi);
+          ra[k - 1] = fma(t.z, Ar, -t.w * Ai);
+          rb[k - 1] = fma(t.z, Br, -t.w * Bi);
         }
       }
     } else {
       // odd extension of length N = 2n: 0, y_0 .. y_{n-2}, 0, -y_{n-2} .. -y_0;
       // element l = j + q N/8 is in the second half exactly when q >= 4, and
       // the zeros are l = 0 and l = n (j = 0 with q = 0 or 4)
-      wstage_first<N>(buf, ls, [&](int j, int q) {
+      wstage_first<T, N>(buf, ls, [&](int j, int q) {
         const int l = j + q * (N / 8);
         const bool hi = q >= 4;
         const int i = hi ? N - 1 - l : l - 1;
-        float ya = 0.f, yb = 0.f;
+        T ya = T(0), yb = T(0);
         if (!((q == 0 || q == 4) && j == 0)) {
           if (uniform) {
             ya = ra[i + ax.o];
@@ -363,13 +381,13 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
             yb = reg_gather(rb, i, ax);
           }
         }
-        return Cplx<float>{neg_if(ya, hi), neg_if(yb, hi)};
+        return Cplx<T>{neg_if(ya, hi), neg_if(yb, hi)};
       });
-      wfft_rest<N>(buf, ls, wt);
+      wfft_rest<T, N>(buf, ls, wt);
       // DST-I output j is -Im Z[j+1] (pencil a) and Re Z[j+1] (pencil b), times 1/(2 D~_j)
       for (int j = ls; j < NR; j += LS) {
-        const Cplx<float> z = wld(buf, wpad(j + 1));
-        const float sc = __ldg(ax.post + j);
+        const Cplx<T> z = wld<T>(buf, wpad(j + 1));
+        const T sc = __ldg(ax.post + j);
         ra[j] = -sc * z.y;
         rb[j] = sc * z.x;
       }
@@ -385,12 +403,12 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
   if (MODE == PM_FUSED) {
     // divide by the summed eigenvalues of all directions
     const int pa = 2 * pr, pb = pa + 1;
-    const float la = __ldg(lamA + pia[pa]), lb = __ldg(lamA + pia[pb]);
-    const float ma = (dims.d == 3) ? __ldg(lamB + pib[pa]) : 0.f;
-    const float mb = (dims.d == 3) ? __ldg(lamB + pib[pb]) : 0.f;
+    const T la = __ldg(lamA + pia[pa]), lb = __ldg(lamA + pia[pb]);
+    const T ma = (dims.d == 3) ? __ldg(lamB + pib[pa]) : T(0);
+    const T mb = (dims.d == 3) ? __ldg(lamB + pib[pb]) : T(0);
     for (int i = ls; i < m; i += LS) {
-      const float li = __ldg(ax.lam + i);
-      float da = li + la, db = li + lb;
+      const T li = __ldg(ax.lam + i);
+      T da = li + la, db = li + lb;
       if (dims.d == 3) {
         da += ma;
         db += mb;
@@ -409,35 +427,35 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
     if constexpr (KIND == 1) {
       // inverse of the separation: G[k], G[N-k] from rows N-1-k and k-1
       for (int k = ls; k <= N / 2; k += LS) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(ax.post) + k);
+        const Post4<T> t = ldpost(ax.post, k);
         if (k == 0 || 2 * k == N) {
-          const float s = t.x + t.x;
-          buf[wpad(k)] = make_float2(s * ra[N - 1 - k], s * rb[N - 1 - k]);
+          const T s = t.x + t.x;
+          buf[wpad(k)] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
         } else {
-          const float ar = fmaf(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
-          const float ai = fmaf(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
-          const float br = fmaf(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
-          const float bi = fmaf(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
-          buf[wpad(k)] = make_float2(ar - bi, ai + br);
-          buf[wpad(N - k)] = make_float2(ar + bi, br - ai);
+          const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
+          const T ai = fma(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
+          const T br = fma(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
+          const T bi = fma(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+          buf[wpad(k)] = vec2_t<T>{ar - bi, ai + br};
+          buf[wpad(N - k)] = vec2_t<T>{ar + bi, br - ai};
         }
       }
     } else {
       // odd extension of the scaled input w_j / (2 D~_j)
       for (int l = ls; l < N; l += LS) {
-        float va = 0.f, vb = 0.f;
+        T va = T(0), vb = T(0);
         if (l != 0 && l != N / 2) {
           const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
-          const float sc = (l < N / 2) ? __ldg(ax.post + jj) : -__ldg(ax.post + jj);
+          const T sc = (l < N / 2) ? __ldg(ax.post + jj) : -__ldg(ax.post + jj);
           va = sc * ra[jj];
           vb = sc * rb[jj];
         }
-        buf[wpad(l)] = make_float2(va, vb);
+        buf[wpad(l)] = vec2_t<T>{va, vb};
       }
     }
     __syncwarp();
-    wstage<N, 8, 1>(buf, ls, wt);
-    wfft_rest<N>(buf, ls, wt);
+    wstage<T, N, 8, 1>(buf, ls, wt);
+    wfft_rest<T, N>(buf, ls, wt);
     // x = V_reg w + W z_out, row by row (DST-III output j is +-Re/Im Z[l(j)];
     // DST-I output j is -Im Z[j+1] / Re Z[j+1])
     for (int i = ls; i < m; i += LS) {
@@ -457,7 +475,7 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
           return buf[wpad(j + 1)].x;
         }
       };
-      float xa, xb;
+      T xa, xb;
       if (ax.nblk == 0 && i >= ax.rowsL && i < m - ax.rowsR) {  // identity rows
         xa = wa(i - ax.o);
         xb = wb(i - ax.o);
@@ -467,9 +485,9 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
       }
       if (i < ax.wlo || i >= ax.whi) {
         for (int k = 0; k < nw; ++k) {
-          const float w = __ldg(ax.W + i * nw + k);
-          xa = fmaf(w, ova[k], xa);
-          xb = fmaf(w, ovb[k], xb);
+          const T w = __ldg(ax.W + i * nw + k);
+          xa = fma(w, ova[k], xa);
+          xb = fma(w, ovb[k], xb);
         }
       }
       ra[i] = xa;
@@ -478,20 +496,19 @@ __device__ __forceinline__ void wtransform(float* tile, float2* wbuf, float* out
   }
 }
 
-template <int N, typename Tout, int NDOT>
-__device__ __forceinline__ void wstore_tile(const float* tile, Tout* __restrict__ out, int axis, int ldt,
-                                            const AxisTab<float>& ax, const long long* pbase, const TileInfo& g,
+template <int N, typename T, typename Tout, int NDOT>
+__device__ __forceinline__ void wstore_tile(const T* tile, Tout* __restrict__ out, int axis, int ldt,
+                                            const AxisTab<T>& ax, const long long* pbase, const TileInfo& g,
                                             const double* __restrict__ dotv0, const double* __restrict__ dotv1,
                                             double* __restrict__ partial, int ptile, int pstride) {
-  constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
+  constexpr int PP = warp_pencils<N>();
   const int m = ax.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  (void)LS; (void)G; (void)tid; (void)warp; (void)lane;
   // ---- coalesced store (and the partial dot products of a PCG step)
   double d0 = 0.0, d1 = 0.0;
   if (axis == 0) {
     for (int pc = warp; pc < g.nvalid; pc += kThreads / 32) {
-      const float* row = tile + pc * ldt;
+      const T* row = tile + pc * ldt;
       Tout* dst = out + pbase[pc];
       const long long off0 = pbase[pc];
       for (int i = lane; i < m; i += 32) {
@@ -537,54 +554,83 @@ __device__ __forceinline__ void wstore_tile(const float* tile, Tout* __restrict_
   }
 }
 
-// One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
-template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
-__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
-                                           int axis, int ldt, const AxisTab<float>& ax, const float2* __restrict__ wt,
-                                           const float* __restrict__ lamA, const float* __restrict__ lamB,
-                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
-                                           double* __restrict__ partial, long long tile_id, int ptile, int pstride,
-                                           unsigned char* smem) {
+// FP64 FUSED passes divide by the summed eigenvalues between the forward and
+// the backward transform as one block-wide step: a multiply with the
+// precomputed reciprocal, read in the coalesced order of the tile load (the
+// same product as the block kernel's), else a division.
+template <int N>
+__device__ __forceinline__ void wscale_tile(double* tile, int axis, int ldt, const AxisTab<double>& ax,
+                                            const Dims& dims, const double* __restrict__ lamA,
+                                            const double* __restrict__ lamB, const long long* pbase, const int* pia,
+                                            const int* pib, const TileInfo& g) {
   constexpr int PP = warp_pencils<N>();
-  float* tile = reinterpret_cast<float*>(smem);
-  float2* wbuf = reinterpret_cast<float2*>(tile + (size_t)PP * ldt);
-  float* outv = reinterpret_cast<float*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
+  const int m = ax.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (ax.rden == nullptr) {
+    for (int e = tid; e < PP * m; e += kThreads) {
+      const int pc = e / m, i = e - pc * m;
+      if (pc >= g.nvalid) continue;
+      double den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
+      if (dims.d == 3) den += __ldg(lamB + pib[pc]);
+      tile[pc * ldt + i] = tile[pc * ldt + i] / den;
+    }
+  } else if (axis == 0) {
+    for (int pc = warp; pc < g.nvalid; pc += kThreads / 32)
+      for (int i = lane; i < m; i += 32) tile[pc * ldt + i] = tile[pc * ldt + i] * __ldg(ax.rden + pbase[pc] + i);
+  } else {
+    constexpr int RS = kThreads / PP;
+    const int pc = tid & (PP - 1);
+    if (pc < g.nvalid)
+      for (int i = tid / PP; i < m; i += RS)
+        tile[pc * ldt + i] = tile[pc * ldt + i] * __ldg(ax.rden + pbase[pc] + i * g.S);
+  }
+}
+
+// One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
+template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
+                                           int axis, int ldt, const AxisTab<T>& ax,
+                                           const vec2_t<T>* __restrict__ wt, const T* __restrict__ lamA,
+                                           const T* __restrict__ lamB, const double* __restrict__ dotv0,
+                                           const double* __restrict__ dotv1, double* __restrict__ partial,
+                                           long long tile_id, int ptile, int pstride, unsigned char* smem) {
+  constexpr int PP = warp_pencils<N>();
+  T* tile = reinterpret_cast<T*>(smem);
+  vec2_t<T>* wbuf = reinterpret_cast<vec2_t<T>*>(tile + (size_t)PP * ldt);
+  T* outv = reinterpret_cast<T*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
   __shared__ long long pbase[PP];
   __shared__ int pia[PP], pib[PP];
   const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
   __syncthreads();
-  wload_tile<N, Tin>(in, tile, axis, ldt, ax, pbase, g);
+  wload_tile<N, T, Tin>(in, tile, axis, ldt, ax, pbase, g);
   __syncthreads();
-  wtransform<N, KIND, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+  if constexpr (std::is_same<T, double>::value && MODE == PM_FUSED) {
+    wtransform<T, N, KIND, PM_FWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    __syncthreads();
+    wscale_tile<N>(tile, axis, ldt, ax, dims, lamA, lamB, pbase, pia, pib, g);
+    __syncthreads();
+    wtransform<T, N, KIND, PM_BWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+  } else {
+    wtransform<T, N, KIND, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+  }
   __syncthreads();
-  wstore_tile<N, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
+  wstore_tile<N, T, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
 }
 
-template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
-precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<float> ax, const float2* wt,
-              const float* __restrict__ lamA, const float* __restrict__ lamB, const double* __restrict__ dotv0,
+precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<T> ax, const vec2_t<T>* wt,
+              const T* __restrict__ lamA, const T* __restrict__ lamB, const double* __restrict__ dotv0,
               const double* __restrict__ dotv1, double* __restrict__ partial, const int* __restrict__ done) {
   if (done != nullptr && *((volatile const int*)done)) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  wpass_body<N, KIND, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
-                                             blockIdx.x, blockIdx.x, gridDim.x, smem);
+  wpass_body<T, N, KIND, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
+                                                blockIdx.x, blockIdx.x, gridDim.x, smem);
 }
 
-// ---------------------------------------------------------------- launchers
-inline int warp_sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
-  }
-  return n;
-}
-
-// Batched warp-FFT pass: every system of the launch runs the warp-FFT pass of
-// length N (a separate kernel from the block one, so that neither carries the
-// other's register allocation).
+// Batched warp-FFT pass (FP32): every system of the launch runs the warp-FFT
+// pass of length N (a separate kernel from the block one, so that neither
+// carries the other's register allocation).
 template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
 precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const long long* __restrict__ tile_prefix,
@@ -607,14 +653,16 @@ precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const 
   if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
   const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
   const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
-  wpass_body<N, KIND, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA, sd.lamB,
-                                       sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles, smem);
+  wpass_body<float, N, KIND, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
+                                                    sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles,
+                                                    smem);
 }
 
-template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
-cudaError_t launch_wpass_n(const PassLaunch<float>& P, const Tin* in, Tout* out, cudaStream_t st) {
-  auto kern = precond_wpass<N, KIND, Tin, Tout, MODE, NDOT>;
-  const size_t sm = wpass_smem_bytes(N, P.ldt);
+// ---------------------------------------------------------------- launchers
+template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_wpass_n(const PassLaunch<T>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  auto kern = precond_wpass<T, N, KIND, Tin, Tout, MODE, NDOT>;
+  const size_t sm = wpass_smem_bytes(N, P.ldt, sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
@@ -625,7 +673,7 @@ cudaError_t launch_wpass_n(const PassLaunch<float>& P, const Tin* in, Tout* out,
 
 template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                     long long total_tiles, size_t smem, cudaStream_t st) {
+                              long long total_tiles, size_t smem, cudaStream_t st) {
   auto kern = precond_wpass_batched<N, KIND, Tin, Tout, MODE, NDOT>;
   static size_t smem_set = 0;  // attribute is raised only when needed (not inside a graph capture)
   if (smem > smem_set) {
@@ -638,40 +686,34 @@ cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long 
   return cudaGetLastError();
 }
 
-template <int N, int KIND, typename Tin, typename Tout>
-cudaError_t launch_wbatched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                     long long total_tiles, size_t smem, int mode, int ndot, cudaStream_t st) {
-  if (mode == PM_FWD)
-    return launch_wbatched_t<N, KIND, Tin, Tout, PM_FWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (mode == PM_FUSED)
-    return launch_wbatched_t<N, KIND, Tin, Tout, PM_FUSED, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (ndot == 0)
-    return launch_wbatched_t<N, KIND, Tin, Tout, PM_BWD, 0>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  if (ndot == 1)
-    return launch_wbatched_t<N, KIND, Tin, Tout, PM_BWD, 1>(sys, tile_prefix, nsys, total_tiles, smem, st);
-  return launch_wbatched_t<N, KIND, Tin, Tout, PM_BWD, 2>(sys, tile_prefix, nsys, total_tiles, smem, st);
-}
-
-
-// Only the (input, output) type and mode combinations the FP32 preconditioner
-// uses exist: FP64 -> FP32 forward passes (first direction), FP32 -> FP32
-// forward, fused and backward passes (ndot 0), FP32 -> FP64 backward passes
-// (last direction, ndot 0..2).
-template <typename Tin, typename Tout>
+// Only the (arithmetic, input, output) type and mode combinations the
+// preconditioners use exist: FP64 throughout (every mode, 0..2 dot products
+// in backward passes); FP32 transforms with FP64 input (forward passes of the
+// first direction), FP32 in and out (forward, fused and backward passes
+// without dot products), FP64 output (backward passes of the first direction,
+// 0..2 dot products).
+template <typename Tc, typename Tin, typename Tout>
 constexpr bool wpass_combo_ok(int mode, int ndot) {
+  if (std::is_same<Tc, double>::value) return std::is_same<Tin, double>::value && std::is_same<Tout, double>::value;
   if (std::is_same<Tin, double>::value) return mode == PM_FWD;
   if (std::is_same<Tout, double>::value) return mode == PM_BWD;
   return ndot == 0;
 }
 
-template <int N, typename Tin, typename Tout>
-cudaError_t launch_wpass(const PassLaunch<float>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
-  if (!wpass_combo_ok<Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
+template <int N, typename Tc, typename Tin, typename Tout>
+cudaError_t launch_wpass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
+  if (!wpass_combo_ok<Tc, Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
   const bool k1 = P.ax.kind == 1;
 #define IFFD_WL(MODE, NDOT)                                                                            \
-  return k1 ? launch_wpass_n<N, 1, Tin, Tout, MODE, NDOT>(P, in, out, st)                              \
-            : launch_wpass_n<N, 0, Tin, Tout, MODE, NDOT>(P, in, out, st);
-  if constexpr (std::is_same<Tin, double>::value) {
+  return k1 ? launch_wpass_n<Tc, N, 1, Tin, Tout, MODE, NDOT>(P, in, out, st)                          \
+            : launch_wpass_n<Tc, N, 0, Tin, Tout, MODE, NDOT>(P, in, out, st);
+  if constexpr (std::is_same<Tc, double>::value) {
+    if (mode == PM_FWD) { IFFD_WL(PM_FWD, 0) }
+    if (mode == PM_FUSED) { IFFD_WL(PM_FUSED, 0) }
+    if (ndot == 0) { IFFD_WL(PM_BWD, 0) }
+    if (ndot == 1) { IFFD_WL(PM_BWD, 1) }
+    IFFD_WL(PM_BWD, 2)
+  } else if constexpr (std::is_same<Tin, double>::value) {
     IFFD_WL(PM_FWD, 0)
   } else if constexpr (std::is_same<Tout, double>::value) {
     if (ndot == 0) { IFFD_WL(PM_BWD, 0) }
@@ -689,7 +731,7 @@ template <int N, typename Tin, typename Tout>
 cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                                    long long total_tiles, size_t smem, int kind, int mode, int ndot,
                                    cudaStream_t st) {
-  if (!wpass_combo_ok<Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
+  if (!wpass_combo_ok<float, Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
   const bool k1 = kind == 1;
 #define IFFD_WB(MODE, NDOT)                                                                                   \
   return k1 ? launch_wbatched_t<N, 1, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st)  \
@@ -709,14 +751,15 @@ cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const 
 }
 
 // Explicit instantiation of one FFT length (one translation unit each, so
-// that they compile in parallel).
+// that they compile in parallel): the FP32 passes and their batched forms,
+// and (IFFD_WARP_INSTANTIATE_F64, lengths up to 256) the FP64 passes.
 #define IFFD_WARP_INSTANTIATE(NN)                                                                              \
-  template cudaError_t launch_wpass<NN, double, float>(const PassLaunch<float>&, int, int, const double*, float*, \
-                                                       cudaStream_t);                                           \
-  template cudaError_t launch_wpass<NN, float, float>(const PassLaunch<float>&, int, int, const float*, float*,   \
-                                                      cudaStream_t);                                            \
-  template cudaError_t launch_wpass<NN, float, double>(const PassLaunch<float>&, int, int, const float*, double*, \
-                                                       cudaStream_t);                                           \
+  template cudaError_t launch_wpass<NN, float, double, float>(const PassLaunch<float>&, int, int, const double*,  \
+                                                              float*, cudaStream_t);                             \
+  template cudaError_t launch_wpass<NN, float, float, float>(const PassLaunch<float>&, int, int, const float*,    \
+                                                             float*, cudaStream_t);                              \
+  template cudaError_t launch_wpass<NN, float, float, double>(const PassLaunch<float>&, int, int, const float*,   \
+                                                              double*, cudaStream_t);                            \
   template cudaError_t launch_wpass_batched_n<NN, double, float>(const PassDesc<float, double, float>*,            \
                                                                  const long long*, int, long long, size_t, int,   \
                                                                  int, int, cudaStream_t);                         \
@@ -726,5 +769,8 @@ cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const 
   template cudaError_t launch_wpass_batched_n<NN, float, double>(const PassDesc<float, float, double>*,            \
                                                                  const long long*, int, long long, size_t, int,   \
                                                                  int, int, cudaStream_t);
+#define IFFD_WARP_INSTANTIATE_F64(NN)                                                                             \
+  template cudaError_t launch_wpass<NN, double, double, double>(const PassLaunch<double>&, int, int,               \
+                                                                const double*, double*, cudaStream_t);
 
 }  // namespace iffd

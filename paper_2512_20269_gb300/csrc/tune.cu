@@ -119,7 +119,7 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
     set_fft(&ax, P->fvar[a][vi]);
     PPs[a] = pp;
     pipes[a] = pipe;
-    if constexpr (!f64) P->warp_f[a] = warp;
+    (f64 ? P->warp_d : P->warp_f)[a] = warp;
   };
   if (precond_tiles(P->dims, a, PPs[a]) < kMinTuneTiles) return IFFD_OK;
   {
@@ -293,17 +293,17 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
   auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
   if (pipelined == 2) {
-    if (f64 || wpass_len(P.axf[axis]) == 0)
-      return fail(IFFD_ERR_UNSUPPORTED, "the warp-FFT pass needs FP32 transforms and a DST-II/III direction of "
-                                        "length 64, 128, 256 or 512");
+    if (f64 ? wpass_len(P.axd[axis]) == 0 : wpass_len(P.axf[axis]) == 0)
+      return fail(IFFD_ERR_UNSUPPORTED, "the warp-FFT pass needs a D = {0,1} direction of FFT length 64, 128, 256 "
+                                        "or 512 (FP64: up to 256)");
     if (pencils_transform > 0) return fail(IFFD_ERR_INVALID_ARG, "the warp-FFT pass has a fixed tile");
-    P.warp_f[axis] = 1;
-    P.pipe_f[axis] = 0;
+    (f64 ? P.warp_d : P.warp_f)[axis] = 1;
+    (f64 ? P.pipe_d : P.pipe_f)[axis] = 0;
     pipelined = -1;
   } else if (pipelined > 2) {
     return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1 or 2 (or < 0)");
-  } else if (!f64 && (pencils_transform > 0 || pipelined >= 0)) {
-    P.warp_f[axis] = 0;  // a block-kernel geometry set by hand
+  } else if (pencils_transform > 0 || pipelined >= 0) {
+    (f64 ? P.warp_d : P.warp_f)[axis] = 0;  // a block-kernel geometry set by hand
   }
   if (pencils_transform > 0) {
     if (!pow2(pencils_transform)) return fail(IFFD_ERR_INVALID_ARG, "pencils per tile must be 2, 4, 8, 16 or 32");
@@ -340,12 +340,13 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   const Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
-  if (pencils_transform) *pencils_transform = f64 ? P.PPd[axis] : f32_geom(P, axis).PP;
+  const int wd = f64 ? f64_warp_len(P, axis) : 0;
+  if (pencils_transform) *pencils_transform = f64 ? (wd ? wpass_pencils(wd) : P.PPd[axis]) : f32_geom(P, axis).PP;
   if (pencils_stiffness)
     *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
   const int nst = f64 ? P.axd[axis].nst : P.axf[axis].nst;
   if (nstages) *nstages = nst;
-  if (pipelined) *pipelined = f64 ? P.pipe_d[axis] : (f32_geom(P, axis).wN ? 2 : P.pipe_f[axis]);
+  if (pipelined) *pipelined = f64 ? (wd ? 2 : P.pipe_d[axis]) : (f32_geom(P, axis).wN ? 2 : P.pipe_f[axis]);
   if (radices)
     for (int s = 0; s < nst; ++s) radices[s] = f64 ? P.axd[axis].radix[s] : P.axf[axis].radix[s];
   return IFFD_OK;

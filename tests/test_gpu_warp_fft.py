@@ -1,9 +1,10 @@
-"""GPU parity of the FP32 warp-FFT transform pass (Dirichlet at both ends,
-FFT length 64, 128, 256, 512: DST-II/III for even p with n_reg of that length,
+"""GPU parity of the warp-FFT transform pass (Dirichlet at both ends, FFT
+length 64, 128, 256, 512: DST-II/III for even p with n_reg of that length,
 DST-I for odd p with 2 (n_reg + 1) = 2 n): each pencil pair is transformed by
-the lanes of one warp. Compared with the oracle (FP32
-tolerance 1e-5) and with the block kernel on the same plan (same operator,
-different FP32 rounding)."""
+the lanes of one warp. FP32 (the default where eligible) is compared with the
+oracle (tolerance 1e-5) and with the block kernel on the same plan (same
+operator, different FP32 rounding); FP64 (opt-in, lengths up to 256) with the
+oracle at 1e-12 and with the FP64 block kernel."""
 
 import numpy as np
 import pytest
@@ -104,7 +105,68 @@ def test_warp_geometry_switches():
     with pytest.raises(IFFDError):
         plan.set_geometry(1, warp=True)  # n_reg = 40
     with pytest.raises(IFFDError):
-        IFFDPlan(2, 64, 4).set_geometry(0, warp=True)  # FP64 plan
+        IFFDPlan(2, 512, 4).set_geometry(0, warp=True)  # FP64 plan, length 512
     with pytest.raises(IFFDError):
         IFFDPlan(2, 40, 3, precision="fp32").set_geometry(0, warp=True)  # DST-I of length 80
 
+
+
+# FP64 warp-FFT pass (opt-in): lengths 64, 128, 256, both transform kinds,
+# directions that do not qualify (n = 40, 37, 30, 48, 512) next to ones that do,
+# repeated knots
+CASES64 = [
+    (2, (64, 64), 4, None), (2, (128, 40), 2, None), (3, (64, 64, 64), 4, None), (3, (256, 37, 20), 6, None),
+    (3, (128, 64, 30), 8, None), (2, (64, 128), 4, ({32: 1}, {20: 2, 100: 1})), (2, (32, 64), 3, None),
+    (3, (128, 40, 64), 5, None), (2, (64, 48), 3, ({20: 2}, None)), (2, (512, 64), 4, None),
+]
+
+
+def _warp_len64(n, p):
+    L = _warp_len(n, p)
+    return L if L <= 256 else 0
+
+
+@pytest.mark.parametrize("d,ns,p,knots", CASES64)
+def test_fp64_warp_pass_matches_oracle_and_block_kernel(d, ns, p, knots):
+    torch = require_gpu()
+    from oracle import operators, splitting
+    from paper_2512_20269_gb300 import IFFDPlan
+    kw = {} if knots is None else {"knots": list(knots)}
+    plan = IFFDPlan(d, list(ns), p, **kw)
+    block = IFFDPlan(d, list(ns), p, **kw)
+    warp_axes = [a for a in range(d) if _warp_len64(ns[a], p)]
+    for a in range(d):
+        assert not plan.tiles(a)["warp"]  # opt-in for FP64
+    for a in warp_axes:
+        plan.set_geometry(a, warp=True)
+    for a in range(d):
+        t = plan.tiles(a)
+        assert t["warp"] == (a in warp_axes)
+        if t["warp"]:
+            assert t["pencils_transform"] == {64: 64, 128: 32, 256: 16}[_warp_len64(ns[a], p)]
+    r = inputs.rhs(plan.shape, "normal", seed=930 + sum(ns) + p)
+    rg = _gpu(torch, r)
+    sp = [splitting.axis_split(n, p, (0, 1), rep=(knots[a] if knots else None)) for a, n in enumerate(ns)]
+    zo = operators.iffd_apply(r, sp)
+    z = plan.apply_preconditioner(rg).cpu().numpy()
+    zb = block.apply_preconditioner(rg).cpu().numpy()
+    assert np.max(np.abs(z - zo)) <= 1e-12 * np.max(np.abs(zo))
+    assert _rel(z, zb) <= 1e-13
+    assert np.array_equal(plan.apply_preconditioner(rg).cpu().numpy(), z)
+
+
+def test_fp64_warp_pass_pcg():
+    """PCG with FP64 warp-FFT passes on every direction (the fused dot
+    products of the last backward pass included): same iteration count as the
+    block kernel, true relative residual <= 1.1e-8, solutions within 1e-10."""
+    torch = require_gpu()
+    from paper_2512_20269_gb300 import IFFDPlan
+    for ns, p in (((64, 128, 128), 4), ((64, 32, 64), 3)):
+        plan = IFFDPlan(3, ns, p)
+        f = _gpu(torch, inputs.rhs(plan.shape, "normal", seed=6 + p))
+        ub, ib = plan.pcg_solve(f)
+        for a in range(3):
+            plan.set_geometry(a, warp=True)
+        uw, iw = plan.pcg_solve(f)
+        assert iw["status"] == 0 and iw["true_rel_res"] <= 1.1e-8 and iw["iters"] == ib["iters"]
+        assert float(torch.linalg.norm(uw - ub) / torch.linalg.norm(ub)) <= 1e-10
