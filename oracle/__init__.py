@@ -24,6 +24,11 @@ What it computes, plainly and slowly, in float64 (numpy / scipy):
                    Kronecker stiffness (eq. "system_matrix"), the separable
                    variable-coefficient stiffness, dense assembly for tiny
                    grids, textbook PCG (Section 3) and spectral estimates.
+* ``general``   -- the stiffness of -div(C grad u) with a general symmetric
+                   coefficient C(x) sampled at the tensor Gauss points (Section
+                   2's Galerkin form; a geometry map of Section 7 pulled back to
+                   the parameter domain has this form), by the plain
+                   sum over derivative directions of G_k^T diag(w C_kl) G_l.
 
 Pins (what fixes each function independently of itself) live in
 ``tests/test_oracle_*.py``. Every oracle function is pinned; the only values

@@ -3,8 +3,10 @@
     python -m paper_2512_20269_gb300.probe --op precond --d 3 --n 256 --p 4 --precision fp64
     python -m paper_2512_20269_gb300.probe --op stiffness --n 256 --p 4
     python -m paper_2512_20269_gb300.probe --op solve --n 64 --p 4 --autotune
+    python -m paper_2512_20269_gb300.probe --op precond --n 256 --p 4 --warp
 
-Builds the plan (optionally autotuned), draws the N(0,1) right-hand side of
+Builds the plan (optionally autotuned, or with the warp-FFT transform pass
+on every eligible direction), draws the N(0,1) right-hand side of
 seed 1 on the host, and runs the operation once on cuda:0 through the C ABI.
 Prints the plan's launch geometry.
 """
@@ -24,6 +26,7 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--coef", choices=["const", "sin"], default="const")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--warp", action="store_true", help="warp-FFT pass on every eligible direction")
     a = ap.parse_args(argv)
 
     import torch
@@ -32,6 +35,13 @@ def main(argv=None) -> int:
     plan = IFFDPlan(a.d, a.n, a.p, precision=a.precision, coef=a.coef, true_residual=False)
     if a.autotune:
         plan.autotune()
+    if a.warp:
+        from . import IFFDError
+        for k in range(a.d):
+            try:
+                plan.set_geometry(k, warp=True)
+            except IFFDError:
+                pass  # not eligible: block kernel
     f = torch.from_numpy(inputs.rhs(plan.shape, "normal", 1)).cuda()
     if a.op == "precond":
         plan.apply_preconditioner(f)
