@@ -269,6 +269,45 @@ int iffd_apply_stiffness_noalloc(iffd_handle h, const double* u, double* Au, voi
  * iterate), or an argument / CUDA error. */
 int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* stream, iffd_pcg_info* info);
 
+/* ---- General coefficient (stiffness of -div(C(x) grad u), A != A^) ----
+ * Section 2's Galerkin form with a symmetric coefficient C(x) under the
+ * integral, A_ij = int grad B_i . C grad B_j dx, integrated with the tensor
+ * (p+1)-point Gauss rule of every element. A geometry map F of Section 7,
+ * pulled back to the parameter domain, has this form with C = det(DF) DF^-1
+ * DF^-T. The preconditioner stays the plan's IFFD (that of A^). */
+
+/* Gauss points and weights of direction `axis` on [0, 1]: *nq = n (p + 1)
+ * (element e owns points e (p+1) .. e (p+1) + p, increasing). x and w are
+ * caller-owned host arrays of *nq entries, or NULL. Host only. Errors:
+ * INVALID_ARG. */
+int iffd_quad_points(iffd_handle h, int axis, int* nq, double* x, double* w);
+
+/* Bytes of the scratch workspace of the general-coefficient operator (two
+ * arrays of nq_0 m_1 m_2 doubles, three of nq_0 nq_1 m_2 (3D) and d of
+ * nq_0 nq_1 nq_2: about d (p+1)^d times the DoF count in doubles). Errors:
+ * INVALID_ARG. */
+int iffd_general_workspace_bytes(iffd_handle h, size_t* bytes);
+
+/* Au = A_C u on the device. C: device array of ncomp * nq_0 nq_1 (nq_2)
+ * doubles at the tensor Gauss points (nq_k from iffd_quad_points, direction 0
+ * fastest), component by component: ncomp = 1 is a scalar a(x) (C = a I);
+ * ncomp = d (d + 1) / 2 is the upper triangle of the symmetric C row by row,
+ * (C11, C12, C22) in 2D and (C11, C12, C13, C22, C23, C33) in 3D. u, Au:
+ * device arrays of the plan's shape; they may not alias. gws: device scratch
+ * of iffd_general_workspace_bytes, 256-byte aligned, caller-owned. Stream-
+ * ordered, asynchronous. Errors: INVALID_ARG (NULL, aliasing, ncomp),
+ * WORKSPACE, CUDA. */
+int iffd_apply_stiffness_general(iffd_handle h, const double* C, int ncomp, const double* u, double* Au, void* gws,
+                                 void* stream);
+
+/* PCG on A_C u = f (zero start) with the plan's preconditioner, the loop of
+ * iffd_pcg_solve (same options, stopping rule, info and return values) with
+ * A_C in place of A^. ws: the plan's workspace; gws: as above. Where the
+ * eigenvalues of C lie in [c_lo, c_hi], c_lo A^ <= A_C <= c_hi A^, so the
+ * condition number is at most c_hi / c_lo times that with A^. */
+int iffd_pcg_solve_general(iffd_handle h, const double* C, int ncomp, const double* f, double* u, void* ws, void* gws,
+                           void* stream, iffd_pcg_info* info);
+
 /* Kernel kinds reported by the profiler (iffd_profile_read). */
 typedef enum {
   IFFD_K_PRECOND_FWD = 0,    /* IFFD pass Q~^T along one direction */
@@ -282,7 +321,8 @@ typedef enum {
   IFFD_K_FINALIZE = 8,       /* fixed-order reduction of partial sums + scalar updates */
   IFFD_K_FD_PASS = 9,        /* exact FD dense contraction pass */
   IFFD_K_VECTOR = 10,        /* copies, plain dot products, residual norm */
-  IFFD_K_KINDS = 11
+  IFFD_K_GENERAL = 11,       /* general-coefficient stiffness: sweeps, Gauss-point step, p-update */
+  IFFD_K_KINDS = 12
 } iffd_kernel_kind;
 
 /* Per-kernel device timing of this plan's launches by CUDA events recorded on

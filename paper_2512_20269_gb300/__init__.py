@@ -210,8 +210,69 @@ class IFFDPlan:
               "iffd_apply_stiffness_noalloc")
         return Au
 
+    # -- general coefficient: stiffness of -div(C grad u) at the Gauss points
+    def quad_points(self, axis: int):
+        """Gauss points and weights of one direction on [0, 1] (iffd_quad_points)."""
+        nq = ctypes.c_int()
+        check(self._lib.iffd_quad_points(self._h, axis, ctypes.byref(nq), None, None), "iffd_quad_points")
+        x = np.empty(nq.value)
+        w = np.empty(nq.value)
+        check(self._lib.iffd_quad_points(self._h, axis, None, x.ctypes.data_as(_lib.c_double_p),
+                                         w.ctypes.data_as(_lib.c_double_p)), "iffd_quad_points")
+        return x, w
+
+    @property
+    def quad_shape(self):
+        """Shape of one coefficient component: (nq_{d-1}, ..., nq_0), x fastest."""
+        return tuple(self.quad_points(a)[0].size for a in reversed(range(self.d)))
+
+    def _gws(self):
+        import torch
+        if getattr(self, "_gws_buf", None) is None:
+            nb = ctypes.c_size_t()
+            check(self._lib.iffd_general_workspace_bytes(self._h, ctypes.byref(nb)), "iffd_general_workspace_bytes")
+            self._gws_buf = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        return (_ptr(self._gws_buf) + 255) // 256 * 256
+
+    def _check_coef(self, C):
+        import torch
+        if not (C.is_cuda and C.dtype == torch.float64 and C.is_contiguous()):
+            raise ValueError("C must be a contiguous float64 CUDA tensor")
+        ncomp = C.numel() // int(np.prod(self.quad_shape))
+        if ncomp * int(np.prod(self.quad_shape)) != C.numel():
+            raise ValueError(f"C must hold ncomp x {self.quad_shape} values")
+        return ncomp
+
+    def iffd_apply_stiffness_general(self, C, u, Au=None, stream=None):
+        """Au = A_C u; C of shape (ncomp,) + quad_shape, ncomp 1 (scalar) or
+        d (d + 1) / 2 (upper triangle of the symmetric tensor, row by row)."""
+        Au = self.empty() if Au is None else Au
+        self._check_vec(u, "u")
+        self._check_vec(Au, "Au")
+        ncomp = self._check_coef(C)
+        check(self._lib.iffd_apply_stiffness_general(self._h, _ptr(C), ncomp, _ptr(u), _ptr(Au), self._gws(),
+                                                     _stream_handle(stream)), "iffd_apply_stiffness_general")
+        return Au
+
+    def iffd_pcg_solve_general(self, C, f, u=None, stream=None, raise_on_error: bool = True):
+        """PCG on A_C u = f with the plan's IFFD preconditioner."""
+        u = self.empty() if u is None else u
+        self._check_vec(f, "f")
+        self._check_vec(u, "u")
+        ncomp = self._check_coef(C)
+        info = iffd_pcg_info()
+        rc = self._lib.iffd_pcg_solve_general(self._h, _ptr(C), ncomp, _ptr(f), _ptr(u), self._ws_ptr, self._gws(),
+                                              _stream_handle(stream), ctypes.byref(info))
+        if raise_on_error:
+            check(rc, "iffd_pcg_solve_general")
+        return u, {"iters": info.iters, "rel_res": info.rel_res, "true_rel_res": info.true_rel_res,
+                   "status": info.status}
+
+    apply_stiffness_general = iffd_apply_stiffness_general
+    pcg_solve_general = iffd_pcg_solve_general
+
     # -- profiling (CUDA events around every launch of this plan)
-    KERNEL_KINDS = 11
+    KERNEL_KINDS = 12
 
     def autotune(self, stream=None):
         """Tune tiles and radix sequences on this GPU (iffd_autotune; uses the

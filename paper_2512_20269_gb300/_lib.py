@@ -68,6 +68,14 @@ SIGNATURES = [
                                                     ctypes.c_void_p]),
     ("iffd_pcg_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.POINTER(iffd_pcg_info)]),
+    ("iffd_quad_points", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_double_p, c_double_p]),
+    ("iffd_general_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, c_size_t_p]),
+    ("iffd_apply_stiffness_general", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p]),
+    ("iffd_pcg_solve_general", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.POINTER(iffd_pcg_info)]),
     ("iffd_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("iffd_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("iffd_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),

@@ -917,10 +917,12 @@ int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const if
     if (e != cudaSuccess) rc = cuda_fail(e, "eigenvalue reciprocals");
     else P->axd[d - 1].rden = P->rden;
   }
+  if (rc == IFFD_OK) rc = build_general_tables(P, stream);
   if (rc != IFFD_OK) {
     const std::string msg = g_err;
     if (P->dev) cudaFree(P->dev);
     if (P->rden) cudaFree(P->rden);
+    if (P->gen_mem) cudaFree(P->gen_mem);
     if (P->host_state) cudaFreeHost(P->host_state);
     delete h;
     g_err = msg;
@@ -936,6 +938,7 @@ void plan_release(iffd_plan* h) {
   P->prof.release();
   if (P->dev) cudaFree(P->dev);
   if (P->rden) cudaFree(P->rden);
+  if (P->gen_mem) cudaFree(P->gen_mem);
   if (P->host_state) cudaFreeHost(P->host_state);
   delete h;
 }
@@ -1157,9 +1160,128 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   return IFFD_OK;
 }
 
+// ------------------------------------------ general-coefficient stiffness
+int iffd_quad_points(iffd_handle h, int axis, int* nq, double* x, double* w) {
+  g_err.clear();
+  if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
+  QuadAxis Q;
+  build_quad_axis(h->P.host[axis], &Q);
+  if (nq) *nq = Q.nq;
+  if (x) std::memcpy(x, Q.x.data(), Q.x.size() * sizeof(double));
+  if (w) std::memcpy(w, Q.w.data(), Q.w.size() * sizeof(double));
+  return IFFD_OK;
+}
+
+int iffd_general_workspace_bytes(iffd_handle h, size_t* bytes) {
+  g_err.clear();
+  if (!h || !bytes) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  *bytes = general_ws_bytes(&h->P);
+  return IFFD_OK;
+}
+
+static int check_general(const Plan* P, const double* C, int ncomp, const void* gws) {
+  if (!C) return fail(IFFD_ERR_INVALID_ARG, "coefficient is NULL");
+  if (ncomp != 1 && ncomp != P->d * (P->d + 1) / 2)
+    return fail(IFFD_ERR_INVALID_ARG, "ncomp must be 1 or d (d + 1) / 2");
+  if (!gws) return fail(IFFD_ERR_WORKSPACE, "general workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(gws) % 256 != 0) return fail(IFFD_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  return check_device(P);
+}
+
+int iffd_apply_stiffness_general(iffd_handle h, const double* C, int ncomp, const double* u, double* Au, void* gws,
+                                 void* stream) {
+  g_err.clear();
+  if (!h || !u || !Au) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (u == Au) return fail(IFFD_ERR_INVALID_ARG, "u and Au must not alias");
+  int rc = check_general(&h->P, C, ncomp, gws);
+  if (rc) return rc;
+  return run_general(&h->P, C, ncomp, u, Au, gws, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+// PCG on A_C u = f with the plan's preconditioner (the IFFD preconditioner of
+// the constant-coefficient operator): the loop of iffd_pcg_solve with the
+// general operator in place of the stiffness sweeps.
+int iffd_pcg_solve_general(iffd_handle h, const double* C, int ncomp, const double* f, double* u, void* ws, void* gws,
+                           void* stream, iffd_pcg_info* info) {
+  g_err.clear();
+  if (!h || !f || !u) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  if (f == u) return fail(IFFD_ERR_INVALID_ARG, "f and u must not alias");
+  Plan* P = &h->P;
+  int rc = check_ws(P, ws);
+  if (rc) return rc;
+  rc = check_general(P, C, ncomp, gws);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long N = P->dims.N;
+  double* r = reinterpret_cast<double*>(wsb(ws, P->off_r));
+  double* z = reinterpret_cast<double*>(wsb(ws, P->off_z));
+  double* p = reinterpret_cast<double*>(wsb(ws, P->off_p));
+  double* q = reinterpret_cast<double*>(wsb(ws, P->off_q));
+  double* part = reinterpret_cast<double*>(wsb(ws, P->off_part));
+  SolveState* S = reinterpret_cast<SolveState*>(wsb(ws, P->off_state));
+  const int* done = &S->done;
+  const double tol2 = P->opt.rtol * P->opt.rtol;
+  const int maxit = P->opt.maxit;
+  const bool flex = P->opt.flexible || P->opt.precision == IFFD_PREC_FP32_TRANSFORM;
+  const int g = vec_grid(N);
+  int np = 0;
+
+  IFFD_CUDA(cudaMemsetAsync(S, 0, sizeof(SolveState), st));
+  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st));
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, g, FP_FF, tol2, maxit, st));
+  rc = run_precond(P, r, z, ws, st, done, 1, r, nullptr, part, &np);
+  if (rc) return rc;
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_RZ0, tol2, maxit, st));
+  int it = 0;
+  const int chunk = 4;
+  bool finished = false;
+  while (!finished) {
+    for (int c = 0; c < chunk && it < maxit; ++c, ++it) {
+      IFFD_LAUNCH(P, IFFD_K_GENERAL, st, launch_gen_pupdate(z, p, S, it == 0 ? 1 : 2, N, done, st));
+      rc = run_general(P, C, ncomp, p, q, gws, st, done);
+      if (rc) return rc;
+      P->prof.begin(IFFD_K_VECTOR, st);
+      dot_kernel<<<g, kThreads, 0, st>>>(p, q, N, part, done);
+      IFFD_CUDA(cudaGetLastError());
+      P->prof.end(st);
+      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, g, FP_PQ, tol2, maxit, st));
+      IFFD_LAUNCH(P, IFFD_K_PCG_UPDATE, st, launch_pcg_update(u, r, p, q, S, N, part, done, st));
+      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, g, FP_RR, tol2, maxit, st));
+      rc = run_precond(P, r, z, ws, st, done, flex ? 2 : 1, r, q, part, &np);
+      if (rc) return rc;
+      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, flex ? FP_RZ_FLEX : FP_RZ, tol2, maxit, st));
+    }
+    IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    IFFD_CUDA(cudaStreamSynchronize(st));
+    finished = P->host_state->done || it >= maxit;
+  }
+  SolveState hs = *P->host_state;
+  double true_rel = -1.0;
+  if (P->opt.true_residual && hs.ff > 0.0) {
+    rc = run_general(P, C, ncomp, u, q, gws, st, nullptr);
+    if (rc) return rc;
+    IFFD_LAUNCH(P, IFFD_K_VECTOR, st, launch_residual(f, q, N, part, st));
+    IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, g, FP_TRUE, tol2, maxit, st));
+    IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    IFFD_CUDA(cudaStreamSynchronize(st));
+    true_rel = std::sqrt(P->host_state->zq / hs.ff);
+  }
+  int status = hs.status;
+  if (!hs.done) status = IFFD_ERR_NOT_CONVERGED;
+  if (info) {
+    info->iters = hs.iters;
+    info->rel_res = hs.ff > 0 ? std::sqrt(hs.rr / hs.ff) : 0.0;
+    info->true_rel_res = true_rel;
+    info->status = status;
+  }
+  if (status == IFFD_ERR_NOT_CONVERGED) return fail(status, "PCG did not reach rtol within maxit");
+  if (status == IFFD_ERR_BREAKDOWN) return fail(status, "PCG breakdown (non-positive curvature or NaN)");
+  return IFFD_OK;
+}
+
 static const char* kKindNames[IFFD_K_KINDS] = {
     "precond_fwd", "precond_fused", "precond_bwd", "stiff_first", "stiff_mid", "stiff_last",
-    "pcg_update", "pcg_init", "finalize", "fd_pass", "vector"};
+    "pcg_update", "pcg_init", "finalize", "fd_pass", "vector", "general"};
 
 int iffd_profile_enable(iffd_handle h, int enable) {
   if (!h) return fail(IFFD_ERR_INVALID_ARG, "NULL handle");

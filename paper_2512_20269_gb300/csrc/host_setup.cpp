@@ -921,6 +921,55 @@ void expand_vreg(const Axis1D& A, double* V) {
   }
 }
 
+void build_quad_axis(const Axis1D& A, QuadAxis* Q) {
+  const int n = A.n, p = A.p, m = A.m, s0 = A.dir0 ? 1 : 0;
+  const std::vector<double> kn = open_knots(n, p, A.reps);
+  std::vector<double> gx, gw, B(p + 1), dB(p + 1);
+  gauss_legendre(p + 1, &gx, &gw);
+  std::vector<int> ord(p + 1);  // nodes in increasing order
+  for (int g = 0; g <= p; ++g) ord[g] = g;
+  std::sort(ord.begin(), ord.end(), [&](int i, int j) { return gx[i] < gx[j]; });
+  Q->nq = n * (p + 1);
+  Q->m = m;
+  Q->x.clear(); Q->w.clear(); Q->col.clear(); Q->bv.clear(); Q->dv.clear();
+  Q->rp.assign(1, 0);
+  for (int e = 0; e < n; ++e) {
+    const double a = double(e) / n, b = double(e + 1) / n;
+    const int sp = element_span(kn, n, e);
+    for (int gi = 0; gi <= p; ++gi) {
+      const int g = ord[gi];
+      const double x = 0.5 * (b - a) * gx[g] + 0.5 * (a + b);
+      Q->x.push_back(x);
+      Q->w.push_back(0.5 * (b - a) * gw[g]);
+      bspline_local(kn, p, sp, x, 0, B.data());
+      bspline_local(kn, p, sp, x, 1, dB.data());
+      for (int t = 0; t <= p; ++t) {
+        const int j = sp - p + t - s0;  // index among the kept functions
+        if (j < 0 || j >= m) continue;
+        Q->col.push_back(j);
+        Q->bv.push_back(B[t]);
+        Q->dv.push_back(dB[t]);
+      }
+      Q->rp.push_back((int)Q->col.size());
+    }
+  }
+  // transpose (counting sort by column; points stay increasing within a row)
+  Q->trp.assign(m + 1, 0);
+  for (int c : Q->col) ++Q->trp[c + 1];
+  for (int j = 0; j < m; ++j) Q->trp[j + 1] += Q->trp[j];
+  Q->tcol.assign(Q->col.size(), 0);
+  Q->tbv.assign(Q->col.size(), 0.0);
+  Q->tdv.assign(Q->col.size(), 0.0);
+  std::vector<int> next(Q->trp.begin(), Q->trp.end() - 1);
+  for (int q = 0; q < Q->nq; ++q)
+    for (int k = Q->rp[q]; k < Q->rp[q + 1]; ++k) {
+      const int t = next[Q->col[k]]++;
+      Q->tcol[t] = q;
+      Q->tbv[t] = Q->bv[k];
+      Q->tdv[t] = Q->dv[k];
+    }
+}
+
 void build_weighted_bands(Axis1D* A) {
   assemble_bands(A->n, A->p, open_knots(A->n, A->p, A->reps), A->dir0, A->dir1, sin_2pi, &A->Msband, &A->Ksband);
 }

@@ -70,6 +70,22 @@ void build_weighted_bands(Axis1D* A);
 std::string build_axis(int n, int p, bool dir0, bool dir1, Axis1D* out,
                        const std::vector<std::pair<int, int>>& reps = {});
 
+// Values and first derivatives of the kept B-splines of one direction at its
+// n (p+1) Gauss points (the (p+1)-point rule of every element, element e
+// owning points e (p+1) .. e (p+1) + p), for the general-coefficient
+// stiffness: x, w (points and weights on [0, 1]); B and D as CSR matrices with
+// one pattern (rows = points, at most p+1 columns each, increasing), and their
+// transposes (rows = basis functions) with one pattern.
+struct QuadAxis {
+  int nq = 0, m = 0;
+  std::vector<double> x, w;
+  std::vector<int> rp, col;       // nq + 1 row pointers, column indices
+  std::vector<double> bv, dv;     // B and D values on that pattern
+  std::vector<int> trp, tcol;     // transpose: m + 1 row pointers, point indices
+  std::vector<double> tbv, tdv;   // B^T and D^T values
+};
+void build_quad_axis(const Axis1D& A, QuadAxis* Q);
+
 // Dense V_reg (m x n_reg, row-major) as the device passes apply it.
 void expand_vreg(const Axis1D& A, double* V);
 

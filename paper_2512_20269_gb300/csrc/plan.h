@@ -107,6 +107,14 @@ struct FftVar {
 };
 
 // Plan of one problem: host 1D data, device tables, launch geometry.
+// One direction of the general-coefficient stiffness: its Gauss-point
+// tables (QuadAxis) on the device.
+struct GenAxis {
+  int nq = 0, m = 0;
+  const int *rp = nullptr, *col = nullptr, *trp = nullptr, *tcol = nullptr;
+  const double *bv = nullptr, *dv = nullptr, *tbv = nullptr, *tdv = nullptr, *w = nullptr;
+};
+
 struct Plan {
   mutable Profiler prof;
   int d = 0, p = 0;
@@ -138,6 +146,10 @@ struct Plan {
   // off by default, chosen by hand or by the tuner) and its FP64 twiddles
   int warp_d[3] = {0, 0, 0};
   const double2* wtab_d[3] = {nullptr, nullptr, nullptr};
+  // General-coefficient stiffness: per direction the Gauss-point tables (one
+  // device allocation, gen_mem)
+  GenAxis gen[3];
+  char* gen_mem = nullptr;
   bool tuned = false;
   // exact FD tables
   const double* QT[3] = {nullptr, nullptr, nullptr};
@@ -173,6 +185,15 @@ struct F32Geom {
   size_t smem;
 };
 F32Geom f32_geom(const Plan& P, int a);
+// General-coefficient stiffness (general.cu): device tables (at plan
+// creation), scratch bytes of one application, the application Au = A_C u
+// (C: ncomp arrays at the Gauss points), and the p-update of its PCG.
+int build_general_tables(Plan* P, cudaStream_t st);
+size_t general_ws_bytes(const Plan* P);
+int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au, void* gws, cudaStream_t st,
+                const int* done);
+cudaError_t launch_gen_pupdate(const double* z, double* p, const SolveState* S, int mode, long long N,
+                               const int* done, cudaStream_t st);
 // FFT length of direction a's FP64 warp-FFT pass (0: the block kernel runs).
 int f64_warp_len(const Plan& P, int a);
 StiffLaunch plan_stiff_launch(const Plan* P, int axis);
