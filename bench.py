@@ -517,6 +517,51 @@ def main():
                               "true_rel_res": ichk["true_rel_res"]}
             del pv, pchk
 
+    # ---------------- general coefficient (-div(a grad u), a non-separable) on a
+    # 130^3 grid, p = 4: the operator at the tensor Gauss points and PCG with the
+    # IFFD preconditioner of the constant-coefficient operator. Algorithmic
+    # bytes of one apply: u and Au (16 per DoF) and a at every Gauss point (8).
+    if not args.no_variants:
+        pg = IFFDPlan(w.d, 128, w.p, precision="fp64", true_residual=True)
+        xs = [torch.from_numpy(pg.quad_points(k)[0]).cuda() for k in range(w.d)]
+        if w.d == 3:
+            Zg, Yg, Xg = torch.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+        else:
+            Yg, Xg = torch.meshgrid(xs[1], xs[0], indexing="ij")
+            Zg = torch.zeros_like(Xg)
+        coef = (1.0 + 0.5 * torch.sin(2 * math.pi * (Xg + 2 * Yg + 3 * Zg)) * torch.cos(math.pi * Xg * Yg))
+        coef = coef[None].contiguous()
+        del Xg, Yg, Zg
+        fg = torch.from_numpy(inputs.rhs(pg.shape, "uniform", seed=3)).cuda()
+        ug = pg.empty()
+        for _ in range(2):
+            pg.apply_stiffness_general(coef, fg, ug)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            pg.apply_stiffness_general(coef, fg, ug)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gms = a.elapsed_time(b) / 5
+        pg.pcg_solve_general(coef, fg, ug)
+        torch.cuda.synchronize()
+        a.record(stream)
+        _, ig = pg.pcg_solve_general(coef, fg, ug)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sms = a.elapsed_time(b)
+        gbytes = 16.0 * pg.N + 8.0 * coef.numel()
+        variants["general_coef"] = {
+            "config": {"workload": f"cube n=128 p={w.p}, a = 1 + sin(2 pi (x + 2y + 3z)) cos(pi x y) / 2",
+                       "dofs": pg.N, "gauss_points": int(coef.numel())},
+            "apply_ms": gms, "apply_alg_bytes": gbytes, "apply_hbm_frac": gbytes / (gms / 1e3) / 1e9 / hbm_peak,
+            "ms_per_solve": sms, "value": pg.N / (sms / 1e3), "unit": UNIT, "iters": ig["iters"],
+            "true_rel_res": ig["true_rel_res"]}
+        del pg, coef, fg, ug, xs
+        torch.cuda.empty_cache()
+
     # ---------------- preconditioner applies per second (inputs resident)
     # algorithmic bytes per DoF of one apply: FP64, 16 per pass and 24 for the
     # fused pass (it also reads 1/sum(lambda)); FP32 transforms, 12 for the

@@ -1185,6 +1185,8 @@ static int check_general(const Plan* P, const double* C, int ncomp, const void* 
     return fail(IFFD_ERR_INVALID_ARG, "ncomp must be 1 or d (d + 1) / 2");
   if (!gws) return fail(IFFD_ERR_WORKSPACE, "general workspace is NULL");
   if (reinterpret_cast<uintptr_t>(gws) % 256 != 0) return fail(IFFD_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  const long long rows = (long long)P->gen[1].nq * (P->d == 3 ? P->gen[2].nq : 1);
+  if (rows >= (1LL << 31)) return fail(IFFD_ERR_UNSUPPORTED, "Gauss grid too large");
   return check_device(P);
 }
 

@@ -9,9 +9,9 @@
 // d-dimensional array with x fastest.
 //
 // 3D forward: U_B = B_x u, U_D = D_x u; V_BB = B_y U_B, V_BD = D_y U_B,
-// V_DB = B_y U_D; g_x = B_z V_DB, g_y = B_z V_BD, g_z = D_z V_BB. Pointwise
-// h = w C g. Backward with the transposes in the reverse order, the two
-// contributions of each sweep summed in one pass.
+// V_DB = B_y U_D; then g = (B_z V_DB, B_z V_BD, D_z V_BB) and h = w C g in
+// one pass over the Gauss grid. Backward with the transposes in the reverse
+// order, the two contributions of each sweep summed in one pass.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -28,83 +28,152 @@ namespace {
 // GS_TWO_IN: out = A in + A2 in2.
 enum GenSweep : int { GS_ONE = 0, GS_TWO_OUT = 1, GS_TWO_IN = 2 };
 
+// Launch shape of the sweeps and the pointwise step: threads along x (the
+// fastest index, coalesced), one (y, z) row of the output per block row, so
+// that the row's offsets are computed once per block and not per element.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 gen_sweep(const double* __restrict__ in, const double* __restrict__ in2, double* __restrict__ out,
-          double* __restrict__ out2, long long o0, long long o1, long long o2, int in_len, int axis,
-          const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-          const double* __restrict__ val2, const int* __restrict__ done) {
+          double* __restrict__ out2, int o0, int o1, int o2, int in_len, int axis, const int* __restrict__ rp,
+          const int* __restrict__ col, const double* __restrict__ val, const double* __restrict__ val2,
+          const int* __restrict__ done) {
   if (done != nullptr && *((volatile const int*)done)) return;
-  const long long total = o0 * o1 * o2;
   const long long n0 = axis == 0 ? in_len : o0, n1 = axis == 1 ? in_len : o1;
   const long long s_ax = axis == 0 ? 1 : (axis == 1 ? n0 : n0 * n1);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = t % o0, r = t / o0;
-    const long long i1 = r % o1, i2 = r / o1;
-    const long long base = (axis == 0 ? 0 : i0) + (axis == 1 ? 0 : i1 * n0) + (axis == 2 ? 0 : i2 * n0 * n1);
-    const int row = (int)(axis == 0 ? i0 : (axis == 1 ? i1 : i2));
-    double s = 0.0, s2 = 0.0;
-    const int k1 = __ldg(rp + row + 1);
-    for (int k = __ldg(rp + row); k < k1; ++k) {
-      const long long at = base + (long long)__ldg(col + k) * s_ax;
-      const double v = in[at];
-      s = fma(__ldg(val + k), v, s);
-      if (MODE == GS_TWO_OUT) s2 = fma(__ldg(val2 + k), v, s2);
-      if (MODE == GS_TWO_IN) s = fma(__ldg(val2 + k), in2[at], s);
+  const int rows = o1 * o2;
+  for (int rr = blockIdx.y; rr < rows; rr += gridDim.y) {
+    const int i1 = rr % o1, i2 = rr / o1;
+    const long long rbase = (axis == 1 ? 0 : (long long)i1 * n0) + (axis == 2 ? 0 : (long long)i2 * n0 * n1);
+    double* orow = out + (long long)rr * o0;
+    double* orow2 = (MODE == GS_TWO_OUT) ? out2 + (long long)rr * o0 : nullptr;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < o0; i0 += gridDim.x * blockDim.x) {
+      const long long base = rbase + (axis == 0 ? 0 : i0);
+      const int row = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+      double s = 0.0, s2 = 0.0;
+      const int k1 = __ldg(rp + row + 1);
+      int k = __ldg(rp + row);
+      // four entries per step: their loads are issued before the first FMA
+      // waits, so a row costs about one memory latency per four entries
+      for (; k + 4 <= k1; k += 4) {
+        double v[4], v2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const long long at = base + (long long)__ldg(col + k + e) * s_ax;
+          v[e] = in[at];
+          if (MODE == GS_TWO_IN) v2[e] = in2[at];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          s = fma(__ldg(val + k + e), v[e], s);
+          if (MODE == GS_TWO_OUT) s2 = fma(__ldg(val2 + k + e), v[e], s2);
+          if (MODE == GS_TWO_IN) s = fma(__ldg(val2 + k + e), v2[e], s);
+        }
+      }
+      for (; k < k1; ++k) {
+        const long long at = base + (long long)__ldg(col + k) * s_ax;
+        const double v = in[at];
+        s = fma(__ldg(val + k), v, s);
+        if (MODE == GS_TWO_OUT) s2 = fma(__ldg(val2 + k), v, s2);
+        if (MODE == GS_TWO_IN) s = fma(__ldg(val2 + k), in2[at], s);
+      }
+      orow[i0] = s;
+      if (MODE == GS_TWO_OUT) orow2[i0] = s2;
     }
-    out[t] = s;
-    if (MODE == GS_TWO_OUT) out2[t] = s2;
   }
 }
 
-// h_k = w sum_l C_kl g_l at every Gauss point (in place); w = w_z (w_y w_x).
+// h = w C g at Gauss point t (C: ncomp components of `total` points each).
+template <int D>
+__device__ __forceinline__ void coef_apply(double* g, const double* __restrict__ C, int ncomp, long long total,
+                                           long long t, double w) {
+  if (ncomp == 1) {
+    const double c = __ldg(C + t);
+#pragma unroll
+    for (int k = 0; k < D; ++k) g[k] = w * (c * g[k]);
+    return;
+  }
+  if (D == 2) {
+    const double c11 = __ldg(C + t), c12 = __ldg(C + total + t), c22 = __ldg(C + 2 * total + t);
+    const double h0 = fma(c12, g[1], c11 * g[0]), h1 = fma(c22, g[1], c12 * g[0]);
+    g[0] = w * h0;
+    g[1] = w * h1;
+  } else {
+    const double c11 = __ldg(C + t), c12 = __ldg(C + total + t), c13 = __ldg(C + 2 * total + t);
+    const double c22 = __ldg(C + 3 * total + t), c23 = __ldg(C + 4 * total + t), c33 = __ldg(C + 5 * total + t);
+    const double h0 = fma(c13, g[2], fma(c12, g[1], c11 * g[0]));
+    const double h1 = fma(c23, g[2], fma(c22, g[1], c12 * g[0]));
+    const double h2 = fma(c33, g[2], fma(c23, g[1], c13 * g[0]));
+    g[0] = w * h0;
+    g[1] = w * h1;
+    g[2] = w * h2;
+  }
+}
+
+// The last forward sweep (along direction D-1) fused with the Gauss-point
+// step: the D partial derivatives of the point, then h = w C g, written once.
+// 3D: g_x = B_z in0, g_y = B_z in1, g_z = D_z in2; 2D: g_x = B_y in0,
+// g_y = D_y in1. Output (q0, q1[, q2]), x fastest; w = w_z (w_y w_x).
+template <int D>
 __global__ void __launch_bounds__(kThreads)
-gen_pointwise(double* __restrict__ g0, double* __restrict__ g1, double* __restrict__ g2,
-              const double* __restrict__ C, int ncomp, int d, long long q0, long long q1, long long q2,
-              const double* __restrict__ w0, const double* __restrict__ w1, const double* __restrict__ w2,
-              const int* __restrict__ done) {
+gen_last_fwd(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ in2,
+             double* __restrict__ h0, double* __restrict__ h1, double* __restrict__ h2, int q0, int q1, int q2,
+             const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ bv,
+             const double* __restrict__ dv, const double* __restrict__ C, int ncomp, const double* __restrict__ w0,
+             const double* __restrict__ w1, const double* __restrict__ w2, const int* __restrict__ done) {
   if (done != nullptr && *((volatile const int*)done)) return;
-  const long long total = q0 * q1 * q2;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = t % q0, r = t / q0;
-    const long long i1 = r % q1, i2 = r / q1;
-    double w = __ldg(w1 + i1) * __ldg(w0 + i0);
-    if (d == 3) w = __ldg(w2 + i2) * w;
-    const double a0 = g0[t], a1 = g1[t];
-    if (d == 2) {
-      double h0, h1;
-      if (ncomp == 1) {
-        const double c = __ldg(C + t);
-        h0 = c * a0;
-        h1 = c * a1;
-      } else {
-        const double c11 = __ldg(C + t), c12 = __ldg(C + total + t), c22 = __ldg(C + 2 * total + t);
-        h0 = fma(c12, a1, c11 * a0);
-        h1 = fma(c22, a1, c12 * a0);
+  const long long total = (long long)q0 * q1 * q2;
+  const long long s_ax = (D == 3) ? (long long)q0 * q1 : q0;  // stride of the last direction in the inputs
+  const int rows = q1 * q2;
+  for (int rr = blockIdx.y; rr < rows; rr += gridDim.y) {
+    const int i1 = rr % q1, i2 = rr / q1;
+    const int row = (D == 3) ? i2 : i1;  // Gauss point along the last direction
+    const long long rbase = (D == 3) ? (long long)i1 * q0 : 0;
+    const double wr = (D == 3) ? __ldg(w2 + i2) : 1.0, wy = __ldg(w1 + i1);
+    const int k0 = __ldg(rp + row), k1 = __ldg(rp + row + 1);
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < q0; i0 += gridDim.x * blockDim.x) {
+      const long long base = rbase + i0;
+      double g[3] = {0.0, 0.0, 0.0};
+      int k = k0;
+      for (; k + 2 <= k1; k += 2) {  // loads of two entries before their FMAs
+        double a[2][3];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const long long at = base + (long long)__ldg(col + k + e) * s_ax;
+          a[e][0] = in0[at];
+          a[e][1] = in1[at];
+          if (D == 3) a[e][2] = in2[at];
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const double b = __ldg(bv + k + e), dd = __ldg(dv + k + e);
+          g[0] = fma(b, a[e][0], g[0]);
+          if (D == 3) {
+            g[1] = fma(b, a[e][1], g[1]);
+            g[2] = fma(dd, a[e][2], g[2]);
+          } else {
+            g[1] = fma(dd, a[e][1], g[1]);
+          }
+        }
       }
-      g0[t] = w * h0;
-      g1[t] = w * h1;
-    } else {
-      const double a2 = g2[t];
-      double h0, h1, h2;
-      if (ncomp == 1) {
-        const double c = __ldg(C + t);
-        h0 = c * a0;
-        h1 = c * a1;
-        h2 = c * a2;
-      } else {
-        const double c11 = __ldg(C + t), c12 = __ldg(C + total + t), c13 = __ldg(C + 2 * total + t);
-        const double c22 = __ldg(C + 3 * total + t), c23 = __ldg(C + 4 * total + t);
-        const double c33 = __ldg(C + 5 * total + t);
-        h0 = fma(c13, a2, fma(c12, a1, c11 * a0));
-        h1 = fma(c23, a2, fma(c22, a1, c12 * a0));
-        h2 = fma(c33, a2, fma(c23, a1, c13 * a0));
+      for (; k < k1; ++k) {
+        const long long at = base + (long long)__ldg(col + k) * s_ax;
+        const double b = __ldg(bv + k), dd = __ldg(dv + k);
+        if (D == 3) {
+          g[0] = fma(b, in0[at], g[0]);
+          g[1] = fma(b, in1[at], g[1]);
+          g[2] = fma(dd, in2[at], g[2]);
+        } else {
+          g[0] = fma(b, in0[at], g[0]);
+          g[1] = fma(dd, in1[at], g[1]);
+        }
       }
-      g0[t] = w * h0;
-      g1[t] = w * h1;
-      g2[t] = w * h2;
+      double w = wy * __ldg(w0 + i0);
+      if (D == 3) w = wr * w;
+      const long long t = (long long)rr * q0 + i0;
+      coef_apply<D>(g, C, ncomp, total, t, w);
+      h0[t] = g[0];
+      h1[t] = g[1];
+      if (D == 3) h2[t] = g[2];
     }
   }
 }
@@ -119,9 +188,16 @@ gen_pupdate(const double* __restrict__ z, double* __restrict__ p, const SolveSta
     p[i] = (mode == 2) ? fma(beta, p[i], z[i]) : z[i];
 }
 
-int grid_for(long long total) {
-  const long long g = (total + kThreads - 1) / kThreads;
-  return (int)std::max(1LL, std::min(g, 152LL * 16));
+// Block of up to 256 threads along x (128 for short rows) and a grid of
+// (x blocks, rows), the rows capped at the grid's y limit (grid-stride loop).
+struct Shape2 {
+  dim3 grid, block;
+};
+Shape2 shape_for(long long o0, long long rows) {
+  const int tb = o0 > 128 ? kThreads : 128;
+  const unsigned gx = (unsigned)((o0 + tb - 1) / tb);
+  const unsigned gy = (unsigned)std::min<long long>(rows, 65535);
+  return {dim3(gx, gy), dim3(tb)};
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -209,15 +285,17 @@ int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au
   auto sweep = [&](int mode, const double* in, const double* in2, double* out, double* out2, long long o0,
                    long long o1, long long o2, int in_len, int axis, const int* rp, const int* col, const double* v,
                    const double* v2) -> cudaError_t {
-    const int g = grid_for(o0 * o1 * o2);
+    const Shape2 sh = shape_for(o0, o1 * o2);
+    const int a0 = (int)o0, a1 = (int)o1, a2 = (int)o2;
     if (mode == GS_ONE)
-      gen_sweep<GS_ONE><<<g, kThreads, 0, st>>>(in, in2, out, out2, o0, o1, o2, in_len, axis, rp, col, v, v2, done);
+      gen_sweep<GS_ONE><<<sh.grid, sh.block, 0, st>>>(in, in2, out, out2, a0, a1, a2, in_len, axis, rp, col, v, v2,
+                                                      done);
     else if (mode == GS_TWO_OUT)
-      gen_sweep<GS_TWO_OUT><<<g, kThreads, 0, st>>>(in, in2, out, out2, o0, o1, o2, in_len, axis, rp, col, v, v2,
-                                                     done);
+      gen_sweep<GS_TWO_OUT><<<sh.grid, sh.block, 0, st>>>(in, in2, out, out2, a0, a1, a2, in_len, axis, rp, col, v,
+                                                          v2, done);
     else
-      gen_sweep<GS_TWO_IN><<<g, kThreads, 0, st>>>(in, in2, out, out2, o0, o1, o2, in_len, axis, rp, col, v, v2,
-                                                    done);
+      gen_sweep<GS_TWO_IN><<<sh.grid, sh.block, 0, st>>>(in, in2, out, out2, a0, a1, a2, in_len, axis, rp, col, v,
+                                                         v2, done);
     return cudaGetLastError();
   };
   const GenAxis &X = G[0], &Y = G[1];
@@ -225,17 +303,14 @@ int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au
   IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_OUT, u, nullptr, U[0], U[1], q0, m1, m2, (int)m0, 0, X.rp, X.col,
                                            X.bv, X.dv));
   if (d == 2) {
-    // g_x = B_y U_D, g_y = D_y U_B
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, U[1], nullptr, H[0], nullptr, q0, q1, 1, (int)m1, 1, Y.rp,
-                                             Y.col, Y.bv, nullptr));
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, U[0], nullptr, H[1], nullptr, q0, q1, 1, (int)m1, 1, Y.rp,
-                                             Y.col, Y.dv, nullptr));
-    auto pointwise2 = [&] {
-      gen_pointwise<<<grid_for(q0 * q1), kThreads, 0, st>>>(H[0], H[1], nullptr, C, ncomp, 2, q0, q1, 1, X.w, Y.w,
-                                                            nullptr, done);
+    // h = w C (B_y U_D, D_y U_B) at every Gauss point
+    auto last2 = [&] {
+      const Shape2 sh = shape_for(q0, q1);
+      gen_last_fwd<2><<<sh.grid, sh.block, 0, st>>>(U[1], U[0], nullptr, H[0], H[1], nullptr, (int)q0, (int)q1, 1,
+                                                    Y.rp, Y.col, Y.bv, Y.dv, C, ncomp, X.w, Y.w, nullptr, done);
       return cudaGetLastError();
     };
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, pointwise2());
+    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, last2());
     // X_D = B_y^T h_x, X_B = D_y^T h_y; Au = D_x^T X_D + B_x^T X_B
     IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[0], nullptr, U[1], nullptr, q0, m1, 1, (int)q1, 1, Y.trp,
                                              Y.tcol, Y.tbv, nullptr));
@@ -251,19 +326,14 @@ int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au
                                            Y.col, Y.bv, Y.dv));
   IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, U[1], nullptr, V[2], nullptr, q0, q1, m2, (int)m1, 1, Y.rp,
                                            Y.col, Y.bv, nullptr));
-  // g_x = B_z V_DB, g_y = B_z V_BD, g_z = D_z V_BB
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, V[2], nullptr, H[0], nullptr, q0, q1, q2, (int)m2, 2, Z.rp, Z.col,
-                                           Z.bv, nullptr));
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, V[1], nullptr, H[1], nullptr, q0, q1, q2, (int)m2, 2, Z.rp, Z.col,
-                                           Z.bv, nullptr));
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, V[0], nullptr, H[2], nullptr, q0, q1, q2, (int)m2, 2, Z.rp, Z.col,
-                                           Z.dv, nullptr));
-  auto pointwise3 = [&] {
-    gen_pointwise<<<grid_for(q0 * q1 * q2), kThreads, 0, st>>>(H[0], H[1], H[2], C, ncomp, 3, q0, q1, q2, X.w, Y.w,
-                                                               Z.w, done);
+  // h = w C (B_z V_DB, B_z V_BD, D_z V_BB) at every Gauss point
+  auto last3 = [&] {
+    const Shape2 sh = shape_for(q0, q1 * q2);
+    gen_last_fwd<3><<<sh.grid, sh.block, 0, st>>>(V[2], V[1], V[0], H[0], H[1], H[2], (int)q0, (int)q1, (int)q2,
+                                                  Z.rp, Z.col, Z.bv, Z.dv, C, ncomp, X.w, Y.w, Z.w, done);
     return cudaGetLastError();
   };
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, pointwise3());
+  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, last3());
   // W_DB = B_z^T h_x -> V[2], W_BD = B_z^T h_y -> V[1], W_BB = D_z^T h_z -> V[0]
   IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[0], nullptr, V[2], nullptr, q0, q1, m2, (int)q2, 2, Z.trp,
                                            Z.tcol, Z.tbv, nullptr));
