@@ -519,8 +519,15 @@ def main():
 
     # ---------------- general coefficient (-div(a grad u), a non-separable) on a
     # 130^3 grid, p = 4: the operator at the tensor Gauss points and PCG with the
-    # IFFD preconditioner of the constant-coefficient operator. Algorithmic
-    # bytes of one apply: u and Au (16 per DoF) and a at every Gauss point (8).
+    # IFFD preconditioner of the constant-coefficient operator. The application
+    # is bound by the FP64 pipe: its sum-factorised sweeps cost, per output
+    # value, 2 flops per matrix entry (an FMA), i.e. (3D, p1 = p + 1 entries per
+    # Gauss point row, q / m = n p1 / m entries per basis-function row)
+    #   x: 2 x q0 m1 m2 outputs x p1;  y: 3 x q0 q1 m2 x p1;
+    #   z (fused): per Gauss point 3 p1 (gradient) + 3 p1 (transpose) FMAs and
+    #     7 multiplies for w a g;
+    #   y^T: 3 x q0 m1 m2 x q1 p1 / m1;  x^T: 2 x m0 m1 m2 x q0 p1 / m0.
+    # Algorithmic bytes: u and Au (16 per DoF) and a at every Gauss point (8).
     if not args.no_variants:
         pg = IFFDPlan(w.d, 128, w.p, precision="fp64", true_residual=True)
         xs = [torch.from_numpy(pg.quad_points(k)[0]).cuda() for k in range(w.d)]
@@ -553,10 +560,23 @@ def main():
         torch.cuda.synchronize()
         sms = a.elapsed_time(b)
         gbytes = 16.0 * pg.N + 8.0 * coef.numel()
+        p1 = w.p + 1
+        qd = [pg.quad_points(k)[0].size for k in range(w.d)]
+        md = list(pg.m)
+        if w.d == 3:
+            q0, q1, q2 = qd
+            m0, m1, m2 = md
+            gflop = (2 * (2 * q0 * m1 * m2 * p1 + 3 * q0 * q1 * m2 * p1 + 3 * q0 * m1 * m2 * q1 * p1 / m1
+                          + 2 * m0 * m1 * m2 * q0 * p1 / m0) + q0 * q1 * q2 * (12 * p1 + 7)) / 1e9
+        else:
+            q0, q1 = qd
+            m0, m1 = md
+            gflop = (2 * (2 * q0 * m1 * p1 + 2 * m0 * m1 * q0 * p1 / m0) + q0 * q1 * (8 * p1 + 5)) / 1e9
         variants["general_coef"] = {
             "config": {"workload": f"cube n=128 p={w.p}, a = 1 + sin(2 pi (x + 2y + 3z)) cos(pi x y) / 2",
                        "dofs": pg.N, "gauss_points": int(coef.numel())},
             "apply_ms": gms, "apply_alg_bytes": gbytes, "apply_hbm_frac": gbytes / (gms / 1e3) / 1e9 / hbm_peak,
+            "apply_gflop": gflop, "apply_fp64_tflops": gflop / gms, "apply_fp64_frac": gflop / gms / FP64_PEAK_TFLOPS,
             "ms_per_solve": sms, "value": pg.N / (sms / 1e3), "unit": UNIT, "iters": ig["iters"],
             "true_rel_res": ig["true_rel_res"]}
         del pg, coef, fg, ug, xs

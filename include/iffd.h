@@ -282,10 +282,10 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
  * INVALID_ARG. */
 int iffd_quad_points(iffd_handle h, int axis, int* nq, double* x, double* w);
 
-/* Bytes of the scratch workspace of the general-coefficient operator (two
- * arrays of nq_0 m_1 m_2 doubles, three of nq_0 nq_1 m_2 (3D) and d of
- * nq_0 nq_1 nq_2: about d (p+1)^d times the DoF count in doubles). Errors:
- * INVALID_ARG. */
+/* Bytes of the scratch workspace of the general-coefficient operator: 3D,
+ * two arrays of nq_0 m_1 m_2 doubles and six of nq_0 nq_1 m_2 (about
+ * 6 (p+1)^2 times the DoF count in doubles); 2D, four of nq_0 m_1. Values at
+ * all Gauss points are never stored. Errors: INVALID_ARG. */
 int iffd_general_workspace_bytes(iffd_handle h, size_t* bytes);
 
 /* Au = A_C u on the device. C: device array of ncomp * nq_0 nq_1 (nq_2)
@@ -296,7 +296,7 @@ int iffd_general_workspace_bytes(iffd_handle h, size_t* bytes);
  * device arrays of the plan's shape; they may not alias. gws: device scratch
  * of iffd_general_workspace_bytes, 256-byte aligned, caller-owned. Stream-
  * ordered, asynchronous. Errors: INVALID_ARG (NULL, aliasing, ncomp),
- * WORKSPACE, CUDA. */
+ * WORKSPACE, UNSUPPORTED (p > 11), CUDA. */
 int iffd_apply_stiffness_general(iffd_handle h, const double* C, int ncomp, const double* u, double* Au, void* gws,
                                  void* stream);
 

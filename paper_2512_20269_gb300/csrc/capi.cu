@@ -1187,6 +1187,7 @@ static int check_general(const Plan* P, const double* C, int ncomp, const void* 
   if (reinterpret_cast<uintptr_t>(gws) % 256 != 0) return fail(IFFD_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   const long long rows = (long long)P->gen[1].nq * (P->d == 3 ? P->gen[2].nq : 1);
   if (rows >= (1LL << 31)) return fail(IFFD_ERR_UNSUPPORTED, "Gauss grid too large");
+  if (P->p > kGenMaxDegree) return fail(IFFD_ERR_UNSUPPORTED, "general coefficient: degree above 11");
   return check_device(P);
 }
 

@@ -9,9 +9,10 @@
 // d-dimensional array with x fastest.
 //
 // 3D forward: U_B = B_x u, U_D = D_x u; V_BB = B_y U_B, V_BD = D_y U_B,
-// V_DB = B_y U_D; then g = (B_z V_DB, B_z V_BD, D_z V_BB) and h = w C g in
-// one pass over the Gauss grid. Backward with the transposes in the reverse
-// order, the two contributions of each sweep summed in one pass.
+// V_DB = B_y U_D; then along z, in one pass element by element, g = (B_z V_DB,
+// B_z V_BD, D_z V_BB), h = w C g and the transposed z products, so that the
+// Gauss-grid values never reach memory. Backward along y and x with the
+// transposes, the two contributions of each sweep summed in one pass.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -109,73 +110,122 @@ __device__ __forceinline__ void coef_apply(double* g, const double* __restrict__
   }
 }
 
-// The last forward sweep (along direction D-1) fused with the Gauss-point
-// step: the D partial derivatives of the point, then h = w C g, written once.
-// 3D: g_x = B_z in0, g_y = B_z in1, g_z = D_z in2; 2D: g_x = B_y in0,
-// g_y = D_y in1. Output (q0, q1[, q2]), x fastest; w = w_z (w_y w_x).
-template <int D>
-__global__ void __launch_bounds__(kThreads)
-gen_last_fwd(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ in2,
-             double* __restrict__ h0, double* __restrict__ h1, double* __restrict__ h2, int q0, int q1, int q2,
-             const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ bv,
-             const double* __restrict__ dv, const double* __restrict__ C, int ncomp, const double* __restrict__ w0,
-             const double* __restrict__ w1, const double* __restrict__ w2, const int* __restrict__ done) {
+// The last direction (D-1) in one pass: forward sweep, Gauss-point step and
+// transposed sweep. A thread owns one column of the Gauss grid along that
+// direction (a fixed (x, y) Gauss point in 3D, a fixed x Gauss point in 2D)
+// and walks its elements in order. The p+1 Gauss points of element e share the
+// element's basis functions (cnt <= p+1 columns of the sparse 1D matrices):
+// at each point the thread forms g (3D: B_z in0, B_z in1, D_z in2; 2D: B_y in0,
+// D_y in1), h = w C g, and accumulates the transposed products for those
+// functions in registers; the element's sums are then added to the thread's
+// own entries of out0..out2 (no other thread writes them). 3D: out = W_DB,
+// W_BD, W_BB; 2D: out = X_D, X_B. Inputs and outputs have the shape
+// (q0[, q1], m_last), x fastest; w = w_z (w_y w_x).
+// P1: p + 1 (compile time, so that the per-thread arrays stay in registers).
+constexpr int kFusedThreads = 128;
+
+template <int D, int P1>
+__global__ void __launch_bounds__(kFusedThreads)
+gen_last_fused(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ in2,
+               double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ out2, int q0, int q1,
+               int nel, int m_last, const int* __restrict__ rp, const int* __restrict__ col,
+               const double* __restrict__ bv, const double* __restrict__ dv, const double* __restrict__ C, int ncomp,
+               const double* __restrict__ w0, const double* __restrict__ w1, const double* __restrict__ wl,
+               const int* __restrict__ done) {
   if (done != nullptr && *((volatile const int*)done)) return;
-  const long long total = (long long)q0 * q1 * q2;
-  const long long s_ax = (D == 3) ? (long long)q0 * q1 : q0;  // stride of the last direction in the inputs
-  const int rows = q1 * q2;
-  for (int rr = blockIdx.y; rr < rows; rr += gridDim.y) {
-    const int i1 = rr % q1, i2 = rr / q1;
-    const int row = (D == 3) ? i2 : i1;  // Gauss point along the last direction
-    const long long rbase = (D == 3) ? (long long)i1 * q0 : 0;
-    const double wr = (D == 3) ? __ldg(w2 + i2) : 1.0, wy = __ldg(w1 + i1);
-    const int k0 = __ldg(rp + row), k1 = __ldg(rp + row + 1);
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < q0; i0 += gridDim.x * blockDim.x) {
-      const long long base = rbase + i0;
+  const long long ncol = (D == 3) ? (long long)q0 * q1 : q0;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  const int i0 = (int)(c % q0);
+  const double wxy = (D == 3) ? __ldg(w1 + c / q0) * __ldg(w0 + i0) : __ldg(w0 + i0);
+  const long long s = ncol;                       // stride of the last direction
+  const long long total = ncol * (long long)nel * P1;  // Gauss points (one coefficient component)
+  for (int j = 0; j < m_last; ++j) {
+    out0[c + j * s] = 0.0;
+    out1[c + j * s] = 0.0;
+    if (D == 3) out2[c + j * s] = 0.0;
+  }
+  for (int e = 0; e < nel; ++e) {
+    const int qa = e * P1;
+    const int k0 = __ldg(rp + qa), cnt = __ldg(rp + qa + 1) - k0;
+    long long at[P1];
+    double a0[P1], a1[P1], a2[P1];
+    double acc0[P1], acc1[P1], acc2[P1];
+#pragma unroll
+    for (int t = 0; t < P1; ++t) {
+      acc0[t] = acc1[t] = acc2[t] = 0.0;
+      if (t < cnt) {
+        at[t] = c + (long long)__ldg(col + k0 + t) * s;
+        a0[t] = in0[at[t]];
+        a1[t] = in1[at[t]];
+        if (D == 3) a2[t] = in2[at[t]];
+      }
+    }
+    for (int qq = 0; qq < P1; ++qq) {
+      const int q = qa + qq, kq = k0 + qq * cnt;  // every point of the element has the same cnt columns
       double g[3] = {0.0, 0.0, 0.0};
-      int k = k0;
-      for (; k + 2 <= k1; k += 2) {  // loads of two entries before their FMAs
-        double a[2][3];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const long long at = base + (long long)__ldg(col + k + e) * s_ax;
-          a[e][0] = in0[at];
-          a[e][1] = in1[at];
-          if (D == 3) a[e][2] = in2[at];
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const double b = __ldg(bv + k + e), dd = __ldg(dv + k + e);
-          g[0] = fma(b, a[e][0], g[0]);
+      for (int t = 0; t < P1; ++t)
+        if (t < cnt) {
+          const double b = __ldg(bv + kq + t), dd = __ldg(dv + kq + t);
+          g[0] = fma(b, a0[t], g[0]);
           if (D == 3) {
-            g[1] = fma(b, a[e][1], g[1]);
-            g[2] = fma(dd, a[e][2], g[2]);
+            g[1] = fma(b, a1[t], g[1]);
+            g[2] = fma(dd, a2[t], g[2]);
           } else {
-            g[1] = fma(dd, a[e][1], g[1]);
+            g[1] = fma(dd, a1[t], g[1]);
           }
         }
-      }
-      for (; k < k1; ++k) {
-        const long long at = base + (long long)__ldg(col + k) * s_ax;
-        const double b = __ldg(bv + k), dd = __ldg(dv + k);
-        if (D == 3) {
-          g[0] = fma(b, in0[at], g[0]);
-          g[1] = fma(b, in1[at], g[1]);
-          g[2] = fma(dd, in2[at], g[2]);
-        } else {
-          g[0] = fma(b, in0[at], g[0]);
-          g[1] = fma(dd, in1[at], g[1]);
+      coef_apply<D>(g, C, ncomp, total, c + (long long)q * s, __ldg(wl + q) * wxy);
+#pragma unroll
+      for (int t = 0; t < P1; ++t)
+        if (t < cnt) {
+          const double b = __ldg(bv + kq + t), dd = __ldg(dv + kq + t);
+          acc0[t] = fma(b, g[0], acc0[t]);
+          if (D == 3) {
+            acc1[t] = fma(b, g[1], acc1[t]);
+            acc2[t] = fma(dd, g[2], acc2[t]);
+          } else {
+            acc1[t] = fma(dd, g[1], acc1[t]);
+          }
         }
-      }
-      double w = wy * __ldg(w0 + i0);
-      if (D == 3) w = wr * w;
-      const long long t = (long long)rr * q0 + i0;
-      coef_apply<D>(g, C, ncomp, total, t, w);
-      h0[t] = g[0];
-      h1[t] = g[1];
-      if (D == 3) h2[t] = g[2];
     }
+#pragma unroll
+    for (int t = 0; t < P1; ++t)
+      if (t < cnt) {
+        out0[at[t]] += acc0[t];
+        out1[at[t]] += acc1[t];
+        if (D == 3) out2[at[t]] += acc2[t];
+      }
   }
+}
+
+template <int D, int P1>
+cudaError_t launch_fused_p(const double* in0, const double* in1, const double* in2, double* out0, double* out1,
+                           double* out2, int q0, int q1, int nel, int m_last, const GenAxis& L, const double* C,
+                           int ncomp, const double* w0, const double* w1, const int* done, cudaStream_t st) {
+  const long long ncol = (D == 3) ? (long long)q0 * q1 : q0;
+  const int blocks = (int)((ncol + kFusedThreads - 1) / kFusedThreads);
+  gen_last_fused<D, P1><<<blocks, kFusedThreads, 0, st>>>(in0, in1, in2, out0, out1, out2, q0, q1, nel, m_last, L.rp,
+                                                          L.col, L.bv, L.dv, C, ncomp, w0, w1, L.w, done);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_fused(int p1, const double* in0, const double* in1, const double* in2, double* out0,
+                         double* out1, double* out2, int q0, int q1, int nel, int m_last, const GenAxis& L,
+                         const double* C, int ncomp, const double* w0, const double* w1, const int* done,
+                         cudaStream_t st) {
+#define IFFD_FUSED(PP)                                                                                          \
+  case PP:                                                                                                     \
+    return launch_fused_p<D, PP>(in0, in1, in2, out0, out1, out2, q0, q1, nel, m_last, L, C, ncomp, w0, w1, done, \
+                                 st);
+  switch (p1) {
+    IFFD_FUSED(2) IFFD_FUSED(3) IFFD_FUSED(4) IFFD_FUSED(5) IFFD_FUSED(6) IFFD_FUSED(7)
+    IFFD_FUSED(8) IFFD_FUSED(9) IFFD_FUSED(10) IFFD_FUSED(11) IFFD_FUSED(12)
+    default: return cudaErrorInvalidValue;
+  }
+#undef IFFD_FUSED
 }
 
 // p = z (mode 1) or p = z + beta p (mode 2), beta read on the device.
@@ -253,13 +303,14 @@ int build_general_tables(Plan* P, cudaStream_t st) {
   return IFFD_OK;
 }
 
-// Scratch of one application: two arrays with direction 0 at the Gauss
-// points, three with directions 0 and 1 (3D), d with all of them.
+// Scratch of one application: 3D, two arrays with direction 0 at the Gauss
+// points and six with directions 0 and 1; 2D, four with direction 0 at the
+// Gauss points. No array spans the whole Gauss grid.
 size_t general_ws_bytes(const Plan* P) {
   const long long q0 = P->gen[0].nq, q1 = P->gen[1].nq, m1 = P->gen[1].m;
-  if (P->d == 2) return 2 * al256(q0 * m1 * 8) + 2 * al256(q0 * q1 * 8);
-  const long long q2 = P->gen[2].nq, m2 = P->gen[2].m;
-  return 2 * al256(q0 * m1 * m2 * 8) + 3 * al256(q0 * q1 * m2 * 8) + 3 * al256(q0 * q1 * q2 * 8);
+  if (P->d == 2) return 4 * al256(q0 * m1 * 8);
+  const long long m2 = P->gen[2].m;
+  return 2 * al256(q0 * m1 * m2 * 8) + 6 * al256(q0 * q1 * m2 * 8);
 }
 
 int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au, void* gws, cudaStream_t st,
@@ -281,7 +332,17 @@ int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au
     V[1] = take(q0 * q1 * m2);
     V[2] = take(q0 * q1 * m2);
   }
-  double* H[3] = {take(q0 * q1 * q2), take(q0 * q1 * q2), d == 3 ? take(q0 * q1 * q2) : nullptr};
+  // outputs of the fused last direction: 3D W_DB, W_BD, W_BB (as V); 2D X_D, X_B (as U)
+  double* T[3] = {nullptr, nullptr, nullptr};
+  if (d == 3) {
+    T[0] = take(q0 * q1 * m2);
+    T[1] = take(q0 * q1 * m2);
+    T[2] = take(q0 * q1 * m2);
+  } else {
+    T[0] = take(q0 * m1);
+    T[1] = take(q0 * m1);
+  }
+  const int p1 = P->p + 1;
   auto sweep = [&](int mode, const double* in, const double* in2, double* out, double* out2, long long o0,
                    long long o1, long long o2, int in_len, int axis, const int* rp, const int* col, const double* v,
                    const double* v2) -> cudaError_t {
@@ -303,20 +364,12 @@ int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au
   IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_OUT, u, nullptr, U[0], U[1], q0, m1, m2, (int)m0, 0, X.rp, X.col,
                                            X.bv, X.dv));
   if (d == 2) {
-    // h = w C (B_y U_D, D_y U_B) at every Gauss point
-    auto last2 = [&] {
-      const Shape2 sh = shape_for(q0, q1);
-      gen_last_fwd<2><<<sh.grid, sh.block, 0, st>>>(U[1], U[0], nullptr, H[0], H[1], nullptr, (int)q0, (int)q1, 1,
-                                                    Y.rp, Y.col, Y.bv, Y.dv, C, ncomp, X.w, Y.w, nullptr, done);
-      return cudaGetLastError();
-    };
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, last2());
-    // X_D = B_y^T h_x, X_B = D_y^T h_y; Au = D_x^T X_D + B_x^T X_B
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[0], nullptr, U[1], nullptr, q0, m1, 1, (int)q1, 1, Y.trp,
-                                             Y.tcol, Y.tbv, nullptr));
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[1], nullptr, U[0], nullptr, q0, m1, 1, (int)q1, 1, Y.trp,
-                                             Y.tcol, Y.tdv, nullptr));
-    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_IN, U[1], U[0], Au, nullptr, m0, m1, 1, (int)q0, 0, X.trp,
+    // X_D = B_y^T h_x, X_B = D_y^T h_y with h = w C (B_y U_D, D_y U_B), fused
+    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, launch_fused<2>(p1, U[1], U[0], nullptr, T[1], T[0], nullptr, (int)q0, 1,
+                                                       (int)(q1 / p1), (int)m1, Y, C, ncomp, X.w, nullptr, done,
+                                                       st));
+    // Au = D_x^T X_D + B_x^T X_B
+    IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_IN, T[1], T[0], Au, nullptr, m0, m1, 1, (int)q0, 0, X.trp,
                                              X.tcol, X.tdv, X.tbv));
     return IFFD_OK;
   }
@@ -326,25 +379,14 @@ int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au
                                            Y.col, Y.bv, Y.dv));
   IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, U[1], nullptr, V[2], nullptr, q0, q1, m2, (int)m1, 1, Y.rp,
                                            Y.col, Y.bv, nullptr));
-  // h = w C (B_z V_DB, B_z V_BD, D_z V_BB) at every Gauss point
-  auto last3 = [&] {
-    const Shape2 sh = shape_for(q0, q1 * q2);
-    gen_last_fwd<3><<<sh.grid, sh.block, 0, st>>>(V[2], V[1], V[0], H[0], H[1], H[2], (int)q0, (int)q1, (int)q2,
-                                                  Z.rp, Z.col, Z.bv, Z.dv, C, ncomp, X.w, Y.w, Z.w, done);
-    return cudaGetLastError();
-  };
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, last3());
-  // W_DB = B_z^T h_x -> V[2], W_BD = B_z^T h_y -> V[1], W_BB = D_z^T h_z -> V[0]
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[0], nullptr, V[2], nullptr, q0, q1, m2, (int)q2, 2, Z.trp,
-                                           Z.tcol, Z.tbv, nullptr));
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[1], nullptr, V[1], nullptr, q0, q1, m2, (int)q2, 2, Z.trp,
-                                           Z.tcol, Z.tbv, nullptr));
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, H[2], nullptr, V[0], nullptr, q0, q1, m2, (int)q2, 2, Z.trp,
-                                           Z.tcol, Z.tdv, nullptr));
+  // W_DB = B_z^T h_x, W_BD = B_z^T h_y, W_BB = D_z^T h_z with
+  // h = w C (B_z V_DB, B_z V_BD, D_z V_BB), fused along z
+  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, launch_fused<3>(p1, V[2], V[1], V[0], T[2], T[1], T[0], (int)q0, (int)q1,
+                                                     (int)(q2 / p1), (int)m2, Z, C, ncomp, X.w, Y.w, done, st));
   // X_D = B_y^T W_DB -> U[1]; X_B = D_y^T W_BD + B_y^T W_BB -> U[0]
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, V[2], nullptr, U[1], nullptr, q0, m1, m2, (int)q1, 1, Y.trp,
+  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_ONE, T[2], nullptr, U[1], nullptr, q0, m1, m2, (int)q1, 1, Y.trp,
                                            Y.tcol, Y.tbv, nullptr));
-  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_IN, V[1], V[0], U[0], nullptr, q0, m1, m2, (int)q1, 1, Y.trp,
+  IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_IN, T[1], T[0], U[0], nullptr, q0, m1, m2, (int)q1, 1, Y.trp,
                                            Y.tcol, Y.tdv, Y.tbv));
   // Au = D_x^T X_D + B_x^T X_B
   IFFD_LAUNCH(P, IFFD_K_GENERAL, st, sweep(GS_TWO_IN, U[1], U[0], Au, nullptr, m0, m1, m2, (int)q0, 0, X.trp, X.tcol,

@@ -188,6 +188,7 @@ F32Geom f32_geom(const Plan& P, int a);
 // General-coefficient stiffness (general.cu): device tables (at plan
 // creation), scratch bytes of one application, the application Au = A_C u
 // (C: ncomp arrays at the Gauss points), and the p-update of its PCG.
+constexpr int kGenMaxDegree = 11;  // the fused last-direction pass holds p + 1 entries per thread
 int build_general_tables(Plan* P, cudaStream_t st);
 size_t general_ws_bytes(const Plan* P);
 int run_general(Plan* P, const double* C, int ncomp, const double* u, double* Au, void* gws, cudaStream_t st,
