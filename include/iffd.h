@@ -282,6 +282,15 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
  * INVALID_ARG. */
 int iffd_quad_points(iffd_handle h, int axis, int* nq, double* x, double* w);
 
+/* Host only, no plan: the Gauss points x and weights w (nq = n (p+1)
+ * entries) of one direction, and the dense nq x m row-major matrices B
+ * (values) and D (first derivatives) of its kept B-splines there, expanded
+ * from the sparse tables the device passes use (which are also checked
+ * against their transposes). Arguments as iffd_host_axis_knots; any output
+ * may be NULL (query nq and m first). Errors: INVALID_ARG, UNSUPPORTED. */
+int iffd_host_quad_axis(int n, int p, const int* dirichlet, int nrep, const int* reps, int* nq, int* m, double* x,
+                        double* w, double* B, double* D);
+
 /* Bytes of the scratch workspace of the general-coefficient operator: 3D,
  * two arrays of nq_0 m_1 m_2 doubles and six of nq_0 nq_1 m_2 (about
  * 6 (p+1)^2 times the DoF count in doubles); 2D, four of nq_0 m_1. Values at

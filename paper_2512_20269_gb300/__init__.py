@@ -78,6 +78,27 @@ def host_axis(n: int, p: int, dirichlet=(1, 1), rep=None) -> dict:
     return out
 
 
+def host_quad_axis(n: int, p: int, dirichlet=(1, 1), rep=None) -> dict:
+    """Gauss points, weights and the dense value / derivative matrices of the
+    kept B-splines at them, from the tables the general-coefficient operator
+    uses (iffd_host_quad_axis; no GPU)."""
+    lib = _lib.load()
+    dir_arr = (ctypes.c_int * 2)(*dirichlet)
+    flat = _rep_pairs(rep)
+    rep_arr = (ctypes.c_int * max(1, len(flat)))(*flat)
+    nq, m = ctypes.c_int(), ctypes.c_int()
+    check(lib.iffd_host_quad_axis(n, p, dir_arr, len(flat) // 2, rep_arr, ctypes.byref(nq), ctypes.byref(m), None,
+                                  None, None, None), "iffd_host_quad_axis")
+    nq, m = nq.value, m.value
+    out = {"x": np.zeros(nq), "w": np.zeros(nq), "B": np.zeros(nq * m), "D": np.zeros(nq * m)}
+    dp = lambda a: a.ctypes.data_as(_lib.c_double_p)
+    check(lib.iffd_host_quad_axis(n, p, dir_arr, len(flat) // 2, rep_arr, None, None, dp(out["x"]), dp(out["w"]),
+                                  dp(out["B"]), dp(out["D"])), "iffd_host_quad_axis")
+    out["B"] = out["B"].reshape(nq, m)
+    out["D"] = out["D"].reshape(nq, m)
+    return out
+
+
 class IFFDPlan:
     """One problem (d, n per direction, p, boundary conditions) on the current CUDA device.
 

@@ -68,6 +68,8 @@ SIGNATURES = [
                                                     ctypes.c_void_p]),
     ("iffd_pcg_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.POINTER(iffd_pcg_info)]),
+    ("iffd_host_quad_axis", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_int, c_int_p, c_int_p,
+                                           c_int_p] + [c_double_p] * 4),
     ("iffd_quad_points", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_double_p, c_double_p]),
     ("iffd_general_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, c_size_t_p]),
     ("iffd_apply_stiffness_general", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,

@@ -1172,6 +1172,46 @@ int iffd_quad_points(iffd_handle h, int axis, int* nq, double* x, double* w) {
   return IFFD_OK;
 }
 
+int iffd_host_quad_axis(int n, int p, const int* dirichlet, int nrep, const int* reps, int* nq, int* m, double* x,
+                        double* w, double* B, double* D) {
+  g_err.clear();
+  if (!dirichlet) return fail(IFFD_ERR_INVALID_ARG, "dirichlet is NULL");
+  if (nrep < 0 || (nrep > 0 && !reps)) return fail(IFFD_ERR_INVALID_ARG, "bad repeated-knot list");
+  std::vector<std::pair<int, int>> ra;
+  for (int r = 0; r < nrep; ++r) ra.push_back({reps[2 * r], reps[2 * r + 1]});
+  Axis1D A;
+  const std::string err = build_axis(n, p, dirichlet[0] != 0, dirichlet[1] != 0, &A, ra);
+  if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
+  QuadAxis Q;
+  build_quad_axis(A, &Q);
+  if (nq) *nq = Q.nq;
+  if (m) *m = Q.m;
+  if (x) std::memcpy(x, Q.x.data(), Q.x.size() * sizeof(double));
+  if (w) std::memcpy(w, Q.w.data(), Q.w.size() * sizeof(double));
+  // dense B and D from the CSR rows, and their transposes checked against the
+  // transposed CSR (the device applies both)
+  for (int q = 0; q < Q.nq; ++q)
+    for (int j = 0; j < Q.m; ++j) {
+      if (B) B[(size_t)q * Q.m + j] = 0.0;
+      if (D) D[(size_t)q * Q.m + j] = 0.0;
+    }
+  for (int q = 0; q < Q.nq; ++q)
+    for (int k = Q.rp[q]; k < Q.rp[q + 1]; ++k) {
+      if (B) B[(size_t)q * Q.m + Q.col[k]] = Q.bv[k];
+      if (D) D[(size_t)q * Q.m + Q.col[k]] = Q.dv[k];
+    }
+  for (int j = 0; j < Q.m; ++j)
+    for (int k = Q.trp[j]; k < Q.trp[j + 1]; ++k) {
+      const int q = Q.tcol[k];
+      bool found = false;
+      for (int kk = Q.rp[q]; kk < Q.rp[q + 1]; ++kk)
+        if (Q.col[kk] == j) found = Q.bv[kk] == Q.tbv[k] && Q.dv[kk] == Q.tdv[k];
+      if (!found) return fail(IFFD_ERR_UNSUPPORTED, "transposed Gauss-point table is inconsistent");
+    }
+  if ((int)Q.tcol.size() != Q.rp[Q.nq]) return fail(IFFD_ERR_UNSUPPORTED, "transposed Gauss-point table size");
+  return IFFD_OK;
+}
+
 int iffd_general_workspace_bytes(iffd_handle h, size_t* bytes) {
   g_err.clear();
   if (!h || !bytes) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");

@@ -200,3 +200,20 @@ def test_reduced_regularity_input_errors(lib, rep, msg):
     assert lib.iffd_host_axis_knots(16, 4, d, 2, reps, None, None, None, None, None, None, None, None, None) == 2
     assert lib.iffd_host_axis_knots(16, 4, d, 1, None, None, None, None, None, None, None, None, None, None) == 1
     assert lib.iffd_host_axis_knots(16, 4, d, -1, reps, None, None, None, None, None, None, None, None, None) == 1
+
+
+@pytest.mark.parametrize("n,p,dirichlet,rep", [(7, 3, (1, 1), None), (6, 4, (1, 0), {3: 2}), (5, 2, (0, 0), None),
+                                                (9, 5, (0, 1), {2: 1, 6: 4})])
+def test_library_gauss_tables_match_the_oracle(n, p, dirichlet, rep):
+    """The library's host tables of the general-coefficient operator (points,
+    weights, and the sparse value / derivative matrices, expanded) equal the
+    oracle's quad_axis: independent evaluations of the same B-splines."""
+    from oracle import general
+    from paper_2512_20269_gb300 import host_quad_axis
+    t = host_quad_axis(n, p, dirichlet, rep=rep)
+    dset = tuple(k for k, v in zip((0, 1), dirichlet) if v)
+    x, w, B, D = general.quad_axis(n, p, dset, rep=rep)
+    assert np.max(np.abs(t["x"] - x)) <= 1e-15 and np.max(np.abs(t["w"] - w)) <= 1e-15
+    assert t["B"].shape == B.shape
+    assert np.max(np.abs(t["B"] - B)) <= 1e-13
+    assert np.max(np.abs(t["D"] - D)) <= 1e-11 * max(1.0, np.max(np.abs(D)))

@@ -121,3 +121,4 @@ def test_quadrature_data(n, p, rep):
     assert abs(w.sum() - 1.0) <= 1e-14
     assert np.max(np.abs(B.sum(axis=1) - 1.0)) <= 1e-13
     assert np.max(np.abs(D.sum(axis=1))) <= 1e-11
+
