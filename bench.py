@@ -525,7 +525,7 @@ def main():
     # Gauss point row, q / m = n p1 / m entries per basis-function row)
     #   x: 2 x q0 m1 m2 outputs x p1;  y: 3 x q0 q1 m2 x p1;
     #   z (fused): per Gauss point 3 p1 (gradient) + 3 p1 (transpose) FMAs and
-    #     7 multiplies for w a g;
+    #     5 multiplies for w a g (w, w a, 3 products; 2D: 2 p1 + 2 p1 and 4);
     #   y^T: 3 x q0 m1 m2 x q1 p1 / m1;  x^T: 2 x m0 m1 m2 x q0 p1 / m0.
     # Algorithmic bytes: u and Au (16 per DoF) and a at every Gauss point (8).
     if not args.no_variants:
@@ -567,11 +567,11 @@ def main():
             q0, q1, q2 = qd
             m0, m1, m2 = md
             gflop = (2 * (2 * q0 * m1 * m2 * p1 + 3 * q0 * q1 * m2 * p1 + 3 * q0 * m1 * m2 * q1 * p1 / m1
-                          + 2 * m0 * m1 * m2 * q0 * p1 / m0) + q0 * q1 * q2 * (12 * p1 + 7)) / 1e9
+                          + 2 * m0 * m1 * m2 * q0 * p1 / m0) + q0 * q1 * q2 * (12 * p1 + 5)) / 1e9
         else:
             q0, q1 = qd
             m0, m1 = md
-            gflop = (2 * (2 * q0 * m1 * p1 + 2 * m0 * m1 * q0 * p1 / m0) + q0 * q1 * (8 * p1 + 5)) / 1e9
+            gflop = (2 * (2 * q0 * m1 * p1 + 2 * m0 * m1 * q0 * p1 / m0) + q0 * q1 * (8 * p1 + 4)) / 1e9
         variants["general_coef"] = {
             "config": {"workload": f"cube n=128 p={w.p}, a = 1 + sin(2 pi (x + 2y + 3z)) cos(pi x y) / 2",
                        "dofs": pg.N, "gauss_points": int(coef.numel())},

@@ -88,9 +88,9 @@ template <int D>
 __device__ __forceinline__ void coef_apply(double* g, const double* __restrict__ C, int ncomp, long long total,
                                            long long t, double w) {
   if (ncomp == 1) {
-    const double c = __ldg(C + t);
+    const double wc = w * __ldg(C + t);
 #pragma unroll
-    for (int k = 0; k < D; ++k) g[k] = w * (c * g[k]);
+    for (int k = 0; k < D; ++k) g[k] = wc * g[k];
     return;
   }
   if (D == 2) {
