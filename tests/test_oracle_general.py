@@ -11,7 +11,10 @@ it independently of itself.
 * A is symmetric, and positive definite with Dirichlet ends, for a random
   symmetric positive definite field C(x);
 * the quadrature data: weights sum to 1, values form a partition of unity,
-  derivatives sum to 0.
+  derivatives sum to 0;
+* and mistakes planted in the oracle (values and derivatives swapped,
+  directions reversed, a wrong or dropped tensor component, transposed
+  weights) each break one of these pins.
 """
 
 import numpy as np
@@ -122,3 +125,73 @@ def test_quadrature_data(n, p, rep):
     assert np.max(np.abs(B.sum(axis=1) - 1.0)) <= 1e-13
     assert np.max(np.abs(D.sum(axis=1))) <= 1e-11
 
+
+
+def _pin_errors():
+    """The pins above as numbers (each must be ~0 for a correct oracle)."""
+    errs = {}
+    ns, p, dsets = (5, 7), 2, [(0, 1), (0,)]
+    axes = _axes(ns, p, dsets)
+    mk = _mk(ns, p, dsets)
+    u = _rand(tuple(M.shape[0] for M, _ in reversed(mk)), 1)
+    C = np.ones((1,) + tuple(ax[0].size for ax in reversed(axes)))
+    ref = operators.stiffness_apply(u, mk)
+    errs["unit"] = np.max(np.abs(general.general_stiffness_apply(u, axes, C) - ref)) / np.max(np.abs(ref))
+    ns, p, dsets = (5, 6, 4), 2, [(0, 1), (0,), (1,)]
+    axes = _axes(ns, p, dsets)
+    mk = _mk(ns, p, dsets)
+    c = (0.7, 1.9, 3.1)
+    C = np.zeros((6,) + tuple(ax[0].size for ax in reversed(axes)))
+    C[0], C[3], C[5] = c
+    u = _rand(tuple(M.shape[0] for M, _ in reversed(mk)), 3)
+    ref = sum(c[k] * operators.kron_apply([mk[j][1] if j == k else mk[j][0] for j in range(3)], u) for k in range(3))
+    errs["diag"] = np.max(np.abs(general.general_stiffness_apply(u, axes, C) - ref)) / np.max(np.abs(ref))
+    ax = general.quad_axis(4, 2, ())
+    shape_q = (ax[0].size, ax[0].size)
+    C = np.stack([np.full(shape_q, 1.3), np.full(shape_q, -0.4), np.full(shape_q, 0.8)])
+    lin, sq = _project(ax, lambda t: t), _project(ax, lambda t: t * t)
+    val = float(np.sum(np.multiply.outer(sq, lin) * general.general_stiffness_apply(np.multiply.outer(lin, sq),
+                                                                                    [ax, ax], C)))
+    errs["offdiag"] = abs(val - (1.3 / 4 + 5 * -0.4 / 9 + 0.8 / 4))
+    return errs
+
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """Plausible mistakes planted in the oracle (on the CPU) each break at
+    least one pin: the pins fix the derivative placement, the direction
+    order, the component order of the tensor, and the weight layout."""
+    assert max(_pin_errors().values()) <= 1e-12
+    real_kron = general.kron_apply
+    real_component = general.component
+    real_weights = general.weights
+    real_quad = general.quad_axis
+
+    def swapped_bd(n, p, dirichlet=(0, 1), rep=None):  # derivatives in place of values and back
+        x, w, B, D = real_quad(n, p, dirichlet, rep)
+        return x, w, D, B
+
+    def reversed_directions(mats, u):  # direction k's matrix applied along another direction
+        return real_kron(mats[::-1], u)
+
+    def wrong_component(C, d, k, l):  # C12 read from the C22 slot
+        if C.shape[0] > 1 and {k, l} == {0, 1}:
+            return real_component(C, d, 1, 1)
+        return real_component(C, d, k, l)
+
+    def dropped_offdiag(C, d, k, l):  # off-diagonal terms dropped
+        return real_component(C, d, k, l) if k == l else 0.0
+
+    def transposed_weights(axes):  # direction 1's weights on the slowest axis
+        return np.transpose(real_weights(axes))
+
+    for name, attr, fake in (("swap", "quad_axis", swapped_bd), ("direction", "kron_apply", reversed_directions),
+                             ("component", "component", wrong_component),
+                             ("offdiag", "component", dropped_offdiag), ("weights", "weights", transposed_weights)):
+        with monkeypatch.context() as m:
+            m.setattr(general, attr, fake)
+            try:
+                errs = _pin_errors()
+                worst = max(errs.values())
+            except ValueError:  # shapes no longer match: the mistake is caught too
+                worst = np.inf
+            assert worst > 1e-6, name
