@@ -217,3 +217,13 @@ def test_library_gauss_tables_match_the_oracle(n, p, dirichlet, rep):
     assert t["B"].shape == B.shape
     assert np.max(np.abs(t["B"] - B)) <= 1e-13
     assert np.max(np.abs(t["D"] - D)) <= 1e-11 * max(1.0, np.max(np.abs(D)))
+
+
+def test_host_quad_axis_input_errors():
+    from paper_2512_20269_gb300 import IFFDError, host_quad_axis
+    with pytest.raises(IFFDError):
+        host_quad_axis(8, 3, (1, 1), rep={0: 1})  # knot 0 is not interior
+    with pytest.raises(IFFDError):
+        host_quad_axis(8, 3, (1, 1), rep={4: 3})  # multiplicity above p - 1
+    t = host_quad_axis(8, 3, (1, 1), rep={4: 2})
+    assert t["B"].shape == (32, 8 + 3 + 2 - 2)
