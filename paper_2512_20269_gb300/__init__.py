@@ -245,7 +245,9 @@ class IFFDPlan:
     @property
     def quad_shape(self):
         """Shape of one coefficient component: (nq_{d-1}, ..., nq_0), x fastest."""
-        return tuple(self.quad_points(a)[0].size for a in reversed(range(self.d)))
+        if getattr(self, "_quad_shape", None) is None:
+            self._quad_shape = tuple(self.quad_points(a)[0].size for a in reversed(range(self.d)))
+        return self._quad_shape
 
     def _gws(self):
         import torch
@@ -259,8 +261,9 @@ class IFFDPlan:
         import torch
         if not (C.is_cuda and C.dtype == torch.float64 and C.is_contiguous()):
             raise ValueError("C must be a contiguous float64 CUDA tensor")
-        ncomp = C.numel() // int(np.prod(self.quad_shape))
-        if ncomp * int(np.prod(self.quad_shape)) != C.numel():
+        nq = int(np.prod(self.quad_shape))
+        ncomp = C.numel() // nq
+        if ncomp * nq != C.numel():
             raise ValueError(f"C must hold ncomp x {self.quad_shape} values")
         return ncomp
 
