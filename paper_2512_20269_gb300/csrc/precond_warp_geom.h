@@ -1,4 +1,4 @@
-// Compile-time geometry of the FP32 warp-FFT passes (precond_warp.cuh), shared
+// Compile-time geometry of the warp-FFT passes (precond_warp.cuh), shared
 // with the host code that sizes their launches (precond.cu).
 #pragma once
 
