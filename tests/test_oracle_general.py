@@ -10,6 +10,9 @@ it independently of itself.
   polynomials the spline space reproduces;
 * A is symmetric, and positive definite with Dirichlet ends, for a random
   symmetric positive definite field C(x);
+* for non-separable scalar and tensor fields on a tiny 2D grid, A equals a
+  brute-force element-by-element Galerkin assembly (tensor-product B-splines
+  and their gradients evaluated point by point, no Kronecker factorisation);
 * the quadrature data: weights sum to 1, values form a partition of unity,
   derivatives sum to 0;
 * and mistakes planted in the oracle (values and derivatives swapped,
@@ -195,3 +198,57 @@ def test_pins_catch_planted_mistakes(monkeypatch):
             except ValueError:  # shapes no longer match: the mistake is caught too
                 worst = np.inf
             assert worst > 1e-6, name
+
+
+@pytest.mark.parametrize("kind", ["scalar", "tensor"])
+def test_non_separable_coefficient_by_element_assembly(kind):
+    """Brute force on a tiny 2D grid: A_ij = sum over elements and tensor Gauss
+    points of w grad B_i . C grad B_j, with the tensor-product B-splines and
+    their gradients evaluated point by point (no Kronecker factorisation),
+    for a non-separable C, equals the oracle's matrix."""
+    ns, p, dsets = (3, 4), 2, [(0, 1), (0,)]
+    knots = [splines.open_knots(n, p) for n in ns]
+    keep = [splines.kept_indices(n, p, D) for n, D in zip(ns, dsets)]
+    m = [len(k) for k in keep]
+    pos = [{int(g): i for i, g in enumerate(k)} for k in keep]
+
+    def coef(x, y):
+        if kind == "scalar":
+            return np.array([[1.0 + x * y * y + np.sin(x + 2 * y), 0.0], [0.0, 0.0]])
+        a, b = 1.2 + np.cos(3 * x * y), 0.9 + x * x
+        c = 0.3 * np.sin(x + y)
+        return np.array([[a, c], [c, b]])
+
+    A = np.zeros((m[0] * m[1], m[0] * m[1]))
+    for ex in range(ns[0]):
+        xg, wx = splines.gauss_rule(p + 1, ex / ns[0], (ex + 1) / ns[0])
+        Bx, Dx = splines.bspline_derivs(knots[0], p, ex, xg, 0), splines.bspline_derivs(knots[0], p, ex, xg, 1)
+        sx = splines._element_span(knots[0], ex, ns[0]) - p
+        for ey in range(ns[1]):
+            yg, wy = splines.gauss_rule(p + 1, ey / ns[1], (ey + 1) / ns[1])
+            By, Dy = splines.bspline_derivs(knots[1], p, ey, yg, 0), splines.bspline_derivs(knots[1], p, ey, yg, 1)
+            sy = splines._element_span(knots[1], ey, ns[1]) - p
+            for gx in range(p + 1):
+                for gy in range(p + 1):
+                    C = coef(xg[gx], yg[gy])
+                    if kind == "scalar":
+                        C = C[0, 0] * np.eye(2)
+                    funcs = []
+                    for ix in range(p + 1):
+                        for iy in range(p + 1):
+                            gi, gj = sx + ix, sy + iy
+                            if gi in pos[0] and gj in pos[1]:
+                                grad = np.array([Dx[gx, ix] * By[gy, iy], Bx[gx, ix] * Dy[gy, iy]])
+                                funcs.append((pos[0][gi] + m[0] * pos[1][gj], grad))
+                    for r, gr in funcs:
+                        for c, gc in funcs:
+                            A[r, c] += wx[gx] * wy[gy] * gr @ C @ gc
+    axes = _axes(ns, p, dsets)
+    X = np.meshgrid(axes[1][0], axes[0][0], indexing="ij")  # (y, x) grids
+    Y, Xx = X[0], X[1]
+    if kind == "scalar":
+        Cq = (1.0 + Xx * Y * Y + np.sin(Xx + 2 * Y))[None]
+    else:
+        Cq = np.stack([1.2 + np.cos(3 * Xx * Y), 0.3 * np.sin(Xx + Y), 0.9 + Xx * Xx])
+    got = general.general_stiffness_dense(axes, Cq)
+    assert np.max(np.abs(got - A)) <= 1e-12 * np.max(np.abs(A))
