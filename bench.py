@@ -13,12 +13,15 @@ the exact Fast Diagonalization preconditioner (the comparator) and with the
 FP32-transform IFFD preconditioner; per-kernel device time from CUDA events
 recorded by the library on the launching stream during the timed region; SM
 clocks sampled by nvidia-smi during the timed region; an end-to-end number
-with host buffers; and the CPU oracle on a bounded sample.
+with host buffers; the GPU's FP64 and FP32 FMA rates (measured by the
+library's calibration kernel, the roofline denominators of the arithmetic-
+bound kernels); and the CPU oracle's own full PCG solve of the same problem.
 
 Multi-GPU: problems are independent, so N ranks solve N independent copies
 (replicas, weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --probe precond|stiffness|solve|general [--n 256 --p 4 ...]   (one operation, for ncu)
 """
 
 from __future__ import annotations
@@ -41,8 +44,6 @@ if ROOT not in sys.path:
 
 METRIC = "PCG-solved DoF/s at rel. res 1e-8, IGA-FFD vs exact FD on 1 GB300; % HBM peak"
 UNIT = "DoF/s"
-# FP64 ALU roofline: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz (max SM clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 SRC_FILES = {"precond": "paper_2512_20269_gb300/csrc/precond.cu",
              "stiff": "paper_2512_20269_gb300/csrc/stiffness.cu"}
 
@@ -165,11 +166,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(w, iters: int):
-    """Time the oracle (CPU, float64) on the full workload: the initial
-    preconditioner apply plus one full PCG iteration, extrapolated to `iters`
-    iterations. Setup of the 1D data is excluded (as for the GPU)."""
-    import numpy as np
+def _cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_oracle_solve(w):
+    """The oracle (CPU, float64, numpy/scipy) solving the same problem the GPU
+    solves: its own textbook PCG with its own IFFD preconditioner, zero start,
+    to the same relative residual 1e-8. The 1D setup (splitting and eigendata,
+    also excluded on the GPU) and the right-hand side are prepared before the
+    clock starts; the timed region is the whole PCG solve."""
     import scipy.sparse
 
     from oracle import operators, splitting
@@ -180,53 +186,70 @@ def cpu_oracle_sample(w, iters: int):
     MK = [(scipy.sparse.csr_matrix(s.M), scipy.sparse.csr_matrix(s.K))] * w.d
     f = inputs.workload_rhs(w)
     t0 = time.perf_counter()
-    r = f.copy()
-    z = operators.iffd_apply(r, splits)
-    p = z.copy()
-    rz = float(np.vdot(r, z))
-    t1 = time.perf_counter()
-    u = np.zeros_like(f)
-    q = operators.stiffness_apply(p, MK)
-    alpha = rz / float(np.vdot(p, q))
-    u += alpha * p
-    r -= alpha * q
-    _ = np.linalg.norm(r.ravel())
-    z = operators.iffd_apply(r, splits)
-    rz_new = float(np.vdot(r, z))
-    p = z + (rz_new / rz) * p
-    t2 = time.perf_counter()
-    t_solve = (t1 - t0) + iters * (t2 - t1)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": w.N / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle (numpy/scipy FP64) on the full {w.name} problem: initial preconditioner apply "
-                       f"({t1 - t0:.2f} s) + one PCG iteration ({t2 - t1:.2f} s) timed, extrapolated to "
-                       f"{iters} iterations; BLAS threads = all cores"),
-            "seconds_per_iteration": t2 - t1}
+    u, iters, hist = operators.pcg(f, lambda v: operators.stiffness_apply(v, MK),
+                                   lambda v: operators.iffd_apply(v, splits), rtol=1e-8)
+    sec = time.perf_counter() - t0
+    return {"value": w.N / sec, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": (f"full solve: the oracle's PCG (numpy/scipy FP64, IFFD preconditioner by dense Q~ per "
+                       f"direction) on the whole {w.name} problem ({w.N} DoFs), zero start to relative residual "
+                       f"1e-8, {iters} iterations, {sec:.2f} s; 1D setup excluded as on the GPU; BLAS threads = "
+                       f"all cores"),
+            "iters": int(iters), "rel_res": float(hist[-1]), "seconds": sec}
+
+
+def cpu_subcase_errors(sub, u_gpu: dict):
+    """Error of the GPU solves of the 64^3 subcase (n = 64, p = 4, 66^3 DoFs,
+    N(0,1) seed 1) against the oracle's exact solution A^{-1} f (its exact Fast
+    Diagonalization with dense generalized eigenvectors, which is A^{-1} on the
+    cube), and the oracle's own PCG iteration count there. u_gpu: {variant:
+    (u as numpy, iterations)}."""
+    import scipy.sparse
+
+    from oracle import operators, splitting
+    from paper_2512_20269_gb300 import inputs
+
+    s = splitting.axis_split(sub.n, sub.p, (0, 1))
+    f = inputs.workload_rhs(sub)
+    Q, lam = operators.exact_fd_eig(s.M, s.K)
+    u_ex = operators.exact_fd_apply(f, [(Q, lam)] * sub.d)
+    MK = [(scipy.sparse.csr_matrix(s.M), scipy.sparse.csr_matrix(s.K))] * sub.d
+    _, it_or, _ = operators.pcg(f, lambda v: operators.stiffness_apply(v, MK),
+                                lambda v: operators.iffd_apply(v, [s] * sub.d), rtol=1e-8)
+    nrm = float(np.linalg.norm(u_ex))
+    out = {"workload": sub.name, "N": sub.N, "oracle_pcg_iters": int(it_or),
+           "reference": "oracle exact-FD solve A^-1 f (dense generalized eigenvectors)"}
+    for name, (u, it) in u_gpu.items():
+        out[name] = {"iters": int(it), "rel_err_vs_oracle": float(np.linalg.norm(u - u_ex) / nrm),
+                     "max_rel_err_vs_oracle": float(np.abs(u - u_ex).max() / np.abs(u_ex).max())}
+    return out
 
 
 def run_reference(args, rank: int, world: int):
+    """Reference arm: the oracle as it stands, on the host cores. Each step is
+    one full oracle PCG solve of the 258^3 problem (cpu_oracle_solve)."""
     from paper_2512_20269_gb300 import inputs
     if rank != 0:
         return 0
     w = inputs.CUBE_N256_P4
-    iters = 5  # the FP64 oracle PCG takes 5 iterations on this workload (same as the GPU solve)
     for _ in range(args.warmup):
-        cpu_oracle_sample(w, iters)
-    vals = []
+        cpu_oracle_solve(w)
+    secs = []
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_oracle_sample(w, iters)
-        vals.append(last["value"])
+        last = cpu_oracle_solve(w)
+        secs.append(last["seconds"])
     wall = time.perf_counter() - t0
-    value = statistics.median(vals)
+    total = sum(secs)
+    value = w.N * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w.N / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w),
             "cpu_baseline": dict(last, value=value),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
+    line["cpu_baseline"].pop("seconds", None)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -286,20 +309,24 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
         coef = "const" if args.workload == "square" else "sin"
         f = torch.from_numpy(inputs.workload_rhs(w)).cuda()
         res = {}
-        for prec in ("fp64", "fp32"):
-            plan = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=False).autotune()
+        for prec, pc in (("fp64", "iffd"), ("fp32", "iffd"), ("exact_fd", "exact_fd")):
+            pr = "fp64" if prec == "exact_fd" else prec
+            plan = IFFDPlan(w.d, w.n, w.p, precision=pr, precond=pc, coef=coef, true_residual=False).autotune()
             u = plan.empty()
-            ms, (_, info) = _timed(lambda: plan.pcg_solve(f, u), args.steps, max(args.warmup, 1))
-            chk = IFFDPlan(w.d, w.n, w.p, precision=prec, coef=coef, true_residual=True).autotune()
+            reps = args.steps if pc == "iffd" else min(args.steps, 2)
+            ms, (_, info) = _timed(lambda: plan.pcg_solve(f, u), reps, 1 if pc != "iffd" else max(args.warmup, 1))
+            chk = IFFDPlan(w.d, w.n, w.p, precision=pr, precond=pc, coef=coef, true_residual=True).autotune()
             _, ic = chk.pcg_solve(f)
             res[prec] = {"value": w.N / (ms / 1e3), "ms_per_solve": ms, "iters": info["iters"],
                          "true_rel_res": ic["true_rel_res"]}
             del plan, chk
+            torch.cuda.empty_cache()
         line.update({"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_solve"], "dtype": "f64",
                      "config": {"workload": w.name, "d": w.d, "n": w.n, "p": w.p, "N": w.N,
                                 "coefficient": "1 + 0.5 prod sin(2 pi x_k)" if coef == "sin" else "1",
                                 "rhs": f"{w.dist} seed {w.seed}"},
-                     "variants": {"fp32_transform": res["fp32"]}, "fp64": res["fp64"]})
+                     "variants": {"fp32_transform": res["fp32"], "exact_fd": res["exact_fd"]},
+                     "fp64": res["fp64"]})
     elif args.workload == "batched":
         probs = inputs.batched_problems()
         systems = []
@@ -358,6 +385,49 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
     return 0
 
 
+def run_probe(args) -> int:
+    """One library operation on cuda:0 through the C ABI, for profilers (ncu):
+    the plan of (d, n, p) (optionally autotuned, or with the warp-FFT pass on
+    every eligible direction), the N(0,1) right-hand side of seed 1, and one
+    preconditioner apply, stiffness apply, PCG solve, or general-coefficient
+    stiffness apply (scalar a = 1 + sin(2 pi (x + 2y + 3z)) cos(pi x y) / 2 at
+    the Gauss points). Prints the launch geometry; not a benchmark."""
+    import torch
+
+    from paper_2512_20269_gb300 import IFFDError, IFFDPlan, _lib, inputs
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2512_20269_gb300 import build
+        build.build()
+    plan = IFFDPlan(args.d, args.n, args.p, precision=args.precision, coef=args.coef, true_residual=False)
+    if args.autotune:
+        plan.autotune()
+    if args.warp:
+        for k in range(args.d):
+            try:
+                plan.set_geometry(k, warp=True)
+            except IFFDError:
+                pass  # not eligible: block kernel
+    f = torch.from_numpy(inputs.rhs(plan.shape, "normal", 1)).cuda()
+    for _ in range(max(1, args.probe_reps)):
+        if args.probe == "precond":
+            plan.apply_preconditioner(f)
+        elif args.probe == "stiffness":
+            plan.apply_stiffness(f)
+        elif args.probe == "general":
+            xs = [torch.from_numpy(plan.quad_points(k)[0]).cuda() for k in range(args.d)]
+            g = torch.meshgrid(*reversed(xs), indexing="ij")[::-1]
+            X, Y = g[0], g[1]
+            Z = g[2] if args.d == 3 else torch.zeros_like(X)
+            coef = (1.0 + 0.5 * torch.sin(2 * math.pi * (X + 2 * Y + 3 * Z)) * torch.cos(math.pi * X * Y))[None]
+            plan.apply_stiffness_general(coef.contiguous(), f)
+        else:
+            _, info = plan.pcg_solve(f)
+            print("iters", info["iters"], "rel_res", info["rel_res"])
+    torch.cuda.synchronize()
+    print("ok", args.probe, "N", plan.N, [plan.tiles(k) for k in range(args.d)])
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,7 +444,19 @@ def main():
     ap.add_argument("--serve-iters", type=int, default=2, help="serving: PCG iterations per engine step")
     ap.add_argument("--serve-cap-dofs", type=int, default=0,
                     help="serving: cap on the DoFs in flight (0 = HBM budget only)")
+    ap.add_argument("--probe", choices=["precond", "stiffness", "solve", "general"], default=None,
+                    help="run one library operation once (for ncu) instead of the benchmark")
+    ap.add_argument("--d", type=int, default=3, help="--probe: dimension")
+    ap.add_argument("--n", type=int, default=256, help="--probe: elements per direction")
+    ap.add_argument("--p", type=int, default=4, help="--probe: degree")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64", help="--probe: transform precision")
+    ap.add_argument("--coef", choices=["const", "sin"], default="const", help="--probe: coefficient")
+    ap.add_argument("--autotune", action="store_true", help="--probe: autotune the plan first")
+    ap.add_argument("--warp", action="store_true", help="--probe: warp-FFT pass on every eligible direction")
+    ap.add_argument("--probe-reps", type=int, default=1, help="--probe: repetitions of the operation")
     args = ap.parse_args()
+    if args.probe:
+        return run_probe(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -402,6 +484,14 @@ def main():
             dist.barrier()
 
     w = inputs.CUBE_N256_P4
+    # roofline denominators of the arithmetic-bound kernels, measured on this
+    # GPU by the library's FMA-chain calibration kernel (not timed)
+    from paper_2512_20269_gb300 import measure_peak
+    pk64 = measure_peak("fp64")
+    pk32 = measure_peak("fp32")
+    fp64_peak = pk64["tflops"]
+    peak_src = (f"measured: iffd_measure_peak FP64 FMA chains on {pk64['sm_count']} SMs (cudaDeviceGetAttribute), "
+                f"best of 3 CUDA-event-timed launches")
     # setup (excluded from timing): plan, then the launch-geometry autotuner
     plan = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=False).autotune()
     f_host = torch.from_numpy(inputs.workload_rhs(w))
@@ -459,8 +549,8 @@ def main():
             avg_s = kms / n_eff / 1e3
             if unit == "flop":
                 ach = amount / avg_s / 1e12
-                entry.update({"bound": bound, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": ach / FP64_PEAK_TFLOPS, "alg_per_launch": amount})
+                entry.update({"bound": bound, "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": ach / fp64_peak, "alg_per_launch": amount})
             else:
                 ach = amount / avg_s / 1e9
                 entry.update({"bound": bound, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -470,8 +560,7 @@ def main():
     d = rooflines[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": ncu_traffic(dom), "kernel": dom,
-                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz" if d["bound"] == "alu"
-                                else "MEASURED_PEAKS.json hbm_gbs")}
+                "peak_source": (peak_src if d["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (measured copy)")}
 
     # ---------------- end to end: pinned host f -> device, solve, u -> host
     f_pin = f_host.pin_memory()
@@ -576,7 +665,7 @@ def main():
             "config": {"workload": f"cube n=128 p={w.p}, a = 1 + sin(2 pi (x + 2y + 3z)) cos(pi x y) / 2",
                        "dofs": pg.N, "gauss_points": int(coef.numel())},
             "apply_ms": gms, "apply_alg_bytes": gbytes, "apply_hbm_frac": gbytes / (gms / 1e3) / 1e9 / hbm_peak,
-            "apply_gflop": gflop, "apply_fp64_tflops": gflop / gms, "apply_fp64_frac": gflop / gms / FP64_PEAK_TFLOPS,
+            "apply_gflop": gflop, "apply_fp64_tflops": gflop / gms, "apply_fp64_frac": gflop / gms / fp64_peak,
             "ms_per_solve": sms, "value": pg.N / (sms / 1e3), "unit": UNIT, "iters": ig["iters"],
             "true_rel_res": ig["true_rel_res"]}
         del pg, coef, fg, ug, xs
@@ -610,13 +699,32 @@ def main():
                                  "tiles": [pa.tiles(k) for k in range(w.d)]}
             del pa, zz
 
+    # ---------------- the 64^3 subcase (n = 64, p = 4): FP64 and FP32-transform
+    # solves on the GPU, compared with the oracle's exact solution below
+    sub = inputs.CUBE_N64_P4
+    sub_u = {}
+    fs = torch.from_numpy(inputs.workload_rhs(sub)).cuda()
+    for name, prec in (("fp64", "fp64"), ("fp32_transform", "fp32")):
+        ps = IFFDPlan(sub.d, sub.n, sub.p, precision=prec, true_residual=False)
+        us, isub = ps.pcg_solve(fs)
+        sub_u[name] = (us.cpu().numpy(), isub["iters"])
+        del ps
+    del fs
+
     cpu = None
+    subcase = None
     if rank == 0 and not args.no_cpu_baseline:
+        # cpu_baseline leg: the oracle's own full solve of the headline problem,
+        # and the oracle's exact solution of the subcase
         try:
-            cpu = cpu_oracle_sample(w, iters)
-            cpu.pop("seconds_per_iteration", None)
+            cpu = cpu_oracle_solve(w)
+            cpu.pop("seconds", None)
         except Exception as exc:  # report, never fail the bench line
-            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {exc}"}
+            cpu = {"value": None, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": f"failed: {exc}"}
+        try:
+            subcase = cpu_subcase_errors(sub, sub_u)
+        except Exception as exc:
+            subcase = {"failed": str(exc)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -627,7 +735,9 @@ def main():
                 "tiles": [plan.tiles(a) for a in range(w.d)],
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clk,
                 "variants": variants, "precond_apply": apply_stats, "kernels": rooflines,
-                "hbm_frac_of_solve": None}
+                "hbm_frac_of_solve": None, "subcase_64": subcase,
+                "peaks": {"fp64_fma_tflops": fp64_peak, "fp32_fma_tflops": pk32["tflops"],
+                          "sm_count": pk64["sm_count"], "hbm_gbs": hbm_peak}}
         # fraction of HBM peak of the whole solve at the method's algorithmic traffic
         # (176 B/DoF per PCG iteration: 96 preconditioner + 32 stiffness with the
         # direction update + 48 for the x, r update; 96 for the initial apply)

@@ -237,22 +237,26 @@ int iffd_apply_preconditioner(iffd_handle h, const double* r, double* z, void* w
 int iffd_apply_stiffness(iffd_handle h, const double* u, double* Au, void* ws, void* stream);
 
 /* Allocation-free variant of iffd_apply_stiffness (the paper has no
- * counterpart: it exists for callers that cannot allocate device memory when
- * they need A^ u -- code running while its stream is captured into a CUDA
- * graph, latency-critical loops that must avoid cudaMalloc's implicit
- * synchronisation, frameworks whose allocator owns all device memory, or
- * callers with a device-memory budget fixed at start-up).
+ * counterpart). It exists for callers that cannot allocate device memory at
+ * the point where they need A^ u: a host framework whose caching allocator
+ * owns all device memory and allows no side allocations, an embedded solver
+ * with a device-memory budget fixed at start-up, or a latency-critical loop
+ * that must not pay the implicit device synchronisation of cudaMalloc.
  * Same result as iffd_apply_stiffness(h, u, Au, ws, stream) for plans with
  * IFFD_COEF_CONST (other plans are rejected with IFFD_ERR_UNSUPPORTED), without a
  * workspace: the two N-vector temporaries live in a static device array of
  * 2 * IFFD_NOALLOC_MAX_DOFS doubles (16 MiB) inside the library, which every
  * GPU that loads the library's module holds until the process exits. The call
  * itself allocates nothing (no cudaMalloc / cudaFree).
- * - Plans with N > IFFD_NOALLOC_MAX_DOFS are rejected with
- *   IFFD_ERR_UNSUPPORTED and a message naming the limit.
+ * - The checks run in the order of iffd_apply_stiffness (arguments, plan
+ *   device, coefficient kind), then the size limit: plans with
+ *   N > IFFD_NOALLOC_MAX_DOFS are rejected with IFFD_ERR_UNSUPPORTED and a
+ *   message naming the limit.
  * - The first call on each device resolves the array's device address
- *   (cudaGetSymbolAddress, with that device current) and caches it; make that
- *   first call before any stream capture.
+ *   (cudaGetSymbolAddress, with that device current) and caches it with the
+ *   CUDA context it belongs to; make that first call before any stream
+ *   capture. A call that finds a different context current on the device
+ *   (after cudaDeviceReset) resolves the address again.
  * - Every call shares the one array, so calls that overlap on the GPU (other
  *   streams, other plans, other host threads) race: order them on one stream
  *   or synchronise between them. The array keeps the last call's contents;
@@ -402,6 +406,47 @@ int iffd_engine_poll(iffd_engine_handle e, iffd_completion* out, int capacity, i
 /* Active requests, free arena bytes, kernels launched so far (any may be NULL). */
 int iffd_engine_stats(iffd_engine_handle e, int* active, size_t* bytes_free, long long* kernel_launches);
 int iffd_engine_destroy(iffd_engine_handle e);
+
+/* ---------------------------------------------------------------------------
+ * Batched solve of many systems in one call: PCG of Section 3 with the IFFD
+ * preconditioner of eq. "preconditioner" (or the plan's own preconditioner),
+ * for `count` plans, plan i with nrhs[i] right-hand sides. System (i, j),
+ * j < nrhs[i], solves A_i u = f with f = f[i] + j N_i and writes u[i] + j N_i
+ * (N_i the plan's DoF count): f[i] and u[i] are caller-owned DEVICE arrays of
+ * nrhs[i] * N_i float64, right-hand side after right-hand side, x fastest
+ * within each; u is output only (zero start). The right-hand sides of one plan
+ * share that plan's device tables (no copy per right-hand side).
+ * ws: caller-owned device workspace of iffd_batch_workspace_bytes() bytes,
+ * 256-byte aligned (one plan workspace per system, in (i, j) order).
+ * infos: HOST array of sum_i nrhs[i] entries, filled in (i, j) order (iters,
+ * rel_res, status; true_rel_res when the plan's options ask for it, else -1).
+ * Systems of IFFD-preconditioned constant-coefficient plans advance together
+ * through the batched launches of the engine (below), one set of launches per
+ * phase for all of them, grouped by the plans' solve options; the kernels,
+ * tiles and reduction order of each system are those of iffd_pcg_solve on its
+ * plan, so every u equals (bitwise) iffd_pcg_solve's on the same plan. Other
+ * plans (exact FD, variable coefficient, FP64 warp-FFT geometry) are solved by
+ * iffd_pcg_solve one after the other on their slice of ws. Waits for the work
+ * already on `stream` and returns after every system has finished (the
+ * batched part runs on library streams; it allocates small descriptor
+ * buffers and a CUDA graph). Returns IFFD_OK if every system converged, else
+ * the status of the first system (in (i, j) order) that did not (every info is
+ * still filled), or an argument / workspace / CUDA error (INVALID_ARG: NULL or
+ * aliasing arrays, negative counts, a plan of another device). The paper
+ * solves one system at a time and has no batched counterpart. */
+int iffd_batch_workspace_bytes(int count, const iffd_handle* plans, const int* nrhs, size_t* bytes);
+int iffd_batch_solve(int count, const iffd_handle* plans, const double* const* f, double* const* u, const int* nrhs,
+                     void* ws, void* stream, iffd_pcg_info* infos);
+
+/* Measures the arithmetic rate of the current GPU for the roofline of the
+ * compute-bound kernels (the paper prints no timings and has no counterpart):
+ * kind 0 = FP64 fused multiply-add, kind 1 = FP32 fused multiply-add. Every
+ * thread of a grid of 4 CTAs x 256 threads per SM runs eight independent FMA
+ * chains; *tflops receives 2 x FMAs / the best of three CUDA-event times
+ * (~40 ms each) in TFLOP/s, *sm_count (may be NULL) the SM count read from the
+ * device. Runs on `stream` and synchronises it; allocates and frees a few KB.
+ * Errors: INVALID_ARG (kind, NULL tflops), CUDA. */
+int iffd_measure_peak(int kind, void* stream, int* sm_count, double* tflops);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* iffd_last_error(void);

@@ -19,7 +19,8 @@ PRECISION = {"fp64": 0, "fp32": 1}
 PRECOND = {"iffd": 0, "exact_fd": 1, "none": 2}
 COEF = {"const": 0, "sin": 1}
 
-__all__ = ["IFFDPlan", "IFFDEngine", "IFFDError", "host_axis", "PRECISION", "PRECOND"]
+__all__ = ["IFFDPlan", "IFFDEngine", "IFFDError", "batch_solve", "host_axis", "measure_peak", "PRECISION",
+           "PRECOND"]
 
 
 def _ptr(t) -> int:
@@ -97,6 +98,16 @@ def host_quad_axis(n: int, p: int, dirichlet=(1, 1), rep=None) -> dict:
     out["B"] = out["B"].reshape(nq, m)
     out["D"] = out["D"].reshape(nq, m)
     return out
+
+
+def measure_peak(kind: str = "fp64", stream=None) -> dict:
+    """FMA rate of the current GPU (iffd_measure_peak): kind "fp64" or "fp32";
+    returns {"tflops": ..., "sm_count": ...}."""
+    lib = _lib.load()
+    sms, tf = ctypes.c_int(), ctypes.c_double()
+    check(lib.iffd_measure_peak({"fp64": 0, "fp32": 1}[kind], _stream_handle(stream), ctypes.byref(sms),
+                                ctypes.byref(tf)), "iffd_measure_peak")
+    return {"tflops": tf.value, "sm_count": sms.value}
 
 
 class IFFDPlan:
@@ -358,6 +369,45 @@ class IFFDPlan:
             self.close()
         except Exception:
             pass
+
+
+def batch_solve(plans, fs, us=None, stream=None, raise_on_error: bool = True):
+    """iffd_batch_solve: plans[i] with the right-hand sides fs[i] (a float64
+    CUDA tensor of nrhs_i * N_i entries, right-hand side after right-hand side;
+    nrhs_i = numel / N_i). Returns (us, infos): us[i] like fs[i], infos a list
+    (in (i, j) order) of dicts as IFFDPlan.pcg_solve returns them."""
+    import torch
+    lib = _lib.load()
+    count = len(plans)
+    if len(fs) != count:
+        raise ValueError("one right-hand-side tensor per plan")
+    nrhs = []
+    for pl, f in zip(plans, fs):
+        if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+                and f.numel() % pl.N == 0):
+            raise ValueError("fs[i] must be a contiguous float64 CUDA tensor of nrhs * N entries")
+        nrhs.append(f.numel() // pl.N)
+    if us is None:
+        us = [torch.empty_like(f) for f in fs]
+    for f, u in zip(fs, us):
+        if not (u.is_cuda and u.dtype == torch.float64 and u.is_contiguous() and u.numel() == f.numel()):
+            raise ValueError("us[i] must match fs[i]")
+    harr = (ctypes.c_void_p * max(1, count))(*[pl._h.value for pl in plans])
+    narr = (ctypes.c_int * max(1, count))(*nrhs)
+    nb = ctypes.c_size_t()
+    check(lib.iffd_batch_workspace_bytes(count, harr, narr, ctypes.byref(nb)), "iffd_batch_workspace_bytes")
+    ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+    wsp = (_ptr(ws) + 255) // 256 * 256
+    farr = (ctypes.c_void_p * max(1, count))(*[_ptr(f) for f in fs])
+    uarr = (ctypes.c_void_p * max(1, count))(*[_ptr(u) for u in us])
+    nsys = sum(nrhs)
+    infos = (iffd_pcg_info * max(1, nsys))()
+    rc = lib.iffd_batch_solve(count, harr, farr, uarr, narr, wsp, _stream_handle(stream), infos)
+    if raise_on_error:
+        check(rc, "iffd_batch_solve")
+    out = [{"iters": infos[k].iters, "rel_res": infos[k].rel_res, "true_rel_res": infos[k].true_rel_res,
+            "status": infos[k].status} for k in range(nsys)]
+    return us, out
 
 
 class IFFDEngine:

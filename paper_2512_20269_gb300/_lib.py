@@ -94,6 +94,12 @@ SIGNATURES = [
     ("iffd_engine_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(iffd_completion), ctypes.c_int, c_int_p]),
     ("iffd_engine_stats", ctypes.c_int, [ctypes.c_void_p, c_int_p, c_size_t_p, ctypes.POINTER(ctypes.c_longlong)]),
     ("iffd_engine_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("iffd_batch_workspace_bytes", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), c_int_p,
+                                                  c_size_t_p]),
+    ("iffd_batch_solve", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), c_int_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(iffd_pcg_info)]),
+    ("iffd_measure_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, c_int_p, c_double_p]),
     ("iffd_last_error", ctypes.c_char_p, []),
 ]
 

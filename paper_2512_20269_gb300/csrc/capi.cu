@@ -854,7 +854,38 @@ int plan_stiffness_with_scratch(iffd_handle h, const double* u, double* Au, doub
   return IFFD_OK;
 }
 
+int plan_check_noalloc(iffd_handle h) {
+  const Plan* P = &h->P;
+  int rc = check_device(P);
+  if (rc) return rc;
+  if (P->opt.coef != IFFD_COEF_CONST)
+    return fail(IFFD_ERR_UNSUPPORTED, "iffd_apply_stiffness_noalloc: only IFFD_COEF_CONST plans are supported");
+  return IFFD_OK;
+}
+
 long long plan_num_dofs(iffd_handle h) { return h->P.dims.N; }
+
+// ||f - A u|| / ||f|| of a finished solve, with the kernels of iffd_pcg_solve's
+// exit check, on the plan's workspace ws (its solve state is overwritten).
+int plan_true_residual(iffd_handle h, const double* f, const double* u, void* ws, cudaStream_t st, double* out) {
+  const Plan* P = &h->P;
+  const long long N = P->dims.N;
+  double* q = reinterpret_cast<double*>(wsb(ws, P->off_q));
+  double* part = reinterpret_cast<double*>(wsb(ws, P->off_part));
+  SolveState* S = reinterpret_cast<SolveState*>(wsb(ws, P->off_state));
+  const double tol2 = P->opt.rtol * P->opt.rtol;
+  IFFD_LAUNCH(P, IFFD_K_VECTOR, st, (dot_kernel<<<vec_grid(N), kThreads, 0, st>>>(f, f, N, part, nullptr),
+                                     cudaGetLastError()));
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_FF, tol2, P->opt.maxit, st));
+  int rc = run_stiffness(P, u, nullptr, nullptr, nullptr, 0, q, ws, st, nullptr, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  IFFD_LAUNCH(P, IFFD_K_VECTOR, st, launch_residual(f, q, N, part, st));
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_TRUE, tol2, P->opt.maxit, st));
+  IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  IFFD_CUDA(cudaStreamSynchronize(st));
+  *out = P->host_state->ff > 0.0 ? std::sqrt(P->host_state->zq / P->host_state->ff) : 0.0;
+  return IFFD_OK;
+}
 
 int record_error(int code, const std::string& msg) { return fail(code, msg); }
 

@@ -652,6 +652,13 @@ struct iffd_engine {
   Engine E;
 };
 
+namespace iffd {
+// One engine step (iffd_engine_step without the handle): initialise the
+// admitted systems, run `iterations` PCG iterations of every active system,
+// retire the finished ones.
+int engine_step(Engine& E, int iterations, int* active);
+}  // namespace iffd
+
 extern "C" {
 
 int iffd_engine_create(const iffd_options* opt, size_t budget_bytes, void* stream, iffd_engine_handle* out) {
@@ -758,7 +765,14 @@ int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const int* dir
 
 int iffd_engine_step(iffd_engine_handle h, int iterations, int* active) {
   if (!h || iterations < 0) return fail(IFFD_ERR_INVALID_ARG, "bad argument");
-  Engine& E = h->E;
+  return engine_step(h->E, iterations, active);
+}
+
+}  // extern "C"
+
+namespace iffd {
+
+int engine_step(Engine& E, int iterations, int* active) {
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != E.device) return fail(IFFD_ERR_INVALID_ARG, "engine was created on another device");
@@ -826,6 +840,10 @@ int iffd_engine_step(iffd_engine_handle h, int iterations, int* active) {
   return IFFD_OK;
 }
 
+}  // namespace iffd
+
+extern "C" {
+
 int iffd_engine_poll(iffd_engine_handle h, iffd_completion* out, int capacity, int* count) {
   if (!h || !count || (capacity > 0 && !out)) return fail(IFFD_ERR_INVALID_ARG, "bad argument");
   Engine& E = h->E;
@@ -848,6 +866,181 @@ int iffd_engine_destroy(iffd_engine_handle h) {
   if (!h) return IFFD_OK;
   cudaStreamSynchronize(h->E.st);
   delete h;
+  return IFFD_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batch solve
+// iffd_batch_solve: the systems (plan i, right-hand side j < nrhs[i]) of one
+// call run through the engine's batched launches, over the caller's plans and
+// the caller's workspace. Systems whose plans the engine's kernels cannot run
+// exactly as iffd_pcg_solve would (another preconditioner or coefficient, or
+// an FP64 plan set to the FP64 warp-FFT pass) are solved one by one with
+// iffd_pcg_solve on their slice of the same workspace. Every result is
+// therefore that of iffd_pcg_solve on the same plan.
+
+namespace iffd {
+
+int plan_true_residual(iffd_handle h, const double* f, const double* u, void* ws, cudaStream_t st, double* out);
+
+namespace {
+
+bool engine_runs_exactly(const Plan& P) {
+  if (P.opt.precond != IFFD_PRECOND_IFFD || P.opt.coef != IFFD_COEF_CONST) return false;
+  if (P.opt.precision == IFFD_PREC_FP64)
+    for (int a = 0; a < P.d; ++a)
+      if (f64_warp_len(P, a)) return false;
+  return true;
+}
+
+// Engine options of a plan's systems: the solve options that the engine
+// applies to all systems of one engine.
+std::tuple<int, int, double, int> engine_key(const Plan& P) {
+  const int flex = (P.opt.flexible || P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? 1 : 0;
+  return std::make_tuple(P.opt.precision, flex, P.opt.rtol, P.opt.maxit);
+}
+
+int batch_check(int count, const iffd_handle* plans, const int* nrhs) {
+  if (count < 0 || (count > 0 && (!plans || !nrhs))) return fail(IFFD_ERR_INVALID_ARG, "bad count or NULL array");
+  int dev = -1;
+  IFFD_CUDA(cudaGetDevice(&dev));
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i]) return fail(IFFD_ERR_INVALID_ARG, "NULL plan in the batch");
+    if (nrhs[i] < 0) return fail(IFFD_ERR_INVALID_ARG, "negative right-hand-side count");
+    if (plans[i]->P.device != dev) return fail(IFFD_ERR_INVALID_ARG, "a plan was created on another CUDA device");
+  }
+  return IFFD_OK;
+}
+
+}  // namespace
+}  // namespace iffd
+
+extern "C" {
+
+int iffd_batch_workspace_bytes(int count, const iffd_handle* plans, const int* nrhs, size_t* bytes) {
+  g_err.clear();
+  if (!bytes) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
+  int rc = batch_check(count, plans, nrhs);
+  if (rc) return rc;
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) total += (size_t)nrhs[i] * al256(plans[i]->P.ws_bytes);
+  *bytes = total;
+  return IFFD_OK;
+}
+
+int iffd_batch_solve(int count, const iffd_handle* plans, const double* const* f, double* const* u, const int* nrhs,
+                     void* ws, void* stream, iffd_pcg_info* infos) {
+  g_err.clear();
+  int rc = batch_check(count, plans, nrhs);
+  if (rc) return rc;
+  long long nsys = 0;
+  for (int i = 0; i < count; ++i) {
+    if (nrhs[i] > 0 && (!f || !u || !f[i] || !u[i])) return fail(IFFD_ERR_INVALID_ARG, "NULL right-hand side or solution");
+    if (nrhs[i] > 0 && f[i] == u[i]) return fail(IFFD_ERR_INVALID_ARG, "f[i] and u[i] must not alias");
+    nsys += nrhs[i];
+  }
+  if (nsys == 0) return IFFD_OK;
+  if (!infos) return fail(IFFD_ERR_INVALID_ARG, "NULL infos");
+  if (!ws) return fail(IFFD_ERR_WORKSPACE, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(IFFD_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  size_t total = 0;
+  iffd_batch_workspace_bytes(count, plans, nrhs, &total);
+
+  // every system: its plan, right-hand side, solution and workspace slice
+  struct Item {
+    iffd_plan* plan;
+    const double* f;
+    double* u;
+    char* ws;
+    size_t off, bytes;
+    long long slot;  // index into infos
+  };
+  std::vector<Item> items;
+  {
+    size_t off = 0;
+    long long slot = 0;
+    for (int i = 0; i < count; ++i) {
+      const long long N = plans[i]->P.dims.N;
+      const size_t b = al256(plans[i]->P.ws_bytes);
+      for (int j = 0; j < nrhs[i]; ++j, ++slot) {
+        items.push_back({plans[i], f[i] + (size_t)j * N, u[i] + (size_t)j * N, base + off, off, b, slot});
+        off += b;
+      }
+    }
+  }
+  for (long long k = 0; k < nsys; ++k) infos[k] = iffd_pcg_info{0, 0.0, -1.0, IFFD_OK};
+
+  // engine groups (one engine per set of solve options); the rest one by one
+  std::map<std::tuple<int, int, double, int>, std::vector<const Item*>> groups;
+  std::vector<const Item*> alone;
+  for (const Item& it : items) {
+    if (engine_runs_exactly(it.plan->P)) groups[engine_key(it.plan->P)].push_back(&it);
+    else alone.push_back(&it);
+  }
+  for (auto& kv : groups) {
+    Engine E;
+    iffd_default_options(&E.opt);
+    E.opt.precision = std::get<0>(kv.first);
+    E.opt.flexible = std::get<1>(kv.first);
+    E.opt.rtol = std::get<2>(kv.first);
+    E.opt.maxit = std::get<3>(kv.first);
+    E.user_st = st;
+    IFFD_CUDA(cudaGetDevice(&E.device));
+    IFFD_CUDA(cudaStreamCreateWithFlags(&E.st, cudaStreamNonBlocking));
+    IFFD_CUDA(cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming));
+    IFFD_CUDA(cudaEventCreateWithFlags(&E.fork_ev, cudaEventDisableTiming));
+    // the arena bookkeeping spans the caller's workspace and hands every
+    // system of the group its slice laid out above (E.arena_mem stays null:
+    // the engine frees nothing of the caller's)
+    E.arena.init(base, total);
+    for (const Item& it : items) {
+      size_t off = 0;
+      if (!E.arena.alloc(it.bytes, &off) || off != it.off) return fail(IFFD_ERR_WORKSPACE, "batch workspace layout");
+    }
+    std::map<long long, const Item*> by_id;
+    for (const Item* it : kv.second) {
+      Sys s{};
+      s.id = E.next_id++;
+      s.plan = it->plan;
+      s.f = it->f;
+      s.u = it->u;
+      s.off = it->off;
+      s.bytes = it->bytes;
+      s.ws = it->ws;
+      s.phase = 0;
+      E.active.push_back(s);
+      by_id[s.id] = it;
+    }
+    int active = (int)E.active.size();
+    while (active > 0) {
+      rc = engine_step(E, 4, &active);
+      if (rc) return rc;
+    }
+    for (const iffd_completion& c : E.done_list) infos[by_id[c.id]->slot] = c.info;
+  }
+  for (const Item* it : alone) {
+    iffd_pcg_info info{};
+    rc = iffd_pcg_solve(it->plan, it->f, it->u, it->ws, stream, &info);
+    if (rc != IFFD_OK && rc != IFFD_ERR_NOT_CONVERGED && rc != IFFD_ERR_BREAKDOWN) return rc;
+    infos[it->slot] = info;
+  }
+  // true residuals where the plan asks for them (as iffd_pcg_solve reports them)
+  for (const Item& it : items) {
+    if (!it.plan->P.opt.true_residual || !engine_runs_exactly(it.plan->P)) continue;
+    double tr = -1.0;
+    rc = plan_true_residual(it.plan, it.f, it.u, it.ws, st, &tr);
+    if (rc) return rc;
+    infos[it.slot].true_rel_res = tr;
+  }
+  g_err.clear();
+  for (long long k = 0; k < nsys; ++k)
+    if (infos[k].status != IFFD_OK)
+      return fail(infos[k].status, "system " + std::to_string(k) + " of the batch: " +
+                                       (infos[k].status == IFFD_ERR_NOT_CONVERGED ? "PCG did not reach rtol within maxit"
+                                                                                  : "PCG breakdown"));
   return IFFD_OK;
 }
 

@@ -6,27 +6,34 @@
 //
 // One launch contracts all pencils along one direction with A = Q^T (FWD) or
 // A = Q (BWD); FUSED does Q^T, the eigenvalue scaling and Q on the last
-// direction. A CTA holds 32 pencils in shared memory and computes the
-// 128 x 32 output blocks of C = A B with a 4 x 4 register block per thread,
-// staging 32-column slabs of A through shared memory. FP64 FMA throughput
-// bounds it.
+// direction. A CTA holds PP pencils in shared memory (32, or 16 where two
+// tiles of 32 pencils would not fit: m > ~340) and computes the
+// (4 * 256 / (PP / 4)) x PP output blocks of C = A B with a 4 x 4 register
+// block per thread, staging 32-column slabs of A through shared memory. FP64
+// FMA throughput bounds it.
 #include "device_common.cuh"
 #include "kernels.h"
 #include "fd.h"
 
 namespace iffd {
 
-constexpr int kFdPP = 32;   // pencils per CTA
-constexpr int kFdBI = 128;  // output rows per block
-constexpr int kFdBJ = 32;   // A slab width
+constexpr int kFdBJ = 32;  // A slab width
+// output rows per block for PP pencils per CTA (PP / 4 pencil groups of 4)
+template <int PP>
+__host__ __device__ constexpr int fd_bi() {
+  return 4 * (kThreads / (PP / 4));
+}
 
 // C[i][pc] = sum_j A[i][j] * B[pc][j] for the tile (B rows = pencils), in place
 // into Cout (separate smem array).
+template <int PP>
 __device__ void fd_contract(const double* __restrict__ A, int m, const double* Bt, int ldb, double* Ct,
                             double* As) {
+  constexpr int kFdBI = fd_bi<PP>();
+  constexpr int TP = PP / 4;
   const int tid = threadIdx.x;
-  const int ti = tid >> 3;        // 0..31 -> rows 4*ti .. 4*ti+3
-  const int tp = tid & 7;         // 0..7  -> pencils 4*tp .. 4*tp+3
+  const int ti = tid / TP;        // rows 4*ti .. 4*ti+3
+  const int tp = tid % TP;        // pencils 4*tp .. 4*tp+3
   for (int i0 = 0; i0 < m; i0 += kFdBI) {
     double acc[4][4];
 #pragma unroll
@@ -67,7 +74,7 @@ __device__ void fd_contract(const double* __restrict__ A, int m, const double* B
   __syncthreads();
 }
 
-template <int MODE>
+template <int MODE, int kFdPP>
 __global__ void __launch_bounds__(kThreads)
 fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const double* __restrict__ QT,
         const double* __restrict__ Q, const double* __restrict__ lam, const double* __restrict__ lamA,
@@ -91,7 +98,7 @@ fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const doubl
   __syncthreads();
   double* res = B;
   if (MODE == PM_FWD || MODE == PM_FUSED) {
-    fd_contract(QT, m, B, ldb, C, As);
+    fd_contract<kFdPP>(QT, m, B, ldb, C, As);
     res = C;
   }
   if (MODE == PM_FUSED) {
@@ -103,11 +110,11 @@ fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const doubl
       C[pc * ldb + i] = C[pc * ldb + i] / den;
     }
     __syncthreads();
-    fd_contract(Q, m, C, ldb, B, As);
+    fd_contract<kFdPP>(Q, m, C, ldb, B, As);
     res = B;
   }
   if (MODE == PM_BWD) {
-    fd_contract(Q, m, B, ldb, C, As);
+    fd_contract<kFdPP>(Q, m, B, ldb, C, As);
     res = C;
   }
   for (int e = threadIdx.x; e < kFdPP * m; e += blockDim.x) {
@@ -118,35 +125,47 @@ fd_pass(const double* in, double* out, Dims dims, int axis, int ldb, const doubl
   }
 }
 
-int fd_tiles(const Dims& dims, int axis) { return (int)host_num_tiles(dims, axis, kFdPP); }
-
-size_t fd_smem(int m) {
+static size_t fd_smem_pp(int m, int PP) {
   const int ldb = m | 1;
-  return (size_t)2 * kFdPP * ldb * sizeof(double) + (size_t)kFdBJ * (kFdBI + 1) * sizeof(double);
+  const int bi = 4 * (kThreads / (PP / 4));
+  return (size_t)2 * PP * ldb * sizeof(double) + (size_t)kFdBJ * (bi + 1) * sizeof(double);
+}
+
+// 32 pencils per CTA while two tiles fit in 200 KB of shared memory, else 16
+static int fd_pp(int m) { return fd_smem_pp(m, 32) <= 200 * 1024 ? 32 : 16; }
+
+int fd_tiles(const Dims& dims, int axis) {
+  return (int)host_num_tiles(dims, axis, fd_pp(dims.m[axis]));
+}
+
+size_t fd_smem(int m) { return fd_smem_pp(m, fd_pp(m)); }
+
+template <int MODE, int PP>
+static cudaError_t launch_fd_t(const double* in, double* out, const Dims& dims, int axis, const double* QT,
+                               const double* Q, const double* lam, const double* lamA, const double* lamB,
+                               const int* done, cudaStream_t st) {
+  const int m = dims.m[axis];
+  const int ldb = m | 1;
+  const size_t sm = fd_smem_pp(m, PP);
+  const int tiles = (int)host_num_tiles(dims, axis, PP);
+  cudaError_t e = cudaFuncSetAttribute(fd_pass<MODE, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  fd_pass<MODE, PP><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fd_pass(int mode, const double* in, double* out, const Dims& dims, int axis,
                            const double* QT, const double* Q, const double* lam, const double* lamA,
                            const double* lamB, const int* done, cudaStream_t st) {
-  const int m = dims.m[axis];
-  const int ldb = m | 1;
-  const size_t sm = fd_smem(m);
-  const int tiles = fd_tiles(dims, axis);
-  cudaError_t e;
-  if (mode == PM_FWD) {
-    e = cudaFuncSetAttribute(fd_pass<PM_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    fd_pass<PM_FWD><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
-  } else if (mode == PM_BWD) {
-    e = cudaFuncSetAttribute(fd_pass<PM_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    fd_pass<PM_BWD><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
-  } else {
-    e = cudaFuncSetAttribute(fd_pass<PM_FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    fd_pass<PM_FUSED><<<tiles, kThreads, sm, st>>>(in, out, dims, axis, ldb, QT, Q, lam, lamA, lamB, done);
-  }
-  return cudaGetLastError();
+  const bool big = fd_pp(dims.m[axis]) == 16;
+  if (mode == PM_FWD)
+    return big ? launch_fd_t<PM_FWD, 16>(in, out, dims, axis, QT, Q, lam, lamA, lamB, done, st)
+               : launch_fd_t<PM_FWD, 32>(in, out, dims, axis, QT, Q, lam, lamA, lamB, done, st);
+  if (mode == PM_BWD)
+    return big ? launch_fd_t<PM_BWD, 16>(in, out, dims, axis, QT, Q, lam, lamA, lamB, done, st)
+               : launch_fd_t<PM_BWD, 32>(in, out, dims, axis, QT, Q, lam, lamA, lamB, done, st);
+  return big ? launch_fd_t<PM_FUSED, 16>(in, out, dims, axis, QT, Q, lam, lamA, lamB, done, st)
+             : launch_fd_t<PM_FUSED, 32>(in, out, dims, axis, QT, Q, lam, lamA, lamB, done, st);
 }
 
 }  // namespace iffd

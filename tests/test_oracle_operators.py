@@ -158,6 +158,41 @@ def test_p12_prop1_condition_bound(p):
     assert abs(kl - kap) <= 1e-6 * kap
 
 
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
+def test_kappa_lanczos_bounded_in_h_and_p(p):
+    """Theorem 1 / Proposition 1 / Table "tab:square": kappa(P^{-1} A^) of the
+    2D tensor system, found by Lanczos, stays below the Proposition 1 bound of
+    the 1D pencil (K, K~), does not grow as h = 1/n shrinks (n = 16, 32, 64),
+    and stays bounded uniformly in p (it is 1 for p = 2, where IFFD is exact)."""
+    kap = []
+    for n in (16, 32, 64):
+        s = splitting.axis_split(n, p, (0, 1))
+        MK = [(s.M, s.K)] * 2
+        k = operators.kappa_lanczos([s, s], (s.m, s.m), lambda u: operators.stiffness_apply(u, MK), k=60)
+        bound = operators.prop1_bound(s.K, splitting.ktilde_basis_free(s.M, s.K, s.V_reg))
+        assert 1.0 - 1e-9 <= k <= bound * (1 + 1e-6)
+        kap.append(k)
+    assert kap[2] <= kap[0] * (1 + 1e-6) and kap[1] <= kap[0] * (1 + 1e-6)
+    assert max(kap) <= 1.3
+    if p == 2:
+        assert max(kap) <= 1.0 + 1e-9
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_kappa_lanczos_3d_bounded_in_h(p):
+    """The same in 3D (n = 8, 16): kappa does not grow with 1/h and stays below
+    the Proposition 1 bound."""
+    kap = []
+    for n in (8, 16):
+        s = splitting.axis_split(n, p, (0, 1))
+        MK = [(s.M, s.K)] * 3
+        k = operators.kappa_lanczos([s] * 3, (s.m,) * 3, lambda u: operators.stiffness_apply(u, MK), k=60)
+        bound = operators.prop1_bound(s.K, splitting.ktilde_basis_free(s.M, s.K, s.V_reg))
+        assert 1.0 <= k <= bound * (1 + 1e-6)
+        kap.append(k)
+    assert kap[1] <= kap[0] * (1 + 1e-6)
+
+
 def test_pcg_matches_dense_solve_and_p9_one_iteration():
     """Textbook PCG converges to A^{-1} f within the residual bound; with p = 2
     and D = {0,1} the IFFD is exact so PCG stops after 1 iteration (P9)."""
