@@ -489,6 +489,7 @@ def main():
     from paper_2512_20269_gb300 import measure_peak
     pk64 = measure_peak("fp64")
     pk32 = measure_peak("fp32")
+    pk32x2 = measure_peak("fp32x2")
     fp64_peak = pk64["tflops"]
     peak_src = (f"measured: iffd_measure_peak FP64 FMA chains on {pk64['sm_count']} SMs (cudaDeviceGetAttribute), "
                 f"best of 3 CUDA-event-timed launches")
@@ -737,6 +738,7 @@ def main():
                 "variants": variants, "precond_apply": apply_stats, "kernels": rooflines,
                 "hbm_frac_of_solve": None, "subcase_64": subcase,
                 "peaks": {"fp64_fma_tflops": fp64_peak, "fp32_fma_tflops": pk32["tflops"],
+                          "fp32x2_fma_tflops": pk32x2["tflops"],
                           "sm_count": pk64["sm_count"], "hbm_gbs": hbm_peak}}
         # fraction of HBM peak of the whole solve at the method's algorithmic traffic
         # (176 B/DoF per PCG iteration: 96 preconditioner + 32 stiffness with the

@@ -438,14 +438,61 @@ int iffd_batch_workspace_bytes(int count, const iffd_handle* plans, const int* n
 int iffd_batch_solve(int count, const iffd_handle* plans, const double* const* f, double* const* u, const int* nrhs,
                      void* ws, void* stream, iffd_pcg_info* infos);
 
+/* ---------------------------------------------------------------------------
+ * Building blocks of the slab-decomposed solve of ONE problem over several
+ * GPUs (one process per GPU; the Python module slab.py exchanges the data
+ * between the ranks and sums the inner products). A rank holds a box of the
+ * global grid of plan h: its slab of rows [z0, z0 + nz) of the slowest
+ * direction, or, for the fused pass, a box with whole pencils along the
+ * slowest direction. Boxes are float64 device arrays, direction 0 fastest;
+ * box[k] / offset[k] give the extent and the global offset per direction
+ * (direction 0 first; d entries, or 3 with trailing 1 / 0).
+ *
+ * iffd_apply_pass: one transform pass of the preconditioner of eq.
+ * "preconditioner" along `axis` on a box holding whole pencils along it
+ * (box[axis] = m_axis, offset[axis] = 0): mode 0 applies Q~^T, 1 applies Q~,
+ * 2 (axis = d - 1 only) Q~^T, the division by the summed eigenvalues of all
+ * directions (the box offset selects the eigenvalues of the other directions)
+ * and Q~. in and out may alias. FP64 IFFD plans (FP64-pipe block kernel).
+ * Errors: INVALID_ARG (box outside the grid, partial pencils, bad axis or
+ * mode), UNSUPPORTED (other precisions or preconditioners), CUDA.
+ *
+ * iffd_slab_stiffness: Au = A^ u (eq. "system_matrix") on the rows
+ * [z0, z0 + nz) of the slowest direction. u_ext holds u on the rows
+ * [max(0, z0 - p), min(m, z0 + nz + p)) (the slab and its halo from the
+ * neighbouring ranks), Au the nz rows; ws: device scratch of
+ * iffd_slab_workspace_bytes(h, nz) bytes, 256-byte aligned. The sweep along
+ * the slowest direction takes the global band rows of M and K; the sweeps
+ * along the other directions are those of iffd_apply_stiffness. IFFD_COEF_CONST
+ * plans. Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED, CUDA.
+ *
+ * iffd_copy_box: dst box <- src box, both 3D arrays (dims, direction 0
+ * fastest), boxes of extent ext at offsets src_off / dst_off (the packing of
+ * the exchanges). Errors: INVALID_ARG (box outside an array), CUDA.
+ *
+ * iffd_vec_dot: *result (device) = (a, b) over n entries, a fixed reduction
+ * order (per-block partial sums, then one block adds them in order); ws:
+ * device scratch of iffd_vec_dot_workspace_bytes(). iffd_vec_axpby:
+ * y = a x + b y (the PCG updates of Section 3 on a rank's part). */
+int iffd_apply_pass(iffd_handle h, int axis, int mode, const int* box, const int* offset, const double* in,
+                    double* out, void* stream);
+int iffd_slab_workspace_bytes(iffd_handle h, int nz, size_t* bytes);
+int iffd_slab_stiffness(iffd_handle h, int z0, int nz, const double* u_ext, double* Au, void* ws, void* stream);
+int iffd_copy_box(const double* src, const int* src_dims, const int* src_off, double* dst, const int* dst_dims,
+                  const int* dst_off, const int* ext, void* stream);
+int iffd_vec_dot_workspace_bytes(size_t* bytes);
+int iffd_vec_dot(const double* a, const double* b, long long n, double* result, void* ws, void* stream);
+int iffd_vec_axpby(long long n, double a, const double* x, double b, double* y, void* stream);
+
 /* Measures the arithmetic rate of the current GPU for the roofline of the
  * compute-bound kernels (the paper prints no timings and has no counterpart):
- * kind 0 = FP64 fused multiply-add, kind 1 = FP32 fused multiply-add. Every
+ * kind 0 = FP64 fused multiply-add, kind 1 = FP32 fused multiply-add, kind 2 =
+ * packed FP32 pairs (fma.rn.f32x2: two FMAs per instruction). Every
  * thread of a grid of 4 CTAs x 256 threads per SM runs eight independent FMA
  * chains; *tflops receives 2 x FMAs / the best of three CUDA-event times
  * (~40 ms each) in TFLOP/s, *sm_count (may be NULL) the SM count read from the
  * device. Runs on `stream` and synchronises it; allocates and frees a few KB.
- * Errors: INVALID_ARG (kind, NULL tflops), CUDA. */
+ * Errors: INVALID_ARG (kind not in 0..2, NULL tflops), CUDA. */
 int iffd_measure_peak(int kind, void* stream, int* sm_count, double* tflops);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */

@@ -101,11 +101,12 @@ def host_quad_axis(n: int, p: int, dirichlet=(1, 1), rep=None) -> dict:
 
 
 def measure_peak(kind: str = "fp64", stream=None) -> dict:
-    """FMA rate of the current GPU (iffd_measure_peak): kind "fp64" or "fp32";
+    """FMA rate of the current GPU (iffd_measure_peak): kind "fp64", "fp32" or
+    "fp32x2" (packed pairs);
     returns {"tflops": ..., "sm_count": ...}."""
     lib = _lib.load()
     sms, tf = ctypes.c_int(), ctypes.c_double()
-    check(lib.iffd_measure_peak({"fp64": 0, "fp32": 1}[kind], _stream_handle(stream), ctypes.byref(sms),
+    check(lib.iffd_measure_peak({"fp64": 0, "fp32": 1, "fp32x2": 2}[kind], _stream_handle(stream), ctypes.byref(sms),
                                 ctypes.byref(tf)), "iffd_measure_peak")
     return {"tflops": tf.value, "sm_count": sms.value}
 
@@ -316,11 +317,14 @@ class IFFDPlan:
         return self
 
     def set_geometry(self, axis: int, pencils_transform: int = 0, pencils_stiffness: int = 0, pipelined=None,
-                     warp: bool = False):
+                     warp: bool = False, double_float: bool = False):
         """Set one direction's launch geometry by hand (iffd_set_geometry).
         `warp`: run the warp-FFT transform pass (its tile is fixed; the FP32
-        default where eligible, opt-in for FP64 plans up to FFT length 256)."""
-        pl = 2 if warp else (-1 if pipelined is None else int(bool(pipelined)))
+        default where eligible, opt-in for FP64 plans up to FFT length 256).
+        `double_float`: FP64 plans, every transform pass in double-float
+        arithmetic on the FP32 pipe (the default where every direction has a
+        warp-FFT pass; any other FP64 transform geometry set here turns it off)."""
+        pl = 3 if double_float else (2 if warp else (-1 if pipelined is None else int(bool(pipelined))))
         check(self._lib.iffd_set_geometry(self._h, axis, int(pencils_transform), int(pencils_stiffness), pl),
               "iffd_set_geometry")
         return self
@@ -332,7 +336,7 @@ class IFFDPlan:
         check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns),
                                        ctypes.byref(pl)), "iffd_get_tiles")
         return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value]),
-                "pipelined": pl.value == 1, "warp": pl.value == 2}
+                "pipelined": pl.value == 1, "warp": pl.value in (2, 3), "double_float": pl.value == 3}
 
     def profile_enable(self, on: bool = True):
         check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")

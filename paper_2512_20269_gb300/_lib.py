@@ -99,6 +99,18 @@ SIGNATURES = [
     ("iffd_batch_solve", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), c_int_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(iffd_pcg_info)]),
+    ("iffd_apply_pass", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_int_p, c_int_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("iffd_slab_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_size_t_p]),
+    ("iffd_slab_stiffness", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("iffd_copy_box", ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, ctypes.c_void_p, c_int_p, c_int_p, c_int_p,
+                                     ctypes.c_void_p]),
+    ("iffd_vec_dot_workspace_bytes", ctypes.c_int, [c_size_t_p]),
+    ("iffd_vec_dot", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    ("iffd_vec_axpby", ctypes.c_int, [ctypes.c_longlong, ctypes.c_double, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     ("iffd_measure_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, c_int_p, c_double_p]),
     ("iffd_last_error", ctypes.c_char_p, []),
 ]

@@ -45,7 +45,8 @@ struct TableBuilder {
   template <typename T>
   size_t add_vec(const std::vector<T>& v) {
     if (v.empty()) {  // keep a valid (zero) entry so the device pointer is never dangling
-      const T zero = T(0);
+      T zero;
+      std::memset(&zero, 0, sizeof(T));
       return add(&zero, sizeof(T));
     }
     return add(v.data(), v.size() * sizeof(T));
@@ -60,6 +61,14 @@ static std::vector<T> cast_vec(const std::vector<double>& v) {
 struct AxisOffsets {
   size_t VL, VR, W, lam, post, chirp, bhat, VB, blk;
 };
+
+// double-float copies of FP64 tables (hi = nearest float, lo = the rounded rest)
+static std::vector<df> df_vec(const std::vector<double>& v) {
+  std::vector<df> o;
+  o.reserve(v.size());
+  for (double x : v) o.push_back(df(x));
+  return o;
+}
 
 static bool register_radix(int r) { return r == 8 || r == 4 || r == 2 || r == 3 || r == 5; }
 
@@ -367,13 +376,13 @@ static int choose_transform(const Axis1D& A, size_t elt, int* L, int* F, int* PP
 static int build_plan(Plan* P, cudaStream_t stream) {
   TableBuilder tb;
   struct PerAxis {
-    AxisOffsets od, of;
+    AxisOffsets od, of, oq;  // FP64, FP32 and double-float tables
     size_t Mb, Kb, Mt, Kt, QT, Q, lamQ, Msb, Ksb;
     int L, F;                          // DFT length; Bluestein FFT length (0: direct)
     std::vector<FftPlan> vars;         // radix sequences of length L (and F)
     std::vector<size_t> var_d, var_f;  // their twiddle tables (FP64, FP32)
     int ilo, ihi;
-    size_t wt, wt_d;                   // warp-FFT twiddles, FP32 and FP64 (D = {0,1} directions)
+    size_t wt, wt_d, wt_q;             // warp-FFT twiddles, FP32, FP64 and df (D = {0,1} directions)
   } pa[3];
   for (int a = 0; a < P->d; ++a) {
     const Axis1D& A = P->host[a];
@@ -421,7 +430,18 @@ static int build_plan(Plan* P, cudaStream_t stream) {
         }
       pa[a].wt = tb.add_vec(cast_vec<float>(wt));
       pa[a].wt_d = tb.add_vec(wt);
+      std::vector<df2> wq;
+      for (size_t e = 0; e + 1 < wt.size(); e += 2) wq.push_back(df2{df(wt[e]), df(wt[e + 1])});
+      pa[a].wt_q = tb.add_vec(wq);
     }
+    pa[a].oq.VL = tb.add_vec(df_vec(A.VL));
+    pa[a].oq.VR = tb.add_vec(df_vec(A.VR));
+    pa[a].oq.W = tb.add_vec(df_vec(A.W));
+    pa[a].oq.lam = tb.add_vec(df_vec(A.lam));
+    pa[a].oq.post = tb.add_vec(df_vec(post));
+    pa[a].oq.VB = tb.add_vec(df_vec(A.VB));
+    pa[a].oq.blk = pa[a].od.blk;
+    pa[a].oq.chirp = pa[a].oq.bhat = tb.add_vec(std::vector<df>{});  // the warp pass runs no Bluestein
     pa[a].of.VL = tb.add_vec(cast_vec<float>(A.VL));
     pa[a].of.VR = tb.add_vec(cast_vec<float>(A.VR));
     pa[a].of.W = tb.add_vec(cast_vec<float>(A.W));
@@ -520,6 +540,11 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     set_fft(&P->axf[a], P->fvar[a][P->vsel_f[a]]);
     P->wtab[a] = reinterpret_cast<const float2*>(base + pa[a].wt);
     P->wtab_d[a] = reinterpret_cast<const double2*>(base + pa[a].wt_d);
+    // double-float tables: the FP64 transform layout (L, F), no block-kernel FFT
+    fill_axistab(&P->axq[a], A, P->axd[a].L, P->axd[a].F, base, pa[a].oq);
+    P->axq[a].nst = 0;
+    P->axq[a].tw = nullptr;
+    P->wtab_q[a] = reinterpret_cast<const df2*>(base + pa[a].wt_q);
     P->warp_f[a] = 0;
     P->warp_d[a] = 0;
     if (const int wN = wpass_len(P->axf[a])) {
@@ -560,6 +585,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     max_parts = std::max(max_parts, stiff_tiles(P->dims, a, kMinTunePP));
   }
   P->max_parts = max_parts;
+  P->dfq = dfq_eligible(*P);
   const size_t vec = align256((size_t)N * sizeof(double));
   size_t off = 0;
   P->off_r = off; off += vec;
@@ -649,6 +675,30 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
   return L;
 }
 
+int dfq_eligible(const Plan& P) {
+  if (P.opt.precision != IFFD_PREC_FP64 || P.opt.precond != IFFD_PRECOND_IFFD) return 0;
+  for (int a = 0; a < P.d; ++a)
+    if (wpass_len(P.axq[a]) == 0 || P.dims.N / P.axq[a].m >= (1LL << 31)) return 0;
+  return 1;
+}
+
+// A double-float warp pass along direction `axis` (see Plan::dfq).
+static PassLaunch<df> make_pass_df(const Plan* P, int axis, const int* done) {
+  PassLaunch<df> L{};
+  L.dims = P->dims;
+  L.axis = axis;
+  L.wN = wpass_len(P->axq[axis]);
+  L.PP = wpass_pencils(L.wN);
+  L.ldt = P->axq[axis].m | 1;
+  L.ax = P->axq[axis];
+  L.lamA = P->axq[0].lam;
+  L.lamB = (P->d == 3) ? P->axq[1].lam : P->axq[0].lam;
+  L.done = done;
+  L.pipe = 0;
+  L.wt = P->wtab_q[axis];
+  return L;
+}
+
 int f64_warp_len(const Plan& P, int a) {
   return (P.warp_d[a] && P.dims.N / P.axd[a].m < (1LL << 31)) ? wpass_len(P.axd[a]) : 0;
 }
@@ -712,6 +762,40 @@ static int run_precond(const Plan* P, const double* r, double* z, void* ws, cuda
         P->prof.end(st);
       }
       *nparts = g;
+    }
+    return IFFD_OK;
+  }
+  if (P->opt.precision == IFFD_PREC_FP64 && P->dfq) {
+    // double-float passes: r (FP64) -> z holding df values -> ... -> z (FP64);
+    // a df value takes the 8 bytes of the FP64 value it stands for
+    df* zq = reinterpret_cast<df*>(z);
+    {
+      auto L = make_pass_df(P, 0, done);
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_FWD, st, (launch_pass_df<double, df>(L, PM_FWD, 0, r, zq, st)));
+    }
+    for (int a = 1; a < d - 1; ++a) {
+      auto L = make_pass_df(P, a, done);
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_FWD, st, (launch_pass_df<df, df>(L, PM_FWD, 0, zq, zq, st)));
+    }
+    {
+      auto L = make_pass_df(P, d - 1, done);
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_FUSED, st, (launch_pass_df<df, df>(L, PM_FUSED, 0, zq, zq, st)));
+    }
+    for (int a = d - 2; a >= 1; --a) {
+      auto L = make_pass_df(P, a, done);
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_BWD, st, (launch_pass_df<df, df>(L, PM_BWD, 0, zq, zq, st)));
+    }
+    {
+      auto L = make_pass_df(P, 0, done);
+      int nd = 0;
+      if (ndot >= 1) {
+        nd = ndot;
+        L.dot0 = d0;
+        L.dot1 = d1;
+        L.partial = partial;
+        *nparts = precond_tiles(P->dims, 0, L.PP);
+      }
+      IFFD_LAUNCH(P, IFFD_K_PRECOND_BWD, st, (launch_pass_df<df, double>(L, PM_BWD, nd, zq, z, st)));
     }
     return IFFD_OK;
   }

@@ -47,6 +47,35 @@ __device__ __forceinline__ Cplx<T> mul_mi(Cplx<T> a) { return {a.y, -a.x}; }
 template <typename T>
 __device__ __forceinline__ Cplx<T> mul_pi(Cplx<T> a) { return {-a.y, a.x}; }
 
+// Read-only loads through the non-coherent cache, for any type __ldg takes;
+// the double-float types (dfloat.cuh) add their own overloads.
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+
+__device__ __forceinline__ float shfl_xor(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ double shfl_xor(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+
+// Value conversion between the storage and arithmetic types (identity, or a
+// float <-> double cast; dfloat.cuh adds the double-float conversions).
+template <typename To>
+struct Cvt {
+  template <typename From>
+  __device__ __forceinline__ static To from(From v) {
+    return (To)v;
+  }
+};
+}  // namespace iffd
+
+#include "dfloat.cuh"
+
+namespace iffd {
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From v) {
+  return Cvt<To>::from(v);
+}
+
 // Quotient of a non-negative n < 2^31 by an invariant divisor d >= 1 through
 // one 64-bit multiply and a shift -- division by invariant integers using
 // multiplication (Granlund and Montgomery, PLDI 1994). With l = ceil(log2 d),

@@ -42,6 +42,13 @@ struct __align__(16) df2 {
   df x, y;
 };
 
+template <typename T>
+struct Vec2Of;
+template <>
+struct Vec2Of<df> {
+  using type = df2;
+};
+
 __device__ __forceinline__ df fast_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   const float e = __fadd_rn(b, -__fadd_rn(s, -a));
@@ -83,6 +90,9 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
   return fast_two_sum(s.hi, t);
 }
 
+// the float / double overloads stay visible next to the df one inside the namespace
+using ::fma;
+
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 
 // 1 / b: the float reciprocal refined by one Newton step x + x (1 - b x)
@@ -102,11 +112,109 @@ __device__ __forceinline__ df neg_if(df v, bool neg) {
   return {__int_as_float(__float_as_int(v.hi) ^ m), __int_as_float(__float_as_int(v.lo) ^ m)};
 }
 
-__device__ __forceinline__ df to_df(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
+// ------------------------------------------------------------ conversions
+// FP64 <-> double-float at the first and last transform pass. On this GPU a
+// float64 conversion or addition runs on the FP64 pipe, so both directions
+// work on the bit patterns with integer instructions and leave the FP64 pipe
+// one addition (df -> double) or nothing (double -> df) per value; values
+// outside the range where the integer route is exact take the FP64 route.
+__host__ __device__ __forceinline__ unsigned long long bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  __builtin_memcpy(&u, &x, sizeof u);
+  return u;
+#endif
 }
-__device__ __forceinline__ double to_double(df v) { return (double)v.hi + (double)v.lo; }
+__host__ __device__ __forceinline__ double double_of(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  __builtin_memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned bits_of(float x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__float_as_int(x);
+#else
+  unsigned u;
+  __builtin_memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float((int)u);
+#else
+  float x;
+  __builtin_memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ int clz32(unsigned x) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)x);
+#else
+  return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// x = hi + lo with hi the first 24 significant bits of x (truncated) and lo
+// the next 29 bits rounded to 24 (relative error <= 2^-48 of |x|), from the
+// bit pattern of x. The binary exponent of x must lie in [-74, 127] (float
+// exponent field 53..254) so that hi and lo are normal floats; zero, smaller,
+// larger and non-finite values take the float64 route.
+__host__ __device__ __forceinline__ df to_df(double x) {
+  const unsigned long long b = bits_of(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sign = h32 & 0x80000000u;
+  const int fe = (int)((h32 >> 20) & 0x7FFu) - 896;  // float exponent field of hi
+  if ((b << 1) == 0) return {float_of(sign), 0.f};
+  if (fe < 53 || fe > 254) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+  }
+  const float h = float_of(sign | ((unsigned)fe << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+  const unsigned r = l32 & 0x1FFFFFFFu;  // x - hi = r 2^(fe - 179)
+  if (r == 0) return {h, 0.f};
+  const int lz = clz32(r) - 3;   // leading zeros inside the 29-bit field
+  const unsigned rn = r << lz;   // leading one at bit 28
+  // 23 fraction bits, rounded half up (a carry moves into the exponent field)
+  const unsigned lb = ((unsigned)(fe - 24 - lz) << 23) + ((rn >> 5) & 0x7FFFFFu) + ((rn >> 4) & 1u);
+  return {h, float_of(sign | lb)};
+}
+
+// exact float -> double on the integer pipe (normal floats and zeros)
+__host__ __device__ __forceinline__ double float_to_double_bits(float f) {
+  const unsigned u = bits_of(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7FFFFFFFu) == 0) return double_of(s);
+  if (e == 0 || e == 255) return (double)f;  // subnormal, inf, nan
+  return double_of(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29));
+}
+
+// hi + lo rounded to float64: one FP64 addition
+__host__ __device__ __forceinline__ double to_double(df v) {
+  return float_to_double_bits(v.hi) + float_to_double_bits(v.lo);
+}
+
+template <typename To>
+struct Cvt;
+template <>
+struct Cvt<df> {
+  __device__ __forceinline__ static df from(double v) { return to_df(v); }
+  __device__ __forceinline__ static df from(df v) { return v; }
+};
+template <>
+struct Cvt<double> {
+  __device__ __forceinline__ static double from(double v) { return v; }
+  __device__ __forceinline__ static double from(float v) { return (double)v; }
+  __device__ __forceinline__ static double from(df v) { return to_double(v); }
+};
 
 __device__ __forceinline__ df ldg(const df* p) {
   const float2 t = __ldg(reinterpret_cast<const float2*>(p));

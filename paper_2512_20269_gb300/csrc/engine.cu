@@ -714,6 +714,7 @@ static int engine_plan(iffd_engine* h, int d, int n, int p, const int* dirichlet
   iffd_plan* P = nullptr;
   const int rc = plan_create(d, nn, p, dir, &o, E.st, &P);
   if (rc) return rc;
+  P->P.dfq = 0;  // the engine's batched FP64 passes are the block kernel
   E.plans[key] = P;
   *out = P;
   return IFFD_OK;
@@ -888,6 +889,7 @@ namespace {
 
 bool engine_runs_exactly(const Plan& P) {
   if (P.opt.precond != IFFD_PRECOND_IFFD || P.opt.coef != IFFD_COEF_CONST) return false;
+  if (P.opt.precision == IFFD_PREC_FP64 && P.dfq) return false;  // double-float passes: not batched
   if (P.opt.precision == IFFD_PREC_FP64)
     for (int a = 0; a < P.d; ++a)
       if (f64_warp_len(P, a)) return false;

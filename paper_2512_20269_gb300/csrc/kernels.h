@@ -79,6 +79,12 @@ int precond_tiles(const Dims& dims, int axis, int PP);
 // tile row length ldt and arithmetic of elt bytes.
 int wpass_len(const AxisTab<float>& ax);
 int wpass_len(const AxisTab<double>& ax);
+int wpass_len(const AxisTab<df>& ax);
+// Double-float transform pass (the warp-FFT pass of length P.wN with df
+// arithmetic): FP64 in / df out (FWD), df in and out (any mode), df in / FP64
+// out (BWD, 0..2 dot products).
+template <typename Tin, typename Tout>
+cudaError_t launch_pass_df(const PassLaunch<df>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
 int wpass_pencils(int N);
 size_t wpass_smem_bytes(int N, int ldt, size_t elt = sizeof(float));
 

@@ -8,11 +8,14 @@
 // x <- x * a + b (no memory traffic inside the loop), and the rate is the
 // counted flops (2 per FMA) over the kernel's CUDA-event time. The chains are
 // independent so that the FMA latency is covered by the other chains and by
-// the other resident warps.
+// the other resident warps. A third kind times packed FP32 pairs
+// (fma.rn.f32x2, two FMAs per instruction), which the double-float arithmetic
+// can use for the real and imaginary parts of a complex value.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include "../../include/iffd.h"
 
@@ -43,13 +46,47 @@ __global__ void __launch_bounds__(kPeakThreads) fma_chains(T* out, int iters, T 
   if (s < T(-1)) out[blockIdx.x] = s;
 }
 
+// Packed pairs of FP32 values: one fma.rn.f32x2 instruction carries two FMAs.
+__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
+__global__ void __launch_bounds__(kPeakThreads) fma_chains_x2(float2* out, int iters, float2 a, float2 b) {
+  float2 x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = make_float2((threadIdx.x + c) * 1e-3f, (threadIdx.x + 2 * c) * 1e-3f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = fma_x2(x[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c].x + x[c].y;
+  if (s < -1.f) out[blockIdx.x] = make_float2(s, s);
+}
+
+template <typename T>
+void launch_chains(T* sink, int grid, int iters, cudaStream_t st) {
+  fma_chains<T><<<grid, kPeakThreads, 0, st>>>(sink, iters, T(0.9999), T(1e-4));
+}
+template <>
+void launch_chains<float2>(float2* sink, int grid, int iters, cudaStream_t st) {
+  fma_chains_x2<<<grid, kPeakThreads, 0, st>>>(sink, iters, make_float2(0.9999f, 0.9999f), make_float2(1e-4f, 1e-4f));
+}
+
 template <typename T>
 int run_peak(cudaStream_t st, int sms, double* tflops) {
   const int grid = sms * kBlocksPerSm;
   T* sink = nullptr;  // one slot per block; never written in practice (see fma_chains)
   cudaError_t e = cudaMalloc(&sink, sizeof(T) * grid);
   if (e != cudaSuccess) return iffd::record_error(IFFD_ERR_CUDA, cudaGetErrorString(e));
-  const double fl_per_iter = 2.0 * kChains * (double)grid * kPeakThreads;
+  // flops per loop trip: 2 per FMA, two FMAs per packed instruction
+  const double fl_per_iter = 2.0 * kChains * (double)grid * kPeakThreads * (std::is_same<T, float2>::value ? 2 : 1);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -58,7 +95,6 @@ int run_peak(cudaStream_t st, int sms, double* tflops) {
     cudaFree(sink);
     return iffd::record_error(IFFD_ERR_CUDA, cudaGetErrorString(e));
   }
-  const T a = T(0.9999), b = T(1e-4);
   int iters = 256;
   double best = 0.0;
   int rc = IFFD_OK;
@@ -66,7 +102,7 @@ int run_peak(cudaStream_t st, int sms, double* tflops) {
   // of three timed launches
   for (int rep = 0; rep < 4 && rc == IFFD_OK; ++rep) {
     cudaEventRecord(e0, st);
-    fma_chains<T><<<grid, kPeakThreads, 0, st>>>(sink, iters, a, b);
+    launch_chains<T>(sink, grid, iters, st);
     cudaEventRecord(e1, st);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -93,8 +129,8 @@ int run_peak(cudaStream_t st, int sms, double* tflops) {
 }  // namespace
 
 extern "C" int iffd_measure_peak(int kind, void* stream, int* sm_count, double* tflops) {
-  if (!tflops || (kind != 0 && kind != 1))
-    return iffd::record_error(IFFD_ERR_INVALID_ARG, "iffd_measure_peak: kind must be 0 or 1, tflops non-NULL");
+  if (!tflops || kind < 0 || kind > 2)
+    return iffd::record_error(IFFD_ERR_INVALID_ARG, "iffd_measure_peak: kind must be 0, 1 or 2, tflops non-NULL");
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -102,5 +138,6 @@ extern "C" int iffd_measure_peak(int kind, void* stream, int* sm_count, double* 
     return iffd::record_error(IFFD_ERR_CUDA, std::string("iffd_measure_peak: ") + cudaGetErrorString(e));
   if (sm_count) *sm_count = sms;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (kind == 2) return run_peak<float2>(st, sms, tflops);
   return kind == 0 ? run_peak<double>(st, sms, tflops) : run_peak<float>(st, sms, tflops);
 }

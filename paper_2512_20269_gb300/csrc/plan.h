@@ -146,6 +146,13 @@ struct Plan {
   // off by default, chosen by hand or by the tuner) and its FP64 twiddles
   int warp_d[3] = {0, 0, 0};
   const double2* wtab_d[3] = {nullptr, nullptr, nullptr};
+  // FP64 IFFD plans whose directions all have a warp-FFT pass of length 64,
+  // 128 or 256 (D = {0,1}): dfq = 1 runs every transform pass in double-float
+  // arithmetic on the FP32 pipe (the default for such plans; a transform
+  // geometry set by hand turns it off), with these tables and twiddles
+  int dfq = 0;
+  AxisTab<df> axq[3];
+  const df2* wtab_q[3] = {nullptr, nullptr, nullptr};
   // General-coefficient stiffness: per direction the Gauss-point tables (one
   // device allocation, gen_mem)
   GenAxis gen[3];
@@ -197,6 +204,8 @@ cudaError_t launch_gen_pupdate(const double* z, double* p, const SolveState* S, 
                                const int* done, cudaStream_t st);
 // FFT length of direction a's FP64 warp-FFT pass (0: the block kernel runs).
 int f64_warp_len(const Plan& P, int a);
+// 1 if every direction of an FP64 IFFD plan can run the double-float warp pass.
+int dfq_eligible(const Plan& P);
 StiffLaunch plan_stiff_launch(const Plan* P, int axis);
 template <typename T>
 void set_fft(AxisTab<T>* t, const FftVar& v);

@@ -733,6 +733,21 @@ static int wpass_len_t(const AxisTab<T>& ax, int nmax) {
 int wpass_len(const AxisTab<float>& ax) { return wpass_len_t(ax, 512); }
 // FP64: a length-512 tile (141 KB of shared memory) would leave one CTA per SM
 int wpass_len(const AxisTab<double>& ax) { return wpass_len_t(ax, 256); }
+int wpass_len(const AxisTab<df>& ax) { return wpass_len_t(ax, 256); }
+
+template <typename Tin, typename Tout>
+cudaError_t launch_pass_df(const PassLaunch<df>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
+  if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
+  switch (P.wN) {
+    case 64: return launch_wpass<64, df, Tin, Tout>(P, mode, ndot, in, out, st);
+    case 128: return launch_wpass<128, df, Tin, Tout>(P, mode, ndot, in, out, st);
+    case 256: return launch_wpass<256, df, Tin, Tout>(P, mode, ndot, in, out, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_pass_df<double, df>(const PassLaunch<df>&, int, int, const double*, df*, cudaStream_t);
+template cudaError_t launch_pass_df<df, df>(const PassLaunch<df>&, int, int, const df*, df*, cudaStream_t);
+template cudaError_t launch_pass_df<df, double>(const PassLaunch<df>&, int, int, const df*, double*, cudaStream_t);
 
 int wpass_pencils(int N) {
   switch (N) {

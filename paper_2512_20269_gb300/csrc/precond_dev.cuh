@@ -9,7 +9,7 @@ namespace iffd {
 
 template <typename T>
 __device__ __forceinline__ Cplx<T> ldc(const T* p) {
-  return {__ldg(p), __ldg(p + 1)};
+  return {ldg(p), ldg(p + 1)};
 }
 
 // ------------------------------------------------------------- small DFTs
@@ -58,28 +58,28 @@ template <typename T>
 __device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
   if (i < ax.nL) {
     T s = T(0);
-    for (int r = 0; r < ax.rowsL; ++r) s = fma(__ldg(ax.VL + r * ax.nL + i), row[r], s);
+    for (int r = 0; r < ax.rowsL; ++r) s = fma(ldg(ax.VL + r * ax.nL + i), row[r], s);
     return s;
   }
   if (i >= ax.n_reg - ax.nR) {
     const int c = ax.n_reg - 1 - i;
     T s = T(0);
-    for (int r = 0; r < ax.rowsR; ++r) s = fma(__ldg(ax.VR + r * ax.nR + c), row[ax.m - 1 - r], s);
+    for (int r = 0; r < ax.rowsR; ++r) s = fma(ldg(ax.VR + r * ax.nR + c), row[ax.m - 1 - r], s);
     return s;
   }
   int o = ax.o;
   for (int b = 0; b < ax.nblk; ++b) {  // interior blocks (repeated knots only)
     const int* B = ax.blk + 6 * b;
-    const int c0 = __ldg(B), c1 = __ldg(B + 1);
+    const int c0 = ldg(B), c1 = ldg(B + 1);
     if (i < c0) break;
     if (i < c1) {
-      const int r0 = __ldg(B + 2), r1 = __ldg(B + 3), w = c1 - c0;
-      const T* V = ax.VB + __ldg(B + 5) + (i - c0);
+      const int r0 = ldg(B + 2), r1 = ldg(B + 3), w = c1 - c0;
+      const T* V = ax.VB + ldg(B + 5) + (i - c0);
       T s = T(0);
-      for (int r = r0; r < r1; ++r) s = fma(__ldg(V + (r - r0) * w), row[r], s);
+      for (int r = r0; r < r1; ++r) s = fma(ldg(V + (r - r0) * w), row[r], s);
       return s;
     }
-    o = __ldg(B + 4);
+    o = ldg(B + 4);
   }
   return row[i + o];
 }

@@ -43,13 +43,19 @@ struct Post4 {
   T x, y, z, w;
 };
 __device__ __forceinline__ Post4<float> ldpost(const float* p, int k) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
+  const float4 t = ldg(reinterpret_cast<const float4*>(p) + k);
   return {t.x, t.y, t.z, t.w};
 }
 __device__ __forceinline__ Post4<double> ldpost(const double* p, int k) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p) + 2 * k);
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 2 * k + 1);
+  const double2 a = ldg(reinterpret_cast<const double2*>(p) + 2 * k);
+  const double2 b = ldg(reinterpret_cast<const double2*>(p) + 2 * k + 1);
   return {a.x, a.y, b.x, b.y};
+}
+
+__device__ __forceinline__ Post4<df> ldpost(const df* p, int k) {
+  const float4 a = ldg(reinterpret_cast<const float4*>(p) + 2 * k);
+  const float4 b = ldg(reinterpret_cast<const float4*>(p) + 2 * k + 1);
+  return {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
 }
 
 template <int r, typename T>
@@ -87,7 +93,7 @@ __device__ __forceinline__ void wstage(vec2_t<T>* buf, int ls, const vec2_t<T>* 
     if constexpr (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < r; ++q) {
-        const vec2_t<T> w = __ldg(wt + q * k * (N / (Ns * r)));
+        const vec2_t<T> w = ldg(wt + q * k * (N / (Ns * r)));
         v[u][q] = cmul(v[u][q], Cplx<T>{w.x, w.y});
       }
     }
@@ -136,7 +142,7 @@ __device__ __forceinline__ void wstage_first(vec2_t<T>* buf, int ls, Src src) {
 template <int LS, typename T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
-  for (int off = LS / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  for (int off = LS / 2; off > 0; off >>= 1) v += shfl_xor(v, off);
   return v;
 }
 
@@ -147,28 +153,28 @@ __device__ __forceinline__ T wscatter_row(int i, const AxisTab<T>& ax, WReg wreg
   const int m = ax.m, N = ax.n_reg;
   if (i < ax.rowsL) {
     T x = T(0);
-    for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
+    for (int c = 0; c < ax.nL; ++c) x = fma(ldg(ax.VL + i * ax.nL + c), wreg(c), x);
     return x;
   }
   if (i >= m - ax.rowsR) {
     const int r = m - 1 - i;
     T x = T(0);
-    for (int c = 0; c < ax.nR; ++c) x = fma(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
+    for (int c = 0; c < ax.nR; ++c) x = fma(ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
     return x;
   }
   int o = ax.o;
   for (int b = 0; b < ax.nblk; ++b) {
     const int* B = ax.blk + 6 * b;
-    const int r0 = __ldg(B + 2), r1 = __ldg(B + 3);
+    const int r0 = ldg(B + 2), r1 = ldg(B + 3);
     if (i < r0) break;
     if (i < r1) {
-      const int c0 = __ldg(B), c1 = __ldg(B + 1);
-      const T* V = ax.VB + __ldg(B + 5) + (i - r0) * (c1 - c0);
+      const int c0 = ldg(B), c1 = ldg(B + 1);
+      const T* V = ax.VB + ldg(B + 5) + (i - r0) * (c1 - c0);
       T x = T(0);
-      for (int c = c0; c < c1; ++c) x = fma(__ldg(V + (c - c0)), wreg(c), x);
+      for (int c = c0; c < c1; ++c) x = fma(ldg(V + (c - c0)), wreg(c), x);
       return x;
     }
-    o = __ldg(B + 4);
+    o = ldg(B + 4);
   }
   return wreg(i - o);
 }
@@ -221,7 +227,7 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, T* tile, 
       if (pc < g.nvalid) {
         const Tin* src = in + pbase[pc];
 #pragma unroll 4
-        for (int i = lane; i < m; i += 32) row[i] = (T)src[i];
+        for (int i = lane; i < m; i += 32) row[i] = cvt<T>(src[i]);
       } else {
         for (int i = lane; i < m; i += 32) row[i] = T(0);
       }
@@ -242,12 +248,12 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, T* tile, 
         v2 = p[2 * step];
         v3 = p[3 * step];
       }
-      tile[pc * ldt + i] = (T)v0;
-      tile[pc * ldt + i + RS] = (T)v1;
-      tile[pc * ldt + i + 2 * RS] = (T)v2;
-      tile[pc * ldt + i + 3 * RS] = (T)v3;
+      tile[pc * ldt + i] = cvt<T>(v0);
+      tile[pc * ldt + i + RS] = cvt<T>(v1);
+      tile[pc * ldt + i + 2 * RS] = cvt<T>(v2);
+      tile[pc * ldt + i + 3 * RS] = cvt<T>(v3);
     }
-    for (; i < m; i += RS, p += step) tile[pc * ldt + i] = valid ? (T)p[0] : T(0);
+    for (; i < m; i += RS, p += step) tile[pc * ldt + i] = valid ? cvt<T>(p[0]) : T(0);
   }
 }
 
@@ -273,7 +279,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
   const int nw = ax.n_out;
   constexpr int NR = (KIND == 1) ? N : N / 2 - 1;  // n_reg
 
-  if (MODE == PM_FWD || MODE == PM_FUSED) {
+  if constexpr (MODE == PM_FWD || MODE == PM_FUSED) {
     // y_out = W^T r over the support rows of W, four columns per row read
     for (int k0 = 0; k0 < nw; k0 += 4) {
       T sa[4] = {T(0), T(0), T(0), T(0)}, sb[4] = {T(0), T(0), T(0), T(0)};
@@ -284,7 +290,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             if (k0 + k < nw) {
-              const T wk = __ldg(w + k);
+              const T wk = ldg(w + k);
               sa[k] = fma(wk, xa, sa[k]);
               sb[k] = fma(wk, xb, sb[k]);
             }
@@ -387,7 +393,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       // DST-I output j is -Im Z[j+1] (pencil a) and Re Z[j+1] (pencil b), times 1/(2 D~_j)
       for (int j = ls; j < NR; j += LS) {
         const Cplx<T> z = wld<T>(buf, wpad(j + 1));
-        const T sc = __ldg(ax.post + j);
+        const T sc = ldg(ax.post + j);
         ra[j] = -sc * z.y;
         rb[j] = sc * z.x;
       }
@@ -400,14 +406,14 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
     __syncwarp();
   }
 
-  if (MODE == PM_FUSED) {
+  if constexpr (MODE == PM_FUSED) {
     // divide by the summed eigenvalues of all directions
     const int pa = 2 * pr, pb = pa + 1;
-    const T la = __ldg(lamA + pia[pa]), lb = __ldg(lamA + pia[pb]);
-    const T ma = (dims.d == 3) ? __ldg(lamB + pib[pa]) : T(0);
-    const T mb = (dims.d == 3) ? __ldg(lamB + pib[pb]) : T(0);
+    const T la = ldg(lamA + pia[pa]), lb = ldg(lamA + pia[pb]);
+    const T ma = (dims.d == 3) ? ldg(lamB + pib[pa]) : T(0);
+    const T mb = (dims.d == 3) ? ldg(lamB + pib[pb]) : T(0);
     for (int i = ls; i < m; i += LS) {
-      const T li = __ldg(ax.lam + i);
+      const T li = ldg(ax.lam + i);
       T da = li + la, db = li + lb;
       if (dims.d == 3) {
         da += ma;
@@ -419,7 +425,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
     __syncwarp();
   }
 
-  if (MODE == PM_BWD || MODE == PM_FUSED) {
+  if constexpr (MODE == PM_BWD || MODE == PM_FUSED) {
     for (int k = ls; k < nw; k += LS) {
       ova[k] = ra[NR + k];
       ovb[k] = rb[NR + k];
@@ -446,7 +452,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
         T va = T(0), vb = T(0);
         if (l != 0 && l != N / 2) {
           const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
-          const T sc = (l < N / 2) ? __ldg(ax.post + jj) : -__ldg(ax.post + jj);
+          const T sc = (l < N / 2) ? ldg(ax.post + jj) : -ldg(ax.post + jj);
           va = sc * ra[jj];
           vb = sc * rb[jj];
         }
@@ -485,7 +491,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       }
       if (i < ax.wlo || i >= ax.whi) {
         for (int k = 0; k < nw; ++k) {
-          const T w = __ldg(ax.W + i * nw + k);
+          const T w = ldg(ax.W + i * nw + k);
           xa = fma(w, ova[k], xa);
           xb = fma(w, ovb[k], xb);
         }
@@ -512,10 +518,10 @@ __device__ __forceinline__ void wstore_tile(const T* tile, Tout* __restrict__ ou
       Tout* dst = out + pbase[pc];
       const long long off0 = pbase[pc];
       for (int i = lane; i < m; i += 32) {
-        const Tout v = (Tout)row[i];
+        const Tout v = cvt<Tout>(row[i]);
         dst[i] = v;
-        if (NDOT >= 1) d0 = fma(__ldg(dotv0 + off0 + i), (double)v, d0);
-        if (NDOT >= 2) d1 = fma(__ldg(dotv1 + off0 + i), (double)v, d1);
+        if (NDOT >= 1) d0 = fma(ldg(dotv0 + off0 + i), cvt<double>(v), d0);
+        if (NDOT >= 2) d1 = fma(ldg(dotv1 + off0 + i), cvt<double>(v), d1);
       }
     }
   } else {
@@ -526,10 +532,10 @@ __device__ __forceinline__ void wstore_tile(const T* tile, Tout* __restrict__ ou
       int i = tid / PP;
       long long off = pbase[pc] + i * g.S;
       for (; i < m; i += RS, off += step) {
-        const Tout v = (Tout)tile[pc * ldt + i];
+        const Tout v = cvt<Tout>(tile[pc * ldt + i]);
         out[off] = v;
-        if (NDOT >= 1) d0 = fma(__ldg(dotv0 + off), (double)v, d0);
-        if (NDOT >= 2) d1 = fma(__ldg(dotv1 + off), (double)v, d1);
+        if (NDOT >= 1) d0 = fma(ldg(dotv0 + off), cvt<double>(v), d0);
+        if (NDOT >= 2) d1 = fma(ldg(dotv1 + off), cvt<double>(v), d1);
       }
     }
   }
@@ -570,19 +576,37 @@ __device__ __forceinline__ void wscale_tile(double* tile, int axis, int ldt, con
     for (int e = tid; e < PP * m; e += kThreads) {
       const int pc = e / m, i = e - pc * m;
       if (pc >= g.nvalid) continue;
-      double den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
-      if (dims.d == 3) den += __ldg(lamB + pib[pc]);
+      double den = ldg(ax.lam + i) + ldg(lamA + pia[pc]);
+      if (dims.d == 3) den += ldg(lamB + pib[pc]);
       tile[pc * ldt + i] = tile[pc * ldt + i] / den;
     }
   } else if (axis == 0) {
     for (int pc = warp; pc < g.nvalid; pc += kThreads / 32)
-      for (int i = lane; i < m; i += 32) tile[pc * ldt + i] = tile[pc * ldt + i] * __ldg(ax.rden + pbase[pc] + i);
+      for (int i = lane; i < m; i += 32) tile[pc * ldt + i] = tile[pc * ldt + i] * ldg(ax.rden + pbase[pc] + i);
   } else {
     constexpr int RS = kThreads / PP;
     const int pc = tid & (PP - 1);
     if (pc < g.nvalid)
       for (int i = tid / PP; i < m; i += RS)
-        tile[pc * ldt + i] = tile[pc * ldt + i] * __ldg(ax.rden + pbase[pc] + i * g.S);
+        tile[pc * ldt + i] = tile[pc * ldt + i] * ldg(ax.rden + pbase[pc] + i * g.S);
+  }
+}
+
+// Double-float FUSED passes: the same block-wide step, dividing by the summed
+// eigenvalues through a double-float reciprocal formed on the fly (no
+// per-DoF table is read): the eigenvalues of the other directions are summed
+// once per pencil, then lam_i is added and the reciprocal refined by Newton.
+template <int N>
+__device__ __forceinline__ void wscale_tile_df(df* tile, int ldt, const AxisTab<df>& ax, const Dims& dims,
+                                               const df* __restrict__ lamA, const df* __restrict__ lamB,
+                                               const int* pia, const int* pib, const TileInfo& g) {
+  const int m = ax.m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int pc = warp; pc < g.nvalid; pc += kThreads / 32) {
+    df lp = ldg(lamA + pia[pc]);
+    if (dims.d == 3) lp = lp + ldg(lamB + pib[pc]);
+    df* row = tile + pc * ldt;
+    for (int i = lane; i < m; i += 32) row[i] = row[i] * recip(ldg(ax.lam + i) + lp);
   }
 }
 
@@ -608,6 +632,12 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
     wtransform<T, N, KIND, PM_FWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
     __syncthreads();
     wscale_tile<N>(tile, axis, ldt, ax, dims, lamA, lamB, pbase, pia, pib, g);
+    __syncthreads();
+    wtransform<T, N, KIND, PM_BWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+  } else if constexpr (std::is_same<T, df>::value && MODE == PM_FUSED) {
+    wtransform<T, N, KIND, PM_FWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    __syncthreads();
+    wscale_tile_df<N>(tile, ldt, ax, dims, lamA, lamB, pia, pib, g);
     __syncthreads();
     wtransform<T, N, KIND, PM_BWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
   } else {
@@ -695,6 +725,13 @@ cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long 
 template <typename Tc, typename Tin, typename Tout>
 constexpr bool wpass_combo_ok(int mode, int ndot) {
   if (std::is_same<Tc, double>::value) return std::is_same<Tin, double>::value && std::is_same<Tout, double>::value;
+  if (std::is_same<Tc, df>::value) {
+    // double-float: FP64 in (forward passes of the first direction), FP64 out
+    // (backward passes of the first direction, 0..2 dot products), df between
+    if (std::is_same<Tin, double>::value) return mode == PM_FWD && std::is_same<Tout, df>::value;
+    if (std::is_same<Tout, double>::value) return mode == PM_BWD;
+    return ndot == 0;
+  }
   if (std::is_same<Tin, double>::value) return mode == PM_FWD;
   if (std::is_same<Tout, double>::value) return mode == PM_BWD;
   return ndot == 0;
@@ -772,5 +809,12 @@ cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const 
 #define IFFD_WARP_INSTANTIATE_F64(NN)                                                                             \
   template cudaError_t launch_wpass<NN, double, double, double>(const PassLaunch<double>&, int, int,               \
                                                                 const double*, double*, cudaStream_t);
+// Double-float passes (FP64-accurate transforms on the FP32 pipe), lengths up to 256.
+#define IFFD_WARP_INSTANTIATE_DF(NN)                                                                                 \
+  template cudaError_t launch_wpass<NN, df, double, df>(const PassLaunch<df>&, int, int, const double*, df*,          \
+                                                        cudaStream_t);                                              \
+  template cudaError_t launch_wpass<NN, df, df, df>(const PassLaunch<df>&, int, int, const df*, df*, cudaStream_t); \
+  template cudaError_t launch_wpass<NN, df, df, double>(const PassLaunch<df>&, int, int, const df*, double*,         \
+                                                        cudaStream_t);
 
 }  // namespace iffd

@@ -258,7 +258,8 @@ int plan_autotune(Plan* P, void* ws, cudaStream_t st) {
     IFFD_CUDA(cudaMemsetAsync(w + P->off_tf, 0, (size_t)P->dims.N * sizeof(float), st));
   int rc;
   for (int a = 0; a < P->d; ++a) {
-    if (P->opt.precond == IFFD_PRECOND_IFFD) {
+    // the double-float passes of an FP64 plan have a fixed geometry
+    if (P->opt.precond == IFFD_PRECOND_IFFD && !(P->opt.precision == IFFD_PREC_FP64 && P->dfq)) {
       rc = (P->opt.precision == IFFD_PREC_FP64) ? tune_transform<double>(P, a, w, st, tm)
                                                 : tune_transform<float>(P, a, w, st, tm);
       if (rc) return rc;
@@ -292,6 +293,18 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
   auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
+  if (pipelined == 3) {
+    // double-float transforms for the whole plan (FP64 IFFD plans whose every
+    // direction has a warp-FFT pass of length 64, 128 or 256)
+    if (!f64 || !dfq_eligible(P))
+      return fail(IFFD_ERR_UNSUPPORTED, "double-float transforms need an FP64 IFFD plan whose every direction has "
+                                        "D = {0,1} and a warp-FFT length of 64, 128 or 256");
+    if (pencils_transform > 0) return fail(IFFD_ERR_INVALID_ARG, "the double-float pass has a fixed tile");
+    P.dfq = 1;
+    pipelined = -1;
+  } else if (f64 && (pencils_transform > 0 || (pipelined >= 0 && pipelined <= 2))) {
+    P.dfq = 0;  // an FP64-pipe transform geometry set by hand
+  }
   if (pipelined == 2) {
     if (f64 ? wpass_len(P.axd[axis]) == 0 : wpass_len(P.axf[axis]) == 0)
       return fail(IFFD_ERR_UNSUPPORTED, "the warp-FFT pass needs a D = {0,1} direction of FFT length 64, 128, 256 "
@@ -301,7 +314,7 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
     (f64 ? P.pipe_d : P.pipe_f)[axis] = 0;
     pipelined = -1;
   } else if (pipelined > 2) {
-    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1 or 2 (or < 0)");
+    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1, 2 or 3 (or < 0)");
   } else if (pencils_transform > 0 || pipelined >= 0) {
     (f64 ? P.warp_d : P.warp_f)[axis] = 0;  // a block-kernel geometry set by hand
   }
@@ -340,6 +353,19 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   const Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
+  if (f64 && P.dfq) {  // double-float warp pass: fixed tile and radices 8, 8, then 4 or 2
+    const int N = wpass_len(P.axq[axis]);
+    if (pencils_transform) *pencils_transform = wpass_pencils(N);
+    if (pencils_stiffness)
+      *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
+    const int rad[3] = {8, 8, N == 256 ? 4 : 2};
+    const int ns = N == 64 ? 2 : 3;
+    if (nstages) *nstages = ns;
+    if (radices)
+      for (int s = 0; s < ns; ++s) radices[s] = rad[s];
+    if (pipelined) *pipelined = 3;
+    return IFFD_OK;
+  }
   const int wd = f64 ? f64_warp_len(P, axis) : 0;
   if (pencils_transform) *pencils_transform = f64 ? (wd ? wpass_pencils(wd) : P.PPd[axis]) : f32_geom(P, axis).PP;
   if (pencils_stiffness)

@@ -23,6 +23,11 @@ MIX = [(2, 30, 4), (3, 16, 2), (3, 24, 3), (3, 32, 4), (3, 16, 5), (3, 24, 6), (
 def _alone(torch, d, n, p, f, precision):
     from paper_2512_20269_gb300 import IFFDPlan
     plan = IFFDPlan(d, n, p, precision=precision, true_residual=False)
+    if precision == "fp64":
+        # the engine runs FP64 systems on the FP64-pipe block kernel (not the
+        # double-float passes that stand-alone FP64 plans take by default)
+        for a in range(d):
+            plan.set_geometry(a, pipelined=False)
     u, info = plan.pcg_solve(f)
     return u.clone(), info
 

@@ -136,6 +136,10 @@ def test_fp64_warp_pass_matches_oracle_and_block_kernel(d, ns, p, knots):
     block = IFFDPlan(d, list(ns), p, **kw)
     warp_axes = [a for a in range(d) if _warp_len64(ns[a], p)]
     for a in range(d):
+        # the FP64-pipe block kernel (plans whose every direction has a warp
+        # pass default to the double-float passes instead)
+        block.set_geometry(a, pipelined=False)
+        plan.set_geometry(a, pipelined=False)
         assert not plan.tiles(a)["warp"]  # opt-in for FP64
     for a in warp_axes:
         plan.set_geometry(a, warp=True)
@@ -163,6 +167,8 @@ def test_fp64_warp_pass_pcg():
     from paper_2512_20269_gb300 import IFFDPlan
     for ns, p in (((64, 128, 128), 4), ((64, 32, 64), 3)):
         plan = IFFDPlan(3, ns, p)
+        for a in range(3):
+            plan.set_geometry(a, pipelined=False)  # FP64-pipe block kernel
         f = _gpu(torch, inputs.rhs(plan.shape, "normal", seed=6 + p))
         ub, ib = plan.pcg_solve(f)
         for a in range(3):
