@@ -71,6 +71,14 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
     its d - 1 directions, adds 2 / (d - 1). PCG update 48 B/DoF."""
     per_pass = 2.5 * math.log2(n) + 2 * n_out
     if kind.startswith("precond"):
+        if precision == "df":
+            # double-float passes (FP64 accuracy on the FP32 pipe): each pass
+            # reads and writes 8 B per DoF (FP64 or a float pair); the last
+            # backward pass also reads r for the fused dot product (averaged
+            # over the d - 1 backward directions). They are bound by FP32
+            # instruction issue (ncu), far from HBM; reported against HBM.
+            byt = {"precond_fwd": 16.0, "precond_fused": 16.0, "precond_bwd": 16.0 + 8.0 / (d - 1)}[kind]
+            return byt * N, "B", "hbm"
         if precision == "fp32":
             # FP32 intermediates: the first FWD pass reads FP64 and writes FP32
             # (12 B/DoF), the last BWD pass the reverse (12), the others read
@@ -539,10 +547,11 @@ def main():
     eff = {"precond_fwd": applies * (w.d - 1), "precond_fused": applies, "precond_bwd": applies * (w.d - 1),
            "stiff_first": args.steps * iters, "stiff_mid": args.steps * iters, "stiff_last": args.steps * iters,
            "pcg_update": args.steps * iters}
+    arith = "df" if all(plan.tiles(a).get("double_float") for a in range(w.d)) else "fp64"
     for kind, (cnt, kms) in prof.items():
         if cnt == 0:
             continue
-        amount, unit, bound = algorithmic(kind, w.d, w.n, w.p, n_out, w.N, "fp64")
+        amount, unit, bound = algorithmic(kind, w.d, w.n, w.p, n_out, w.N, arith)
         entry = {"launches": cnt, "ms": kms, "share": kms / total_k}
         if amount is not None:
             n_eff = min(cnt, eff.get(kind, cnt))
@@ -589,8 +598,13 @@ def main():
 
     variants = {}
     if not args.no_variants:
-        for name, prec, pc, reps in (("fp32_transform", "fp32", "iffd", args.steps), ("exact_fd", "fp64", "exact_fd", 2)):
-            pv = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=False).autotune()
+        for name, prec, pc, reps in (("fp32_transform", "fp32", "iffd", args.steps), ("exact_fd", "fp64", "exact_fd", 2),
+                                     ("fp64_pipe_transforms", "fp64", "iffd", args.steps)):
+            pv = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=False)
+            if name == "fp64_pipe_transforms":  # FP64 arithmetic on the FP64 pipe instead of double-float
+                for a in range(w.d):
+                    pv.set_geometry(a, pipelined=False)
+            pv.autotune()
             pv.pcg_solve(f, u_dev)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
@@ -601,7 +615,11 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             vms = a.elapsed_time(b) / reps
-            pchk = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=True).autotune()
+            pchk = IFFDPlan(w.d, w.n, w.p, precision=prec, precond=pc, true_residual=True)
+            if name == "fp64_pipe_transforms":
+                for a in range(w.d):
+                    pchk.set_geometry(a, pipelined=False)
+            pchk.autotune()
             _, ichk = pchk.pcg_solve(f, u_dev)
             variants[name] = {"value": w.N / (vms / 1e3), "unit": UNIT, "ms_per_solve": vms, "iters": iv["iters"],
                               "true_rel_res": ichk["true_rel_res"]}
@@ -678,8 +696,12 @@ def main():
     # first and last pass and 8 for the others
     apply_stats = {}
     if not args.no_variants:
-        for name, prec in (("fp64", "fp64"), ("fp32_transform", "fp32")):
-            pa = IFFDPlan(w.d, w.n, w.p, precision=prec, true_residual=False).autotune()
+        for name, prec in (("fp64", "fp64"), ("fp32_transform", "fp32"), ("fp64_pipe", "fp64")):
+            pa = IFFDPlan(w.d, w.n, w.p, precision=prec, true_residual=False)
+            if name == "fp64_pipe":
+                for a in range(w.d):
+                    pa.set_geometry(a, pipelined=False)
+            pa.autotune()
             zz = pa.empty()
             for _ in range(3):
                 pa.apply_preconditioner(f, zz)
@@ -693,9 +715,14 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             ams = a.elapsed_time(b) / reps
-            bpd = (16.0 * (2 * w.d - 2) + 24.0) if prec == "fp64" else (24.0 + 8.0 * (2 * w.d - 3))
+            df_mode = prec == "fp64" and all(pa.tiles(a).get("double_float") for a in range(w.d))
+            if prec == "fp32":
+                bpd = 24.0 + 8.0 * (2 * w.d - 3)
+            else:  # FP64: 16 B per pass; the FP64-pipe fused pass also reads 1/sum(lambda)
+                bpd = 16.0 * (2 * w.d - 1) + (0.0 if df_mode else 8.0)
             gbs = bpd * w.N / (ams / 1e3) / 1e9
             apply_stats[name] = {"ms": ams, "applies_per_s": 1e3 / ams, "alg_bytes_per_dof": bpd,
+                                 "arithmetic": "double-float" if (prec == "fp64" and df_mode) else prec,
                                  "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
                                  "tiles": [pa.tiles(k) for k in range(w.d)]}
             del pa, zz

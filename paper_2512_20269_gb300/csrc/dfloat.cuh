@@ -62,10 +62,14 @@ __device__ __forceinline__ df two_sum(float a, float b) {
   return {s, e};
 }
 
+// The sum leaves the pair unnormalised: lo = (error of hi + hi) + a.lo + b.lo
+// may exceed ulp(hi) / 2 by a few units. The next product (or fma)
+// renormalises (its fast_two_sum), which happens at least once per FFT stage
+// (the twiddle products) and in every separation step; the error bound of the
+// sum stays near 2^-47 of |a| + |b|. Saves 3 of 11 instructions per addition.
 __device__ __forceinline__ df operator+(df a, df b) {
   const df s = two_sum(a.hi, b.hi);
-  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-  return fast_two_sum(s.hi, e);
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
 
 __device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
@@ -162,6 +166,15 @@ __host__ __device__ __forceinline__ int clz32(unsigned x) {
 #endif
 }
 
+// The rare values outside the integer route: a real branch to a function of
+// its own (kept out of line so that the common path carries no float64
+// instruction).
+static __device__ __noinline__ df to_df_fp64(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+static __device__ __noinline__ double float_to_double_fp64(float f) { return (double)f; }
+
 // x = hi + lo with hi the first 24 significant bits of x (truncated) and lo
 // the next 29 bits rounded to 24 (relative error <= 2^-48 of |x|), from the
 // bit pattern of x. The binary exponent of x must lie in [-74, 127] (float
@@ -174,8 +187,12 @@ __host__ __device__ __forceinline__ df to_df(double x) {
   const int fe = (int)((h32 >> 20) & 0x7FFu) - 896;  // float exponent field of hi
   if ((b << 1) == 0) return {float_of(sign), 0.f};
   if (fe < 53 || fe > 254) {
+#ifdef __CUDA_ARCH__
+    return to_df_fp64(x);
+#else
     const float h = (float)x;
     return {h, (float)(x - (double)h)};
+#endif
   }
   const float h = float_of(sign | ((unsigned)fe << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
   const unsigned r = l32 & 0x1FFFFFFFu;  // x - hi = r 2^(fe - 179)
@@ -193,7 +210,13 @@ __host__ __device__ __forceinline__ double float_to_double_bits(float f) {
   const unsigned e = (u >> 23) & 0xFFu;
   const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
   if ((u & 0x7FFFFFFFu) == 0) return double_of(s);
-  if (e == 0 || e == 255) return (double)f;  // subnormal, inf, nan
+  if (e == 0 || e == 255) {  // subnormal, inf, nan
+#ifdef __CUDA_ARCH__
+    return float_to_double_fp64(f);
+#else
+    return (double)f;
+#endif
+  }
   return double_of(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29));
 }
 
