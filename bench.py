@@ -346,7 +346,7 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
         budget = 64 << 30
         outs = [torch.empty_like(f) for *_, f in systems]
 
-        eng = IFFDEngine(budget, precision="fp32", autotune=not args.no_autotune)
+        eng = IFFDEngine(budget, precision="fp32", autotune=not args.no_autotune, persistent=args.persistent)
 
         def solve_all():
             k0 = eng.stats()["kernel_launches"]
@@ -370,9 +370,12 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
                      "config": {"workload": "batched_512_cubes", "problems": len(probs), "systems": len(systems),
                                 "dofs": int(total), "n": list(inputs.BATCH_N), "p": list(inputs.BATCH_P),
                                 "precond": "IFFD, FP32 transforms", "pcg": "fp64", "seed": 3,
-                                "autotune": not args.no_autotune},
+                                "autotune": not args.no_autotune, "persistent": args.persistent},
                      "iters_min_max_mean": [min(iters), max(iters), float(np.mean(iters))],
                      "gpu_launches": kl,
+                     "launch_mode": ("one persistent launch per engine step over a device work queue (block "
+                                     "transform kernels)" if args.persistent else
+                                     "captured graph of batched launches per iteration"),
                      "timing": "wall clock around submit + engine steps to completion; plans cached, arena "
                                "allocated once (setup excluded)"})
     else:
@@ -449,6 +452,8 @@ def main():
                          "variable coefficient; batched: 512 uneven 3D problems; serving: Poisson request stream")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-autotune", action="store_true", help="batched: default launch geometry")
+    ap.add_argument("--persistent", action="store_true",
+                    help="batched: each engine step as one persistent launch over a device work queue")
     ap.add_argument("--serve-iters", type=int, default=2, help="serving: PCG iterations per engine step")
     ap.add_argument("--serve-cap-dofs", type=int, default=0,
                     help="serving: cap on the DoFs in flight (0 = HBM budget only)")

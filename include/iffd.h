@@ -48,7 +48,7 @@ typedef enum {
   IFFD_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
   IFFD_ERR_NOT_CONVERGED = 6,/* PCG reached maxit without the relative residual rtol */
   IFFD_ERR_BREAKDOWN = 7,    /* PCG breakdown: (p, A p) <= 0, (r, z) <= 0, or NaN/Inf */
-  IFFD_ERR_TIMEOUT = 8       /* reserved: a bounded device wait expired */
+  IFFD_ERR_TIMEOUT = 8       /* a bounded device wait expired (persistent engine launch) */
 } iffd_status;
 
 /* Arithmetic of the preconditioner transforms (the PCG vectors, residuals,
@@ -405,6 +405,21 @@ int iffd_engine_step(iffd_engine_handle e, int iterations, int* active);
 int iffd_engine_poll(iffd_engine_handle e, iffd_completion* out, int capacity, int* count);
 /* Active requests, free arena bytes, kernels launched so far (any may be NULL). */
 int iffd_engine_stats(iffd_engine_handle e, int* active, size_t* bytes_free, long long* kernel_launches);
+/* Launch mode of the engine's iterations (only while no request is active).
+ * on = 1: every iffd_engine_step runs its `iterations` PCG iterations of all
+ * active requests as ONE persistent kernel launch that walks a device work
+ * queue of (request, phase, tile) items: CTAs take items in ticket order; an
+ * item starts once its request has completed every earlier item (a
+ * per-request counter); the device bodies, tiles and reduction orders are
+ * those of the per-phase kernels, so each result is bitwise that of
+ * iffd_pcg_solve with the same kernels (transform passes: the block kernel --
+ * the engine's plans then run no warp-FFT pass; degrees 2..8). Every wait is
+ * bounded by wait_limit polls of ~64 ns (<= 0: 2^26); a wait that runs out
+ * makes the step return IFFD_ERR_TIMEOUT (that step's results are not valid)
+ * instead of hanging. inject_stall = 1 is a test hook that makes one item
+ * wait on a count that is never reached (so the timeout path runs).
+ * on = 0: one captured graph of batched launches per iteration (default). */
+int iffd_engine_set_persistent(iffd_engine_handle e, int on, long long wait_limit, int inject_stall);
 int iffd_engine_destroy(iffd_engine_handle e);
 
 /* ---------------------------------------------------------------------------

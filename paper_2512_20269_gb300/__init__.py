@@ -421,10 +421,14 @@ class IFFDEngine:
     while their workspace fits the device arena of `budget_bytes`; step() runs
     one engine step (initialise new requests, `iterations` PCG iterations of
     every active request, retire finished ones); poll() returns completions.
+    `persistent`: each step's iterations run as one persistent launch over a
+    device work queue (iffd_engine_set_persistent); `wait_limit` bounds its
+    device waits (polls), `inject_stall` is the test hook of that call.
     """
 
     def __init__(self, budget_bytes: int, precision: str = "fp32", rtol: float = 1e-8, maxit: int = 500,
-                 flexible: bool = False, stream=None, autotune: bool = False):
+                 flexible: bool = False, stream=None, autotune: bool = False, persistent: bool = False,
+                 wait_limit: int = 0, inject_stall: bool = False):
         self._lib = _lib.load()
         opt = iffd_options()
         self._lib.iffd_default_options(ctypes.byref(opt))
@@ -440,6 +444,9 @@ class IFFDEngine:
                                            ctypes.byref(h)), "iffd_engine_create")
         self._h = h
         self._keep = {}  # request id -> (f, u) tensors kept alive until completion
+        if persistent or inject_stall:
+            check(self._lib.iffd_engine_set_persistent(h, int(persistent), int(wait_limit), int(inject_stall)),
+                  "iffd_engine_set_persistent")
 
     @staticmethod
     def _flags(d, dirichlet):

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("iffd_engine_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p]),
     ("iffd_engine_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(iffd_completion), ctypes.c_int, c_int_p]),
     ("iffd_engine_stats", ctypes.c_int, [ctypes.c_void_p, c_int_p, c_size_t_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("iffd_engine_set_persistent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
     ("iffd_engine_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("iffd_batch_workspace_bytes", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), c_int_p,
                                                   c_size_t_p]),

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libiffd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["host_setup.cpp", "precond.cu", "precond_warp64.cu", "precond_warp128.cu", "precond_warp256.cu",
            "precond_warp512.cu", "precond_wdf64.cu", "precond_wdf128.cu", "precond_wdf256.cu", "stiffness.cu", "pcg.cu", "fd.cu", "capi.cu", "noalloc.cu", "varcoef.cu", "engine.cu",
-           "tune.cu", "general.cu", "peak.cu", "slab.cu"]
+           "tune.cu", "general.cu", "peak.cu", "slab.cu", "persist.cu"]
 
 
 def _nvcc() -> str:

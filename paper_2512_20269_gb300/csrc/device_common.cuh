@@ -54,6 +54,22 @@ __device__ __forceinline__ T ldg(const T* p) {
   return __ldg(p);
 }
 
+// Loads of solver data (vectors, partial sums, solve states). With CG set
+// they go through the L2-coherent path (ld.global.cg): in one persistent
+// launch, data written by other CTAs after this SM cached a line must not be
+// read from L1 or the read-only cache. ldd: plain load otherwise; ldr: the
+// read-only cache otherwise (data that no kernel of the launch writes).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldd(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+template <bool CG, typename T>
+__device__ __forceinline__ T ldr(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
 __device__ __forceinline__ float shfl_xor(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 __device__ __forceinline__ double shfl_xor(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 

@@ -95,6 +95,7 @@ struct Sys {
   size_t off, bytes;
   char* ws;
   int phase;  // 0: admitted, not initialised; 1: iterating
+  int slot;   // index among the active systems (persistent launch counters)
 };
 
 // Growable device buffer.
@@ -151,6 +152,17 @@ struct Engine {
   long long graph_kernels = 0;
   int graph_lanes = 0;
   std::vector<long long> graph_ids;
+  // persistent mode: one launch per step walks a device work queue
+  // (persist.cu) instead of replaying the graph of batched launches
+  bool persistent = false;
+  long long wait_limit = 1LL << 26;  // polls of a bounded wait (64 ns sleeps)
+  int inject_stall = 0;              // test hook: the first dependent range waits on a count never reached
+  DevBuf dpers;                      // ranges, counters and the queue of the persistent launch
+  std::vector<long long> pers_ids;   // membership the staged descriptors were built for
+  std::vector<PRange> pers_ranges;   // host copy of the ranges of the current staging (one iteration)
+  size_t pers_smem = 0;
+  long long pers_items_per_iter = 0;
+  PQueue* hqueue = nullptr;          // pinned copy of the queue after a launch
   // lane streams (forked from and joined to `st` inside the captured graph)
   std::vector<cudaStream_t> lane_st;
   std::vector<cudaEvent_t> lane_ev;
@@ -166,6 +178,7 @@ struct Engine {
     for (auto& kv : plans) plan_release(kv.second);
     if (arena_mem) cudaFree(arena_mem);
     if (hstates) cudaFreeHost(hstates);
+    if (hqueue) cudaFreeHost(hqueue);
   }
 };
 
@@ -196,8 +209,10 @@ struct PassLaunchB {
   int wN = 0;     // > 0: every system runs the FP32 warp-FFT pass of this length
   int wkind = 0;  // and this transform kind (AxisTab::kind)
   size_t off_desc = 0, off_prefix = 0;
-  void add(const PassDesc<Tc, Tin, Tout>& d, int tiles, size_t sm) {
+  std::vector<int> sid;  // slot of the system of every descriptor
+  void add(const PassDesc<Tc, Tin, Tout>& d, int tiles, size_t sm, int slot) {
     desc.push_back(d);
+    sid.push_back(slot);
     prefix.push_back(prefix.back() + tiles);
     smem = std::max(smem, sm);
   }
@@ -206,6 +221,7 @@ struct PassLaunchB {
 struct StiffLaunchB {
   int p = 0, stage = 0;
   std::vector<StiffDesc> desc;
+  std::vector<int> sid;
   std::vector<long long> prefix{0};
   size_t smem = 0;
   size_t off_desc = 0, off_prefix = 0;
@@ -213,12 +229,14 @@ struct StiffLaunchB {
 
 struct VecLaunchB {
   std::vector<VecDesc> desc;
+  std::vector<int> sid;
   std::vector<long long> prefix{0};
   size_t off_desc = 0, off_prefix = 0;
 };
 
 struct FinLaunchB {
   std::vector<FinDesc> desc;
+  std::vector<int> sid;
   int phase = 0;
   size_t off = 0;
 };
@@ -303,7 +321,7 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
           D.partial = vpart(*s);
         }
         seq->d64[k].add(D, precond_tiles(P.dims, a, P.PPd[a]),
-                        precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].F, sizeof(double)));
+                        precond_smem_bytes(P.PPd[a], P.ldtd[a], P.axd[a].F, sizeof(double)), s->slot);
       }
     }
     return;
@@ -324,7 +342,8 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.done = done;
       D.in = vr(*s);
       D.out = vtf(*s);
-      pass_slot(seq->f_first, D.wN, D.ax.kind, PM_FWD, 0).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
+      pass_slot(seq->f_first, D.wN, D.ax.kind, PM_FWD, 0)
+          .add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem, s->slot);
     }
     const int axes[3] = {1, d - 1, 1};
     for (int k = 0; k < 3; ++k) {
@@ -333,7 +352,8 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       auto D = pdesc_same<float>(P, a, P.axf, P.PPf, P.ldtf, done);
       D.in = vtf(*s);
       D.out = vtf(*s);
-      pass_slot(seq->f_mid[k], D.wN, D.ax.kind, mid_modes[k], 0).add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem);
+      pass_slot(seq->f_mid[k], D.wN, D.ax.kind, mid_modes[k], 0)
+          .add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem, s->slot);
     }
     {
       PassDesc<float, float, double> D{};
@@ -346,7 +366,8 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       D.dot0 = vr(*s);
       D.dot1 = use_q ? vq(*s) : nullptr;
       D.partial = vpart(*s);
-      pass_slot(seq->f_last, D.wN, D.ax.kind, PM_BWD, ndot).add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem);
+      pass_slot(seq->f_last, D.wN, D.ax.kind, PM_BWD, ndot)
+          .add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem, s->slot);
     }
   }
 }
@@ -522,10 +543,12 @@ void build_lane(const Engine* E, const std::vector<const Sys*>& sys, IterSeq* ou
       D.partial = vpart(*s);
       D.done = &vst(*s)->done;
       l.desc.push_back(D);
+      l.sid.push_back(s->slot);
       l.prefix.push_back(l.prefix.back() + stiff_tiles(P.dims, axis, S.PP));
       l.smem = std::max(l.smem, (size_t)(stage == SS_FIRST ? 1 : 2) * S.PP * S.ldt * sizeof(double));
     }
     it.fpq.desc.push_back({vst(*s), vpart(*s), stiff_tiles(P.dims, 0, P.PPs[0])});
+    it.fpq.sid.push_back(s->slot);
     VecDesc v{};
     v.x = s->u;
     v.r = vr(*s);
@@ -535,10 +558,13 @@ void build_lane(const Engine* E, const std::vector<const Sys*>& sys, IterSeq* ou
     v.N = P.dims.N;
     v.part_rr = vpart(*s);
     it.upd.desc.push_back(v);
+    it.upd.sid.push_back(s->slot);
     it.upd.prefix.push_back(it.upd.prefix.back() + vec_grid(P.dims.N));
     it.frr.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
+    it.frr.sid.push_back(s->slot);
     const int PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_geom(P, 0).PP : P.PPd[0];
     it.frz.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0)});
+    it.frz.sid.push_back(s->slot);
   }
   // A system's three sweeps must run in stage order. Groups are created in the
   // order systems are met (a 2D system creates no MID group), so order them by
@@ -638,7 +664,165 @@ int build_iteration(Engine* E) {
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
   E->graph_ids.clear();
   for (auto& s : E->active) E->graph_ids.push_back(s.id);
+  E->pers_ids.clear();  // the persistent ranges' descriptors in diter were overwritten
   E->graph_lanes = (int)seqs.size();
+  return IFFD_OK;
+}
+
+// ---- persistent launch: the item ranges of one iteration of every active
+// system (all lanes), phase-major. Phase slots: the three stiffness stages,
+// (p, A p), the update, (r, r), the five (3D) or three (2D) transform passes
+// and (r, z); within a slot, the lanes' launches in lane order and their
+// systems in launch order. `need` is filled per iteration by the caller.
+template <typename L>
+void add_ranges(std::vector<PRange>& out, char* base, L& l, size_t dsize, int kind, int arg) {
+  for (size_t j = 0; j < l.desc.size(); ++j) {
+    PRange r{};
+    r.ntiles = (int)(l.prefix[j + 1] - l.prefix[j]);
+    if (r.ntiles <= 0) continue;
+    r.kind = kind;
+    r.arg = arg;
+    r.sys = l.sid[j];
+    r.desc = base + l.off_desc + j * dsize;
+    r.desc_bytes = (int)dsize;
+    out.push_back(r);
+  }
+}
+
+void add_fin_ranges(std::vector<PRange>& out, char* base, FinLaunchB& f) {
+  for (size_t j = 0; j < f.desc.size(); ++j) {
+    PRange r{};
+    r.ntiles = 1;
+    r.kind = PK_FIN;
+    r.arg = f.phase;
+    r.sys = f.sid[j];
+    r.desc = base + f.off + j * sizeof(FinDesc);
+    r.desc_bytes = (int)sizeof(FinDesc);
+    out.push_back(r);
+  }
+}
+
+int build_persistent(Engine* E) {
+  std::map<std::pair<int, int>, std::vector<const Sys*>> lanes;
+  for (auto& s : E->active) lanes[lane_key(s)].push_back(&s);
+  std::vector<IterSeq> seqs(lanes.size());
+  {
+    size_t k = 0;
+    for (auto& kv : lanes) build_lane(E, kv.second, &seqs[k++]);
+  }
+  Staging sg;
+  for (auto& it : seqs) {
+    for (auto& l : it.stiff) stage_pass(sg, l);
+    it.fpq.off = sg.put(it.fpq.desc);
+    it.frr.off = sg.put(it.frr.desc);
+    it.frz.off = sg.put(it.frz.desc);
+    stage_pass(sg, it.upd);
+    stage_precond(sg, it.pc);
+  }
+  IFFD_CUDA(E->diter.reserve(sg.bytes.size()));
+  char* base = E->diter.p;
+  IFFD_CUDA(cudaMemcpyAsync(base, sg.bytes.data(), sg.bytes.size(), cudaMemcpyHostToDevice, E->st));
+  std::vector<PRange>& R = E->pers_ranges;
+  R.clear();
+  size_t smem = 0;
+  for (int stage = SS_FIRST; stage <= SS_LAST; ++stage)
+    for (auto& it : seqs)
+      for (auto& l : it.stiff)
+        if (l.stage == stage) {
+          add_ranges(R, base, l, sizeof(StiffDesc), PK_STIFF, stage * 32 + l.p);
+          smem = std::max(smem, l.smem);
+        }
+  for (auto& it : seqs) add_fin_ranges(R, base, it.fpq);
+  for (auto& it : seqs) add_ranges(R, base, it.upd, sizeof(VecDesc), PK_UPD, 0);
+  for (auto& it : seqs) add_fin_ranges(R, base, it.frr);
+  for (int k = 0; k < 5; ++k) {
+    for (auto& it : seqs) {
+      PrecondSeq& q = it.pc;
+      if (!q.fp32) {
+        auto& l = q.d64[k];
+        add_ranges(R, base, l, sizeof(PassDesc<double, double, double>), PK_PASS_D, l.mode * 4 + l.ndot);
+        smem = std::max(smem, l.smem);
+      } else if (k == 0) {
+        for (auto& kv : q.f_first) {
+          if (kv.second.wN) return fail(IFFD_ERR_UNSUPPORTED, "persistent engine launch: warp-FFT passes");
+          add_ranges(R, base, kv.second, sizeof(PassDesc<float, double, float>), PK_PASS_F_IN, 0);
+          smem = std::max(smem, kv.second.smem);
+        }
+      } else if (k == 4) {
+        for (auto& kv : q.f_last) {
+          if (kv.second.wN) return fail(IFFD_ERR_UNSUPPORTED, "persistent engine launch: warp-FFT passes");
+          add_ranges(R, base, kv.second, sizeof(PassDesc<float, float, double>), PK_PASS_F_OUT, kv.second.ndot);
+          smem = std::max(smem, kv.second.smem);
+        }
+      } else {
+        for (auto& kv : q.f_mid[k - 1]) {
+          if (kv.second.wN) return fail(IFFD_ERR_UNSUPPORTED, "persistent engine launch: warp-FFT passes");
+          add_ranges(R, base, kv.second, sizeof(PassDesc<float, float, float>), PK_PASS_F_MID, kv.second.mode);
+          smem = std::max(smem, kv.second.smem);
+        }
+      }
+    }
+  }
+  for (auto& it : seqs) add_fin_ranges(R, base, it.frz);
+  long long items = 0;
+  for (auto& r : R) items += r.ntiles;
+  E->pers_items_per_iter = items;
+  E->pers_smem = smem;
+  E->pers_ids.clear();
+  for (auto& s : E->active) E->pers_ids.push_back(s.id);
+  E->graph_ids.clear();  // the graph's descriptors in diter were overwritten
+  // the host staging must outlive the asynchronous upload
+  IFFD_CUDA(cudaStreamSynchronize(E->st));
+  return IFFD_OK;
+}
+
+// One persistent launch running `iterations` iterations of every active
+// system; returns IFFD_ERR_TIMEOUT if a bounded wait ran out.
+int run_persistent(Engine* E, int iterations) {
+  const int nsys = (int)E->active.size();
+  std::vector<PRange> all;
+  all.reserve(E->pers_ranges.size() * iterations);
+  std::vector<long long> cnt(nsys, 0);
+  long long first = 0;
+  for (int it = 0; it < iterations; ++it)
+    for (const PRange& r0 : E->pers_ranges) {
+      PRange r = r0;
+      r.first = first;
+      r.need = cnt[r.sys];
+      cnt[r.sys] += r.ntiles;
+      first += r.ntiles;
+      all.push_back(r);
+    }
+  if (E->inject_stall) {
+    // test hook: the first range that depends on earlier work waits on a
+    // count nothing reaches, so its waits run out
+    for (auto& r : all)
+      if (r.need > 0) {
+        r.need = 1LL << 62;
+        break;
+      }
+  }
+  const size_t off_cnt = al256(all.size() * sizeof(PRange));
+  const size_t off_q = off_cnt + al256(nsys * sizeof(long long));
+  const size_t bytes = off_q + al256(sizeof(PQueue));
+  std::vector<char> host(bytes, 0);
+  if (!all.empty()) std::memcpy(host.data(), all.data(), all.size() * sizeof(PRange));
+  IFFD_CUDA(E->dpers.reserve(bytes));
+  char* d = E->dpers.p;
+  IFFD_CUDA(cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, E->st));
+  const int grid = std::min<long long>(persistent_grid(E->pers_smem), std::max<long long>(1, first));
+  if (grid < 1) return fail(IFFD_ERR_UNSUPPORTED, "persistent engine launch does not fit on an SM");
+  IFFD_CUDA(launch_persistent(reinterpret_cast<PRange*>(d), (int)all.size(), first,
+                              reinterpret_cast<long long*>(d + off_cnt), reinterpret_cast<PQueue*>(d + off_q),
+                              E->wait_limit, E->opt.rtol * E->opt.rtol, E->opt.maxit, E->pers_smem, grid, E->st));
+  ++E->launches;
+  if (!E->hqueue) IFFD_CUDA(cudaHostAlloc((void**)&E->hqueue, sizeof(PQueue), cudaHostAllocDefault));
+  IFFD_CUDA(cudaMemcpyAsync(E->hqueue, d + off_q, sizeof(PQueue), cudaMemcpyDeviceToHost, E->st));
+  // the host copy must outlive the upload; the status is read after the step's sync
+  IFFD_CUDA(cudaStreamSynchronize(E->st));
+  if (E->hqueue->status != 0)
+    return fail(IFFD_ERR_TIMEOUT, "persistent engine launch: a bounded device wait ran out (results of this step "
+                                  "are not valid)");
   return IFFD_OK;
 }
 
@@ -715,6 +899,8 @@ static int engine_plan(iffd_engine* h, int d, int n, int p, const int* dirichlet
   const int rc = plan_create(d, nn, p, dir, &o, E.st, &P);
   if (rc) return rc;
   P->P.dfq = 0;  // the engine's batched FP64 passes are the block kernel
+  if (E.persistent)
+    for (int a = 0; a < d; ++a) P->P.warp_f[a] = 0;  // the persistent launch runs the block kernel
   E.plans[key] = P;
   *out = P;
   return IFFD_OK;
@@ -734,6 +920,8 @@ int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const int* dir
   if (!h || !f || !u || !id) return fail(IFFD_ERR_INVALID_ARG, "NULL argument");
   if (f == u) return fail(IFFD_ERR_INVALID_ARG, "f and u must not alias");
   Engine& E = h->E;
+  if (E.persistent && (p < kPersistMinP || p > kPersistMaxP))
+    return fail(IFFD_ERR_UNSUPPORTED, "the persistent engine launch serves degrees 2..8");
   iffd_plan* P = nullptr;
   int rc = engine_plan(h, d, n, p, dirichlet, &P);
   if (rc) return rc;
@@ -749,6 +937,8 @@ int iffd_engine_submit(iffd_engine_handle h, int d, int n, int p, const int* dir
       E.arena.release(off, need);
       return rc;
     }
+    if (E.persistent)
+      for (int a = 0; a < d; ++a) P->P.warp_f[a] = 0;
   }
   Sys s{};
   s.id = E.next_id++;
@@ -779,6 +969,7 @@ int engine_step(Engine& E, int iterations, int* active) {
   if (dev != E.device) return fail(IFFD_ERR_INVALID_ARG, "engine was created on another device");
   IFFD_CUDA(cudaEventRecord(E.ev, E.user_st));
   IFFD_CUDA(cudaStreamWaitEvent(E.st, E.ev, 0));
+  for (size_t i = 0; i < E.active.size(); ++i) E.active[i].slot = (int)i;
   // 1. initialise newly admitted systems
   std::vector<const Sys*> fresh;
   for (auto& s : E.active)
@@ -786,8 +977,19 @@ int engine_step(Engine& E, int iterations, int* active) {
   int rc = run_init(&E, fresh);
   if (rc) return rc;
   for (auto& s : E.active) s.phase = 1;
-  // 2. iterations of every active system (graph rebuilt when membership changed)
-  if (!E.active.empty() && iterations > 0) {
+  // 2. iterations of every active system: one persistent launch (descriptors
+  // rebuilt when membership changed), or the captured graph of batched
+  // launches (rebuilt when membership changed)
+  if (E.persistent && !E.active.empty() && iterations > 0) {
+    bool same = E.pers_ids.size() == E.active.size();
+    for (size_t i = 0; same && i < E.active.size(); ++i) same = E.pers_ids[i] == E.active[i].id;
+    if (!same) {
+      rc = build_persistent(&E);
+      if (rc) return rc;
+    }
+    rc = run_persistent(&E, iterations);
+    if (rc) return rc;
+  } else if (!E.active.empty() && iterations > 0) {
     bool same = E.graph && E.graph_ids.size() == E.active.size();
     for (size_t i = 0; same && i < E.active.size(); ++i) same = E.graph_ids[i] == E.active[i].id;
     if (!same) {
@@ -860,6 +1062,21 @@ int iffd_engine_stats(iffd_engine_handle h, int* active, size_t* bytes_free, lon
   if (active) *active = (int)h->E.active.size();
   if (bytes_free) *bytes_free = h->E.arena.available();
   if (kernel_launches) *kernel_launches = h->E.launches;
+  return IFFD_OK;
+}
+
+int iffd_engine_set_persistent(iffd_engine_handle h, int on, long long wait_limit, int inject_stall) {
+  g_err.clear();
+  if (!h) return fail(IFFD_ERR_INVALID_ARG, "NULL handle");
+  Engine& E = h->E;
+  if (!E.active.empty()) return fail(IFFD_ERR_INVALID_ARG, "change the launch mode only while no request is active");
+  E.persistent = on != 0;
+  E.wait_limit = wait_limit > 0 ? wait_limit : (1LL << 26);
+  E.inject_stall = inject_stall != 0;
+  if (E.persistent)
+    for (auto& kv : E.plans)
+      for (int a = 0; a < kv.second->P.d; ++a) kv.second->P.warp_f[a] = 0;
+  E.pers_ids.clear();
   return IFFD_OK;
 }
 

@@ -199,4 +199,49 @@ cudaError_t launch_pcg_update_batched(const VecDesc* sys, const long long* prefi
                                       cudaStream_t st);
 cudaError_t launch_finalize_batched(const FinDesc* sys, int nsys, int phase, double tol2, int maxit, cudaStream_t st);
 
+// ------------------------------------------------------ persistent engine
+// One persistent launch walks a device work queue of item ranges: the tiles
+// (or vector blocks, or the single reduction) of one system in one phase of
+// one PCG iteration. Ranges are listed phase-major (iteration, phase, system),
+// so an item waits only on items of its own system with earlier tickets.
+enum PersistKind : int {
+  PK_STIFF = 0,       // StiffDesc; arg = stage * 32 + p
+  PK_FIN = 1,         // FinDesc; arg = finalize phase
+  PK_UPD = 2,         // VecDesc (block = tile of the range)
+  PK_PASS_D = 3,      // PassDesc<double, double, double>; arg = mode * 4 + ndot
+  PK_PASS_F_IN = 4,   // PassDesc<float, double, float> (forward, first direction)
+  PK_PASS_F_MID = 5,  // PassDesc<float, float, float>; arg = mode
+  PK_PASS_F_OUT = 6   // PassDesc<float, float, double> (backward, first direction); arg = ndot
+};
+
+struct PRange {
+  long long first;   // first ticket of the range
+  int ntiles;        // items (tiles / blocks) in the range
+  int kind;          // PersistKind
+  int arg;
+  int sys;           // index of the system's completion counter
+  long long need;    // completed items of that system required before the range starts
+  const void* desc;  // device address of the system's descriptor
+  int desc_bytes;    // its size (copied to shared memory per item)
+  int pad;
+};
+
+struct PQueue {
+  unsigned long long head;  // next ticket
+  int status;               // 0, or IFFD_ERR_TIMEOUT (8) when a bounded wait ran out
+  int pad;
+};
+
+// Degrees the persistent launch carries (stiffness bodies instantiated).
+constexpr int kPersistMinP = 2, kPersistMaxP = 8;
+
+// Launches the persistent kernel over ranges[0..nranges) (total tickets
+// `total`); done_cnt: one counter per system, zero at launch; q: zeroed.
+// wait_limit bounds every wait (polls); smem: dynamic shared memory (the
+// largest of the items'); grid: CTAs (at most the resident count).
+cudaError_t launch_persistent(const PRange* ranges, int nranges, long long total, long long* done_cnt, PQueue* q,
+                              long long wait_limit, double tol2, int maxit, size_t smem, int grid, cudaStream_t st);
+// CTAs of the persistent kernel that fit on the GPU at once with smem bytes.
+int persistent_grid(size_t smem);
+
 }  // namespace iffd

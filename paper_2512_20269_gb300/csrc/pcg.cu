@@ -8,6 +8,7 @@
 // host can enqueue iterations ahead without synchronising.
 #include "device_common.cuh"
 #include "kernels.h"
+#include "pcg_dev.cuh"
 
 namespace iffd {
 
@@ -16,49 +17,6 @@ int vec_grid(long long N) {
   if (g > 4 * 152) g = 4 * 152;
   if (g < 1) g = 1;
   return (int)g;
-}
-
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double red[kThreads / 32];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;
-}
-
-// x = 0, r = f, partial ||f||^2 (block `blk` of `nblk`)
-__device__ __forceinline__ void init_body(const double* __restrict__ f, double* __restrict__ x, double* __restrict__ r,
-                                          long long N, double* __restrict__ partial, int blk, int nblk) {
-  double s = 0.0;
-  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)nblk * blockDim.x) {
-    const double v = f[i];
-    x[i] = 0.0;
-    r[i] = v;
-    s = fma(v, v, s);
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partial[blk] = s;
-}
-
-// x += alpha p, r -= alpha q, partial ||r||^2
-__device__ __forceinline__ void update_body(double* __restrict__ x, double* __restrict__ r,
-                                            const double* __restrict__ p, const double* __restrict__ q,
-                                            const SolveState* __restrict__ st, long long N,
-                                            double* __restrict__ partial, int blk, int nblk) {
-  const double alpha = st->alpha;
-  double s = 0.0;
-  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)nblk * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double rv = fma(-alpha, q[i], r[i]);
-    r[i] = rv;
-    s = fma(rv, rv, s);
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partial[blk] = s;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -131,79 +89,6 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ Au, lon
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-// status codes mirror iffd_status in include/iffd.h
-constexpr int kStOk = 0, kStNotConverged = 6, kStBreakdown = 7;
-
-__device__ __forceinline__ void finalize_body(SolveState* st, const double* __restrict__ partial, int nparts, int phase,
-                                              double tol2, int maxit) {
-  __shared__ double red[2][32];
-  if (phase != FP_FF && phase != FP_TRUE && st->done) return;
-  // fixed-order reduction: thread t sums parts t, t+1024, ...; then a fixed
-  // tree. The flexible beta also needs the second set partial[nparts..2 nparts).
-  const bool two = (phase == FP_RZ_FLEX);
-  double s = 0.0, s2 = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    s += partial[i];
-    if (two) s2 += partial[nparts + i];
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, off);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = s;
-    red[1][threadIdx.x >> 5] = s2;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double tot = 0.0, tot2 = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    tot += red[0][w];
-    tot2 += red[1][w];
-  }
-  switch (phase) {
-    case FP_FF:
-      st->ff = tot;
-      st->iters = 0;
-      st->status = kStOk;
-      st->done = (tot == 0.0) ? 1 : 0;
-      st->rr = tot;
-      break;
-    case FP_RZ0:
-      st->rz = tot;
-      if (!(tot > 0.0)) { st->status = kStBreakdown; st->done = 1; }
-      break;
-    case FP_PQ:
-      st->pq = tot;
-      if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
-      else st->alpha = st->rz / tot;
-      break;
-    case FP_RR:
-      st->rr = tot;
-      st->iters += 1;
-      if (!isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
-      else if (tot <= tol2 * st->ff) { st->status = kStOk; st->done = 1; }
-      else if (st->iters >= maxit) { st->status = kStNotConverged; st->done = 1; }
-      break;
-    case FP_RZ:
-      if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
-      else { st->beta = tot / st->rz; st->rz_old = st->rz; st->rz = tot; }
-      break;
-    case FP_RZ_FLEX:
-      // flexible (Polak-Ribiere) beta = (z_new, r_new - r_old) / (z_old, r_old)
-      //                              = -alpha (z_new, q) / rz_old;
-      // partial[0..nparts) holds (r,z), partial[nparts..2 nparts) holds (q,z)
-      st->zq = tot2;
-      if (!(tot > 0.0) || !isfinite(tot)) { st->status = kStBreakdown; st->done = 1; }
-      else { st->beta = -st->alpha * tot2 / st->rz; st->rz_old = st->rz; st->rz = tot; }
-      break;
-    case FP_TRUE:
-      st->zq = tot;  // ||f - A u||^2 of the final iterate
-      break;
-  }
 }
 
 __global__ void __launch_bounds__(1024)
