@@ -44,8 +44,12 @@ if ROOT not in sys.path:
 
 METRIC = "PCG-solved DoF/s at rel. res 1e-8, IGA-FFD vs exact FD on 1 GB300; % HBM peak"
 UNIT = "DoF/s"
-SRC_FILES = {"precond": "paper_2512_20269_gb300/csrc/precond.cu",
-             "stiff": "paper_2512_20269_gb300/csrc/stiffness.cu"}
+_CSRC = "paper_2512_20269_gb300/csrc/"
+# source files whose kernels a traffic record (profiles/ncu_traffic.txt) covers
+SRC_FILES = {"precond": [_CSRC + f for f in ("precond.cu", "precond_block.cuh", "device_common.cuh")],
+             "precond_df": [_CSRC + f for f in ("precond_warp.cuh", "dfloat.cuh", "device_common.cuh")],
+             "stiff": [_CSRC + f for f in ("stiffness.cu", "stiff_dev.cuh", "device_common.cuh")],
+             "pcg": [_CSRC + f for f in ("pcg.cu", "pcg_dev.cuh", "device_common.cuh")]}
 
 
 def measured_peaks():
@@ -103,17 +107,22 @@ def algorithmic(kind: str, d: int, n: int, p: int, n_out: int, N: int, precision
     return None, None, None
 
 
-def file_sha(rel: str) -> str:
+def file_sha(rel) -> str:
+    """sha256[:16] of one file, or of the concatenation of a list of files."""
+    h = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            return hashlib.sha256(fh.read()).hexdigest()[:16]
+        for r in ([rel] if isinstance(rel, str) else rel):
+            with open(os.path.join(ROOT, r), "rb") as fh:
+                h.update(fh.read())
     except Exception:
         return ""
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kind: str):
-    """DRAM bytes per launch of `kind` from the committed ncu summary, only if the
-    kernel source still has the hash recorded with the capture (else None)."""
+    """DRAM bytes per launch of `kind` (for transform passes `kind/arith`, the
+    pass arithmetic) from the committed ncu summary, only if the kernel sources
+    still have the hash recorded with the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -380,13 +389,18 @@ def run_other_workload(args, rank: int, world: int, local: int) -> int:
                                "allocated once (setup excluded)"})
     else:
         from paper_2512_20269_gb300.serving import Server
-        reqs = inputs.serving_requests()
+        # the configured 2000 req/s, or a lower rate (--serve-rate) at which one
+        # GPU keeps up, to show latency in normal operation
+        reqs = inputs.serving_requests(rate=args.serve_rate, duration=60.0 if args.serve_rate >= 2000 else
+                                       max(args.serve_seconds, 1.0))
         cap = args.serve_cap_dofs if args.serve_cap_dofs > 0 else None
         srv = Server(budget_bytes=150 * (1 << 30), precision="fp32", iterations_per_step=args.serve_iters,
                      max_inflight_dofs=cap)
-        st = srv.run(reqs, max_wall_s=args.serve_seconds)
+        # at a sustainable rate the run also drains the requests still in flight
+        st = srv.run(reqs, max_wall_s=args.serve_seconds if args.serve_rate >= 2000 else args.serve_seconds + 30.0)
         line.update({"value": st["dof_per_s"], "ms_per_step": None, "dtype": "f64",
-                     "config": {"workload": "serving_poisson_2000rps", "rate_rps": 2000, "arrival_window_s": 60,
+                     "config": {"workload": f"serving_poisson_{args.serve_rate:g}rps", "rate_rps": args.serve_rate,
+                                "arrival_window_s": 60 if args.serve_rate >= 2000 else max(args.serve_seconds, 1.0),
                                 "run_wall_s": args.serve_seconds, "budget_bytes": 150 * (1 << 30),
                                 "precond": "IFFD, FP32 transforms", "seed": 4, "max_inflight_dofs": cap,
                                 "iterations_per_step": args.serve_iters},
@@ -419,6 +433,9 @@ def run_probe(args) -> int:
             except IFFDError:
                 pass  # not eligible: block kernel
     f = torch.from_numpy(inputs.rhs(plan.shape, "normal", 1)).cuda()
+    torch.cuda.synchronize()
+    # profiler range: `ncu --profile-from-start off` captures only the operation
+    torch.cuda.profiler.start()
     for _ in range(max(1, args.probe_reps)):
         if args.probe == "precond":
             plan.apply_preconditioner(f)
@@ -435,6 +452,7 @@ def run_probe(args) -> int:
             _, info = plan.pcg_solve(f)
             print("iters", info["iters"], "rel_res", info["rel_res"])
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     print("ok", args.probe, "N", plan.N, [plan.tiles(k) for k in range(args.d)])
     return 0
 
@@ -455,6 +473,8 @@ def main():
     ap.add_argument("--persistent", action="store_true",
                     help="batched: each engine step as one persistent launch over a device work queue")
     ap.add_argument("--serve-iters", type=int, default=2, help="serving: PCG iterations per engine step")
+    ap.add_argument("--serve-rate", type=float, default=2000.0,
+                    help="serving: arrival rate (req/s); below 2000 the arrival window equals --serve-seconds")
     ap.add_argument("--serve-cap-dofs", type=int, default=0,
                     help="serving: cap on the DoFs in flight (0 = HBM budget only)")
     ap.add_argument("--probe", choices=["precond", "stiffness", "solve", "general"], default=None,
@@ -570,11 +590,14 @@ def main():
                 ach = amount / avg_s / 1e9
                 entry.update({"bound": bound, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                               "frac": ach / hbm_peak, "alg_per_launch": amount})
+        tk = ncu_traffic(f"{kind}/{arith}" if kind.startswith("precond") else kind)
+        if tk is not None:
+            entry["traffic"] = tk
         rooflines[kind] = entry
     dom = max((k for k in rooflines if "bound" in rooflines[k]), key=lambda k: rooflines[k]["ms"])
     d = rooflines[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": ncu_traffic(dom), "kernel": dom,
+                "frac": d["frac"], "traffic": d.get("traffic"), "kernel": dom,
                 "peak_source": (peak_src if d["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (measured copy)")}
 
     # ---------------- end to end: pinned host f -> device, solve, u -> host

@@ -42,6 +42,7 @@ BATCH = [
     (3, 20, 4, "fp32", "iffd", "const", ((1, 0), (1, 1), (0, 1)), 2, False),
     (3, 12, 3, "fp64", "exact_fd", "const", None, 1, False),
     (3, 16, 4, "fp64", "iffd", "sin", None, 1, False),
+    (3, 64, 4, "fp64", "iffd", "const", None, 2, False),  # double-float transforms: solved one by one
 ]
 
 
