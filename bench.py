@@ -724,12 +724,17 @@ def main():
     # first and last pass and 8 for the others
     apply_stats = {}
     if not args.no_variants:
-        for name, prec in (("fp64", "fp64"), ("fp32_transform", "fp32"), ("fp64_pipe", "fp64")):
+        for name, prec in (("fp64", "fp64"), ("fp32_transform", "fp32"), ("fp32_unpaired", "fp32"),
+                           ("fp64_pipe", "fp64")):
             pa = IFFDPlan(w.d, w.n, w.p, precision=prec, true_residual=False)
             if name == "fp64_pipe":
                 for a in range(w.d):
                     pa.set_geometry(a, pipelined=False)
             pa.autotune()
+            if name == "fp32_unpaired":  # the warp-FFT pass with one sequence per lane group
+                for a in range(w.d):
+                    if pa.tiles(a)["warp"]:
+                        pa.set_geometry(a, warp=True)
             zz = pa.empty()
             for _ in range(3):
                 pa.apply_preconditioner(f, zz)

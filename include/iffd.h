@@ -166,8 +166,14 @@ int iffd_autotune(iffd_handle h, void* ws, void* stream);
  * whose FFT length is 64, 128, 256 or 512, FP64 plans up to 256: DST-II/III
  * with n_reg of that length, DST-I with 2 (n_reg + 1); each pencil pair is
  * transformed by the lanes of one warp, register butterflies, fixed tile;
- * the default for such directions of FP32 plans, opt-in for FP64 plans),
- * < 0 unchanged. Setting a tile size or pipelined 0/1 selects the block
+ * opt-in for FP64 plans), 3 = double-float transforms for the whole plan
+ * (FP64 IFFD plans whose every direction has a warp-FFT pass of length 64,
+ * 128 or 256: FP64-accurate arithmetic on pairs of FP32 values; their
+ * default), 4 = the paired FP32 warp-FFT pass (FFT length 64, 128 or 256:
+ * every lane group carries two sequences, four pencils, at once; each
+ * pencil's values are bitwise those of pipelined 2, and so are the partial
+ * sums of the fused dot products; the default for the last direction of
+ * FP32 plans when it qualifies), < 0 unchanged. Setting a tile size or pipelined 0/1 selects the block
  * kernel. The block-kernel geometry does not change any transformed value; it
  * changes the grouping of the partial sums of the dot products (the warp-FFT
  * pass rounds differently, within the FP32 or FP64 tolerance). The batched
@@ -182,7 +188,8 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
  * sweep, the radix sequence of its FFT (radices[0..*nstages), at most 12),
  * and the schedule of its transform passes (*pipelined = 1: persistent
  * pipelined kernel, each CTA loads its next tile asynchronously while it
- * transforms the current one; 2: warp-FFT pass; 0: one tile per CTA). */
+ * transforms the current one; 2: warp-FFT pass; 3: double-float warp-FFT
+ * pass; 4: paired FP32 warp-FFT pass; 0: one tile per CTA). */
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
                    int* nstages, int* pipelined);
 

@@ -317,14 +317,18 @@ class IFFDPlan:
         return self
 
     def set_geometry(self, axis: int, pencils_transform: int = 0, pencils_stiffness: int = 0, pipelined=None,
-                     warp: bool = False, double_float: bool = False):
+                     warp: bool = False, double_float: bool = False, paired: bool = False):
         """Set one direction's launch geometry by hand (iffd_set_geometry).
         `warp`: run the warp-FFT transform pass (its tile is fixed; the FP32
         default where eligible, opt-in for FP64 plans up to FFT length 256).
+        `paired`: the FP32 warp-FFT pass with two sequences per lane group
+        (FFT length up to 256; the FP32 default there); `warp` alone selects
+        the unpaired pass.
         `double_float`: FP64 plans, every transform pass in double-float
         arithmetic on the FP32 pipe (the default where every direction has a
         warp-FFT pass; any other FP64 transform geometry set here turns it off)."""
-        pl = 3 if double_float else (2 if warp else (-1 if pipelined is None else int(bool(pipelined))))
+        pl = 3 if double_float else (4 if paired else (2 if warp else (-1 if pipelined is None
+                                                                        else int(bool(pipelined)))))
         check(self._lib.iffd_set_geometry(self._h, axis, int(pencils_transform), int(pencils_stiffness), pl),
               "iffd_set_geometry")
         return self
@@ -336,7 +340,9 @@ class IFFDPlan:
         check(self._lib.iffd_get_tiles(self._h, axis, ctypes.byref(pt), ctypes.byref(ps), rad, ctypes.byref(ns),
                                        ctypes.byref(pl)), "iffd_get_tiles")
         return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value]),
-                "pipelined": pl.value == 1, "warp": pl.value in (2, 3), "double_float": pl.value == 3}
+
+                "pipelined": pl.value == 1, "warp": pl.value in (2, 3, 4), "double_float": pl.value == 3,
+                "paired": pl.value == 4}
 
     def profile_enable(self, on: bool = True):
         check(self._lib.iffd_profile_enable(self._h, int(on)), "iffd_profile_enable")

@@ -208,6 +208,7 @@ struct PassLaunchB {
   int mode = PM_FWD, ndot = 0;
   int wN = 0;     // > 0: every system runs the FP32 warp-FFT pass of this length
   int wkind = 0;  // and this transform kind (AxisTab::kind)
+  int pair = 0;   // paired FP32 warp-FFT pass
   size_t off_desc = 0, off_prefix = 0;
   std::vector<int> sid;  // slot of the system of every descriptor
   void add(const PassDesc<Tc, Tin, Tout>& d, int tiles, size_t sm, int slot) {
@@ -257,8 +258,8 @@ struct PrecondSeq {
 };
 
 template <typename L>
-L& pass_slot(std::map<int, L>& m, int wN, int wkind, int mode, int ndot) {
-  const int key = wN ? 2 * wN + (wkind == 1 ? 1 : 0) : 0;
+L& pass_slot(std::map<int, L>& m, int wN, int wkind, int pair, int mode, int ndot) {
+  const int key = wN ? 4 * wN + 2 * (pair ? 1 : 0) + (wkind == 1 ? 1 : 0) : 0;
   auto it = m.find(key);
   if (it == m.end()) {
     L l;
@@ -266,6 +267,7 @@ L& pass_slot(std::map<int, L>& m, int wN, int wkind, int mode, int ndot) {
     l.ndot = ndot;
     l.wN = wN;
     l.wkind = wkind;
+    l.pair = pair;
     it = m.emplace(key, std::move(l)).first;
   }
   return it->second;
@@ -285,12 +287,14 @@ PassDesc<Tc, Tc, Tc> pdesc_same(const Plan& P, int axis, const AxisTab<Tc>* tabs
   d.done = done;
   d.wN = 0;
   d.wt = nullptr;
+  d.pair = 0;
   if constexpr (std::is_same<Tc, float>::value) {
     const F32Geom g = f32_geom(P, axis);
     d.PP = g.PP;
     d.ldt = g.ldt;
     d.wN = g.wN;
     d.wt = g.wt;
+    d.pair = g.pair;
   }
   return d;
 }
@@ -338,11 +342,11 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       PassDesc<float, double, float> D{};
       auto T = pdesc_same<float>(P, 0, P.axf, P.PPf, P.ldtf, done);
       D.dims = T.dims; D.axis = 0; D.PP = T.PP; D.ldt = T.ldt; D.ax = T.ax; D.lamA = T.lamA; D.lamB = T.lamB;
-      D.wN = T.wN; D.wt = T.wt;
+      D.wN = T.wN; D.wt = T.wt; D.pair = T.pair;
       D.done = done;
       D.in = vr(*s);
       D.out = vtf(*s);
-      pass_slot(seq->f_first, D.wN, D.ax.kind, PM_FWD, 0)
+      pass_slot(seq->f_first, D.wN, D.ax.kind, D.pair, PM_FWD, 0)
           .add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem, s->slot);
     }
     const int axes[3] = {1, d - 1, 1};
@@ -352,21 +356,21 @@ void build_precond(const std::vector<const Sys*>& sys, int ndot, bool use_q, Pre
       auto D = pdesc_same<float>(P, a, P.axf, P.PPf, P.ldtf, done);
       D.in = vtf(*s);
       D.out = vtf(*s);
-      pass_slot(seq->f_mid[k], D.wN, D.ax.kind, mid_modes[k], 0)
+      pass_slot(seq->f_mid[k], D.wN, D.ax.kind, D.pair, mid_modes[k], 0)
           .add(D, precond_tiles(P.dims, a, D.PP), f32_geom(P, a).smem, s->slot);
     }
     {
       PassDesc<float, float, double> D{};
       auto T = pdesc_same<float>(P, 0, P.axf, P.PPf, P.ldtf, done);
       D.dims = T.dims; D.axis = 0; D.PP = T.PP; D.ldt = T.ldt; D.ax = T.ax; D.lamA = T.lamA; D.lamB = T.lamB;
-      D.wN = T.wN; D.wt = T.wt;
+      D.wN = T.wN; D.wt = T.wt; D.pair = T.pair;
       D.done = done;
       D.in = vtf(*s);
       D.out = vz(*s);
       D.dot0 = vr(*s);
       D.dot1 = use_q ? vq(*s) : nullptr;
       D.partial = vpart(*s);
-      pass_slot(seq->f_last, D.wN, D.ax.kind, PM_BWD, ndot)
+      pass_slot(seq->f_last, D.wN, D.ax.kind, D.pair, PM_BWD, ndot)
           .add(D, precond_tiles(P.dims, 0, D.PP), f32_geom(P, 0).smem, s->slot);
     }
   }
@@ -396,7 +400,8 @@ int run_pass(Engine* E, char* base, PassLaunchB<Tc, Tin, Tout>& l, cudaStream_t 
     if (l.wN) {
       IFFD_CUDA((launch_wpass_batched<Tin, Tout>(at<PassDesc<Tc, Tin, Tout>>(base, l.off_desc),
                                                  at<long long>(base, l.off_prefix), (int)l.desc.size(),
-                                                 l.prefix.back(), l.smem, l.wN, l.wkind, l.mode, l.ndot, st)));
+                                                 l.prefix.back(), l.smem, l.wN, l.wkind, l.pair, l.mode,
+                                                 l.ndot, st)));
       if (l.prefix.back() > 0) ++E->launches;
       return IFFD_OK;
     }
@@ -453,8 +458,9 @@ int run_init(Engine* E, const std::vector<const Sys*>& sys) {
     vl.desc.push_back(v);
     vl.prefix.push_back(vl.prefix.back() + vec_grid(P.dims.N));
     fff.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
-    const int PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_geom(P, 0).PP : P.PPd[0];
-    frz0.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0)});
+    frz0.desc.push_back({vst(*s), vpart(*s),
+                         (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_last_parts(P)
+                                                                        : precond_tiles(P.dims, 0, P.PPd[0])});
   }
   PrecondSeq pc;
   build_precond(sys, 1, false, &pc);
@@ -562,8 +568,9 @@ void build_lane(const Engine* E, const std::vector<const Sys*>& sys, IterSeq* ou
     it.upd.prefix.push_back(it.upd.prefix.back() + vec_grid(P.dims.N));
     it.frr.desc.push_back({vst(*s), vpart(*s), vec_grid(P.dims.N)});
     it.frr.sid.push_back(s->slot);
-    const int PP0 = (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_geom(P, 0).PP : P.PPd[0];
-    it.frz.desc.push_back({vst(*s), vpart(*s), precond_tiles(P.dims, 0, PP0)});
+    it.frz.desc.push_back({vst(*s), vpart(*s),
+                           (P.opt.precision == IFFD_PREC_FP32_TRANSFORM) ? f32_last_parts(P)
+                                                                          : precond_tiles(P.dims, 0, P.PPd[0])});
     it.frz.sid.push_back(s->slot);
   }
   // A system's three sweeps must run in stage order. Groups are created in the

@@ -25,6 +25,7 @@ struct PassLaunch {
   int pipe;            // 1: persistent two-stage pipelined kernel (same input and arithmetic type only)
   int wN;              // > 0 runs the warp-FFT pass of length wN (PP, ldt as wpass_pencils)
   const vec2_t<Tc>* wt;  // its twiddles exp(-2 pi i e / wN), e < wN
+  int pair;            // FP32 warp pass with two sequences per lane group (wN <= 256)
 };
 
 // Per-system descriptor of one batched transform pass.
@@ -43,6 +44,7 @@ struct PassDesc {
   const int* done;
   int wN;            // as PassLaunch
   const vec2_t<Tc>* wt;
+  int pair;          // as PassLaunch
 };
 
 template <typename Tc, typename Tin, typename Tout>
@@ -53,8 +55,8 @@ cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long l
 // transform kind `kind` (AxisTab::kind: 1 DST-II/III, 0 DST-I).
 template <typename Tin, typename Tout>
 cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                 long long total_tiles, size_t smem, int N, int kind, int mode, int ndot,
-                                 cudaStream_t st);
+                                 long long total_tiles, size_t smem, int N, int kind, int pair, int mode,
+                                 int ndot, cudaStream_t st);
 
 // Per FFT length N (one translation unit each): the warp-FFT pass of one
 // direction, and its batched form (every system of the launch has wN == N and
@@ -63,7 +65,7 @@ template <int N, typename Tc, typename Tin, typename Tout>
 cudaError_t launch_wpass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
 template <int N, typename Tin, typename Tout>
 cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                   long long total_tiles, size_t smem, int kind, int mode, int ndot,
+                                   long long total_tiles, size_t smem, int kind, int pair, int mode, int ndot,
                                    cudaStream_t st);
 
 size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt);       // F: FFT length (AxisTab::F)
@@ -85,8 +87,12 @@ int wpass_len(const AxisTab<df>& ax);
 // out (BWD, 0..2 dot products).
 template <typename Tin, typename Tout>
 cudaError_t launch_pass_df(const PassLaunch<df>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);
-int wpass_pencils(int N);
-size_t wpass_smem_bytes(int N, int ldt, size_t elt = sizeof(float));
+// Pencils per CTA and shared memory of the warp-FFT pass of length N (pair:
+// the paired FP32 pass, N <= 256; ldt: tile row length in pencil values).
+int wpass_pencils(int N, bool pair = false);
+// SMs of the current device (cached at the first call).
+int device_sm_count();
+size_t wpass_smem_bytes(int N, int ldt, size_t elt = sizeof(float), bool pair = false);
 
 template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);

@@ -141,6 +141,9 @@ struct Plan {
   // wpass_len(axf[a]) > 0; on by default, off once a tile size is set by
   // hand or the tuner finds the block kernel faster), and its twiddle table
   int warp_f[3] = {0, 0, 0};
+  // 1 where that warp-FFT pass runs paired (two sequences per lane group, FFT
+  // length <= 256; the default for the last direction, whose pass is fused)
+  int pair_f[3] = {0, 0, 0};
   const float2* wtab[3] = {nullptr, nullptr, nullptr};
   // FP64 transforms: the same for the FP64 warp-FFT pass (wpass_len(axd[a]) > 0;
   // off by default, chosen by hand or by the tuner) and its FP64 twiddles
@@ -190,7 +193,10 @@ struct F32Geom {
   int PP, ldt, wN;
   const float2* wt;
   size_t smem;
+  int pair;  // the paired warp-FFT pass
 };
+// Partial sums of the last FP32 backward pass (two per tile when paired).
+int f32_last_parts(const Plan& P);
 F32Geom f32_geom(const Plan& P, int a);
 // General-coefficient stiffness (general.cu): device tables (at plan
 // creation), scratch bytes of one application, the application Au = A_C u

@@ -168,7 +168,7 @@ size_t precond_smem_bytes(int PP, int ldt, int F, size_t elt) {
 
 int precond_tiles(const Dims& dims, int axis, int PP) { return (int)host_num_tiles(dims, axis, PP); }
 
-static int sm_count() {
+int device_sm_count() {
   static int n = 0;
   if (n == 0) {
     int dev = 0;
@@ -193,7 +193,7 @@ static cudaError_t launch_pipe_t(const PassLaunch<Tc>& P, const Tc* in, Tc* out,
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int tiles = precond_tiles(P.dims, P.axis, P.PP);
-  const int grid = std::min(tiles, per_sm * sm_count());
+  const int grid = std::min(tiles, per_sm * device_sm_count());
   kern<<<grid, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.PP, P.ldt, P.ax, P.lamA, P.lamB, P.dot0, P.dot1,
                                    P.partial, tiles, P.done);
   return cudaGetLastError();
@@ -227,24 +227,28 @@ template cudaError_t launch_pass_df<double, df>(const PassLaunch<df>&, int, int,
 template cudaError_t launch_pass_df<df, df>(const PassLaunch<df>&, int, int, const df*, df*, cudaStream_t);
 template cudaError_t launch_pass_df<df, double>(const PassLaunch<df>&, int, int, const df*, double*, cudaStream_t);
 
-int wpass_pencils(int N) {
+int wpass_pencils(int N, bool pair) {
   switch (N) {
-    case 64: return warp_pencils<64>();
-    case 128: return warp_pencils<128>();
-    case 256: return warp_pencils<256>();
+    case 64: return pair ? warp_pencils<64, true>() : warp_pencils<64>();
+    case 128: return pair ? warp_pencils<128, true>() : warp_pencils<128>();
+    case 256: return pair ? warp_pencils<256, true>() : warp_pencils<256>();
     default: return warp_pencils<512>();
   }
 }
 
-size_t wpass_smem_bytes(int N, int ldt, size_t elt) {
-  const int PP = wpass_pencils(N);
+// tile (PP pencil rows of ldt values), PP / 2 sequence buffers of wpad(N)
+// complex values and PP rows of kMaxNout remainder coefficients -- for the
+// paired pass the same bytes per pencil (rows and buffers hold two pencils'
+// or two sequences' values)
+size_t wpass_smem_bytes(int N, int ldt, size_t elt, bool pair) {
+  const int PP = wpass_pencils(N, pair);
   return (size_t)PP * ldt * elt + (size_t)(PP / 2) * wpad(N) * 2 * elt + (size_t)PP * kMaxNout * elt;
 }
 
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
   if (P.wN != 0) {
-    if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
+    if (P.PP != wpass_pencils(P.wN, P.pair != 0) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
     switch (P.wN) {
       case 64: return launch_wpass<64, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
       case 128: return launch_wpass<128, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
@@ -347,22 +351,30 @@ cudaError_t launch_pass_batched(const PassDesc<Tc, Tin, Tout>* sys, const long l
 
 template <typename Tin, typename Tout>
 cudaError_t launch_wpass_batched(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                 long long total_tiles, size_t smem, int N, int kind, int mode, int ndot,
+                                 long long total_tiles, size_t smem, int N, int kind, int pair, int mode, int ndot,
                                  cudaStream_t st) {
   switch (N) {
-    case 64: return launch_wpass_batched_n<64, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
-    case 128: return launch_wpass_batched_n<128, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
-    case 256: return launch_wpass_batched_n<256, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
-    case 512: return launch_wpass_batched_n<512, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, mode, ndot, st);
+    case 64:
+      return launch_wpass_batched_n<64, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, pair, mode, ndot,
+                                                   st);
+    case 128:
+      return launch_wpass_batched_n<128, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, pair, mode, ndot,
+                                                    st);
+    case 256:
+      return launch_wpass_batched_n<256, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, pair, mode, ndot,
+                                                    st);
+    case 512:
+      return launch_wpass_batched_n<512, Tin, Tout>(sys, tile_prefix, nsys, total_tiles, smem, kind, pair, mode, ndot,
+                                                    st);
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_wpass_batched<double, float>(const PassDesc<float, double, float>*, const long long*, int,
-                                                         long long, size_t, int, int, int, int, cudaStream_t);
+                                                         long long, size_t, int, int, int, int, int, cudaStream_t);
 template cudaError_t launch_wpass_batched<float, float>(const PassDesc<float, float, float>*, const long long*, int,
-                                                        long long, size_t, int, int, int, int, cudaStream_t);
+                                                        long long, size_t, int, int, int, int, int, cudaStream_t);
 template cudaError_t launch_wpass_batched<float, double>(const PassDesc<float, float, double>*, const long long*, int,
-                                                         long long, size_t, int, int, int, int, cudaStream_t);
+                                                         long long, size_t, int, int, int, int, int, cudaStream_t);
 
 #define IFFD_INST_BATCHED(Tc, Tin, Tout)                                                                      \
   template cudaError_t launch_pass_batched<Tc, Tin, Tout>(const PassDesc<Tc, Tin, Tout>*, const long long*, int, \

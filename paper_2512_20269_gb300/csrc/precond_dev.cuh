@@ -53,9 +53,10 @@ __device__ __forceinline__ void dft8(Cplx<T>* v) {
   v[7] = {fma(-r, s3x, e[3].x), fma(r, s3y, e[3].y)};
 }
 
-// y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1].
-template <typename T>
-__device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& ax) {
+// y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1] (row values of
+// type T, tables of type TT: the same type, or FP32 tables for a pair).
+template <typename T, typename TT>
+__device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<TT>& ax) {
   if (i < ax.nL) {
     T s = T(0);
     for (int r = 0; r < ax.rowsL; ++r) s = fma(ldg(ax.VL + r * ax.nL + i), row[r], s);
@@ -74,7 +75,7 @@ __device__ __forceinline__ T reg_gather(const T* row, int i, const AxisTab<T>& a
     if (i < c0) break;
     if (i < c1) {
       const int r0 = ldg(B + 2), r1 = ldg(B + 3), w = c1 - c0;
-      const T* V = ax.VB + ldg(B + 5) + (i - c0);
+      const TT* V = ax.VB + ldg(B + 5) + (i - c0);
       T s = T(0);
       for (int r = r0; r < r1; ++r) s = fma(ldg(V + (r - r0) * w), row[r], s);
       return s;

@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "device_common.cuh"
+#include "fpair.cuh"
 #include "kernels.h"
 #include "precond_dev.cuh"
 #include "precond_warp_geom.h"
@@ -70,7 +71,7 @@ __device__ __forceinline__ void wdft(Cplx<T>* v) {
 // exp(-2 pi i q k / (Ns r)), k = j mod Ns (table wt[e] = exp(-2 pi i e / N)),
 // and writes out[(j - k) r + k + t Ns]. Lane ls runs butterflies ls + LS u.
 template <typename T, int N, int r, int Ns>
-__device__ __forceinline__ void wstage(vec2_t<T>* buf, int ls, const vec2_t<T>* __restrict__ wt) {
+__device__ __forceinline__ void wstage(vec2_t<T>* buf, int ls, const vec2_t<tab_t<T>>* __restrict__ wt) {
   constexpr int R = WarpFft<N>::R, LS = WarpFft<N>::LS, nb = N / r, BPL = R / r;
   static_assert(N % r == 0 && R % r == 0 && nb == LS * BPL, "stage does not tile the warp");
   // with nb and Ns multiples of 8 (Ns = 1 only with r = 8), the padded index
@@ -93,8 +94,8 @@ __device__ __forceinline__ void wstage(vec2_t<T>* buf, int ls, const vec2_t<T>* 
     if constexpr (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < r; ++q) {
-        const vec2_t<T> w = ldg(wt + q * k * (N / (Ns * r)));
-        v[u][q] = cmul(v[u][q], Cplx<T>{w.x, w.y});
+        const vec2_t<tab_t<T>> w = ldg(wt + q * k * (N / (Ns * r)));
+        v[u][q] = cmul(v[u][q], Cplx<tab_t<T>>{w.x, w.y});
       }
     }
     wdft<r>(v[u]);
@@ -107,7 +108,7 @@ __device__ __forceinline__ void wstage(vec2_t<T>* buf, int ls, const vec2_t<T>* 
 
 // The stages after the first (span Ns = 8).
 template <typename T, int N>
-__device__ __forceinline__ void wfft_rest(vec2_t<T>* buf, int ls, const vec2_t<T>* __restrict__ wt) {
+__device__ __forceinline__ void wfft_rest(vec2_t<T>* buf, int ls, const vec2_t<tab_t<T>>* __restrict__ wt) {
   wstage<T, N, 8, 8>(buf, ls, wt);
   if constexpr (N == 128) wstage<T, N, 2, 64>(buf, ls, wt);
   if constexpr (N == 256) wstage<T, N, 4, 64>(buf, ls, wt);
@@ -148,8 +149,8 @@ __device__ __forceinline__ T group_sum(T v) {
 
 // V_reg row rule of the scatter (x_i = sum_j V_reg[i][j] w_j): edge blocks,
 // interior blocks, identity runs (see AxisTab).
-template <typename T, typename WReg>
-__device__ __forceinline__ T wscatter_row(int i, const AxisTab<T>& ax, WReg wreg) {
+template <typename T, typename TT, typename WReg>
+__device__ __forceinline__ T wscatter_row(int i, const AxisTab<TT>& ax, WReg wreg) {
   const int m = ax.m, N = ax.n_reg;
   if (i < ax.rowsL) {
     T x = T(0);
@@ -169,7 +170,7 @@ __device__ __forceinline__ T wscatter_row(int i, const AxisTab<T>& ax, WReg wreg
     if (i < r0) break;
     if (i < r1) {
       const int c0 = ldg(B), c1 = ldg(B + 1);
-      const T* V = ax.VB + ldg(B + 5) + (i - r0) * (c1 - c0);
+      const TT* V = ax.VB + ldg(B + 5) + (i - r0) * (c1 - c0);
       T x = T(0);
       for (int c = c0; c < c1; ++c) x = fma(ldg(V + (c - c0)), wreg(c), x);
       return x;
@@ -257,13 +258,31 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, T* tile, 
   }
 }
 
+// Pencils of tile row `row`: the row itself, or for a pair (f2 rows) the two
+// pencils 4 (row / 2) + row % 2 and that + 2, so that the two sequences of a
+// lane group combine the pencils (4 s, 4 s + 1) and (4 s + 2, 4 s + 3) as the
+// unpaired pass combines (2 s, 2 s + 1).
+template <typename T>
+__device__ __forceinline__ int row_pencil(int row) {
+  if constexpr (IsPair<T>::value) return 4 * (row >> 1) + (row & 1);
+  else return row;
+}
+// A per-pencil table entry (eigenvalue of another direction) for tile row `row`.
+template <typename T>
+__device__ __forceinline__ T row_lam(const tab_t<T>* __restrict__ lam, const int* idx, int row) {
+  const int p = row_pencil<T>(row);
+  if constexpr (IsPair<T>::value) return f2{ldg(lam + idx[p]), ldg(lam + idx[p + 2])};
+  else return ldg(lam + idx[p]);
+}
+
 // KIND 1: DST-II / DST-III (even p), FFT length N = n_reg in Makhoul's order;
 // KIND 0: DST-I (odd p), FFT length N = 2 (n_reg + 1) of the odd extension.
 template <typename T, int N, int KIND, int MODE>
 __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, const Dims& dims, int ldt,
-                                           const AxisTab<T>& ax, const vec2_t<T>* __restrict__ wt,
-                                           const T* __restrict__ lamA, const T* __restrict__ lamB,
+                                           const AxisTab<tab_t<T>>& ax, const vec2_t<tab_t<T>>* __restrict__ wt,
+                                           const tab_t<T>* __restrict__ lamA, const tab_t<T>* __restrict__ lamB,
                                            const int* pia, const int* pib) {
+  using TT = tab_t<T>;
   constexpr int LS = WarpFft<N>::LS, PP = warp_pencils<N>(), G = 32 / LS;
   const int m = ax.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -286,11 +305,11 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       auto rows = [&](int i0, int i1) {
         for (int i = i0 + ls; i < i1; i += LS) {
           const T xa = ra[i], xb = rb[i];
-          const T* w = ax.W + i * nw + k0;
+          const TT* w = ax.W + i * nw + k0;
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             if (k0 + k < nw) {
-              const T wk = ldg(w + k);
+              const TT wk = ldg(w + k);
               sa[k] = fma(wk, xa, sa[k]);
               sb[k] = fma(wk, xb, sb[k]);
             }
@@ -361,7 +380,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
         const Cplx<T> zm = wld<T>(buf, wpad(k == 0 ? 0 : N - k));
         const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
         const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
-        const Post4<T> t = ldpost(ax.post, k);
+        const Post4<TT> t = ldpost(ax.post, k);
         ra[N - 1 - k] = fma(t.x, Ar, t.y * Ai);
         rb[N - 1 - k] = fma(t.x, Br, t.y * Bi);
         if (k > 0 && 2 * k != N) {
@@ -393,7 +412,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       // DST-I output j is -Im Z[j+1] (pencil a) and Re Z[j+1] (pencil b), times 1/(2 D~_j)
       for (int j = ls; j < NR; j += LS) {
         const Cplx<T> z = wld<T>(buf, wpad(j + 1));
-        const T sc = ldg(ax.post + j);
+        const TT sc = ldg(ax.post + j);
         ra[j] = -sc * z.y;
         rb[j] = sc * z.x;
       }
@@ -408,12 +427,12 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
 
   if constexpr (MODE == PM_FUSED) {
     // divide by the summed eigenvalues of all directions
-    const int pa = 2 * pr, pb = pa + 1;
-    const T la = ldg(lamA + pia[pa]), lb = ldg(lamA + pia[pb]);
-    const T ma = (dims.d == 3) ? ldg(lamB + pib[pa]) : T(0);
-    const T mb = (dims.d == 3) ? ldg(lamB + pib[pb]) : T(0);
+    const int pa = 2 * pr, pb = pa + 1;  // rows of the tile
+    const T la = row_lam<T>(lamA, pia, pa), lb = row_lam<T>(lamA, pia, pb);
+    const T ma = (dims.d == 3) ? row_lam<T>(lamB, pib, pa) : T(0);
+    const T mb = (dims.d == 3) ? row_lam<T>(lamB, pib, pb) : T(0);
     for (int i = ls; i < m; i += LS) {
-      const T li = ldg(ax.lam + i);
+      const TT li = ldg(ax.lam + i);
       T da = li + la, db = li + lb;
       if (dims.d == 3) {
         da += ma;
@@ -433,9 +452,9 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
     if constexpr (KIND == 1) {
       // inverse of the separation: G[k], G[N-k] from rows N-1-k and k-1
       for (int k = ls; k <= N / 2; k += LS) {
-        const Post4<T> t = ldpost(ax.post, k);
+        const Post4<TT> t = ldpost(ax.post, k);
         if (k == 0 || 2 * k == N) {
-          const T s = t.x + t.x;
+          const TT s = t.x + t.x;
           buf[wpad(k)] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
         } else {
           const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
@@ -452,7 +471,7 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
         T va = T(0), vb = T(0);
         if (l != 0 && l != N / 2) {
           const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
-          const T sc = (l < N / 2) ? ldg(ax.post + jj) : -ldg(ax.post + jj);
+          const TT sc = (l < N / 2) ? ldg(ax.post + jj) : -ldg(ax.post + jj);
           va = sc * ra[jj];
           vb = sc * rb[jj];
         }
@@ -486,12 +505,12 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
         xa = wa(i - ax.o);
         xb = wb(i - ax.o);
       } else {
-        xa = wscatter_row(i, ax, wa);
-        xb = wscatter_row(i, ax, wb);
+        xa = wscatter_row<T>(i, ax, wa);
+        xb = wscatter_row<T>(i, ax, wb);
       }
       if (i < ax.wlo || i >= ax.whi) {
         for (int k = 0; k < nw; ++k) {
-          const T w = ldg(ax.W + i * nw + k);
+          const TT w = ldg(ax.W + i * nw + k);
           xa = fma(w, ova[k], xa);
           xb = fma(w, ovb[k], xb);
         }
@@ -560,6 +579,181 @@ __device__ __forceinline__ void wstore_tile(const T* tile, Tout* __restrict__ ou
   }
 }
 
+// Tile load and store of the paired pass: tile row r (f2) holds pencils
+// row_pencil(r) and row_pencil(r) + 2. Along direction 0 a warp reads the two
+// pencil rows of a tile row; along the others a thread moves four adjacent
+// pencils of one grid line (one 16- or two 8-byte accesses where they are
+// contiguous and aligned in memory), the CTA covering 256 / (PP / 4) lines
+// per sweep.
+template <int N, typename Tin>
+__device__ __forceinline__ void wload_tile_pair(const Tin* __restrict__ in, f2* tile, int axis, int ldt, int m,
+                                                const long long* pbase, const TileInfo& g) {
+  constexpr int PP = warp_pencils<N, true>(), PR = PP / 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (axis == 0) {
+    for (int r = warp; r < PR; r += kThreads / 32) {
+      const int pa = row_pencil<f2>(r), pb = pa + 2;
+      const bool va = pa < g.nvalid, vb = pb < g.nvalid;
+      const Tin* sa = in + pbase[pa];
+      const Tin* sb = in + pbase[pb];
+      f2* row = tile + r * ldt;
+#pragma unroll 4
+      for (int i = lane; i < m; i += 32)
+        row[i] = f2{va ? cvt<float>(sa[i]) : 0.f, vb ? cvt<float>(sb[i]) : 0.f};
+    }
+  } else {
+    constexpr int QU = PP / 4, RS = kThreads / QU;  // pencil quads, lines per sweep
+    const int qu = tid % QU;
+    const int p0 = 4 * qu;
+    const long long b0 = pbase[p0];
+    const bool full = p0 + 3 < g.nvalid && pbase[p0 + 3] == b0 + 3;  // four contiguous pencils
+    int mode = 0;  // 0: element loads, 1: two 8-byte loads, 2: one 16-byte load
+    if constexpr (std::is_same<Tin, float>::value) {
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(in + b0), sb = (uintptr_t)g.S * sizeof(float);
+      if (full && (a0 % 16) == 0 && (sb % 16) == 0) mode = 2;
+      else if (full && (a0 % 8) == 0 && (sb % 8) == 0) mode = 1;
+    }
+    bool v[4];
+    const Tin* src[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = p0 + k < g.nvalid;
+      src[k] = in + pbase[p0 + k];
+    }
+    f2* ra = tile + (2 * qu) * ldt;  // pencils p0, p0 + 2
+    f2* rb = ra + ldt;               // pencils p0 + 1, p0 + 3
+    for (int i = tid / QU; i < m; i += RS) {
+      const long long o = (long long)i * g.S;
+      float x0, x1, x2, x3;
+      if constexpr (std::is_same<Tin, float>::value) {
+        if (mode == 2) {
+          const float4 t = *reinterpret_cast<const float4*>(src[0] + o);
+          x0 = t.x; x1 = t.y; x2 = t.z; x3 = t.w;
+        } else if (mode == 1) {
+          const float2 t0 = *reinterpret_cast<const float2*>(src[0] + o);
+          const float2 t1 = *reinterpret_cast<const float2*>(src[0] + o + 2);
+          x0 = t0.x; x1 = t0.y; x2 = t1.x; x3 = t1.y;
+        } else {
+          x0 = v[0] ? src[0][o] : 0.f;
+          x1 = v[1] ? src[1][o] : 0.f;
+          x2 = v[2] ? src[2][o] : 0.f;
+          x3 = v[3] ? src[3][o] : 0.f;
+        }
+      } else {
+        x0 = v[0] ? cvt<float>(src[0][o]) : 0.f;
+        x1 = v[1] ? cvt<float>(src[1][o]) : 0.f;
+        x2 = v[2] ? cvt<float>(src[2][o]) : 0.f;
+        x3 = v[3] ? cvt<float>(src[3][o]) : 0.f;
+      }
+      ra[i] = f2{x0, x2};
+      rb[i] = f2{x1, x3};
+    }
+  }
+}
+
+// Paired store. The partial dot products of a PCG step are formed per half
+// tile (pencils 0..PP/2-1 and PP/2..PP-1) with the thread-to-element map and
+// summation order of the unpaired pass on its tile of PP/2 pencils, and stored
+// as partials 2 ptile and 2 ptile + 1: the same partials as the unpaired pass.
+template <int N, typename Tout, int NDOT>
+__device__ __forceinline__ void wstore_tile_pair(const f2* tile, Tout* __restrict__ out, int axis, int ldt, int m,
+                                                 const long long* pbase, const TileInfo& g,
+                                                 const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                                 double* __restrict__ partial, int ptile, int pstride) {
+  constexpr int PP = warp_pencils<N, true>(), HP = PP / 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* tf = reinterpret_cast<const float*>(tile);
+  double d0[2] = {0.0, 0.0}, d1[2] = {0.0, 0.0};  // per half tile (indexed by constants only)
+  if (axis == 0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int nv = min(max(g.nvalid - h * HP, 0), HP);
+      for (int pc = warp; pc < nv; pc += kThreads / 32) {
+        const int P = h * HP + pc;                           // pencil 4 s + k
+        const int row = 2 * (P >> 2) + (P & 1), comp = (P >> 1) & 1;  // tile row, f2 component
+        const float* src = tf + 2 * (long long)row * ldt + comp;
+        Tout* dst = out + pbase[P];
+        const long long off0 = pbase[P];
+        for (int i = lane; i < m; i += 32) {
+          const Tout v = cvt<Tout>(src[2 * i]);
+          dst[i] = v;
+          if (NDOT >= 1) d0[h] = fma(ldg(dotv0 + off0 + i), cvt<double>(v), d0[h]);
+          if (NDOT >= 2) d1[h] = fma(ldg(dotv1 + off0 + i), cvt<double>(v), d1[h]);
+        }
+      }
+    }
+  } else {
+    constexpr int QU = PP / 4, RS = kThreads / QU;
+    const int qu = tid % QU;
+    const int p0 = 4 * qu;
+    const long long b0 = pbase[p0];
+    const bool full = p0 + 3 < g.nvalid && pbase[p0 + 3] == b0 + 3;
+    int mode = 0;
+    if constexpr (std::is_same<Tout, float>::value) {
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(out + b0), sb = (uintptr_t)g.S * sizeof(float);
+      if (full && (a0 % 16) == 0 && (sb % 16) == 0) mode = 2;
+      else if (full && (a0 % 8) == 0 && (sb % 8) == 0) mode = 1;
+    }
+    const f2* ra = tile + (2 * qu) * ldt;
+    const f2* rb = ra + ldt;
+    for (int i = tid / QU; i < m; i += RS) {
+      const long long o = (long long)i * g.S;
+      const f2 ya = ra[i], yb = rb[i];
+      const float x[4] = {ya.a, yb.a, ya.b, yb.b};
+      if constexpr (std::is_same<Tout, float>::value) {
+        if (mode == 2) {
+          *reinterpret_cast<float4*>(out + b0 + o) = float4{x[0], x[1], x[2], x[3]};
+          continue;
+        }
+        if (mode == 1) {
+          *reinterpret_cast<float2*>(out + b0 + o) = float2{x[0], x[1]};
+          *reinterpret_cast<float2*>(out + b0 + o + 2) = float2{x[2], x[3]};
+          continue;
+        }
+      }
+      const bool hi = p0 >= HP;  // the four pencils lie in one half (HP is a multiple of 4)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (p0 + k < g.nvalid) {
+          const long long off = pbase[p0 + k] + o;
+          const Tout v = cvt<Tout>(x[k]);
+          out[off] = v;
+          if (NDOT >= 1) {
+            const double t = ldg(dotv0 + off);
+            if (hi) d0[1] = fma(t, cvt<double>(v), d0[1]);
+            else d0[0] = fma(t, cvt<double>(v), d0[0]);
+          }
+          if (NDOT >= 2) {
+            const double t = ldg(dotv1 + off);
+            if (hi) d1[1] = fma(t, cvt<double>(v), d1[1]);
+            else d1[0] = fma(t, cvt<double>(v), d1[0]);
+          }
+        }
+    }
+  }
+  if (NDOT >= 1) {
+    __shared__ double red[2][2][kThreads / 32];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double s0 = warp_sum(d0[h]), s1 = warp_sum(d1[h]);
+      if (lane == 0) {
+        red[h][0][warp] = s0;
+        red[h][1][warp] = s1;
+      }
+    }
+    __syncthreads();
+    if (tid < 2) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        s0 += red[tid][0][w];
+        s1 += red[tid][1][w];
+      }
+      partial[2 * ptile + tid] = s0;
+      if (NDOT >= 2) partial[pstride + 2 * ptile + tid] = s1;
+    }
+  }
+}
+
 // FP64 FUSED passes divide by the summed eigenvalues between the forward and
 // the backward transform as one block-wide step: a multiply with the
 // precomputed reciprocal, read in the coalesced order of the tile load (the
@@ -610,24 +804,13 @@ __device__ __forceinline__ void wscale_tile_df(df* tile, int ldt, const AxisTab<
   }
 }
 
-// One CTA: tile `tile_id` of PP = warp_pencils<N>() pencils.
-template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
-__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
-                                           int axis, int ldt, const AxisTab<T>& ax,
-                                           const vec2_t<T>* __restrict__ wt, const T* __restrict__ lamA,
-                                           const T* __restrict__ lamB, const double* __restrict__ dotv0,
-                                           const double* __restrict__ dotv1, double* __restrict__ partial,
-                                           long long tile_id, int ptile, int pstride, unsigned char* smem) {
-  constexpr int PP = warp_pencils<N>();
-  T* tile = reinterpret_cast<T*>(smem);
-  vec2_t<T>* wbuf = reinterpret_cast<vec2_t<T>*>(tile + (size_t)PP * ldt);
-  T* outv = reinterpret_cast<T*>(wbuf + (size_t)(PP / 2) * wbuf_len<N>());  // PP * kMaxNout
-  __shared__ long long pbase[PP];
-  __shared__ int pia[PP], pib[PP];
-  const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
-  __syncthreads();
-  wload_tile<N, T, Tin>(in, tile, axis, ldt, ax, pbase, g);
-  __syncthreads();
+// The transform of one loaded tile, in place (FWD, BWD, or both with the
+// eigenvalue scaling between them), by the whole CTA.
+template <typename T, int N, int KIND, int MODE>
+__device__ __forceinline__ void wcompute(T* tile, vec2_t<T>* wbuf, T* outv, const Dims& dims, int axis, int ldt,
+                                         const AxisTab<tab_t<T>>& ax, const vec2_t<tab_t<T>>* __restrict__ wt,
+                                         const tab_t<T>* __restrict__ lamA, const tab_t<T>* __restrict__ lamB,
+                                         const long long* pbase, const int* pia, const int* pib, const TileInfo& g) {
   if constexpr (std::is_same<T, double>::value && MODE == PM_FUSED) {
     wtransform<T, N, KIND, PM_FWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
     __syncthreads();
@@ -643,25 +826,64 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
   } else {
     wtransform<T, N, KIND, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
   }
+}
+
+template <int N, typename T, typename Tout, int NDOT>
+__device__ __forceinline__ void wstore_any(const T* tile, Tout* __restrict__ out, int axis, int ldt,
+                                           const AxisTab<tab_t<T>>& ax, const long long* pbase, const TileInfo& g,
+                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                           double* __restrict__ partial, int ptile, int pstride) {
+  if constexpr (IsPair<T>::value)
+    wstore_tile_pair<N, Tout, NDOT>(tile, out, axis, ldt, ax.m, pbase, g, dotv0, dotv1, partial, ptile, pstride);
+  else
+    wstore_tile<N, T, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
+}
+
+// One CTA: tile `tile_id` of PP = warp_pencils<N, pair>() pencils (T = f2:
+// the paired pass, PP / 2 tile rows of two pencils each).
+template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+__device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __restrict__ out, const Dims& dims,
+                                           int axis, int ldt, const AxisTab<tab_t<T>>& ax,
+                                           const vec2_t<tab_t<T>>* __restrict__ wt,
+                                           const tab_t<T>* __restrict__ lamA, const tab_t<T>* __restrict__ lamB,
+                                           const double* __restrict__ dotv0, const double* __restrict__ dotv1,
+                                           double* __restrict__ partial, long long tile_id, int ptile, int pstride,
+                                           unsigned char* smem) {
+  constexpr bool PAIR = IsPair<T>::value;
+  constexpr int PP = warp_pencils<N, PAIR>(), PR = PAIR ? PP / 2 : PP;  // pencils, tile rows
+  T* tile = reinterpret_cast<T*>(smem);
+  vec2_t<T>* wbuf = reinterpret_cast<vec2_t<T>*>(tile + (size_t)PR * ldt);
+  T* outv = reinterpret_cast<T*>(wbuf + (size_t)(PR / 2) * wbuf_len<N>());  // PR * kMaxNout
+  __shared__ long long pbase[PP];
+  __shared__ int pia[PP], pib[PP];
+  const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
   __syncthreads();
-  wstore_tile<N, T, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
+  if constexpr (PAIR) wload_tile_pair<N, Tin>(in, tile, axis, ldt, ax.m, pbase, g);
+  else wload_tile<N, T, Tin>(in, tile, axis, ldt, ax, pbase, g);
+  __syncthreads();
+  wcompute<T, N, KIND, MODE>(tile, wbuf, outv, dims, axis, ldt, ax, wt, lamA, lamB, pbase, pia, pib, g);
+  __syncthreads();
+  wstore_any<N, T, Tout, NDOT>(tile, out, axis, ldt, ax, pbase, g, dotv0, dotv1, partial, ptile, pstride);
 }
 
 template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
-precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<T> ax, const vec2_t<T>* wt,
-              const T* __restrict__ lamA, const T* __restrict__ lamB, const double* __restrict__ dotv0,
-              const double* __restrict__ dotv1, double* __restrict__ partial, const int* __restrict__ done) {
+precond_wpass(const Tin* in, Tout* out, Dims dims, int axis, int ldt, AxisTab<tab_t<T>> ax,
+              const vec2_t<tab_t<T>>* wt, const tab_t<T>* __restrict__ lamA, const tab_t<T>* __restrict__ lamB,
+              const double* __restrict__ dotv0, const double* __restrict__ dotv1, double* __restrict__ partial,
+              const int* __restrict__ done) {
   if (done != nullptr && *((volatile const int*)done)) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  // the paired pass stores two partial sums per tile
+  const int np = IsPair<T>::value ? 2 * gridDim.x : gridDim.x;
   wpass_body<T, N, KIND, Tin, Tout, MODE, NDOT>(in, out, dims, axis, ldt, ax, wt, lamA, lamB, dotv0, dotv1, partial,
-                                                blockIdx.x, blockIdx.x, gridDim.x, smem);
+                                                blockIdx.x, blockIdx.x, np, smem);
 }
 
-// Batched warp-FFT pass (FP32): every system of the launch runs the warp-FFT
-// pass of length N (a separate kernel from the block one, so that neither
-// carries the other's register allocation).
-template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+// Batched warp-FFT pass (FP32, T = float or the pair f2): every system of the
+// launch runs the warp-FFT pass of length N (a separate kernel from the block
+// one, so that neither carries the other's register allocation).
+template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 __global__ void __launch_bounds__(kThreads)
 precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const long long* __restrict__ tile_prefix,
                       int nsys) {
@@ -683,28 +905,30 @@ precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const 
   if (sd.done != nullptr && *((volatile const int*)sd.done)) return;
   const long long tile = (long long)blockIdx.x - tile_prefix[s_sys];
   const int ntiles = (int)(tile_prefix[s_sys + 1] - tile_prefix[s_sys]);
-  wpass_body<float, N, KIND, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
-                                                    sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, ntiles,
-                                                    smem);
+  // the paired pass stores two partial sums per tile
+  const int np = IsPair<T>::value ? 2 * ntiles : ntiles;
+  wpass_body<T, N, KIND, Tin, Tout, MODE, NDOT>(sd.in, sd.out, sd.dims, sd.axis, sd.ldt, sd.ax, sd.wt, sd.lamA,
+                                                sd.lamB, sd.dot0, sd.dot1, sd.partial, tile, (int)tile, np, smem);
 }
 
 // ---------------------------------------------------------------- launchers
 template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
-cudaError_t launch_wpass_n(const PassLaunch<T>& P, const Tin* in, Tout* out, cudaStream_t st) {
+cudaError_t launch_wpass_n(const PassLaunch<tab_t<T>>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  constexpr bool PAIR = IsPair<T>::value;
+  const size_t sm = wpass_smem_bytes(N, P.ldt, sizeof(tab_t<T>), PAIR);
+  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N, PAIR>());
   auto kern = precond_wpass<T, N, KIND, Tin, Tout, MODE, NDOT>;
-  const size_t sm = wpass_smem_bytes(N, P.ldt, sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N>());
   kern<<<tiles, kThreads, sm, st>>>(in, out, P.dims, P.axis, P.ldt, P.ax, P.wt, P.lamA, P.lamB, P.dot0, P.dot1,
                                     P.partial, P.done);
   return cudaGetLastError();
 }
 
-template <int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
+template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_wbatched_t(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
                               long long total_tiles, size_t smem, cudaStream_t st) {
-  auto kern = precond_wpass_batched<N, KIND, Tin, Tout, MODE, NDOT>;
+  auto kern = precond_wpass_batched<T, N, KIND, Tin, Tout, MODE, NDOT>;
   static size_t smem_set = 0;  // attribute is raised only when needed (not inside a graph capture)
   if (smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -737,13 +961,25 @@ constexpr bool wpass_combo_ok(int mode, int ndot) {
   return ndot == 0;
 }
 
+// The kernel of one (mode, dot count): transform kind 1 or 0, paired (FP32,
+// N <= 256, P.pair set) or not.
+template <typename Tc, int N, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_wk(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
+  const bool k1 = P.ax.kind == 1;
+  if constexpr (std::is_same<Tc, float>::value && N <= 256) {
+    if (P.pair)
+      return k1 ? launch_wpass_n<f2, N, 1, Tin, Tout, MODE, NDOT>(P, in, out, st)
+                : launch_wpass_n<f2, N, 0, Tin, Tout, MODE, NDOT>(P, in, out, st);
+  }
+  if (P.pair) return cudaErrorInvalidValue;
+  return k1 ? launch_wpass_n<Tc, N, 1, Tin, Tout, MODE, NDOT>(P, in, out, st)
+            : launch_wpass_n<Tc, N, 0, Tin, Tout, MODE, NDOT>(P, in, out, st);
+}
+
 template <int N, typename Tc, typename Tin, typename Tout>
 cudaError_t launch_wpass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
   if (!wpass_combo_ok<Tc, Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
-  const bool k1 = P.ax.kind == 1;
-#define IFFD_WL(MODE, NDOT)                                                                            \
-  return k1 ? launch_wpass_n<Tc, N, 1, Tin, Tout, MODE, NDOT>(P, in, out, st)                          \
-            : launch_wpass_n<Tc, N, 0, Tin, Tout, MODE, NDOT>(P, in, out, st);
+#define IFFD_WL(MODE, NDOT) return launch_wk<Tc, N, Tin, Tout, MODE, NDOT>(P, in, out, st);
   if constexpr (std::is_same<Tc, double>::value) {
     if (mode == PM_FWD) { IFFD_WL(PM_FWD, 0) }
     if (mode == PM_FUSED) { IFFD_WL(PM_FUSED, 0) }
@@ -764,15 +1000,27 @@ cudaError_t launch_wpass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin*
 #undef IFFD_WL
 }
 
+template <int N, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_wbk(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
+                       long long total_tiles, size_t smem, int kind, int pair, cudaStream_t st) {
+  const bool k1 = kind == 1;
+  if constexpr (N <= 256) {
+    if (pair)
+      return k1 ? launch_wbatched_t<f2, N, 1, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st)
+                : launch_wbatched_t<f2, N, 0, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st);
+  }
+  if (pair) return cudaErrorInvalidValue;
+  return k1 ? launch_wbatched_t<float, N, 1, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st)
+            : launch_wbatched_t<float, N, 0, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st);
+}
+
 template <int N, typename Tin, typename Tout>
 cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const long long* tile_prefix, int nsys,
-                                   long long total_tiles, size_t smem, int kind, int mode, int ndot,
+                                   long long total_tiles, size_t smem, int kind, int pair, int mode, int ndot,
                                    cudaStream_t st) {
   if (!wpass_combo_ok<float, Tin, Tout>(mode, ndot)) return cudaErrorInvalidValue;
-  const bool k1 = kind == 1;
-#define IFFD_WB(MODE, NDOT)                                                                                   \
-  return k1 ? launch_wbatched_t<N, 1, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st)  \
-            : launch_wbatched_t<N, 0, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, st);
+#define IFFD_WB(MODE, NDOT) \
+  return launch_wbk<N, Tin, Tout, MODE, NDOT>(sys, tile_prefix, nsys, total_tiles, smem, kind, pair, st);
   if constexpr (std::is_same<Tin, double>::value) {
     IFFD_WB(PM_FWD, 0)
   } else if constexpr (std::is_same<Tout, double>::value) {
@@ -799,13 +1047,13 @@ cudaError_t launch_wpass_batched_n(const PassDesc<float, Tin, Tout>* sys, const 
                                                               double*, cudaStream_t);                            \
   template cudaError_t launch_wpass_batched_n<NN, double, float>(const PassDesc<float, double, float>*,            \
                                                                  const long long*, int, long long, size_t, int,   \
-                                                                 int, int, cudaStream_t);                         \
+                                                                 int, int, int, cudaStream_t);                         \
   template cudaError_t launch_wpass_batched_n<NN, float, float>(const PassDesc<float, float, float>*,              \
                                                                 const long long*, int, long long, size_t, int,    \
-                                                                int, int, cudaStream_t);                          \
+                                                                int, int, int, cudaStream_t);                          \
   template cudaError_t launch_wpass_batched_n<NN, float, double>(const PassDesc<float, float, double>*,            \
                                                                  const long long*, int, long long, size_t, int,   \
-                                                                 int, int, cudaStream_t);
+                                                                 int, int, int, cudaStream_t);
 #define IFFD_WARP_INSTANTIATE_F64(NN)                                                                             \
   template cudaError_t launch_wpass<NN, double, double, double>(const PassLaunch<double>&, int, int,               \
                                                                 const double*, double*, cudaStream_t);

@@ -27,9 +27,11 @@ struct WarpFft<512> {
   static constexpr int R = 16, LS = 32;
 };
 
-template <int N>
+// Pencils per CTA: two per sequence (real and imaginary part), one sequence
+// per LS lanes; the paired pass (FP32, two sequences per lane group) twice that.
+template <int N, bool PAIR = false>
 __host__ __device__ constexpr int warp_pencils() {
-  return 2 * (kThreads / 32) * (32 / WarpFft<N>::LS);
+  return (PAIR ? 4 : 2) * (kThreads / 32) * (32 / WarpFft<N>::LS);
 }
 
 // Sequence buffers skip one complex slot after every 8, so that the strided

@@ -114,12 +114,14 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
   std::vector<int> vars;
   for (size_t i = 0; i < P->fvar[a].size(); ++i)
     if (P->fvar[a][i].len == ax.F) vars.push_back((int)i);
+  // warp: 0 block kernel, 1 warp-FFT pass, 2 paired warp-FFT pass (FP32)
   auto apply = [&](int vi, int pp, int pipe, int warp) {
     vsel[a] = vi;
     set_fft(&ax, P->fvar[a][vi]);
     PPs[a] = pp;
     pipes[a] = pipe;
-    (f64 ? P->warp_d : P->warp_f)[a] = warp;
+    (f64 ? P->warp_d : P->warp_f)[a] = warp > 0 ? 1 : 0;
+    if (!f64) P->pair_f[a] = warp == 2 ? 1 : 0;
   };
   if (precond_tiles(P->dims, a, PPs[a]) < kMinTuneTiles) return IFFD_OK;
   {
@@ -150,13 +152,17 @@ int tune_transform(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
     }
   };
   if constexpr (!f64) {
-    if (wpass_len(ax) > 0) {  // the warp-FFT pass (its tile is fixed)
-      apply(vsel[a], PPs[a], 0, 1);
-      float ms = 0.f;
-      if (int rc = time_pass(&ms)) return rc;
-      best = ms;
-      best_warp = 1;
-      best_pipe = 0;
+    if (const int wN = wpass_len(ax)) {  // the warp-FFT pass (its tile is fixed), unpaired and paired
+      for (int w = 1; w <= (wN <= 256 ? 2 : 1); ++w) {
+        apply(vsel[a], PPs[a], 0, w);
+        float ms = 0.f;
+        if (int rc = time_pass(&ms)) return rc;
+        if (ms < best) {
+          best = ms;
+          best_warp = w;
+          best_pipe = 0;
+        }
+      }
     }
   }
   for (int vi : vars)
@@ -305,16 +311,20 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   } else if (f64 && (pencils_transform > 0 || (pipelined >= 0 && pipelined <= 2))) {
     P.dfq = 0;  // an FP64-pipe transform geometry set by hand
   }
-  if (pipelined == 2) {
+  if (pipelined == 2 || pipelined == 4) {
     if (f64 ? wpass_len(P.axd[axis]) == 0 : wpass_len(P.axf[axis]) == 0)
       return fail(IFFD_ERR_UNSUPPORTED, "the warp-FFT pass needs a D = {0,1} direction of FFT length 64, 128, 256 "
                                         "or 512 (FP64: up to 256)");
+    if (pipelined == 4 && (f64 || wpass_len(P.axf[axis]) > 256))
+      return fail(IFFD_ERR_UNSUPPORTED, "the paired warp-FFT pass needs FP32 transforms and an FFT length of 64, "
+                                        "128 or 256");
     if (pencils_transform > 0) return fail(IFFD_ERR_INVALID_ARG, "the warp-FFT pass has a fixed tile");
     (f64 ? P.warp_d : P.warp_f)[axis] = 1;
     (f64 ? P.pipe_d : P.pipe_f)[axis] = 0;
+    if (!f64) P.pair_f[axis] = pipelined == 4 ? 1 : 0;
     pipelined = -1;
   } else if (pipelined > 2) {
-    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1, 2 or 3 (or < 0)");
+    return fail(IFFD_ERR_INVALID_ARG, "pipelined must be 0, 1, 2, 3 or 4 (or < 0)");
   } else if (pencils_transform > 0 || pipelined >= 0) {
     (f64 ? P.warp_d : P.warp_f)[axis] = 0;  // a block-kernel geometry set by hand
   }
@@ -372,7 +382,10 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
     *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
   const int nst = f64 ? P.axd[axis].nst : P.axf[axis].nst;
   if (nstages) *nstages = nst;
-  if (pipelined) *pipelined = f64 ? (wd ? 2 : P.pipe_d[axis]) : (f32_geom(P, axis).wN ? 2 : P.pipe_f[axis]);
+  if (pipelined) {
+    const F32Geom g = f32_geom(P, axis);
+    *pipelined = f64 ? (wd ? 2 : P.pipe_d[axis]) : (g.wN ? (g.pair ? 4 : 2) : P.pipe_f[axis]);
+  }
   if (radices)
     for (int s = 0; s < nst; ++s) radices[s] = f64 ? P.axd[axis].radix[s] : P.axf[axis].radix[s];
   return IFFD_OK;

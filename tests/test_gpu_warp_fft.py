@@ -97,11 +97,18 @@ def test_warp_geometry_switches():
     from paper_2512_20269_gb300 import IFFDError, IFFDPlan
     plan = IFFDPlan(2, (64, 40), 4, precision="fp32")
     assert plan.tiles(0)["warp"] and not plan.tiles(1)["warp"]
-    assert plan.tiles(0)["pencils_transform"] == 64
+    assert not plan.tiles(0)["paired"] and plan.tiles(0)["pencils_transform"] == 64
+    assert IFFDPlan(2, (40, 64), 4, precision="fp32").tiles(1)["paired"]  # the last (fused) direction: paired
     plan.set_geometry(0, pencils_transform=4)
     assert not plan.tiles(0)["warp"] and plan.tiles(0)["pencils_transform"] == 4
     plan.set_geometry(0, warp=True)
-    assert plan.tiles(0)["warp"]
+    assert plan.tiles(0)["warp"] and not plan.tiles(0)["paired"] and plan.tiles(0)["pencils_transform"] == 64
+    plan.set_geometry(0, paired=True)
+    assert plan.tiles(0)["paired"] and plan.tiles(0)["pencils_transform"] == 128
+    with pytest.raises(IFFDError):
+        IFFDPlan(2, 512, 4, precision="fp32").set_geometry(0, paired=True)  # length 512: unpaired only
+    with pytest.raises(IFFDError):
+        IFFDPlan(2, 64, 4).set_geometry(0, paired=True)  # FP64 plan
     with pytest.raises(IFFDError):
         plan.set_geometry(1, warp=True)  # n_reg = 40
     with pytest.raises(IFFDError):
