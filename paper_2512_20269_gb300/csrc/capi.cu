@@ -15,6 +15,7 @@
 #include "host_setup.h"
 #include "kernels.h"
 #include "plan.h"
+#include "precond_warp_geom.h"
 
 namespace iffd {
 
@@ -672,7 +673,7 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
   } else {
     if (const int wN = f64_warp_len(*P, axis)) {
       L.PP = wpass_pencils(wN);
-      L.ldt = P->axd[axis].m | 1;
+      L.ldt = wpass_ldt(wN, P->axd[axis].m, walias<double>());
       L.wN = wN;
       L.wt = P->wtab_d[axis];
       L.pipe = 0;
@@ -695,7 +696,7 @@ static PassLaunch<df> make_pass_df(const Plan* P, int axis, const int* done) {
   L.axis = axis;
   L.wN = wpass_len(P->axq[axis]);
   L.PP = wpass_pencils(L.wN);
-  L.ldt = P->axq[axis].m | 1;
+  L.ldt = wpass_ldt(L.wN, P->axq[axis].m, walias<df>());
   L.ax = P->axq[axis];
   L.lamA = P->axq[0].lam;
   L.lamB = (P->d == 3) ? P->axq[1].lam : P->axq[0].lam;
@@ -722,8 +723,8 @@ F32Geom f32_geom(const Plan& P, int a) {
     g.wt = P.wtab[a];
     g.pair = (P.pair_f[a] && wN <= 256) ? 1 : 0;
     g.PP = wpass_pencils(wN, g.pair);
-    g.ldt = P.axf[a].m | 1;
-    g.smem = wpass_smem_bytes(wN, g.ldt, sizeof(float), g.pair);
+    g.ldt = wpass_ldt(wN, P.axf[a].m, walias<float>());
+    g.smem = wpass_smem_bytes(wN, g.ldt, sizeof(float), g.pair, walias<float>());
   } else {
     g.smem = precond_smem_bytes(g.PP, g.ldt, P.axf[a].F, sizeof(float));
   }

@@ -92,7 +92,11 @@ cudaError_t launch_pass_df(const PassLaunch<df>& P, int mode, int ndot, const Ti
 int wpass_pencils(int N, bool pair = false);
 // SMs of the current device (cached at the first call).
 int device_sm_count();
-size_t wpass_smem_bytes(int N, int ldt, size_t elt = sizeof(float), bool pair = false);
+size_t wpass_smem_bytes(int N, int ldt, size_t elt = sizeof(float), bool pair = false, bool alias = false);
+// Tile row length of the warp-FFT pass of length N for m values per pencil
+// (odd, for banks; with alias the rows of a pencil pair also hold its
+// sequence buffer, see walias).
+int wpass_ldt(int N, int m, bool alias);
 
 template <typename Tc, typename Tin, typename Tout>
 cudaError_t launch_pass(const PassLaunch<Tc>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st);

@@ -205,7 +205,7 @@ static int wpass_len_t(const AxisTab<T>& ax, int nmax) {
   if (ax.kind == 1) N = ax.n_reg;                 // DST-II/III: Makhoul, length n_reg
   else if (ax.kind == 0) N = 2 * (ax.n_reg + 1);  // DST-I: odd extension
   else return 0;
-  if (ax.blu || ax.L != N || ax.F != N || N > nmax) return 0;
+  if (ax.blu || ax.L != N || ax.F != N || N > nmax || ax.m > N + kMaxNout) return 0;
   return (N == 64 || N == 128 || N == 256 || N == 512) ? N : 0;
 }
 int wpass_len(const AxisTab<float>& ax) { return wpass_len_t(ax, 512); }
@@ -215,7 +215,7 @@ int wpass_len(const AxisTab<df>& ax) { return wpass_len_t(ax, 256); }
 
 template <typename Tin, typename Tout>
 cudaError_t launch_pass_df(const PassLaunch<df>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
-  if (P.PP != wpass_pencils(P.wN) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
+  if (P.PP != wpass_pencils(P.wN) || P.ldt < wpass_ldt(P.wN, P.ax.m, true)) return cudaErrorInvalidConfiguration;
   switch (P.wN) {
     case 64: return launch_wpass<64, df, Tin, Tout>(P, mode, ndot, in, out, st);
     case 128: return launch_wpass<128, df, Tin, Tout>(P, mode, ndot, in, out, st);
@@ -237,18 +237,22 @@ int wpass_pencils(int N, bool pair) {
 }
 
 // tile (PP pencil rows of ldt values), PP / 2 sequence buffers of wpad(N)
-// complex values and PP rows of kMaxNout remainder coefficients -- for the
-// paired pass the same bytes per pencil (rows and buffers hold two pencils'
-// or two sequences' values)
-size_t wpass_smem_bytes(int N, int ldt, size_t elt, bool pair) {
+// complex values (none with alias: they live in the pairs' rows) and PP rows
+// of kMaxNout remainder coefficients -- for the paired pass the same bytes
+// per pencil (rows and buffers hold two pencils' or two sequences' values)
+size_t wpass_smem_bytes(int N, int ldt, size_t elt, bool pair, bool alias) {
   const int PP = wpass_pencils(N, pair);
-  return (size_t)PP * ldt * elt + (size_t)(PP / 2) * wpad(N) * 2 * elt + (size_t)PP * kMaxNout * elt;
+  return (size_t)PP * ldt * elt + (alias ? 0 : (size_t)(PP / 2) * wpad(N) * 2 * elt) +
+         (size_t)PP * kMaxNout * elt;
 }
+
+int wpass_ldt(int N, int m, bool alias) { return (alias ? std::max(m, wbuf_len_host(N)) : m) | 1; }
 
 template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st) {
   if (P.wN != 0) {
-    if (P.PP != wpass_pencils(P.wN, P.pair != 0) || P.ldt < P.ax.m) return cudaErrorInvalidConfiguration;
+    if (P.PP != wpass_pencils(P.wN, P.pair != 0) || P.ldt < wpass_ldt(P.wN, P.ax.m, false))
+      return cudaErrorInvalidConfiguration;
     switch (P.wN) {
       case 64: return launch_wpass<64, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);
       case 128: return launch_wpass<128, Tc, Tin, Tout>(P, MODE, NDOT, in, out, st);

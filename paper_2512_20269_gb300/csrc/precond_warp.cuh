@@ -277,7 +277,12 @@ __device__ __forceinline__ T row_lam(const tab_t<T>* __restrict__ lam, const int
 
 // KIND 1: DST-II / DST-III (even p), FFT length N = n_reg in Makhoul's order;
 // KIND 0: DST-I (odd p), FFT length N = 2 (n_reg + 1) of the odd extension.
-template <typename T, int N, int KIND, int MODE>
+// ALIAS: the sequence buffer of pencil pair pr occupies the pair's own two
+// tile rows (ldt >= wbuf_len<N>(), see wpass_ldt; no separate buffer, so more
+// CTAs fit on an SM): every step that moves values between the rows and the
+// buffer reads all it needs into registers before the warp writes, and no
+// other warp touches those rows. Otherwise the buffers follow the tile (wbuf).
+template <typename T, int N, int KIND, int MODE, bool ALIAS>
 __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, const Dims& dims, int ldt,
                                            const AxisTab<tab_t<T>>& ax, const vec2_t<tab_t<T>>* __restrict__ wt,
                                            const tab_t<T>* __restrict__ lamA, const tab_t<T>* __restrict__ lamB,
@@ -294,7 +299,8 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
   T* rb = ra + ldt;
   T* ova = outv + (2 * pr) * kMaxNout;
   T* ovb = ova + kMaxNout;
-  vec2_t<T>* buf = wbuf + (size_t)pr * wbuf_len<N>();
+  vec2_t<T>* buf = ALIAS ? reinterpret_cast<vec2_t<T>*>(ra)  // 2 ldt values >= wbuf_len<N>() complex
+                         : wbuf + (size_t)pr * wbuf_len<N>();
   const int nw = ax.n_out;
   constexpr int NR = (KIND == 1) ? N : N / 2 - 1;  // n_reg
 
@@ -375,17 +381,50 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       });
       wfft_rest<T, N>(buf, ls, wt);
       // separation, twiddle and D~^{-1}: outputs N-1-k and k-1 from Z[k], Z[N-k]
-      for (int k = ls; k <= N / 2; k += LS) {
-        const Cplx<T> zk = wld<T>(buf, wpad(k));
-        const Cplx<T> zm = wld<T>(buf, wpad(k == 0 ? 0 : N - k));
-        const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
-        const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
-        const Post4<TT> t = ldpost(ax.post, k);
-        ra[N - 1 - k] = fma(t.x, Ar, t.y * Ai);
-        rb[N - 1 - k] = fma(t.x, Br, t.y * Bi);
-        if (k > 0 && 2 * k != N) {
-          ra[k - 1] = fma(t.z, Ar, -t.w * Ai);
-          rb[k - 1] = fma(t.z, Br, -t.w * Bi);
+      if constexpr (ALIAS) {
+        constexpr int US = (N / 2 + LS) / LS;  // k = ls + LS u <= N / 2
+        T o1a[US], o1b[US], o2a[US], o2b[US];
+        auto put = [&](int u) {
+          const int k = ls + LS * u;
+          ra[N - 1 - k] = o1a[u];
+          rb[N - 1 - k] = o1b[u];
+          if (k > 0 && 2 * k != N) {
+            ra[k - 1] = o2a[u];
+            rb[k - 1] = o2b[u];
+          }
+        };
+#pragma unroll
+        for (int u = 0; u < US; ++u) {
+          const int k = ls + LS * u;
+          if (k <= N / 2) {
+            const Cplx<T> zk = wld<T>(buf, wpad(k));
+            const Cplx<T> zm = wld<T>(buf, wpad(k == 0 ? 0 : N - k));
+            const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
+            const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
+            const Post4<TT> t = ldpost(ax.post, k);
+            o1a[u] = fma(t.x, Ar, t.y * Ai);
+            o1b[u] = fma(t.x, Br, t.y * Bi);
+            o2a[u] = fma(t.z, Ar, -t.w * Ai);
+            o2b[u] = fma(t.z, Br, -t.w * Bi);
+                    }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < US; ++u)
+          if (ls + LS * u <= N / 2) put(u);
+      } else {
+        for (int k = ls; k <= N / 2; k += LS) {
+          const Cplx<T> zk = wld<T>(buf, wpad(k));
+          const Cplx<T> zm = wld<T>(buf, wpad(k == 0 ? 0 : N - k));
+          const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
+          const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
+          const Post4<TT> t = ldpost(ax.post, k);
+          ra[N - 1 - k] = fma(t.x, Ar, t.y * Ai);
+          rb[N - 1 - k] = fma(t.x, Br, t.y * Bi);
+          if (k > 0 && 2 * k != N) {
+            ra[k - 1] = fma(t.z, Ar, -t.w * Ai);
+            rb[k - 1] = fma(t.z, Br, -t.w * Bi);
+          }
         }
       }
     } else {
@@ -410,11 +449,35 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       });
       wfft_rest<T, N>(buf, ls, wt);
       // DST-I output j is -Im Z[j+1] (pencil a) and Re Z[j+1] (pencil b), times 1/(2 D~_j)
-      for (int j = ls; j < NR; j += LS) {
-        const Cplx<T> z = wld<T>(buf, wpad(j + 1));
-        const TT sc = ldg(ax.post + j);
-        ra[j] = -sc * z.y;
-        rb[j] = sc * z.x;
+      if constexpr (ALIAS) {
+        constexpr int UJ = (NR + LS - 1) / LS;
+        T oa[UJ], ob[UJ];
+#pragma unroll
+        for (int u = 0; u < UJ; ++u) {
+          const int j = ls + LS * u;
+          if (j < NR) {
+            const Cplx<T> z = wld<T>(buf, wpad(j + 1));
+            const TT sc = ldg(ax.post + j);
+            oa[u] = -sc * z.y;
+            ob[u] = sc * z.x;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < UJ; ++u) {
+          const int j = ls + LS * u;
+          if (j < NR) {
+            ra[j] = oa[u];
+            rb[j] = ob[u];
+          }
+        }
+      } else {
+        for (int j = ls; j < NR; j += LS) {
+          const Cplx<T> z = wld<T>(buf, wpad(j + 1));
+          const TT sc = ldg(ax.post + j);
+          ra[j] = -sc * z.y;
+          rb[j] = sc * z.x;
+        }
       }
     }
     __syncwarp();
@@ -451,72 +514,160 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
     }
     if constexpr (KIND == 1) {
       // inverse of the separation: G[k], G[N-k] from rows N-1-k and k-1
-      for (int k = ls; k <= N / 2; k += LS) {
-        const Post4<TT> t = ldpost(ax.post, k);
-        if (k == 0 || 2 * k == N) {
-          const TT s = t.x + t.x;
-          buf[wpad(k)] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
-        } else {
-          const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
-          const T ai = fma(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
-          const T br = fma(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
-          const T bi = fma(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
-          buf[wpad(k)] = vec2_t<T>{ar - bi, ai + br};
-          buf[wpad(N - k)] = vec2_t<T>{ar + bi, br - ai};
+      if constexpr (ALIAS) {
+        constexpr int US = (N / 2 + LS) / LS;
+        vec2_t<T> g1[US], g2[US];
+        auto put = [&](int u) {
+          const int k = ls + LS * u;
+          buf[wpad(k)] = g1[u];
+          if (k != 0 && 2 * k != N) buf[wpad(N - k)] = g2[u];
+        };
+#pragma unroll
+        for (int u = 0; u < US; ++u) {
+          const int k = ls + LS * u;
+          if (k <= N / 2) {
+            const Post4<TT> t = ldpost(ax.post, k);
+            if (k == 0 || 2 * k == N) {
+              const TT s = t.x + t.x;
+              g1[u] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
+            } else {
+              const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
+              const T ai = fma(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
+              const T br = fma(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
+              const T bi = fma(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+              g1[u] = vec2_t<T>{ar - bi, ai + br};
+              g2[u] = vec2_t<T>{ar + bi, br - ai};
+            }
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < US; ++u)
+          if (ls + LS * u <= N / 2) put(u);
+      } else {
+        for (int k = ls; k <= N / 2; k += LS) {
+          const Post4<TT> t = ldpost(ax.post, k);
+          if (k == 0 || 2 * k == N) {
+            const TT s = t.x + t.x;
+            buf[wpad(k)] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
+          } else {
+            const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
+            const T ai = fma(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
+            const T br = fma(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
+            const T bi = fma(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+            buf[wpad(k)] = vec2_t<T>{ar - bi, ai + br};
+            buf[wpad(N - k)] = vec2_t<T>{ar + bi, br - ai};
+          }
         }
       }
     } else {
       // odd extension of the scaled input w_j / (2 D~_j)
-      for (int l = ls; l < N; l += LS) {
-        T va = T(0), vb = T(0);
-        if (l != 0 && l != N / 2) {
-          const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
-          const TT sc = (l < N / 2) ? ldg(ax.post + jj) : -ldg(ax.post + jj);
-          va = sc * ra[jj];
-          vb = sc * rb[jj];
+      if constexpr (ALIAS) {
+        constexpr int UL = N / LS;
+        vec2_t<T> gv[UL];
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+          const int l = ls + LS * u;
+          T va = T(0), vb = T(0);
+          if (l != 0 && l != N / 2) {
+            const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
+            const TT sc = (l < N / 2) ? ldg(ax.post + jj) : -ldg(ax.post + jj);
+            va = sc * ra[jj];
+            vb = sc * rb[jj];
+          }
+          gv[u] = vec2_t<T>{va, vb};
         }
-        buf[wpad(l)] = vec2_t<T>{va, vb};
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < UL; ++u) buf[wpad(ls + LS * u)] = gv[u];
+      } else {
+        for (int l = ls; l < N; l += LS) {
+          T va = T(0), vb = T(0);
+          if (l != 0 && l != N / 2) {
+            const int jj = (l < N / 2) ? l - 1 : N - 1 - l;
+            const TT sc = (l < N / 2) ? ldg(ax.post + jj) : -ldg(ax.post + jj);
+            va = sc * ra[jj];
+            vb = sc * rb[jj];
+          }
+          buf[wpad(l)] = vec2_t<T>{va, vb};
+        }
       }
     }
     __syncwarp();
     wstage<T, N, 8, 1>(buf, ls, wt);
     wfft_rest<T, N>(buf, ls, wt);
     // x = V_reg w + W z_out, row by row (DST-III output j is +-Re/Im Z[l(j)];
-    // DST-I output j is -Im Z[j+1] / Re Z[j+1])
-    for (int i = ls; i < m; i += LS) {
-      auto wa = [&](int j) {
-        if constexpr (KIND == 1) {
-          const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
-          return neg_if(buf[wpad(l)].x, j & 1);
-        } else {
-          return -buf[wpad(j + 1)].y;
-        }
-      };
-      auto wb = [&](int j) {
-        if constexpr (KIND == 1) {
-          const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
-          return neg_if(buf[wpad(l)].y, j & 1);
-        } else {
-          return buf[wpad(j + 1)].x;
-        }
-      };
-      T xa, xb;
-      if (ax.nblk == 0 && i >= ax.rowsL && i < m - ax.rowsR) {  // identity rows
-        xa = wa(i - ax.o);
-        xb = wb(i - ax.o);
+    // DST-I output j is -Im Z[j+1] / Re Z[j+1]); with ALIAS all rows of the
+    // lane are formed from the buffer before any is written (m <= N + kMaxNout)
+    auto wa = [&](int j) {
+      if constexpr (KIND == 1) {
+        const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+        return neg_if(buf[wpad(l)].x, j & 1);
       } else {
-        xa = wscatter_row<T>(i, ax, wa);
-        xb = wscatter_row<T>(i, ax, wb);
+        return -buf[wpad(j + 1)].y;
       }
-      if (i < ax.wlo || i >= ax.whi) {
-        for (int k = 0; k < nw; ++k) {
-          const TT w = ldg(ax.W + i * nw + k);
-          xa = fma(w, ova[k], xa);
-          xb = fma(w, ovb[k], xb);
+    };
+    auto wb = [&](int j) {
+      if constexpr (KIND == 1) {
+        const int l = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+        return neg_if(buf[wpad(l)].y, j & 1);
+      } else {
+        return buf[wpad(j + 1)].x;
+      }
+    };
+    if constexpr (ALIAS) {
+      constexpr int UO = (N + kMaxNout + LS - 1) / LS;
+      T xs[UO][2];
+#pragma unroll
+      for (int u = 0; u < UO; ++u) {
+        const int i = ls + LS * u;
+        if (i >= m) break;
+        T xa, xb;
+        if (ax.nblk == 0 && i >= ax.rowsL && i < m - ax.rowsR) {  // identity rows
+          xa = wa(i - ax.o);
+          xb = wb(i - ax.o);
+        } else {
+          xa = wscatter_row<T>(i, ax, wa);
+          xb = wscatter_row<T>(i, ax, wb);
         }
+        if (i < ax.wlo || i >= ax.whi) {
+          for (int k = 0; k < nw; ++k) {
+            const TT w = ldg(ax.W + i * nw + k);
+            xa = fma(w, ova[k], xa);
+            xb = fma(w, ovb[k], xb);
+          }
+        }
+        xs[u][0] = xa;
+        xs[u][1] = xb;
       }
-      ra[i] = xa;
-      rb[i] = xb;
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < UO; ++u) {
+        const int i = ls + LS * u;
+        if (i >= m) break;
+        ra[i] = xs[u][0];
+        rb[i] = xs[u][1];
+      }
+    } else {
+      for (int i = ls; i < m; i += LS) {
+        T xa, xb;
+        if (ax.nblk == 0 && i >= ax.rowsL && i < m - ax.rowsR) {  // identity rows
+          xa = wa(i - ax.o);
+          xb = wb(i - ax.o);
+        } else {
+          xa = wscatter_row<T>(i, ax, wa);
+          xb = wscatter_row<T>(i, ax, wb);
+        }
+        if (i < ax.wlo || i >= ax.whi) {
+          for (int k = 0; k < nw; ++k) {
+            const TT w = ldg(ax.W + i * nw + k);
+            xa = fma(w, ova[k], xa);
+            xb = fma(w, ovb[k], xb);
+          }
+        }
+        ra[i] = xa;
+        rb[i] = xb;
+      }
     }
   }
 }
@@ -812,19 +963,19 @@ __device__ __forceinline__ void wcompute(T* tile, vec2_t<T>* wbuf, T* outv, cons
                                          const tab_t<T>* __restrict__ lamA, const tab_t<T>* __restrict__ lamB,
                                          const long long* pbase, const int* pia, const int* pib, const TileInfo& g) {
   if constexpr (std::is_same<T, double>::value && MODE == PM_FUSED) {
-    wtransform<T, N, KIND, PM_FWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    wtransform<T, N, KIND, PM_FWD, walias<T>()>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
     __syncthreads();
     wscale_tile<N>(tile, axis, ldt, ax, dims, lamA, lamB, pbase, pia, pib, g);
     __syncthreads();
-    wtransform<T, N, KIND, PM_BWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    wtransform<T, N, KIND, PM_BWD, walias<T>()>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
   } else if constexpr (std::is_same<T, df>::value && MODE == PM_FUSED) {
-    wtransform<T, N, KIND, PM_FWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    wtransform<T, N, KIND, PM_FWD, walias<T>()>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
     __syncthreads();
     wscale_tile_df<N>(tile, ldt, ax, dims, lamA, lamB, pia, pib, g);
     __syncthreads();
-    wtransform<T, N, KIND, PM_BWD>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    wtransform<T, N, KIND, PM_BWD, walias<T>()>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
   } else {
-    wtransform<T, N, KIND, MODE>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
+    wtransform<T, N, KIND, MODE, walias<T>()>(tile, wbuf, outv, dims, ldt, ax, wt, lamA, lamB, pia, pib);
   }
 }
 
@@ -851,9 +1002,11 @@ __device__ __forceinline__ void wpass_body(const Tin* __restrict__ in, Tout* __r
                                            unsigned char* smem) {
   constexpr bool PAIR = IsPair<T>::value;
   constexpr int PP = warp_pencils<N, PAIR>(), PR = PAIR ? PP / 2 : PP;  // pencils, tile rows
-  T* tile = reinterpret_cast<T*>(smem);
-  vec2_t<T>* wbuf = reinterpret_cast<vec2_t<T>*>(tile + (size_t)PR * ldt);
-  T* outv = reinterpret_cast<T*>(wbuf + (size_t)(PR / 2) * wbuf_len<N>());  // PR * kMaxNout
+  T* tile = reinterpret_cast<T*>(smem);  // PR rows of ldt values
+  // sequence buffers inside the rows (walias) or after them
+  vec2_t<T>* wbuf = walias<T>() ? nullptr : reinterpret_cast<vec2_t<T>*>(tile + (size_t)PR * ldt);
+  T* outv = walias<T>() ? tile + (size_t)PR * ldt
+                        : reinterpret_cast<T*>(wbuf + (size_t)(PR / 2) * wbuf_len<N>());  // PR * kMaxNout
   __shared__ long long pbase[PP];
   __shared__ int pia[PP], pib[PP];
   const TileInfo g = wtile_setup(dims, axis, PP, tile_id, pbase, pia, pib);
@@ -915,7 +1068,7 @@ precond_wpass_batched(const PassDesc<float, Tin, Tout>* __restrict__ sys, const 
 template <typename T, int N, int KIND, typename Tin, typename Tout, int MODE, int NDOT>
 cudaError_t launch_wpass_n(const PassLaunch<tab_t<T>>& P, const Tin* in, Tout* out, cudaStream_t st) {
   constexpr bool PAIR = IsPair<T>::value;
-  const size_t sm = wpass_smem_bytes(N, P.ldt, sizeof(tab_t<T>), PAIR);
+  const size_t sm = wpass_smem_bytes(N, P.ldt, sizeof(tab_t<T>), PAIR, walias<T>());
   const int tiles = precond_tiles(P.dims, P.axis, warp_pencils<N, PAIR>());
   auto kern = precond_wpass<T, N, KIND, Tin, Tout, MODE, NDOT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

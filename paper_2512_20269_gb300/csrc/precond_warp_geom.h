@@ -2,6 +2,8 @@
 // with the host code that sizes their launches (precond.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace iffd {
@@ -40,6 +42,15 @@ __host__ __device__ constexpr int wpad(int i) { return i + (i >> 3); }
 template <int N>
 __host__ __device__ constexpr int wbuf_len() {
   return N + N / 8;
+}
+inline int wbuf_len_host(int N) { return N + N / 8; }
+
+// Whether the warp pass of arithmetic T keeps each pencil pair's sequence
+// buffer inside the pair's tile rows (double-float: a fourth resident CTA per
+// SM, measured faster; FP32 kept the separate buffers, measured faster there).
+template <typename T>
+__host__ __device__ constexpr bool walias() {
+  return std::is_same<T, df>::value;
 }
 
 }  // namespace iffd
