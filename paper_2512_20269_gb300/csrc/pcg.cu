@@ -14,7 +14,8 @@ namespace iffd {
 
 int vec_grid(long long N) {
   long long g = (N + 1023) / 1024;
-  if (g > 4 * 152) g = 4 * 152;
+  const long long cap = 4LL * device_sm_count();  // four 256-thread CTAs per SM
+  if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
 }
