@@ -291,7 +291,9 @@ def replica_throughput(dofs_per_solve: int, steps: int, world: int, max_ms: floa
 def workload_config(w):
     return {"workload": w.name, "d": w.d, "n": w.n, "p": w.p, "N": w.N, "rhs": f"{w.dist} seed {w.seed}",
             "precond": "IFFD", "precision": "fp64", "rtol": 1e-8, "boundary": "Dirichlet on all faces",
-            "l2": "no flush: 137 MB vectors, ~1 GB working set > 126 MB L2"}
+            "l2": "no flush: 137 MB vectors, ~1 GB working set > 126 MB L2",
+            "timing": "the timed solves record a CUDA event pair around every kernel launch (per-kernel "
+                      "roofline); the e2e solves run without them"}
 
 
 def _timed(fn, reps: int, warm: int):
