@@ -1060,9 +1060,136 @@ int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const if
   return IFFD_OK;
 }
 
+// The opening launches of a PCG solve (Section 3, zero start): state reset,
+// x = 0, r = f, (f, f), z = P^{-1} r with (r, z).
+static int enqueue_start(const Plan* P, const double* f, double* u, void* ws, cudaStream_t st) {
+  const long long N = P->dims.N;
+  double* r = reinterpret_cast<double*>(wsb(ws, P->off_r));
+  double* z = reinterpret_cast<double*>(wsb(ws, P->off_z));
+  double* part = reinterpret_cast<double*>(wsb(ws, P->off_part));
+  SolveState* S = reinterpret_cast<SolveState*>(wsb(ws, P->off_state));
+  const double tol2 = P->opt.rtol * P->opt.rtol;
+  const int maxit = P->opt.maxit;
+  int np = 0;
+  IFFD_CUDA(cudaMemsetAsync(S, 0, sizeof(SolveState), st));
+  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st));
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_FF, tol2, maxit, st));
+  const int rc = run_precond(P, r, z, ws, st, &S->done, 1, r, nullptr, part, &np);
+  if (rc) return rc;
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_RZ0, tol2, maxit, st));
+  return IFFD_OK;
+}
+
+// One PCG iteration: p = z (it == 0) or z + beta p fused into the first
+// stiffness sweep, q = A^ p with (p, q), alpha, x += alpha p, r -= alpha q with
+// (r, r) and the stopping test, z = P^{-1} r with (r, z) (and (q, z) for the
+// flexible beta), beta. Every kernel returns at once after the solve is done.
+static int enqueue_iteration(const Plan* P, double* u, void* ws, cudaStream_t st, int it) {
+  const long long N = P->dims.N;
+  double* r = reinterpret_cast<double*>(wsb(ws, P->off_r));
+  double* z = reinterpret_cast<double*>(wsb(ws, P->off_z));
+  double* p = reinterpret_cast<double*>(wsb(ws, P->off_p));
+  double* q = reinterpret_cast<double*>(wsb(ws, P->off_q));
+  double* part = reinterpret_cast<double*>(wsb(ws, P->off_part));
+  SolveState* S = reinterpret_cast<SolveState*>(wsb(ws, P->off_state));
+  const int* done = &S->done;
+  const double tol2 = P->opt.rtol * P->opt.rtol;
+  const int maxit = P->opt.maxit;
+  const bool flex = P->opt.flexible || P->opt.precision == IFFD_PREC_FP32_TRANSFORM;
+  int np = 0;
+  int rc = run_stiffness(P, nullptr, z, p, &S->beta, it == 0 ? 1 : 2, q, ws, st, done, p, part, &np);
+  if (rc) return rc;
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_PQ, tol2, maxit, st));
+  IFFD_LAUNCH(P, IFFD_K_PCG_UPDATE, st, launch_pcg_update(u, r, p, q, S, N, part, done, st));
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_RR, tol2, maxit, st));
+  rc = run_precond(P, r, z, ws, st, done, flex ? 2 : 1, r, q, part, &np);
+  if (rc) return rc;
+  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, flex ? FP_RZ_FLEX : FP_RZ, tol2, maxit, st));
+  return IFFD_OK;
+}
+
+static void drop_graphs(Plan::SolveGraphs& G) {
+  if (G.first) cudaGraphExecDestroy(G.first);
+  if (G.next) cudaGraphExecDestroy(G.next);
+  G.first = G.next = nullptr;
+  G.f = nullptr;
+  G.u = nullptr;
+  G.ws = nullptr;
+}
+
+void plan_drop_graphs(Plan* P) {
+  drop_graphs(P->graphs);
+  P->graphs.failed = false;
+}
+
+// Captures what `enqueue` launches on the plan's private stream into an
+// executable graph; `kernels` receives the number of kernel launches in it.
+template <typename Fn>
+static int capture_graph(const Plan* P, Fn enqueue, cudaGraphExec_t* exec, long long* kernels) {
+  cudaStream_t cap = P->graphs.cap;
+  const long long l0 = P->prof.launches;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+  const int rc = enqueue(cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cap, &g);
+  *kernels = P->prof.launches - l0;
+  P->prof.launches = l0;  // captured, not run
+  if (rc || e != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : cuda_fail(e, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return IFFD_OK;
+}
+
+// The two graphs of a solve on (f, u, ws): the opening launches with the
+// first `chunk` iterations, and `chunk` later iterations.
+static int capture_solve_graphs(const Plan* P, const double* f, double* u, void* ws, int chunk) {
+  Plan::SolveGraphs& G = P->graphs;
+  drop_graphs(G);
+  if (!G.cap) {
+    const cudaError_t e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      G.cap = nullptr;
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+  }
+  int rc = capture_graph(
+      P,
+      [&](cudaStream_t cs) {
+        int r = enqueue_start(P, f, u, ws, cs);
+        for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, c);
+        return r;
+      },
+      &G.first, &G.kfirst);
+  if (rc) return rc;
+  rc = capture_graph(
+      P,
+      [&](cudaStream_t cs) {
+        int r = IFFD_OK;
+        for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, chunk + c);
+        return r;
+      },
+      &G.next, &G.knext);
+  if (rc) return rc;
+  G.f = f;
+  G.u = u;
+  G.ws = ws;
+  return IFFD_OK;
+}
+
 void plan_release(iffd_plan* h) {
   if (!h) return;
   Plan* P = &h->P;
+  drop_graphs(P->graphs);
+  if (P->graphs.cap) cudaStreamDestroy(P->graphs.cap);
   P->prof.release();
   if (P->dev) cudaFree(P->dev);
   if (P->rden) cudaFree(P->rden);
@@ -1228,41 +1355,66 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   const Plan* P = &h->P;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long N = P->dims.N;
-  double* r = reinterpret_cast<double*>(wsb(ws, P->off_r));
-  double* z = reinterpret_cast<double*>(wsb(ws, P->off_z));
-  double* p = reinterpret_cast<double*>(wsb(ws, P->off_p));
   double* q = reinterpret_cast<double*>(wsb(ws, P->off_q));
   double* part = reinterpret_cast<double*>(wsb(ws, P->off_part));
   SolveState* S = reinterpret_cast<SolveState*>(wsb(ws, P->off_state));
-  const int* done = &S->done;
   const double tol2 = P->opt.rtol * P->opt.rtol;
   const int maxit = P->opt.maxit;
-  const bool flex = P->opt.flexible || P->opt.precision == IFFD_PREC_FP32_TRANSFORM;
-  int np = 0;
+  const int chunk = 4;  // iterations enqueued between two reads of the solve state
 
-  IFFD_CUDA(cudaMemsetAsync(S, 0, sizeof(SolveState), st));
-  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st));
-  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_FF, tol2, maxit, st));
-  rc = run_precond(P, r, z, ws, st, done, 1, r, nullptr, part, &np);
-  if (rc) return rc;
-  IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_RZ0, tol2, maxit, st));
-  int it = 0;
-  const int chunk = 4;
-  bool finished = false;
-  while (!finished) {
-    for (int c = 0; c < chunk && it < maxit; ++c, ++it) {
-      rc = run_stiffness(P, nullptr, z, p, &S->beta, it == 0 ? 1 : 2, q, ws, st, done, p, part, &np);
-      if (rc) return rc;
-      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, FP_PQ, tol2, maxit, st));
-      IFFD_LAUNCH(P, IFFD_K_PCG_UPDATE, st, launch_pcg_update(u, r, p, q, S, N, part, done, st));
-      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_RR, tol2, maxit, st));
-      rc = run_precond(P, r, z, ws, st, done, flex ? 2 : 1, r, q, part, &np);
-      if (rc) return rc;
-      IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, np, flex ? FP_RZ_FLEX : FP_RZ, tol2, maxit, st));
+  // Chunks run from captured CUDA graphs when they can (one launch per chunk
+  // instead of ~50): not while per-launch event timing is on, and only for
+  // the (f, u, workspace) they were captured with.
+  bool graphed = false;
+  if (!P->prof.on && !P->graphs.failed && maxit >= chunk) {
+    Plan::SolveGraphs& G = P->graphs;
+    const bool repeat = G.last_f == f && G.last_u == u && G.last_ws == ws;
+    G.last_f = f;
+    G.last_u = u;
+    G.last_ws = ws;
+    if (repeat && !(G.first && G.next && G.f == f && G.u == u && G.ws == ws)) {
+      rc = capture_solve_graphs(P, f, u, ws, chunk);
+      if (rc) {  // not capturable here: fall back to direct launches for good
+        drop_graphs(G);
+        G.failed = true;
+        g_err.clear();
+      }
     }
+    graphed = G.first && G.next && G.f == f && G.u == u && G.ws == ws;
+  }
+  auto read_state = [&]() -> int {
     IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
     IFFD_CUDA(cudaStreamSynchronize(st));
+    return IFFD_OK;
+  };
+  int it = 0;
+  bool finished = false;
+  if (graphed) {
+    IFFD_CUDA(cudaGraphLaunch(P->graphs.first, st));
+    P->prof.launches += P->graphs.kfirst;
+    it = chunk;
+    if ((rc = read_state())) return rc;
     finished = P->host_state->done || it >= maxit;
+    while (!finished) {
+      if (it + chunk <= maxit) {
+        IFFD_CUDA(cudaGraphLaunch(P->graphs.next, st));
+        P->prof.launches += P->graphs.knext;
+        it += chunk;
+      } else {
+        for (; it < maxit; ++it)
+          if ((rc = enqueue_iteration(P, u, ws, st, it))) return rc;
+      }
+      if ((rc = read_state())) return rc;
+      finished = P->host_state->done || it >= maxit;
+    }
+  } else {
+    if ((rc = enqueue_start(P, f, u, ws, st))) return rc;
+    while (!finished) {
+      for (int c = 0; c < chunk && it < maxit; ++c, ++it)
+        if ((rc = enqueue_iteration(P, u, ws, st, it))) return rc;
+      if ((rc = read_state())) return rc;
+      finished = P->host_state->done || it >= maxit;
+    }
   }
   SolveState hs = *P->host_state;
   double true_rel = -1.0;

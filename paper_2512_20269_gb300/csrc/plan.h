@@ -169,6 +169,24 @@ struct Plan {
   size_t off_r, off_z, off_p, off_q, off_t1, off_t2, off_t3, off_t4, off_tf, off_part, off_state, ws_bytes;
   int max_parts = 0;
   SolveState* host_state = nullptr;  // pinned
+  // Captured CUDA graphs of the PCG solve's chunks (iffd_pcg_solve): the
+  // start and first iterations, and a chunk of later iterations, for one
+  // (f, u, workspace); rebuilt when those or the launch geometry change.
+  struct SolveGraphs {
+    const double* f = nullptr;
+    double* u = nullptr;
+    void* ws = nullptr;
+    cudaStream_t cap = nullptr;  // private capture stream
+    cudaGraphExec_t first = nullptr, next = nullptr;
+    long long kfirst = 0, knext = 0;  // kernels per replay
+    bool failed = false;              // capture not possible here: launch directly
+    // the previous solve's (f, u, workspace): graphs are captured when a
+    // solve repeats them, so one-off solves pay no capture
+    const double* last_f = nullptr;
+    double* last_u = nullptr;
+    void* last_ws = nullptr;
+  };
+  mutable SolveGraphs graphs;
 };
 
 
@@ -186,6 +204,8 @@ namespace iffd {
 int plan_create(int d, const int* n_elems, int p, const int* dirichlet, const iffd_options* opt, cudaStream_t stream,
                 iffd_plan** out, const int* nrep = nullptr, const int* reps = nullptr);
 void plan_release(iffd_plan* h);
+// Drops the captured solve graphs (after a change of launch geometry).
+void plan_drop_graphs(Plan* P);
 // Launch geometry of the FP32 transform passes of direction a: pencils per
 // tile, tile row length, warp-FFT length (0: block kernel) and its twiddles,
 // shared memory of one (non-pipelined) CTA.

@@ -246,6 +246,7 @@ int tune_stiffness(Plan* P, int a, char* ws, cudaStream_t st, Timer& tm) {
 }  // namespace
 
 int plan_autotune(Plan* P, void* ws, cudaStream_t st) {
+  plan_drop_graphs(P);
   char* w = static_cast<char*>(ws);
   Timer tm;
   IFFD_CUDA(cudaEventCreate(&tm.e0));
@@ -297,6 +298,7 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   g_err.clear();
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   Plan& P = h->P;
+  plan_drop_graphs(&P);
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
   auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
   if (pipelined == 3) {
