@@ -590,7 +590,22 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     max_parts = std::max(max_parts, stiff_tiles(P->dims, a, kMinTunePP));
   }
   P->max_parts = max_parts;
-  P->dfq = dfq_eligible(*P);
+  // FP64 plans: the double-float passes by default where every direction has
+  // one and their tiles fill the GPU. Small problems are latency-bound (a few
+  // long CTAs); they take the FP64-pipe block kernel instead, its tile
+  // narrowed (8, 4, 2 pencils) until the tiles fill the GPU or reach 2 pencils
+  // (65^2, p = 3: 0.61 against 0.71 ms per solve).
+  {
+    const int sms = device_sm_count();
+    bool fills = true;
+    for (int a = 0; a < P->d; ++a) {
+      const int wN = wpass_len(P->axq[a]);
+      if (wN == 0 || precond_tiles(P->dims, a, wpass_pencils(wN)) < sms) fills = false;
+    }
+    P->dfq = dfq_eligible(*P) && fills;
+    for (int a = 0; a < P->d; ++a)
+      while (P->PPd[a] > 2 && precond_tiles(P->dims, a, P->PPd[a]) < sms) P->PPd[a] /= 2;
+  }
   const size_t vec = align256((size_t)N * sizeof(double));
   size_t off = 0;
   P->off_r = off; off += vec;
@@ -1108,13 +1123,14 @@ static int enqueue_iteration(const Plan* P, double* u, void* ws, cudaStream_t st
   return IFFD_OK;
 }
 
+static void drop_graph(Plan::SolveGraph& g) {
+  if (g.first) cudaGraphExecDestroy(g.first);
+  if (g.next) cudaGraphExecDestroy(g.next);
+  g = Plan::SolveGraph{};
+}
+
 static void drop_graphs(Plan::SolveGraphs& G) {
-  if (G.first) cudaGraphExecDestroy(G.first);
-  if (G.next) cudaGraphExecDestroy(G.next);
-  G.first = G.next = nullptr;
-  G.f = nullptr;
-  G.u = nullptr;
-  G.ws = nullptr;
+  for (auto& g : G.g) drop_graph(g);
 }
 
 void plan_drop_graphs(Plan* P) {
@@ -1149,11 +1165,12 @@ static int capture_graph(const Plan* P, Fn enqueue, cudaGraphExec_t* exec, long 
   return IFFD_OK;
 }
 
-// The two graphs of a solve on (f, u, ws): the opening launches with the
-// first `chunk` iterations, and `chunk` later iterations.
-static int capture_solve_graphs(const Plan* P, const double* f, double* u, void* ws, int chunk) {
+// The two graphs of a solve on (f, u, ws), into slot g: the opening launches
+// with the first `chunk` iterations, and `chunk` later iterations.
+static int capture_solve_graphs(const Plan* P, Plan::SolveGraph& g, const double* f, double* u, void* ws,
+                                int chunk) {
   Plan::SolveGraphs& G = P->graphs;
-  drop_graphs(G);
+  drop_graph(g);
   if (!G.cap) {
     const cudaError_t e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -1168,7 +1185,7 @@ static int capture_solve_graphs(const Plan* P, const double* f, double* u, void*
         for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, c);
         return r;
       },
-      &G.first, &G.kfirst);
+      &g.first, &g.kfirst);
   if (rc) return rc;
   rc = capture_graph(
       P,
@@ -1177,12 +1194,42 @@ static int capture_solve_graphs(const Plan* P, const double* f, double* u, void*
         for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, chunk + c);
         return r;
       },
-      &G.next, &G.knext);
+      &g.next, &g.knext);
   if (rc) return rc;
-  G.f = f;
-  G.u = u;
-  G.ws = ws;
+  g.f = f;
+  g.u = u;
+  g.ws = ws;
   return IFFD_OK;
+}
+
+// The graph set for a solve on (f, u, ws), captured if this triple was one of
+// the last two solves' (nullptr: launch directly).
+static const Plan::SolveGraph* solve_graphs_for(const Plan* P, const double* f, double* u, void* ws, int chunk) {
+  Plan::SolveGraphs& G = P->graphs;
+  const unsigned long long now = ++G.tick;
+  for (auto& g : G.g)
+    if (g.first && g.next && g.f == f && g.u == u && g.ws == ws) {
+      g.used = now;
+      return &g;
+    }
+  bool seen = false;
+  for (int k = 0; k < 2; ++k) seen = seen || (G.seen_f[k] == f && G.seen_u[k] == u && G.seen_ws[k] == ws);
+  G.seen_f[1] = G.seen_f[0];
+  G.seen_u[1] = G.seen_u[0];
+  G.seen_ws[1] = G.seen_ws[0];
+  G.seen_f[0] = f;
+  G.seen_u[0] = u;
+  G.seen_ws[0] = ws;
+  if (!seen) return nullptr;
+  Plan::SolveGraph& slot = G.g[0].used <= G.g[1].used ? G.g[0] : G.g[1];
+  if (capture_solve_graphs(P, slot, f, u, ws, chunk)) {  // not capturable here: direct launches for good
+    drop_graphs(G);
+    G.failed = true;
+    g_err.clear();
+    return nullptr;
+  }
+  slot.used = now;
+  return &slot;
 }
 
 void plan_release(iffd_plan* h) {
@@ -1365,23 +1412,8 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   // Chunks run from captured CUDA graphs when they can (one launch per chunk
   // instead of ~50): not while per-launch event timing is on, and only for
   // the (f, u, workspace) they were captured with.
-  bool graphed = false;
-  if (!P->prof.on && !P->graphs.failed && maxit >= chunk) {
-    Plan::SolveGraphs& G = P->graphs;
-    const bool repeat = G.last_f == f && G.last_u == u && G.last_ws == ws;
-    G.last_f = f;
-    G.last_u = u;
-    G.last_ws = ws;
-    if (repeat && !(G.first && G.next && G.f == f && G.u == u && G.ws == ws)) {
-      rc = capture_solve_graphs(P, f, u, ws, chunk);
-      if (rc) {  // not capturable here: fall back to direct launches for good
-        drop_graphs(G);
-        G.failed = true;
-        g_err.clear();
-      }
-    }
-    graphed = G.first && G.next && G.f == f && G.u == u && G.ws == ws;
-  }
+  const Plan::SolveGraph* graph = nullptr;
+  if (!P->prof.on && !P->graphs.failed && maxit >= chunk) graph = solve_graphs_for(P, f, u, ws, chunk);
   auto read_state = [&]() -> int {
     IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
     IFFD_CUDA(cudaStreamSynchronize(st));
@@ -1389,16 +1421,16 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   };
   int it = 0;
   bool finished = false;
-  if (graphed) {
-    IFFD_CUDA(cudaGraphLaunch(P->graphs.first, st));
-    P->prof.launches += P->graphs.kfirst;
+  if (graph) {
+    IFFD_CUDA(cudaGraphLaunch(graph->first, st));
+    P->prof.launches += graph->kfirst;
     it = chunk;
     if ((rc = read_state())) return rc;
     finished = P->host_state->done || it >= maxit;
     while (!finished) {
       if (it + chunk <= maxit) {
-        IFFD_CUDA(cudaGraphLaunch(P->graphs.next, st));
-        P->prof.launches += P->graphs.knext;
+        IFFD_CUDA(cudaGraphLaunch(graph->next, st));
+        P->prof.launches += graph->knext;
         it += chunk;
       } else {
         for (; it < maxit; ++it)

@@ -171,20 +171,26 @@ struct Plan {
   SolveState* host_state = nullptr;  // pinned
   // Captured CUDA graphs of the PCG solve's chunks (iffd_pcg_solve): the
   // start and first iterations, and a chunk of later iterations, for one
-  // (f, u, workspace); rebuilt when those or the launch geometry change.
-  struct SolveGraphs {
+  // (f, u, workspace) each; two such sets (double-buffered callers), dropped
+  // when the launch geometry changes.
+  struct SolveGraph {
     const double* f = nullptr;
     double* u = nullptr;
     void* ws = nullptr;
-    cudaStream_t cap = nullptr;  // private capture stream
     cudaGraphExec_t first = nullptr, next = nullptr;
     long long kfirst = 0, knext = 0;  // kernels per replay
-    bool failed = false;              // capture not possible here: launch directly
-    // the previous solve's (f, u, workspace): graphs are captured when a
-    // solve repeats them, so one-off solves pay no capture
-    const double* last_f = nullptr;
-    double* last_u = nullptr;
-    void* last_ws = nullptr;
+    unsigned long long used = 0;      // last use (replacement order)
+  };
+  struct SolveGraphs {
+    cudaStream_t cap = nullptr;  // private capture stream
+    SolveGraph g[2];
+    bool failed = false;  // capture not possible here: launch directly
+    // the (f, u, workspace) of the last two solves: graphs are captured when
+    // a solve repeats one, so one-off solves pay no capture
+    const double* seen_f[2] = {nullptr, nullptr};
+    double* seen_u[2] = {nullptr, nullptr};
+    void* seen_ws[2] = {nullptr, nullptr};
+    unsigned long long tick = 0;
   };
   mutable SolveGraphs graphs;
 };

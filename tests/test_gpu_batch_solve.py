@@ -63,6 +63,8 @@ def test_batch_solve_mixed_equals_alone_and_oracle():
     plans, fs, hosts = [], [], []
     for k, (d, n, p, prec, pc, coef, dirichlet, nrhs, _) in enumerate(BATCH):
         pl = IFFDPlan(d, n, p, precision=prec, precond=pc, coef=coef, dirichlet=dirichlet, true_residual=True)
+        if (d, n, p, prec) == (3, 64, 4, "fp64"):
+            pl.set_geometry(0, double_float=True)
         fh = np.stack([inputs.rhs(pl.shape, "normal", seed=600 + 10 * k + j) for j in range(nrhs)])
         plans.append(pl)
         hosts.append(fh)

@@ -38,7 +38,7 @@ def _gpu(torch, a):
 def test_double_float_preconditioner_matches_oracle(d, n, p):
     torch = require_gpu()
     from paper_2512_20269_gb300 import IFFDPlan
-    plan = IFFDPlan(d, n, p)
+    plan = IFFDPlan(d, n, p).set_geometry(0, double_float=True)  # small grids default to the FP64 kernel
     assert all(plan.tiles(a)["double_float"] for a in range(d))
     r = inputs.rhs(plan.shape, "normal", seed=800 + n + p)
     rg = _gpu(torch, r)
@@ -60,7 +60,7 @@ def test_double_float_unequal_directions_and_ragged_tiles():
     from oracle import operators
     from paper_2512_20269_gb300 import IFFDPlan
     ns = (64, 128, 256)  # p = 4: lengths 64, 128, 256; 130 x 66 x 258 pencils leave ragged tiles
-    plan = IFFDPlan(3, list(ns), 4)
+    plan = IFFDPlan(3, list(ns), 4).set_geometry(0, double_float=True)
     assert all(plan.tiles(a)["double_float"] for a in range(3))
     r = inputs.rhs(plan.shape, "uniform", seed=810)
     z = plan.apply_preconditioner(_gpu(torch, r)).cpu().numpy()
@@ -75,7 +75,7 @@ def test_double_float_zeros_and_far_magnitudes(scale):
     torch = require_gpu()
     from paper_2512_20269_gb300 import IFFDPlan
     n, p = 64, 4
-    plan = IFFDPlan(3, n, p)
+    plan = IFFDPlan(3, n, p).set_geometry(0, double_float=True)
     r = inputs.rhs(plan.shape, "normal", seed=820)
     r[::3] = 0.0  # zeros inside every pencil
     if scale:
@@ -91,7 +91,7 @@ def test_double_float_zeros_and_far_magnitudes(scale):
 def test_double_float_pcg(d, n, p):
     torch = require_gpu()
     from paper_2512_20269_gb300 import IFFDPlan
-    plan = IFFDPlan(d, n, p)
+    plan = IFFDPlan(d, n, p).set_geometry(0, double_float=True)
     f = inputs.rhs(plan.shape, "uniform", seed=830 + n)
     u, info = plan.pcg_solve(_gpu(torch, f))
     uh = u.cpu().numpy()
@@ -118,3 +118,8 @@ def test_double_float_switch():
         IFFDPlan(3, 64, 4, precision="fp32").set_geometry(0, double_float=True)
     assert not any(IFFDPlan(3, 64, 4, precision="fp32").tiles(a)["double_float"] for a in range(3))
     assert not IFFDPlan(3, 96, 4).tiles(0)["double_float"]       # length 96: FP64 block kernel
+    # the default: double-float where the warp tiles fill the GPU (130^3: 16,900 / 32 pencils
+    # per tile >= SMs), the FP64 block kernel with narrowed tiles on small grids
+    assert all(IFFDPlan(3, 128, 4).tiles(a)["double_float"] for a in range(3))
+    small = IFFDPlan(2, 64, 3)
+    assert not small.tiles(0)["double_float"] and small.tiles(0)["pencils_transform"] == 2

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 PLANS = [
     dict(d=3, n=24, p=4, precision="fp64"),                      # FP64 block passes
-    dict(d=3, n=64, p=4, precision="fp64"),                      # double-float passes
+    dict(d=3, n=128, p=4, precision="fp64"),                     # double-float passes
     dict(d=3, n=64, p=3, precision="fp32"),                      # FP32 warp passes (flexible beta)
     dict(d=2, n=40, p=5, precision="fp64", precond="exact_fd"),  # exact FD comparator
 ]
