@@ -577,7 +577,10 @@ def main():
     # Launches that did work: iterations are enqueued in chunks of 4 and the
     # surplus launches after convergence return at their first instruction, so
     # per-launch rates use the launches of the executed iterations only.
-    applies = args.steps * (iters + 1)  # preconditioner applies (initial + one per iteration)
+    # preconditioner applies that did work: the initial one and one per
+    # iteration except the last (its residual met the tolerance, so its apply
+    # exits at once)
+    applies = args.steps * iters
     eff = {"precond_fwd": applies * (w.d - 1), "precond_fused": applies, "precond_bwd": applies * (w.d - 1),
            "stiff_first": args.steps * iters, "stiff_mid": args.steps * iters, "stiff_last": args.steps * iters,
            "pcg_update": args.steps * iters}
