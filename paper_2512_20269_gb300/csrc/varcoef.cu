@@ -49,9 +49,10 @@ __device__ __forceinline__ void t_mk(const VCoefs<P>& c, const double* row, int 
   kx = ak;
 }
 
+// acc + (M x)_i, the product chain continuing from acc (no separate add)
 template <int P>
-__device__ __forceinline__ double t_m(const VCoefs<P>& c, const double* row, int i) {
-  double a = c.m[0] * row[i];
+__device__ __forceinline__ double t_m_acc(const VCoefs<P>& c, const double* row, int i, double acc) {
+  double a = fma(c.m[0], row[i], acc);
 #pragma unroll
   for (int k = 1; k <= P; ++k) a = fma(c.m[k], row[i - k] + row[i + k], a);
   return a;
@@ -82,10 +83,11 @@ __device__ __forceinline__ void w_ab(const double* __restrict__ Ab, const double
   bx = sb;
 }
 
+// acc + (A x)_i over the full band window
 template <int P>
-__device__ __forceinline__ double w_a(const double* __restrict__ Ab, const double* row, int i) {
+__device__ __forceinline__ double w_a(const double* __restrict__ Ab, const double* row, int i, double acc = 0.0) {
   const double* a = Ab + (size_t)i * (2 * P + 1);
-  double s = 0.0;
+  double s = acc;
 #pragma unroll
   for (int d = 0; d <= 2 * P; ++d) s = fma(__ldg(a + d), row[i - P + d], s);
   return s;
@@ -207,14 +209,12 @@ vstiff_mid(Dims dims, int axis, int PP, int ldt, BandTab bt, WBandTab wb, double
     const int i = bt.ilo + r;
     double mx, kx, ms3, ks3;
     t_mk<P>(c, t1 + pc * ldt, i, mx, kx);
-    const double m2 = t_m<P>(c, t2 + pc * ldt, i);
     w_ab<P>(wb.Msb, wb.Ksb, t3 + pc * ldt, i, ms3, ks3);
-    const double ms4 = w_a<P>(wb.Msb, t4 + pc * ldt, i);
     const long long off = pbase[pc] + i * g.S;
     T1[off] = mx;
-    T2[off] = kx + m2;
+    T2[off] = t_m_acc<P>(c, t2 + pc * ldt, i, kx);            // K T1 + M T2
     T3[off] = ms3;
-    T4[off] = ks3 + ms4;
+    T4[off] = w_a<P>(wb.Msb, t4 + pc * ldt, i, ks3);           // K^s T3 + M^s T4
   }
   for (int e = threadIdx.x; e < PP * nbd; e += blockDim.x) {
     int pc, r;
@@ -269,8 +269,8 @@ vstiff_last(Dims dims, int axis, int PP, int ldt, BandTab bt, WBandTab wb, const
     vcoords(axis, e, PP, nint, pc, r);
     if (pc >= g.nvalid) continue;
     const int i = bt.ilo + r;
-    const double cpart = t_k<P>(c, t1 + pc * ldt, i) + t_m<P>(c, t2 + pc * ldt, i);
-    const double wpart = w_a<P>(wb.Ksb, t3 + pc * ldt, i) + w_a<P>(wb.Msb, t4 + pc * ldt, i);
+    const double cpart = t_m_acc<P>(c, t2 + pc * ldt, i, t_k<P>(c, t1 + pc * ldt, i));
+    const double wpart = w_a<P>(wb.Msb, t4 + pc * ldt, i, w_a<P>(wb.Ksb, t3 + pc * ldt, i));
     const double v = fma(cc, wpart, cpart);
     const long long off = pbase[pc] + i * g.S;
     out[off] = v;
