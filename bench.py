@@ -626,6 +626,11 @@ def main():
     d2h = [torch.cuda.Event() for _ in range(2)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    for k in range(max(args.warmup, 4)):  # untimed: both buffer pairs seen (the solve graphs captured)
+        b = k & 1
+        f_dev[b].copy_(f_pin)
+        plan.pcg_solve(f_dev[b], u_dev2[b], stream=stream)
+        u_pin[b].copy_(u_dev2[b])
     torch.cuda.synchronize()
     e0.record(stream)
     copy_st.wait_event(e0)
