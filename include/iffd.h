@@ -168,8 +168,10 @@ int iffd_autotune(iffd_handle h, void* ws, void* stream);
  * transformed by the lanes of one warp, register butterflies, fixed tile;
  * opt-in for FP64 plans), 3 = double-float transforms for the whole plan
  * (FP64 IFFD plans whose every direction has a warp-FFT pass of length 64,
- * 128 or 256: FP64-accurate arithmetic on pairs of FP32 values; their
- * default), 4 = the paired FP32 warp-FFT pass (FFT length 64, 128 or 256:
+ * 128 or 256 or a transform run without Bluestein's convolution: the
+ * warp-FFT pass or the block kernel in FP64-accurate arithmetic on pairs of
+ * FP32 values; their default where the passes' tiles fill the GPU),
+ * 4 = the paired FP32 warp-FFT pass (FFT length 64, 128 or 256:
  * every lane group carries two sequences, four pencils, at once; each
  * pencil's values are bitwise those of pipelined 2, and so are the partial
  * sums of the fused dot products; the default for the last direction of
@@ -189,7 +191,8 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
  * and the schedule of its transform passes (*pipelined = 1: persistent
  * pipelined kernel, each CTA loads its next tile asynchronously while it
  * transforms the current one; 2: warp-FFT pass; 3: double-float warp-FFT
- * pass; 4: paired FP32 warp-FFT pass; 0: one tile per CTA). */
+ * pass; 4: paired FP32 warp-FFT pass; 5: double-float block kernel (the
+ * reported tile and radices); 0: one tile per CTA). */
 int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils_stiffness, int* radices,
                    int* nstages, int* pipelined);
 

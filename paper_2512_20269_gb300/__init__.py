@@ -341,7 +341,7 @@ class IFFDPlan:
                                        ctypes.byref(pl)), "iffd_get_tiles")
         return {"pencils_transform": pt.value, "pencils_stiffness": ps.value, "radices": list(rad[:ns.value]),
 
-                "pipelined": pl.value == 1, "warp": pl.value in (2, 3, 4), "double_float": pl.value == 3,
+                "pipelined": pl.value == 1, "warp": pl.value in (2, 3, 4), "double_float": pl.value in (3, 5),
                 "paired": pl.value == 4}
 
     def profile_enable(self, on: bool = True):

@@ -312,6 +312,8 @@ template <>
 const double* var_tw<double>(const FftVar& v) { return v.twd; }
 template <>
 const float* var_tw<float>(const FftVar& v) { return v.twf; }
+template <>
+const df* var_tw<df>(const FftVar& v) { return v.twq; }
 
 // Selects the radix sequence v (whose length must equal t->F).
 template <typename T>
@@ -329,6 +331,7 @@ void set_fft(AxisTab<T>* t, const FftVar& v) {
 }
 template void set_fft<double>(AxisTab<double>*, const FftVar&);
 template void set_fft<float>(AxisTab<float>*, const FftVar&);
+template void set_fft<df>(AxisTab<df>*, const FftVar&);
 
 // Index of the default (first) radix sequence of length len in fvar.
 static int default_var(const std::vector<FftVar>& fv, int len) {
@@ -381,7 +384,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     size_t Mb, Kb, Mt, Kt, QT, Q, lamQ, Msb, Ksb;
     int L, F;                          // DFT length; Bluestein FFT length (0: direct)
     std::vector<FftPlan> vars;         // radix sequences of length L (and F)
-    std::vector<size_t> var_d, var_f;  // their twiddle tables (FP64, FP32)
+    std::vector<size_t> var_d, var_f, var_q;  // their twiddle tables (FP64, FP32, double-float)
     int ilo, ihi;
     size_t wt, wt_d, wt_q;             // warp-FFT twiddles, FP32, FP64 and df (D = {0,1} directions)
   } pa[3];
@@ -403,6 +406,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
         if (!err.empty()) return fail(IFFD_ERR_UNSUPPORTED, err);
         pa[a].var_d.push_back(tb.add_vec(fp.tw));
         pa[a].var_f.push_back(tb.add_vec(cast_vec<float>(fp.tw)));
+        pa[a].var_q.push_back(tb.add_vec(df_vec(fp.tw)));
         pa[a].vars.push_back(std::move(fp));
       }
     }
@@ -524,6 +528,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
       }
       v.twd = reinterpret_cast<const double*>(base + pa[a].var_d[k]);
       v.twf = reinterpret_cast<const float*>(base + pa[a].var_f[k]);
+      v.twq = reinterpret_cast<const df*>(base + pa[a].var_q[k]);
       P->fvar[a].push_back(v);
     }
     // per precision: Bluestein (F > L) or the direct length-L FFT, default
@@ -541,10 +546,10 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     set_fft(&P->axf[a], P->fvar[a][P->vsel_f[a]]);
     P->wtab[a] = reinterpret_cast<const float2*>(base + pa[a].wt);
     P->wtab_d[a] = reinterpret_cast<const double2*>(base + pa[a].wt_d);
-    // double-float tables: the FP64 transform layout (L, F), no block-kernel FFT
+    // double-float tables: the FP64 transform layout (L, F) and its radix
+    // sequence (the block passes of directions without a warp-FFT pass)
     fill_axistab(&P->axq[a], A, P->axd[a].L, P->axd[a].F, base, pa[a].oq);
-    P->axq[a].nst = 0;
-    P->axq[a].tw = nullptr;
+    set_fft(&P->axq[a], P->fvar[a][P->vsel_d[a]]);
     P->wtab_q[a] = reinterpret_cast<const df2*>(base + pa[a].wt_q);
     P->warp_f[a] = 0;
     P->warp_d[a] = 0;
@@ -590,9 +595,9 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     max_parts = std::max(max_parts, stiff_tiles(P->dims, a, kMinTunePP));
   }
   P->max_parts = max_parts;
-  // FP64 plans: the double-float passes by default where every direction has
-  // one and their tiles fill the GPU. Small problems are latency-bound (a few
-  // long CTAs); they take the FP64-pipe block kernel instead, its tile
+  // FP64 plans: the double-float passes by default where every direction can
+  // run one and their tiles fill the GPU. Small problems are latency-bound (a
+  // few long CTAs); they take the FP64-pipe block kernel instead, its tile
   // narrowed (8, 4, 2 pencils) until the tiles fill the GPU or reach 2 pencils
   // (65^2, p = 3: 0.61 against 0.71 ms per solve).
   {
@@ -600,7 +605,7 @@ static int build_plan(Plan* P, cudaStream_t stream) {
     bool fills = true;
     for (int a = 0; a < P->d; ++a) {
       const int wN = wpass_len(P->axq[a]);
-      if (wN == 0 || precond_tiles(P->dims, a, wpass_pencils(wN)) < sms) fills = false;
+      if (precond_tiles(P->dims, a, wN ? wpass_pencils(wN) : P->PPd[a]) < sms) fills = false;
     }
     P->dfq = dfq_eligible(*P) && fills;
     for (int a = 0; a < P->d; ++a)
@@ -697,27 +702,41 @@ PassLaunch<Tc> make_pass(const Plan* P, int axis, const AxisTab<Tc>* tabs, const
   return L;
 }
 
+// Double-float transforms for an FP64 IFFD plan: every direction runs the
+// double-float warp-FFT pass (lengths 64, 128, 256) or the double-float block
+// kernel (any length run without Bluestein's convolution).
+static bool df_warp_dir(const Plan& P, int a) {
+  return wpass_len(P.axq[a]) > 0 && P.dims.N / P.axq[a].m < (1LL << 31);
+}
 int dfq_eligible(const Plan& P) {
   if (P.opt.precision != IFFD_PREC_FP64 || P.opt.precond != IFFD_PRECOND_IFFD) return 0;
   for (int a = 0; a < P.d; ++a)
-    if (wpass_len(P.axq[a]) == 0 || P.dims.N / P.axq[a].m >= (1LL << 31)) return 0;
+    if (!df_warp_dir(P, a) && P.axq[a].blu) return 0;
   return 1;
 }
 
-// A double-float warp pass along direction `axis` (see Plan::dfq).
+// The double-float pass along direction `axis` (see Plan::dfq): the warp-FFT
+// pass, or the block kernel with the FP64 plan's tile (both values take 8 bytes).
 static PassLaunch<df> make_pass_df(const Plan* P, int axis, const int* done) {
   PassLaunch<df> L{};
   L.dims = P->dims;
   L.axis = axis;
-  L.wN = wpass_len(P->axq[axis]);
-  L.PP = wpass_pencils(L.wN);
-  L.ldt = wpass_ldt(L.wN, P->axq[axis].m, walias<df>());
   L.ax = P->axq[axis];
   L.lamA = P->axq[0].lam;
   L.lamB = (P->d == 3) ? P->axq[1].lam : P->axq[0].lam;
   L.done = done;
   L.pipe = 0;
-  L.wt = P->wtab_q[axis];
+  if (df_warp_dir(*P, axis)) {
+    L.wN = wpass_len(P->axq[axis]);
+    L.PP = wpass_pencils(L.wN);
+    L.ldt = wpass_ldt(L.wN, P->axq[axis].m, walias<df>());
+    L.wt = P->wtab_q[axis];
+  } else {
+    L.wN = 0;
+    L.PP = P->PPd[axis];
+    L.ldt = P->ldtd[axis];
+    L.wt = nullptr;
+  }
   return L;
 }
 

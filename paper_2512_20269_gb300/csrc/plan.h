@@ -104,6 +104,7 @@ struct FftVar {
   int radix[kMaxStages], twoff[kMaxStages];
   const double* twd;
   const float* twf;
+  const df* twq;  // double-float copy (the double-float block passes)
 };
 
 // Plan of one problem: host 1D data, device tables, launch geometry.

@@ -213,8 +213,28 @@ int wpass_len(const AxisTab<float>& ax) { return wpass_len_t(ax, 512); }
 int wpass_len(const AxisTab<double>& ax) { return wpass_len_t(ax, 256); }
 int wpass_len(const AxisTab<df>& ax) { return wpass_len_t(ax, 256); }
 
+template <typename Tc, typename Tin, typename Tout, int MODE, int NDOT>
+cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cudaStream_t st);
+
 template <typename Tin, typename Tout>
 cudaError_t launch_pass_df(const PassLaunch<df>& P, int mode, int ndot, const Tin* in, Tout* out, cudaStream_t st) {
+  if (P.wN == 0) {  // the block kernel (the combinations the preconditioner uses)
+    if (P.ax.blu || P.pipe) return cudaErrorInvalidValue;
+    if constexpr (std::is_same<Tin, double>::value) {
+      if (mode != PM_FWD) return cudaErrorInvalidValue;
+      return launch_pass_t<df, double, df, PM_FWD, 0>(P, in, out, st);
+    } else if constexpr (std::is_same<Tout, double>::value) {
+      if (mode != PM_BWD) return cudaErrorInvalidValue;
+      if (ndot == 0) return launch_pass_t<df, df, double, PM_BWD, 0>(P, in, out, st);
+      if (ndot == 1) return launch_pass_t<df, df, double, PM_BWD, 1>(P, in, out, st);
+      return launch_pass_t<df, df, double, PM_BWD, 2>(P, in, out, st);
+    } else {
+      if (ndot != 0) return cudaErrorInvalidValue;
+      if (mode == PM_FWD) return launch_pass_t<df, df, df, PM_FWD, 0>(P, in, out, st);
+      if (mode == PM_FUSED) return launch_pass_t<df, df, df, PM_FUSED, 0>(P, in, out, st);
+      return launch_pass_t<df, df, df, PM_BWD, 0>(P, in, out, st);
+    }
+  }
   if (P.PP != wpass_pencils(P.wN) || P.ldt < wpass_ldt(P.wN, P.ax.m, true)) return cudaErrorInvalidConfiguration;
   switch (P.wN) {
     case 64: return launch_wpass<64, df, Tin, Tout>(P, mode, ndot, in, out, st);
@@ -263,7 +283,7 @@ cudaError_t launch_pass_t(const PassLaunch<Tc>& P, const Tin* in, Tout* out, cud
       default: return cudaErrorInvalidValue;
     }
   }
-  if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value) {
+  if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value && !std::is_same<Tc, df>::value) {
     if (P.pipe) return launch_pipe_t<Tc, MODE, NDOT>(P, in, out, st);
   }
   auto kern = precond_pass<Tc, Tin, Tout, MODE, NDOT>;

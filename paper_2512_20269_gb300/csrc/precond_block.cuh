@@ -221,7 +221,7 @@ __device__ __forceinline__ void load_tile(const Tin* __restrict__ in, Tc* tile, 
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (slot[u] >= 0) tile[slot[u]] = (Tc)v[u];
+        if (slot[u] >= 0) tile[slot[u]] = cvt<Tc>(v[u]);
     }
   }
 }
@@ -257,12 +257,12 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         pc = ax.fnout.div(job);
         k = job - pc * nw;
         const Tc* row = tile + pc * ldt;
-        for (int i = sub; i < ax.wlo; i += 8) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
-        for (int i = ax.whi + sub; i < m; i += 8) acc = fma(__ldg(ax.W + i * nw + k), row[i], acc);
+        for (int i = sub; i < ax.wlo; i += 8) acc = fma(ldg(ax.W + i * nw + k), row[i], acc);
+        for (int i = ax.whi + sub; i < m; i += 8) acc = fma(ldg(ax.W + i * nw + k), row[i], acc);
       }
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += shfl_xor(acc, 4);
+      acc += shfl_xor(acc, 2);
+      acc += shfl_xor(acc, 1);
       if (sub == 0 && job < PP * nw) outv[pc * kMaxNout + k] = acc;
     }
     // pack the regular part of two pencils into one complex sequence
@@ -299,7 +299,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         const Tc Ar = zk.x + zm.x, Ai = zk.y - zm.y;
         const Tc Br = zk.y + zm.y, Bi = zm.x - zk.x;
         const Tc* t4 = ax.post + 4 * k;
-        const Tc A = __ldg(t4), B = __ldg(t4 + 1), C = __ldg(t4 + 2), E = __ldg(t4 + 3);
+        const Tc A = ldg(t4), B = ldg(t4 + 1), C = ldg(t4 + 2), E = ldg(t4 + 3);
         ra[N - 1 - k] = fma(A, Ar, B * Ai);
         rb[N - 1 - k] = fma(A, Br, B * Bi);
         if (k > 0 && 2 * k != N) {
@@ -311,7 +311,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
       for (int w = tid; w < npairs * N; w += blockDim.x) {
         const int pr = ax.fN.div(w), j = w - pr * N;
         Tc ya, yb;
-        gen_im(Z + (size_t)pr * F, ax.gq * (j + 1) - ax.gqe, L, __ldg(ax.post + 2 * j), __ldg(ax.post + 2 * j + 1),
+        gen_im(Z + (size_t)pr * F, ax.gq * (j + 1) - ax.gqe, L, ldg(ax.post + 2 * j), ldg(ax.post + 2 * j + 1),
                ya, yb);
         tile[(2 * pr) * ldt + j] = ya;
         tile[(2 * pr + 1) * ldt + j] = yb;
@@ -320,7 +320,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
       for (int w = tid; w < npairs * N; w += blockDim.x) {
         const int pr = ax.fN.div(w), j = w - pr * N;
         const Cplx<Tc> z = Z[(size_t)pr * F + j + 1];
-        const Tc sc = __ldg(ax.post + j);
+        const Tc sc = ldg(ax.post + j);
         tile[(2 * pr) * ldt + j] = -sc * z.y;
         tile[(2 * pr + 1) * ldt + j] = sc * z.x;
       }
@@ -336,7 +336,16 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
     // divide by the summed eigenvalues of all directions: by a multiply with
     // the precomputed reciprocal (FP64 plans; read in the coalesced order of
     // the tile load), else by a division
-    if (ax.rden != nullptr) {
+    if constexpr (std::is_same<Tc, df>::value) {
+      // double-float: the product with a Newton-refined reciprocal of the sum
+      for (int e = tid; e < PP * m; e += blockDim.x) {
+        const int pc = ax.fm.div(e), i = e - pc * m;
+        if (pc >= g.nvalid) continue;  // padding pencils
+        df den = ldg(lamA + pia[pc]);
+        if (dims.d == 3) den = den + ldg(lamB + pib[pc]);
+        tile[pc * ldt + i] = tile[pc * ldt + i] * recip(ldg(ax.lam + i) + den);
+      }
+    } else if (ax.rden != nullptr) {
       for (int e = tid; e < PP * m; e += blockDim.x) {
         int pc, i;
         if (axis == 0) { pc = ax.fm.div(e); i = e - pc * m; }
@@ -348,8 +357,8 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
       for (int e = tid; e < PP * m; e += blockDim.x) {
         const int pc = ax.fm.div(e), i = e - pc * m;
         if (pc >= g.nvalid) continue;  // padding pencils
-        Tc den = __ldg(ax.lam + i) + __ldg(lamA + pia[pc]);
-        if (dims.d == 3) den += __ldg(lamB + pib[pc]);
+        Tc den = ldg(ax.lam + i) + ldg(lamA + pia[pc]);
+        if (dims.d == 3) den += ldg(lamB + pib[pc]);
         tile[pc * ldt + i] = tile[pc * ldt + i] / den;
       }
     }
@@ -368,7 +377,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         const Tc* za = tile + (2 * pr) * ldt;
         const Tc* zb = za + ldt;
         const Tc* t4 = ax.post + 4 * k;
-        const Tc A = __ldg(t4), B = __ldg(t4 + 1), C = __ldg(t4 + 2), E = __ldg(t4 + 3);
+        const Tc A = ldg(t4), B = ldg(t4 + 1), C = ldg(t4 + 2), E = ldg(t4 + 3);
         Cplx<Tc>* G = bufA + (size_t)pr * F;
         if (k == 0 || 2 * k == N) {
           const Tc s = A + A;
@@ -389,7 +398,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         const Tc* zb = za + ldt;
         Tc va = Tc(0), vb = Tc(0);
         if (l >= 1 && l <= N) {
-          const Tc sc = __ldg(ax.post + 4 * N + l - 1);  // 1 / D~
+          const Tc sc = ldg(ax.post + 4 * N + l - 1);  // 1 / D~
           va = sc * za[l - 1];
           vb = sc * zb[l - 1];
         }
@@ -404,11 +413,11 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         Tc va, vb;
         if (l == 0 || l == n) { va = Tc(0); vb = Tc(0); }
         else if (l < n) {
-          const Tc sc = __ldg(ax.post + l - 1);
+          const Tc sc = ldg(ax.post + l - 1);
           va = sc * za[l - 1];
           vb = sc * zb[l - 1];
         } else {
-          const Tc sc = __ldg(ax.post + 2 * n - 1 - l);
+          const Tc sc = ldg(ax.post + 2 * n - 1 - l);
           va = -sc * za[2 * n - 1 - l];
           vb = -sc * zb[2 * n - 1 - l];
         }
@@ -430,7 +439,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
           return neg_if(isb ? z.y : z.x, j & 1);
         } else if (ax.kind == 2) {
           Tc xa, xb;
-          gen_im(Zp, ax.gq * (j + 1) - ax.gqc, L, __ldg(ax.post + 2 * N + 2 * j), __ldg(ax.post + 2 * N + 2 * j + 1),
+          gen_im(Zp, ax.gq * (j + 1) - ax.gqc, L, ldg(ax.post + 2 * N + 2 * j), ldg(ax.post + 2 * N + 2 * j + 1),
                  xa, xb);
           return isb ? xb : xa;
         } else {
@@ -441,11 +450,11 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
       Tc x;
       if (i < ax.rowsL) {
         x = Tc(0);
-        for (int c = 0; c < ax.nL; ++c) x = fma(__ldg(ax.VL + i * ax.nL + c), wreg(c), x);
+        for (int c = 0; c < ax.nL; ++c) x = fma(ldg(ax.VL + i * ax.nL + c), wreg(c), x);
       } else if (i >= m - ax.rowsR) {
         const int r = m - 1 - i;
         x = Tc(0);
-        for (int c = 0; c < ax.nR; ++c) x = fma(__ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
+        for (int c = 0; c < ax.nR; ++c) x = fma(ldg(ax.VR + r * ax.nR + c), wreg(N - 1 - c), x);
       } else {
         int o = ax.o;
         bool inblk = false;
@@ -457,7 +466,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
             const int c0 = __ldg(B), c1 = __ldg(B + 1);
             const Tc* V = ax.VB + __ldg(B + 5) + (i - r0) * (c1 - c0);
             x = Tc(0);
-            for (int c = c0; c < c1; ++c) x = fma(__ldg(V + (c - c0)), wreg(c), x);
+            for (int c = c0; c < c1; ++c) x = fma(ldg(V + (c - c0)), wreg(c), x);
             inblk = true;
             break;
           }
@@ -466,7 +475,7 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         if (!inblk) x = wreg(i - o);
       }
       if (i < ax.wlo || i >= ax.whi) {
-        for (int k = 0; k < ax.n_out; ++k) x = fma(__ldg(ax.W + i * ax.n_out + k), outv[pc * kMaxNout + k], x);
+        for (int k = 0; k < ax.n_out; ++k) x = fma(ldg(ax.W + i * ax.n_out + k), outv[pc * kMaxNout + k], x);
       }
       tile[pc * ldt + i] = x;
     }
@@ -493,9 +502,10 @@ __device__ __forceinline__ void store_tile(const Tc* tile, Tout* __restrict__ ou
     if (pc < g.nvalid) {
       const long long off = pbase[pc] + i * g.S;
       const Tc v = tile[pc * ldt + i];
-      out[off] = (Tout)v;
-      if (NDOT >= 1) d0 = fma(ldr<CG>(dotv0 + off), (double)(Tout)v, d0);
-      if (NDOT >= 2) d1 = fma(ldr<CG>(dotv1 + off), (double)(Tout)v, d1);
+      const Tout vo = cvt<Tout>(v);
+      out[off] = vo;
+      if (NDOT >= 1) d0 = fma(ldr<CG>(dotv0 + off), cvt<double>(vo), d0);
+      if (NDOT >= 2) d1 = fma(ldr<CG>(dotv1 + off), cvt<double>(vo), d1);
     }
   }
   if (NDOT >= 1) {

@@ -302,11 +302,11 @@ int iffd_set_geometry(iffd_handle h, int axis, int pencils_transform, int pencil
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
   auto pow2 = [](int v) { return v >= kMinTunePP && v <= 32 && (v & (v - 1)) == 0; };
   if (pipelined == 3) {
-    // double-float transforms for the whole plan (FP64 IFFD plans whose every
-    // direction has a warp-FFT pass of length 64, 128 or 256)
+    // double-float transforms for the whole plan (FP64 IFFD plans; every
+    // direction by the warp-FFT pass or the block kernel without Bluestein)
     if (!f64 || !dfq_eligible(P))
-      return fail(IFFD_ERR_UNSUPPORTED, "double-float transforms need an FP64 IFFD plan whose every direction has "
-                                        "D = {0,1} and a warp-FFT length of 64, 128 or 256");
+      return fail(IFFD_ERR_UNSUPPORTED, "double-float transforms need an FP64 IFFD plan whose every direction runs "
+                                        "its transform without Bluestein's convolution");
     if (pencils_transform > 0) return fail(IFFD_ERR_INVALID_ARG, "the double-float pass has a fixed tile");
     P.dfq = 1;
     pipelined = -1;
@@ -365,6 +365,16 @@ int iffd_get_tiles(iffd_handle h, int axis, int* pencils_transform, int* pencils
   if (!h || axis < 0 || axis >= h->P.d) return fail(IFFD_ERR_INVALID_ARG, "bad handle or axis");
   const Plan& P = h->P;
   const bool f64 = P.opt.precision == IFFD_PREC_FP64;
+  if (f64 && P.dfq && wpass_len(P.axq[axis]) == 0) {  // double-float block pass: the FP64 tile and radices
+    if (pencils_transform) *pencils_transform = P.PPd[axis];
+    if (pencils_stiffness)
+      *pencils_stiffness = (P.opt.coef == IFFD_COEF_SEPARABLE_SIN) ? P.PPv[axis] : P.PPs[axis];
+    if (nstages) *nstages = P.axq[axis].nst;
+    if (radices)
+      for (int s = 0; s < P.axq[axis].nst; ++s) radices[s] = P.axq[axis].radix[s];
+    if (pipelined) *pipelined = 5;
+    return IFFD_OK;
+  }
   if (f64 && P.dfq) {  // double-float warp pass: fixed tile and radices 8, 8, then 4 or 2
     const int N = wpass_len(P.axq[axis]);
     if (pencils_transform) *pencils_transform = wpass_pencils(N);

@@ -27,6 +27,12 @@ SHAPES = [
     (2, 256, 8),     # length 256, p = 8
     (3, 128, 2),     # p = 2: no remainder space
     (2, 128, 3),     # DST-I, length 256
+    # no warp-FFT length: the double-float block kernel
+    (3, 96, 4),      # DST-II/III, length 96 = 2^5 3
+    (2, 96, 3),      # DST-I, length 192
+    (3, 40, 6),      # length 40 = 2^3 5, n_out = 4
+    (2, 80, 5),      # DST-I, length 160
+    (3, 48, 4),      # length 48
 ]
 
 
@@ -66,6 +72,25 @@ def test_double_float_unequal_directions_and_ragged_tiles():
     z = plan.apply_preconditioner(_gpu(torch, r)).cpu().numpy()
     zo = operators.iffd_apply(r, [oracle_split(n, 4) for n in ns])
     assert rel_max_err(z, zo) <= 1e-12
+
+
+def test_double_float_warp_and_block_directions():
+    """One plan whose directions mix the warp-FFT pass (length 64, 128) and
+    the block kernel (length 96): the FP64 tolerance, and PCG."""
+    torch = require_gpu()
+    from oracle import operators
+    from paper_2512_20269_gb300 import IFFDPlan
+    ns = (64, 96, 128)
+    plan = IFFDPlan(3, list(ns), 4).set_geometry(0, double_float=True)
+    assert all(plan.tiles(a)["double_float"] for a in range(3))
+    assert 3 in plan.tiles(1)["radices"]  # the block kernel's radix sequence
+    r = inputs.rhs(plan.shape, "normal", seed=840)
+    z = plan.apply_preconditioner(_gpu(torch, r)).cpu().numpy()
+    zo = operators.iffd_apply(r, [oracle_split(n, 4) for n in ns])
+    assert rel_max_err(z, zo) <= 1e-12
+    f = inputs.rhs(plan.shape, "uniform", seed=841)
+    _, info = plan.pcg_solve(_gpu(torch, f))
+    assert info["status"] == 0 and info["true_rel_res"] <= 1.1e-8
 
 
 @pytest.mark.parametrize("scale", [1e-25, 1e25, 0.0])
@@ -112,12 +137,14 @@ def test_double_float_switch():
     assert all(plan.tiles(a)["double_float"] for a in range(3))
     t = plan.tiles(2)
     assert t["pencils_transform"] == 64 and t["radices"] == [8, 8]
+    IFFDPlan(3, 40, 4).set_geometry(0, double_float=True)        # length 40: the double-float block kernel
     with pytest.raises(IFFDError):
-        IFFDPlan(3, 40, 4).set_geometry(0, double_float=True)     # length 40: no warp pass
+        IFFDPlan(2, 67, 4).set_geometry(0, double_float=True)     # length 67 (prime): Bluestein, FP64 only
     with pytest.raises(IFFDError):
         IFFDPlan(3, 64, 4, precision="fp32").set_geometry(0, double_float=True)
     assert not any(IFFDPlan(3, 64, 4, precision="fp32").tiles(a)["double_float"] for a in range(3))
-    assert not IFFDPlan(3, 96, 4).tiles(0)["double_float"]       # length 96: FP64 block kernel
+    t96 = IFFDPlan(3, 96, 4).tiles(0)                              # length 96: double-float block kernel
+    assert t96["double_float"] and 3 in t96["radices"]
     # the default: double-float where the warp tiles fill the GPU (130^3: 16,900 / 32 pencils
     # per tile >= SMs), the FP64 block kernel with narrowed tiles on small grids
     assert all(IFFDPlan(3, 128, 4).tiles(a)["double_float"] for a in range(3))

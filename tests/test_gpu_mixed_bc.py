@@ -72,6 +72,17 @@ def test_mixed_preconditioner_and_stiffness_parity(d, n, p, dirichlet):
     assert rel_max_err(plan.apply_stiffness(rg).cpu().numpy(), Ao) <= 1e-13
     z32 = IFFDPlan(d, n, p, precision="fp32", dirichlet=dirichlet).apply_preconditioner(rg).cpu().numpy()
     assert np.linalg.norm(z32 - zo) <= 1e-5 * np.linalg.norm(zo)
+    # double-float transforms (the block kernel in pairs of FP32 values) where
+    # no direction needs Bluestein's convolution: the FP64 tolerance
+    from paper_2512_20269_gb300 import IFFDError
+    dfp = IFFDPlan(d, n, p, dirichlet=dirichlet)
+    try:
+        dfp.set_geometry(0, double_float=True)
+    except IFFDError:
+        assert n == 37  # the Bluestein length
+        return
+    zq = dfp.apply_preconditioner(rg).cpu().numpy()
+    assert rel_max_err(zq, zo) <= 1e-12
 
 
 @pytest.mark.parametrize("d,n,p,dirichlet", [(2, 16, 3, ((1, 0), (0, 0))), (3, 9, 4, ((1, 0), (0, 1), (0, 0)))])
