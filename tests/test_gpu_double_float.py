@@ -33,6 +33,8 @@ SHAPES = [
     (3, 40, 6),      # length 40 = 2^3 5, n_out = 4
     (2, 80, 5),      # DST-I, length 160
     (3, 48, 4),      # length 48
+    (2, 56, 4),      # length 56 = 8 7: a direct-DFT stage of radix 7
+    (2, 100, 6),     # length 100 = 4 25: radix-5 stages
 ]
 
 

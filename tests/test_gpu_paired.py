@@ -92,3 +92,26 @@ def test_paired_dot_partials_with_a_ragged_half_tile():
     us, is_ = single.pcg_solve(f)
     assert ip["iters"] == is_["iters"] and torch.equal(up, us)
 
+
+
+def test_paired_passes_in_the_batched_solve():
+    """iffd_batch_solve runs the plans' own geometry through the engine's
+    batched launches: with every direction paired (the last backward pass then
+    forms its dot products per half tile in the batched kernel too), every
+    solution equals the stand-alone paired solve bit for bit."""
+    torch = require_gpu()
+    from paper_2512_20269_gb300 import batch_solve
+    plans, fs = [], []
+    for k, (d, ns, p) in enumerate([(3, (64, 64, 64), 4), (2, (128, 256), 3), (3, (128, 64, 64), 6)]):
+        paired, _ = _plans(d, ns, p, None)
+        plans.append(paired)
+        fs.append(torch.from_numpy(np.stack([inputs.rhs(paired.shape, "normal", seed=2000 + 10 * k + j)
+                                              for j in range(2)])).cuda())
+    us, infos = batch_solve(plans, fs)
+    slot = 0
+    for k, pl in enumerate(plans):
+        for j in range(2):
+            ua, ia = pl.pcg_solve(fs[k][j].contiguous())
+            assert infos[slot]["status"] == 0 and infos[slot]["iters"] == ia["iters"]
+            assert torch.equal(us[k][j], ua), (k, j)
+            slot += 1
