@@ -1229,6 +1229,7 @@ static const Plan::SolveGraph* solve_graphs_for(const Plan* P, const double* f, 
   for (auto& g : G.g)
     if (g.first && g.next && g.f == f && g.u == u && g.ws == ws) {
       g.used = now;
+      ++g.replays;
       return &g;
     }
   bool seen = false;
@@ -1241,6 +1242,11 @@ static const Plan::SolveGraph* solve_graphs_for(const Plan* P, const double* f, 
   G.seen_ws[0] = ws;
   if (!seen) return nullptr;
   Plan::SolveGraph& slot = G.g[0].used <= G.g[1].used ? G.g[0] : G.g[1];
+  if (slot.first && slot.replays == 0) {  // captures that are evicted unused: the caller's pattern
+    drop_graphs(G);                       // does not repeat, launch directly from now on
+    G.failed = true;
+    return nullptr;
+  }
   if (capture_solve_graphs(P, slot, f, u, ws, chunk)) {  // not capturable here: direct launches for good
     drop_graphs(G);
     G.failed = true;

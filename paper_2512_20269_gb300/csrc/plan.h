@@ -181,6 +181,7 @@ struct Plan {
     cudaGraphExec_t first = nullptr, next = nullptr;
     long long kfirst = 0, knext = 0;  // kernels per replay
     unsigned long long used = 0;      // last use (replacement order)
+    long long replays = 0;            // launches after the capture
   };
   struct SolveGraphs {
     cudaStream_t cap = nullptr;  // private capture stream
