@@ -92,6 +92,19 @@ __device__ __forceinline__ To cvt(From v) {
   return Cvt<To>::from(v);
 }
 
+// a * b + c * d: a fused multiply-add onto a product (double-float: one sum of
+// the two exact products, dfloat.cuh)
+template <typename S, typename T>
+__device__ __forceinline__ T dot2(S a, T b, S c, T d) {
+  return fma(a, b, c * d);
+}
+
+// a * w for double-float values, through dot2 (the generic cmul's operations
+// for float and double)
+__device__ __forceinline__ Cplx<df> cmul(Cplx<df> a, Cplx<df> w) {
+  return {dot2(a.x, w.x, -a.y, w.y), dot2(a.x, w.y, a.y, w.x)};
+}
+
 // Quotient of a non-negative n < 2^31 by an invariant divisor d >= 1 through
 // one 64-bit multiply and a shift -- division by invariant integers using
 // multiplication (Granlund and Montgomery, PLDI 1994). With l = ceil(log2 d),

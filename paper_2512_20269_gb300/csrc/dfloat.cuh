@@ -97,6 +97,23 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
 // the float / double overloads stay visible next to the df one inside the namespace
 using ::fma;
 
+// a * b + c * d with one sum of the two exact high products: their errors
+// and cross terms join the low part, left unnormalised as in the sum (the
+// next product renormalises). 16 instructions against 22 for a product and a
+// fused multiply-add; the error stays near 2^-47 of |a b| + |c d|.
+__device__ __forceinline__ df dot2(df a, df b, df c, df d) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  e1 = __fmaf_rn(a.hi, b.lo, e1);
+  e1 = __fmaf_rn(a.lo, b.hi, e1);
+  const float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  e2 = __fmaf_rn(c.hi, d.lo, e2);
+  e2 = __fmaf_rn(c.lo, d.hi, e2);
+  const df s = two_sum(p1, p2);
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2))};
+}
+
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 
 // 1 / b: the float reciprocal refined by one Newton step x + x (1 - b x)

@@ -179,8 +179,8 @@ __device__ __forceinline__ void gen_im(const Cplx<T>* Zp, int k, int L, T fx, T 
   const Cplx<T> z1 = Zp[k == 0 ? 0 : L - k], z2 = Zp[k];
   const T tax = z1.x + z2.x, tay = z1.y - z2.y;  // 2 T_a(k)
   const T tbx = z1.y + z2.y, tby = z2.x - z1.x;  // 2 T_b(k)
-  ya = fma(fx, tay, fy * tax);
-  yb = fma(fx, tby, fy * tbx);
+  ya = dot2(fx, tay, fy, tax);
+  yb = dot2(fx, tby, fy, tbx);
 }
 
 
@@ -300,11 +300,11 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
         const Tc Br = zk.y + zm.y, Bi = zm.x - zk.x;
         const Tc* t4 = ax.post + 4 * k;
         const Tc A = ldg(t4), B = ldg(t4 + 1), C = ldg(t4 + 2), E = ldg(t4 + 3);
-        ra[N - 1 - k] = fma(A, Ar, B * Ai);
-        rb[N - 1 - k] = fma(A, Br, B * Bi);
+        ra[N - 1 - k] = dot2(A, Ar, B, Ai);
+        rb[N - 1 - k] = dot2(A, Br, B, Bi);
         if (k > 0 && 2 * k != N) {
-          ra[k - 1] = fma(C, Ar, -E * Ai);
-          rb[k - 1] = fma(C, Br, -E * Bi);
+          ra[k - 1] = dot2(C, Ar, -E, Ai);
+          rb[k - 1] = dot2(C, Br, -E, Bi);
         }
       }
     } else if (ax.kind == 2) {
@@ -383,10 +383,10 @@ __device__ __forceinline__ void compute_tile(Tc* tile, Cplx<Tc>* bufA, Cplx<Tc>*
           const Tc s = A + A;
           G[k] = {s * za[N - 1 - k], s * zb[N - 1 - k]};
         } else {
-          const Tc ar = fma(A, za[N - 1 - k], C * za[k - 1]);
-          const Tc ai = fma(-B, za[N - 1 - k], E * za[k - 1]);
-          const Tc br = fma(A, zb[N - 1 - k], C * zb[k - 1]);
-          const Tc bi = fma(-B, zb[N - 1 - k], E * zb[k - 1]);
+          const Tc ar = dot2(A, za[N - 1 - k], C, za[k - 1]);
+          const Tc ai = dot2(-B, za[N - 1 - k], E, za[k - 1]);
+          const Tc br = dot2(A, zb[N - 1 - k], C, zb[k - 1]);
+          const Tc bi = dot2(-B, zb[N - 1 - k], E, zb[k - 1]);
           G[k] = {ar - bi, ai + br};
           G[N - k] = {ar + bi, br - ai};
         }

@@ -402,10 +402,10 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
             const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
             const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
             const Post4<TT> t = ldpost(ax.post, k);
-            o1a[u] = fma(t.x, Ar, t.y * Ai);
-            o1b[u] = fma(t.x, Br, t.y * Bi);
-            o2a[u] = fma(t.z, Ar, -t.w * Ai);
-            o2b[u] = fma(t.z, Br, -t.w * Bi);
+            o1a[u] = dot2(t.x, Ar, t.y, Ai);
+            o1b[u] = dot2(t.x, Br, t.y, Bi);
+            o2a[u] = dot2(t.z, Ar, -t.w, Ai);
+            o2b[u] = dot2(t.z, Br, -t.w, Bi);
                     }
         }
         __syncwarp();
@@ -419,11 +419,11 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
           const T Ar = zk.x + zm.x, Ai = zk.y - zm.y;
           const T Br = zk.y + zm.y, Bi = zm.x - zk.x;
           const Post4<TT> t = ldpost(ax.post, k);
-          ra[N - 1 - k] = fma(t.x, Ar, t.y * Ai);
-          rb[N - 1 - k] = fma(t.x, Br, t.y * Bi);
+          ra[N - 1 - k] = dot2(t.x, Ar, t.y, Ai);
+          rb[N - 1 - k] = dot2(t.x, Br, t.y, Bi);
           if (k > 0 && 2 * k != N) {
-            ra[k - 1] = fma(t.z, Ar, -t.w * Ai);
-            rb[k - 1] = fma(t.z, Br, -t.w * Bi);
+            ra[k - 1] = dot2(t.z, Ar, -t.w, Ai);
+            rb[k - 1] = dot2(t.z, Br, -t.w, Bi);
           }
         }
       }
@@ -531,10 +531,10 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
               const TT s = t.x + t.x;
               g1[u] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
             } else {
-              const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
-              const T ai = fma(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
-              const T br = fma(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
-              const T bi = fma(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+              const T ar = dot2(t.x, ra[N - 1 - k], t.z, ra[k - 1]);
+              const T ai = dot2(-t.y, ra[N - 1 - k], t.w, ra[k - 1]);
+              const T br = dot2(t.x, rb[N - 1 - k], t.z, rb[k - 1]);
+              const T bi = dot2(-t.y, rb[N - 1 - k], t.w, rb[k - 1]);
               g1[u] = vec2_t<T>{ar - bi, ai + br};
               g2[u] = vec2_t<T>{ar + bi, br - ai};
             }
@@ -551,10 +551,10 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
             const TT s = t.x + t.x;
             buf[wpad(k)] = vec2_t<T>{s * ra[N - 1 - k], s * rb[N - 1 - k]};
           } else {
-            const T ar = fma(t.x, ra[N - 1 - k], t.z * ra[k - 1]);
-            const T ai = fma(-t.y, ra[N - 1 - k], t.w * ra[k - 1]);
-            const T br = fma(t.x, rb[N - 1 - k], t.z * rb[k - 1]);
-            const T bi = fma(-t.y, rb[N - 1 - k], t.w * rb[k - 1]);
+            const T ar = dot2(t.x, ra[N - 1 - k], t.z, ra[k - 1]);
+            const T ai = dot2(-t.y, ra[N - 1 - k], t.w, ra[k - 1]);
+            const T br = dot2(t.x, rb[N - 1 - k], t.z, rb[k - 1]);
+            const T bi = dot2(-t.y, rb[N - 1 - k], t.w, rb[k - 1]);
             buf[wpad(k)] = vec2_t<T>{ar - bi, ai + br};
             buf[wpad(N - k)] = vec2_t<T>{ar + bi, br - ai};
           }
