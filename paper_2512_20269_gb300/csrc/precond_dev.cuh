@@ -3,6 +3,8 @@
 // gather of one pencil, a warp sum.
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace iffd {
@@ -31,6 +33,21 @@ __device__ __forceinline__ void dft4(Cplx<T>* v) {
   v[3] = csub(t1, mul_mi(t3));
 }
 
+// plus = e + r s and minus = e - r s: two fused multiply-adds (float,
+// double); for double-float one product and two sums (23 instead of 30
+// FP32 instructions)
+template <typename T>
+__device__ __forceinline__ void pm_fma(T r, T s, T e, T& plus, T& minus) {
+  if constexpr (std::is_same<T, df>::value) {
+    const T t = r * s;
+    plus = e + t;
+    minus = e - t;
+  } else {
+    plus = fma(r, s, e);
+    minus = fma(-r, s, e);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void dft8(Cplx<T>* v) {
   const T r = T(0.70710678118654752440084436210484903928);
@@ -45,12 +62,12 @@ __device__ __forceinline__ void dft8(Cplx<T>* v) {
   const Cplx<T> o2 = mul_mi(o[2]);
   v[0] = cadd(e[0], o[0]);
   v[4] = csub(e[0], o[0]);
-  v[1] = {fma(r, s1x, e[1].x), fma(r, s1y, e[1].y)};
-  v[5] = {fma(-r, s1x, e[1].x), fma(-r, s1y, e[1].y)};
+  pm_fma(r, s1x, e[1].x, v[1].x, v[5].x);
+  pm_fma(r, s1y, e[1].y, v[1].y, v[5].y);
   v[2] = cadd(e[2], o2);
   v[6] = csub(e[2], o2);
-  v[3] = {fma(r, s3x, e[3].x), fma(-r, s3y, e[3].y)};
-  v[7] = {fma(-r, s3x, e[3].x), fma(r, s3y, e[3].y)};
+  pm_fma(r, s3x, e[3].x, v[3].x, v[7].x);
+  pm_fma(r, s3y, e[3].y, v[7].y, v[3].y);
 }
 
 // y_reg[i] = (V_reg^T r)_i for the pencil held in row[0..m-1] (row values of
