@@ -47,7 +47,7 @@ UNIT = "DoF/s"
 _CSRC = "paper_2512_20269_gb300/csrc/"
 # source files whose kernels a traffic record (profiles/ncu_traffic.txt) covers
 SRC_FILES = {"precond": [_CSRC + f for f in ("precond.cu", "precond_block.cuh", "device_common.cuh")],
-             "precond_df": [_CSRC + f for f in ("precond_warp.cuh", "dfloat.cuh", "device_common.cuh")],
+             "precond_df": [_CSRC + f for f in ("precond_warp.cuh", "precond_dev.cuh", "dfloat.cuh", "device_common.cuh")],
              "stiff": [_CSRC + f for f in ("stiffness.cu", "stiff_dev.cuh", "device_common.cuh")],
              "pcg": [_CSRC + f for f in ("pcg.cu", "pcg_dev.cuh", "device_common.cuh")]}
 
@@ -574,9 +574,10 @@ def main():
     rooflines = {}
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # Launches that did work: iterations are enqueued in chunks of 4 and the
-    # surplus launches after convergence return at their first instruction, so
-    # per-launch rates use the launches of the executed iterations only.
+    # Launches that did work: iterations are enqueued in chunks (the first as
+    # long as the plan's previous solve, then 4); launches enqueued past
+    # convergence return at their first instruction, so per-launch rates use
+    # the launches of the executed iterations only.
     # preconditioner applies that did work: the initial one and one per
     # iteration except the last (its residual met the tolerance, so its apply
     # exits at once)
@@ -613,15 +614,16 @@ def main():
                 "peak_source": (peak_src if d["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (measured copy)")}
 
     # ---------------- end to end: pinned host f -> device, solve, u -> host.
-    # Every step copies its f in and its u out; the copies run on a second
-    # stream (the copy engines), double-buffered, so that step k+1's input and
-    # step k-1's output move while step k solves: the timed region is the
-    # first input copy, the K solves and the last output copy.
+    # Every step copies its f in and its u out; the copies run on two more
+    # streams (one per direction, so that the two copy engines work at once),
+    # double-buffered, so that step k+1's input and step k-1's output move
+    # while step k solves: the timed region is the first input copy, the K
+    # solves and the last output copy.
     f_pin = f_host.pin_memory()
     u_pin = [torch.empty_like(f_pin).pin_memory() for _ in range(2)]
     f_dev = [torch.empty_like(f) for _ in range(2)]
     u_dev2 = [plan.empty() for _ in range(2)]
-    copy_st = torch.cuda.Stream()
+    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
     h2d = [torch.cuda.Event() for _ in range(2)]
     d2h = [torch.cuda.Event() for _ in range(2)]
     e0 = torch.cuda.Event(enable_timing=True)
@@ -633,34 +635,34 @@ def main():
         u_pin[b].copy_(u_dev2[b])
     torch.cuda.synchronize()
     e0.record(stream)
-    copy_st.wait_event(e0)
-    with torch.cuda.stream(copy_st):
+    copy_in.wait_event(e0)
+    with torch.cuda.stream(copy_in):
         f_dev[0].copy_(f_pin, non_blocking=True)
-        h2d[0].record(copy_st)
+        h2d[0].record(copy_in)
     for k in range(args.steps):
         b = k & 1
         if k + 1 < args.steps:  # the next step's input (its buffer's last solve has returned)
-            with torch.cuda.stream(copy_st):
+            with torch.cuda.stream(copy_in):
                 f_dev[b ^ 1].copy_(f_pin, non_blocking=True)
-                h2d[b ^ 1].record(copy_st)
+                h2d[b ^ 1].record(copy_in)
         stream.wait_event(h2d[b])
         if k >= 2:
             stream.wait_event(d2h[b])  # u_dev2[b] copied out (step k-2)
         plan.pcg_solve(f_dev[b], u_dev2[b], stream=stream)  # returns when the solve is done
         solved = torch.cuda.Event()
         solved.record(stream)
-        copy_st.wait_event(solved)
-        with torch.cuda.stream(copy_st):
+        copy_out.wait_event(solved)
+        with torch.cuda.stream(copy_out):
             u_pin[b].copy_(u_dev2[b], non_blocking=True)
-            d2h[b].record(copy_st)
-    e1.record(copy_st)
+            d2h[b].record(copy_out)
+    e1.record(copy_out)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
     u_dev = u_dev2[(args.steps - 1) & 1]
     assert torch.equal(u_pin[(args.steps - 1) & 1], u_dev.cpu())
     e2e = {"value": w.N * args.steps * world / (ms_e2e / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin[0].numel() * 8),
-           "copies": "pinned host, on a second stream overlapping the neighbouring steps' solves"}
+           "copies": "pinned host, one stream per direction, overlapping the neighbouring steps' solves"}
 
     # ---------------- accuracy of the timed solve's iterate (true residual)
     plan_chk = IFFDPlan(w.d, w.n, w.p, precision="fp64", precond="iffd", true_residual=True).autotune()

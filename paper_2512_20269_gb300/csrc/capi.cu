@@ -1105,8 +1105,7 @@ static int enqueue_start(const Plan* P, const double* f, double* u, void* ws, cu
   const double tol2 = P->opt.rtol * P->opt.rtol;
   const int maxit = P->opt.maxit;
   int np = 0;
-  IFFD_CUDA(cudaMemsetAsync(S, 0, sizeof(SolveState), st));
-  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st));
+  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st, S));
   IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, vec_grid(N), FP_FF, tol2, maxit, st));
   const int rc = run_precond(P, r, z, ws, st, &S->done, 1, r, nullptr, part, &np);
   if (rc) return rc;
@@ -1185,9 +1184,9 @@ static int capture_graph(const Plan* P, Fn enqueue, cudaGraphExec_t* exec, long 
 }
 
 // The two graphs of a solve on (f, u, ws), into slot g: the opening launches
-// with the first `chunk` iterations, and `chunk` later iterations.
+// with the first `nfirst` iterations, and `chunk` later iterations.
 static int capture_solve_graphs(const Plan* P, Plan::SolveGraph& g, const double* f, double* u, void* ws,
-                                int chunk) {
+                                int nfirst, int chunk) {
   Plan::SolveGraphs& G = P->graphs;
   drop_graph(g);
   if (!G.cap) {
@@ -1201,7 +1200,7 @@ static int capture_solve_graphs(const Plan* P, Plan::SolveGraph& g, const double
       P,
       [&](cudaStream_t cs) {
         int r = enqueue_start(P, f, u, ws, cs);
-        for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, c);
+        for (int c = 0; c < nfirst && !r; ++c) r = enqueue_iteration(P, u, ws, cs, c);
         return r;
       },
       &g.first, &g.kfirst);
@@ -1210,7 +1209,7 @@ static int capture_solve_graphs(const Plan* P, Plan::SolveGraph& g, const double
       P,
       [&](cudaStream_t cs) {
         int r = IFFD_OK;
-        for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, chunk + c);
+        for (int c = 0; c < chunk && !r; ++c) r = enqueue_iteration(P, u, ws, cs, nfirst + c);
         return r;
       },
       &g.next, &g.knext);
@@ -1218,16 +1217,29 @@ static int capture_solve_graphs(const Plan* P, Plan::SolveGraph& g, const double
   g.f = f;
   g.u = u;
   g.ws = ws;
+  g.nfirst = nfirst;
   return IFFD_OK;
 }
 
-// The graph set for a solve on (f, u, ws), captured if this triple was one of
-// the last two solves' (nullptr: launch directly).
-static const Plan::SolveGraph* solve_graphs_for(const Plan* P, const double* f, double* u, void* ws, int chunk) {
+// The graph set for a solve on (f, u, ws) whose first graph runs `nfirst`
+// iterations, captured if this triple was one of the last two solves'
+// (nullptr: launch directly).
+static const Plan::SolveGraph* solve_graphs_for(const Plan* P, const double* f, double* u, void* ws, int nfirst,
+                                                int chunk) {
   Plan::SolveGraphs& G = P->graphs;
   const unsigned long long now = ++G.tick;
   for (auto& g : G.g)
     if (g.first && g.next && g.f == f && g.u == u && g.ws == ws) {
+      if (g.nfirst != nfirst) {  // the iteration count moved: capture again, same slot
+        const long long replays = g.replays;
+        if (capture_solve_graphs(P, g, f, u, ws, nfirst, chunk)) {
+          drop_graphs(G);
+          G.failed = true;
+          g_err.clear();
+          return nullptr;
+        }
+        g.replays = replays;
+      }
       g.used = now;
       ++g.replays;
       return &g;
@@ -1247,7 +1259,7 @@ static const Plan::SolveGraph* solve_graphs_for(const Plan* P, const double* f, 
     G.failed = true;
     return nullptr;
   }
-  if (capture_solve_graphs(P, slot, f, u, ws, chunk)) {  // not capturable here: direct launches for good
+  if (capture_solve_graphs(P, slot, f, u, ws, nfirst, chunk)) {  // not capturable here: direct launches for good
     drop_graphs(G);
     G.failed = true;
     g_err.clear();
@@ -1433,12 +1445,17 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   const double tol2 = P->opt.rtol * P->opt.rtol;
   const int maxit = P->opt.maxit;
   const int chunk = 4;  // iterations enqueued between two reads of the solve state
+  // The first chunk runs as many iterations as the plan's last converged
+  // solve took, so that a repeated solve of the same kind reads its state
+  // once and enqueues no iterations past its convergence (each of which
+  // would launch a dozen kernels that exit at once).
+  const int nfirst = std::min(maxit, P->last_iters > 0 ? P->last_iters : chunk);
 
   // Chunks run from captured CUDA graphs when they can (one launch per chunk
   // instead of ~50): not while per-launch event timing is on, and only for
   // the (f, u, workspace) they were captured with.
   const Plan::SolveGraph* graph = nullptr;
-  if (!P->prof.on && !P->graphs.failed && maxit >= chunk) graph = solve_graphs_for(P, f, u, ws, chunk);
+  if (!P->prof.on && !P->graphs.failed && maxit >= chunk) graph = solve_graphs_for(P, f, u, ws, nfirst, chunk);
   auto read_state = [&]() -> int {
     IFFD_CUDA(cudaMemcpyAsync(P->host_state, S, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
     IFFD_CUDA(cudaStreamSynchronize(st));
@@ -1449,7 +1466,7 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   if (graph) {
     IFFD_CUDA(cudaGraphLaunch(graph->first, st));
     P->prof.launches += graph->kfirst;
-    it = chunk;
+    it = graph->nfirst;
     if ((rc = read_state())) return rc;
     finished = P->host_state->done || it >= maxit;
     while (!finished) {
@@ -1467,13 +1484,15 @@ int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* st
   } else {
     if ((rc = enqueue_start(P, f, u, ws, st))) return rc;
     while (!finished) {
-      for (int c = 0; c < chunk && it < maxit; ++c, ++it)
+      const int n = it == 0 ? nfirst : chunk;
+      for (int c = 0; c < n && it < maxit; ++c, ++it)
         if ((rc = enqueue_iteration(P, u, ws, st, it))) return rc;
       if ((rc = read_state())) return rc;
       finished = P->host_state->done || it >= maxit;
     }
   }
   SolveState hs = *P->host_state;
+  if (hs.done && hs.status == IFFD_OK && hs.iters > 0) P->last_iters = hs.iters;
   double true_rel = -1.0;
   if (P->opt.true_residual && hs.ff > 0.0) {
     rc = run_stiffness(P, u, nullptr, nullptr, nullptr, 0, q, ws, st, nullptr, nullptr, nullptr, nullptr);
@@ -1606,8 +1625,7 @@ int iffd_pcg_solve_general(iffd_handle h, const double* C, int ncomp, const doub
   const int g = vec_grid(N);
   int np = 0;
 
-  IFFD_CUDA(cudaMemsetAsync(S, 0, sizeof(SolveState), st));
-  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st));
+  IFFD_LAUNCH(P, IFFD_K_PCG_INIT, st, launch_pcg_init(f, u, r, N, part, st, S));
   IFFD_LAUNCH(P, IFFD_K_FINALIZE, st, launch_finalize(S, part, g, FP_FF, tol2, maxit, st));
   rc = run_precond(P, r, z, ws, st, done, 1, r, nullptr, part, &np);
   if (rc) return rc;

@@ -176,7 +176,9 @@ cudaError_t launch_vstiff_last(const StiffLaunch& S, const WBandTab& wb, const d
 
 // ---------------------------------------------------------------- PCG vectors
 int vec_grid(long long N);
-cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st);
+// x = 0, r = f, partial ||f||^2; a non-null state is reset to zero first.
+cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st,
+                            SolveState* state = nullptr);
 cudaError_t launch_pcg_update(double* x, double* r, const double* p, const double* q, const SolveState* s,
                               long long N, double* partial, const int* done, cudaStream_t st);
 // phase-specific reduction of `nparts` partial sums into the solve state

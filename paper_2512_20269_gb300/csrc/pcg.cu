@@ -22,7 +22,10 @@ int vec_grid(long long N) {
 
 __global__ void __launch_bounds__(kThreads)
 pcg_init(const double* __restrict__ f, double* __restrict__ x, double* __restrict__ r, long long N,
-         double* __restrict__ partial) {
+         double* __restrict__ partial, SolveState* __restrict__ state) {
+  // the solve state starts from zero (a kernel store rather than a memset
+  // node, which in a captured graph can queue behind the caller's copies)
+  if (state != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *state = SolveState{};
   init_body(f, x, r, N, partial, blockIdx.x, gridDim.x);
 }
 
@@ -104,8 +107,9 @@ finalize_batched(const FinDesc* __restrict__ sys, int phase, double tol2, int ma
   finalize_body(d.st, d.partial, d.nparts, phase, tol2, maxit);
 }
 
-cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st) {
-  pcg_init<<<vec_grid(N), kThreads, 0, st>>>(f, x, r, N, partial);
+cudaError_t launch_pcg_init(const double* f, double* x, double* r, long long N, double* partial, cudaStream_t st,
+                            SolveState* state) {
+  pcg_init<<<vec_grid(N), kThreads, 0, st>>>(f, x, r, N, partial, state);
   return cudaGetLastError();
 }
 

@@ -179,6 +179,7 @@ struct Plan {
     double* u = nullptr;
     void* ws = nullptr;
     cudaGraphExec_t first = nullptr, next = nullptr;
+    int nfirst = 0;                   // iterations in `first`
     long long kfirst = 0, knext = 0;  // kernels per replay
     unsigned long long used = 0;      // last use (replacement order)
     long long replays = 0;            // launches after the capture
@@ -195,6 +196,9 @@ struct Plan {
     unsigned long long tick = 0;
   };
   mutable SolveGraphs graphs;
+  // iterations of the last converged solve: the length of the first chunk
+  // of iterations enqueued before the solve state is read (0: none yet)
+  mutable int last_iters = 0;
 };
 
 

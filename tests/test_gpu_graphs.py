@@ -5,7 +5,9 @@ graphs captured on the plan's private stream. The graph solves must be
 bitwise the direct solves (same kernels, same order; the direct path is
 forced by per-launch event timing), count the same kernel launches, follow
 a change of f, of u and of the launch geometry, and handle an iteration cap
-that is not a multiple of the chunk."""
+that is not a multiple of the chunk. A solve's first chunk runs as many
+iterations as the plan's last converged solve took, so repeated solves
+enqueue no iterations past convergence."""
 
 import numpy as np
 import pytest
@@ -41,7 +43,16 @@ def test_graph_solves_bitwise_equal_direct(kw):
     plan = IFFDPlan(true_residual=False, **kw)
     f = torch.from_numpy(inputs.rhs(plan.shape, "normal", seed=1700 + kw["n"])).cuda()
     u = plan.empty()
-    ud, idir, nd = _direct(plan, f, u)
+    ud, idir, n_cold = _direct(plan, f, u)
+    # the first chunk of a later solve runs as many iterations as this one
+    # took, so no iteration is enqueued past convergence
+    ud2, _, nd = _direct(plan, f, u)
+    assert torch.equal(ud2, ud)
+    surplus = (-idir["iters"]) % 4  # iterations past convergence in chunks of 4
+    if surplus:
+        assert nd < n_cold and (n_cold - nd) % surplus == 0
+    else:
+        assert nd == n_cold
     for _ in range(3):  # the first of these records (f, u), the second captures, the third replays
         u.fill_(float("nan"))
         n0 = plan.launch_count()
