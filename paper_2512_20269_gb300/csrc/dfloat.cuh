@@ -202,7 +202,7 @@ __host__ __device__ __forceinline__ df to_df(double x) {
   const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
   const unsigned sign = h32 & 0x80000000u;
   const int fe = (int)((h32 >> 20) & 0x7FFu) - 896;  // float exponent field of hi
-  if ((b << 1) == 0) return {float_of(sign), 0.f};
+  if (((h32 << 1) | l32) == 0) return {float_of(sign), 0.f};  // +-0, tested on the 32-bit halves
   if (fe < 53 || fe > 254) {
 #ifdef __CUDA_ARCH__
     return to_df_fp64(x);

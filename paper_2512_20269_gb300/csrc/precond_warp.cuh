@@ -147,6 +147,30 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// Sums of V values (a power of two, V <= LS) of every lane over the LS lanes
+// of its sequence group, scattered over the lanes: the halving rounds send
+// half of a lane's values to its partner and keep the other half (V - 1
+// exchanges instead of V log2(LS)), the remaining rounds exchange the single
+// value left. Lane ls returns the group total of value ls / (LS / V).
+template <int LS, int V, typename T>
+__device__ __forceinline__ T group_sum_scatter(T (&v)[V], int ls) {
+  static_assert(V >= 1 && V <= LS && (V & (V - 1)) == 0, "V: a power of two up to LS");
+#pragma unroll
+  for (int H = V / 2, off = LS / 2; H >= 1; H /= 2, off /= 2) {
+    const bool upper = (ls & off) != 0;  // keeps the upper half of the values
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const T keep = upper ? v[H + i] : v[i];
+      const T send = upper ? v[i] : v[H + i];
+      v[i] = keep + shfl_xor(send, off);
+    }
+  }
+  T x = v[0];
+#pragma unroll
+  for (int off = LS / (2 * V); off > 0; off >>= 1) x += shfl_xor(x, off);
+  return x;
+}
+
 // V_reg row rule of the scatter (x_i = sum_j V_reg[i][j] w_j): edge blocks,
 // interior blocks, identity runs (see AxisTab).
 template <typename T, typename TT, typename WReg>
@@ -323,15 +347,34 @@ __device__ __forceinline__ void wtransform(T* tile, vec2_t<T>* wbuf, T* outv, co
       };
       rows(0, ax.wlo);
       rows(ax.whi, m);
+      // the lane sums of the (up to) 2 x 4 columns, reduced and scattered
+      // over the group's lanes in one set of exchanges (double-float and
+      // FP64, where an exchange and a sum cost several instructions); FP32,
+      // paired or not, sums every column over the group (measured faster
+      // there, and the paired pass keeps the unpaired order)
+      if constexpr (std::is_same<TT, float>::value) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k0 + k < nw) {
-          const T ya = group_sum<LS>(sa[k]), yb = group_sum<LS>(sb[k]);
-          if (ls == 0) {
-            ova[k0 + k] = ya;
-            ovb[k0 + k] = yb;
+        for (int k = 0; k < 4; ++k)
+          if (k0 + k < nw) {
+            const T ya = group_sum<LS>(sa[k]), yb = group_sum<LS>(sb[k]);
+            if (ls == 0) {
+              ova[k0 + k] = ya;
+              ovb[k0 + k] = yb;
+            }
           }
-        }
+      } else if (nw - k0 <= 2) {
+        T v[4] = {sa[0], sa[1], sb[0], sb[1]};
+        const T y = group_sum_scatter<LS, 4>(v, ls);
+        constexpr int S = LS / 4;
+        const int j = ls / S, k = j & 1;
+        if (ls % S == 0 && k0 + k < nw) (j < 2 ? ova : ovb)[k0 + k] = y;
+      } else {
+        T v[8] = {sa[0], sa[1], sa[2], sa[3], sb[0], sb[1], sb[2], sb[3]};
+        const T y = group_sum_scatter<LS, 8>(v, ls);
+        constexpr int S = LS / 8;
+        const int j = ls / S, k = j & 3;
+        if (ls % S == 0 && k0 + k < nw) (j < 4 ? ova : ovb)[k0 + k] = y;
+      }
     }
     // Makhoul order of u_i = (-1)^i y_i, y = V_reg^T r, as the first stage's
     // input: element l = j + q N/8 lies in the first half exactly when q < 4.
