@@ -247,14 +247,22 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, T* tile, 
   (void)LS; (void)G; (void)tid; (void)warp; (void)lane;
   // ---- coalesced tile load (padding pencils are zero)
   if (axis == 0) {
-    for (int pc = warp; pc < PP; pc += kThreads / 32) {
-      T* row = tile + pc * ldt;
-      if (pc < g.nvalid) {
-        const Tin* src = in + pbase[pc];
+    // two rows per warp at a time (rows pc and pc + 8): twice the loads in
+    // flight of one row
+    constexpr int W = kThreads / 32;
+    static_assert(PP % (2 * W) == 0, "rows come in pairs per warp");
+    for (int pc = warp; pc < PP; pc += 2 * W) {
+      T* row0 = tile + pc * ldt;
+      T* row1 = row0 + W * ldt;
+      const bool v0 = pc < g.nvalid, v1 = pc + W < g.nvalid;
+      const Tin* src0 = in + pbase[pc];
+      const Tin* src1 = in + pbase[pc + W];
 #pragma unroll 4
-        for (int i = lane; i < m; i += 32) row[i] = cvt<T>(src[i]);
-      } else {
-        for (int i = lane; i < m; i += 32) row[i] = T(0);
+      for (int i = lane; i < m; i += 32) {
+        const Tin a = v0 ? src0[i] : Tin(0);
+        const Tin b = v1 ? src1[i] : Tin(0);
+        row0[i] = cvt<T>(a);
+        row1[i] = cvt<T>(b);
       }
     }
   } else {
