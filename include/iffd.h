@@ -280,7 +280,14 @@ int iffd_apply_stiffness_noalloc(iffd_handle h, const double* u, double* Au, voi
  * f, u: device, N float64 each, must not alias; u is output only. info: HOST
  * pointer, filled on return (may be NULL). Synchronises `stream`. Returns
  * IFFD_OK, IFFD_ERR_NOT_CONVERGED or IFFD_ERR_BREAKDOWN (u then holds the last
- * iterate), or an argument / CUDA error. */
+ * iterate), or an argument / CUDA error.
+ * All PCG scalars stay on the device; the host enqueues the iterations in
+ * chunks and reads the solve state after each chunk (iterations enqueued past
+ * convergence return at once). The first chunk is as long as the plan's last
+ * converged solve, later chunks 4 iterations. A solve that repeats one of the
+ * plan's two previous (f, u, ws) triples replays its chunks from CUDA graphs
+ * captured on a private stream (bitwise the same kernels; not while per-launch
+ * event timing is on). */
 int iffd_pcg_solve(iffd_handle h, const double* f, double* u, void* ws, void* stream, iffd_pcg_info* info);
 
 /* ---- General coefficient (stiffness of -div(C(x) grad u), A != A^) ----
