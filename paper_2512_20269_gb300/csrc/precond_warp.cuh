@@ -733,7 +733,47 @@ __device__ __forceinline__ void wstore_tile(const T* tile, Tout* __restrict__ ou
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // ---- coalesced store (and the partial dot products of a PCG step)
   double d0 = 0.0, d1 = 0.0;
-  if (axis == 0) {
+  constexpr int kW = kThreads / 32, kIPR = (N + kMaxNout + 31) / 32;  // rows of a warp: PP / kW
+  constexpr bool kPrefetch = NDOT == 1 && !std::is_same<tab_t<T>, float>::value && (PP / kW) * kIPR <= 20;
+  if constexpr (kPrefetch) {
+    if (axis == 0) {
+      // double-float and FP64 (lengths 128, 256): every value of the dot
+      // vector this thread needs is loaded first (all in flight at once),
+      // then the store and the dot product run in the same order as below
+      constexpr int W = kW, RPW = PP / W, IPR = kIPR;
+      double rv[RPW][IPR];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int pc = warp + r * W;
+        const long long off = pbase[pc];
+#pragma unroll
+        for (int u = 0; u < IPR; ++u) {
+          const int i = lane + 32 * u;
+          rv[r][u] = (pc < g.nvalid && i < m) ? ldg(dotv0 + off + i) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int pc = warp + r * W;
+        if (pc < g.nvalid) {
+          const T* row = tile + pc * ldt;
+          Tout* dst = out + pbase[pc];
+#pragma unroll
+          for (int u = 0; u < IPR; ++u) {
+            const int i = lane + 32 * u;
+            if (i < m) {
+              const Tout v = cvt<Tout>(row[i]);
+              dst[i] = v;
+              d0 = fma(rv[r][u], cvt<double>(v), d0);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (kPrefetch && axis == 0) {
+    // stored above
+  } else if (axis == 0) {
     for (int pc = warp; pc < g.nvalid; pc += kThreads / 32) {
       const T* row = tile + pc * ldt;
       Tout* dst = out + pbase[pc];
