@@ -246,7 +246,34 @@ __device__ __forceinline__ void wload_tile(const Tin* __restrict__ in, T* tile, 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   (void)LS; (void)G; (void)tid; (void)warp; (void)lane;
   // ---- coalesced tile load (padding pencils are zero)
-  if (axis == 0) {
+  constexpr int kW = kThreads / 32, kIPR = (N + kMaxNout + 31) / 32;  // rows of a warp: PP / kW
+  constexpr bool kAll = std::is_same<T, df>::value && std::is_same<Tin, double>::value && (PP / kW) * kIPR <= 20;
+  if (kAll && axis == 0) {
+    // FP64 input of the double-float passes (lengths 128, 256): every value
+    // of the warp's rows is loaded first (all in flight at once), then
+    // converted and stored
+    constexpr int RPW = PP / kW, IPR = kIPR;
+    Tin v[RPW][IPR];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int pc = warp + r * kW;
+      const Tin* src = in + pbase[pc];
+#pragma unroll
+      for (int u = 0; u < IPR; ++u) {
+        const int i = lane + 32 * u;
+        v[r][u] = (pc < g.nvalid && i < m) ? src[i] : Tin(0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      T* row = tile + (warp + r * kW) * ldt;
+#pragma unroll
+      for (int u = 0; u < IPR; ++u) {
+        const int i = lane + 32 * u;
+        if (i < m) row[i] = cvt<T>(v[r][u]);
+      }
+    }
+  } else if (axis == 0) {
     // two rows per warp at a time (rows pc and pc + 8): twice the loads in
     // flight of one row
     constexpr int W = kThreads / 32;
